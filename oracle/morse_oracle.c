@@ -1,0 +1,591 @@
+/*
+ * Plain, slow, FP64 CPU oracle for the MORSE hot path (McDougall & Albrow,
+ * "MORSE code for GPUs", MNRAS 2015).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant with the CUDA library; the two are independent
+ * statements of the same mathematics.
+ *
+ * Every function follows the plain definition of what it computes, one ray /
+ * one epoch / one trajectory at a time, with no blocking, fusion or
+ * reordering:
+ *
+ *   lens geometry ........ §4.1 (origin at the centre of mass, masses on the
+ *                          first axis) and §3 Eq. 2 (mass fractions eps_k)
+ *   inverse ray shooting .. §3 (ray-shooting magnification maps) and §5
+ *                          (inverse ray shooting); binned on the uniform
+ *                          source grid of §4.1
+ *   quintic + roots ....... §3 (inversion of Eq. 2 gives a fifth-order
+ *                          polynomial with 3 or 5 image solutions); roots by
+ *                          Laguerre's method with deflation and polishing
+ *   magnification ......... §3 Eq. 3-4 (A_j = 1/det J, J = d zeta / d z,
+ *                          total = sum over images; absolute value taken)
+ *   Paczynski curve ....... §4.3 (ii) single-lens light curve
+ *   map lookup ............ §4.2 (bilinear interpolation of the map at the
+ *                          source position of each data point)
+ *   flux model + fit ...... §4.1 Eq. 5-6 (F = Fs A + Fb, linear in A), chi^2
+ *                          as the sum of per-data-point contributions (§4.2)
+ *   seeds (top-K) ......... §4.4 (best local minima of the coarse search)
+ *
+ * Readings where the paper is silent (all mirrored by the CUDA path and
+ * listed in the design notes): cell-centred image rays; half-open source
+ * bins [-L, L); q = m2/m1 with the primary at -s q/(1+q); outside the map
+ * the magnification is the Paczynski A(|y|) about the centre of mass; the
+ * degenerate-fit rule; top-K order by (chi^2, index).
+ *
+ * Parity pins: every function here is pinned by a CPU test against closed
+ * forms, invariants or brute force (Witt-Mao sum, q->0 Paczynski limit,
+ * equal-mass on-axis closed form, ray conservation and mirror symmetry,
+ * least-squares by QR, argmin by exhaustive search).
+ *
+ * Build: gcc -O2 -ffp-contract=off -fno-fast-math -fopenmp -shared -fPIC.
+ * FMA contraction must stay off: the ray-shooting counts are compared
+ * bit-for-bit with the GPU's FP64 path.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+/* ------------------------------------------------------------------ */
+/* Lens geometry (§4.1, §3 Eq. 2)                                       */
+/* ------------------------------------------------------------------ */
+
+/* q = m2/m1; eps1 = 1/(1+q), eps2 = q/(1+q); the origin is the centre of
+ * mass, so the primary sits at -s*eps2 and the secondary at +s*eps1. */
+void orc_lens(double s, double q, double *eps1, double *eps2, double *xa,
+              double *xb) {
+  double e1 = 1.0 / (1.0 + q);
+  double e2 = q / (1.0 + q);
+  *eps1 = e1;
+  *eps2 = e2;
+  *xa = -(s * e2);
+  *xb = s * e1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Inverse ray shooting (§3, §5)                                        */
+/* ------------------------------------------------------------------ */
+
+/* Shoot nray x nray image-plane rays on the cell-centred grid over
+ * [-X, X]^2 through Eq. 2 (real form) and histogram them on the npix x npix
+ * source grid over [-L, L)^2.  counts is row-major, second source
+ * coordinate major: counts[iy*npix + ix].  Rays landing outside the map are
+ * counted in off_map; rays exactly on a lens are counted in lost.
+ * nthreads > 1 splits image rows over OpenMP threads with private
+ * histograms (integer sums: identical result for any thread count). */
+int orc_rayshoot(double s, double q, double L, int npix, long long nray,
+                 double X, uint32_t *counts, uint64_t *off_map, uint64_t *lost,
+                 int nthreads) {
+  if (npix <= 0 || nray <= 0 || !(L > 0.0) || !(X > 0.0)) return -1;
+  double e1, e2, xa, xb;
+  orc_lens(s, q, &e1, &e2, &xa, &xb);
+  double h = (2.0 * X) / (double)nray;
+  double dlt = (2.0 * L) / (double)npix;
+  size_t nbin = (size_t)npix * (size_t)npix;
+  memset(counts, 0, nbin * sizeof(uint32_t));
+  uint64_t off_total = 0, lost_total = 0;
+  if (nthreads < 1) nthreads = 1;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads) reduction(+ : off_total, lost_total)
+#endif
+  {
+    uint32_t *mine = counts;
+    int tid = 0, nth = 1;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+    nth = omp_get_num_threads();
+#endif
+    if (nth > 1) mine = (uint32_t *)calloc(nbin, sizeof(uint32_t));
+    for (long long j = tid; j < nray; j += nth) {
+      double x2 = -X + ((double)j + 0.5) * h;
+      for (long long i = 0; i < nray; ++i) {
+        double x1 = -X + ((double)i + 0.5) * h;
+        double d1x = x1 - xa;
+        double r1 = d1x * d1x + x2 * x2;
+        double d2x = x1 - xb;
+        double r2 = d2x * d2x + x2 * x2;
+        if (r1 == 0.0 || r2 == 0.0) {
+          lost_total += 1;
+          continue;
+        }
+        double y1 = x1 - e1 * d1x / r1 - e2 * d2x / r2;
+        double y2 = x2 - e1 * x2 / r1 - e2 * x2 / r2;
+        double v1 = (y1 + L) / dlt;
+        double v2 = (y2 + L) / dlt;
+        if (!(v1 >= 0.0 && v1 < (double)npix && v2 >= 0.0 &&
+              v2 < (double)npix)) {
+          off_total += 1;
+          continue;
+        }
+        long ix = (long)floor(v1);
+        long iy = (long)floor(v2);
+        mine[(size_t)iy * (size_t)npix + (size_t)ix] += 1u;
+      }
+    }
+    if (nth > 1) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+      {
+        for (size_t k = 0; k < nbin; ++k) counts[k] += mine[k];
+      }
+      free(mine);
+    }
+  }
+  *off_map = off_total;
+  *lost = lost_total;
+  return 0;
+}
+
+/* Map value = area-averaged magnification of the pixel: ray count times the
+ * image-plane area of a ray over the source-plane area of a pixel,
+ * A = n h^2 / Delta^2, evaluated in FP64 and rounded to FP32. */
+void orc_counts_to_mag(const uint32_t *counts, int npix, double L,
+                       long long nray, double X, float *A) {
+  double h = (2.0 * X) / (double)nray;
+  double dlt = (2.0 * L) / (double)npix;
+  double f = (h * h) / (dlt * dlt);
+  size_t nbin = (size_t)npix * (size_t)npix;
+  for (size_t k = 0; k < nbin; ++k) A[k] = (float)((double)counts[k] * f);
+}
+
+/* ------------------------------------------------------------------ */
+/* Fifth-order lens polynomial (§3)                                     */
+/* ------------------------------------------------------------------ */
+
+/* polynomials as coefficient arrays, c[k] multiplies z^k */
+static void pmul(const cplx *a, int na, const cplx *b, int nb, cplx *out) {
+  for (int k = 0; k <= na + nb; ++k) out[k] = 0.0;
+  for (int i = 0; i <= na; ++i)
+    for (int j = 0; j <= nb; ++j) out[i + j] += a[i] * b[j];
+}
+
+/* Build the quintic whose roots contain the images of source zeta.
+ * Conjugating Eq. 2 gives conj(z) = conj(zeta) + e1/(z-z1) + e2/(z-z2)
+ * = N(z)/D(z) with D = (z-z1)(z-z2), N = conj(zeta) D + e1 (z-z2) +
+ * e2 (z-z1).  Substituting back into Eq. 2, with conj(z) - z_k = P_k/D and
+ * P_k = N - z_k D, and clearing denominators:
+ *     (zeta - z) P1 P2 + e1 D P2 + e2 D P1 = 0.
+ * c[0..5] receive the coefficients.  Returns -1 if the leading coefficient
+ * vanishes (source exactly on a lens). */
+int orc_quintic(double s, double q, double y1, double y2, double *cre,
+                double *cim) {
+  double e1, e2, xa, xb;
+  orc_lens(s, q, &e1, &e2, &xa, &xb);
+  cplx zeta = y1 + I * y2;
+  cplx zc = conj(zeta);
+  cplx D[3], Nn[3], P1[3], P2[3], lin[2], a[6], b[6], c6[6];
+  /* D = z^2 - (z1+z2) z + z1 z2 */
+  D[0] = xa * xb;
+  D[1] = -(xa + xb);
+  D[2] = 1.0;
+  for (int k = 0; k < 3; ++k) Nn[k] = zc * D[k];
+  /* + e1 (z - z2) + e2 (z - z1) */
+  Nn[0] += -e1 * xb - e2 * xa;
+  Nn[1] += e1 + e2;
+  for (int k = 0; k < 3; ++k) {
+    P1[k] = Nn[k] - xa * D[k];
+    P2[k] = Nn[k] - xb * D[k];
+  }
+  /* (zeta - z) P1 P2 */
+  {
+    cplx p12[5];
+    pmul(P1, 2, P2, 2, p12);
+    lin[0] = zeta;
+    lin[1] = -1.0;
+    pmul(lin, 1, p12, 4, a); /* degree 5 */
+  }
+  /* e1 D P2 + e2 D P1 */
+  {
+    cplx dp2[5], dp1[5];
+    pmul(D, 2, P2, 2, dp2);
+    pmul(D, 2, P1, 2, dp1);
+    for (int k = 0; k < 6; ++k) b[k] = 0.0;
+    for (int k = 0; k < 5; ++k) b[k] = e1 * dp2[k] + e2 * dp1[k];
+  }
+  for (int k = 0; k < 6; ++k) c6[k] = a[k] + b[k];
+  for (int k = 0; k < 6; ++k) {
+    cre[k] = creal(c6[k]);
+    cim[k] = cimag(c6[k]);
+  }
+  return (cabs(c6[5]) == 0.0) ? -1 : 0;
+}
+
+/* One root of sum_k a[k] z^k (degree m) by Laguerre's method, starting from
+ * *x.  Laguerre step: with G = p'/p and H = G^2 - p''/p,
+ *     dx = m / (G +- sqrt((m-1)(m H - G^2))),
+ * sign chosen to make the denominator largest.  A stalled iteration is
+ * nudged by a fractional step every tenth iteration. */
+static int laguerre(const cplx *a, int m, cplx *x) {
+  static const double frac[] = {0.0, 0.5, 0.25, 0.75, 0.13, 0.38,
+                                0.62, 0.88, 1.0};
+  const double eps = 1e-15;
+  for (int it = 1; it <= 80; ++it) {
+    cplx p = a[m], dp = 0.0, ddp = 0.0; /* ddp accumulates p''/2 */
+    double err = cabs(p), ax = cabs(*x);
+    for (int j = m - 1; j >= 0; --j) {
+      ddp = (*x) * ddp + dp;
+      dp = (*x) * dp + p;
+      p = (*x) * p + a[j];
+      err = cabs(p) + ax * err;
+    }
+    if (cabs(p) <= eps * err) return it; /* at the rounding floor */
+    cplx G = dp / p;
+    cplx H = G * G - 2.0 * ddp / p;
+    cplx sq = csqrt((double)(m - 1) * ((double)m * H - G * G));
+    cplx gp = G + sq, gm = G - sq;
+    double ap = cabs(gp), am = cabs(gm);
+    if (ap < am) {
+      gp = gm;
+      ap = am;
+    }
+    cplx dx = (ap > 0.0) ? (double)m / gp
+                         : (1.0 + ax) * (cos((double)it) + I * sin((double)it));
+    cplx x1 = *x - dx;
+    if (x1 == *x) return it;
+    if (it % 10 != 0)
+      *x = x1;
+    else
+      *x = *x - frac[(it / 10) % 9] * dx;
+  }
+  return -1;
+}
+
+/* All 5 roots: Laguerre on the deflated polynomial from z = 0, synthetic
+ * division after each root, then each root polished on the full polynomial. */
+int orc_roots5(const double *cre, const double *cim, double *rre,
+               double *rim) {
+  cplx a[6], d[6], r[5];
+  for (int k = 0; k < 6; ++k) a[k] = d[k] = cre[k] + I * cim[k];
+  for (int m = 5; m >= 1; --m) {
+    cplx x = 0.0;
+    laguerre(d, m, &x);
+    r[m - 1] = x;
+    /* divide d by (z - x) */
+    cplx carry = d[m];
+    for (int j = m - 1; j >= 0; --j) {
+      cplx t = d[j];
+      d[j] = carry;
+      carry = t + x * carry;
+    }
+  }
+  for (int k = 0; k < 5; ++k) laguerre(a, 5, &r[k]);
+  for (int k = 0; k < 5; ++k) {
+    rre[k] = creal(r[k]);
+    rim[k] = cimag(r[k]);
+  }
+  return 0;
+}
+
+/* zeta(z) from Eq. 2 with real lens positions */
+static cplx lens_map(cplx z, double e1, double e2, double xa, double xb) {
+  cplx zc = conj(z);
+  return z - e1 / (zc - xa) - e2 / (zc - xb);
+}
+
+/* det J = 1 - |d zeta / d conj(z)|^2 with d zeta/d conj(z) =
+ * sum_k eps_k / (conj(z) - z_k)^2  (Eq. 4) */
+static double detj(cplx z, double e1, double e2, double xa, double xb) {
+  cplx zc = conj(z);
+  cplx dz = e1 / ((zc - xa) * (zc - xa)) + e2 / ((zc - xb) * (zc - xb));
+  double m = cabs(dz);
+  return 1.0 - m * m;
+}
+
+/* Newton's method on Eq. 2 itself, from a root of the quintic.  With
+ * f = zeta(z) - zeta and d = d zeta / d conj(z), a step dz solves
+ * f + dz + d conj(dz) = 0, i.e. dz = (d conj(f) - f) / (1 - |d|^2).
+ * Keeps the iterate of smallest residual.  This sharpens images next to a
+ * low-mass lens, where the quintic's coefficients lose digits. */
+static cplx newton_polish(cplx z, cplx zeta, double e1, double e2, double xa,
+                          double xb, double *res_out) {
+  cplx best = z;
+  double best_res = cabs(lens_map(z, e1, e2, xa, xb) - zeta);
+  for (int it = 0; it < 30 && best_res > 0.0; ++it) {
+    cplx zc = conj(z);
+    cplx f = lens_map(z, e1, e2, xa, xb) - zeta;
+    cplx d = e1 / ((zc - xa) * (zc - xa)) + e2 / ((zc - xb) * (zc - xb));
+    double den = 1.0 - creal(d * conj(d));
+    if (den == 0.0 || !isfinite(den)) break;
+    cplx dz = (d * conj(f) - f) / den;
+    z = z + dz;
+    double r = cabs(lens_map(z, e1, e2, xa, xb) - zeta);
+    if (!(r < best_res)) {
+      if (!(r <= 2.0 * best_res)) break; /* diverging: keep the best */
+    } else {
+      best = z;
+      best_res = r;
+    }
+  }
+  *res_out = best_res;
+  return best;
+}
+
+/* Images of a point source at (y1, y2): the quintic's roots, each polished
+ * by Newton on Eq. 2, ranked by their relative Eq. 2 residual
+ * (a root that lands on an image already taken counts as spurious).  The
+ * images are the roots that satisfy Eq. 2 to tol: 3 or 5 of them (§3).
+ * For q below ~1e-7 the faint image next to the secondary sits closer to
+ * it than FP64 resolves and only 2 are returned; its magnification is of
+ * order q^2 and is dropped.  Outputs are ordered by residual.  Returns the
+ * image count, or -1 on failure. */
+int orc_images(double s, double q, double y1, double y2, double tol,
+               double *zre, double *zim, double *dj, double *resid) {
+  double cre[6], cim[6], rre[5], rim[5];
+  double e1, e2, xa, xb;
+  if (orc_quintic(s, q, y1, y2, cre, cim) != 0) return -1;
+  orc_roots5(cre, cim, rre, rim);
+  orc_lens(s, q, &e1, &e2, &xa, &xb);
+  cplx zeta = y1 + I * y2;
+  int order[5] = {0, 1, 2, 3, 4};
+  double res[5];
+  for (int k = 0; k < 5; ++k) {
+    cplx z = newton_polish(rre[k] + I * rim[k], zeta, e1, e2, xa, xb, &res[k]);
+    rre[k] = creal(z);
+    rim[k] = cimag(z);
+  }
+  for (int k = 0; k < 5; ++k) /* duplicates: keep the first, drop the rest */
+    for (int j = 0; j < k; ++j)
+      if (cabs((rre[k] + I * rim[k]) - (rre[j] + I * rim[j])) <=
+          1e-9 * (1.0 + cabs(rre[j] + I * rim[j])))
+        res[k] = INFINITY;
+  /* a residual is judged against the size of the terms that Eq. 2 sums,
+   * |z| + |zeta| + sum_k eps_k/|z - z_k|, so that an image next to a lens
+   * (large, cancelling terms) is held to the same relative precision */
+  double scale[5];
+  for (int k = 0; k < 5; ++k) {
+    cplx z = rre[k] + I * rim[k];
+    scale[k] = cabs(z) + cabs(zeta) + e1 / cabs(z - xa) + e2 / cabs(z - xb);
+    if (isfinite(res[k])) res[k] = res[k] / scale[k];
+  }
+  for (int i = 1; i < 5; ++i) /* insertion sort by residual */
+    for (int j = i; j > 0 && res[order[j]] < res[order[j - 1]]; --j) {
+      int t = order[j];
+      order[j] = order[j - 1];
+      order[j - 1] = t;
+    }
+  int n = 0;
+  while (n < 5 && res[order[n]] < tol) ++n;
+  for (int k = 0; k < 5; ++k) {
+    int o = order[k];
+    zre[k] = rre[o];
+    zim[k] = rim[o];
+    resid[k] = res[o];
+    dj[k] = detj(rre[o] + I * rim[o], e1, e2, xa, xb);
+  }
+  return n;
+}
+
+/* Point-source magnification, sum over images of 1/|det J| (Eq. 3). */
+double orc_mag_point(double s, double q, double y1, double y2, int *nimg) {
+  double zre[5], zim[5], dj[5], res[5];
+  int n = orc_images(s, q, y1, y2, 1e-9, zre, zim, dj, res);
+  if (nimg) *nimg = n;
+  if (n < 0) return NAN;
+  double A = 0.0;
+  for (int k = 0; k < n; ++k) A += 1.0 / fabs(dj[k]);
+  return A;
+}
+
+/* Single-lens (Paczynski) magnification A(u) = (u^2+2)/(u sqrt(u^2+4)). */
+double orc_pspl(double u) {
+  return (u * u + 2.0) / (u * sqrt(u * u + 4.0));
+}
+
+/* ------------------------------------------------------------------ */
+/* Map lookup along a straight trajectory (§4.2)                        */
+/* ------------------------------------------------------------------ */
+
+/* Source position at time t: tau = (t - t0)/tE, moving along angle alpha
+ * from the lens axis with closest approach u0 to the centre of mass. */
+void orc_traj_point(double t, double t0, double tE, double u0, double alpha,
+                    double *y1, double *y2) {
+  double tau = (t - t0) / tE;
+  double ca = cos(alpha), sa = sin(alpha);
+  *y1 = tau * ca - u0 * sa;
+  *y2 = tau * sa + u0 * ca;
+}
+
+/* Bilinear interpolation between texel centres (texel (i,j) centred at
+ * -L + (i+1/2) Delta).  Coordinates are clamped to the outermost texel
+ * centres.  Outside the map (|y1| >= L or |y2| >= L) the Paczynski
+ * magnification at |y| about the centre of mass is used. */
+double orc_map_A(const float *A, int npix, double L, double y1, double y2) {
+  if (fabs(y1) >= L || fabs(y2) >= L) return orc_pspl(sqrt(y1 * y1 + y2 * y2));
+  double dlt = (2.0 * L) / (double)npix;
+  double px = (y1 + L) / dlt - 0.5;
+  double py = (y2 + L) / dlt - 0.5;
+  double hi = (double)(npix - 1);
+  if (px < 0.0) px = 0.0;
+  if (px > hi) px = hi;
+  if (py < 0.0) py = 0.0;
+  if (py > hi) py = hi;
+  long i0 = (long)floor(px), j0 = (long)floor(py);
+  if (i0 > npix - 2) i0 = npix - 2;
+  if (j0 > npix - 2) j0 = npix - 2;
+  if (i0 < 0) i0 = 0; /* npix == 1 */
+  if (j0 < 0) j0 = 0;
+  double fx = px - (double)i0, fy = py - (double)j0;
+  long i1 = (i0 + 1 < npix) ? i0 + 1 : i0, j1 = (j0 + 1 < npix) ? j0 + 1 : j0;
+  double a00 = A[j0 * npix + i0], a10 = A[j0 * npix + i1];
+  double a01 = A[j1 * npix + i0], a11 = A[j1 * npix + i1];
+  return (1.0 - fy) * ((1.0 - fx) * a00 + fx * a10) +
+         fy * ((1.0 - fx) * a01 + fx * a11);
+}
+
+/* ------------------------------------------------------------------ */
+/* Linear flux fit and chi^2 (§4.1 Eq. 5-6, §4.2)                       */
+/* ------------------------------------------------------------------ */
+
+/* Given magnifications A[i] at the epochs, the weighted least-squares
+ * (Fs, Fb) of F = Fs A + Fb (normal equations, closed form) and the chi^2
+ * as the sum of per-point contributions w (F - Fs A - Fb)^2.
+ * Degenerate rule: if det <= 1e-12 S_AA S_1 (A constant along the track)
+ * then Fs = 0, Fb = S_F / S_1 and flag = 1. */
+double orc_fit_A(const double *A, const double *F, const double *w, long n,
+                 double *Fs, double *Fb, int *flag) {
+  double S1 = 0, SA = 0, SAA = 0, SF = 0, SAF = 0;
+  for (long i = 0; i < n; ++i) {
+    S1 += w[i];
+    SA += w[i] * A[i];
+    SAA += w[i] * A[i] * A[i];
+    SF += w[i] * F[i];
+    SAF += w[i] * A[i] * F[i];
+  }
+  double det = SAA * S1 - SA * SA;
+  double fs, fb;
+  int fl = 0;
+  if (!(det > 1e-12 * SAA * S1)) {
+    fs = 0.0;
+    fb = SF / S1;
+    fl = 1;
+  } else {
+    fs = (S1 * SAF - SA * SF) / det;
+    fb = (SAA * SF - SA * SAF) / det;
+  }
+  double chi2 = 0.0;
+  for (long i = 0; i < n; ++i) {
+    double r = F[i] - fs * A[i] - fb;
+    chi2 += w[i] * r * r;
+  }
+  if (Fs) *Fs = fs;
+  if (Fb) *Fb = fb;
+  if (flag) *flag = fl;
+  return chi2;
+}
+
+/* Grid axis values: linear lo + (hi-lo) i/(n-1), or logarithmic
+ * lo (hi/lo)^(i/(n-1)); n == 1 gives lo. */
+void orc_axis(double lo, double hi, int n, int logsp, double *out) {
+  for (int i = 0; i < n; ++i) {
+    double f = (n > 1) ? (double)i / (double)(n - 1) : 0.0;
+    out[i] = logsp ? exp(log(lo) + (log(hi) - log(lo)) * f) : lo + (hi - lo) * f;
+  }
+}
+
+/* Trajectory index = ((i_u0 * n_alpha + i_alpha) * n_t0 + i_t0) * n_tE +
+ * i_tE; alpha_k = 2 pi k / n_alpha. */
+void orc_traj_params(const double *u0v, int nu, int na, const double *t0v,
+                     int nt0, const double *tEv, int ntE, long long idx,
+                     double *t0, double *tE, double *u0, double *alpha) {
+  long long itE = idx % ntE;
+  long long r = idx / ntE;
+  long long it0 = r % nt0;
+  r /= nt0;
+  long long ia = r % na;
+  long long iu = r / na;
+  (void)nu;
+  *t0 = t0v[it0];
+  *tE = tEv[itE];
+  *u0 = u0v[iu];
+  *alpha = 2.0 * M_PI * (double)ia / (double)na;
+}
+
+/* Dense chi^2 over the whole (u0, alpha, t0, tE) grid on a map (mode 0) or
+ * on the point-source polynomial magnification (mode 1, s and q used).
+ * chi2/Fs/Fb/flag receive one entry per trajectory index. */
+int orc_grid_chi2(const float *Amap, int npix, double L, double s, double q,
+                  int mode, const double *t, const double *F, const double *w,
+                  long n, const double *u0v, int nu, int na, const double *t0v,
+                  int nt0, const double *tEv, int ntE, long long first,
+                  long long count, double *chi2, double *Fs, double *Fb,
+                  int *flag, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  long long total = (long long)nu * na * nt0 * ntE;
+  if (first < 0 || first + count > total) return -1;
+  int bad = 0;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads) reduction(| : bad)
+#endif
+  {
+    double *A = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+    for (long long k = 0; k < count; ++k) {
+      double t0, tE, u0, al;
+      orc_traj_params(u0v, nu, na, t0v, nt0, tEv, ntE, first + k, &t0, &tE,
+                      &u0, &al);
+      for (long i = 0; i < n; ++i) {
+        double y1, y2;
+        orc_traj_point(t[i], t0, tE, u0, al, &y1, &y2);
+        if (mode == 0)
+          A[i] = orc_map_A(Amap, npix, L, y1, y2);
+        else
+          A[i] = orc_mag_point(s, q, y1, y2, NULL);
+      }
+      double fs, fb;
+      int fl;
+      chi2[k] = orc_fit_A(A, F, w, n, &fs, &fb, &fl);
+      if (Fs) Fs[k] = fs;
+      if (Fb) Fb[k] = fb;
+      if (flag) flag[k] = fl;
+      if (!isfinite(chi2[k])) bad = 1;
+    }
+    free(A);
+  }
+  return bad ? 1 : 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Seeds: the K best trajectories (§4.4) by a full sort on (chi^2, idx)  */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  double c;
+  long long i;
+} orc_key;
+
+static int cmp_key(const void *a, const void *b) {
+  const orc_key *x = (const orc_key *)a, *y = (const orc_key *)b;
+  if (x->c < y->c) return -1;
+  if (x->c > y->c) return 1;
+  return (x->i < y->i) ? -1 : (x->i > y->i);
+}
+
+/* idx_out receives the k smallest (chi2[j], first + j) in ascending order. */
+int orc_topk(const double *chi2, long long count, long long first, int k,
+             long long *idx_out, double *chi2_out) {
+  orc_key *keys = (orc_key *)malloc((size_t)count * sizeof(orc_key));
+  if (!keys) return -1;
+  for (long long j = 0; j < count; ++j) {
+    keys[j].c = chi2[j];
+    keys[j].i = first + j;
+  }
+  qsort(keys, (size_t)count, sizeof(orc_key), cmp_key);
+  int m = (k < count) ? k : (int)count;
+  for (int j = 0; j < m; ++j) {
+    idx_out[j] = keys[j].i;
+    chi2_out[j] = keys[j].c;
+  }
+  free(keys);
+  return m;
+}

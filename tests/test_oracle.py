@@ -1,0 +1,351 @@
+"""Pins for the CPU oracle against what the paper and the mathematics fix.
+
+None of these tests compares the oracle with itself or with the CUDA path.
+Each one checks a closed form, an invariant, a special case that reduces to
+a textbook routine, or brute force, chosen so that a plausible slip in the
+oracle (a dropped term, a wrong sign or index, a transposed operand) fails:
+
+* equal-mass lens, source at the origin: images and magnification in closed
+  form (derived below from Eq. 2 with z on the real / imaginary axis);
+* every returned image satisfies Eq. 2; the count is 3 or 5 (§3);
+* five-image sources: signed magnifications sum to 1 (Witt & Mao 1995);
+* q -> 0: the Paczynski curve (§4.3 (ii));
+* ray shooting: ray conservation, mirror symmetry about the lens axis,
+  thread-count invariance, and agreement with the pixel-averaged polynomial
+  magnification and (q = 0) with the pixel-averaged Paczynski curve;
+* bilinear lookup: reproduces a plane exactly (pins orientation and the
+  half-texel offset), texel-centre values, the outside rule;
+* trajectory geometry: closest approach u0 at t0, direction alpha;
+* linear fit: equals weighted least squares by QR; chi^2 is a minimum;
+* grid search: self-consistent injection recovers the injected index.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+import synth
+
+
+# ------------------------------------------------------------ lens polynomial
+def equal_mass_origin(s):
+    """Closed form for q = 1, source at the origin (lenses at +-s/2, eps=1/2).
+
+    z = x real:  x - x/(x^2 - s^2/4) = 0  ->  x = 0 or x^2 = 1 + s^2/4.
+    z = i y:     y - y/(y^2 + s^2/4) = 0  ->  y = 0 or y^2 = 1 - s^2/4.
+    d = sum eps_k/(conj z - z_k)^2 is 4/s^2 at 0, 1 + s^2/2 on the real
+    pair and s^2/2 - 1 on the imaginary pair; det J = 1 - |d|^2.
+    """
+    imgs = [(0.0, 1.0 - 16.0 / s ** 4)]
+    x = math.sqrt(1.0 + s * s / 4.0)
+    imgs += [(x, 1.0 - (1.0 + s * s / 2.0) ** 2),
+             (-x, 1.0 - (1.0 + s * s / 2.0) ** 2)]
+    if s < 2.0:
+        y = math.sqrt(1.0 - s * s / 4.0)
+        imgs += [(1j * y, 1.0 - (s * s / 2.0 - 1.0) ** 2),
+                 (-1j * y, 1.0 - (s * s / 2.0 - 1.0) ** 2)]
+    return imgs
+
+
+@pytest.mark.parametrize("s", [0.5, 0.8, 1.0, 1.5, 1.9, 2.5, 4.0])
+def test_equal_mass_closed_form(s):
+    ref = equal_mass_origin(s)
+    n, z, dj, res = orc.images(s, 1.0, 0.0, 0.0)
+    assert n == len(ref)
+    A_ref = sum(1.0 / abs(d) for _, d in ref)
+    assert orc.mag_point(s, 1.0, 0.0, 0.0) == pytest.approx(A_ref, rel=1e-12)
+    for zr, dr in ref:
+        k = int(np.argmin(np.abs(z[:n] - zr)))
+        assert abs(z[k] - zr) < 1e-12
+        assert dj[k] == pytest.approx(dr, rel=1e-10, abs=1e-12)
+
+
+def _lens_residual(s, q, z, zeta):
+    e1, e2, xa, xb = orc.lens(s, q)
+    zc = np.conj(z)
+    return abs(z - e1 / (zc - xa) - e2 / (zc - xb) - zeta)
+
+
+def test_lens_geometry():
+    e1, e2, xa, xb = orc.lens(1.2, 0.25)
+    assert e1 + e2 == pytest.approx(1.0)
+    assert e2 / e1 == pytest.approx(0.25)
+    assert xb - xa == pytest.approx(1.2)          # separation s
+    assert e1 * xa + e2 * xb == pytest.approx(0.0, abs=1e-15)  # CoM origin
+    assert xa < 0 < xb                            # primary on -x
+
+
+@pytest.mark.parametrize("q", [1.0, 0.1, 1e-3, 1e-5])
+@pytest.mark.parametrize("s", [0.3, 0.7, 1.0, 1.6, 3.0])
+def test_images_solve_lens_equation(s, q):
+    rng = np.random.default_rng(12345)
+    for _ in range(40):
+        y1, y2 = rng.uniform(-1.5, 1.5, 2)
+        n, z, dj, res = orc.images(s, q, y1, y2)
+        assert n in (3, 5)
+        for k in range(n):
+            r = _lens_residual(s, q, z[k], y1 + 1j * y2)
+            scale = abs(z[k]) + math.hypot(y1, y2) + 1.0 / min(
+                abs(z[k] - orc.lens(s, q)[2]), abs(z[k] - orc.lens(s, q)[3]))
+            assert r <= 1e-10 * scale
+        # quintic vanishes at every image
+        c = orc.quintic(s, q, y1, y2)
+        for k in range(n):
+            pz = np.polyval(c[::-1], z[k])
+            mag = np.polyval(np.abs(c[::-1]), abs(z[k]))
+            assert abs(pz) <= 1e-9 * mag
+
+
+def test_witt_mao_five_images():
+    """Inside the caustic (5 images) the signed magnifications sum to 1."""
+    rng = np.random.default_rng(7)
+    seen = 0
+    for q in (1.0, 0.3, 1e-2, 1e-3):
+        for s in (0.6, 0.9, 1.0, 1.2):
+            for _ in range(200):
+                y1, y2 = rng.uniform(-0.3, 0.3, 2)
+                n, z, dj, res = orc.images(s, q, y1, y2)
+                if n == 5:
+                    seen += 1
+                    assert np.sum(1.0 / dj[:5]) == pytest.approx(1.0,
+                                                                 abs=1e-8)
+    assert seen > 50
+
+
+@pytest.mark.parametrize("u", [0.05, 0.2, 0.7, 1.0, 1.8])
+@pytest.mark.parametrize("s,q", [(1.0, 1e-10), (10.0, 1e-8)])
+def test_q_to_zero_is_paczynski(u, s, q):
+    """A planet of mass ratio q perturbs the single-lens curve by O(q); at
+    q = 1e-10 on the Einstein ring, or 1e-8 far away, the Paczynski curve
+    about the primary holds to 1e-6."""
+    e1, e2, xa, xb = orc.lens(s, q)
+    for ang in (0.3, 1.9, 4.0):
+        y1 = xa + u * math.cos(ang)
+        y2 = u * math.sin(ang)
+        A = orc.mag_point(s, q, y1, y2)
+        assert A == pytest.approx(orc.pspl(u), rel=1e-6)
+
+
+def test_paczynski_closed_forms():
+    assert orc.pspl(1.0) == pytest.approx(3.0 / math.sqrt(5.0), rel=1e-15)
+    assert orc.pspl(1e-4) * 1e-4 == pytest.approx(1.0, rel=1e-7)
+    u = 30.0
+    assert orc.pspl(u) - 1.0 == pytest.approx(2.0 / u ** 4, rel=1e-2)
+
+
+# ------------------------------------------------------------ ray shooting
+def test_rayshoot_conservation_and_threads():
+    c1, off1, lost1 = orc.rayshoot(0.9, 5e-3, 1.5, 64, 1500, 3.0, nthreads=1)
+    c4, off4, lost4 = orc.rayshoot(0.9, 5e-3, 1.5, 64, 1500, 3.0, nthreads=4)
+    assert int(c1.sum(dtype=np.uint64)) + off1 + lost1 == 1500 * 1500
+    assert np.array_equal(c1, c4) and off1 == off4 and lost1 == lost4
+
+
+def test_rayshoot_lost_ray_on_lens():
+    # X = 0.75 with 3 rays per axis puts ray centres at -0.5, 0, 0.5;
+    # s = 1, q = 1 puts the lenses at (-0.5, 0) and (0.5, 0): exactly two
+    # rays sit on a lens and are counted as lost.
+    c, off, lost = orc.rayshoot(1.0, 1.0, 2.0, 8, 3, 0.75, nthreads=1)
+    assert lost == 2
+    assert int(c.sum()) + off + lost == 9
+
+
+def test_rayshoot_mirror_symmetry():
+    npix = 64
+    c, off, lost = orc.rayshoot(1.1, 0.02, 1.5, npix, 2000, 3.0, nthreads=4)
+    flip = c[::-1, :]
+    diff = np.abs(c.astype(np.int64) - flip.astype(np.int64)).sum()
+    # only rays whose y2 sits on a bin edge (to rounding) may differ
+    assert diff <= 1e-4 * c.sum()
+    # but the map is not symmetric in y1 (q != 1): pins the axis order
+    diffx = np.abs(c.astype(np.int64) - c[:, ::-1].astype(np.int64)).sum()
+    assert diffx > 0.01 * c.sum()
+
+
+def test_counts_to_mag_scale():
+    c = np.full((8, 8), 7, dtype=np.uint32)
+    A = orc.counts_to_mag(c, 1.0, 100, 2.0)
+    h = 4.0 / 100
+    d = 2.0 / 8
+    assert np.all(A == np.float32(7 * (h * h) / (d * d)))
+
+
+def _pixel_average(f, L, npix, sub):
+    dl = 2 * L / npix
+    P = np.zeros((npix, npix))
+    G = np.zeros((npix, npix))
+    for j in range(npix):
+        for i in range(npix):
+            v = np.array([f(-L + (i + (a + 0.5) / sub) * dl,
+                            -L + (j + (b + 0.5) / sub) * dl)
+                          for b in range(sub) for a in range(sub)])
+            P[j, i] = v.mean()
+            G[j, i] = v.max() / v.min()
+    return P, G
+
+
+def _smooth_mask(G, lim=1.3):
+    from scipy.ndimage import binary_erosion
+    return binary_erosion(G < lim, iterations=1)
+
+
+def test_map_matches_polynomial_away_from_caustics():
+    s, q, L, npix, nray, X = 1.0, 1e-2, 1.0, 32, 6000, 3.0
+    A, c, off, lost = orc.build_map(s, q, L, npix, nray, X, nthreads=8)
+    P, G = _pixel_average(lambda a, b: orc.mag_point(s, q, a, b), L, npix, 6)
+    m = _smooth_mask(G)
+    assert m.mean() > 0.5
+    rel = (A - P) / P
+    assert np.all(np.abs(rel[m]) <= 3.0 / np.sqrt(c[m]))
+    assert abs(np.sum((A - P)[m]) / np.sum(P[m])) < 1e-3
+    # the caustic region is where the two disagree most: the map is not
+    # simply the polynomial at pixel centres
+    assert np.max(np.abs(rel[~m])) > np.max(np.abs(rel[m]))
+
+
+def test_map_single_lens_is_paczynski():
+    L, npix, nray, X = 1.0, 24, 5000, 3.0
+    A, c, off, lost = orc.build_map(1.0, 0.0, L, npix, nray, X, nthreads=8)
+    P, G = _pixel_average(lambda a, b: orc.pspl(math.hypot(a, b)), L, npix, 8)
+    m = _smooth_mask(G, 1.2)
+    rel = (A - P) / P
+    assert np.all(np.abs(rel[m]) <= 3.0 / np.sqrt(c[m]))
+    assert abs(np.sum((A - P)[m]) / np.sum(P[m])) < 1e-3
+
+
+# ------------------------------------------------------------ lookup
+def test_lookup_reproduces_plane():
+    npix, L = 16, 2.0
+    jj, ii = np.meshgrid(np.arange(npix), np.arange(npix), indexing="ij")
+    A = (1.0 + 2.0 * ii + 3.0 * jj).astype(np.float32)   # A[j, i]
+    dl = 2 * L / npix
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        y1, y2 = rng.uniform(-L + dl / 2, L - dl / 2, 2)
+        px = (y1 + L) / dl - 0.5
+        py = (y2 + L) / dl - 0.5
+        assert orc.map_A(A, L, y1, y2) == pytest.approx(
+            1.0 + 2.0 * px + 3.0 * py, rel=1e-12)
+
+
+def test_lookup_texel_centres_edges_and_outside():
+    npix, L = 8, 1.0
+    rng = np.random.default_rng(4)
+    A = rng.uniform(0.5, 3.0, (npix, npix)).astype(np.float32)
+    dl = 2 * L / npix
+    for j in range(npix):
+        for i in range(npix):
+            y1 = -L + (i + 0.5) * dl
+            y2 = -L + (j + 0.5) * dl
+            assert orc.map_A(A, L, y1, y2) == pytest.approx(float(A[j, i]),
+                                                            rel=1e-12)
+    # within half a texel of the edge: clamped to the edge texel centre
+    assert orc.map_A(A, L, -L + 0.1 * dl, -L + 0.5 * dl) == pytest.approx(
+        float(A[0, 0]), rel=1e-12)
+    assert orc.map_A(A, L, L - 0.1 * dl, L - 0.2 * dl) == pytest.approx(
+        float(A[-1, -1]), rel=1e-12)
+    # outside: Paczynski about the centre of mass
+    for y in [(L, 0.0), (-L - 0.3, 0.2), (0.1, 1.5 * L)]:
+        assert orc.map_A(A, L, *y) == pytest.approx(
+            orc.pspl(math.hypot(*y)), rel=1e-14)
+
+
+def test_trajectory_geometry():
+    t0, tE, u0, al = 3.0, 12.0, 0.2, 0.9
+    y1, y2 = orc.traj_point(t0, t0, tE, u0, al)
+    assert math.hypot(y1, y2) == pytest.approx(u0, rel=1e-14)
+    # closest approach: position is perpendicular to the motion
+    assert y1 * math.cos(al) + y2 * math.sin(al) == pytest.approx(0, abs=1e-15)
+    # motion: one tE later the source moved by one unit along alpha
+    z1, z2 = orc.traj_point(t0 + tE, t0, tE, u0, al)
+    assert z1 - y1 == pytest.approx(math.cos(al), rel=1e-12)
+    assert z2 - y2 == pytest.approx(math.sin(al), rel=1e-12)
+    # counter-clockwise: the closest-approach point is alpha + 90 degrees
+    assert math.atan2(y2, y1) == pytest.approx(al + math.pi / 2, rel=1e-12)
+
+
+# ------------------------------------------------------------ linear fit
+def test_fit_equals_weighted_lstsq():
+    rng = np.random.default_rng(11)
+    n = 37
+    A = rng.uniform(1.0, 8.0, n)
+    w = rng.uniform(100.0, 1e4, n)
+    F = 0.7 * A + 0.4 + rng.normal(0, 1, n) / np.sqrt(w)
+    chi2, fs, fb, flag = orc.fit_A(A, F, w)
+    sw = np.sqrt(w)
+    M = np.stack([A * sw, sw], axis=1)
+    sol, *_ = np.linalg.lstsq(M, F * sw, rcond=None)
+    assert flag == 0
+    assert fs == pytest.approx(sol[0], rel=1e-10)
+    assert fb == pytest.approx(sol[1], rel=1e-10)
+    r = F - sol[0] * A - sol[1]
+    assert chi2 == pytest.approx(float(np.sum(w * r * r)), rel=1e-10)
+    for dfs, dfb in [(1e-4, 0), (-1e-4, 0), (0, 1e-4), (0, -1e-4)]:
+        rr = F - (fs + dfs) * A - (fb + dfb)
+        assert np.sum(w * rr * rr) > chi2
+
+
+def test_fit_degenerate_constant_magnification():
+    A = np.full(10, 2.5)
+    F = np.linspace(1.0, 2.0, 10)
+    w = np.arange(1, 11, dtype=float)
+    chi2, fs, fb, flag = orc.fit_A(A, F, w)
+    assert flag == 1 and fs == 0.0
+    assert fb == pytest.approx(np.sum(w * F) / np.sum(w), rel=1e-14)
+    assert chi2 == pytest.approx(float(np.sum(w * (F - fb) ** 2)), rel=1e-12)
+
+
+# ------------------------------------------------------------ grid search
+def test_axes():
+    a = orc.axis(1e-3, 0.5, 20, True)
+    assert a[0] == pytest.approx(1e-3) and a[-1] == pytest.approx(0.5)
+    assert np.allclose(np.diff(np.log(a)), np.log(500.0) / 19)
+    b = orc.axis(-2.0, 2.0, 10, False)
+    assert np.allclose(np.diff(b), 4.0 / 9)
+
+
+def test_grid_self_consistent_injection_recovers_index():
+    """A noiseless light curve made by map lookup at grid trajectory k*
+    gives chi^2 ~ 0 at k* and nowhere else (pins the index order)."""
+    L, npix = 2.0, 64
+    A, c, off, lost = orc.build_map(0.8, 0.05, L, npix, 1200, 3.0,
+                                    nthreads=4)
+    g = orc.Grid(3, 4, 3, 3, 0.05, 0.4, -1.0, 1.0, 8.0, 30.0)
+    t = synth.epoch_times(50, 5)
+    t = t[np.abs(t) < 25]
+    for kstar in (0, 17, g.size - 1, 58):
+        t0, tE, u0, al = g.params(kstar)
+        At = orc.lightcurve_map(A, L, t, t0, tE, u0, al)
+        F = 0.9 * At + 0.25
+        w = np.full(len(t), 1e4)
+        chi2, fs, fb, fl = orc.grid_chi2(g, t, F, w, A=A, L=L)
+        assert int(np.argmin(chi2)) == kstar
+        assert chi2[kstar] < 1e-12 * np.sum(w * F * F)
+        assert fs[kstar] == pytest.approx(0.9, rel=1e-9)
+        assert fb[kstar] == pytest.approx(0.25, rel=1e-8)
+        idx, val = orc.topk(chi2, 5)
+        assert idx[0] == kstar
+        # brute force: every listed chi^2 is the plain definition
+        for k in idx:
+            p = g.params(int(k))
+            Ak = orc.lightcurve_map(A, L, t, *p)
+            assert orc.fit_A(Ak, F, w)[0] == pytest.approx(chi2[k], rel=1e-12)
+
+
+def test_topk_order_and_ties():
+    chi2 = np.array([5.0, 1.0, 3.0, 1.0, 2.0, 3.0])
+    idx, val = orc.topk(chi2, 4, first=100)
+    assert list(idx) == [101, 103, 104, 102]
+    assert list(val) == [1.0, 1.0, 2.0, 3.0]
+
+
+def test_grid_polynomial_mode_matches_lightcurve():
+    g = orc.Grid(2, 3, 2, 2, 0.05, 0.3, -1.0, 1.0, 10.0, 20.0)
+    t = synth.epoch_times(40, 9)
+    F = 1.0 + 0.1 * np.cos(t)
+    w = np.full(len(t), 100.0)
+    chi2, fs, fb, fl = orc.grid_chi2(g, t, F, w, s=1.1, q=0.01)
+    for k in (0, 5, g.size - 1):
+        Ak = orc.lightcurve_point(1.1, 0.01, t, *g.params(k))
+        assert orc.fit_A(Ak, F, w)[0] == pytest.approx(chi2[k], rel=1e-12)
