@@ -1,0 +1,457 @@
+"""Benchmark of the MORSE hot path on GB300.
+
+Workload: the full (s, q) search of one event -- s 31 log-spaced in
+[0.3, 3], q 21 log-spaced in [1e-5, 1e-1] (651 maps), each map 1024 x 1024
+texels over [-2, 2]^2 from 10^4 x 10^4 FP32-deflected rays, a 3000-epoch
+light curve, 40 u0 x 72 alpha x 25 t0 x 20 tE = 1.44 M trajectories per
+map, top-K = 256.  One step = one (s, q) map of that sweep: ray shooting,
+counts -> texels, the trajectory chi^2 search, the top-K merge and the fit
+records.  Steps walk the (s, q) grid; under torchrun rank r takes maps
+r, r + N, ... (no collective on the data path, weak scaling).
+
+Metric: trajectory-epoch chi^2 evaluations per second (whole job).  Also
+reported: rays/s of the map build, the dominant kernel's roofline, the CPU
+oracle on a bounded sample, and the end-to-end rate through morse_search
+from host buffers.
+
+`--impl reference` times the CPU oracle (the plain FP64 definition) on the
+host cores, each step a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = ("trajectory-epoch chi^2 evals/s and rays/s (% of roofline); "
+          "time-to-best-fit vs plain")
+UNIT = "traj-epoch evals/s"
+# FP32 instructions one trajectory-epoch evaluation needs by its definition:
+# tau 1, y 2, pixel coords 2, floor/frac/convert 6, bilinear 6, normal-
+# equation sums 3, residual sweep 2.
+ALG_INSTR_PER_EVAL = 22
+FP32_LANES_PER_SM = 128
+KERNEL_SRC = os.path.join(ROOT, "paper_1511_01157_gb300", "csrc",
+                          "k_search.cu")
+PROFILE = os.path.join(ROOT, "profiles", "k_search_cfg1.md")
+
+
+def workload_config(cfg):
+    g = cfg["grid"]
+    return {
+        "workload": "full (s,q) search of one 3000-epoch event; one step = "
+                    "one (s,q) map of the 31x21 sweep",
+        "maps_total": cfg["n_s"] * cfg["n_q"], "maps_per_step": 1,
+        "npix": cfg["npix"], "extent": cfg["L"],
+        "rays_per_map": cfg["nray"] ** 2, "deflect": "fp32",
+        "epochs": cfg["n"],
+        "trajectories_per_map": g["n_u0"] * g["n_alpha"] * g["n_t0"] *
+        g["n_tE"], "top_k": cfg["top_k"],
+        "grid": f'{g["n_u0"]}u0 x {g["n_alpha"]}alpha x {g["n_t0"]}t0 x '
+                f'{g["n_tE"]}tE',
+        "l2": "flushed between steps (256 MB write); the 16 MB map texels "
+              "are produced inside each step and read from L2 by design",
+    }
+
+
+def sq_of(step, rank, world, cfg):
+    s_ax, q_ax = synth.sq_axes(cfg)
+    k = (step * world + rank) % (len(s_ax) * len(q_ax))
+    return float(s_ax[k // len(q_ax)]), float(q_ax[k % len(q_ax)])
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200",
+                 "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                rows.append((float(p[0]), float(p[1]), p[4], p[5], p[6],
+                             p[7]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown",
+                                "sw_thermal_slowdown", "sw_power_cap"),
+                               r[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(
+            r[1] for r in rows), "samples": len(rows),
+            "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the search kernel from the committed ncu
+    summary, valid only while the kernel source is unchanged."""
+    if not os.path.exists(PROFILE):
+        return None
+    src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    bytes_, h = None, None
+    for line in open(PROFILE):
+        if line.startswith("traffic_bytes_per_launch:"):
+            try:
+                bytes_ = float(line.split(":", 1)[1])
+            except ValueError:
+                bytes_ = None
+        if line.startswith("kernel_source_sha256_16:"):
+            h = line.split(":", 1)[1].strip()
+    if h != src_hash:
+        return None
+    return bytes_
+
+
+def make_event(ctx, m, cfg):
+    """Synthetic 3000-epoch light curve: the truth magnification is read
+    through the library from a map of the truth lens (self-consistent
+    injection), then noise and outliers are drawn by ``synth``."""
+    truth = ctx.build_map(cfg["s"], cfg["q"], cfg["L"], cfg["npix"],
+                          cfg["nray"], image_halfwidth=cfg["X"],
+                          deflect="fp32")
+    t = synth.epoch_times(cfg["n"], cfg["seed"], cfg["t0"])
+    A = ctx.lightcurve(truth, cfg["t0"], cfg["tE"], cfg["u0"], cfg["alpha"],
+                       t)
+    F, sig = synth.photometry(cfg["Fs"] * A + cfg["Fb"], cfg["seed"],
+                              cfg["outliers"])
+    truth.free()
+    return t, F, sig
+
+
+def grid_of(m, cfg):
+    g = cfg["grid"]
+    return m.Grid.make(g["n_u0"], g["n_alpha"], g["n_t0"], g["n_tE"],
+                       g["u0_lo"], g["u0_hi"], g["t0_lo"], g["t0_hi"],
+                       g["tE_lo"], g["tE_hi"], g["u0_log"], g["tE_log"],
+                       cfg["top_k"])
+
+
+# ---------------------------------------------------------------- dist
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_sample(cfg, frac, seed, nthreads, sq=None):
+    """Time the oracle on a bounded sample: one FP64 map build plus a seeded
+    contiguous slice of `frac` of the trajectories.  Returns the rate in
+    trajectory-epoch evals/s for a full step extrapolated from the sample,
+    and the description of the sample."""
+    import oracle as orc
+    g = cfg["grid"]
+    og = orc.Grid(g["n_u0"], g["n_alpha"], g["n_t0"], g["n_tE"], g["u0_lo"],
+                  g["u0_hi"], g["t0_lo"], g["t0_hi"], g["tE_lo"], g["tE_hi"],
+                  g["u0_log"], g["tE_log"])
+    s, q = sq if sq else (cfg["s"], cfg["q"])
+    t0 = time.perf_counter()
+    A, c, off, lost = orc.build_map(s, q, cfg["L"], cfg["npix"], cfg["nray"],
+                                    cfg["X"], nthreads=nthreads)
+    t_map = time.perf_counter() - t0
+    t = synth.epoch_times(cfg["n"], cfg["seed"], cfg["t0"])
+    At = orc.lightcurve_map(A, cfg["L"], t, cfg["t0"], cfg["tE"], cfg["u0"],
+                            cfg["alpha"])
+    F, sig = synth.photometry(cfg["Fs"] * At + cfg["Fb"], cfg["seed"],
+                              cfg["outliers"])
+    count = max(1, int(og.size * frac))
+    first = int(np.random.default_rng(seed).integers(0, og.size - count + 1))
+    t0 = time.perf_counter()
+    orc.grid_chi2(og, t, F, 1.0 / sig ** 2, A=A, L=cfg["L"], first=first,
+                  count=count, nthreads=nthreads)
+    t_search = time.perf_counter() - t0
+    evals_step = og.size * len(t)
+    t_step = t_map + t_search * og.size / count
+    return {
+        "value": evals_step / t_step,
+        "rays_per_s": cfg["nray"] ** 2 / t_map,
+        "t_map_s": t_map, "t_search_sample_s": t_search,
+        "sample": (f"1 FP64 map ({cfg['nray']}^2 rays) + {count} "
+                   f"trajectories ({100 * frac:.2f}% of {og.size}) x "
+                   f"{len(t)} epochs; full step extrapolated linearly"),
+    }
+
+
+def run_reference(args, cfg):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle as orc
+    orc.build()
+    nth = os.cpu_count() or 1
+    frac = args.ref_frac
+    for w in range(args.warmup):
+        oracle_sample(cfg, frac * 0.1, 100 + w, nth)
+    vals, walls = [], []
+    for k in range(args.steps):
+        sq = sq_of(k, 0, 1, cfg)
+        t0 = time.perf_counter()
+        r = oracle_sample(cfg, frac, 1000 + k, nth, sq=sq)
+        walls.append(time.perf_counter() - t0)
+        vals.append(r["value"])
+    value = float(np.mean(vals))
+    evals_step = cfg["grid"]["n_u0"] * cfg["grid"]["n_alpha"] * \
+        cfg["grid"]["n_t0"] * cfg["grid"]["n_tE"] * cfg["n"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * evals_step / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": workload_config(cfg),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nth,
+                         "kind": "oracle", "sample": r["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "wall_s_per_sample_step": float(np.mean(walls)),
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args, cfg):
+    import torch
+    world, rank, local = dist_setup()
+    import paper_1511_01157_gb300 as m
+    dev = local if world > 1 else 0
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = m.Context(dev, stream=stream)
+    grid = grid_of(m, cfg)
+    n_traj = grid.size
+    t, F, sig = make_event(ctx, m, cfg)
+    ev = ctx.event(t, F, sig)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32,
+                        device=f"cuda:{dev}")
+    evals_step = n_traj * len(t)
+    rays_step = cfg["nray"] ** 2
+
+    def step(k):
+        s, q = sq_of(k, rank, world, cfg)
+        mp = ctx.build_map(s, q, cfg["L"], cfg["npix"], cfg["nray"],
+                           image_halfwidth=cfg["X"], deflect="fp32")
+        fits = ctx.grid_chi2(ev, mp, grid)
+        ms = [ctx.kernel_ms(i) for i in range(5)]
+        mp.free()
+        return fits, ms
+
+    with torch.cuda.stream(stream):
+        for w in range(args.warmup):
+            step(w)
+            flush.fill_(float(w))
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        launches0 = ctx.launch_count()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        kernel_ms = []
+        best = None
+        with ClockSampler(dev) as clk:
+            ev0.record(stream)
+            for k in range(args.steps):
+                fits, ms = step(args.warmup + k)
+                kernel_ms.append(ms)
+                if best is None or fits["chi2"][0] < best:
+                    best = float(fits["chi2"][0])
+                flush.fill_(float(k))
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        elapsed = ev0.elapsed_time(ev1) / 1e3
+        launches = ctx.launch_count() - launches0 + args.steps  # + flushes
+        barrier(world)
+        torch.cuda.synchronize()
+        elapsed = max_over_ranks(elapsed, world)
+
+        # end to end through morse_search with host buffers (pinned)
+        tp = torch.from_numpy(np.ascontiguousarray(t)).pin_memory().numpy()
+        Fp = torch.from_numpy(np.ascontiguousarray(F)).pin_memory().numpy()
+        sp = torch.from_numpy(np.ascontiguousarray(sig)).pin_memory().numpy()
+        e2e_steps = max(1, args.steps // 2)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(e2e_steps):
+            s, q = sq_of(args.warmup + k, rank, world, cfg)
+            ctx.search(tp, Fp, sp, 0.0, s, q, cfg["L"], cfg["npix"],
+                       cfg["nray"], grid, image_halfwidth=cfg["X"],
+                       deflect="fp32")
+        torch.cuda.synchronize()
+        e2e_elapsed = max_over_ranks(time.perf_counter() - t0, world)
+
+    km = np.array(kernel_ms)  # [steps, 5]
+    search_ms = float(km[:, 2].mean())
+    ray_ms = float(km[:, 0].mean())
+    value = evals_step * args.steps * world / elapsed
+    e2e_value = evals_step * e2e_steps * world / e2e_elapsed
+
+    peaks, peak_kind = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_instr = props.multi_processor_count * FP32_LANES_PER_SM * \
+        sm_max * 1e6 / 1e12
+    achieved = evals_step * ALG_INSTR_PER_EVAL / (search_ms * 1e-3) / 1e12
+    traffic = recorded_traffic()
+    clocks = clk.summary()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (FP64 solve and cross-lane sums)", "data": "synthetic",
+        "config": workload_config(cfg),
+        "rays_per_s": rays_step * args.steps * world / elapsed,
+        "rays_per_s_kernel": rays_step / (ray_ms * 1e-3),
+        "kernel_ms": {"rayshoot": ray_ms,
+                      "counts_to_map": float(km[:, 1].mean()),
+                      "search": search_ms, "topk_merge": float(km[:, 3].mean()),
+                      "fill": float(km[:, 4].mean())},
+        "roofline": {
+            "kernel": "k_search", "bound": "alu", "achieved": achieved,
+            "peak": peak_instr, "unit": "T FP32-instr/s",
+            "frac": achieved / peak_instr, "traffic": traffic,
+            "algorithmic": f"{ALG_INSTR_PER_EVAL} FP32 instr per "
+                           f"trajectory-epoch x {evals_step} per launch",
+            "peak_source": f"{props.multi_processor_count} SMs x "
+                           f"{FP32_LANES_PER_SM} FP32 lanes x {sm_max} MHz "
+                           f"({peak_kind} sm_max_mhz)"},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(tp.nbytes + Fp.nbytes + sp.nbytes),
+                "d2h_bytes_per_step": int(grid.top_k * m.FIT_DTYPE.itemsize),
+                "steps": e2e_steps,
+                "path": "morse_search (event upload + map build + search + "
+                        "fits to host)"},
+        "gpu_launches": int(launches),
+        "best_chi2": best,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nth = os.cpu_count() or 1
+        r = oracle_sample(cfg, args.cpu_frac, 7, nth)
+        line["cpu_baseline"] = {"value": r["value"], "unit": UNIT,
+                                "cores": nth, "kind": "oracle",
+                                "sample": r["sample"],
+                                "rays_per_s": r["rays_per_s"]}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="morse",
+                    choices=["morse", "reference"])
+    ap.add_argument("--cpu-frac", type=float, default=0.004,
+                    help="trajectory fraction of the CPU-oracle sample")
+    ap.add_argument("--ref-frac", type=float, default=0.002,
+                    help="trajectory fraction per reference-arm step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    cfg = dict(synth.CFG1)
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+    return run_gpu(args, cfg)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

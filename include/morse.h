@@ -1,0 +1,233 @@
+/*
+ * morse.h -- C ABI of the GB300 (sm_103a) MORSE hot path.
+ *
+ * The method is McDougall & Albrow, "Microlensing Observations Rapid Search
+ * for Exoplanets: MORSE code for GPUs" (MNRAS 2015): for each binary-lens
+ * (s, q) a source-plane magnification map is built (§4.1), and a grid of
+ * straight source trajectories is searched through it (§4.2), each data
+ * point's magnification read from the map by bilinear interpolation, the
+ * flux F = Fs A + Fb fitted linearly (Eq. 5-6) and chi^2 summed over the
+ * data points; the best trajectories seed the refinement (§4.4, §5).
+ *
+ * Conventions shared by every call:
+ *  - Units: angles on the sky in Einstein radii; times in days.
+ *  - Lens: masses on the first axis, origin at the centre of mass (§4.1).
+ *    q = m2/m1; eps1 = 1/(1+q), eps2 = q/(1+q); primary at -s*eps2,
+ *    secondary at +s*eps1.
+ *  - Trajectory (§4.1 parameters u0, phi = alpha, t0, tE): at time t the
+ *    source is at tau = (t - t0)/tE,
+ *        y1 = tau cos(alpha) - u0 sin(alpha),
+ *        y2 = tau sin(alpha) + u0 cos(alpha).
+ *  - Map: npix x npix texels over [-L, L)^2 (L = "extent"), row-major with
+ *    the second coordinate major: A[iy*npix + ix]; texel (ix, iy) is centred
+ *    at (-L + (ix+1/2) Delta, -L + (iy+1/2) Delta), Delta = 2L/npix.  A
+ *    texel holds the magnification averaged over its area (ray count times
+ *    h^2/Delta^2, h the image-plane ray spacing).
+ *  - Lookup: bilinear between texel centres, coordinates clamped to the
+ *    outermost centres; outside the map (|y1| >= L or |y2| >= L) the
+ *    single-lens magnification A(u) = (u^2+2)/(u sqrt(u^2+4)), u = |y|.
+ *  - Errors: every call returns a morse_status; morse_last_error() gives a
+ *    message for the context's most recent failure.  No call aborts, traps
+ *    or throws.  Invalid arguments return MORSE_EINVAL before any GPU work.
+ *  - Memory: handles own their device memory; input arrays are copied and
+ *    stay owned by the caller; output arrays are caller-allocated HOST
+ *    memory unless the name ends in _dev.  Calls are synchronous on the
+ *    context's stream unless noted.
+ *  - Threads: a context may be used by one host thread at a time.
+ */
+#ifndef MORSE_H
+#define MORSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MORSE_OK = 0,
+  MORSE_EINVAL = 1,       /* bad argument (NaN, sigma <= 0, sizes ...)   */
+  MORSE_ENOMEM = 2,       /* device or host allocation failed            */
+  MORSE_ECUDA = 3,        /* a CUDA runtime call or launch failed        */
+  MORSE_ETIMEOUT = 4,     /* a bounded device loop gave up               */
+  MORSE_EDEGENERATE = 5,  /* linear system singular where not allowed    */
+  MORSE_EUNSUPPORTED = 6  /* valid request this build does not handle    */
+} morse_status;
+
+typedef struct morse_ctx morse_ctx;     /* device, stream, workspaces     */
+typedef struct morse_map morse_map;     /* one (s, q) magnification map   */
+typedef struct morse_event morse_event; /* one light curve on the device  */
+
+/* Human-readable name of a status code (static string). */
+const char *morse_status_string(morse_status st);
+
+/* Library version string, e.g. "morse-gb300 0.1 sm_103a". */
+const char *morse_version(void);
+
+/* Create a context on CUDA device `device`.  cuda_stream is a cudaStream_t
+ * cast to void* on which all work is queued; NULL creates a private
+ * stream.  The context does not own a caller-provided stream. */
+morse_status morse_create(morse_ctx **out, int device, void *cuda_stream);
+void morse_destroy(morse_ctx *ctx);
+const char *morse_last_error(const morse_ctx *ctx);
+
+/* ------------------------------------------------------------------ */
+/* Magnification maps (§3 ray-shooting maps, §4.1)                      */
+/* ------------------------------------------------------------------ */
+
+enum {
+  MORSE_DEFLECT_FP64 = 0, /* FP64 deflection, IEEE division, no FMA
+                             contraction: counts equal those of the plain
+                             FP64 definition ray for ray                  */
+  MORSE_DEFLECT_FP32 = 1  /* FP32 deflection (fast path)                  */
+};
+enum {
+  MORSE_STORE_FP32 = 1,    /* FP32 A (always kept)                        */
+  MORSE_STORE_FP16LOG = 2  /* plus FP16 log10(max(A, A_floor)) texels     */
+};
+
+typedef struct {
+  double image_halfwidth; /* X: rays cover [-X, X]^2; <= 0 means 1.5 L    */
+  int deflect;            /* MORSE_DEFLECT_FP64 or MORSE_DEFLECT_FP32     */
+  int store;              /* OR of MORSE_STORE_* (FP32 is always kept)     */
+} morse_map_opts;
+
+/* Build the magnification map of the binary lens (s, q) by inverse ray
+ * shooting (§3 ray-shooting maps; §5 inverse ray shooting) on the source
+ * grid of §4.1.  rays_per_axis^2 image-plane rays on the cell-centred grid
+ * x = -X + (i+1/2) h, h = 2X/rays_per_axis, are deflected through the real
+ * form of Eq. 2,
+ *     y = x - eps1 (x - x1)/|x - x1|^2 - eps2 (x - x2)/|x - x2|^2,
+ * and counted in half-open source bins [-L, L)^2; rays leaving the map are
+ * counted as off-map, rays exactly on a lens as lost.
+ * Arguments: s > 0, q > 0 finite; extent L > 0; 2 <= npix <= 16384;
+ * 1 <= rays_per_axis <= 2^31 - 1; opts may be NULL (X = 1.5 L, FP64,
+ * FP32 store).  *out receives a new map owned by the caller
+ * (morse_map_free).  Errors: EINVAL, ENOMEM, ECUDA. */
+morse_status morse_build_map(morse_ctx *ctx, double s, double q,
+                             double extent, int npix, int64_t rays_per_axis,
+                             const morse_map_opts *opts, morse_map **out);
+
+/* Wrap a caller-supplied FP32 map (npix x npix, layout as above, values
+ * copied) so that it can be searched.  A must be finite and >= 0.  The map
+ * has no counts.  Errors: EINVAL, ENOMEM, ECUDA. */
+morse_status morse_map_from_host(morse_ctx *ctx, const float *A, int npix,
+                                 double extent, morse_map **out);
+
+/* Copy the ray counts (npix*npix uint32, host) and the off-map and lost
+ * ray totals of a ray-shot map.  Any output pointer may be NULL.
+ * Errors: EINVAL (map has no counts), ECUDA. */
+morse_status morse_map_counts(const morse_map *map, uint32_t *host_counts,
+                              uint64_t *off_map, uint64_t *lost);
+
+/* Copy the FP32 magnifications (npix*npix floats, host). */
+morse_status morse_map_values(const morse_map *map, float *host_A);
+
+/* Map geometry.  Any output pointer may be NULL. */
+morse_status morse_map_info(const morse_map *map, int *npix, double *extent,
+                            double *s, double *q);
+void morse_map_free(morse_map *map);
+
+/* ------------------------------------------------------------------ */
+/* Light curves (§4.1 Eq. 5)                                            */
+/* ------------------------------------------------------------------ */
+
+/* Copy a light curve to the device: n epochs with times t (days), fluxes
+ * and 1-sigma errors (w = 1/sigma^2).  Times are stored as FP32 offsets
+ * t - t_ref, so t_ref should lie within the data (resolution ~4e-6 d for
+ * offsets up to 40 d); grid t0 values are absolute times in the same frame
+ * as t.  Requires n >= 3, every value finite, sigma > 0.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+morse_status morse_event_create(morse_ctx *ctx, const double *t,
+                                const double *flux, const double *sigma,
+                                int64_t n, double t_ref, morse_event **out);
+void morse_event_free(morse_event *ev);
+morse_status morse_event_info(const morse_event *ev, int64_t *n,
+                              double *t_ref);
+
+/* ------------------------------------------------------------------ */
+/* Trajectory grid search (§4.2 chi^2 over data points; §4.4 seeds)      */
+/* ------------------------------------------------------------------ */
+
+/* The grid: u0 (log or linear in [u0_lo, u0_hi]), alpha_k = 2 pi k /
+ * n_alpha, t0 linear in [t0_lo, t0_hi], tE (log or linear in [tE_lo,
+ * tE_hi]); an axis with n = 1 takes its lo value.  Trajectory index
+ *     idx = ((i_u0 * n_alpha + i_alpha) * n_t0 + i_t0) * n_tE + i_tE.
+ * top_k: number of best trajectories kept (1 <= top_k <= 4096). */
+typedef struct {
+  int n_u0, n_alpha, n_t0, n_tE;
+  double u0_lo, u0_hi, t0_lo, t0_hi, tE_lo, tE_hi;
+  int u0_log, tE_log;
+  int top_k;
+} morse_grid;
+
+enum { MORSE_FIT_DEGENERATE = 1 }; /* A constant along the track: Fs = 0 */
+
+/* One fitted trajectory.  chi2 = sum_i w_i (F_i - Fs A_i - Fb)^2 with
+ * (Fs, Fb) the weighted least-squares solution of Eq. 6. */
+typedef struct {
+  double chi2, t0, tE, u0, alpha, Fs, Fb;
+  int64_t idx;
+  int32_t flags;
+  int32_t reserved;
+} morse_fit;
+
+/* Search every trajectory of the grid through the map and return the
+ * top_k smallest chi^2, ordered by (chi2, idx) ascending, in out[top_k]
+ * (host).  If the grid has fewer than top_k trajectories the tail has
+ * idx = -1 and chi2 = +inf.  Each trajectory's Fs, Fb come from the
+ * closed-form 2x2 solve of the normal equations (Eq. 6) and its chi^2 from
+ * the per-point residuals (§4.2).  Errors: EINVAL, ENOMEM, ECUDA. */
+morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
+                             const morse_map *map, const morse_grid *grid,
+                             morse_fit *out);
+
+/* chi^2, Fs and Fb of every trajectory with index in [first, first+count)
+ * (host arrays of count doubles; Fs/Fb may be NULL).  Same arithmetic as
+ * morse_grid_chi2.  Errors: EINVAL, ENOMEM, ECUDA. */
+morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
+                                   const morse_map *map,
+                                   const morse_grid *grid, int64_t first,
+                                   int64_t count, double *chi2, double *Fs,
+                                   double *Fb);
+
+/* End-to-end search from host buffers: copies the light curve in, builds
+ * the (s, q) map, searches the grid and returns the top_k fits to out
+ * (host), freeing everything it made.  Equivalent to morse_event_create +
+ * morse_build_map + morse_grid_chi2 + frees.  Errors as those calls. */
+morse_status morse_search(morse_ctx *ctx, const double *t, const double *flux,
+                          const double *sigma, int64_t n, double t_ref,
+                          double s, double q, double extent, int npix,
+                          int64_t rays_per_axis, const morse_map_opts *opts,
+                          const morse_grid *grid, morse_fit *out);
+
+/* Map magnification A(t_i) along one trajectory at n host times t (same
+ * lookup as the search), written to A_out (host, n doubles).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+morse_status morse_lightcurve(morse_ctx *ctx, const morse_map *map,
+                              double t0, double tE, double u0, double alpha,
+                              const double *t, int64_t n, double *A_out);
+
+/* Merge n_lists top-K lists (each ascending by (chi2, idx), counts[i]
+ * entries, entries with idx < 0 ignored) into the k best, ascending, in
+ * out[k] (tail padded with idx = -1, chi2 = +inf).  Host-only; used to
+ * combine shards of a search run on several GPUs or several calls.
+ * Errors: EINVAL. */
+morse_status morse_topk_merge(const morse_fit *const *lists,
+                              const int *counts, int n_lists, int k,
+                              morse_fit *out);
+
+/* Timing of the most recent morse_build_map / morse_grid_chi2 kernels on
+ * the context stream, in milliseconds (CUDA events): which = 0 ray
+ * shooting, 1 counts-to-map, 2 grid search, 3 top-K merge, 4 fit fill. */
+morse_status morse_last_kernel_ms(const morse_ctx *ctx, int which,
+                                  double *ms);
+
+/* Number of CUDA kernels this context has launched since morse_create. */
+morse_status morse_launch_count(const morse_ctx *ctx, uint64_t *n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MORSE_H */

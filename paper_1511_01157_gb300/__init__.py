@@ -1,0 +1,356 @@
+"""Python binding of the MORSE GB300 library (libmorse.so, C ABI in
+include/morse.h).
+
+Argument marshalling only: every step of the hot path (ray shooting, map
+texels, trajectory search, top-K, fits) runs in the library's CUDA kernels.
+The library must have been built (``__graft_entry__.build()`` or
+``python paper_1511_01157_gb300/build.py``); importing this module without
+it raises ``ImportError`` -- there is no CPU fallback.
+
+Method: McDougall & Albrow (2015) MORSE -- a binary-lens magnification map
+per (s, q) built by inverse ray shooting (§3, §4.1), a grid of straight
+trajectories searched through it with a linear flux fit and chi^2 (§4.2),
+and the best trajectories kept as seeds (§4.4).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmorse.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "libmorse.so is not built; run `python -c 'import __graft_entry__ as "
+        "g; g.build()'` (needs nvcc for sm_103a)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEGENERATE, EUNSUPPORTED = range(7)
+DEFLECT_FP64, DEFLECT_FP32 = 0, 1
+STORE_FP32, STORE_FP16LOG = 1, 2
+FIT_DEGENERATE = 1
+
+
+class MorseError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        super().__init__(f"{_status_name(status)}: {msg}")
+
+
+class Grid(ctypes.Structure):
+    """morse_grid: trajectory grid over (u0, alpha, t0, tE)."""
+    _fields_ = [("n_u0", ctypes.c_int), ("n_alpha", ctypes.c_int),
+                ("n_t0", ctypes.c_int), ("n_tE", ctypes.c_int),
+                ("u0_lo", ctypes.c_double), ("u0_hi", ctypes.c_double),
+                ("t0_lo", ctypes.c_double), ("t0_hi", ctypes.c_double),
+                ("tE_lo", ctypes.c_double), ("tE_hi", ctypes.c_double),
+                ("u0_log", ctypes.c_int), ("tE_log", ctypes.c_int),
+                ("top_k", ctypes.c_int)]
+
+    @classmethod
+    def make(cls, n_u0, n_alpha, n_t0, n_tE, u0_lo, u0_hi, t0_lo, t0_hi,
+             tE_lo, tE_hi, u0_log=True, tE_log=True, top_k=16):
+        return cls(n_u0, n_alpha, n_t0, n_tE, u0_lo, u0_hi, t0_lo, t0_hi,
+                   tE_lo, tE_hi, int(bool(u0_log)), int(bool(tE_log)), top_k)
+
+    @property
+    def size(self):
+        return self.n_u0 * self.n_alpha * self.n_t0 * self.n_tE
+
+
+class Fit(ctypes.Structure):
+    _fields_ = [("chi2", ctypes.c_double), ("t0", ctypes.c_double),
+                ("tE", ctypes.c_double), ("u0", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("Fs", ctypes.c_double),
+                ("Fb", ctypes.c_double), ("idx", ctypes.c_int64),
+                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+FIT_DTYPE = np.dtype([("chi2", "f8"), ("t0", "f8"), ("tE", "f8"),
+                      ("u0", "f8"), ("alpha", "f8"), ("Fs", "f8"),
+                      ("Fb", "f8"), ("idx", "i8"), ("flags", "i4"),
+                      ("reserved", "i4")])
+assert FIT_DTYPE.itemsize == ctypes.sizeof(Fit)
+
+
+class MapOpts(ctypes.Structure):
+    _fields_ = [("image_halfwidth", ctypes.c_double),
+                ("deflect", ctypes.c_int), ("store", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_S = ctypes.c_int  # morse_status
+
+_SIGS = {
+    "morse_status_string": (ctypes.c_char_p, [_I]),
+    "morse_version": (ctypes.c_char_p, []),
+    "morse_create": (_S, [_P, _I, _P]),
+    "morse_destroy": (None, [_P]),
+    "morse_last_error": (ctypes.c_char_p, [_P]),
+    "morse_build_map": (_S, [_P, _D, _D, _D, _I, _I64, _P, _P]),
+    "morse_map_from_host": (_S, [_P, _P, _I, _D, _P]),
+    "morse_map_counts": (_S, [_P, _P, _P, _P]),
+    "morse_map_values": (_S, [_P, _P]),
+    "morse_map_info": (_S, [_P, _P, _P, _P, _P]),
+    "morse_map_free": (None, [_P]),
+    "morse_event_create": (_S, [_P, _P, _P, _P, _I64, _D, _P]),
+    "morse_event_free": (None, [_P]),
+    "morse_event_info": (_S, [_P, _P, _P]),
+    "morse_grid_chi2": (_S, [_P, _P, _P, _P, _P]),
+    "morse_grid_chi2_dense": (_S, [_P, _P, _P, _P, _I64, _I64, _P, _P, _P]),
+    "morse_search": (_S, [_P, _P, _P, _P, _I64, _D, _D, _D, _D, _I, _I64, _P,
+                          _P, _P]),
+    "morse_lightcurve": (_S, [_P, _P, _D, _D, _D, _D, _P, _I64, _P]),
+    "morse_topk_merge": (_S, [_P, _P, _I, _I, _P]),
+    "morse_last_kernel_ms": (_S, [_P, _I, _P]),
+    "morse_launch_count": (_S, [_P, _P]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+def _status_name(st):
+    return _lib.morse_status_string(int(st)).decode()
+
+
+def version() -> str:
+    return _lib.morse_version().decode()
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    h = getattr(stream, "cuda_stream", None)  # torch.cuda.Stream
+    if h is None:
+        raise TypeError("stream must be a torch.cuda.Stream or an int handle")
+    return ctypes.c_void_p(int(h))
+
+
+class Context:
+    """A device, a CUDA stream and the library's workspaces (morse_create)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._h = ctypes.c_void_p()
+        self._stream_ref = stream  # keep a torch stream alive
+        st = _lib.morse_create(ctypes.byref(self._h), int(device),
+                               _stream_handle(stream))
+        if st != OK:
+            raise MorseError(st, f"morse_create(device={device}) failed")
+        self.device = device
+
+    def _check(self, st, what):
+        if st != OK:
+            msg = _lib.morse_last_error(self._h).decode(errors="replace")
+            raise MorseError(st, f"{what}: {msg}")
+
+    def close(self):
+        if self._h:
+            _lib.morse_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------ maps
+    def build_map(self, s, q, extent, npix, rays_per_axis,
+                  image_halfwidth=None, deflect="fp64", fp16log=False):
+        """Magnification map of the binary lens (s, q) by inverse ray
+        shooting (morse_build_map)."""
+        opts = MapOpts(float(image_halfwidth or 0.0),
+                       DEFLECT_FP64 if deflect == "fp64" else DEFLECT_FP32,
+                       STORE_FP32 | (STORE_FP16LOG if fp16log else 0))
+        h = ctypes.c_void_p()
+        st = _lib.morse_build_map(self._h, float(s), float(q), float(extent),
+                                  int(npix), int(rays_per_axis),
+                                  ctypes.byref(opts), ctypes.byref(h))
+        self._check(st, "morse_build_map")
+        return Map(self, h)
+
+    def map_from_host(self, A, extent):
+        A = np.ascontiguousarray(A, dtype=np.float32)
+        if A.ndim != 2 or A.shape[0] != A.shape[1]:
+            raise ValueError("map must be square [npix, npix]")
+        h = ctypes.c_void_p()
+        st = _lib.morse_map_from_host(self._h, _ptr(A), A.shape[0],
+                                      float(extent), ctypes.byref(h))
+        self._check(st, "morse_map_from_host")
+        return Map(self, h)
+
+    # ------------------------------------------------------------ events
+    def event(self, t, flux, sigma, t_ref=0.0):
+        t, flux, sigma = _f64(t), _f64(flux), _f64(sigma)
+        if not (len(t) == len(flux) == len(sigma)):
+            raise ValueError("t, flux and sigma must have equal length")
+        h = ctypes.c_void_p()
+        st = _lib.morse_event_create(self._h, _ptr(t), _ptr(flux),
+                                     _ptr(sigma), len(t), float(t_ref),
+                                     ctypes.byref(h))
+        self._check(st, "morse_event_create")
+        return Event(self, h, len(t))
+
+    # ------------------------------------------------------------ search
+    def grid_chi2(self, event, map_, grid: Grid) -> np.ndarray:
+        """Top-K trajectories (structured array, FIT_DTYPE)."""
+        out = np.zeros(grid.top_k, dtype=FIT_DTYPE)
+        st = _lib.morse_grid_chi2(self._h, event._h, map_._h,
+                                  ctypes.byref(grid), _ptr(out))
+        self._check(st, "morse_grid_chi2")
+        return out
+
+    def grid_chi2_dense(self, event, map_, grid: Grid, first=0, count=None):
+        if count is None:
+            count = grid.size - first
+        chi2 = np.zeros(count)
+        fs = np.zeros(count)
+        fb = np.zeros(count)
+        st = _lib.morse_grid_chi2_dense(self._h, event._h, map_._h,
+                                        ctypes.byref(grid), int(first),
+                                        int(count), _ptr(chi2), _ptr(fs),
+                                        _ptr(fb))
+        self._check(st, "morse_grid_chi2_dense")
+        return chi2, fs, fb
+
+    def search(self, t, flux, sigma, t_ref, s, q, extent, npix,
+               rays_per_axis, grid: Grid, image_halfwidth=None,
+               deflect="fp32"):
+        """End-to-end from host buffers (morse_search)."""
+        t, flux, sigma = _f64(t), _f64(flux), _f64(sigma)
+        opts = MapOpts(float(image_halfwidth or 0.0),
+                       DEFLECT_FP64 if deflect == "fp64" else DEFLECT_FP32,
+                       STORE_FP32)
+        out = np.zeros(grid.top_k, dtype=FIT_DTYPE)
+        st = _lib.morse_search(self._h, _ptr(t), _ptr(flux), _ptr(sigma),
+                               len(t), float(t_ref), float(s), float(q),
+                               float(extent), int(npix), int(rays_per_axis),
+                               ctypes.byref(opts), ctypes.byref(grid),
+                               _ptr(out))
+        self._check(st, "morse_search")
+        return out
+
+    def lightcurve(self, map_, t0, tE, u0, alpha, t):
+        t = _f64(t)
+        out = np.zeros(len(t))
+        st = _lib.morse_lightcurve(self._h, map_._h, float(t0), float(tE),
+                                   float(u0), float(alpha), _ptr(t), len(t),
+                                   _ptr(out))
+        self._check(st, "morse_lightcurve")
+        return out
+
+    def launch_count(self) -> int:
+        v = ctypes.c_uint64()
+        self._check(_lib.morse_launch_count(self._h, ctypes.byref(v)),
+                    "morse_launch_count")
+        return int(v.value)
+
+    def kernel_ms(self, which: int) -> float:
+        v = ctypes.c_double()
+        self._check(_lib.morse_last_kernel_ms(self._h, int(which),
+                                              ctypes.byref(v)),
+                    "morse_last_kernel_ms")
+        return v.value
+
+
+class Map:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self._h = ctx, h
+        n = ctypes.c_int()
+        L = ctypes.c_double()
+        s = ctypes.c_double()
+        q = ctypes.c_double()
+        ctx._check(_lib.morse_map_info(h, ctypes.byref(n), ctypes.byref(L),
+                                       ctypes.byref(s), ctypes.byref(q)),
+                   "morse_map_info")
+        self.npix, self.extent, self.s, self.q = n.value, L.value, s.value, \
+            q.value
+
+    def counts(self):
+        c = np.zeros((self.npix, self.npix), dtype=np.uint32)
+        off = ctypes.c_uint64()
+        lost = ctypes.c_uint64()
+        self.ctx._check(_lib.morse_map_counts(self._h, _ptr(c),
+                                              ctypes.byref(off),
+                                              ctypes.byref(lost)),
+                        "morse_map_counts")
+        return c, int(off.value), int(lost.value)
+
+    def values(self):
+        A = np.zeros((self.npix, self.npix), dtype=np.float32)
+        self.ctx._check(_lib.morse_map_values(self._h, _ptr(A)),
+                        "morse_map_values")
+        return A
+
+    def free(self):
+        if self._h:
+            _lib.morse_map_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self.ctx._h:
+                self.free()
+        except Exception:
+            pass
+
+
+class Event:
+    def __init__(self, ctx: Context, h, n):
+        self.ctx, self._h, self.n = ctx, h, n
+
+    def free(self):
+        if self._h:
+            _lib.morse_event_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self.ctx._h:
+                self.free()
+        except Exception:
+            pass
+
+
+def topk_merge(lists, k):
+    """Merge sorted top-K lists (FIT_DTYPE arrays) on the host."""
+    arrs = [np.ascontiguousarray(a, dtype=FIT_DTYPE) for a in lists]
+    ptrs = (ctypes.c_void_p * max(1, len(arrs)))(
+        *[a.ctypes.data for a in arrs])
+    counts = (ctypes.c_int * max(1, len(arrs)))(*[len(a) for a in arrs])
+    out = np.zeros(k, dtype=FIT_DTYPE)
+    st = _lib.morse_topk_merge(ptrs, counts, len(arrs), int(k), _ptr(out))
+    if st != OK:
+        raise MorseError(st, "morse_topk_merge")
+    return out
+
+
+__all__ = ["Context", "Map", "Event", "Grid", "Fit", "FIT_DTYPE", "MapOpts",
+           "MorseError", "topk_merge", "version", "LIB_PATH", "EXPORTED"]

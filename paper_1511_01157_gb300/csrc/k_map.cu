@@ -1,0 +1,304 @@
+// Magnification-map kernels: inverse ray shooting into a shared-memory
+// histogram (K1) and ray counts -> magnification texels (K1b).
+//
+// The method (McDougall & Albrow 2015, §3 ray-shooting maps, §4.1 uniform
+// source grid, §5 inverse ray shooting): image-plane rays on a uniform grid
+// are deflected by the binary lens (Eq. 2) and counted in source-plane
+// pixels; a pixel's magnification is its ray count times the image area of
+// one ray over the source area of one pixel.
+//
+// GB300 design.  A persistent grid of 512-thread blocks walks 256x256-ray
+// image tiles.  A tile's rays land in a compact source window (the lens map
+// is smooth away from the lenses), so each block bins into a 128x128-bin
+// shared-memory window placed on the deflected tile, using shared-memory
+// atomics; rays that fall outside the window go straight to the global map
+// with red.global.add, and the window is flushed with one global add per
+// non-empty bin.  Threads own 8x16-ray sub-blocks so that the 32 lanes of a
+// warp sit 8 rays (~1.2 pixels) apart and rarely hit the same bin.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "morse_internal.cuh"
+
+namespace morse {
+
+namespace {
+
+constexpr int kSubX = 8;    // rays per thread sub-block along x
+constexpr int kSubY = 16;   // rays per thread sub-block along y
+static_assert(kRayThreads == (kRayTile / kSubX) * (kRayTile / kSubY),
+              "one sub-block per thread");
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// FP64 deflection with the operation order of the plain definition:
+//   d1x = x1 - xa; r1 = d1x d1x + x2 x2; d2x = x1 - xb; r2 = d2x d2x + x2 x2
+//   y1 = x1 - (e1 d1x)/r1 - (e2 d2x)/r2;  y2 = x2 - (e1 x2)/r1 - (e2 x2)/r2
+//   v = (y + L)/Delta, bin = floor(v), on the map iff 0 <= v < npix.
+// Every operation is an explicitly rounded IEEE op (no FMA contraction) so
+// the counts equal those of the FP64 definition evaluated on a CPU.
+// Returns 0 on map (bin in *ix, *iy), 1 off map, 2 lost (ray on a lens).
+__device__ __forceinline__ int deflect64(const RayParams &P, long long i,
+                                         double x2, double x2sq, int *ix,
+                                         int *iy) {
+  double x1 = __dadd_rn(-P.X, __dmul_rn(__dadd_rn((double)i, 0.5), P.h));
+  double d1x = __dsub_rn(x1, P.xa);
+  double r1 = __dadd_rn(__dmul_rn(d1x, d1x), x2sq);
+  double d2x = __dsub_rn(x1, P.xb);
+  double r2 = __dadd_rn(__dmul_rn(d2x, d2x), x2sq);
+  if (r1 == 0.0 || r2 == 0.0) return 2;
+  double y1 = __dsub_rn(__dsub_rn(x1, __ddiv_rn(__dmul_rn(P.e1, d1x), r1)),
+                        __ddiv_rn(__dmul_rn(P.e2, d2x), r2));
+  double y2 = __dsub_rn(__dsub_rn(x2, __ddiv_rn(__dmul_rn(P.e1, x2), r1)),
+                        __ddiv_rn(__dmul_rn(P.e2, x2), r2));
+  double v1 = __ddiv_rn(__dadd_rn(y1, P.L), P.dlt);
+  double v2 = __ddiv_rn(__dadd_rn(y2, P.L), P.dlt);
+  double np = (double)P.npix;
+  if (!(v1 >= 0.0 && v1 < np && v2 >= 0.0 && v2 < np)) return 1;
+  *ix = (int)v1;  // truncation == floor for v >= 0
+  *iy = (int)v2;
+  return 0;
+}
+
+// FP32 deflection: one approximate reciprocal of r1 r2 serves both lenses.
+__device__ __forceinline__ int deflect32(const RayParams &P, float x1,
+                                         float x2, float x2sq, int *ix,
+                                         int *iy) {
+  float d1 = x1 - P.xaf;
+  float d2 = x1 - P.xbf;
+  float r1 = fmaf(d1, d1, x2sq);
+  float r2 = fmaf(d2, d2, x2sq);
+  float rr = r1 * r2;
+  if (rr == 0.0f) return 2;
+  float inv = rcp_approx(rr);
+  float a1 = P.e1f * (r2 * inv);
+  float a2 = P.e2f * (r1 * inv);
+  float y1 = fmaf(-a2, d2, fmaf(-a1, d1, x1));
+  float y2 = fmaf(-(a1 + a2), x2, x2);
+  float v1 = fmaf(y1, P.invdf, P.offf);
+  float v2 = fmaf(y2, P.invdf, P.offf);
+  if (!(v1 >= 0.0f && v1 < P.npixf && v2 >= 0.0f && v2 < P.npixf)) return 1;
+  int a = (int)v1, b = (int)v2;
+  if (a >= P.npix || b >= P.npix) return 1;
+  *ix = a;
+  *iy = b;
+  return 0;
+}
+
+// Bin of a sample ray (FP64), clamped into the map; used only to place the
+// shared-memory window, never to count.
+__device__ bool sample_bin(const RayParams &P, long long i, long long j,
+                           int *bx, int *by) {
+  double x2 = -P.X + ((double)j + 0.5) * P.h;
+  int ix = 0, iy = 0;
+  int st = deflect64(P, i, x2, x2 * x2, &ix, &iy);
+  if (st != 0) return false;
+  *bx = ix;
+  *by = iy;
+  return true;
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(kRayThreads)
+    k_rayshoot(const RayParams P) {
+  extern __shared__ uint32_t win[];  // kRayWin * kRayWin bins
+  __shared__ int s_wx, s_wy;
+  const int tid = threadIdx.x;
+  for (int k = tid; k < kRayWin * kRayWin; k += kRayThreads) win[k] = 0u;
+  unsigned int n_off = 0, n_lost = 0;
+  const int ntiles = P.tiles_x * P.tiles_y;
+  const int sx = tid & 31;   // sub-block column (lane)
+  const int sy = tid >> 5;   // sub-block row (warp)
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long i0 = (long long)(tile % P.tiles_x) * kRayTile;
+    const long long j0 = (long long)(tile / P.tiles_x) * kRayTile;
+    if (tid < 32) {
+      // place the window on the bounding box of 9 deflected sample rays
+      int bx = 0, by = 0;
+      bool ok = false;
+      if (tid < 9) {
+        long long span = kRayTile - 1;
+        long long ii = i0 + (tid % 3) * span / 2;
+        long long jj = j0 + (tid / 3) * span / 2;
+        if (ii >= P.nray) ii = P.nray - 1;
+        if (jj >= P.nray) jj = P.nray - 1;
+        ok = sample_bin(P, ii, jj, &bx, &by);
+      }
+      int lo_x = ok ? bx : 0x7fffffff, hi_x = ok ? bx : -1;
+      int lo_y = ok ? by : 0x7fffffff, hi_y = ok ? by : -1;
+      for (int o = 16; o; o >>= 1) {
+        lo_x = min(lo_x, __shfl_xor_sync(0xffffffffu, lo_x, o));
+        hi_x = max(hi_x, __shfl_xor_sync(0xffffffffu, hi_x, o));
+        lo_y = min(lo_y, __shfl_xor_sync(0xffffffffu, lo_y, o));
+        hi_y = max(hi_y, __shfl_xor_sync(0xffffffffu, hi_y, o));
+      }
+      if (tid == 0) {
+        int cx = (hi_x >= 0) ? (lo_x + hi_x) / 2 : P.npix / 2;
+        int cy = (hi_y >= 0) ? (lo_y + hi_y) / 2 : P.npix / 2;
+        int wx = cx - kRayWin / 2, wy = cy - kRayWin / 2;
+        int wmax = P.npix - kRayWin;
+        if (wmax < 0) wmax = 0;
+        s_wx = min(max(wx, 0), wmax);
+        s_wy = min(max(wy, 0), wmax);
+      }
+    }
+    __syncthreads();
+    const int wx0 = s_wx, wy0 = s_wy;
+    const long long ib = i0 + sx * kSubX;
+    const long long jb = j0 + sy * kSubY;
+#pragma unroll 1
+    for (int b = 0; b < kSubY; ++b) {
+      const long long j = jb + b;
+      if (j >= P.nray) break;
+      double x2d = 0.0, x2sqd = 0.0;
+      float x2f = 0.f, x2sqf = 0.f;
+      if (FP64) {
+        x2d = __dadd_rn(-P.X, __dmul_rn(__dadd_rn((double)j, 0.5), P.h));
+        x2sqd = __dmul_rn(x2d, x2d);
+      } else {
+        x2f = fmaf((float)j, P.hf, P.x0f);
+        x2sqf = x2f * x2f;
+      }
+#pragma unroll
+      for (int a = 0; a < kSubX; ++a) {
+        const long long i = ib + a;
+        if (i < P.nray) {
+          int ix = 0, iy = 0, st;
+          if (FP64)
+            st = deflect64(P, i, x2d, x2sqd, &ix, &iy);
+          else
+            st = deflect32(P, fmaf((float)i, P.hf, P.x0f), x2f, x2sqf, &ix,
+                           &iy);
+          if (st == 0) {
+            unsigned lx = (unsigned)(ix - wx0), ly = (unsigned)(iy - wy0);
+            if (lx < (unsigned)kRayWin && ly < (unsigned)kRayWin)
+              atomicAdd(&win[ly * kRayWin + lx], 1u);
+            else
+              atomicAdd(&P.counts[(size_t)iy * P.npix + ix], 1u);
+          } else if (st == 1) {
+            ++n_off;
+          } else {
+            ++n_lost;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // flush the window: one global add per non-empty bin, then clear
+    for (int k = tid; k < kRayWin * kRayWin; k += kRayThreads) {
+      uint32_t v = win[k];
+      if (v) {
+        win[k] = 0u;
+        int gx = wx0 + (k % kRayWin), gy = wy0 + (k / kRayWin);
+        atomicAdd(&P.counts[(size_t)gy * P.npix + gx], v);
+      }
+    }
+    __syncthreads();
+  }
+  // off-map and lost totals
+  unsigned long long o = n_off, l = n_lost;
+  for (int s = 16; s; s >>= 1) {
+    o += __shfl_xor_sync(0xffffffffu, o, s);
+    l += __shfl_xor_sync(0xffffffffu, l, s);
+  }
+  if ((tid & 31) == 0) {
+    if (o) atomicAdd(&P.tot[0], o);
+    if (l) atomicAdd(&P.tot[1], l);
+  }
+}
+
+// counts -> A = count * f (FP64 product rounded to FP32) and 2x2 quads with
+// the last row/column replicated.
+__device__ __forceinline__ float mag_of(const uint32_t *c, int npix, int x,
+                                        int y, double f) {
+  return __double2float_rn(__dmul_rn((double)c[(size_t)y * npix + x], f));
+}
+
+__global__ void k_counts_to_map(const uint32_t *__restrict__ counts, int npix,
+                                double f, float *__restrict__ A,
+                                float4 *__restrict__ quad) {
+  size_t n = (size_t)npix * npix;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x) {
+    int x = (int)(k % npix), y = (int)(k / npix);
+    int x1 = min(x + 1, npix - 1), y1 = min(y + 1, npix - 1);
+    float a00 = mag_of(counts, npix, x, y, f);
+    A[k] = a00;
+    quad[k] = make_float4(a00, mag_of(counts, npix, x1, y, f),
+                          mag_of(counts, npix, x, y1, f),
+                          mag_of(counts, npix, x1, y1, f));
+  }
+}
+
+__global__ void k_quads_from_A(const float *__restrict__ A, int npix,
+                               float4 *__restrict__ quad) {
+  size_t n = (size_t)npix * npix;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x) {
+    int x = (int)(k % npix), y = (int)(k / npix);
+    int x1 = min(x + 1, npix - 1), y1 = min(y + 1, npix - 1);
+    quad[k] = make_float4(A[(size_t)y * npix + x], A[(size_t)y * npix + x1],
+                          A[(size_t)y1 * npix + x], A[(size_t)y1 * npix + x1]);
+  }
+}
+
+}  // namespace
+
+static size_t ray_smem() { return sizeof(uint32_t) * kRayWin * kRayWin; }
+
+int rayshoot_blocks_per_sm() {
+  static int cached = -1;
+  if (cached > 0) return cached;
+  cudaFuncSetAttribute(k_rayshoot<true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)ray_smem());
+  cudaFuncSetAttribute(k_rayshoot<false>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)ray_smem());
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &b, k_rayshoot<false>, kRayThreads, ray_smem()) != cudaSuccess ||
+      b < 1)
+    b = 1;
+  cached = b;
+  return b;
+}
+
+cudaError_t launch_rayshoot(const RayParams &P, bool fp64, int grid,
+                            cudaStream_t st) {
+  rayshoot_blocks_per_sm();  // sets the shared-memory attribute once
+  if (fp64)
+    k_rayshoot<true><<<grid, kRayThreads, ray_smem(), st>>>(P);
+  else
+    k_rayshoot<false><<<grid, kRayThreads, ray_smem(), st>>>(P);
+  return cudaGetLastError();
+}
+
+static int elementwise_grid(size_t n) {
+  size_t g = (n + 255) / 256;
+  if (g > 8192) g = 8192;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t launch_counts_to_map(const uint32_t *counts, int npix, double f,
+                                 float *A, float4 *quad, cudaStream_t st) {
+  size_t n = (size_t)npix * npix;
+  k_counts_to_map<<<elementwise_grid(n), 256, 0, st>>>(counts, npix, f, A,
+                                                       quad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quads_from_A(const float *A, int npix, float4 *quad,
+                                cudaStream_t st) {
+  size_t n = (size_t)npix * npix;
+  k_quads_from_A<<<elementwise_grid(n), 256, 0, st>>>(A, npix, quad);
+  return cudaGetLastError();
+}
+
+}  // namespace morse

@@ -1,0 +1,548 @@
+// Trajectory chi^2 grid search (K2), top-K merge (K2b), fit fill (K2c) and
+// the single-trajectory light curve.
+//
+// The method (McDougall & Albrow 2015, §4.2): a trajectory is a straight
+// source track through the (s, q) magnification map; each data point's
+// magnification A(t_i) is read from the map by bilinear interpolation, the
+// flux model F = Fs A + Fb (Eq. 5-6) is linear in A, and chi^2 is the sum
+// of the per-point contributions.  §4.4 keeps the best trajectories as
+// seeds.  Here (Fs, Fb) are profiled out by the closed-form weighted
+// least-squares solve, and the grid covers (u0, alpha, t0, tE).
+//
+// GB300 design.
+//  * Lanes of a warp take consecutive epochs of one trajectory, so the 32
+//    bilinear gathers of a warp fall within a few texels of each other
+//    (one 16-byte float4 load fetches a texel's 2x2 neighbourhood) and the
+//    map, kept resident in the 129 MB L2, is served mostly from L1.
+//  * The epoch block (t, w, wF, F) of the light curve is staged once per
+//    block in shared memory and re-read by every trajectory.
+//  * Phase 1 accumulates the normal-equation sums in FP32 per lane (the
+//    magnification and the flux centred on 1 and on the weighted mean
+//    flux), reduces them across the warp, and solves the 2x2 system in
+//    FP64 with one trajectory per lane (32 solves per warp instruction).
+//  * The closed-form chi^2 from those sums, S_FF - Fs S_AF - Fb S_F, loses
+//    digits to cancellation, so it is used only with a rigorous error bound
+//    to discard trajectories that cannot enter the current top-K.  Every
+//    reported chi^2 comes from phase 2: a second sweep that sums the
+//    per-point residuals w (F - Fs A - Fb)^2 (FP32 per lane, FP64 across
+//    lanes).
+//  * Each block keeps its own sorted top-K in shared memory, merges new
+//    candidates after each round, and prunes against its K-th chi^2;
+//    a tree of pairwise merges produces the global top-K.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "morse_internal.cuh"
+
+namespace morse {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct Consts {
+  float ax, bx, ay, by;  // pixel coordinates p = a t + b
+};
+
+__device__ __forceinline__ bool key_less(const Entry &a, const Entry &b) {
+  return a.chi2 < b.chi2 || (a.chi2 == b.chi2 && a.idx < b.idx);
+}
+
+// Per-trajectory constants from the grid tables.  Pixel coordinate along
+// the track: p = (y + L)/Delta - 1/2 with y1 = tau cos(alpha) - u0 sin(alpha),
+// y2 = tau sin(alpha) + u0 cos(alpha), tau = (t - t0)/tE, i.e. p = a t + b.
+__device__ __forceinline__ Consts traj_consts(const SearchParams &P,
+                                              long long j) {
+  long long r = j;
+  const int itE = (int)(r % P.n_tE);
+  r /= P.n_tE;
+  const int it0 = (int)(r % P.n_t0);
+  r /= P.n_t0;
+  const int ia = (int)(r % P.n_alpha);
+  const int iu = (int)(r / P.n_alpha);
+  const double k = P.invtEd[itE];   // 1/(tE Delta)
+  const double c = P.ca[ia], s = P.sa[ia];
+  const double u = P.u0v[iu], t0 = P.t0rel[it0];
+  const double ax = __dmul_rn(c, k), ay = __dmul_rn(s, k);
+  const double cx =
+      __dsub_rn(__dmul_rn(__dsub_rn(P.L, __dmul_rn(u, s)), P.invD), 0.5);
+  const double cy =
+      __dsub_rn(__dmul_rn(__dadd_rn(P.L, __dmul_rn(u, c)), P.invD), 0.5);
+  Consts o;
+  o.ax = __double2float_rn(ax);
+  o.ay = __double2float_rn(ay);
+  o.bx = __double2float_rn(__dsub_rn(cx, __dmul_rn(t0, ax)));
+  o.by = __double2float_rn(__dsub_rn(cy, __dmul_rn(t0, ay)));
+  return o;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Magnification at pixel coordinates (px, py).  Inside the map
+// (-1/2 < p < npix - 1/2): bilinear between texel centres, clamped to the
+// outermost centres (the quad of the last texel repeats its edge values).
+// Outside: the single-lens magnification at |y| about the centre of mass.
+__device__ __forceinline__ float lookupA(const SearchParams &P, float px,
+                                         float py) {
+  const bool inside = (px > -0.5f) & (px < P.hi) & (py > -0.5f) & (py < P.hi);
+  if (inside) {
+    const float cx = fmaxf(px, 0.f), cy = fmaxf(py, 0.f);
+    // floor via the 2^23 shift with round-toward-zero (cx, cy >= 0)
+    const float tx = __fadd_rz(cx, 8388608.f), ty = __fadd_rz(cy, 8388608.f);
+    const int ix = __float_as_int(tx) - 0x4B000000;
+    const int iy = __float_as_int(ty) - 0x4B000000;
+    const float fx = __fsub_rn(cx, __fsub_rn(tx, 8388608.f));
+    const float fy = __fsub_rn(cy, __fsub_rn(ty, 8388608.f));
+    const float4 q = __ldg(&P.quad[iy * P.npix + ix]);
+    const float r0 = __fmaf_rn(fx, __fsub_rn(q.y, q.x), q.x);
+    const float r1 = __fmaf_rn(fx, __fsub_rn(q.w, q.z), q.z);
+    return __fmaf_rn(fy, __fsub_rn(r1, r0), r0);
+  }
+  const float y1 = __fmaf_rn(__fadd_rn(px, 0.5f), P.dltf, -P.Lf);
+  const float y2 = __fmaf_rn(__fadd_rn(py, 0.5f), P.dltf, -P.Lf);
+  const float u2 = __fmaf_rn(y1, y1, __fmul_rn(y2, y2));
+  return __fmul_rn(__fadd_rn(u2, 2.f),
+                   rsqrt_approx(__fmul_rn(u2, __fadd_rn(u2, 4.f))));
+}
+
+// Phase 1: per-lane FP32 sums over epochs lane, lane+32, ... of
+//   S_A = sum w (A-1), S_AA = sum w (A-1)^2, S_AF = sum w (F-Fref) (A-1),
+// then an xor butterfly; the value of lane 0 is returned to all lanes so
+// that every caller sees the same rounding.
+__device__ __forceinline__ void phase1(const SearchParams &P,
+                                       const float4 *ep, const Consts c,
+                                       const int lane, float &oA, float &oAA,
+                                       float &oAF) {
+  float a = 0.f, b = 0.f, d = 0.f;
+#pragma unroll 4
+  for (int e = lane; e < P.n_ep; e += 32) {
+    const float4 v = ep[e];
+    const float px = __fmaf_rn(c.ax, v.x, c.bx);
+    const float py = __fmaf_rn(c.ay, v.x, c.by);
+    const float Ac = __fsub_rn(lookupA(P, px, py), 1.f);
+    const float wAc = __fmul_rn(v.y, Ac);
+    a = __fadd_rn(a, wAc);
+    b = __fmaf_rn(wAc, Ac, b);
+    d = __fmaf_rn(v.z, Ac, d);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a = __fadd_rn(a, __shfl_xor_sync(kFull, a, o));
+    b = __fadd_rn(b, __shfl_xor_sync(kFull, b, o));
+    d = __fadd_rn(d, __shfl_xor_sync(kFull, d, o));
+  }
+  oA = __shfl_sync(kFull, a, 0);
+  oAA = __shfl_sync(kFull, b, 0);
+  oAF = __shfl_sync(kFull, d, 0);
+}
+
+// Phase 2: chi^2 = sum w (F - Fs A - Fb)^2, written with centred values as
+// w (Fc - Fs Ac - Bc)^2, Bc = Fs + Fb - Fref.  FP32 per lane, FP64 across
+// lanes; lane 0's value is returned to all lanes.
+__device__ __forceinline__ double phase2(const SearchParams &P,
+                                         const float4 *ep, const Consts c,
+                                         const int lane, const float Fs,
+                                         const float Bc) {
+  float chi = 0.f;
+#pragma unroll 4
+  for (int e = lane; e < P.n_ep; e += 32) {
+    const float4 v = ep[e];
+    const float px = __fmaf_rn(c.ax, v.x, c.bx);
+    const float py = __fmaf_rn(c.ay, v.x, c.by);
+    const float Ac = __fsub_rn(lookupA(P, px, py), 1.f);
+    const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
+    chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
+  }
+  double x = (double)chi;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x = __dadd_rn(x, __shfl_xor_sync(kFull, x, o));
+  return __shfl_sync(kFull, x, 0);
+}
+
+struct Solved {
+  double Fs, Bc;      // Fb = Bc + Fref - Fs
+  double chi2_cf;     // closed form from the phase-1 sums
+  double bound;       // |closed form - exact| bound
+  bool degenerate;
+  bool always;        // too ill-conditioned to prune on the bound
+};
+
+// 2x2 weighted least squares (Eq. 6) in FP64 from the centred sums.
+// Degenerate rule: det <= 1e-12 S_AA S_1 (uncentred S_AA) -> Fs = 0,
+// Fb = weighted mean flux.
+__device__ __forceinline__ Solved solve2(const SearchParams &P, double SA,
+                                         double SAA, double SAF) {
+  Solved o;
+  const double S1 = P.S1, SF = P.SF, SFF = P.SFF;
+  const double SAAu = SAA + 2.0 * SA + S1;
+  const double det = SAA * S1 - SA * SA;
+  if (!(det > 1e-12 * SAAu * S1)) {
+    o.Fs = 0.0;
+    o.Bc = SF / S1;
+    o.chi2_cf = SFF - o.Bc * SF;
+    o.bound = 0.0;
+    o.degenerate = true;
+    o.always = true;
+    return o;
+  }
+  const double inv = 1.0 / det;
+  o.Fs = (S1 * SAF - SA * SF) * inv;
+  o.Bc = (SAA * SF - SA * SAF) * inv;
+  o.chi2_cf = SFF - o.Fs * SAF - o.Bc * SF;
+  // Perturbing the sums by relative gamma changes the minimum of the
+  // quadratic by at most gamma (2|Fs| T_AF + Fs^2 S_AA + 2|Fs Bc| T_A) with
+  // T_AF = sum |w Ac Fc| <= sqrt(S_AA S_FF), T_A = sum |w Ac| <= sqrt(S_1
+  // S_AA); AM-GM removes the square roots.
+  o.bound = P.gamma * (3.0 * o.Fs * o.Fs * SAA + SFF + o.Bc * o.Bc * S1);
+  const double cond = (SAA + S1) * (SAA + S1) * inv;
+  o.degenerate = false;
+  o.always = !(P.gamma * cond < 0.1);
+  return o;
+}
+
+template <bool DENSE, bool EP_SMEM>
+__global__ void __launch_bounds__(kSearchWarps * 32)
+    k_search(const SearchParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int K = P.top_k;
+
+  const float4 *ep = P.ep;
+  Entry *bufA = nullptr, *bufB = nullptr, *cand = nullptr;
+  {
+    unsigned char *p = smem;
+    if (EP_SMEM) {
+      float4 *s = reinterpret_cast<float4 *>(p);
+      for (int e = threadIdx.x; e < P.n_ep; e += blockDim.x) s[e] = P.ep[e];
+      ep = s;
+      p += sizeof(float4) * (size_t)P.n_ep;
+    }
+    if (!DENSE) {
+      bufA = reinterpret_cast<Entry *>(p);
+      bufB = bufA + K;
+      cand = bufB + K;
+    }
+  }
+  __shared__ int s_ncand, s_nkeep, s_cur;
+  __shared__ double s_thr;
+  if (threadIdx.x == 0) {
+    s_ncand = 0;
+    s_nkeep = 0;
+    s_cur = 0;
+    s_thr = CUDART_INF;
+  }
+  __syncthreads();
+
+  const long long n_groups = (P.count + 31) / 32;
+  const long long per_round = (long long)gridDim.x * kSearchWarps;
+  const long long rounds = (n_groups + per_round - 1) / per_round;
+
+  for (long long rd = 0; rd < rounds; ++rd) {
+    const long long g = (rd * gridDim.x + blockIdx.x) * kSearchWarps + warp;
+    if (g < n_groups) {
+      const long long base = g * 32;
+      const int nvalid = (int)min(32LL, P.count - base);
+      const long long my = P.first + base + lane;
+      Consts mine = traj_consts(P, lane < nvalid ? my : P.first + base);
+      float mA = 0.f, mAA = 0.f, mAF = 0.f;
+      for (int k = 0; k < nvalid; ++k) {
+        Consts c;
+        c.ax = __shfl_sync(kFull, mine.ax, k);
+        c.bx = __shfl_sync(kFull, mine.bx, k);
+        c.ay = __shfl_sync(kFull, mine.ay, k);
+        c.by = __shfl_sync(kFull, mine.by, k);
+        float sA, sAA, sAF;
+        phase1(P, ep, c, lane, sA, sAA, sAF);
+        if (lane == k) {
+          mA = sA;
+          mAA = sAA;
+          mAF = sAF;
+        }
+      }
+      const Solved sol = solve2(P, (double)mA, (double)mAA, (double)mAF);
+      const double thr = DENSE ? CUDART_INF : s_thr;
+      bool cand_me = lane < nvalid;
+      if (!DENSE && cand_me && !sol.always && thr < CUDART_INF)
+        cand_me = (sol.chi2_cf - 4.0 * sol.bound) * (1.0 - 1e-4) <= thr;
+      unsigned todo = __ballot_sync(kFull, cand_me);
+      const float myFs = __double2float_rn(sol.Fs);
+      const float myBc = __double2float_rn(sol.Bc);
+      while (todo) {
+        const int k = __ffs(todo) - 1;
+        todo &= todo - 1;
+        Consts c;
+        c.ax = __shfl_sync(kFull, mine.ax, k);
+        c.bx = __shfl_sync(kFull, mine.bx, k);
+        c.ay = __shfl_sync(kFull, mine.ay, k);
+        c.by = __shfl_sync(kFull, mine.by, k);
+        const float Fs = __shfl_sync(kFull, myFs, k);
+        const float Bc = __shfl_sync(kFull, myBc, k);
+        const double chi2 = phase2(P, ep, c, lane, Fs, Bc);
+        if (lane == k) {
+          const double x = isnan(chi2) ? CUDART_INF : chi2;
+          if (DENSE) {
+            const long long o = base + k;
+            P.dchi2[o] = x;
+            if (P.dFs) P.dFs[o] = sol.Fs;
+            if (P.dFb) P.dFb[o] = sol.Bc + P.Fref - sol.Fs;
+          } else if (x <= thr) {
+            const int pos = atomicAdd(&s_ncand, 1);
+            cand[pos].chi2 = x;
+            cand[pos].idx = P.first + base + k;
+          }
+        }
+      }
+    }
+    if (!DENSE) {
+      __syncthreads();
+      const int nc = s_ncand;
+      if (nc > 0) {
+        const int nk = s_nkeep;
+        Entry *cur = s_cur ? bufB : bufA;
+        Entry *nxt = s_cur ? bufA : bufB;
+        // rank-based merge of the sorted list cur[0..nk) with the unsorted
+        // candidates cand[0..nc); keys (chi2, idx) are unique
+        for (int i = threadIdx.x; i < nk; i += blockDim.x) {
+          const Entry e = cur[i];
+          int r = i;
+          for (int j = 0; j < nc; ++j) r += key_less(cand[j], e);
+          if (r < K) nxt[r] = e;
+        }
+        for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+          const Entry e = cand[i];
+          int lo = 0, hi = nk;  // number of cur entries below e
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (key_less(cur[mid], e))
+              lo = mid + 1;
+            else
+              hi = mid;
+          }
+          int r = lo;
+          for (int j = 0; j < nc; ++j) r += key_less(cand[j], e);
+          if (r < K) nxt[r] = e;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          const int nn = min(K, nk + nc);
+          s_nkeep = nn;
+          s_cur ^= 1;
+          s_thr = (nn == K) ? nxt[K - 1].chi2 : CUDART_INF;
+          s_ncand = 0;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (!DENSE) {
+    const int nk = s_nkeep;
+    const Entry *cur = s_cur ? bufB : bufA;
+    Entry *out = P.partial + (size_t)blockIdx.x * K;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+      Entry e;
+      if (i < nk) {
+        e = cur[i];
+      } else {
+        e.chi2 = CUDART_INF;  // unique sentinel keys sort after real ones
+        e.idx = 0x7fffffffffffffffLL - ((long long)blockIdx.x * K + i);
+      }
+      out[i] = e;
+    }
+  }
+}
+
+// One level of the merge tree: list pairs (2p, 2p+1) -> list p, keeping the
+// first k of each merged pair.  An odd last list is copied.
+__global__ void k_merge_level(const Entry *__restrict__ in, Entry *__restrict__ out,
+                              int lists, int k) {
+  const int pairs = (lists + 1) / 2;
+  const long long total = (long long)pairs * 2 * k;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(t / (2 * k));
+    const int side = (int)((t / k) & 1);
+    const int i = (int)(t % k);
+    const int la = 2 * p, lb = 2 * p + 1;
+    if (lb >= lists) {  // odd list out: copy
+      if (side == 0) out[(size_t)p * k + i] = in[(size_t)la * k + i];
+      continue;
+    }
+    const Entry *A = in + (size_t)(side ? lb : la) * k;
+    const Entry *B = in + (size_t)(side ? la : lb) * k;
+    const Entry e = A[i];
+    int lo = 0, hi = k;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (key_less(B[mid], e))
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    const int r = i + lo;
+    if (r < k) out[(size_t)p * k + r] = e;
+  }
+}
+
+// Fit fill: one warp per selected trajectory recomputes the phase-1 sums,
+// the solve and the phase-2 chi^2 with the same device functions as the
+// search, and writes the public morse_fit record.
+__global__ void k_fill(const FillParams F) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= F.k) return;
+  const SearchParams &P = F.S;
+  const Entry e = F.sel[w];
+  morse_fit r;
+  const long long total = (long long)P.n_u0 * P.n_alpha * P.n_t0 * P.n_tE;
+  if (e.idx < 0 || e.idx >= total) {
+    if (lane == 0) {
+      r.chi2 = CUDART_INF;
+      r.t0 = r.tE = r.u0 = r.alpha = r.Fs = r.Fb = 0.0;
+      r.idx = -1;
+      r.flags = 0;
+      r.reserved = 0;
+      F.out[w] = r;
+    }
+    return;
+  }
+  const Consts c = traj_consts(P, e.idx);
+  float sA, sAA, sAF;
+  phase1(P, P.ep, c, lane, sA, sAA, sAF);
+  const Solved sol = solve2(P, (double)sA, (double)sAA, (double)sAF);
+  const double chi2 = phase2(P, P.ep, c, lane, __double2float_rn(sol.Fs),
+                             __double2float_rn(sol.Bc));
+  if (lane == 0) {
+    long long q = e.idx;
+    const int itE = (int)(q % P.n_tE);
+    q /= P.n_tE;
+    const int it0 = (int)(q % P.n_t0);
+    q /= P.n_t0;
+    const int ia = (int)(q % P.n_alpha);
+    const int iu = (int)(q / P.n_alpha);
+    r.chi2 = isnan(chi2) ? CUDART_INF : chi2;
+    r.t0 = F.t0abs[it0];
+    r.tE = F.tEv[itE];
+    r.u0 = P.u0v[iu];
+    r.alpha = 2.0 * CUDART_PI * (double)ia / (double)P.n_alpha;
+    r.Fs = sol.Fs;
+    r.Fb = sol.Bc + P.Fref - sol.Fs;
+    r.idx = e.idx;
+    r.flags = sol.degenerate ? MORSE_FIT_DEGENERATE : 0;
+    r.reserved = 0;
+    F.out[w] = r;
+  }
+}
+
+__global__ void k_lightcurve(const SearchParams P, Consts c,
+                             const float *__restrict__ t, int n,
+                             float *__restrict__ A) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += gridDim.x * blockDim.x) {
+    const float px = __fmaf_rn(c.ax, t[i], c.bx);
+    const float py = __fmaf_rn(c.ay, t[i], c.by);
+    A[i] = lookupA(P, px, py);
+  }
+}
+
+}  // namespace
+
+size_t search_smem_bytes(int n_ep_smem, int top_k) {
+  return sizeof(float4) * (size_t)n_ep_smem +
+         sizeof(Entry) * ((size_t)2 * top_k + kSearchWarps * 32);
+}
+
+template <bool D, bool E>
+static void set_smem_attr(size_t smem) {
+  cudaFuncSetAttribute(k_search<D, E>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int search_blocks_per_sm(bool dense, bool ep_smem, size_t smem) {
+  int b = 0;
+  cudaError_t e;
+  if (dense && ep_smem) {
+    set_smem_attr<true, true>(smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &b, k_search<true, true>, kSearchWarps * 32, smem);
+  } else if (dense) {
+    set_smem_attr<true, false>(smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &b, k_search<true, false>, kSearchWarps * 32, smem);
+  } else if (ep_smem) {
+    set_smem_attr<false, true>(smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &b, k_search<false, true>, kSearchWarps * 32, smem);
+  } else {
+    set_smem_attr<false, false>(smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &b, k_search<false, false>, kSearchWarps * 32, smem);
+  }
+  if (e != cudaSuccess) return 0;
+  return b;
+}
+
+cudaError_t launch_search(const SearchParams &P, bool dense, bool ep_smem,
+                          int grid, size_t smem, cudaStream_t st) {
+  const int threads = kSearchWarps * 32;
+  if (dense && ep_smem)
+    k_search<true, true><<<grid, threads, smem, st>>>(P);
+  else if (dense)
+    k_search<true, false><<<grid, threads, smem, st>>>(P);
+  else if (ep_smem)
+    k_search<false, true><<<grid, threads, smem, st>>>(P);
+  else
+    k_search<false, false><<<grid, threads, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_topk_merge(Entry *a, Entry *b, int lists, int k,
+                              Entry **result, int *levels, cudaStream_t st) {
+  Entry *in = a, *out = b;
+  *levels = 0;
+  while (lists > 1) {
+    const int pairs = (lists + 1) / 2;
+    const long long total = (long long)pairs * 2 * k;
+    long long g = (total + 255) / 256;
+    if (g > 65535) g = 65535;
+    k_merge_level<<<(int)g, 256, 0, st>>>(in, out, lists, k);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ++*levels;
+    lists = pairs;
+    Entry *t = in;
+    in = out;
+    out = t;
+  }
+  *result = in;
+  return cudaSuccess;
+}
+
+cudaError_t launch_fill(const FillParams &F, cudaStream_t st) {
+  const int threads = 256;
+  const int blocks = (F.k * 32 + threads - 1) / threads;
+  k_fill<<<blocks, threads, 0, st>>>(F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lightcurve(const SearchParams &P, float ax, float bx,
+                              float ay, float by, const float *t, int n,
+                              float *A, cudaStream_t st) {
+  Consts c;
+  c.ax = ax;
+  c.bx = bx;
+  c.ay = ay;
+  c.by = by;
+  int blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_lightcurve<<<blocks, 256, 0, st>>>(P, c, t, n, A);
+  return cudaGetLastError();
+}
+
+}  // namespace morse

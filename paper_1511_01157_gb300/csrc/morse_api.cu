@@ -1,0 +1,808 @@
+// Host runtime of the MORSE GB300 library: contexts, handles, argument
+// checks, workspaces and the extern "C" entry points declared in morse.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "morse_internal.cuh"
+
+using morse::Entry;
+
+namespace {
+
+morse_status fail(morse_ctx *ctx, morse_status st, const char *fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+morse_status cuda_fail(morse_ctx *ctx, cudaError_t e, const char *where) {
+  return fail(ctx, MORSE_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define MORSE_CUDA(ctx, expr)                                     \
+  do {                                                            \
+    cudaError_t e_ = (expr);                                      \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #expr);    \
+  } while (0)
+
+// Grow-only device workspace.
+morse_status ws_reserve(morse_ctx *ctx, size_t bytes, void **out) {
+  if (bytes > ctx->ws_bytes) {
+    if (ctx->ws) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(ctx->ws);
+      ctx->ws = nullptr;
+      ctx->ws_bytes = 0;
+    }
+    size_t want = bytes + bytes / 4 + 4096;
+    if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, MORSE_ENOMEM, "workspace of %zu bytes", want);
+    }
+    ctx->ws_bytes = want;
+  }
+  *out = ctx->ws;
+  return MORSE_OK;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+void ev_begin(morse_ctx *ctx, int k) {
+  cudaEventRecord(ctx->ev[k][0], ctx->stream);
+}
+void ev_end(morse_ctx *ctx, int k) {
+  cudaEventRecord(ctx->ev[k][1], ctx->stream);
+  ctx->ev_used[k] = true;
+}
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+morse_status check_grid(morse_ctx *ctx, const morse_grid *g) {
+  if (!g) return fail(ctx, MORSE_EINVAL, "grid is NULL");
+  if (g->n_u0 < 1 || g->n_alpha < 1 || g->n_t0 < 1 || g->n_tE < 1)
+    return fail(ctx, MORSE_EINVAL, "grid axes need at least one value");
+  if (!is_fin(g->u0_lo) || !is_fin(g->u0_hi) || !is_fin(g->t0_lo) ||
+      !is_fin(g->t0_hi) || !is_fin(g->tE_lo) || !is_fin(g->tE_hi))
+    return fail(ctx, MORSE_EINVAL, "grid bounds must be finite");
+  if (!(g->tE_lo > 0.0) || !(g->tE_hi > 0.0))
+    return fail(ctx, MORSE_EINVAL, "tE bounds must be > 0");
+  if (g->u0_log && (!(g->u0_lo > 0.0) || !(g->u0_hi > 0.0)))
+    return fail(ctx, MORSE_EINVAL, "log-spaced u0 needs positive bounds");
+  if (g->top_k < 1 || g->top_k > 4096)
+    return fail(ctx, MORSE_EINVAL, "top_k must be in [1, 4096]");
+  double total = (double)g->n_u0 * g->n_alpha * g->n_t0 * g->n_tE;
+  if (total > 9.0e15)
+    return fail(ctx, MORSE_EINVAL, "grid has too many trajectories");
+  return MORSE_OK;
+}
+
+void axis(double lo, double hi, int n, int logsp, std::vector<double> &out) {
+  out.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double f = (n > 1) ? (double)i / (double)(n - 1) : 0.0;
+    out[i] = logsp ? exp(log(lo) + (log(hi) - log(lo)) * f)
+                   : lo + (hi - lo) * f;
+  }
+}
+
+// Device grid tables: u0, cos/sin alpha, t0 - t_ref, 1/(tE Delta), plus the
+// absolute t0 and tE for the output records.
+struct Tables {
+  double *u0v, *ca, *sa, *t0rel, *invtEd, *t0abs, *tEv;
+  size_t bytes;
+};
+
+size_t tables_bytes(const morse_grid *g) {
+  return sizeof(double) *
+         (size_t)(g->n_u0 + 2 * g->n_alpha + 2 * g->n_t0 + 2 * g->n_tE);
+}
+
+morse_status upload_tables(morse_ctx *ctx, const morse_grid *g, double t_ref,
+                           double dlt, void *dev, Tables *T) {
+  std::vector<double> u0, t0, tE, h;
+  axis(g->u0_lo, g->u0_hi, g->n_u0, g->u0_log, u0);
+  axis(g->t0_lo, g->t0_hi, g->n_t0, 0, t0);
+  axis(g->tE_lo, g->tE_hi, g->n_tE, g->tE_log, tE);
+  h.reserve(tables_bytes(g) / sizeof(double));
+  h.insert(h.end(), u0.begin(), u0.end());
+  for (int k = 0; k < g->n_alpha; ++k)
+    h.push_back(cos(2.0 * M_PI * (double)k / (double)g->n_alpha));
+  for (int k = 0; k < g->n_alpha; ++k)
+    h.push_back(sin(2.0 * M_PI * (double)k / (double)g->n_alpha));
+  for (double v : t0) h.push_back(v - t_ref);
+  for (double v : tE) h.push_back(1.0 / (v * dlt));
+  h.insert(h.end(), t0.begin(), t0.end());
+  h.insert(h.end(), tE.begin(), tE.end());
+  double *d = (double *)dev;
+  T->u0v = d;
+  T->ca = T->u0v + g->n_u0;
+  T->sa = T->ca + g->n_alpha;
+  T->t0rel = T->sa + g->n_alpha;
+  T->invtEd = T->t0rel + g->n_t0;
+  T->t0abs = T->invtEd + g->n_tE;
+  T->tEv = T->t0abs + g->n_t0;
+  T->bytes = h.size() * sizeof(double);
+  MORSE_CUDA(ctx, cudaMemcpyAsync(dev, h.data(), T->bytes,
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  return MORSE_OK;
+}
+
+void fill_search_params(const morse_event *ev, const morse_map *map,
+                        const morse_grid *g, const Tables &T,
+                        morse::SearchParams *P) {
+  memset(P, 0, sizeof(*P));
+  const double dlt = (2.0 * map->L) / (double)map->npix;
+  P->quad = map->quad;
+  P->npix = map->npix;
+  P->hi = (float)map->npix - 0.5f;
+  P->dltf = (float)dlt;
+  P->Lf = (float)map->L;
+  P->L = map->L;
+  P->invD = 1.0 / dlt;
+  if (ev) {
+    P->ep = ev->ep;
+    P->n_ep = (int)ev->n;
+    P->S1 = ev->S1;
+    P->SF = ev->SF;
+    P->SFF = ev->SFF;
+    P->Fref = ev->Fref;
+    const double m = (double)((ev->n + 31) / 32);
+    P->gamma = (m + 8.0) * ldexp(1.0, -24);
+  }
+  if (g) {
+    P->u0v = T.u0v;
+    P->ca = T.ca;
+    P->sa = T.sa;
+    P->t0rel = T.t0rel;
+    P->invtEd = T.invtEd;
+    P->n_u0 = g->n_u0;
+    P->n_alpha = g->n_alpha;
+    P->n_t0 = g->n_t0;
+    P->n_tE = g->n_tE;
+    P->top_k = g->top_k;
+  }
+}
+
+// Largest epoch count staged in shared memory for a given top-K.
+int ep_smem_cap(morse_ctx *ctx, int top_k) {
+  size_t fixed = morse::search_smem_bytes(0, top_k);
+  size_t budget = ctx->smem_optin > 4096 ? ctx->smem_optin - 2048 : 0;
+  if (budget <= fixed) return 0;
+  return (int)((budget - fixed) / sizeof(float4));
+}
+
+morse_status check_pair(morse_ctx *ctx, const morse_event *ev,
+                        const morse_map *map) {
+  if (!ev || !map) return fail(ctx, MORSE_EINVAL, "event or map is NULL");
+  if (ev->ctx != ctx || map->ctx != ctx)
+    return fail(ctx, MORSE_EINVAL, "event and map must belong to ctx");
+  return MORSE_OK;
+}
+
+// Run the search kernel over [first, first+count) in top-K or dense mode.
+morse_status run_search(morse_ctx *ctx, const morse_event *ev,
+                        const morse_map *map, const morse_grid *g,
+                        long long first, long long count, bool dense,
+                        morse_fit *out_host, double *chi2, double *Fs,
+                        double *Fb) {
+  const int K = dense ? 1 : g->top_k;
+  const int cap = ep_smem_cap(ctx, K);
+  const bool ep_smem = ev->n <= cap;
+  const size_t smem =
+      morse::search_smem_bytes(ep_smem ? (int)ev->n : 0, dense ? 0 : K) -
+      (dense ? sizeof(Entry) * morse::kSearchWarps * 32 : 0);
+  int bps = morse::search_blocks_per_sm(dense, ep_smem, smem);
+  if (bps < 1)
+    return fail(ctx, MORSE_EUNSUPPORTED,
+                "search kernel does not fit (epochs %lld, top_k %d)",
+                (long long)ev->n, K);
+  long long groups = (count + 31) / 32;
+  long long want = (groups + morse::kSearchWarps - 1) / morse::kSearchWarps;
+  int grid = (int)std::min<long long>((long long)bps * ctx->sm_count, want);
+  if (grid < 1) grid = 1;
+
+  // workspace: tables | partial lists A | B | selected fits | dense outputs
+  const double dlt = (2.0 * map->L) / (double)map->npix;
+  size_t off_tab = 0;
+  size_t off_pa = align_up(off_tab + tables_bytes(g), 256);
+  size_t list_bytes = dense ? 0 : sizeof(Entry) * (size_t)grid * K;
+  size_t off_pb = align_up(off_pa + list_bytes, 256);
+  size_t off_fit = align_up(off_pb + list_bytes, 256);
+  size_t fit_bytes = dense ? 0 : sizeof(morse_fit) * (size_t)K;
+  size_t off_dense = align_up(off_fit + fit_bytes, 256);
+  size_t dense_bytes = dense ? sizeof(double) * 3 * (size_t)count : 0;
+  void *ws = nullptr;
+  morse_status st = ws_reserve(ctx, off_dense + dense_bytes, &ws);
+  if (st != MORSE_OK) return st;
+  char *base = (char *)ws;
+  Tables T;
+  st = upload_tables(ctx, g, ev->t_ref, dlt, base + off_tab, &T);
+  if (st != MORSE_OK) return st;
+
+  morse::SearchParams P;
+  fill_search_params(ev, map, g, T, &P);
+  P.first = first;
+  P.count = count;
+  P.top_k = K;
+  if (dense) {
+    P.dchi2 = (double *)(base + off_dense);
+    P.dFs = P.dchi2 + count;
+    P.dFb = P.dFs + count;
+  } else {
+    P.partial = (Entry *)(base + off_pa);
+  }
+  ev_begin(ctx, 2);
+  MORSE_CUDA(ctx, morse::launch_search(P, dense, ep_smem, grid, smem,
+                                       ctx->stream));
+  ev_end(ctx, 2);
+  ctx->launches += 1;
+  if (dense) {
+    MORSE_CUDA(ctx, cudaMemcpyAsync(chi2, P.dchi2, sizeof(double) * count,
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+    if (Fs)
+      MORSE_CUDA(ctx, cudaMemcpyAsync(Fs, P.dFs, sizeof(double) * count,
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+    if (Fb)
+      MORSE_CUDA(ctx, cudaMemcpyAsync(Fb, P.dFb, sizeof(double) * count,
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+    MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return MORSE_OK;
+  }
+  Entry *sel = nullptr;
+  int levels = 0;
+  ev_begin(ctx, 3);
+  MORSE_CUDA(ctx, morse::launch_topk_merge((Entry *)(base + off_pa),
+                                           (Entry *)(base + off_pb), grid, K,
+                                           &sel, &levels, ctx->stream));
+  ev_end(ctx, 3);
+  ctx->launches += (uint64_t)levels;
+  morse::FillParams F;
+  F.S = P;
+  F.sel = sel;
+  F.k = K;
+  F.t0abs = T.t0abs;
+  F.tEv = T.tEv;
+  F.out = (morse_fit *)(base + off_fit);
+  ev_begin(ctx, 4);
+  MORSE_CUDA(ctx, morse::launch_fill(F, ctx->stream));
+  ev_end(ctx, 4);
+  ctx->launches += 1;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(out_host, F.out, sizeof(morse_fit) * K,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return MORSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *morse_status_string(morse_status st) {
+  switch (st) {
+    case MORSE_OK: return "MORSE_OK";
+    case MORSE_EINVAL: return "MORSE_EINVAL";
+    case MORSE_ENOMEM: return "MORSE_ENOMEM";
+    case MORSE_ECUDA: return "MORSE_ECUDA";
+    case MORSE_ETIMEOUT: return "MORSE_ETIMEOUT";
+    case MORSE_EDEGENERATE: return "MORSE_EDEGENERATE";
+    case MORSE_EUNSUPPORTED: return "MORSE_EUNSUPPORTED";
+  }
+  return "MORSE_UNKNOWN";
+}
+
+const char *morse_version(void) { return "morse-gb300 0.1 sm_103a"; }
+
+morse_status morse_create(morse_ctx **out, int device, void *cuda_stream) {
+  if (!out) return MORSE_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return MORSE_ECUDA;
+  }
+  if (device < 0 || device >= ndev) return MORSE_EINVAL;
+  morse_ctx *c = (morse_ctx *)calloc(1, sizeof(morse_ctx));
+  if (!c) return MORSE_ENOMEM;
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    free(c);
+    return MORSE_ECUDA;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    free(c);
+    return MORSE_ECUDA;
+  }
+  c->sm_count = prop.multiProcessorCount;
+  c->smem_optin = prop.sharedMemPerBlockOptin;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+    c->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) !=
+        cudaSuccess) {
+      free(c);
+      return MORSE_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  for (int k = 0; k < 5; ++k)
+    for (int j = 0; j < 2; ++j) cudaEventCreate(&c->ev[k][j]);
+  *out = c;
+  return MORSE_OK;
+}
+
+void morse_destroy(morse_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws) cudaFree(ctx->ws);
+  for (int k = 0; k < 5; ++k)
+    for (int j = 0; j < 2; ++j) cudaEventDestroy(ctx->ev[k][j]);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  free(ctx);
+}
+
+const char *morse_last_error(const morse_ctx *ctx) {
+  return ctx ? ctx->err : "no context";
+}
+
+morse_status morse_last_kernel_ms(const morse_ctx *ctx, int which,
+                                  double *ms) {
+  if (!ctx || !ms || which < 0 || which >= 5) return MORSE_EINVAL;
+  if (!ctx->ev_used[which]) {
+    *ms = 0.0;
+    return MORSE_OK;
+  }
+  float f = 0.f;
+  if (cudaEventElapsedTime(&f, ctx->ev[which][0], ctx->ev[which][1]) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return MORSE_ECUDA;
+  }
+  *ms = f;
+  return MORSE_OK;
+}
+
+// ------------------------------------------------------------------ maps
+static morse_map *map_alloc(morse_ctx *ctx, int npix, bool counts) {
+  morse_map *m = (morse_map *)calloc(1, sizeof(morse_map));
+  if (!m) return nullptr;
+  m->ctx = ctx;
+  m->npix = npix;
+  size_t n = (size_t)npix * npix;
+  bool ok = cudaMalloc(&m->A, n * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&m->quad, n * sizeof(float4)) == cudaSuccess &&
+            cudaMalloc(&m->tot, 2 * sizeof(unsigned long long)) == cudaSuccess;
+  if (ok && counts)
+    ok = cudaMalloc(&m->counts, n * sizeof(uint32_t)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (m->A) cudaFree(m->A);
+    if (m->quad) cudaFree(m->quad);
+    if (m->tot) cudaFree(m->tot);
+    if (m->counts) cudaFree(m->counts);
+    free(m);
+    return nullptr;
+  }
+  m->has_counts = counts;
+  return m;
+}
+
+morse_status morse_build_map(morse_ctx *ctx, double s, double q,
+                             double extent, int npix, int64_t rays_per_axis,
+                             const morse_map_opts *opts, morse_map **out) {
+  if (!ctx || !out) return MORSE_EINVAL;
+  *out = nullptr;
+  if (!(s > 0.0) || !is_fin(s) || !(q > 0.0) || !is_fin(q))
+    return fail(ctx, MORSE_EINVAL, "s and q must be finite and > 0");
+  if (!(extent > 0.0) || !is_fin(extent))
+    return fail(ctx, MORSE_EINVAL, "extent must be finite and > 0");
+  if (npix < 2 || npix > 16384)
+    return fail(ctx, MORSE_EINVAL, "npix must be in [2, 16384]");
+  if (rays_per_axis < 1 || rays_per_axis > 2147483647LL)
+    return fail(ctx, MORSE_EINVAL, "rays_per_axis must be in [1, 2^31-1]");
+  double X = 1.5 * extent;
+  int deflect = MORSE_DEFLECT_FP64;
+  int store = MORSE_STORE_FP32;
+  if (opts) {
+    if (opts->image_halfwidth > 0.0) X = opts->image_halfwidth;
+    if (!is_fin(X)) return fail(ctx, MORSE_EINVAL, "image_halfwidth");
+    deflect = opts->deflect;
+    store = opts->store | MORSE_STORE_FP32;
+    if (deflect != MORSE_DEFLECT_FP64 && deflect != MORSE_DEFLECT_FP32)
+      return fail(ctx, MORSE_EINVAL, "unknown deflect mode %d", deflect);
+    if (store & ~(MORSE_STORE_FP32 | MORSE_STORE_FP16LOG))
+      return fail(ctx, MORSE_EINVAL, "unknown store flags %d", store);
+    if (store & MORSE_STORE_FP16LOG)
+      return fail(ctx, MORSE_EUNSUPPORTED, "FP16 log10 maps not built yet");
+  }
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  morse_map *m = map_alloc(ctx, npix, true);
+  if (!m) return fail(ctx, MORSE_ENOMEM, "map of %d^2 texels", npix);
+  m->L = extent;
+  m->s = s;
+  m->q = q;
+  m->X = X;
+  m->nray = rays_per_axis;
+
+  morse::RayParams P;
+  memset(&P, 0, sizeof(P));
+  P.e1 = 1.0 / (1.0 + q);
+  P.e2 = q / (1.0 + q);
+  P.xa = -(s * P.e2);
+  P.xb = s * P.e1;
+  P.X = X;
+  P.h = (2.0 * X) / (double)rays_per_axis;
+  P.L = extent;
+  P.dlt = (2.0 * extent) / (double)npix;
+  P.e1f = (float)P.e1;
+  P.e2f = (float)P.e2;
+  P.xaf = (float)P.xa;
+  P.xbf = (float)P.xb;
+  P.x0f = (float)(-X + 0.5 * P.h);
+  P.hf = (float)P.h;
+  P.invdf = (float)(1.0 / P.dlt);
+  P.offf = (float)(extent / P.dlt);
+  P.npixf = (float)npix;
+  P.npix = npix;
+  P.nray = rays_per_axis;
+  P.tiles_x = (int)((rays_per_axis + morse::kRayTile - 1) / morse::kRayTile);
+  P.tiles_y = P.tiles_x;
+  P.counts = m->counts;
+  P.tot = m->tot;
+  size_t n = (size_t)npix * npix;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(m->counts, 0, n * sizeof(uint32_t), ctx->stream)) !=
+          cudaSuccess ||
+      (e = cudaMemsetAsync(m->tot, 0, 2 * sizeof(unsigned long long),
+                           ctx->stream)) != cudaSuccess) {
+    morse_map_free(m);
+    return cuda_fail(ctx, e, "clear map");
+  }
+  long long tiles = (long long)P.tiles_x * P.tiles_y;
+  int grid = (int)std::min<long long>(
+      tiles, (long long)morse::rayshoot_blocks_per_sm() * ctx->sm_count);
+  ev_begin(ctx, 0);
+  e = morse::launch_rayshoot(P, deflect == MORSE_DEFLECT_FP64, grid,
+                             ctx->stream);
+  ev_end(ctx, 0);
+  ctx->launches += 1;
+  if (e != cudaSuccess) {
+    morse_map_free(m);
+    return cuda_fail(ctx, e, "ray shooting launch");
+  }
+  const double f = (P.h * P.h) / (P.dlt * P.dlt);
+  ev_begin(ctx, 1);
+  e = morse::launch_counts_to_map(m->counts, npix, f, m->A, m->quad,
+                                  ctx->stream);
+  ev_end(ctx, 1);
+  ctx->launches += 1;
+  if (e != cudaSuccess) {
+    morse_map_free(m);
+    return cuda_fail(ctx, e, "counts to map launch");
+  }
+  unsigned long long tot[2] = {0, 0};
+  e = cudaMemcpyAsync(tot, m->tot, sizeof(tot), cudaMemcpyDeviceToHost,
+                      ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    morse_map_free(m);
+    return cuda_fail(ctx, e, "map build");
+  }
+  m->off_map = tot[0];
+  m->lost = tot[1];
+  *out = m;
+  return MORSE_OK;
+}
+
+morse_status morse_map_from_host(morse_ctx *ctx, const float *A, int npix,
+                                 double extent, morse_map **out) {
+  if (!ctx || !out || !A) return MORSE_EINVAL;
+  *out = nullptr;
+  if (npix < 2 || npix > 16384)
+    return fail(ctx, MORSE_EINVAL, "npix must be in [2, 16384]");
+  if (!(extent > 0.0) || !is_fin(extent))
+    return fail(ctx, MORSE_EINVAL, "extent must be finite and > 0");
+  size_t n = (size_t)npix * npix;
+  for (size_t k = 0; k < n; ++k)
+    if (!(A[k] >= 0.0f) || !isfinite(A[k]))
+      return fail(ctx, MORSE_EINVAL, "map value %zu is negative or not finite",
+                  k);
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  morse_map *m = map_alloc(ctx, npix, false);
+  if (!m) return fail(ctx, MORSE_ENOMEM, "map of %d^2 texels", npix);
+  m->L = extent;
+  cudaError_t e = cudaMemcpyAsync(m->A, A, n * sizeof(float),
+                                  cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) {
+    e = morse::launch_quads_from_A(m->A, npix, m->quad, ctx->stream);
+    ctx->launches += 1;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    morse_map_free(m);
+    return cuda_fail(ctx, e, "map upload");
+  }
+  *out = m;
+  return MORSE_OK;
+}
+
+morse_status morse_map_counts(const morse_map *map, uint32_t *host_counts,
+                              uint64_t *off_map, uint64_t *lost) {
+  if (!map) return MORSE_EINVAL;
+  morse_ctx *ctx = map->ctx;
+  if (!map->has_counts)
+    return fail(ctx, MORSE_EINVAL, "map was not built by ray shooting");
+  if (host_counts) {
+    size_t n = (size_t)map->npix * map->npix;
+    MORSE_CUDA(ctx, cudaMemcpyAsync(host_counts, map->counts,
+                                    n * sizeof(uint32_t),
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+    MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  if (off_map) *off_map = map->off_map;
+  if (lost) *lost = map->lost;
+  return MORSE_OK;
+}
+
+morse_status morse_map_values(const morse_map *map, float *host_A) {
+  if (!map || !host_A) return MORSE_EINVAL;
+  morse_ctx *ctx = map->ctx;
+  size_t n = (size_t)map->npix * map->npix;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(host_A, map->A, n * sizeof(float),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return MORSE_OK;
+}
+
+morse_status morse_map_info(const morse_map *map, int *npix, double *extent,
+                            double *s, double *q) {
+  if (!map) return MORSE_EINVAL;
+  if (npix) *npix = map->npix;
+  if (extent) *extent = map->L;
+  if (s) *s = map->s;
+  if (q) *q = map->q;
+  return MORSE_OK;
+}
+
+void morse_map_free(morse_map *map) {
+  if (!map) return;
+  cudaStreamSynchronize(map->ctx->stream);
+  if (map->A) cudaFree(map->A);
+  if (map->quad) cudaFree(map->quad);
+  if (map->tot) cudaFree(map->tot);
+  if (map->counts) cudaFree(map->counts);
+  free(map);
+}
+
+// ------------------------------------------------------------------ events
+morse_status morse_event_create(morse_ctx *ctx, const double *t,
+                                const double *flux, const double *sigma,
+                                int64_t n, double t_ref, morse_event **out) {
+  if (!ctx || !out) return MORSE_EINVAL;
+  *out = nullptr;
+  if (!t || !flux || !sigma) return fail(ctx, MORSE_EINVAL, "NULL array");
+  if (n < 3) return fail(ctx, MORSE_EINVAL, "need at least 3 epochs");
+  if (n > 0x7fffffffLL) return fail(ctx, MORSE_EINVAL, "too many epochs");
+  if (!is_fin(t_ref)) return fail(ctx, MORSE_EINVAL, "t_ref not finite");
+  for (int64_t i = 0; i < n; ++i) {
+    if (!is_fin(t[i]) || !is_fin(flux[i]) || !is_fin(sigma[i]))
+      return fail(ctx, MORSE_EINVAL, "epoch %lld has a non-finite value",
+                  (long long)i);
+    if (!(sigma[i] > 0.0))
+      return fail(ctx, MORSE_EINVAL, "epoch %lld has sigma <= 0",
+                  (long long)i);
+  }
+  // weights, weighted mean flux, FP32 storage; the FP64 constants are sums
+  // of the stored FP32 values so that the device data is self-consistent
+  std::vector<float4> h((size_t)n);
+  double sw = 0.0, swf = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double w = 1.0 / (sigma[i] * sigma[i]);
+    sw += w;
+    swf += w * flux[i];
+  }
+  const double Fref = swf / sw;
+  double S1 = 0.0, SF = 0.0, SFF = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double w = 1.0 / (sigma[i] * sigma[i]);
+    double fc = flux[i] - Fref;
+    float4 v;
+    v.x = (float)(t[i] - t_ref);
+    v.y = (float)w;
+    v.z = (float)(w * fc);
+    v.w = (float)fc;
+    if (!isfinite(v.y) || !isfinite(v.z) || v.y <= 0.0f)
+      return fail(ctx, MORSE_EINVAL,
+                  "epoch %lld: weight 1/sigma^2 outside FP32 range",
+                  (long long)i);
+    h[(size_t)i] = v;
+    S1 += (double)v.y;
+    SF += (double)v.z;
+    SFF += (double)v.z * (double)v.w;
+  }
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  morse_event *ev = (morse_event *)calloc(1, sizeof(morse_event));
+  if (!ev) return fail(ctx, MORSE_ENOMEM, "event");
+  if (cudaMalloc(&ev->ep, sizeof(float4) * (size_t)n) != cudaSuccess) {
+    cudaGetLastError();
+    free(ev);
+    return fail(ctx, MORSE_ENOMEM, "event of %lld epochs", (long long)n);
+  }
+  cudaError_t e = cudaMemcpyAsync(ev->ep, h.data(), sizeof(float4) * (size_t)n,
+                                  cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    cudaFree(ev->ep);
+    free(ev);
+    return cuda_fail(ctx, e, "event upload");
+  }
+  ev->ctx = ctx;
+  ev->n = n;
+  ev->t_ref = t_ref;
+  ev->S1 = S1;
+  ev->SF = SF;
+  ev->SFF = SFF;
+  ev->Fref = Fref;
+  *out = ev;
+  return MORSE_OK;
+}
+
+void morse_event_free(morse_event *ev) {
+  if (!ev) return;
+  cudaStreamSynchronize(ev->ctx->stream);
+  if (ev->ep) cudaFree(ev->ep);
+  free(ev);
+}
+
+morse_status morse_event_info(const morse_event *ev, int64_t *n,
+                              double *t_ref) {
+  if (!ev) return MORSE_EINVAL;
+  if (n) *n = ev->n;
+  if (t_ref) *t_ref = ev->t_ref;
+  return MORSE_OK;
+}
+
+// ------------------------------------------------------------------ search
+morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
+                             const morse_map *map, const morse_grid *grid,
+                             morse_fit *out) {
+  if (!ctx || !out) return MORSE_EINVAL;
+  morse_status st = check_pair(ctx, ev, map);
+  if (st != MORSE_OK) return st;
+  if ((st = check_grid(ctx, grid)) != MORSE_OK) return st;
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  long long total =
+      (long long)grid->n_u0 * grid->n_alpha * grid->n_t0 * grid->n_tE;
+  return run_search(ctx, ev, map, grid, 0, total, false, out, nullptr,
+                    nullptr, nullptr);
+}
+
+morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
+                                   const morse_map *map,
+                                   const morse_grid *grid, int64_t first,
+                                   int64_t count, double *chi2, double *Fs,
+                                   double *Fb) {
+  if (!ctx || !chi2) return MORSE_EINVAL;
+  morse_status st = check_pair(ctx, ev, map);
+  if (st != MORSE_OK) return st;
+  if ((st = check_grid(ctx, grid)) != MORSE_OK) return st;
+  long long total =
+      (long long)grid->n_u0 * grid->n_alpha * grid->n_t0 * grid->n_tE;
+  if (first < 0 || count < 0 || first + count > total)
+    return fail(ctx, MORSE_EINVAL, "range [%lld, %lld) outside the grid",
+                (long long)first, (long long)(first + count));
+  if (count == 0) return MORSE_OK;
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  return run_search(ctx, ev, map, grid, first, count, true, nullptr, chi2, Fs,
+                    Fb);
+}
+
+morse_status morse_search(morse_ctx *ctx, const double *t, const double *flux,
+                          const double *sigma, int64_t n, double t_ref,
+                          double s, double q, double extent, int npix,
+                          int64_t rays_per_axis, const morse_map_opts *opts,
+                          const morse_grid *grid, morse_fit *out) {
+  if (!ctx || !out) return MORSE_EINVAL;
+  morse_status st = check_grid(ctx, grid);
+  if (st != MORSE_OK) return st;
+  morse_event *ev = nullptr;
+  morse_map *map = nullptr;
+  st = morse_event_create(ctx, t, flux, sigma, n, t_ref, &ev);
+  if (st == MORSE_OK)
+    st = morse_build_map(ctx, s, q, extent, npix, rays_per_axis, opts, &map);
+  if (st == MORSE_OK) st = morse_grid_chi2(ctx, ev, map, grid, out);
+  morse_map_free(map);
+  morse_event_free(ev);
+  return st;
+}
+
+morse_status morse_lightcurve(morse_ctx *ctx, const morse_map *map,
+                              double t0, double tE, double u0, double alpha,
+                              const double *t, int64_t n, double *A_out) {
+  if (!ctx || !map || !t || !A_out) return MORSE_EINVAL;
+  if (map->ctx != ctx) return fail(ctx, MORSE_EINVAL, "map of another ctx");
+  if (!is_fin(t0) || !is_fin(tE) || !is_fin(u0) || !is_fin(alpha) ||
+      !(tE > 0.0))
+    return fail(ctx, MORSE_EINVAL, "trajectory parameters");
+  if (n < 0 || n > 0x7fffffffLL) return fail(ctx, MORSE_EINVAL, "n");
+  if (n == 0) return MORSE_OK;
+  for (int64_t i = 0; i < n; ++i)
+    if (!is_fin(t[i])) return fail(ctx, MORSE_EINVAL, "time not finite");
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  std::vector<float> tf((size_t)n);
+  for (int64_t i = 0; i < n; ++i) tf[(size_t)i] = (float)(t[i] - t0);
+  void *ws = nullptr;
+  size_t bytes = 2 * sizeof(float) * (size_t)n;
+  morse_status st = ws_reserve(ctx, bytes, &ws);
+  if (st != MORSE_OK) return st;
+  float *dt = (float *)ws, *dA = dt + n;
+  morse::SearchParams P;
+  Tables T;
+  memset(&T, 0, sizeof(T));
+  fill_search_params(nullptr, map, nullptr, T, &P);
+  const double dlt = (2.0 * map->L) / (double)map->npix;
+  const double k = 1.0 / (tE * dlt);
+  const double c = cos(alpha), s = sin(alpha);
+  const float ax = (float)(c * k), ay = (float)(s * k);
+  const float bx = (float)((map->L - u0 * s) / dlt - 0.5);
+  const float by = (float)((map->L + u0 * c) / dlt - 0.5);
+  std::vector<float> hA((size_t)n);
+  MORSE_CUDA(ctx, cudaMemcpyAsync(dt, tf.data(), sizeof(float) * n,
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  MORSE_CUDA(ctx, morse::launch_lightcurve(P, ax, bx, ay, by, dt, (int)n, dA,
+                                           ctx->stream));
+  ctx->launches += 1;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(hA.data(), dA, sizeof(float) * n,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int64_t i = 0; i < n; ++i) A_out[i] = hA[(size_t)i];
+  return MORSE_OK;
+}
+
+morse_status morse_launch_count(const morse_ctx *ctx, uint64_t *n) {
+  if (!ctx || !n) return MORSE_EINVAL;
+  *n = ctx->launches;
+  return MORSE_OK;
+}
+
+morse_status morse_topk_merge(const morse_fit *const *lists,
+                              const int *counts, int n_lists, int k,
+                              morse_fit *out) {
+  if (!out || k < 1 || n_lists < 0 || (n_lists > 0 && (!lists || !counts)))
+    return MORSE_EINVAL;
+  std::vector<morse_fit> all;
+  for (int i = 0; i < n_lists; ++i) {
+    if (counts[i] < 0 || (counts[i] > 0 && !lists[i])) return MORSE_EINVAL;
+    for (int j = 0; j < counts[i]; ++j)
+      if (lists[i][j].idx >= 0) all.push_back(lists[i][j]);
+  }
+  std::sort(all.begin(), all.end(), [](const morse_fit &a, const morse_fit &b) {
+    return a.chi2 < b.chi2 || (a.chi2 == b.chi2 && a.idx < b.idx);
+  });
+  for (int j = 0; j < k; ++j) {
+    if (j < (int)all.size()) {
+      out[j] = all[(size_t)j];
+    } else {
+      memset(&out[j], 0, sizeof(morse_fit));
+      out[j].chi2 = INFINITY;
+      out[j].idx = -1;
+    }
+  }
+  return MORSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// Internal declarations of the MORSE GB300 library: handle layouts, kernel
+// parameter blocks and launchers.  Not part of the public ABI (morse.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "morse.h"
+
+struct morse_ctx {
+  int device;
+  cudaStream_t stream;
+  bool own_stream;
+  int sm_count;
+  size_t smem_optin;        // max dynamic shared memory per block
+  char err[512];
+  void *ws;                 // device workspace (grow-only)
+  size_t ws_bytes;
+  cudaEvent_t ev[5][2];     // per-kernel timing events
+  bool ev_used[5];
+  uint64_t launches;        // kernels launched by this context
+};
+
+struct morse_map {
+  morse_ctx *ctx;
+  int npix;
+  double L, s, q, X;
+  int64_t nray;
+  bool has_counts;
+  uint32_t *counts;         // [npix*npix] ray counts (device)
+  float *A;                 // [npix*npix] FP32 magnification (device)
+  float4 *quad;             // [npix*npix] 2x2 texel neighbourhoods (device)
+  unsigned long long *tot;  // [2] off-map, lost (device)
+  uint64_t off_map, lost;
+};
+
+struct morse_event {
+  morse_ctx *ctx;
+  int64_t n;
+  double t_ref;
+  float4 *ep;               // [n] (t - t_ref, w, w (F - F_ref), F - F_ref)
+  double S1, SF, SFF, Fref; // FP64 sums of the stored FP32 values
+};
+
+namespace morse {
+
+// ---------------------------------------------------------------- maps
+struct RayParams {
+  double e1, e2, xa, xb;    // lens mass fractions and positions
+  double X, h, L, dlt;      // image half-width, ray spacing, map half-width,
+                            // texel size
+  float e1f, e2f, xaf, xbf; // FP32 copies
+  float x0f, hf;            // first ray centre, ray spacing
+  float invdf, offf;        // v = y / Delta + L / Delta
+  float npixf;
+  int npix;
+  int64_t nray;
+  int tiles_x, tiles_y;
+  uint32_t *counts;
+  unsigned long long *tot;
+};
+
+constexpr int kRayTile = 256;     // rays per tile side
+constexpr int kRayWin = 128;      // shared-memory window side (bins)
+constexpr int kRayThreads = 512;  // threads per ray-shooting block
+
+cudaError_t launch_rayshoot(const RayParams &P, bool fp64, int grid,
+                            cudaStream_t st);
+cudaError_t launch_counts_to_map(const uint32_t *counts, int npix, double f,
+                                 float *A, float4 *quad, cudaStream_t st);
+cudaError_t launch_quads_from_A(const float *A, int npix, float4 *quad,
+                                cudaStream_t st);
+int rayshoot_blocks_per_sm();
+
+// ---------------------------------------------------------------- search
+struct Entry {
+  double chi2;
+  long long idx;
+};
+
+struct SearchParams {
+  // map
+  const float4 *quad;
+  int npix;
+  float hi;                 // npix - 0.5 (upper pixel-coordinate bound)
+  float dltf, Lf;
+  double L, invD;           // map half-width, 1/Delta
+  // event
+  const float4 *ep;
+  int n_ep;
+  double S1, SF, SFF, Fref;
+  double gamma;             // relative bound of the FP32 phase-1 sums
+  // grid tables (device, FP64)
+  const double *u0v, *ca, *sa, *t0rel, *invtEd;
+  int n_u0, n_alpha, n_t0, n_tE;
+  long long first, count;   // trajectory index range
+  int top_k;
+  // outputs
+  Entry *partial;           // [gridDim.x][top_k] (top-K mode)
+  double *dchi2, *dFs, *dFb;  // [count] (dense mode)
+};
+
+struct FillParams {
+  SearchParams S;
+  const Entry *sel;         // [k] selected (chi2, idx)
+  int k;
+  const double *t0abs, *tEv;  // absolute t0 and tE tables
+  morse_fit *out;           // [k]
+};
+
+constexpr int kSearchWarps = 16;
+
+size_t search_smem_bytes(int n_ep_smem, int top_k);
+int search_blocks_per_sm(bool dense, bool ep_smem, size_t smem);
+cudaError_t launch_search(const SearchParams &P, bool dense, bool ep_smem,
+                          int grid, size_t smem, cudaStream_t st);
+// Merge `lists` sorted lists of `k` entries (ping-pong between a and b) into
+// one; returns the buffer that holds the result.
+cudaError_t launch_topk_merge(Entry *a, Entry *b, int lists, int k,
+                              Entry **result, int *levels, cudaStream_t st);
+cudaError_t launch_fill(const FillParams &F, cudaStream_t st);
+cudaError_t launch_lightcurve(const SearchParams &P, float ax, float bx,
+                              float ay, float by, const float *t, int n,
+                              float *A, cudaStream_t st);
+
+}  // namespace morse
