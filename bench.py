@@ -4,15 +4,16 @@ Workload: the full (s, q) search of one event -- s 31 log-spaced in
 [0.3, 3], q 21 log-spaced in [1e-5, 1e-1] (651 maps), each map 1024 x 1024
 texels over [-2, 2]^2 from 10^4 x 10^4 FP32-deflected rays, a 3000-epoch
 light curve, 40 u0 x 72 alpha x 25 t0 x 20 tE = 1.44 M trajectories per
-map, top-K = 256.  One step = one (s, q) map of that sweep: ray shooting,
-counts -> texels, the trajectory chi^2 search, the top-K merge and the fit
-records.  Steps walk the (s, q) grid; under torchrun rank r takes maps
-r, r + N, ... (no collective on the data path, weak scaling).
+map, top-K = 256.  One step = that whole search (morse_sweep): for each of
+the 651 maps, ray shooting, counts -> texels, the trajectory chi^2 search,
+the top-K merge and the fit records.  Under torchrun every rank searches
+its own event (seeded by rank) over all 651 maps: no collective on the data
+path, weak scaling.
 
 Metric: trajectory-epoch chi^2 evaluations per second (whole job).  Also
 reported: rays/s of the map build, the dominant kernel's roofline, the CPU
-oracle on a bounded sample, and the end-to-end rate through morse_search
-from host buffers.
+oracle on a bounded sample, and the end-to-end rate through
+morse_search_sweep from host buffers.
 
 `--impl reference` times the CPU oracle (the plain FP64 definition) on the
 host cores, each step a bounded sample of the same workload.
@@ -52,9 +53,9 @@ PROFILE = os.path.join(ROOT, "profiles", "k_search_cfg1.md")
 def workload_config(cfg):
     g = cfg["grid"]
     return {
-        "workload": "full (s,q) search of one 3000-epoch event; one step = "
-                    "one (s,q) map of the 31x21 sweep",
-        "maps_total": cfg["n_s"] * cfg["n_q"], "maps_per_step": 1,
+        "workload": "full (s,q) search of one 3000-epoch event: 31 s x 21 q "
+                    "= 651 maps per step",
+        "maps_per_step": cfg["n_s"] * cfg["n_q"],
         "npix": cfg["npix"], "extent": cfg["L"],
         "rays_per_map": cfg["nray"] ** 2, "deflect": "fp32",
         "epochs": cfg["n"],
@@ -62,15 +63,15 @@ def workload_config(cfg):
         g["n_tE"], "top_k": cfg["top_k"],
         "grid": f'{g["n_u0"]}u0 x {g["n_alpha"]}alpha x {g["n_t0"]}t0 x '
                 f'{g["n_tE"]}tE',
-        "l2": "flushed between steps (256 MB write); the 16 MB map texels "
-              "are produced inside each step and read from L2 by design",
+        "l2": "flushed between steps (256 MB write); each 16 MB map is "
+              "built inside the step and read from L2 by design",
     }
 
 
-def sq_of(step, rank, world, cfg):
+def sq_lists(cfg):
     s_ax, q_ax = synth.sq_axes(cfg)
-    k = (step * world + rank) % (len(s_ax) * len(q_ax))
-    return float(s_ax[k // len(q_ax)]), float(q_ax[k % len(q_ax)])
+    S, Q = np.meshgrid(s_ax, q_ax, indexing="ij")
+    return S.ravel().copy(), Q.ravel().copy()
 
 
 # ---------------------------------------------------------------- clocks
@@ -168,17 +169,17 @@ def recorded_traffic():
     return bytes_
 
 
-def make_event(ctx, m, cfg):
+def make_event(ctx, m, cfg, seed):
     """Synthetic 3000-epoch light curve: the truth magnification is read
     through the library from a map of the truth lens (self-consistent
     injection), then noise and outliers are drawn by ``synth``."""
     truth = ctx.build_map(cfg["s"], cfg["q"], cfg["L"], cfg["npix"],
                           cfg["nray"], image_halfwidth=cfg["X"],
                           deflect="fp32")
-    t = synth.epoch_times(cfg["n"], cfg["seed"], cfg["t0"])
+    t = synth.epoch_times(cfg["n"], seed, cfg["t0"])
     A = ctx.lightcurve(truth, cfg["t0"], cfg["tE"], cfg["u0"], cfg["alpha"],
                        t)
-    F, sig = synth.photometry(cfg["Fs"] * A + cfg["Fb"], cfg["seed"],
+    F, sig = synth.photometry(cfg["Fs"] * A + cfg["Fb"], seed,
                               cfg["outliers"])
     truth.free()
     return t, F, sig
@@ -228,8 +229,9 @@ def max_over_ranks(x, world):
 def oracle_sample(cfg, frac, seed, nthreads, sq=None):
     """Time the oracle on a bounded sample: one FP64 map build plus a seeded
     contiguous slice of `frac` of the trajectories.  Returns the rate in
-    trajectory-epoch evals/s for a full step extrapolated from the sample,
-    and the description of the sample."""
+    trajectory-epoch evals/s of one map's search extrapolated from the
+    sample (the 651-map step is 651 such maps), and the sample's
+    description."""
     import oracle as orc
     g = cfg["grid"]
     og = orc.Grid(g["n_u0"], g["n_alpha"], g["n_t0"], g["n_tE"], g["u0_lo"],
@@ -271,18 +273,20 @@ def run_reference(args, cfg):
     orc.build()
     nth = os.cpu_count() or 1
     frac = args.ref_frac
+    S, Q = sq_lists(cfg)
     for w in range(args.warmup):
         oracle_sample(cfg, frac * 0.1, 100 + w, nth)
     vals, walls = [], []
     for k in range(args.steps):
-        sq = sq_of(k, 0, 1, cfg)
+        sq = (float(S[k % len(S)]), float(Q[k % len(Q)]))
         t0 = time.perf_counter()
         r = oracle_sample(cfg, frac, 1000 + k, nth, sq=sq)
         walls.append(time.perf_counter() - t0)
         vals.append(r["value"])
     value = float(np.mean(vals))
-    evals_step = cfg["grid"]["n_u0"] * cfg["grid"]["n_alpha"] * \
-        cfg["grid"]["n_t0"] * cfg["grid"]["n_tE"] * cfg["n"]
+    g = cfg["grid"]
+    evals_step = (g["n_u0"] * g["n_alpha"] * g["n_t0"] * g["n_tE"] *
+                  cfg["n"] * len(S))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -291,7 +295,9 @@ def run_reference(args, cfg):
         "dtype": "f64", "data": "synthetic",
         "config": workload_config(cfg),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": nth,
-                         "kind": "oracle", "sample": r["sample"]},
+                         "kind": "oracle",
+                         "sample": r["sample"] + "; one (s,q) map per step, "
+                         "full 651-map step extrapolated linearly"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "wall_s_per_sample_step": float(np.mean(walls)),
@@ -310,26 +316,24 @@ def run_gpu(args, cfg):
     stream = torch.cuda.Stream(device=dev)
     ctx = m.Context(dev, stream=stream)
     grid = grid_of(m, cfg)
-    n_traj = grid.size
-    t, F, sig = make_event(ctx, m, cfg)
+    S, Q = sq_lists(cfg)
+    n_maps = len(S)
+    # weak scaling: every rank searches its own event over all 651 maps
+    t, F, sig = make_event(ctx, m, cfg, cfg["seed"] + rank)
     ev = ctx.event(t, F, sig)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32,
                         device=f"cuda:{dev}")
-    evals_step = n_traj * len(t)
-    rays_step = cfg["nray"] ** 2
+    evals_step = grid.size * len(t) * n_maps
+    rays_step = cfg["nray"] ** 2 * n_maps
 
-    def step(k):
-        s, q = sq_of(k, rank, world, cfg)
-        mp = ctx.build_map(s, q, cfg["L"], cfg["npix"], cfg["nray"],
-                           image_halfwidth=cfg["X"], deflect="fp32")
-        fits = ctx.grid_chi2(ev, mp, grid)
-        ms = [ctx.kernel_ms(i) for i in range(5)]
-        mp.free()
-        return fits, ms
+    def step():
+        fits = ctx.sweep(ev, S, Q, cfg["L"], cfg["npix"], cfg["nray"], grid,
+                         image_halfwidth=cfg["X"], deflect="fp32")
+        return fits, [ctx.kernel_ms(i) for i in range(5)]
 
     with torch.cuda.stream(stream):
         for w in range(args.warmup):
-            step(w)
+            step()
             flush.fill_(float(w))
         torch.cuda.synchronize()
         barrier(world)
@@ -342,20 +346,20 @@ def run_gpu(args, cfg):
         with ClockSampler(dev) as clk:
             ev0.record(stream)
             for k in range(args.steps):
-                fits, ms = step(args.warmup + k)
+                fits, ms = step()
                 kernel_ms.append(ms)
-                if best is None or fits["chi2"][0] < best:
-                    best = float(fits["chi2"][0])
+                b = float(fits["chi2"].min())
+                best = b if best is None else min(best, b)
                 flush.fill_(float(k))
             ev1.record(stream)
             torch.cuda.synchronize()
         elapsed = ev0.elapsed_time(ev1) / 1e3
-        launches = ctx.launch_count() - launches0 + args.steps  # + flushes
+        launches = ctx.launch_count() - launches0
         barrier(world)
         torch.cuda.synchronize()
         elapsed = max_over_ranks(elapsed, world)
 
-        # end to end through morse_search with host buffers (pinned)
+        # end to end through morse_search_sweep from pinned host buffers
         tp = torch.from_numpy(np.ascontiguousarray(t)).pin_memory().numpy()
         Fp = torch.from_numpy(np.ascontiguousarray(F)).pin_memory().numpy()
         sp = torch.from_numpy(np.ascontiguousarray(sig)).pin_memory().numpy()
@@ -364,14 +368,13 @@ def run_gpu(args, cfg):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(e2e_steps):
-            s, q = sq_of(args.warmup + k, rank, world, cfg)
-            ctx.search(tp, Fp, sp, 0.0, s, q, cfg["L"], cfg["npix"],
-                       cfg["nray"], grid, image_halfwidth=cfg["X"],
-                       deflect="fp32")
+            ctx.search_sweep(tp, Fp, sp, 0.0, S, Q, cfg["L"], cfg["npix"],
+                             cfg["nray"], grid, image_halfwidth=cfg["X"],
+                             deflect="fp32")
         torch.cuda.synchronize()
         e2e_elapsed = max_over_ranks(time.perf_counter() - t0, world)
 
-    km = np.array(kernel_ms)  # [steps, 5]
+    km = np.array(kernel_ms)  # [steps, 5], each summed over the 651 maps
     search_ms = float(km[:, 2].mean())
     ray_ms = float(km[:, 0].mean())
     value = evals_step * args.steps * world / elapsed
@@ -385,6 +388,7 @@ def run_gpu(args, cfg):
     achieved = evals_step * ALG_INSTR_PER_EVAL / (search_ms * 1e-3) / 1e12
     traffic = recorded_traffic()
     clocks = clk.summary()
+    per_launch = evals_step // n_maps
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -395,25 +399,26 @@ def run_gpu(args, cfg):
         "config": workload_config(cfg),
         "rays_per_s": rays_step * args.steps * world / elapsed,
         "rays_per_s_kernel": rays_step / (ray_ms * 1e-3),
-        "kernel_ms": {"rayshoot": ray_ms,
-                      "counts_to_map": float(km[:, 1].mean()),
-                      "search": search_ms, "topk_merge": float(km[:, 3].mean()),
-                      "fill": float(km[:, 4].mean())},
+        "kernel_ms_per_step": {
+            "rayshoot": ray_ms, "counts_to_map": float(km[:, 1].mean()),
+            "search": search_ms, "topk_merge": float(km[:, 3].mean()),
+            "fill": float(km[:, 4].mean())},
         "roofline": {
             "kernel": "k_search", "bound": "alu", "achieved": achieved,
             "peak": peak_instr, "unit": "T FP32-instr/s",
             "frac": achieved / peak_instr, "traffic": traffic,
             "algorithmic": f"{ALG_INSTR_PER_EVAL} FP32 instr per "
-                           f"trajectory-epoch x {evals_step} per launch",
+                           f"trajectory-epoch x {per_launch} per launch",
             "peak_source": f"{props.multi_processor_count} SMs x "
                            f"{FP32_LANES_PER_SM} FP32 lanes x {sm_max} MHz "
                            f"({peak_kind} sm_max_mhz)"},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(tp.nbytes + Fp.nbytes + sp.nbytes),
-                "d2h_bytes_per_step": int(grid.top_k * m.FIT_DTYPE.itemsize),
+                "d2h_bytes_per_step": int(grid.top_k * n_maps *
+                                          m.FIT_DTYPE.itemsize),
                 "steps": e2e_steps,
-                "path": "morse_search (event upload + map build + search + "
-                        "fits to host)"},
+                "path": "morse_search_sweep (event upload, 651 map builds "
+                        "and searches, fits to host)"},
         "gpu_launches": int(launches),
         "best_chi2": best,
         "clocks": clocks,
@@ -421,10 +426,11 @@ def run_gpu(args, cfg):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nth = os.cpu_count() or 1
         r = oracle_sample(cfg, args.cpu_frac, 7, nth)
-        line["cpu_baseline"] = {"value": r["value"], "unit": UNIT,
-                                "cores": nth, "kind": "oracle",
-                                "sample": r["sample"],
-                                "rays_per_s": r["rays_per_s"]}
+        line["cpu_baseline"] = {
+            "value": r["value"], "unit": UNIT, "cores": nth, "kind": "oracle",
+            "sample": r["sample"] + "; one (s,q) map, the 651-map step "
+                      "extrapolated linearly",
+            "rays_per_s": r["rays_per_s"]}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -437,7 +443,7 @@ def run_gpu(args, cfg):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="morse",
                     choices=["morse", "reference"])

@@ -202,6 +202,31 @@ morse_status morse_search(morse_ctx *ctx, const double *t, const double *flux,
                           int64_t rays_per_axis, const morse_map_opts *opts,
                           const morse_grid *grid, morse_fit *out);
 
+/* The full (s, q) search of one light curve (§4.1: a grid of maps in
+ * (log d, log q), each searched over trajectories, §4.2): for each of the
+ * n_maps lenses (s[i], q[i]) build the map (as morse_build_map, same
+ * extent, npix, rays and opts for all) and search the grid (as
+ * morse_grid_chi2).  out (host) receives n_maps * top_k fits, map i's list
+ * at out[i*top_k].  The event stays on the device; maps are built one at a
+ * time into storage the context reuses, so memory does not grow with
+ * n_maps.  Errors: EINVAL, ENOMEM, ECUDA. */
+morse_status morse_sweep(morse_ctx *ctx, const morse_event *ev,
+                         const double *s, const double *q, int n_maps,
+                         double extent, int npix, int64_t rays_per_axis,
+                         const morse_map_opts *opts, const morse_grid *grid,
+                         morse_fit *out);
+
+/* morse_sweep from host buffers: copies the light curve to the device
+ * (as morse_event_create), runs the sweep and frees the event.  This is the
+ * end-to-end call of the plain method.  Errors as the calls it combines. */
+morse_status morse_search_sweep(morse_ctx *ctx, const double *t,
+                                const double *flux, const double *sigma,
+                                int64_t n, double t_ref, const double *s,
+                                const double *q, int n_maps, double extent,
+                                int npix, int64_t rays_per_axis,
+                                const morse_map_opts *opts,
+                                const morse_grid *grid, morse_fit *out);
+
 /* Map magnification A(t_i) along one trajectory at n host times t (same
  * lookup as the search), written to A_out (host, n doubles).
  * Errors: EINVAL, ENOMEM, ECUDA. */
@@ -218,9 +243,10 @@ morse_status morse_topk_merge(const morse_fit *const *lists,
                               const int *counts, int n_lists, int k,
                               morse_fit *out);
 
-/* Timing of the most recent morse_build_map / morse_grid_chi2 kernels on
- * the context stream, in milliseconds (CUDA events): which = 0 ray
- * shooting, 1 counts-to-map, 2 grid search, 3 top-K merge, 4 fit fill. */
+/* Device time of the kernels of the most recent call on this context, in
+ * milliseconds (CUDA events on the context stream), summed over every
+ * launch of that kind in the call: which = 0 ray shooting, 1 counts-to-map,
+ * 2 grid search, 3 top-K merge, 4 fit fill; 5..7 reserved (0). */
 morse_status morse_last_kernel_ms(const morse_ctx *ctx, int which,
                                   double *ms);
 

@@ -107,6 +107,9 @@ _SIGS = {
     "morse_grid_chi2_dense": (_S, [_P, _P, _P, _P, _I64, _I64, _P, _P, _P]),
     "morse_search": (_S, [_P, _P, _P, _P, _I64, _D, _D, _D, _D, _I, _I64, _P,
                           _P, _P]),
+    "morse_sweep": (_S, [_P, _P, _P, _P, _I, _D, _I, _I64, _P, _P, _P]),
+    "morse_search_sweep": (_S, [_P, _P, _P, _P, _I64, _D, _P, _P, _I, _D, _I,
+                                _I64, _P, _P, _P]),
     "morse_lightcurve": (_S, [_P, _P, _D, _D, _D, _D, _P, _I64, _P]),
     "morse_topk_merge": (_S, [_P, _P, _I, _I, _P]),
     "morse_last_kernel_ms": (_S, [_P, _I, _P]),
@@ -255,6 +258,45 @@ class Context:
                                ctypes.byref(opts), ctypes.byref(grid),
                                _ptr(out))
         self._check(st, "morse_search")
+        return out
+
+    def sweep(self, event, s, q, extent, npix, rays_per_axis, grid: Grid,
+              image_halfwidth=None, deflect="fp32"):
+        """Full (s, q) search of a device-resident event (morse_sweep):
+        returns fits[n_maps, top_k]."""
+        s, q = _f64(s), _f64(q)
+        if len(s) != len(q):
+            raise ValueError("s and q lists differ in length")
+        opts = MapOpts(float(image_halfwidth or 0.0),
+                       DEFLECT_FP64 if deflect == "fp64" else DEFLECT_FP32,
+                       STORE_FP32)
+        out = np.zeros((len(s), grid.top_k), dtype=FIT_DTYPE)
+        st = _lib.morse_sweep(self._h, event._h, _ptr(s), _ptr(q), len(s),
+                              float(extent), int(npix), int(rays_per_axis),
+                              ctypes.byref(opts), ctypes.byref(grid),
+                              _ptr(out))
+        self._check(st, "morse_sweep")
+        return out
+
+    def search_sweep(self, t, flux, sigma, t_ref, s, q, extent, npix,
+                     rays_per_axis, grid: Grid, image_halfwidth=None,
+                     deflect="fp32"):
+        """morse_search_sweep: the full (s, q) search from host buffers."""
+        t, flux, sigma = _f64(t), _f64(flux), _f64(sigma)
+        s, q = _f64(s), _f64(q)
+        if len(s) != len(q):
+            raise ValueError("s and q lists differ in length")
+        opts = MapOpts(float(image_halfwidth or 0.0),
+                       DEFLECT_FP64 if deflect == "fp64" else DEFLECT_FP32,
+                       STORE_FP32)
+        out = np.zeros((len(s), grid.top_k), dtype=FIT_DTYPE)
+        st = _lib.morse_search_sweep(self._h, _ptr(t), _ptr(flux),
+                                     _ptr(sigma), len(t), float(t_ref),
+                                     _ptr(s), _ptr(q), len(s), float(extent),
+                                     int(npix), int(rays_per_axis),
+                                     ctypes.byref(opts), ctypes.byref(grid),
+                                     _ptr(out))
+        self._check(st, "morse_search_sweep")
         return out
 
     def lightcurve(self, map_, t0, tE, u0, alpha, t):

@@ -49,9 +49,14 @@ __device__ __forceinline__ bool key_less(const Entry &a, const Entry &b) {
   return a.chi2 < b.chi2 || (a.chi2 == b.chi2 && a.idx < b.idx);
 }
 
-// Per-trajectory constants from the grid tables.  Pixel coordinate along
-// the track: p = (y + L)/Delta - 1/2 with y1 = tau cos(alpha) - u0 sin(alpha),
-// y2 = tau sin(alpha) + u0 cos(alpha), tau = (t - t0)/tE, i.e. p = a t + b.
+// Per-trajectory constants from the grid tables.  The kernel works in
+// centred pixel coordinates v = (y + L)/Delta - 1/2 - floor(npix/2) =
+// y/Delta + coff (coff = -1/2 for even npix, 0 for odd), so that texel i
+// (counting from 0 at the map edge) is centred at v = i - floor(npix/2) and
+// the map centre,
+// where the caustics of close and resonant lenses lie, has the finest FP32
+// resolution.  With y1 = tau cos(alpha) - u0 sin(alpha), y2 = tau sin(alpha)
+// + u0 cos(alpha) and tau = (t - t0)/tE the coordinates are v = a t + b.
 __device__ __forceinline__ Consts traj_consts(const SearchParams &P,
                                               long long j) {
   long long r = j;
@@ -65,10 +70,8 @@ __device__ __forceinline__ Consts traj_consts(const SearchParams &P,
   const double c = P.ca[ia], s = P.sa[ia];
   const double u = P.u0v[iu], t0 = P.t0rel[it0];
   const double ax = __dmul_rn(c, k), ay = __dmul_rn(s, k);
-  const double cx =
-      __dsub_rn(__dmul_rn(__dsub_rn(P.L, __dmul_rn(u, s)), P.invD), 0.5);
-  const double cy =
-      __dsub_rn(__dmul_rn(__dadd_rn(P.L, __dmul_rn(u, c)), P.invD), 0.5);
+  const double cx = __dadd_rn(__dmul_rn(-__dmul_rn(u, s), P.invD), P.coff);
+  const double cy = __dadd_rn(__dmul_rn(__dmul_rn(u, c), P.invD), P.coff);
   Consts o;
   o.ax = __double2float_rn(ax);
   o.ay = __double2float_rn(ay);
@@ -83,28 +86,31 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   return r;
 }
 
-// Magnification at pixel coordinates (px, py).  Inside the map
-// (-1/2 < p < npix - 1/2): bilinear between texel centres, clamped to the
-// outermost centres (the quad of the last texel repeats its edge values).
-// Outside: the single-lens magnification at |y| about the centre of mass.
-__device__ __forceinline__ float lookupA(const SearchParams &P, float px,
-                                         float py) {
-  const bool inside = (px > -0.5f) & (px < P.hi) & (py > -0.5f) & (py < P.hi);
+// Magnification at centred pixel coordinates (vx, vy).  Inside the map
+// (-npix/2 - 1/2 < v < npix/2 - 1/2): bilinear between texel centres,
+// clamped to the outermost centres (the quad of the last texel repeats its
+// edge values).  Outside: the single-lens magnification at |y| about the
+// centre of mass, y = (v - coff) Delta.
+__device__ __forceinline__ float lookupA(const SearchParams &P, float vx,
+                                         float vy) {
+  const bool inside =
+      (vx > P.vlo) & (vx < P.vhi) & (vy > P.vlo) & (vy < P.vhi);
   if (inside) {
-    const float cx = fmaxf(px, 0.f), cy = fmaxf(py, 0.f);
-    // floor via the 2^23 shift with round-toward-zero (cx, cy >= 0)
-    const float tx = __fadd_rz(cx, 8388608.f), ty = __fadd_rz(cy, 8388608.f);
-    const int ix = __float_as_int(tx) - 0x4B000000;
-    const int iy = __float_as_int(ty) - 0x4B000000;
-    const float fx = __fsub_rn(cx, __fsub_rn(tx, 8388608.f));
-    const float fy = __fsub_rn(cy, __fsub_rn(ty, 8388608.f));
+    const float cx = fmaxf(vx, P.vmin), cy = fmaxf(vy, P.vmin);
+    // floor: adding 1.5 * 2^23 rounding down leaves floor(c) in the low
+    // mantissa bits; the fraction c - floor(c) is exact
+    const float tx = __fadd_rd(cx, 12582912.f), ty = __fadd_rd(cy, 12582912.f);
+    const int ix = __float_as_int(tx) - 0x4B400000 + P.half;
+    const int iy = __float_as_int(ty) - 0x4B400000 + P.half;
+    const float fx = __fsub_rn(cx, __fsub_rn(tx, 12582912.f));
+    const float fy = __fsub_rn(cy, __fsub_rn(ty, 12582912.f));
     const float4 q = __ldg(&P.quad[iy * P.npix + ix]);
     const float r0 = __fmaf_rn(fx, __fsub_rn(q.y, q.x), q.x);
     const float r1 = __fmaf_rn(fx, __fsub_rn(q.w, q.z), q.z);
     return __fmaf_rn(fy, __fsub_rn(r1, r0), r0);
   }
-  const float y1 = __fmaf_rn(__fadd_rn(px, 0.5f), P.dltf, -P.Lf);
-  const float y2 = __fmaf_rn(__fadd_rn(py, 0.5f), P.dltf, -P.Lf);
+  const float y1 = __fmul_rn(__fadd_rn(vx, P.voff), P.dltf);
+  const float y2 = __fmul_rn(__fadd_rn(vy, P.voff), P.dltf);
   const float u2 = __fmaf_rn(y1, y1, __fmul_rn(y2, y2));
   return __fmul_rn(__fadd_rn(u2, 2.f),
                    rsqrt_approx(__fmul_rn(u2, __fadd_rn(u2, 4.f))));
@@ -206,7 +212,7 @@ __device__ __forceinline__ Solved solve2(const SearchParams &P, double SA,
 }
 
 template <bool DENSE, bool EP_SMEM>
-__global__ void __launch_bounds__(kSearchWarps * 32)
+__global__ void __launch_bounds__(kSearchWarps * 32, 2)
     k_search(const SearchParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;

@@ -1,5 +1,6 @@
 // Host runtime of the MORSE GB300 library: contexts, handles, argument
-// checks, workspaces and the extern "C" entry points declared in morse.h.
+// checks, workspaces, per-call kernel timing and the extern "C" entry
+// points declared in morse.h.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -9,6 +10,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <new>
 #include <vector>
 
 #include "morse_internal.cuh"
@@ -37,6 +39,12 @@ morse_status cuda_fail(morse_ctx *ctx, cudaError_t e, const char *where) {
     if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #expr);    \
   } while (0)
 
+#define MORSE_TRY(expr)                     \
+  do {                                      \
+    morse_status s_ = (expr);               \
+    if (s_ != MORSE_OK) return s_;          \
+  } while (0)
+
 // Grow-only device workspace.
 morse_status ws_reserve(morse_ctx *ctx, size_t bytes, void **out) {
   if (bytes > ctx->ws_bytes) {
@@ -59,14 +67,52 @@ morse_status ws_reserve(morse_ctx *ctx, size_t bytes, void **out) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-void ev_begin(morse_ctx *ctx, int k) {
-  cudaEventRecord(ctx->ev[k][0], ctx->stream);
-}
-void ev_end(morse_ctx *ctx, int k) {
-  cudaEventRecord(ctx->ev[k][1], ctx->stream);
-  ctx->ev_used[k] = true;
+// ---------------------------------------------------------------- timing
+void call_begin(morse_ctx *ctx) {
+  ctx->rec_kind.clear();
+  for (int k = 0; k < KT_COUNT; ++k) ctx->kernel_ms[k] = 0.0;
 }
 
+int t_begin(morse_ctx *ctx, int kind) {
+  size_t r = ctx->rec_kind.size();
+  while (ctx->evpool.size() < 2 * (r + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    ctx->evpool.push_back(e);
+  }
+  ctx->rec_kind.push_back(kind);
+  cudaEventRecord(ctx->evpool[2 * r], ctx->stream);
+  return (int)r;
+}
+
+void t_end(morse_ctx *ctx, int r) {
+  if (r >= 0) cudaEventRecord(ctx->evpool[2 * (size_t)r + 1], ctx->stream);
+}
+
+// after the stream has synchronised
+void call_collect(morse_ctx *ctx) {
+  for (size_t r = 0; r < ctx->rec_kind.size(); ++r) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->evpool[2 * r], ctx->evpool[2 * r + 1]) ==
+        cudaSuccess)
+      ctx->kernel_ms[ctx->rec_kind[r]] += ms;
+    else
+      cudaGetLastError();
+  }
+  ctx->rec_kind.clear();
+}
+
+morse_status sync_and_collect(morse_ctx *ctx, const char *what) {
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+  call_collect(ctx);
+  return MORSE_OK;
+}
+
+// ---------------------------------------------------------------- checks
 bool is_fin(double x) { return std::isfinite(x); }
 
 morse_status check_grid(morse_ctx *ctx, const morse_grid *g) {
@@ -88,6 +134,141 @@ morse_status check_grid(morse_ctx *ctx, const morse_grid *g) {
   return MORSE_OK;
 }
 
+long long grid_size(const morse_grid *g) {
+  return (long long)g->n_u0 * g->n_alpha * g->n_t0 * g->n_tE;
+}
+
+struct BuildSpec {
+  double s, q, L, X;
+  int npix;
+  int64_t nray;
+  bool fp64;
+};
+
+morse_status check_build(morse_ctx *ctx, double s, double q, double extent,
+                         int npix, int64_t rays_per_axis,
+                         const morse_map_opts *opts, BuildSpec *b) {
+  if (!(s > 0.0) || !is_fin(s) || !(q > 0.0) || !is_fin(q))
+    return fail(ctx, MORSE_EINVAL, "s and q must be finite and > 0");
+  if (!(extent > 0.0) || !is_fin(extent))
+    return fail(ctx, MORSE_EINVAL, "extent must be finite and > 0");
+  if (npix < 2 || npix > 16384)
+    return fail(ctx, MORSE_EINVAL, "npix must be in [2, 16384]");
+  if (rays_per_axis < 1 || rays_per_axis > 2147483647LL)
+    return fail(ctx, MORSE_EINVAL, "rays_per_axis must be in [1, 2^31-1]");
+  double X = 1.5 * extent;
+  int deflect = MORSE_DEFLECT_FP64;
+  if (opts) {
+    if (opts->image_halfwidth > 0.0) X = opts->image_halfwidth;
+    if (!is_fin(X)) return fail(ctx, MORSE_EINVAL, "image_halfwidth");
+    deflect = opts->deflect;
+    int store = opts->store | MORSE_STORE_FP32;
+    if (deflect != MORSE_DEFLECT_FP64 && deflect != MORSE_DEFLECT_FP32)
+      return fail(ctx, MORSE_EINVAL, "unknown deflect mode %d", deflect);
+    if (store & ~(MORSE_STORE_FP32 | MORSE_STORE_FP16LOG))
+      return fail(ctx, MORSE_EINVAL, "unknown store flags %d", store);
+    if (store & MORSE_STORE_FP16LOG)
+      return fail(ctx, MORSE_EUNSUPPORTED, "FP16 log10 maps not built yet");
+  }
+  b->s = s;
+  b->q = q;
+  b->L = extent;
+  b->X = X;
+  b->npix = npix;
+  b->nray = rays_per_axis;
+  b->fp64 = deflect == MORSE_DEFLECT_FP64;
+  return MORSE_OK;
+}
+
+// ---------------------------------------------------------------- maps
+morse_map *map_alloc(morse_ctx *ctx, int npix, bool counts) {
+  morse_map *m = (morse_map *)calloc(1, sizeof(morse_map));
+  if (!m) return nullptr;
+  m->ctx = ctx;
+  m->npix = npix;
+  size_t n = (size_t)npix * npix;
+  bool ok = cudaMalloc(&m->A, n * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&m->quad, n * sizeof(float4)) == cudaSuccess &&
+            cudaMalloc(&m->tot, 2 * sizeof(unsigned long long)) == cudaSuccess;
+  if (ok && counts)
+    ok = cudaMalloc(&m->counts, n * sizeof(uint32_t)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (m->A) cudaFree(m->A);
+    if (m->quad) cudaFree(m->quad);
+    if (m->tot) cudaFree(m->tot);
+    if (m->counts) cudaFree(m->counts);
+    free(m);
+    return nullptr;
+  }
+  m->has_counts = counts;
+  return m;
+}
+
+void map_release(morse_map *m) {
+  if (!m) return;
+  if (m->A) cudaFree(m->A);
+  if (m->quad) cudaFree(m->quad);
+  if (m->tot) cudaFree(m->tot);
+  if (m->counts) cudaFree(m->counts);
+  free(m);
+}
+
+// Queue the ray shooting and the texel conversion into existing storage
+// (no host synchronisation).
+morse_status enqueue_build(morse_ctx *ctx, morse_map *m, const BuildSpec &b) {
+  m->L = b.L;
+  m->s = b.s;
+  m->q = b.q;
+  m->X = b.X;
+  m->nray = b.nray;
+  morse::RayParams P;
+  memset(&P, 0, sizeof(P));
+  P.e1 = 1.0 / (1.0 + b.q);
+  P.e2 = b.q / (1.0 + b.q);
+  P.xa = -(b.s * P.e2);
+  P.xb = b.s * P.e1;
+  P.X = b.X;
+  P.h = (2.0 * b.X) / (double)b.nray;
+  P.L = b.L;
+  P.dlt = (2.0 * b.L) / (double)b.npix;
+  P.e1f = (float)P.e1;
+  P.e2f = (float)P.e2;
+  P.xaf = (float)P.xa;
+  P.xbf = (float)P.xb;
+  P.x0f = (float)(-b.X + 0.5 * P.h);
+  P.hf = (float)P.h;
+  P.invdf = (float)(1.0 / P.dlt);
+  P.offf = (float)(b.L / P.dlt);
+  P.npixf = (float)b.npix;
+  P.npix = b.npix;
+  P.nray = b.nray;
+  P.tiles_x = (int)((b.nray + morse::kRayTile - 1) / morse::kRayTile);
+  P.tiles_y = P.tiles_x;
+  P.counts = m->counts;
+  P.tot = m->tot;
+  size_t n = (size_t)b.npix * b.npix;
+  MORSE_CUDA(ctx, cudaMemsetAsync(m->counts, 0, n * sizeof(uint32_t),
+                                  ctx->stream));
+  MORSE_CUDA(ctx, cudaMemsetAsync(m->tot, 0, 2 * sizeof(unsigned long long),
+                                  ctx->stream));
+  long long tiles = (long long)P.tiles_x * P.tiles_y;
+  int grid = (int)std::min<long long>(
+      tiles, (long long)morse::rayshoot_blocks_per_sm() * ctx->sm_count);
+  int r = t_begin(ctx, KT_RAY);
+  MORSE_CUDA(ctx, morse::launch_rayshoot(P, b.fp64, grid, ctx->stream));
+  t_end(ctx, r);
+  ctx->launches += 1;
+  const double f = (P.h * P.h) / (P.dlt * P.dlt);
+  r = t_begin(ctx, KT_MAP);
+  MORSE_CUDA(ctx, morse::launch_counts_to_map(m->counts, b.npix, f, m->A,
+                                              m->quad, ctx->stream));
+  t_end(ctx, r);
+  ctx->launches += 1;
+  return MORSE_OK;
+}
+
+// ---------------------------------------------------------------- search
 void axis(double lo, double hi, int n, int logsp, std::vector<double> &out) {
   out.resize(n);
   for (int i = 0; i < n; ++i) {
@@ -101,7 +282,6 @@ void axis(double lo, double hi, int n, int logsp, std::vector<double> &out) {
 // absolute t0 and tE for the output records.
 struct Tables {
   double *u0v, *ca, *sa, *t0rel, *invtEd, *t0abs, *tEv;
-  size_t bytes;
 };
 
 size_t tables_bytes(const morse_grid *g) {
@@ -133,54 +313,51 @@ morse_status upload_tables(morse_ctx *ctx, const morse_grid *g, double t_ref,
   T->invtEd = T->t0rel + g->n_t0;
   T->t0abs = T->invtEd + g->n_tE;
   T->tEv = T->t0abs + g->n_t0;
-  T->bytes = h.size() * sizeof(double);
-  MORSE_CUDA(ctx, cudaMemcpyAsync(dev, h.data(), T->bytes,
+  // ordered on the context stream, then waited for: the host vector is
+  // pageable and dies on return
+  MORSE_CUDA(ctx, cudaMemcpyAsync(dev, h.data(), h.size() * sizeof(double),
                                   cudaMemcpyHostToDevice, ctx->stream));
+  MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return MORSE_OK;
 }
 
-void fill_search_params(const morse_event *ev, const morse_map *map,
-                        const morse_grid *g, const Tables &T,
-                        morse::SearchParams *P) {
-  memset(P, 0, sizeof(*P));
+void map_params(const morse_map *map, morse::SearchParams *P) {
   const double dlt = (2.0 * map->L) / (double)map->npix;
   P->quad = map->quad;
   P->npix = map->npix;
-  P->hi = (float)map->npix - 0.5f;
+  P->half = map->npix / 2;
+  P->vlo = -(float)(map->npix / 2) - 0.5f;
+  P->vhi = (float)(map->npix - map->npix / 2) - 0.5f;
+  P->vmin = -(float)(map->npix / 2);
+  P->coff = 0.5 * map->npix - (double)(map->npix / 2) - 0.5;
+  P->voff = (float)(-P->coff);
   P->dltf = (float)dlt;
-  P->Lf = (float)map->L;
-  P->L = map->L;
   P->invD = 1.0 / dlt;
-  if (ev) {
-    P->ep = ev->ep;
-    P->n_ep = (int)ev->n;
-    P->S1 = ev->S1;
-    P->SF = ev->SF;
-    P->SFF = ev->SFF;
-    P->Fref = ev->Fref;
-    const double m = (double)((ev->n + 31) / 32);
-    P->gamma = (m + 8.0) * ldexp(1.0, -24);
-  }
-  if (g) {
-    P->u0v = T.u0v;
-    P->ca = T.ca;
-    P->sa = T.sa;
-    P->t0rel = T.t0rel;
-    P->invtEd = T.invtEd;
-    P->n_u0 = g->n_u0;
-    P->n_alpha = g->n_alpha;
-    P->n_t0 = g->n_t0;
-    P->n_tE = g->n_tE;
-    P->top_k = g->top_k;
-  }
 }
 
-// Largest epoch count staged in shared memory for a given top-K.
-int ep_smem_cap(morse_ctx *ctx, int top_k) {
-  size_t fixed = morse::search_smem_bytes(0, top_k);
-  size_t budget = ctx->smem_optin > 4096 ? ctx->smem_optin - 2048 : 0;
-  if (budget <= fixed) return 0;
-  return (int)((budget - fixed) / sizeof(float4));
+void event_params(const morse_event *ev, morse::SearchParams *P) {
+  P->ep = ev->ep;
+  P->n_ep = (int)ev->n;
+  P->S1 = ev->S1;
+  P->SF = ev->SF;
+  P->SFF = ev->SFF;
+  P->Fref = ev->Fref;
+  const double m = (double)((ev->n + 31) / 32);
+  P->gamma = (m + 8.0) * ldexp(1.0, -24);
+}
+
+void grid_params(const morse_grid *g, const Tables &T,
+                 morse::SearchParams *P) {
+  P->u0v = T.u0v;
+  P->ca = T.ca;
+  P->sa = T.sa;
+  P->t0rel = T.t0rel;
+  P->invtEd = T.invtEd;
+  P->n_u0 = g->n_u0;
+  P->n_alpha = g->n_alpha;
+  P->n_t0 = g->n_t0;
+  P->n_tE = g->n_tE;
+  P->top_k = g->top_k;
 }
 
 morse_status check_pair(morse_ctx *ctx, const morse_event *ev,
@@ -191,19 +368,26 @@ morse_status check_pair(morse_ctx *ctx, const morse_event *ev,
   return MORSE_OK;
 }
 
-// Run the search kernel over [first, first+count) in top-K or dense mode.
-morse_status run_search(morse_ctx *ctx, const morse_event *ev,
-                        const morse_map *map, const morse_grid *g,
-                        long long first, long long count, bool dense,
-                        morse_fit *out_host, double *chi2, double *Fs,
-                        double *Fb) {
+// Launch shape and workspace layout of one search.
+struct Plan {
+  int K;
+  bool dense, ep_smem;
+  size_t smem;
+  int grid;
+  size_t off_tab, off_pa, off_pb, off_out, bytes;
+};
+
+morse_status plan_search(morse_ctx *ctx, const morse_event *ev,
+                         const morse_grid *g, long long count, bool dense,
+                         long long n_out, Plan *pl) {
   const int K = dense ? 1 : g->top_k;
-  const int cap = ep_smem_cap(ctx, K);
-  const bool ep_smem = ev->n <= cap;
-  const size_t smem =
-      morse::search_smem_bytes(ep_smem ? (int)ev->n : 0, dense ? 0 : K) -
-      (dense ? sizeof(Entry) * morse::kSearchWarps * 32 : 0);
-  int bps = morse::search_blocks_per_sm(dense, ep_smem, smem);
+  const size_t fixed = morse::search_smem_bytes(0, dense ? 0 : K) -
+                       (dense ? sizeof(Entry) * morse::kSearchWarps * 32 : 0);
+  const size_t budget = ctx->smem_optin > 4096 ? ctx->smem_optin - 2048 : 0;
+  const bool ep_smem =
+      budget > fixed && (size_t)ev->n <= (budget - fixed) / sizeof(float4);
+  const size_t smem = fixed + (ep_smem ? sizeof(float4) * (size_t)ev->n : 0);
+  const int bps = morse::search_blocks_per_sm(dense, ep_smem, smem);
   if (bps < 1)
     return fail(ctx, MORSE_EUNSUPPORTED,
                 "search kernel does not fit (epochs %lld, top_k %d)",
@@ -212,77 +396,105 @@ morse_status run_search(morse_ctx *ctx, const morse_event *ev,
   long long want = (groups + morse::kSearchWarps - 1) / morse::kSearchWarps;
   int grid = (int)std::min<long long>((long long)bps * ctx->sm_count, want);
   if (grid < 1) grid = 1;
-
-  // workspace: tables | partial lists A | B | selected fits | dense outputs
-  const double dlt = (2.0 * map->L) / (double)map->npix;
-  size_t off_tab = 0;
-  size_t off_pa = align_up(off_tab + tables_bytes(g), 256);
+  pl->K = K;
+  pl->dense = dense;
+  pl->ep_smem = ep_smem;
+  pl->smem = smem;
+  pl->grid = grid;
+  pl->off_tab = 0;
+  pl->off_pa = align_up(tables_bytes(g), 256);
   size_t list_bytes = dense ? 0 : sizeof(Entry) * (size_t)grid * K;
-  size_t off_pb = align_up(off_pa + list_bytes, 256);
-  size_t off_fit = align_up(off_pb + list_bytes, 256);
-  size_t fit_bytes = dense ? 0 : sizeof(morse_fit) * (size_t)K;
-  size_t off_dense = align_up(off_fit + fit_bytes, 256);
-  size_t dense_bytes = dense ? sizeof(double) * 3 * (size_t)count : 0;
-  void *ws = nullptr;
-  morse_status st = ws_reserve(ctx, off_dense + dense_bytes, &ws);
-  if (st != MORSE_OK) return st;
-  char *base = (char *)ws;
-  Tables T;
-  st = upload_tables(ctx, g, ev->t_ref, dlt, base + off_tab, &T);
-  if (st != MORSE_OK) return st;
+  pl->off_pb = align_up(pl->off_pa + list_bytes, 256);
+  pl->off_out = align_up(pl->off_pb + list_bytes, 256);
+  size_t out_bytes = dense ? sizeof(double) * 3 * (size_t)n_out
+                           : sizeof(morse_fit) * (size_t)K * (size_t)n_out;
+  pl->bytes = pl->off_out + out_bytes;
+  return MORSE_OK;
+}
 
-  morse::SearchParams P;
-  fill_search_params(ev, map, g, T, &P);
-  P.first = first;
-  P.count = count;
-  P.top_k = K;
-  if (dense) {
-    P.dchi2 = (double *)(base + off_dense);
-    P.dFs = P.dchi2 + count;
-    P.dFb = P.dFs + count;
-  } else {
-    P.partial = (Entry *)(base + off_pa);
-  }
-  ev_begin(ctx, 2);
-  MORSE_CUDA(ctx, morse::launch_search(P, dense, ep_smem, grid, smem,
+// Queue the top-K search of one map: search kernel, merge tree, fit fill
+// into fits_dev[0..K).  No host synchronisation.
+morse_status enqueue_topk(morse_ctx *ctx, const Plan &pl,
+                          morse::SearchParams P, char *base,
+                          const Tables &T, morse_fit *fits_dev) {
+  P.partial = (Entry *)(base + pl.off_pa);
+  int r = t_begin(ctx, KT_SEARCH);
+  MORSE_CUDA(ctx, morse::launch_search(P, false, pl.ep_smem, pl.grid, pl.smem,
                                        ctx->stream));
-  ev_end(ctx, 2);
+  t_end(ctx, r);
   ctx->launches += 1;
-  if (dense) {
-    MORSE_CUDA(ctx, cudaMemcpyAsync(chi2, P.dchi2, sizeof(double) * count,
-                                    cudaMemcpyDeviceToHost, ctx->stream));
-    if (Fs)
-      MORSE_CUDA(ctx, cudaMemcpyAsync(Fs, P.dFs, sizeof(double) * count,
-                                      cudaMemcpyDeviceToHost, ctx->stream));
-    if (Fb)
-      MORSE_CUDA(ctx, cudaMemcpyAsync(Fb, P.dFb, sizeof(double) * count,
-                                      cudaMemcpyDeviceToHost, ctx->stream));
-    MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return MORSE_OK;
-  }
   Entry *sel = nullptr;
   int levels = 0;
-  ev_begin(ctx, 3);
-  MORSE_CUDA(ctx, morse::launch_topk_merge((Entry *)(base + off_pa),
-                                           (Entry *)(base + off_pb), grid, K,
-                                           &sel, &levels, ctx->stream));
-  ev_end(ctx, 3);
+  r = t_begin(ctx, KT_MERGE);
+  MORSE_CUDA(ctx, morse::launch_topk_merge((Entry *)(base + pl.off_pa),
+                                           (Entry *)(base + pl.off_pb),
+                                           pl.grid, pl.K, &sel, &levels,
+                                           ctx->stream));
+  t_end(ctx, r);
   ctx->launches += (uint64_t)levels;
   morse::FillParams F;
   F.S = P;
   F.sel = sel;
-  F.k = K;
+  F.k = pl.K;
   F.t0abs = T.t0abs;
   F.tEv = T.tEv;
-  F.out = (morse_fit *)(base + off_fit);
-  ev_begin(ctx, 4);
+  F.out = fits_dev;
+  r = t_begin(ctx, KT_FILL);
   MORSE_CUDA(ctx, morse::launch_fill(F, ctx->stream));
-  ev_end(ctx, 4);
+  t_end(ctx, r);
   ctx->launches += 1;
-  MORSE_CUDA(ctx, cudaMemcpyAsync(out_host, F.out, sizeof(morse_fit) * K,
-                                  cudaMemcpyDeviceToHost, ctx->stream));
-  MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return MORSE_OK;
+}
+
+// The (s, q) sweep behind morse_sweep and morse_search_sweep.
+morse_status sweep_impl(morse_ctx *ctx, const morse_event *ev,
+                        const double *s, const double *q, int n_maps,
+                        double extent, int npix, int64_t rays_per_axis,
+                        const morse_map_opts *opts, const morse_grid *grid,
+                        morse_fit *out) {
+  if (n_maps < 1 || !s || !q)
+    return fail(ctx, MORSE_EINVAL, "need n_maps >= 1 and (s, q) lists");
+  MORSE_TRY(check_grid(ctx, grid));
+  std::vector<BuildSpec> specs((size_t)n_maps);
+  for (int i = 0; i < n_maps; ++i)
+    MORSE_TRY(check_build(ctx, s[i], q[i], extent, npix, rays_per_axis, opts,
+                          &specs[(size_t)i]));
+  if (ctx->sweep_map && ctx->sweep_map->npix != npix) {
+    cudaStreamSynchronize(ctx->stream);
+    map_release(ctx->sweep_map);
+    ctx->sweep_map = nullptr;
+  }
+  if (!ctx->sweep_map) {
+    ctx->sweep_map = map_alloc(ctx, npix, true);
+    if (!ctx->sweep_map)
+      return fail(ctx, MORSE_ENOMEM, "sweep map of %d^2 texels", npix);
+  }
+  morse_map *m = ctx->sweep_map;
+  m->L = extent;
+  Plan pl;
+  MORSE_TRY(plan_search(ctx, ev, grid, grid_size(grid), false, n_maps, &pl));
+  void *ws = nullptr;
+  MORSE_TRY(ws_reserve(ctx, pl.bytes, &ws));
+  char *base = (char *)ws;
+  Tables T;
+  const double dlt = (2.0 * extent) / (double)npix;
+  MORSE_TRY(upload_tables(ctx, grid, ev->t_ref, dlt, base + pl.off_tab, &T));
+  morse::SearchParams P;
+  memset(&P, 0, sizeof(P));
+  map_params(m, &P);
+  event_params(ev, &P);
+  grid_params(grid, T, &P);
+  P.first = 0;
+  P.count = grid_size(grid);
+  morse_fit *fits = (morse_fit *)(base + pl.off_out);
+  for (int i = 0; i < n_maps; ++i) {
+    MORSE_TRY(enqueue_build(ctx, m, specs[(size_t)i]));
+    MORSE_TRY(enqueue_topk(ctx, pl, P, base, T, fits + (size_t)i * pl.K));
+  }
+  MORSE_CUDA(ctx, cudaMemcpyAsync(out, fits,
+                                  sizeof(morse_fit) * (size_t)pl.K * n_maps,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  return sync_and_collect(ctx, "sweep");
 }
 
 }  // namespace
@@ -313,16 +525,14 @@ morse_status morse_create(morse_ctx **out, int device, void *cuda_stream) {
     return MORSE_ECUDA;
   }
   if (device < 0 || device >= ndev) return MORSE_EINVAL;
-  morse_ctx *c = (morse_ctx *)calloc(1, sizeof(morse_ctx));
+  morse_ctx *c = new (std::nothrow) morse_ctx();
   if (!c) return MORSE_ENOMEM;
   c->device = device;
-  if (cudaSetDevice(device) != cudaSuccess) {
-    free(c);
-    return MORSE_ECUDA;
-  }
   cudaDeviceProp prop;
-  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
-    free(c);
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
     return MORSE_ECUDA;
   }
   c->sm_count = prop.multiProcessorCount;
@@ -333,13 +543,12 @@ morse_status morse_create(morse_ctx **out, int device, void *cuda_stream) {
   } else {
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) !=
         cudaSuccess) {
-      free(c);
+      cudaGetLastError();
+      delete c;
       return MORSE_ECUDA;
     }
     c->own_stream = true;
   }
-  for (int k = 0; k < 5; ++k)
-    for (int j = 0; j < 2; ++j) cudaEventCreate(&c->ev[k][j]);
   *out = c;
   return MORSE_OK;
 }
@@ -348,11 +557,11 @@ void morse_destroy(morse_ctx *ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->sweep_map) map_release(ctx->sweep_map);
   if (ctx->ws) cudaFree(ctx->ws);
-  for (int k = 0; k < 5; ++k)
-    for (int j = 0; j < 2; ++j) cudaEventDestroy(ctx->ev[k][j]);
+  for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
-  free(ctx);
+  delete ctx;
 }
 
 const char *morse_last_error(const morse_ctx *ctx) {
@@ -361,146 +570,41 @@ const char *morse_last_error(const morse_ctx *ctx) {
 
 morse_status morse_last_kernel_ms(const morse_ctx *ctx, int which,
                                   double *ms) {
-  if (!ctx || !ms || which < 0 || which >= 5) return MORSE_EINVAL;
-  if (!ctx->ev_used[which]) {
-    *ms = 0.0;
-    return MORSE_OK;
-  }
-  float f = 0.f;
-  if (cudaEventElapsedTime(&f, ctx->ev[which][0], ctx->ev[which][1]) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return MORSE_ECUDA;
-  }
-  *ms = f;
+  if (!ctx || !ms || which < 0 || which >= KT_COUNT) return MORSE_EINVAL;
+  *ms = ctx->kernel_ms[which];
+  return MORSE_OK;
+}
+
+morse_status morse_launch_count(const morse_ctx *ctx, uint64_t *n) {
+  if (!ctx || !n) return MORSE_EINVAL;
+  *n = ctx->launches;
   return MORSE_OK;
 }
 
 // ------------------------------------------------------------------ maps
-static morse_map *map_alloc(morse_ctx *ctx, int npix, bool counts) {
-  morse_map *m = (morse_map *)calloc(1, sizeof(morse_map));
-  if (!m) return nullptr;
-  m->ctx = ctx;
-  m->npix = npix;
-  size_t n = (size_t)npix * npix;
-  bool ok = cudaMalloc(&m->A, n * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&m->quad, n * sizeof(float4)) == cudaSuccess &&
-            cudaMalloc(&m->tot, 2 * sizeof(unsigned long long)) == cudaSuccess;
-  if (ok && counts)
-    ok = cudaMalloc(&m->counts, n * sizeof(uint32_t)) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    if (m->A) cudaFree(m->A);
-    if (m->quad) cudaFree(m->quad);
-    if (m->tot) cudaFree(m->tot);
-    if (m->counts) cudaFree(m->counts);
-    free(m);
-    return nullptr;
-  }
-  m->has_counts = counts;
-  return m;
-}
-
 morse_status morse_build_map(morse_ctx *ctx, double s, double q,
                              double extent, int npix, int64_t rays_per_axis,
                              const morse_map_opts *opts, morse_map **out) {
   if (!ctx || !out) return MORSE_EINVAL;
   *out = nullptr;
-  if (!(s > 0.0) || !is_fin(s) || !(q > 0.0) || !is_fin(q))
-    return fail(ctx, MORSE_EINVAL, "s and q must be finite and > 0");
-  if (!(extent > 0.0) || !is_fin(extent))
-    return fail(ctx, MORSE_EINVAL, "extent must be finite and > 0");
-  if (npix < 2 || npix > 16384)
-    return fail(ctx, MORSE_EINVAL, "npix must be in [2, 16384]");
-  if (rays_per_axis < 1 || rays_per_axis > 2147483647LL)
-    return fail(ctx, MORSE_EINVAL, "rays_per_axis must be in [1, 2^31-1]");
-  double X = 1.5 * extent;
-  int deflect = MORSE_DEFLECT_FP64;
-  int store = MORSE_STORE_FP32;
-  if (opts) {
-    if (opts->image_halfwidth > 0.0) X = opts->image_halfwidth;
-    if (!is_fin(X)) return fail(ctx, MORSE_EINVAL, "image_halfwidth");
-    deflect = opts->deflect;
-    store = opts->store | MORSE_STORE_FP32;
-    if (deflect != MORSE_DEFLECT_FP64 && deflect != MORSE_DEFLECT_FP32)
-      return fail(ctx, MORSE_EINVAL, "unknown deflect mode %d", deflect);
-    if (store & ~(MORSE_STORE_FP32 | MORSE_STORE_FP16LOG))
-      return fail(ctx, MORSE_EINVAL, "unknown store flags %d", store);
-    if (store & MORSE_STORE_FP16LOG)
-      return fail(ctx, MORSE_EUNSUPPORTED, "FP16 log10 maps not built yet");
-  }
+  BuildSpec b;
+  MORSE_TRY(check_build(ctx, s, q, extent, npix, rays_per_axis, opts, &b));
   MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  call_begin(ctx);
   morse_map *m = map_alloc(ctx, npix, true);
   if (!m) return fail(ctx, MORSE_ENOMEM, "map of %d^2 texels", npix);
-  m->L = extent;
-  m->s = s;
-  m->q = q;
-  m->X = X;
-  m->nray = rays_per_axis;
-
-  morse::RayParams P;
-  memset(&P, 0, sizeof(P));
-  P.e1 = 1.0 / (1.0 + q);
-  P.e2 = q / (1.0 + q);
-  P.xa = -(s * P.e2);
-  P.xb = s * P.e1;
-  P.X = X;
-  P.h = (2.0 * X) / (double)rays_per_axis;
-  P.L = extent;
-  P.dlt = (2.0 * extent) / (double)npix;
-  P.e1f = (float)P.e1;
-  P.e2f = (float)P.e2;
-  P.xaf = (float)P.xa;
-  P.xbf = (float)P.xb;
-  P.x0f = (float)(-X + 0.5 * P.h);
-  P.hf = (float)P.h;
-  P.invdf = (float)(1.0 / P.dlt);
-  P.offf = (float)(extent / P.dlt);
-  P.npixf = (float)npix;
-  P.npix = npix;
-  P.nray = rays_per_axis;
-  P.tiles_x = (int)((rays_per_axis + morse::kRayTile - 1) / morse::kRayTile);
-  P.tiles_y = P.tiles_x;
-  P.counts = m->counts;
-  P.tot = m->tot;
-  size_t n = (size_t)npix * npix;
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(m->counts, 0, n * sizeof(uint32_t), ctx->stream)) !=
-          cudaSuccess ||
-      (e = cudaMemsetAsync(m->tot, 0, 2 * sizeof(unsigned long long),
-                           ctx->stream)) != cudaSuccess) {
-    morse_map_free(m);
-    return cuda_fail(ctx, e, "clear map");
-  }
-  long long tiles = (long long)P.tiles_x * P.tiles_y;
-  int grid = (int)std::min<long long>(
-      tiles, (long long)morse::rayshoot_blocks_per_sm() * ctx->sm_count);
-  ev_begin(ctx, 0);
-  e = morse::launch_rayshoot(P, deflect == MORSE_DEFLECT_FP64, grid,
-                             ctx->stream);
-  ev_end(ctx, 0);
-  ctx->launches += 1;
-  if (e != cudaSuccess) {
-    morse_map_free(m);
-    return cuda_fail(ctx, e, "ray shooting launch");
-  }
-  const double f = (P.h * P.h) / (P.dlt * P.dlt);
-  ev_begin(ctx, 1);
-  e = morse::launch_counts_to_map(m->counts, npix, f, m->A, m->quad,
-                                  ctx->stream);
-  ev_end(ctx, 1);
-  ctx->launches += 1;
-  if (e != cudaSuccess) {
-    morse_map_free(m);
-    return cuda_fail(ctx, e, "counts to map launch");
-  }
+  morse_status st = enqueue_build(ctx, m, b);
   unsigned long long tot[2] = {0, 0};
-  e = cudaMemcpyAsync(tot, m->tot, sizeof(tot), cudaMemcpyDeviceToHost,
-                      ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  if (e != cudaSuccess) {
-    morse_map_free(m);
-    return cuda_fail(ctx, e, "map build");
+  if (st == MORSE_OK) {
+    cudaError_t e = cudaMemcpyAsync(tot, m->tot, sizeof(tot),
+                                    cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "map totals");
+  }
+  if (st == MORSE_OK) st = sync_and_collect(ctx, "map build");
+  if (st != MORSE_OK) {
+    cudaStreamSynchronize(ctx->stream);
+    map_release(m);
+    return st;
   }
   m->off_map = tot[0];
   m->lost = tot[1];
@@ -518,10 +622,11 @@ morse_status morse_map_from_host(morse_ctx *ctx, const float *A, int npix,
     return fail(ctx, MORSE_EINVAL, "extent must be finite and > 0");
   size_t n = (size_t)npix * npix;
   for (size_t k = 0; k < n; ++k)
-    if (!(A[k] >= 0.0f) || !isfinite(A[k]))
+    if (!(A[k] >= 0.0f) || !std::isfinite(A[k]))
       return fail(ctx, MORSE_EINVAL, "map value %zu is negative or not finite",
                   k);
   MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  call_begin(ctx);
   morse_map *m = map_alloc(ctx, npix, false);
   if (!m) return fail(ctx, MORSE_ENOMEM, "map of %d^2 texels", npix);
   m->L = extent;
@@ -533,7 +638,8 @@ morse_status morse_map_from_host(morse_ctx *ctx, const float *A, int npix,
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
-    morse_map_free(m);
+    cudaStreamSynchronize(ctx->stream);
+    map_release(m);
     return cuda_fail(ctx, e, "map upload");
   }
   *out = m;
@@ -581,11 +687,7 @@ morse_status morse_map_info(const morse_map *map, int *npix, double *extent,
 void morse_map_free(morse_map *map) {
   if (!map) return;
   cudaStreamSynchronize(map->ctx->stream);
-  if (map->A) cudaFree(map->A);
-  if (map->quad) cudaFree(map->quad);
-  if (map->tot) cudaFree(map->tot);
-  if (map->counts) cudaFree(map->counts);
-  free(map);
+  map_release(map);
 }
 
 // ------------------------------------------------------------------ events
@@ -625,7 +727,7 @@ morse_status morse_event_create(morse_ctx *ctx, const double *t,
     v.y = (float)w;
     v.z = (float)(w * fc);
     v.w = (float)fc;
-    if (!isfinite(v.y) || !isfinite(v.z) || v.y <= 0.0f)
+    if (!std::isfinite(v.y) || !std::isfinite(v.z) || v.y <= 0.0f)
       return fail(ctx, MORSE_EINVAL,
                   "epoch %lld: weight 1/sigma^2 outside FP32 range",
                   (long long)i);
@@ -646,6 +748,7 @@ morse_status morse_event_create(morse_ctx *ctx, const double *t,
                                   cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
+    cudaStreamSynchronize(ctx->stream);
     cudaFree(ev->ep);
     free(ev);
     return cuda_fail(ctx, e, "event upload");
@@ -681,14 +784,30 @@ morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
                              const morse_map *map, const morse_grid *grid,
                              morse_fit *out) {
   if (!ctx || !out) return MORSE_EINVAL;
-  morse_status st = check_pair(ctx, ev, map);
-  if (st != MORSE_OK) return st;
-  if ((st = check_grid(ctx, grid)) != MORSE_OK) return st;
+  MORSE_TRY(check_pair(ctx, ev, map));
+  MORSE_TRY(check_grid(ctx, grid));
   MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
-  long long total =
-      (long long)grid->n_u0 * grid->n_alpha * grid->n_t0 * grid->n_tE;
-  return run_search(ctx, ev, map, grid, 0, total, false, out, nullptr,
-                    nullptr, nullptr);
+  call_begin(ctx);
+  Plan pl;
+  MORSE_TRY(plan_search(ctx, ev, grid, grid_size(grid), false, 1, &pl));
+  void *ws = nullptr;
+  MORSE_TRY(ws_reserve(ctx, pl.bytes, &ws));
+  char *base = (char *)ws;
+  Tables T;
+  const double dlt = (2.0 * map->L) / (double)map->npix;
+  MORSE_TRY(upload_tables(ctx, grid, ev->t_ref, dlt, base + pl.off_tab, &T));
+  morse::SearchParams P;
+  memset(&P, 0, sizeof(P));
+  map_params(map, &P);
+  event_params(ev, &P);
+  grid_params(grid, T, &P);
+  P.first = 0;
+  P.count = grid_size(grid);
+  morse_fit *fits = (morse_fit *)(base + pl.off_out);
+  MORSE_TRY(enqueue_topk(ctx, pl, P, base, T, fits));
+  MORSE_CUDA(ctx, cudaMemcpyAsync(out, fits, sizeof(morse_fit) * pl.K,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  return sync_and_collect(ctx, "grid search");
 }
 
 morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
@@ -697,18 +816,80 @@ morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
                                    int64_t count, double *chi2, double *Fs,
                                    double *Fb) {
   if (!ctx || !chi2) return MORSE_EINVAL;
-  morse_status st = check_pair(ctx, ev, map);
-  if (st != MORSE_OK) return st;
-  if ((st = check_grid(ctx, grid)) != MORSE_OK) return st;
-  long long total =
-      (long long)grid->n_u0 * grid->n_alpha * grid->n_t0 * grid->n_tE;
+  MORSE_TRY(check_pair(ctx, ev, map));
+  MORSE_TRY(check_grid(ctx, grid));
+  long long total = grid_size(grid);
   if (first < 0 || count < 0 || first + count > total)
     return fail(ctx, MORSE_EINVAL, "range [%lld, %lld) outside the grid",
                 (long long)first, (long long)(first + count));
   if (count == 0) return MORSE_OK;
   MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
-  return run_search(ctx, ev, map, grid, first, count, true, nullptr, chi2, Fs,
-                    Fb);
+  call_begin(ctx);
+  Plan pl;
+  MORSE_TRY(plan_search(ctx, ev, grid, count, true, count, &pl));
+  void *ws = nullptr;
+  MORSE_TRY(ws_reserve(ctx, pl.bytes, &ws));
+  char *base = (char *)ws;
+  Tables T;
+  const double dlt = (2.0 * map->L) / (double)map->npix;
+  MORSE_TRY(upload_tables(ctx, grid, ev->t_ref, dlt, base + pl.off_tab, &T));
+  morse::SearchParams P;
+  memset(&P, 0, sizeof(P));
+  map_params(map, &P);
+  event_params(ev, &P);
+  grid_params(grid, T, &P);
+  P.first = first;
+  P.count = count;
+  P.top_k = 1;
+  P.dchi2 = (double *)(base + pl.off_out);
+  P.dFs = P.dchi2 + count;
+  P.dFb = P.dFs + count;
+  int r = t_begin(ctx, KT_SEARCH);
+  MORSE_CUDA(ctx, morse::launch_search(P, true, pl.ep_smem, pl.grid, pl.smem,
+                                       ctx->stream));
+  t_end(ctx, r);
+  ctx->launches += 1;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(chi2, P.dchi2, sizeof(double) * count,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  if (Fs)
+    MORSE_CUDA(ctx, cudaMemcpyAsync(Fs, P.dFs, sizeof(double) * count,
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+  if (Fb)
+    MORSE_CUDA(ctx, cudaMemcpyAsync(Fb, P.dFb, sizeof(double) * count,
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+  return sync_and_collect(ctx, "dense search");
+}
+
+morse_status morse_sweep(morse_ctx *ctx, const morse_event *ev,
+                         const double *s, const double *q, int n_maps,
+                         double extent, int npix, int64_t rays_per_axis,
+                         const morse_map_opts *opts, const morse_grid *grid,
+                         morse_fit *out) {
+  if (!ctx || !out) return MORSE_EINVAL;
+  if (!ev || ev->ctx != ctx)
+    return fail(ctx, MORSE_EINVAL, "event missing or of another ctx");
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  call_begin(ctx);
+  return sweep_impl(ctx, ev, s, q, n_maps, extent, npix, rays_per_axis, opts,
+                    grid, out);
+}
+
+morse_status morse_search_sweep(morse_ctx *ctx, const double *t,
+                                const double *flux, const double *sigma,
+                                int64_t n, double t_ref, const double *s,
+                                const double *q, int n_maps, double extent,
+                                int npix, int64_t rays_per_axis,
+                                const morse_map_opts *opts,
+                                const morse_grid *grid, morse_fit *out) {
+  if (!ctx || !out) return MORSE_EINVAL;
+  MORSE_TRY(check_grid(ctx, grid));
+  morse_event *ev = nullptr;
+  MORSE_TRY(morse_event_create(ctx, t, flux, sigma, n, t_ref, &ev));
+  call_begin(ctx);
+  morse_status st = sweep_impl(ctx, ev, s, q, n_maps, extent, npix,
+                               rays_per_axis, opts, grid, out);
+  morse_event_free(ev);
+  return st;
 }
 
 morse_status morse_search(morse_ctx *ctx, const double *t, const double *flux,
@@ -716,18 +897,8 @@ morse_status morse_search(morse_ctx *ctx, const double *t, const double *flux,
                           double s, double q, double extent, int npix,
                           int64_t rays_per_axis, const morse_map_opts *opts,
                           const morse_grid *grid, morse_fit *out) {
-  if (!ctx || !out) return MORSE_EINVAL;
-  morse_status st = check_grid(ctx, grid);
-  if (st != MORSE_OK) return st;
-  morse_event *ev = nullptr;
-  morse_map *map = nullptr;
-  st = morse_event_create(ctx, t, flux, sigma, n, t_ref, &ev);
-  if (st == MORSE_OK)
-    st = morse_build_map(ctx, s, q, extent, npix, rays_per_axis, opts, &map);
-  if (st == MORSE_OK) st = morse_grid_chi2(ctx, ev, map, grid, out);
-  morse_map_free(map);
-  morse_event_free(ev);
-  return st;
+  return morse_search_sweep(ctx, t, flux, sigma, n, t_ref, &s, &q, 1, extent,
+                            npix, rays_per_axis, opts, grid, out);
 }
 
 morse_status morse_lightcurve(morse_ctx *ctx, const morse_map *map,
@@ -743,23 +914,21 @@ morse_status morse_lightcurve(morse_ctx *ctx, const morse_map *map,
   for (int64_t i = 0; i < n; ++i)
     if (!is_fin(t[i])) return fail(ctx, MORSE_EINVAL, "time not finite");
   MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  call_begin(ctx);
   std::vector<float> tf((size_t)n);
   for (int64_t i = 0; i < n; ++i) tf[(size_t)i] = (float)(t[i] - t0);
   void *ws = nullptr;
-  size_t bytes = 2 * sizeof(float) * (size_t)n;
-  morse_status st = ws_reserve(ctx, bytes, &ws);
-  if (st != MORSE_OK) return st;
+  MORSE_TRY(ws_reserve(ctx, 2 * sizeof(float) * (size_t)n, &ws));
   float *dt = (float *)ws, *dA = dt + n;
   morse::SearchParams P;
-  Tables T;
-  memset(&T, 0, sizeof(T));
-  fill_search_params(nullptr, map, nullptr, T, &P);
+  memset(&P, 0, sizeof(P));
+  map_params(map, &P);
   const double dlt = (2.0 * map->L) / (double)map->npix;
   const double k = 1.0 / (tE * dlt);
   const double c = cos(alpha), s = sin(alpha);
   const float ax = (float)(c * k), ay = (float)(s * k);
-  const float bx = (float)((map->L - u0 * s) / dlt - 0.5);
-  const float by = (float)((map->L + u0 * c) / dlt - 0.5);
+  const float bx = (float)((-u0 * s) / dlt + P.coff);
+  const float by = (float)((u0 * c) / dlt + P.coff);
   std::vector<float> hA((size_t)n);
   MORSE_CUDA(ctx, cudaMemcpyAsync(dt, tf.data(), sizeof(float) * n,
                                   cudaMemcpyHostToDevice, ctx->stream));
@@ -768,14 +937,8 @@ morse_status morse_lightcurve(morse_ctx *ctx, const morse_map *map,
   ctx->launches += 1;
   MORSE_CUDA(ctx, cudaMemcpyAsync(hA.data(), dA, sizeof(float) * n,
                                   cudaMemcpyDeviceToHost, ctx->stream));
-  MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  MORSE_TRY(sync_and_collect(ctx, "light curve"));
   for (int64_t i = 0; i < n; ++i) A_out[i] = hA[(size_t)i];
-  return MORSE_OK;
-}
-
-morse_status morse_launch_count(const morse_ctx *ctx, uint64_t *n) {
-  if (!ctx || !n) return MORSE_EINVAL;
-  *n = ctx->launches;
   return MORSE_OK;
 }
 

@@ -5,7 +5,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "morse.h"
+
+// kernel kinds timed per call (morse_last_kernel_ms)
+enum { KT_RAY = 0, KT_MAP = 1, KT_SEARCH = 2, KT_MERGE = 3, KT_FILL = 4,
+       KT_COUNT = 8 };
 
 struct morse_ctx {
   int device;
@@ -16,9 +22,13 @@ struct morse_ctx {
   char err[512];
   void *ws;                 // device workspace (grow-only)
   size_t ws_bytes;
-  cudaEvent_t ev[5][2];     // per-kernel timing events
-  bool ev_used[5];
+  // per-call kernel timing: event pairs recorded around each launch, summed
+  // by kind once the call has synchronised
+  std::vector<cudaEvent_t> evpool;
+  std::vector<int> rec_kind;   // kind of record r (events 2r, 2r+1)
+  double kernel_ms[KT_COUNT];
   uint64_t launches;        // kernels launched by this context
+  morse_map *sweep_map;     // map storage reused by sweeps
 };
 
 struct morse_map {
@@ -81,10 +91,13 @@ struct Entry {
 struct SearchParams {
   // map
   const float4 *quad;
-  int npix;
-  float hi;                 // npix - 0.5 (upper pixel-coordinate bound)
-  float dltf, Lf;
-  double L, invD;           // map half-width, 1/Delta
+  int npix, half;           // npix, npix/2
+  float vlo, vhi;           // inside iff vlo < v < vhi (centred coords)
+  float vmin;               // -npix/2: clamp to the first texel centre
+  float voff;               // -coff: y = (v + voff) Delta
+  float dltf;               // Delta
+  double invD;              // 1/Delta
+  double coff;              // v = y/Delta + coff
   // event
   const float4 *ep;
   int n_ep;

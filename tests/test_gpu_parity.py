@@ -351,3 +351,29 @@ def test_cfg1_full_size_search_sampled(ctx, m, cfg1_setup):
         for j in range(64):
             if o[j] < kth * (1 - 2 * CHI2_RTOL):
                 assert int(start) + j in listed
+
+
+def test_sweep_equals_per_map_searches(ctx, m):
+    """morse_sweep (one reused map buffer, no host syncs between maps) gives
+    the same fits as building and searching each map separately, and
+    morse_search_sweep from host buffers gives the same again."""
+    c = synth.CFG0
+    t, F, sig = _event(c, n=300, seed=5)
+    ev = ctx.event(t, F, sig)
+    g = m.Grid.make(4, 9, 3, 4, 0.01, 0.4, -1.0, 1.0, 8.0, 40.0, True, True,
+                    6)
+    S = np.array([0.7, 1.0, 1.4])
+    Q = np.array([1e-3, 1e-2, 3e-4])
+    fits = ctx.sweep(ev, S, Q, 2.0, 96, 700, g, image_halfwidth=3.0,
+                     deflect="fp32")
+    assert fits.shape == (3, 6)
+    for i in range(3):
+        mp = ctx.build_map(S[i], Q[i], 2.0, 96, 700, image_halfwidth=3.0,
+                           deflect="fp32")
+        ref = ctx.grid_chi2(ev, mp, g)
+        assert np.array_equal(fits[i]["idx"], ref["idx"])
+        assert np.array_equal(fits[i]["chi2"], ref["chi2"])
+    fits2 = ctx.search_sweep(t, F, sig, 0.0, S, Q, 2.0, 96, 700, g,
+                             image_halfwidth=3.0, deflect="fp32")
+    assert np.array_equal(fits2["chi2"], fits["chi2"])
+    assert ctx.kernel_ms(2) > 0.0
