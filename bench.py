@@ -317,6 +317,9 @@ def run_gpu(args, cfg):
     ctx = m.Context(dev, stream=stream)
     grid = grid_of(m, cfg)
     S, Q = sq_lists(cfg)
+    if args.maps and args.maps < len(S):  # evenly spaced subset (profiling)
+        pick = np.linspace(0, len(S) - 1, args.maps).round().astype(int)
+        S, Q = S[pick].copy(), Q[pick].copy()
     n_maps = len(S)
     # weak scaling: every rank searches its own event over all 651 maps
     t, F, sig = make_event(ctx, m, cfg, cfg["seed"] + rank)
@@ -390,13 +393,17 @@ def run_gpu(args, cfg):
     clocks = clk.summary()
     per_launch = evals_step // n_maps
 
+    cfg_line = workload_config(cfg)
+    if n_maps != cfg["n_s"] * cfg["n_q"]:
+        cfg_line["maps_per_step"] = n_maps
+        cfg_line["workload"] += f" (SUBSET: {n_maps} maps, profiling only)"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * elapsed / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (FP64 solve and cross-lane sums)", "data": "synthetic",
-        "config": workload_config(cfg),
+        "config": cfg_line,
         "rays_per_s": rays_step * args.steps * world / elapsed,
         "rays_per_s_kernel": rays_step / (ray_ms * 1e-3),
         "kernel_ms_per_step": {
@@ -452,6 +459,9 @@ def main():
     ap.add_argument("--ref-frac", type=float, default=0.002,
                     help="trajectory fraction per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--maps", type=int, default=0,
+                    help="search an evenly spaced subset of the 651 (s,q) "
+                    "maps per step (profiling of small cases only)")
     args = ap.parse_args()
     cfg = dict(synth.CFG1)
     if args.impl == "reference":
