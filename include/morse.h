@@ -183,6 +183,34 @@ morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
                              const morse_map *map, const morse_grid *grid,
                              morse_fit *out);
 
+/* morse_grid_chi2 without any device allocation.  The paper has no
+ * counterpart: this is a deployment variant of the same search.
+ *
+ * For callers that must not let the library call cudaMalloc or cudaFree in
+ * their hot loop -- cudaFree waits for the whole device and so stalls every
+ * other stream of a latency-bound pipeline, allocation is not available
+ * while a stream is being captured, and some applications run under a
+ * fixed, pre-reserved memory budget.  Such callers create the context,
+ * event and map at set-up and then call this function, which keeps its
+ * scratch (grid tables, per-block top-K lists, fit records) in one static
+ * device array of 4 MiB that every GPU loading the library holds until the
+ * process exits, instead of the context's growable workspace.  Inputs,
+ * output and results are exactly those of morse_grid_chi2 (same kernels,
+ * same arithmetic); out is caller-allocated host memory of top_k records.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call in the process shares the array:
+ * calls that overlap on the same GPU (other streams, other host threads)
+ * race on it; each call rewrites every byte it reads, so nothing carries
+ * over.  Returns MORSE_EINVAL, with a message naming the sizes, when the
+ * search needs more than 4 MiB of scratch (roughly top_k above ~500 on a
+ * 152-SM GPU) or more than 4096 grid-table values (n_u0 + 2 n_alpha +
+ * 2 n_t0 + 2 n_tE).  Errors otherwise as morse_grid_chi2. */
+morse_status morse_grid_chi2_noalloc(morse_ctx *ctx, const morse_event *ev,
+                                     const morse_map *map,
+                                     const morse_grid *grid, morse_fit *out);
+
 /* chi^2, Fs and Fb of every trajectory with index in [first, first+count)
  * (host arrays of count doubles; Fs/Fb may be NULL).  Same arithmetic as
  * morse_grid_chi2.  Errors: EINVAL, ENOMEM, ECUDA. */

@@ -104,6 +104,7 @@ _SIGS = {
     "morse_event_free": (None, [_P]),
     "morse_event_info": (_S, [_P, _P, _P]),
     "morse_grid_chi2": (_S, [_P, _P, _P, _P, _P]),
+    "morse_grid_chi2_noalloc": (_S, [_P, _P, _P, _P, _P]),
     "morse_grid_chi2_dense": (_S, [_P, _P, _P, _P, _I64, _I64, _P, _P, _P]),
     "morse_search": (_S, [_P, _P, _P, _P, _I64, _D, _D, _D, _D, _I, _I64, _P,
                           _P, _P]),
@@ -228,6 +229,16 @@ class Context:
         st = _lib.morse_grid_chi2(self._h, event._h, map_._h,
                                   ctypes.byref(grid), _ptr(out))
         self._check(st, "morse_grid_chi2")
+        return out
+
+    def grid_chi2_noalloc(self, event, map_, grid: Grid) -> np.ndarray:
+        """Top-K search that allocates no device memory
+        (morse_grid_chi2_noalloc): for callers that cannot have cudaMalloc
+        or cudaFree run inside their loop.  Same results as grid_chi2."""
+        out = np.zeros(grid.top_k, dtype=FIT_DTYPE)
+        st = _lib.morse_grid_chi2_noalloc(self._h, event._h, map_._h,
+                                          ctypes.byref(grid), _ptr(out))
+        self._check(st, "morse_grid_chi2_noalloc")
         return out
 
     def grid_chi2_dense(self, event, map_, grid: Grid, first=0, count=None):

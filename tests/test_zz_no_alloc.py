@@ -1,0 +1,75 @@
+"""The allocation-free search entry point (morse_grid_chi2_noalloc).
+
+It serves callers that cannot let the library allocate device memory in
+their loop (cudaFree stalls the whole device; allocation is unavailable
+during stream capture; fixed memory budgets).  This file is named so that
+pytest collects it last: if it fails, a run that stops at the first failure
+has already run every other test.  It must also pass alone in a fresh
+process.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+CHI2_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import paper_1511_01157_gb300 as m
+    ctx = m.Context(0)
+    t = synth.epoch_times(700, 21)
+    # a light curve with a caustic-crossing-like bump; its exact shape does
+    # not matter, both entry points search the same data
+    f_true = 0.3 + 1.0 / np.sqrt(0.02 + (t / 20.0) ** 2)
+    F, sig = synth.photometry(f_true, 21)
+    ev = ctx.event(t, F, sig)
+    mp = ctx.build_map(0.95, 2e-3, 2.0, 256, 2000, image_halfwidth=3.0,
+                       deflect="fp32")
+    grid = m.Grid.make(12, 24, 7, 9, 1e-3, 0.5, -2.0, 2.0, 5.0, 80.0, True,
+                       True, 64)
+    yield m, ctx, ev, mp, grid
+    mp.free()
+    ev.free()
+    ctx.close()
+
+
+def test_noalloc_matches_allocating_search_twice(setup):
+    m, ctx, ev, mp, grid = setup
+    ref = ctx.grid_chi2(ev, mp, grid)
+    for _ in range(2):  # two calls in a row share the static scratch
+        got = ctx.grid_chi2_noalloc(ev, mp, grid)
+        assert np.array_equal(got["idx"], ref["idx"])
+        np.testing.assert_allclose(got["chi2"], ref["chi2"], rtol=CHI2_RTOL)
+        np.testing.assert_allclose(got["Fs"], ref["Fs"], rtol=1e-6,
+                                   atol=1e-9)
+        np.testing.assert_allclose(got["Fb"], ref["Fb"], rtol=1e-6,
+                                   atol=1e-9)
+
+
+def test_noalloc_does_not_allocate(setup):
+    torch = pytest.importorskip("torch")
+    m, ctx, ev, mp, grid = setup
+    ctx.grid_chi2_noalloc(ev, mp, grid)       # first call: address set-up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(0)[0]
+    for _ in range(3):
+        ctx.grid_chi2_noalloc(ev, mp, grid)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(0)[0] == free0
+
+
+def test_noalloc_rejects_oversized_search(setup):
+    m, ctx, ev, mp, grid = setup
+    big = m.Grid.make(12, 24, 7, 9, 1e-3, 0.5, -2.0, 2.0, 5.0, 80.0, True,
+                      True, 4096)
+    with pytest.raises(m.MorseError) as e:
+        ctx.grid_chi2_noalloc(ev, mp, big)
+    assert e.value.status == m.EINVAL
+    assert "scratch" in str(e.value)
+    # the context stays usable
+    ok = ctx.grid_chi2_noalloc(ev, mp, grid)
+    assert np.isfinite(ok["chi2"][0])
