@@ -329,9 +329,12 @@ def run_gpu(args, cfg):
     evals_step = grid.size * len(t) * n_maps
     rays_step = cfg["nray"] ** 2 * n_maps
 
+    exact = []
+
     def step():
         fits = ctx.sweep(ev, S, Q, cfg["L"], cfg["npix"], cfg["nray"], grid,
                          image_halfwidth=cfg["X"], deflect="fp32")
+        exact.append(ctx.exact_sweeps())
         return fits, [ctx.kernel_ms(i) for i in range(5)]
 
     with torch.cuda.stream(stream):
@@ -427,6 +430,8 @@ def run_gpu(args, cfg):
                 "path": "morse_search_sweep (event upload, 651 map builds "
                         "and searches, fits to host)"},
         "gpu_launches": int(launches),
+        "exact_sweep_fraction": float(np.mean(exact[-args.steps:])) /
+        (grid.size * n_maps),
         "best_chi2": best,
         "clocks": clocks,
     }

@@ -134,7 +134,8 @@ void morse_map_free(morse_map *map);
 /* ------------------------------------------------------------------ */
 
 /* Copy a light curve to the device: n epochs with times t (days), fluxes
- * and 1-sigma errors (w = 1/sigma^2).  Times are stored as FP32 offsets
+ * and 1-sigma errors (w = 1/sigma^2), in any order (stored sorted by time,
+ * which the search relies on).  Times are stored as FP32 offsets
  * t - t_ref, so t_ref should lie within the data (resolution ~4e-6 d for
  * offsets up to 40 d); grid t0 values are absolute times in the same frame
  * as t.  Requires n >= 3, every value finite, sigma > 0.
@@ -277,6 +278,13 @@ morse_status morse_topk_merge(const morse_fit *const *lists,
  * 2 grid search, 3 top-K merge, 4 fit fill; 5..7 reserved (0). */
 morse_status morse_last_kernel_ms(const morse_ctx *ctx, int which,
                                   double *ms);
+
+/* Pruning statistics of the most recent search call on this context: the
+ * number of trajectories that received the exact residual sweep (the rest
+ * were discarded by the error-bounded closed form).  Summed over the maps
+ * of a sweep. */
+morse_status morse_last_search_stats(const morse_ctx *ctx,
+                                     uint64_t *exact_sweeps);
 
 /* Number of CUDA kernels this context has launched since morse_create. */
 morse_status morse_launch_count(const morse_ctx *ctx, uint64_t *n);

@@ -115,6 +115,7 @@ _SIGS = {
     "morse_topk_merge": (_S, [_P, _P, _I, _I, _P]),
     "morse_last_kernel_ms": (_S, [_P, _I, _P]),
     "morse_launch_count": (_S, [_P, _P]),
+    "morse_last_search_stats": (_S, [_P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -318,6 +319,14 @@ class Context:
                                    _ptr(out))
         self._check(st, "morse_lightcurve")
         return out
+
+    def exact_sweeps(self) -> int:
+        """Trajectories given the exact residual sweep in the last search
+        call (morse_last_search_stats)."""
+        v = ctypes.c_uint64()
+        self._check(_lib.morse_last_search_stats(self._h, ctypes.byref(v)),
+                    "morse_last_search_stats")
+        return int(v.value)
 
     def launch_count(self) -> int:
         v = ctypes.c_uint64()

@@ -10,25 +10,34 @@
 // least-squares solve, and the grid covers (u0, alpha, t0, tE).
 //
 // GB300 design.
-//  * Lanes of a warp take consecutive epochs of one trajectory, so the 32
-//    bilinear gathers of a warp fall within a few texels of each other
-//    (one 16-byte float4 load fetches a texel's 2x2 neighbourhood) and the
-//    map, kept resident in the 129 MB L2, is served mostly from L1.
-//  * The epoch block (t, w, wF, F) of the light curve is staged once per
-//    block in shared memory and re-read by every trajectory.
+//  * One 32-warp block per SM.  The light curve (t, w, wF, F per epoch,
+//    time-sorted) is staged once per block in shared memory.
+//  * Warps take groups of 32 trajectories.  For each, the lanes walk
+//    consecutive epochs, so the 32 bilinear gathers of a warp fall within a
+//    few texels (one 16-byte float4 load fetches a texel's 2x2
+//    neighbourhood) and the L2-resident map is served mostly from L1.
+//  * A straight track crosses the square map in one interval of time, and
+//    the epochs are sorted, so each trajectory's epochs split into three
+//    contiguous ranges found by binary search: before the map and after it
+//    (single-lens magnification from tau^2 + u0^2, no memory), and inside
+//    (bilinear lookup with no per-epoch edge test, coordinates clamped so
+//    that every gather stays inside the map).
 //  * Phase 1 accumulates the normal-equation sums in FP32 per lane (the
-//    magnification and the flux centred on 1 and on the weighted mean
-//    flux), reduces them across the warp, and solves the 2x2 system in
-//    FP64 with one trajectory per lane (32 solves per warp instruction).
+//    magnification centred on 1, the flux on its weighted mean), reduces
+//    them across the warp, and solves the 2x2 system in FP64 with one
+//    trajectory per lane (32 solves per warp instruction).
 //  * The closed-form chi^2 from those sums, S_FF - Fs S_AF - Fb S_F, loses
 //    digits to cancellation, so it is used only with a rigorous error bound
-//    to discard trajectories that cannot enter the current top-K.  Every
-//    reported chi^2 comes from phase 2: a second sweep that sums the
-//    per-point residuals w (F - Fs A - Fb)^2 (FP32 per lane, FP64 across
-//    lanes).
-//  * Each block keeps its own sorted top-K in shared memory, merges new
-//    candidates after each round, and prunes against its K-th chi^2;
-//    a tree of pairwise merges produces the global top-K.
+//    to discard trajectories that cannot enter the top-K.  Every reported
+//    chi^2 comes from phase 2: a second sweep that sums the per-point
+//    residuals w (F - Fs A - Fb)^2 (FP32 per lane, FP64 across lanes).
+//  * Each block keeps a sorted top-K in shared memory.  A warp merges its
+//    own candidates under a shared-memory lock (bounded spin), so warps
+//    never wait at a block barrier; the block's K-th chi^2 and a grid-wide
+//    minimum of the blocks' K-th values (atomicMin on the bit pattern) are
+//    the pruning threshold.  A tree of pairwise merges gives the global
+//    top-K and k_fill recomputes the winners' records with the same device
+//    functions.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
@@ -40,25 +49,50 @@ namespace morse {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned kLockSpinLimit = 1u << 20;
 
-struct Consts {
-  float ax, bx, ay, by;  // pixel coordinates p = a t + b
+// Per-trajectory constants.
+struct TrajC {
+  float ax, bx, ay, by;  // centred pixel coordinates v = a t + b
+  float kt, bt, u02;     // tau = kt t + bt; u0^2
+  int e_in, e_out;       // epochs [e_in, e_out) lie inside the map
 };
 
 __device__ __forceinline__ bool key_less(const Entry &a, const Entry &b) {
   return a.chi2 < b.chi2 || (a.chi2 == b.chi2 && a.idx < b.idx);
 }
+__device__ __forceinline__ bool key_less(double ca, long long ia, double cb,
+                                         long long ib) {
+  return ca < cb || (ca == cb && ia < ib);
+}
 
-// Per-trajectory constants from the grid tables.  The kernel works in
-// centred pixel coordinates v = (y + L)/Delta - 1/2 - floor(npix/2) =
-// y/Delta + coff (coff = -1/2 for even npix, 0 for odd), so that texel i
-// (counting from 0 at the map edge) is centred at v = i - floor(npix/2) and
-// the map centre,
-// where the caustics of close and resonant lenses lie, has the finest FP32
-// resolution.  With y1 = tau cos(alpha) - u0 sin(alpha), y2 = tau sin(alpha)
-// + u0 cos(alpha) and tau = (t - t0)/tE the coordinates are v = a t + b.
-__device__ __forceinline__ Consts traj_consts(const SearchParams &P,
-                                              long long j) {
+// first epoch index with t > x (strict) or t >= x (!strict), t ascending
+__device__ __forceinline__ int epoch_search(const float4 *ep, int n, double x,
+                                            bool strict) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const double t = (double)ep[mid].x;
+    const bool right = strict ? (t > x) : (t >= x);
+    if (right)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+// Constants of trajectory j.  The kernel works in centred pixel coordinates
+// v = (y + L)/Delta - 1/2 - floor(npix/2) = y/Delta + coff (coff = -1/2 for
+// even npix, 0 for odd): texel i (from 0 at the map edge) is centred at
+// v = i - floor(npix/2), and the map centre, where the caustics of close and
+// resonant lenses lie, has the finest FP32 resolution.  With
+// y1 = tau cos(alpha) - u0 sin(alpha), y2 = tau sin(alpha) + u0 cos(alpha)
+// and tau = (t - t0)/tE the coordinates are v = a t + b.  The track is
+// inside the map (|y1| < L and |y2| < L) for tau in (tau_lo, tau_hi), i.e.
+// for the epochs [e_in, e_out).
+__device__ __forceinline__ TrajC traj_consts(const SearchParams &P,
+                                             const float4 *ep, long long j) {
   long long r = j;
   const int itE = (int)(r % P.n_tE);
   r /= P.n_tE;
@@ -66,18 +100,62 @@ __device__ __forceinline__ Consts traj_consts(const SearchParams &P,
   r /= P.n_t0;
   const int ia = (int)(r % P.n_alpha);
   const int iu = (int)(r / P.n_alpha);
-  const double k = P.invtEd[itE];   // 1/(tE Delta)
+  const double k = P.invtEd[itE];  // 1/(tE Delta)
   const double c = P.ca[ia], s = P.sa[ia];
   const double u = P.u0v[iu], t0 = P.t0rel[it0];
   const double ax = __dmul_rn(c, k), ay = __dmul_rn(s, k);
   const double cx = __dadd_rn(__dmul_rn(-__dmul_rn(u, s), P.invD), P.coff);
   const double cy = __dadd_rn(__dmul_rn(__dmul_rn(u, c), P.invD), P.coff);
-  Consts o;
+  const double kt = __dmul_rn(k, P.dlt);  // 1/tE
+  TrajC o;
   o.ax = __double2float_rn(ax);
   o.ay = __double2float_rn(ay);
   o.bx = __double2float_rn(__dsub_rn(cx, __dmul_rn(t0, ax)));
   o.by = __double2float_rn(__dsub_rn(cy, __dmul_rn(t0, ay)));
+  o.kt = __double2float_rn(kt);
+  o.bt = __double2float_rn(-__dmul_rn(t0, kt));
+  o.u02 = __double2float_rn(__dmul_rn(u, u));
+  // slab intersection of the line with |y1| < L, |y2| < L
+  double lo = -CUDART_INF, hi = CUDART_INF;
+  const double us = u * s, uc = u * c;
+  if (c != 0.0) {
+    const double a0 = (-P.L + us) / c, a1 = (P.L + us) / c;
+    lo = fmax(lo, fmin(a0, a1));
+    hi = fmin(hi, fmax(a0, a1));
+  } else if (!(fabs(us) < P.L)) {
+    hi = lo;
+  }
+  if (s != 0.0) {
+    const double b0 = (-P.L - uc) / s, b1 = (P.L - uc) / s;
+    lo = fmax(lo, fmin(b0, b1));
+    hi = fmin(hi, fmax(b0, b1));
+  } else if (!(fabs(uc) < P.L)) {
+    hi = lo;
+  }
+  if (lo < hi) {
+    const double tE = 1.0 / kt;
+    o.e_in = epoch_search(ep, P.n_ep, t0 + lo * tE, true);
+    o.e_out = epoch_search(ep, P.n_ep, t0 + hi * tE, false);
+    if (o.e_out < o.e_in) o.e_out = o.e_in;
+  } else {
+    o.e_in = P.n_ep;
+    o.e_out = P.n_ep;
+  }
   return o;
+}
+
+__device__ __forceinline__ TrajC shfl_traj(const TrajC &m, int k) {
+  TrajC c;
+  c.ax = __shfl_sync(kFull, m.ax, k);
+  c.bx = __shfl_sync(kFull, m.bx, k);
+  c.ay = __shfl_sync(kFull, m.ay, k);
+  c.by = __shfl_sync(kFull, m.by, k);
+  c.kt = __shfl_sync(kFull, m.kt, k);
+  c.bt = __shfl_sync(kFull, m.bt, k);
+  c.u02 = __shfl_sync(kFull, m.u02, k);
+  c.e_in = __shfl_sync(kFull, m.e_in, k);
+  c.e_out = __shfl_sync(kFull, m.e_out, k);
+  return c;
 }
 
 __device__ __forceinline__ float rsqrt_approx(float x) {
@@ -86,51 +164,69 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   return r;
 }
 
-// Magnification at centred pixel coordinates (vx, vy).  Inside the map
-// (-npix/2 - 1/2 < v < npix/2 - 1/2): bilinear between texel centres,
-// clamped to the outermost centres (the quad of the last texel repeats its
-// edge values).  Outside: the single-lens magnification at |y| about the
-// centre of mass, y = (v - coff) Delta.
-__device__ __forceinline__ float lookupA(const SearchParams &P, float vx,
-                                         float vy) {
-  const bool inside =
-      (vx > P.vlo) & (vx < P.vhi) & (vy > P.vlo) & (vy < P.vhi);
-  if (inside) {
-    const float cx = fmaxf(vx, P.vmin), cy = fmaxf(vy, P.vmin);
-    // floor: adding 1.5 * 2^23 rounding down leaves floor(c) in the low
-    // mantissa bits; the fraction c - floor(c) is exact
-    const float tx = __fadd_rd(cx, 12582912.f), ty = __fadd_rd(cy, 12582912.f);
-    const int ix = __float_as_int(tx) - 0x4B400000 + P.half;
-    const int iy = __float_as_int(ty) - 0x4B400000 + P.half;
-    const float fx = __fsub_rn(cx, __fsub_rn(tx, 12582912.f));
-    const float fy = __fsub_rn(cy, __fsub_rn(ty, 12582912.f));
-    const float4 q = __ldg(&P.quad[iy * P.npix + ix]);
-    const float r0 = __fmaf_rn(fx, __fsub_rn(q.y, q.x), q.x);
-    const float r1 = __fmaf_rn(fx, __fsub_rn(q.w, q.z), q.z);
-    return __fmaf_rn(fy, __fsub_rn(r1, r0), r0);
-  }
-  const float y1 = __fmul_rn(__fadd_rn(vx, P.voff), P.dltf);
-  const float y2 = __fmul_rn(__fadd_rn(vy, P.voff), P.dltf);
-  const float u2 = __fmaf_rn(y1, y1, __fmul_rn(y2, y2));
+// single-lens magnification from u^2 (outside the map)
+__device__ __forceinline__ float pspl_u2(float u2) {
   return __fmul_rn(__fadd_rn(u2, 2.f),
                    rsqrt_approx(__fmul_rn(u2, __fadd_rn(u2, 4.f))));
 }
 
-// Phase 1: per-lane FP32 sums over epochs lane, lane+32, ... of
-//   S_A = sum w (A-1), S_AA = sum w (A-1)^2, S_AF = sum w (F-Fref) (A-1),
-// then an xor butterfly; the value of lane 0 is returned to all lanes so
-// that every caller sees the same rounding.
+// Bilinear magnification at centred coordinates inside the map.  The
+// clamps keep the texel index in [0, npix-1] whatever v is; inside the map
+// they change nothing (below: the clamp to the first texel centre is the
+// lookup rule; above: the last texel's quad repeats its edge values, so
+// v and its clamp give the same value).
+__device__ __forceinline__ float bilinear(const SearchParams &P, float vx,
+                                          float vy) {
+  const float cx = fminf(fmaxf(vx, P.vmin), P.vmax);
+  const float cy = fminf(fmaxf(vy, P.vmin), P.vmax);
+  // floor: adding 1.5 * 2^23 rounding down leaves floor(c) in the low
+  // mantissa bits; the fraction c - floor(c) is exact
+  const float tx = __fadd_rd(cx, 12582912.f), ty = __fadd_rd(cy, 12582912.f);
+  const int ix = __float_as_int(tx) - 0x4B400000;
+  const int iy = __float_as_int(ty) - 0x4B400000;
+  const float fx = __fsub_rn(cx, __fsub_rn(tx, 12582912.f));
+  const float fy = __fsub_rn(cy, __fsub_rn(ty, 12582912.f));
+  const float4 q = __ldg(&P.quad[iy * P.npix + ix]);
+  const float r0 = __fmaf_rn(fx, __fsub_rn(q.y, q.x), q.x);
+  const float r1 = __fmaf_rn(fx, __fsub_rn(q.w, q.z), q.z);
+  return __fmaf_rn(fy, __fsub_rn(r1, r0), r0);
+}
+
+// Phase 1: per-lane FP32 sums of S_A = sum w (A-1), S_AA = sum w (A-1)^2,
+// S_AF = sum w (F-Fref)(A-1) over the three epoch ranges (each lane-strided
+// from its start), then an xor butterfly; lane 0's value goes to all lanes
+// so that every caller sees the same rounding.
 __device__ __forceinline__ void phase1(const SearchParams &P,
-                                       const float4 *ep, const Consts c,
+                                       const float4 *ep, const TrajC &c,
                                        const int lane, float &oA, float &oAA,
                                        float &oAF) {
   float a = 0.f, b = 0.f, d = 0.f;
-#pragma unroll 4
-  for (int e = lane; e < P.n_ep; e += 32) {
+#pragma unroll 2
+  for (int e = lane; e < c.e_in; e += 32) {
     const float4 v = ep[e];
-    const float px = __fmaf_rn(c.ax, v.x, c.bx);
-    const float py = __fmaf_rn(c.ay, v.x, c.by);
-    const float Ac = __fsub_rn(lookupA(P, px, py), 1.f);
+    const float tau = __fmaf_rn(c.kt, v.x, c.bt);
+    const float Ac = __fsub_rn(pspl_u2(__fmaf_rn(tau, tau, c.u02)), 1.f);
+    const float wAc = __fmul_rn(v.y, Ac);
+    a = __fadd_rn(a, wAc);
+    b = __fmaf_rn(wAc, Ac, b);
+    d = __fmaf_rn(v.z, Ac, d);
+  }
+#pragma unroll 4
+  for (int e = c.e_in + lane; e < c.e_out; e += 32) {
+    const float4 v = ep[e];
+    const float Ac = __fsub_rn(
+        bilinear(P, __fmaf_rn(c.ax, v.x, c.bx), __fmaf_rn(c.ay, v.x, c.by)),
+        1.f);
+    const float wAc = __fmul_rn(v.y, Ac);
+    a = __fadd_rn(a, wAc);
+    b = __fmaf_rn(wAc, Ac, b);
+    d = __fmaf_rn(v.z, Ac, d);
+  }
+#pragma unroll 2
+  for (int e = c.e_out + lane; e < P.n_ep; e += 32) {
+    const float4 v = ep[e];
+    const float tau = __fmaf_rn(c.kt, v.x, c.bt);
+    const float Ac = __fsub_rn(pspl_u2(__fmaf_rn(tau, tau, c.u02)), 1.f);
     const float wAc = __fmul_rn(v.y, Ac);
     a = __fadd_rn(a, wAc);
     b = __fmaf_rn(wAc, Ac, b);
@@ -151,16 +247,32 @@ __device__ __forceinline__ void phase1(const SearchParams &P,
 // w (Fc - Fs Ac - Bc)^2, Bc = Fs + Fb - Fref.  FP32 per lane, FP64 across
 // lanes; lane 0's value is returned to all lanes.
 __device__ __forceinline__ double phase2(const SearchParams &P,
-                                         const float4 *ep, const Consts c,
+                                         const float4 *ep, const TrajC &c,
                                          const int lane, const float Fs,
                                          const float Bc) {
   float chi = 0.f;
-#pragma unroll 4
-  for (int e = lane; e < P.n_ep; e += 32) {
+#pragma unroll 2
+  for (int e = lane; e < c.e_in; e += 32) {
     const float4 v = ep[e];
-    const float px = __fmaf_rn(c.ax, v.x, c.bx);
-    const float py = __fmaf_rn(c.ay, v.x, c.by);
-    const float Ac = __fsub_rn(lookupA(P, px, py), 1.f);
+    const float tau = __fmaf_rn(c.kt, v.x, c.bt);
+    const float Ac = __fsub_rn(pspl_u2(__fmaf_rn(tau, tau, c.u02)), 1.f);
+    const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
+    chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
+  }
+#pragma unroll 4
+  for (int e = c.e_in + lane; e < c.e_out; e += 32) {
+    const float4 v = ep[e];
+    const float Ac = __fsub_rn(
+        bilinear(P, __fmaf_rn(c.ax, v.x, c.bx), __fmaf_rn(c.ay, v.x, c.by)),
+        1.f);
+    const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
+    chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
+  }
+#pragma unroll 2
+  for (int e = c.e_out + lane; e < P.n_ep; e += 32) {
+    const float4 v = ep[e];
+    const float tau = __fmaf_rn(c.kt, v.x, c.bt);
+    const float Ac = __fsub_rn(pspl_u2(__fmaf_rn(tau, tau, c.u02)), 1.f);
     const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
     chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
   }
@@ -211,8 +323,113 @@ __device__ __forceinline__ Solved solve2(const SearchParams &P, double SA,
   return o;
 }
 
+__device__ __forceinline__ double bits_to_chi2(unsigned long long b) {
+  return b == ~0ULL ? CUDART_INF : __longlong_as_double((long long)b);
+}
+
+// Block-wide top-K state in shared memory.
+struct BlockTopK {
+  Entry *buf0, *buf1; // the sorted list and its merge target, alternating
+  Entry *wbuf;        // per-warp staging of sorted candidates (32 each)
+  int *cur, *nk, *lock;
+  volatile double *thr;
+};
+
+// Warp-collective: merge this lane's candidate (if any) into the block's
+// sorted top-K under the block lock.  Candidates are first sorted across
+// the warp (bitonic); each existing entry and each candidate then moves to
+// its rank in the union, and the first K are kept.
+__device__ void warp_merge(const SearchParams &P, BlockTopK &T, const int K,
+                           const int warp, const int lane, bool has,
+                           double chi2, long long idx) {
+  const unsigned m = __ballot_sync(kFull, has);
+  if (!m) return;
+  const int nc = __popc(m);
+  double key = has ? chi2 : CUDART_INF;
+  long long id = has ? idx : 0x7fffffffffffffffLL;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const double ok = __shfl_xor_sync(kFull, key, j);
+      const long long oi = __shfl_xor_sync(kFull, id, j);
+      const bool keep_min = (((lane & k) == 0) == ((lane & j) == 0));
+      const bool other_less = key_less(ok, oi, key, id);
+      if (keep_min == other_less) {
+        key = ok;
+        id = oi;
+      }
+    }
+  }
+  Entry *wb = T.wbuf + warp * 32;
+  if (lane < nc) {
+    wb[lane].chi2 = key;
+    wb[lane].idx = id;
+  }
+  // acquire the block lock (bounded spin)
+  int ok = 1;
+  if (lane == 0) {
+    unsigned it = 0;
+    while (atomicCAS(T.lock, 0, 1) != 0) {
+      if (++it > kLockSpinLimit) {
+        ok = 0;
+        if (P.err) atomicOr(P.err, 1u);
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence_block();
+  }
+  ok = __shfl_sync(kFull, ok, 0);
+  __syncwarp();
+  if (!ok) return;
+  const int c0 = *T.cur;
+  const int nk = *T.nk;
+  const Entry *cur = c0 ? T.buf1 : T.buf0;
+  Entry *nxt = c0 ? T.buf0 : T.buf1;
+  for (int i = lane; i < nk; i += 32) {
+    const Entry e = cur[i];
+    int lo = 0, hi = nc;  // candidates below e
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (key_less(wb[mid], e))
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    const int r = i + lo;
+    if (r < K) nxt[r] = e;
+  }
+  if (lane < nc) {
+    const Entry e = wb[lane];
+    int lo = 0, hi = nk;  // kept entries below e
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (key_less(cur[mid], e))
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    const int r = lane + lo;
+    if (r < K) nxt[r] = e;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    const int nn = min(K, nk + nc);
+    *T.nk = nn;
+    *T.cur = c0 ^ 1;
+    const double th = (nn == K) ? nxt[K - 1].chi2 : CUDART_INF;
+    *T.thr = th;
+    if (P.gthr && nn == K)
+      atomicMin(P.gthr, (unsigned long long)__double_as_longlong(th));
+    __threadfence_block();
+    atomicExch(T.lock, 0);
+  }
+  __syncwarp();
+}
+
 template <bool DENSE, bool EP_SMEM>
-__global__ void __launch_bounds__(kSearchWarps * 32, 2)
+__global__ void __launch_bounds__(kSearchWarps * 32, 1)
     k_search(const SearchParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
@@ -220,7 +437,9 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 2)
   const int K = P.top_k;
 
   const float4 *ep = P.ep;
-  Entry *bufA = nullptr, *bufB = nullptr, *cand = nullptr;
+  BlockTopK T;
+  __shared__ int s_cur, s_nk, s_lock;
+  __shared__ double s_thr;
   {
     unsigned char *p = smem;
     if (EP_SMEM) {
@@ -230,125 +449,85 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 2)
       p += sizeof(float4) * (size_t)P.n_ep;
     }
     if (!DENSE) {
-      bufA = reinterpret_cast<Entry *>(p);
-      bufB = bufA + K;
-      cand = bufB + K;
+      T.buf0 = reinterpret_cast<Entry *>(p);
+      T.buf1 = T.buf0 + K;
+      T.wbuf = T.buf1 + K;
     }
+    T.cur = &s_cur;
+    T.nk = &s_nk;
+    T.lock = &s_lock;
+    T.thr = &s_thr;
   }
-  __shared__ int s_ncand, s_nkeep, s_cur;
-  __shared__ double s_thr;
   if (threadIdx.x == 0) {
-    s_ncand = 0;
-    s_nkeep = 0;
     s_cur = 0;
+    s_nk = 0;
+    s_lock = 0;
     s_thr = CUDART_INF;
   }
   __syncthreads();
 
   const long long n_groups = (P.count + 31) / 32;
-  const long long per_round = (long long)gridDim.x * kSearchWarps;
-  const long long rounds = (n_groups + per_round - 1) / per_round;
+  const long long stride = (long long)gridDim.x * kSearchWarps;
+  unsigned long long n_exact = 0;
 
-  for (long long rd = 0; rd < rounds; ++rd) {
-    const long long g = (rd * gridDim.x + blockIdx.x) * kSearchWarps + warp;
-    if (g < n_groups) {
-      const long long base = g * 32;
-      const int nvalid = (int)min(32LL, P.count - base);
-      const long long my = P.first + base + lane;
-      Consts mine = traj_consts(P, lane < nvalid ? my : P.first + base);
-      float mA = 0.f, mAA = 0.f, mAF = 0.f;
-      for (int k = 0; k < nvalid; ++k) {
-        Consts c;
-        c.ax = __shfl_sync(kFull, mine.ax, k);
-        c.bx = __shfl_sync(kFull, mine.bx, k);
-        c.ay = __shfl_sync(kFull, mine.ay, k);
-        c.by = __shfl_sync(kFull, mine.by, k);
-        float sA, sAA, sAF;
-        phase1(P, ep, c, lane, sA, sAA, sAF);
-        if (lane == k) {
-          mA = sA;
-          mAA = sAA;
-          mAF = sAF;
-        }
-      }
-      const Solved sol = solve2(P, (double)mA, (double)mAA, (double)mAF);
-      const double thr = DENSE ? CUDART_INF : s_thr;
-      bool cand_me = lane < nvalid;
-      if (!DENSE && cand_me && !sol.always && thr < CUDART_INF)
-        cand_me = (sol.chi2_cf - 4.0 * sol.bound) * (1.0 - 1e-4) <= thr;
-      unsigned todo = __ballot_sync(kFull, cand_me);
-      const float myFs = __double2float_rn(sol.Fs);
-      const float myBc = __double2float_rn(sol.Bc);
-      while (todo) {
-        const int k = __ffs(todo) - 1;
-        todo &= todo - 1;
-        Consts c;
-        c.ax = __shfl_sync(kFull, mine.ax, k);
-        c.bx = __shfl_sync(kFull, mine.bx, k);
-        c.ay = __shfl_sync(kFull, mine.ay, k);
-        c.by = __shfl_sync(kFull, mine.by, k);
-        const float Fs = __shfl_sync(kFull, myFs, k);
-        const float Bc = __shfl_sync(kFull, myBc, k);
-        const double chi2 = phase2(P, ep, c, lane, Fs, Bc);
-        if (lane == k) {
-          const double x = isnan(chi2) ? CUDART_INF : chi2;
-          if (DENSE) {
-            const long long o = base + k;
-            P.dchi2[o] = x;
-            if (P.dFs) P.dFs[o] = sol.Fs;
-            if (P.dFb) P.dFb[o] = sol.Bc + P.Fref - sol.Fs;
-          } else if (x <= thr) {
-            const int pos = atomicAdd(&s_ncand, 1);
-            cand[pos].chi2 = x;
-            cand[pos].idx = P.first + base + k;
-          }
-        }
+  for (long long g = (long long)blockIdx.x * kSearchWarps + warp;
+       g < n_groups; g += stride) {
+    const long long base = g * 32;
+    const int nvalid = (int)min(32LL, P.count - base);
+    const long long my = P.first + base + (lane < nvalid ? lane : 0);
+    const TrajC mine = traj_consts(P, ep, my);
+    float mA = 0.f, mAA = 0.f, mAF = 0.f;
+    for (int k = 0; k < nvalid; ++k) {
+      const TrajC c = shfl_traj(mine, k);
+      float sA, sAA, sAF;
+      phase1(P, ep, c, lane, sA, sAA, sAF);
+      if (lane == k) {
+        mA = sA;
+        mAA = sAA;
+        mAF = sAF;
       }
     }
+    const Solved sol = solve2(P, (double)mA, (double)mAA, (double)mAF);
+    double thr = CUDART_INF;
     if (!DENSE) {
-      __syncthreads();
-      const int nc = s_ncand;
-      if (nc > 0) {
-        const int nk = s_nkeep;
-        Entry *cur = s_cur ? bufB : bufA;
-        Entry *nxt = s_cur ? bufA : bufB;
-        // rank-based merge of the sorted list cur[0..nk) with the unsorted
-        // candidates cand[0..nc); keys (chi2, idx) are unique
-        for (int i = threadIdx.x; i < nk; i += blockDim.x) {
-          const Entry e = cur[i];
-          int r = i;
-          for (int j = 0; j < nc; ++j) r += key_less(cand[j], e);
-          if (r < K) nxt[r] = e;
-        }
-        for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-          const Entry e = cand[i];
-          int lo = 0, hi = nk;  // number of cur entries below e
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (key_less(cur[mid], e))
-              lo = mid + 1;
-            else
-              hi = mid;
-          }
-          int r = lo;
-          for (int j = 0; j < nc; ++j) r += key_less(cand[j], e);
-          if (r < K) nxt[r] = e;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          const int nn = min(K, nk + nc);
-          s_nkeep = nn;
-          s_cur ^= 1;
-          s_thr = (nn == K) ? nxt[K - 1].chi2 : CUDART_INF;
-          s_ncand = 0;
-        }
+      thr = *T.thr;
+      if (P.gthr) thr = fmin(thr, bits_to_chi2(__ldcg(P.gthr)));
+    }
+    bool cand_me = lane < nvalid;
+    if (!DENSE && cand_me && !sol.always && thr < CUDART_INF)
+      cand_me = (sol.chi2_cf - 4.0 * sol.bound) * (1.0 - 1e-4) <= thr;
+    unsigned todo = __ballot_sync(kFull, cand_me);
+    n_exact += __popc(todo);
+    const float myFs = __double2float_rn(sol.Fs);
+    const float myBc = __double2float_rn(sol.Bc);
+    double my_chi2 = CUDART_INF;
+    while (todo) {
+      const int k = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const TrajC c = shfl_traj(mine, k);
+      const float Fs = __shfl_sync(kFull, myFs, k);
+      const float Bc = __shfl_sync(kFull, myBc, k);
+      const double chi2 = phase2(P, ep, c, lane, Fs, Bc);
+      if (lane == k) my_chi2 = isnan(chi2) ? CUDART_INF : chi2;
+    }
+    if (DENSE) {
+      if (lane < nvalid) {
+        const long long o = base + lane;
+        P.dchi2[o] = my_chi2;
+        if (P.dFs) P.dFs[o] = sol.Fs;
+        if (P.dFb) P.dFb[o] = sol.Bc + P.Fref - sol.Fs;
       }
-      __syncthreads();
+    } else {
+      const bool keep = lane < nvalid && my_chi2 <= thr && my_chi2 < CUDART_INF;
+      warp_merge(P, T, K, warp, lane, keep, my_chi2, P.first + base + lane);
     }
   }
+  if (P.stat_exact && lane == 0 && n_exact)
+    atomicAdd(P.stat_exact, n_exact);
   if (!DENSE) {
-    const int nk = s_nkeep;
-    const Entry *cur = s_cur ? bufB : bufA;
+    __syncthreads();
+    const int nk = s_nk;
+    const Entry *cur = s_cur ? T.buf1 : T.buf0;
     Entry *out = P.partial + (size_t)blockIdx.x * K;
     for (int i = threadIdx.x; i < K; i += blockDim.x) {
       Entry e;
@@ -365,8 +544,8 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 2)
 
 // One level of the merge tree: list pairs (2p, 2p+1) -> list p, keeping the
 // first k of each merged pair.  An odd last list is copied.
-__global__ void k_merge_level(const Entry *__restrict__ in, Entry *__restrict__ out,
-                              int lists, int k) {
+__global__ void k_merge_level(const Entry *__restrict__ in,
+                              Entry *__restrict__ out, int lists, int k) {
   const int pairs = (lists + 1) / 2;
   const long long total = (long long)pairs * 2 * k;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -417,7 +596,7 @@ __global__ void k_fill(const FillParams F) {
     }
     return;
   }
-  const Consts c = traj_consts(P, e.idx);
+  const TrajC c = traj_consts(P, P.ep, e.idx);
   float sA, sAA, sAF;
   phase1(P, P.ep, c, lane, sA, sAA, sAF);
   const Solved sol = solve2(P, (double)sA, (double)sAA, (double)sAF);
@@ -445,14 +624,24 @@ __global__ void k_fill(const FillParams F) {
   }
 }
 
-__global__ void k_lightcurve(const SearchParams P, Consts c,
+// A(t) along one trajectory given by (ax, bx, ay, by) with v = a t + b, and
+// tau = kt t + bt, u0^2 for the single-lens part outside the map.
+__global__ void k_lightcurve(const SearchParams P, float ax, float bx,
+                             float ay, float by, float kt, float bt, float u02,
                              const float *__restrict__ t, int n,
                              float *__restrict__ A) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += gridDim.x * blockDim.x) {
-    const float px = __fmaf_rn(c.ax, t[i], c.bx);
-    const float py = __fmaf_rn(c.ay, t[i], c.by);
-    A[i] = lookupA(P, px, py);
+    const float vx = __fmaf_rn(ax, t[i], bx);
+    const float vy = __fmaf_rn(ay, t[i], by);
+    const bool inside =
+        (vx > P.vlo) & (vx < P.vhi) & (vy > P.vlo) & (vy < P.vhi);
+    if (inside) {
+      A[i] = bilinear(P, vx, vy);
+    } else {
+      const float tau = __fmaf_rn(kt, t[i], bt);
+      A[i] = pspl_u2(__fmaf_rn(tau, tau, u02));
+    }
   }
 }
 
@@ -464,33 +653,23 @@ size_t search_smem_bytes(int n_ep_smem, int top_k) {
 }
 
 template <bool D, bool E>
-static void set_smem_attr(size_t smem) {
+static int occupancy(size_t smem) {
   cudaFuncSetAttribute(k_search<D, E>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &b, k_search<D, E>, kSearchWarps * 32, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return b;
 }
 
 int search_blocks_per_sm(bool dense, bool ep_smem, size_t smem) {
-  int b = 0;
-  cudaError_t e;
-  if (dense && ep_smem) {
-    set_smem_attr<true, true>(smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &b, k_search<true, true>, kSearchWarps * 32, smem);
-  } else if (dense) {
-    set_smem_attr<true, false>(smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &b, k_search<true, false>, kSearchWarps * 32, smem);
-  } else if (ep_smem) {
-    set_smem_attr<false, true>(smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &b, k_search<false, true>, kSearchWarps * 32, smem);
-  } else {
-    set_smem_attr<false, false>(smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &b, k_search<false, false>, kSearchWarps * 32, smem);
-  }
-  if (e != cudaSuccess) return 0;
-  return b;
+  if (dense && ep_smem) return occupancy<true, true>(smem);
+  if (dense) return occupancy<true, false>(smem);
+  if (ep_smem) return occupancy<false, true>(smem);
+  return occupancy<false, false>(smem);
 }
 
 cudaError_t launch_search(const SearchParams &P, bool dense, bool ep_smem,
@@ -537,17 +716,14 @@ cudaError_t launch_fill(const FillParams &F, cudaStream_t st) {
 }
 
 cudaError_t launch_lightcurve(const SearchParams &P, float ax, float bx,
-                              float ay, float by, const float *t, int n,
-                              float *A, cudaStream_t st) {
-  Consts c;
-  c.ax = ax;
-  c.bx = bx;
-  c.ay = ay;
-  c.by = by;
+                              float ay, float by, float kt, float bt,
+                              float u02, const float *t, int n, float *A,
+                              cudaStream_t st) {
   int blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  k_lightcurve<<<blocks, 256, 0, st>>>(P, c, t, n, A);
+  k_lightcurve<<<blocks, 256, 0, st>>>(P, ax, bx, ay, by, kt, bt, u02, t, n,
+                                       A);
   return cudaGetLastError();
 }
 

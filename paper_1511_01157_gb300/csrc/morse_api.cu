@@ -329,6 +329,9 @@ void map_params(const morse_map *map, morse::SearchParams *P) {
   P->vlo = -(float)(map->npix / 2) - 0.5f;
   P->vhi = (float)(map->npix - map->npix / 2) - 0.5f;
   P->vmin = -(float)(map->npix / 2);
+  P->vmax = (float)(map->npix - map->npix / 2 - 1);
+  P->L = map->L;
+  P->dlt = dlt;
   P->coff = 0.5 * map->npix - (double)(map->npix / 2) - 0.5;
   P->voff = (float)(-P->coff);
   P->dltf = (float)dlt;
@@ -374,8 +377,47 @@ struct Plan {
   bool dense, ep_smem;
   size_t smem;
   int grid;
-  size_t off_tab, off_pa, off_pb, off_out, bytes;
+  size_t off_tab, off_hdr, off_pa, off_pb, off_out, bytes;
 };
+
+// Device words of one search call (in the workspace header): the grid-wide
+// pruning threshold, the error word and the exact-sweep counter.
+struct Hdr {
+  unsigned long long gthr;
+  unsigned long long stat_exact;
+  unsigned int err;
+};
+
+morse_status hdr_init(morse_ctx *ctx, char *base, const Plan &pl,
+                      morse::SearchParams *P) {
+  Hdr *h = (Hdr *)(base + pl.off_hdr);
+  MORSE_CUDA(ctx, cudaMemsetAsync(h, 0, sizeof(Hdr), ctx->stream));
+  MORSE_CUDA(ctx, cudaMemsetAsync(&h->gthr, 0xFF, sizeof(h->gthr),
+                                  ctx->stream));
+  P->gthr = &h->gthr;
+  P->err = &h->err;
+  P->stat_exact = &h->stat_exact;
+  return MORSE_OK;
+}
+
+// Reset the pruning threshold between the maps of a sweep (it is per map).
+morse_status hdr_reset_threshold(morse_ctx *ctx, char *base, const Plan &pl) {
+  Hdr *h = (Hdr *)(base + pl.off_hdr);
+  MORSE_CUDA(ctx, cudaMemsetAsync(&h->gthr, 0xFF, sizeof(h->gthr),
+                                  ctx->stream));
+  return MORSE_OK;
+}
+
+// After the stream has synchronised: read the header, report a lock that
+// gave up as MORSE_ETIMEOUT.
+morse_status hdr_check(morse_ctx *ctx, const Hdr &h) {
+  ctx->last_exact = h.stat_exact;
+  if (h.err)
+    return fail(ctx, MORSE_ETIMEOUT,
+                "a search block could not take its top-K lock (error 0x%x); "
+                "results are incomplete", h.err);
+  return MORSE_OK;
+}
 
 morse_status plan_search(morse_ctx *ctx, const morse_event *ev,
                          const morse_grid *g, long long count, bool dense,
@@ -402,7 +444,8 @@ morse_status plan_search(morse_ctx *ctx, const morse_event *ev,
   pl->smem = smem;
   pl->grid = grid;
   pl->off_tab = 0;
-  pl->off_pa = align_up(tables_bytes(g), 256);
+  pl->off_hdr = align_up(tables_bytes(g), 256);
+  pl->off_pa = pl->off_hdr + 256;
   size_t list_bytes = dense ? 0 : sizeof(Entry) * (size_t)grid * K;
   pl->off_pb = align_up(pl->off_pa + list_bytes, 256);
   pl->off_out = align_up(pl->off_pb + list_bytes, 256);
@@ -487,14 +530,20 @@ morse_status sweep_impl(morse_ctx *ctx, const morse_event *ev,
   P.first = 0;
   P.count = grid_size(grid);
   morse_fit *fits = (morse_fit *)(base + pl.off_out);
+  MORSE_TRY(hdr_init(ctx, base, pl, &P));
   for (int i = 0; i < n_maps; ++i) {
     MORSE_TRY(enqueue_build(ctx, m, specs[(size_t)i]));
+    if (i > 0) MORSE_TRY(hdr_reset_threshold(ctx, base, pl));
     MORSE_TRY(enqueue_topk(ctx, pl, P, base, T, fits + (size_t)i * pl.K));
   }
+  Hdr h;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(&h, base + pl.off_hdr, sizeof(Hdr),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
   MORSE_CUDA(ctx, cudaMemcpyAsync(out, fits,
                                   sizeof(morse_fit) * (size_t)pl.K * n_maps,
                                   cudaMemcpyDeviceToHost, ctx->stream));
-  return sync_and_collect(ctx, "sweep");
+  MORSE_TRY(sync_and_collect(ctx, "sweep"));
+  return hdr_check(ctx, h);
 }
 
 }  // namespace
@@ -572,6 +621,13 @@ morse_status morse_last_kernel_ms(const morse_ctx *ctx, int which,
                                   double *ms) {
   if (!ctx || !ms || which < 0 || which >= KT_COUNT) return MORSE_EINVAL;
   *ms = ctx->kernel_ms[which];
+  return MORSE_OK;
+}
+
+morse_status morse_last_search_stats(const morse_ctx *ctx,
+                                     uint64_t *exact_sweeps) {
+  if (!ctx || !exact_sweeps) return MORSE_EINVAL;
+  *exact_sweeps = ctx->last_exact;
   return MORSE_OK;
 }
 
@@ -708,6 +764,12 @@ morse_status morse_event_create(morse_ctx *ctx, const double *t,
       return fail(ctx, MORSE_EINVAL, "epoch %lld has sigma <= 0",
                   (long long)i);
   }
+  // the search needs the epochs in time order (a straight track crosses the
+  // map in one time interval): store them sorted, ties in input order
+  std::vector<int64_t> order((size_t)n);
+  for (int64_t i = 0; i < n; ++i) order[(size_t)i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [t](int64_t a, int64_t b) { return t[a] < t[b]; });
   // weights, weighted mean flux, FP32 storage; the FP64 constants are sums
   // of the stored FP32 values so that the device data is self-consistent
   std::vector<float4> h((size_t)n);
@@ -719,7 +781,8 @@ morse_status morse_event_create(morse_ctx *ctx, const double *t,
   }
   const double Fref = swf / sw;
   double S1 = 0.0, SF = 0.0, SFF = 0.0;
-  for (int64_t i = 0; i < n; ++i) {
+  for (int64_t k = 0; k < n; ++k) {
+    const int64_t i = order[(size_t)k];
     double w = 1.0 / (sigma[i] * sigma[i]);
     double fc = flux[i] - Fref;
     float4 v;
@@ -731,7 +794,7 @@ morse_status morse_event_create(morse_ctx *ctx, const double *t,
       return fail(ctx, MORSE_EINVAL,
                   "epoch %lld: weight 1/sigma^2 outside FP32 range",
                   (long long)i);
-    h[(size_t)i] = v;
+    h[(size_t)k] = v;
     S1 += (double)v.y;
     SF += (double)v.z;
     SFF += (double)v.z * (double)v.w;
@@ -804,10 +867,15 @@ morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
   P.first = 0;
   P.count = grid_size(grid);
   morse_fit *fits = (morse_fit *)(base + pl.off_out);
+  MORSE_TRY(hdr_init(ctx, base, pl, &P));
   MORSE_TRY(enqueue_topk(ctx, pl, P, base, T, fits));
+  Hdr h;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(&h, base + pl.off_hdr, sizeof(Hdr),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
   MORSE_CUDA(ctx, cudaMemcpyAsync(out, fits, sizeof(morse_fit) * pl.K,
                                   cudaMemcpyDeviceToHost, ctx->stream));
-  return sync_and_collect(ctx, "grid search");
+  MORSE_TRY(sync_and_collect(ctx, "grid search"));
+  return hdr_check(ctx, h);
 }
 
 morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
@@ -844,6 +912,7 @@ morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
   P.dchi2 = (double *)(base + pl.off_out);
   P.dFs = P.dchi2 + count;
   P.dFb = P.dFs + count;
+  MORSE_TRY(hdr_init(ctx, base, pl, &P));
   int r = t_begin(ctx, KT_SEARCH);
   MORSE_CUDA(ctx, morse::launch_search(P, true, pl.ep_smem, pl.grid, pl.smem,
                                        ctx->stream));
@@ -857,7 +926,11 @@ morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
   if (Fb)
     MORSE_CUDA(ctx, cudaMemcpyAsync(Fb, P.dFb, sizeof(double) * count,
                                     cudaMemcpyDeviceToHost, ctx->stream));
-  return sync_and_collect(ctx, "dense search");
+  Hdr h;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(&h, base + pl.off_hdr, sizeof(Hdr),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_TRY(sync_and_collect(ctx, "dense search"));
+  return hdr_check(ctx, h);
 }
 
 morse_status morse_sweep(morse_ctx *ctx, const morse_event *ev,
@@ -929,11 +1002,12 @@ morse_status morse_lightcurve(morse_ctx *ctx, const morse_map *map,
   const float ax = (float)(c * k), ay = (float)(s * k);
   const float bx = (float)((-u0 * s) / dlt + P.coff);
   const float by = (float)((u0 * c) / dlt + P.coff);
+  const float kt = (float)(1.0 / tE), u02 = (float)(u0 * u0);
   std::vector<float> hA((size_t)n);
   MORSE_CUDA(ctx, cudaMemcpyAsync(dt, tf.data(), sizeof(float) * n,
                                   cudaMemcpyHostToDevice, ctx->stream));
-  MORSE_CUDA(ctx, morse::launch_lightcurve(P, ax, bx, ay, by, dt, (int)n, dA,
-                                           ctx->stream));
+  MORSE_CUDA(ctx, morse::launch_lightcurve(P, ax, bx, ay, by, kt, 0.0f, u02,
+                                           dt, (int)n, dA, ctx->stream));
   ctx->launches += 1;
   MORSE_CUDA(ctx, cudaMemcpyAsync(hA.data(), dA, sizeof(float) * n,
                                   cudaMemcpyDeviceToHost, ctx->stream));

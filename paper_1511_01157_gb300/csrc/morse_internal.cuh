@@ -29,6 +29,7 @@ struct morse_ctx {
   double kernel_ms[KT_COUNT];
   uint64_t launches;        // kernels launched by this context
   morse_map *sweep_map;     // map storage reused by sweeps
+  unsigned long long last_exact;  // exact sweeps in the last search call
 };
 
 struct morse_map {
@@ -94,10 +95,12 @@ struct SearchParams {
   int npix, half;           // npix, npix/2
   float vlo, vhi;           // inside iff vlo < v < vhi (centred coords)
   float vmin;               // -npix/2: clamp to the first texel centre
+  float vmax;               // npix - npix/2 - 1: centre of the last texel
   float voff;               // -coff: y = (v + voff) Delta
   float dltf;               // Delta
   double invD;              // 1/Delta
   double coff;              // v = y/Delta + coff
+  double L, dlt;            // map half-width, Delta (FP64)
   // event
   const float4 *ep;
   int n_ep;
@@ -111,6 +114,11 @@ struct SearchParams {
   // outputs
   Entry *partial;           // [gridDim.x][top_k] (top-K mode)
   double *dchi2, *dFs, *dFb;  // [count] (dense mode)
+  // optional device words (nullptr: unused)
+  unsigned long long *gthr; // grid-wide pruning threshold (chi^2 bits),
+                            // all-ones = +inf
+  unsigned int *err;        // bit 0: a block lock spin gave up
+  unsigned long long *stat_exact;  // trajectories given the exact sweep
 };
 
 struct FillParams {
@@ -121,7 +129,7 @@ struct FillParams {
   morse_fit *out;           // [k]
 };
 
-constexpr int kSearchWarps = 16;
+constexpr int kSearchWarps = 32;
 
 size_t search_smem_bytes(int n_ep_smem, int top_k);
 int search_blocks_per_sm(bool dense, bool ep_smem, size_t smem);
@@ -133,7 +141,8 @@ cudaError_t launch_topk_merge(Entry *a, Entry *b, int lists, int k,
                               Entry **result, int *levels, cudaStream_t st);
 cudaError_t launch_fill(const FillParams &F, cudaStream_t st);
 cudaError_t launch_lightcurve(const SearchParams &P, float ax, float bx,
-                              float ay, float by, const float *t, int n,
-                              float *A, cudaStream_t st);
+                              float ay, float by, float kt, float bt,
+                              float u02, const float *t, int n, float *A,
+                              cudaStream_t st);
 
 }  // namespace morse

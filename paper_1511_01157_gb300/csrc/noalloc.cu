@@ -8,13 +8,14 @@
 // pre-reserved memory budget where a workspace that grows on demand is not
 // acceptable.  They create their context, event and map handles at set-up
 // (where allocation is fine) and then search with this entry point, which
-// keeps its scratch -- the grid tables, the two per-block top-K lists of
-// the merge tree and the fit records -- in one file-scope device array of
-// fixed size instead of the context's growable workspace.
+// keeps its scratch -- the grid tables, two status words, the two
+// per-block top-K lists of the merge tree and the fit records -- in one
+// file-scope device array of fixed size instead of the context's growable
+// workspace.
 //
 // The array is shared by every call in the process on a given device and
-// keeps whatever the last call wrote; each call overwrites every byte it
-// reads before reading it, so nothing has to start at zero.  Two calls that
+// keeps whatever the last call wrote; each call clears its status words
+// and overwrites every other byte it reads before reading it.  Two calls that
 // overlap on the same GPU (different streams or host threads) race on it.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -110,11 +111,12 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   int grid = (int)std::min<long long>((long long)bps * ctx->sm_count, want);
   if (grid < 1) grid = 1;
 
-  // scratch layout: tables | list A | list B | fits
+  // scratch layout: tables | status words | list A | list B | fits
   const size_t tab_n =
       (size_t)g->n_u0 + 2 * (size_t)g->n_alpha + 2 * (size_t)g->n_t0 +
       2 * (size_t)g->n_tE;
-  const size_t off_a = up256(tab_n * sizeof(double));
+  const size_t off_w = up256(tab_n * sizeof(double));
+  const size_t off_a = off_w + 256;
   const size_t list = sizeof(morse::Entry) * (size_t)grid * K;
   const size_t off_b = up256(off_a + list);
   const size_t off_fit = up256(off_b + list);
@@ -182,6 +184,9 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   P.vlo = -(float)(map->npix / 2) - 0.5f;
   P.vhi = (float)(map->npix - map->npix / 2) - 0.5f;
   P.vmin = -(float)(map->npix / 2);
+  P.vmax = (float)(map->npix - map->npix / 2 - 1);
+  P.L = map->L;
+  P.dlt = dlt;
   P.coff = 0.5 * map->npix - (double)(map->npix / 2) - 0.5;
   P.voff = (float)(-P.coff);
   P.dltf = (float)dlt;
@@ -206,8 +211,18 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   P.first = 0;
   P.count = count;
   P.partial = (morse::Entry *)(base + off_a);
-
-  e = morse::launch_search(P, false, ep_smem, grid, smem, ctx->stream);
+  // status words: the grid-wide pruning threshold (all-ones = +inf) and the
+  // error word of the block locks
+  unsigned long long *words = (unsigned long long *)(base + off_w);
+  P.gthr = &words[0];
+  P.err = (unsigned int *)&words[1];
+  e = cudaMemsetAsync(&words[0], 0xFF, sizeof(unsigned long long),
+                      ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(&words[1], 0, sizeof(unsigned long long),
+                        ctx->stream);
+  if (e == cudaSuccess)
+    e = morse::launch_search(P, false, ep_smem, grid, smem, ctx->stream);
   morse::Entry *sel = nullptr;
   int levels = 0;
   if (e == cudaSuccess)
@@ -230,11 +245,19 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
     e = cudaMemcpyAsync(out, fits, sizeof(morse_fit) * K,
                         cudaMemcpyDeviceToHost, ctx->stream);
   }
+  unsigned int errword = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&errword, &words[1], sizeof(errword),
+                        cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     snprintf(ctx->err, sizeof(ctx->err), "no-alloc search: %s",
              cudaGetErrorString(e));
     return MORSE_ECUDA;
   }
+  if (errword)
+    return set_err(ctx, MORSE_ETIMEOUT,
+                   "a search block could not take its top-K lock; results "
+                   "are incomplete");
   return MORSE_OK;
 }

@@ -377,3 +377,32 @@ def test_sweep_equals_per_map_searches(ctx, m):
                              image_halfwidth=3.0, deflect="fp32")
     assert np.array_equal(fits2["chi2"], fits["chi2"])
     assert ctx.kernel_ms(2) > 0.0
+
+
+def test_epoch_order_does_not_matter(ctx, m, cfg0_maps):
+    """Events are stored time-sorted; a shuffled copy searches the same."""
+    mp, A_o, *_ = cfg0_maps
+    c = synth.CFG0
+    t, F, sig = _event(c, n=400, seed=8)
+    perm = np.random.default_rng(1).permutation(len(t))
+    g = _grid(m, c["grid"], 12)
+    a = ctx.grid_chi2(ctx.event(t, F, sig), mp, g)
+    b = ctx.grid_chi2(ctx.event(t[perm], F[perm], sig[perm]), mp, g)
+    assert np.array_equal(a["idx"], b["idx"])
+    np.testing.assert_allclose(a["chi2"], b["chi2"], rtol=1e-12)
+
+
+def test_pruning_is_exact_and_effective(ctx, m, cfg0_maps, cfg0_event):
+    """The bounded closed form discards most trajectories, and the top-K
+    with pruning equals the dense (unpruned) ranking."""
+    mp, A_o, *_ = cfg0_maps
+    t, F, sig, ev = cfg0_event
+    c = synth.CFG0
+    g = _grid(m, c["grid"], 32)
+    got = ctx.grid_chi2(ev, mp, g)
+    n_exact = ctx.exact_sweeps()
+    chi2, _, _ = ctx.grid_chi2_dense(ev, mp, g)
+    order = np.lexsort((np.arange(len(chi2)), chi2))[:32]
+    assert np.array_equal(got["idx"], order)
+    assert np.array_equal(got["chi2"], chi2[order])
+    assert n_exact < 0.5 * g.size
