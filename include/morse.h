@@ -205,7 +205,7 @@ morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
  * calls that overlap on the same GPU (other streams, other host threads)
  * race on it; each call rewrites every byte it reads, so nothing carries
  * over.  Returns MORSE_EINVAL, with a message naming the sizes, when the
- * search needs more than 4 MiB of scratch (roughly top_k above ~500 on a
+ * search needs more than 4 MiB of scratch (top_k above about 850 on a
  * 152-SM GPU) or more than 4096 grid-table values (n_u0 + 2 n_alpha +
  * 2 n_t0 + 2 n_tE).  Errors otherwise as morse_grid_chi2. */
 morse_status morse_grid_chi2_noalloc(morse_ctx *ctx, const morse_event *ev,

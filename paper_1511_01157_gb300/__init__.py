@@ -20,7 +20,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmorse.so")
+# MORSE_LIB=checked selects the bounds-checked build (tests)
+LIB_PATH = os.path.join(
+    _HERE, "libmorse_checked.so" if os.environ.get("MORSE_LIB") == "checked"
+    else "libmorse.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(

@@ -17,6 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libmorse.so")
+OUT_CHECKED = os.path.join(HERE, "libmorse_checked.so")
 BUILD = os.path.join(HERE, "_build", platform.machine())  # per host arch
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -40,8 +41,8 @@ def _stale(out, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def _build_one(out, objdir, force, verbose, extra):
+    os.makedirs(objdir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC)
                if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(INCLUDE, "morse.h"))
@@ -51,28 +52,42 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         flags += ["-Xptxas", "-v"]
     objs, jobs = [], []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
             jobs.append([nvcc(), "-c", src, "-o", obj] + flags)
+    return objs, jobs, out
 
-    def run(cmd):
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" +
-                               r.stdout + r.stderr)
-        return r.stdout + r.stderr
 
+def _run(cmd):
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" +
+                           r.stdout + r.stderr)
+    return r.stdout + r.stderr
+
+
+def build(force: bool = False, verbose: bool = False, extra=(),
+          checked: bool = True) -> str:
+    """Build libmorse.so and, unless checked=False, libmorse_checked.so
+    (every texel index checked in device code; for tests)."""
+    variants = [_build_one(OUT, BUILD, force, verbose, extra)]
+    if checked:
+        variants.append(_build_one(OUT_CHECKED, BUILD + "_checked", force,
+                                   False, list(extra) +
+                                   ["-DMORSE_CHECK_BOUNDS"]))
+    jobs = [j for v in variants for j in v[1]]
     with cf.ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
-        logs = list(ex.map(run, jobs))
+        logs = list(ex.map(_run, jobs))
     if verbose:
         for line in logs:
             sys.stdout.write(line)
-    if force or jobs or _stale(OUT, objs):
-        tmp = OUT + ".tmp"
-        run([nvcc(), "-shared"] + ARCH + objs +
-            ["-o", tmp, "-cudart", "static"])
-        os.replace(tmp, OUT)
+    for objs, vjobs, out in variants:
+        if force or vjobs or _stale(out, objs):
+            tmp = out + ".tmp"
+            _run([nvcc(), "-shared"] + ARCH + objs +
+                 ["-o", tmp, "-cudart", "static"])
+            os.replace(tmp, out)
     return OUT
 
 

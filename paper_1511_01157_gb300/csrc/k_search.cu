@@ -182,10 +182,18 @@ __device__ __forceinline__ float bilinear(const SearchParams &P, float vx,
   // floor: adding 1.5 * 2^23 rounding down leaves floor(c) in the low
   // mantissa bits; the fraction c - floor(c) is exact
   const float tx = __fadd_rd(cx, 12582912.f), ty = __fadd_rd(cy, 12582912.f);
-  const int ix = __float_as_int(tx) - 0x4B400000;
-  const int iy = __float_as_int(ty) - 0x4B400000;
+  // floor(c) is in [-half, npix - half - 1]; + half gives [0, npix - 1]
+  const int ix = __float_as_int(tx) - 0x4B400000 + P.half;
+  const int iy = __float_as_int(ty) - 0x4B400000 + P.half;
   const float fx = __fsub_rn(cx, __fsub_rn(tx, 12582912.f));
   const float fy = __fsub_rn(cy, __fsub_rn(ty, 12582912.f));
+#ifdef MORSE_CHECK_BOUNDS
+  // checked build: record an out-of-range texel and skip the access
+  if ((unsigned)ix >= (unsigned)P.npix || (unsigned)iy >= (unsigned)P.npix) {
+    if (P.err) atomicOr(P.err, 2u);
+    return 0.f;
+  }
+#endif
   const float4 q = __ldg(&P.quad[iy * P.npix + ix]);
   const float r0 = __fmaf_rn(fx, __fsub_rn(q.y, q.x), q.x);
   const float r1 = __fmaf_rn(fx, __fsub_rn(q.w, q.z), q.z);

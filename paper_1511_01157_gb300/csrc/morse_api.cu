@@ -412,7 +412,11 @@ morse_status hdr_reset_threshold(morse_ctx *ctx, char *base, const Plan &pl) {
 // gave up as MORSE_ETIMEOUT.
 morse_status hdr_check(morse_ctx *ctx, const Hdr &h) {
   ctx->last_exact = h.stat_exact;
-  if (h.err)
+  if (h.err & 2u)
+    return fail(ctx, MORSE_ECUDA,
+                "bounds check: a texel index fell outside the map (error "
+                "0x%x); results are invalid", h.err);
+  if (h.err & 1u)
     return fail(ctx, MORSE_ETIMEOUT,
                 "a search block could not take its top-K lock (error 0x%x); "
                 "results are incomplete", h.err);
@@ -563,7 +567,13 @@ const char *morse_status_string(morse_status st) {
   return "MORSE_UNKNOWN";
 }
 
+#ifdef MORSE_CHECK_BOUNDS
+const char *morse_version(void) {
+  return "morse-gb300 0.1 sm_103a bounds-checked";
+}
+#else
 const char *morse_version(void) { return "morse-gb300 0.1 sm_103a"; }
+#endif
 
 morse_status morse_create(morse_ctx **out, int device, void *cuda_stream) {
   if (!out) return MORSE_EINVAL;

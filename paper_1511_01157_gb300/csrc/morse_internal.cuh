@@ -117,7 +117,9 @@ struct SearchParams {
   // optional device words (nullptr: unused)
   unsigned long long *gthr; // grid-wide pruning threshold (chi^2 bits),
                             // all-ones = +inf
-  unsigned int *err;        // bit 0: a block lock spin gave up
+  unsigned int *err;        // bit 0: a block lock spin gave up;
+                            // bit 1: texel index out of range (checked
+                            // build only)
   unsigned long long *stat_exact;  // trajectories given the exact sweep
 };
 

@@ -255,6 +255,9 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
              cudaGetErrorString(e));
     return MORSE_ECUDA;
   }
+  if (errword & 2u)
+    return set_err(ctx, MORSE_ECUDA,
+                   "bounds check: a texel index fell outside the map");
   if (errword)
     return set_err(ctx, MORSE_ETIMEOUT,
                    "a search block could not take its top-K lock; results "

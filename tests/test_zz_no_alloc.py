@@ -64,7 +64,9 @@ def test_noalloc_does_not_allocate(setup):
 
 def test_noalloc_rejects_oversized_search(setup):
     m, ctx, ev, mp, grid = setup
-    big = m.Grid.make(12, 24, 7, 9, 1e-3, 0.5, -2.0, 2.0, 5.0, 80.0, True,
+    # enough trajectories for one block per SM, K = 4096: two per-block
+    # lists of 4096 16-byte entries per block exceed the 4 MiB scratch
+    big = m.Grid.make(20, 72, 12, 10, 1e-3, 0.5, -2.0, 2.0, 5.0, 80.0, True,
                       True, 4096)
     with pytest.raises(m.MorseError) as e:
         ctx.grid_chi2_noalloc(ev, mp, big)
