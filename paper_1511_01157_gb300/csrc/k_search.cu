@@ -26,11 +26,12 @@
 //    magnification centred on 1, the flux on its weighted mean), reduces
 //    them across the warp, and solves the 2x2 system in FP64 with one
 //    trajectory per lane (32 solves per warp instruction).
-//  * The closed-form chi^2 from those sums, S_FF - Fs S_AF - Fb S_F, loses
-//    digits to cancellation, so it is used only with a rigorous error bound
-//    to discard trajectories that cannot enter the top-K.  Every reported
-//    chi^2 comes from phase 2: a second sweep that sums the per-point
-//    residuals w (F - Fs A - Fb)^2 (FP32 per lane, FP64 across lanes).
+//  * The closed-form chi^2 from those sums, C_FF - C_AF^2 / C_AA, loses
+//    digits to cancellation, so it is used only as a rigorous lower bound
+//    (error-bracketed sums) to discard trajectories that cannot enter the
+//    top-K.  Every reported chi^2 comes from phase 2: a second sweep that
+//    sums the per-point residuals w (F - Fs A - Fb)^2 (FP32 per lane, FP64
+//    across lanes).
 //  * Each block keeps a sorted top-K in shared memory.  A warp merges its
 //    own candidates under a shared-memory lock (bounded spin), so warps
 //    never wait at a block barrier; the block's K-th chi^2 and a grid-wide
@@ -292,15 +293,24 @@ __device__ __forceinline__ double phase2(const SearchParams &P,
 
 struct Solved {
   double Fs, Bc;      // Fb = Bc + Fref - Fs
-  double chi2_cf;     // closed form from the phase-1 sums
-  double bound;       // |closed form - exact| bound
+  double lb;          // rigorous lower bound of the exact chi^2
   bool degenerate;
-  bool always;        // too ill-conditioned to prune on the bound
 };
 
-// 2x2 weighted least squares (Eq. 6) in FP64 from the centred sums.
+// 2x2 weighted least squares (Eq. 6) in FP64 from the centred sums, and a
+// lower bound of the chi^2 the exact residual sweep will give.
 // Degenerate rule: det <= 1e-12 S_AA S_1 (uncentred S_AA) -> Fs = 0,
 // Fb = weighted mean flux.
+//
+// Bound.  With C_FF = S_FF - S_F^2/S_1, C_AA = S_AA - S_A^2/S_1 and
+// C_AF = S_AF - S_A S_F/S_1 the minimum is chi^2 = C_FF - C_AF^2 / C_AA.
+// The FP32 sums carry relative errors of at most gamma of the sums of
+// absolute terms (T_A = sum |w Ac| <= sqrt(S_1 S_AA), T_AF = sum |w Ac Fc|
+// <= sqrt(S_AA S_FF); S_AA has positive terms), so |C_AF| and C_AA are
+// bracketed and C_AF^2 / C_AA <= (|C_AF| + d_AF)^2 / (C_AA - d_AA).  This
+// holds however ill-conditioned (Fs, Fb) is: a nearly flat track explains
+// little of C_FF and is discarded all the same.  C_FF is exact (FP64 sums
+// of the stored values).  gamma is doubled as a margin.
 __device__ __forceinline__ Solved solve2(const SearchParams &P, double SA,
                                          double SAA, double SAF) {
   Solved o;
@@ -310,24 +320,26 @@ __device__ __forceinline__ Solved solve2(const SearchParams &P, double SA,
   if (!(det > 1e-12 * SAAu * S1)) {
     o.Fs = 0.0;
     o.Bc = SF / S1;
-    o.chi2_cf = SFF - o.Bc * SF;
-    o.bound = 0.0;
     o.degenerate = true;
-    o.always = true;
-    return o;
+  } else {
+    const double inv = 1.0 / det;
+    o.Fs = (S1 * SAF - SA * SF) * inv;
+    o.Bc = (SAA * SF - SA * SAF) * inv;
+    o.degenerate = false;
   }
-  const double inv = 1.0 / det;
-  o.Fs = (S1 * SAF - SA * SF) * inv;
-  o.Bc = (SAA * SF - SA * SAF) * inv;
-  o.chi2_cf = SFF - o.Fs * SAF - o.Bc * SF;
-  // Perturbing the sums by relative gamma changes the minimum of the
-  // quadratic by at most gamma (2|Fs| T_AF + Fs^2 S_AA + 2|Fs Bc| T_A) with
-  // T_AF = sum |w Ac Fc| <= sqrt(S_AA S_FF), T_A = sum |w Ac| <= sqrt(S_1
-  // S_AA); AM-GM removes the square roots.
-  o.bound = P.gamma * (3.0 * o.Fs * o.Fs * SAA + SFF + o.Bc * o.Bc * S1);
-  const double cond = (SAA + S1) * (SAA + S1) * inv;
-  o.degenerate = false;
-  o.always = !(P.gamma * cond < 0.1);
+  const double g = 2.0 * P.gamma;
+  const double CFF = SFF - SF * SF / S1;
+  const double CAA = SAA - SA * SA / S1;
+  const double CAF = SAF - SA * SF / S1;
+  const double TA = sqrt(S1 * SAA), TAF = sqrt(SAA * SFF);
+  const double dAA = g * (SAA + (2.0 * fabs(SA) * TA + g * TA * TA) / S1);
+  const double dAF = g * (TAF + TA * fabs(SF) / S1);
+  double X = CFF;  // upper bound of the part of C_FF the fit explains
+  if (CAA > dAA) {
+    const double num = fabs(CAF) + dAF;
+    X = fmin(CFF, num * num / (CAA - dAA));
+  }
+  o.lb = CFF - X;
   return o;
 }
 
@@ -502,8 +514,9 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
       if (P.gthr) thr = fmin(thr, bits_to_chi2(__ldcg(P.gthr)));
     }
     bool cand_me = lane < nvalid;
-    if (!DENSE && cand_me && !sol.always && thr < CUDART_INF)
-      cand_me = (sol.chi2_cf - 4.0 * sol.bound) * (1.0 - 1e-4) <= thr;
+    // 1e-4: margin for the FP32 rounding of the exact sweep itself
+    if (!DENSE && cand_me && thr < CUDART_INF)
+      cand_me = sol.lb * (1.0 - 1e-4) <= thr;
     unsigned todo = __ballot_sync(kFull, cand_me);
     n_exact += __popc(todo);
     const float myFs = __double2float_rn(sol.Fs);

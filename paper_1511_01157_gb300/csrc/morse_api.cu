@@ -346,7 +346,7 @@ void event_params(const morse_event *ev, morse::SearchParams *P) {
   P->SFF = ev->SFF;
   P->Fref = ev->Fref;
   const double m = (double)((ev->n + 31) / 32);
-  P->gamma = (m + 8.0) * ldexp(1.0, -24);
+  P->gamma = (m + 10.0) * ldexp(1.0, -24);
 }
 
 void grid_params(const morse_grid *g, const Tables &T,
@@ -805,9 +805,11 @@ morse_status morse_event_create(morse_ctx *ctx, const double *t,
                   "epoch %lld: weight 1/sigma^2 outside FP32 range",
                   (long long)i);
     h[(size_t)k] = v;
+    // constants of the quadratic the exact sweep evaluates: sum w Fc and
+    // sum w Fc^2 with the stored w and Fc
     S1 += (double)v.y;
-    SF += (double)v.z;
-    SFF += (double)v.z * (double)v.w;
+    SF += (double)v.y * (double)v.w;
+    SFF += (double)v.y * (double)v.w * (double)v.w;
   }
   MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
   morse_event *ev = (morse_event *)calloc(1, sizeof(morse_event));

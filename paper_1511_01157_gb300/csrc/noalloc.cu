@@ -197,7 +197,7 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   P.SF = ev->SF;
   P.SFF = ev->SFF;
   P.Fref = ev->Fref;
-  P.gamma = ((double)((ev->n + 31) / 32) + 8.0) * ldexp(1.0, -24);
+  P.gamma = ((double)((ev->n + 31) / 32) + 10.0) * ldexp(1.0, -24);
   P.u0v = u0v;
   P.ca = ca;
   P.sa = sa;
