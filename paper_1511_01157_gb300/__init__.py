@@ -20,10 +20,15 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-# MORSE_LIB=checked selects the bounds-checked build (tests)
-LIB_PATH = os.path.join(
-    _HERE, "libmorse_checked.so" if os.environ.get("MORSE_LIB") == "checked"
-    else "libmorse.so")
+# MORSE_LIB=checked selects the bounds-checked build (tests); a path to a
+# .so selects another build of the same library (tuning experiments)
+_sel = os.environ.get("MORSE_LIB", "")
+if _sel == "checked":
+    LIB_PATH = os.path.join(_HERE, "libmorse_checked.so")
+elif _sel.endswith(".so") and os.path.exists(_sel):
+    LIB_PATH = os.path.abspath(_sel)
+else:
+    LIB_PATH = os.path.join(_HERE, "libmorse.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(

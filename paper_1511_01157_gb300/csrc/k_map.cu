@@ -221,7 +221,7 @@ __device__ __forceinline__ float mag_of(const uint32_t *c, int npix, int x,
 
 __global__ void k_counts_to_map(const uint32_t *__restrict__ counts, int npix,
                                 double f, float *__restrict__ A,
-                                float4 *__restrict__ quad) {
+                                float4 *__restrict__ quad, int qpitch) {
   size_t n = (size_t)npix * npix;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
        k += (size_t)gridDim.x * blockDim.x) {
@@ -229,20 +229,22 @@ __global__ void k_counts_to_map(const uint32_t *__restrict__ counts, int npix,
     int x1 = min(x + 1, npix - 1), y1 = min(y + 1, npix - 1);
     float a00 = mag_of(counts, npix, x, y, f);
     A[k] = a00;
-    quad[k] = make_float4(a00, mag_of(counts, npix, x1, y, f),
+    quad[(size_t)y * qpitch + x] = make_float4(a00,
+                          mag_of(counts, npix, x1, y, f),
                           mag_of(counts, npix, x, y1, f),
                           mag_of(counts, npix, x1, y1, f));
   }
 }
 
 __global__ void k_quads_from_A(const float *__restrict__ A, int npix,
-                               float4 *__restrict__ quad) {
+                               float4 *__restrict__ quad, int qpitch) {
   size_t n = (size_t)npix * npix;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
        k += (size_t)gridDim.x * blockDim.x) {
     int x = (int)(k % npix), y = (int)(k / npix);
     int x1 = min(x + 1, npix - 1), y1 = min(y + 1, npix - 1);
-    quad[k] = make_float4(A[(size_t)y * npix + x], A[(size_t)y * npix + x1],
+    quad[(size_t)y * qpitch + x] =
+        make_float4(A[(size_t)y * npix + x], A[(size_t)y * npix + x1],
                           A[(size_t)y1 * npix + x], A[(size_t)y1 * npix + x1]);
   }
 }
@@ -287,17 +289,18 @@ static int elementwise_grid(size_t n) {
 }
 
 cudaError_t launch_counts_to_map(const uint32_t *counts, int npix, double f,
-                                 float *A, float4 *quad, cudaStream_t st) {
+                                 float *A, float4 *quad, int qpitch,
+                                 cudaStream_t st) {
   size_t n = (size_t)npix * npix;
   k_counts_to_map<<<elementwise_grid(n), 256, 0, st>>>(counts, npix, f, A,
-                                                       quad);
+                                                       quad, qpitch);
   return cudaGetLastError();
 }
 
 cudaError_t launch_quads_from_A(const float *A, int npix, float4 *quad,
-                                cudaStream_t st) {
+                                int qpitch, cudaStream_t st) {
   size_t n = (size_t)npix * npix;
-  k_quads_from_A<<<elementwise_grid(n), 256, 0, st>>>(A, npix, quad);
+  k_quads_from_A<<<elementwise_grid(n), 256, 0, st>>>(A, npix, quad, qpitch);
   return cudaGetLastError();
 }
 

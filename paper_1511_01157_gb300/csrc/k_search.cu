@@ -35,8 +35,10 @@
 //  * Each block keeps a sorted top-K in shared memory.  A warp merges its
 //    own candidates under a shared-memory lock (bounded spin), so warps
 //    never wait at a block barrier; the block's K-th chi^2 and a grid-wide
-//    minimum of the blocks' K-th values (atomicMin on the bit pattern) are
-//    the pruning threshold.  A tree of pairwise merges gives the global
+//    minimum of K-th values (atomicMin on the bit pattern) are the pruning
+//    threshold.  The grid-wide value is seeded by a pilot search over a
+//    strided subset of about sqrt(K N) trajectories, so that it is tight
+//    from the start.  A tree of pairwise merges gives the global
 //    top-K and k_fill recomputes the winners' records with the same device
 //    functions.
 #include <cuda_runtime.h>
@@ -195,7 +197,7 @@ __device__ __forceinline__ float bilinear(const SearchParams &P, float vx,
     return 0.f;
   }
 #endif
-  const float4 q = __ldg(&P.quad[iy * P.npix + ix]);
+  const float4 q = __ldg(&P.quad[iy * P.qpitch + ix]);
   const float r0 = __fmaf_rn(fx, __fsub_rn(q.y, q.x), q.x);
   const float r1 = __fmaf_rn(fx, __fsub_rn(q.w, q.z), q.z);
   return __fmaf_rn(fy, __fsub_rn(r1, r0), r0);
@@ -494,7 +496,8 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
        g < n_groups; g += stride) {
     const long long base = g * 32;
     const int nvalid = (int)min(32LL, P.count - base);
-    const long long my = P.first + base + (lane < nvalid ? lane : 0);
+    const long long my =
+        P.first + (base + (lane < nvalid ? lane : 0)) * P.stride;
     const TrajC mine = traj_consts(P, ep, my);
     float mA = 0.f, mAA = 0.f, mAF = 0.f;
     for (int k = 0; k < nvalid; ++k) {
@@ -540,7 +543,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
       }
     } else {
       const bool keep = lane < nvalid && my_chi2 <= thr && my_chi2 < CUDART_INF;
-      warp_merge(P, T, K, warp, lane, keep, my_chi2, P.first + base + lane);
+      warp_merge(P, T, K, warp, lane, keep, my_chi2, my);
     }
   }
   if (P.stat_exact && lane == 0 && n_exact)
@@ -645,6 +648,16 @@ __global__ void k_fill(const FillParams F) {
   }
 }
 
+// Seed the grid-wide threshold with the K-th chi^2 of a pilot search over
+// a subset of the grid: K trajectories at or below it exist, so anything
+// above it cannot enter the global top-K.
+__global__ void k_seed_threshold(const Entry *sel, int k,
+                                 unsigned long long *gthr) {
+  const Entry e = sel[k - 1];
+  if (e.chi2 < CUDART_INF && e.idx >= 0 && e.idx < 0x7fff000000000000LL)
+    atomicMin(gthr, (unsigned long long)__double_as_longlong(e.chi2));
+}
+
 // A(t) along one trajectory given by (ax, bx, ay, by) with v = a t + b, and
 // tau = kt t + bt, u0^2 for the single-lens part outside the map.
 __global__ void k_lightcurve(const SearchParams P, float ax, float bx,
@@ -673,10 +686,28 @@ size_t search_smem_bytes(int n_ep_smem, int top_k) {
          sizeof(Entry) * ((size_t)2 * top_k + kSearchWarps * 32);
 }
 
+#ifndef MORSE_SMEM_CARVEOUT
+#define MORSE_SMEM_CARVEOUT 1
+#endif
+
 template <bool D, bool E>
 static int occupancy(size_t smem) {
   cudaFuncSetAttribute(k_search<D, E>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+#if MORSE_SMEM_CARVEOUT
+  // ask for the smallest shared-memory carveout that holds the block, so
+  // the rest of the SM's 256 KB serves as L1 for the map gathers
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                         dev);
+  if (optin > 0) {
+    int pct = (int)((100.0 * (double)(smem + 2048)) / (double)optin) + 1;
+    if (pct > 100) pct = 100;
+    cudaFuncSetAttribute(k_search<D, E>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  }
+#endif
   int b = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
           &b, k_search<D, E>, kSearchWarps * 32, smem) != cudaSuccess) {
@@ -733,6 +764,12 @@ cudaError_t launch_fill(const FillParams &F, cudaStream_t st) {
   const int threads = 256;
   const int blocks = (F.k * 32 + threads - 1) / threads;
   k_fill<<<blocks, threads, 0, st>>>(F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed_threshold(const Entry *sel, int k,
+                                  unsigned long long *gthr, cudaStream_t st) {
+  k_seed_threshold<<<1, 1, 0, st>>>(sel, k, gthr);
   return cudaGetLastError();
 }
 

@@ -187,8 +187,10 @@ morse_map *map_alloc(morse_ctx *ctx, int npix, bool counts) {
   m->ctx = ctx;
   m->npix = npix;
   size_t n = (size_t)npix * npix;
+  m->qpitch = morse::quad_pitch(npix);
   bool ok = cudaMalloc(&m->A, n * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&m->quad, n * sizeof(float4)) == cudaSuccess &&
+            cudaMalloc(&m->quad, (size_t)npix * m->qpitch * sizeof(float4)) ==
+                cudaSuccess &&
             cudaMalloc(&m->tot, 2 * sizeof(unsigned long long)) == cudaSuccess;
   if (ok && counts)
     ok = cudaMalloc(&m->counts, n * sizeof(uint32_t)) == cudaSuccess;
@@ -262,7 +264,8 @@ morse_status enqueue_build(morse_ctx *ctx, morse_map *m, const BuildSpec &b) {
   const double f = (P.h * P.h) / (P.dlt * P.dlt);
   r = t_begin(ctx, KT_MAP);
   MORSE_CUDA(ctx, morse::launch_counts_to_map(m->counts, b.npix, f, m->A,
-                                              m->quad, ctx->stream));
+                                              m->quad, m->qpitch,
+                                              ctx->stream));
   t_end(ctx, r);
   ctx->launches += 1;
   return MORSE_OK;
@@ -324,6 +327,7 @@ morse_status upload_tables(morse_ctx *ctx, const morse_grid *g, double t_ref,
 void map_params(const morse_map *map, morse::SearchParams *P) {
   const double dlt = (2.0 * map->L) / (double)map->npix;
   P->quad = map->quad;
+  P->qpitch = map->qpitch;
   P->npix = map->npix;
   P->half = map->npix / 2;
   P->vlo = -(float)(map->npix / 2) - 0.5f;
@@ -465,7 +469,36 @@ morse_status enqueue_topk(morse_ctx *ctx, const Plan &pl,
                           morse::SearchParams P, char *base,
                           const Tables &T, morse_fit *fits_dev) {
   P.partial = (Entry *)(base + pl.off_pa);
-  int r = t_begin(ctx, KT_SEARCH);
+  int r;
+  // pilot: a strided subset of ~sqrt(K N) trajectories (at least 16 K)
+  // seeds the grid-wide pruning threshold
+  const double want = std::max(16.0 * pl.K, std::sqrt((double)pl.K * P.count));
+  const long long stride = (long long)(P.count / want);
+  if (P.gthr && stride >= 4) {
+    morse::SearchParams Q = P;
+    Q.stride = stride;
+    Q.count = (P.count + stride - 1) / stride;
+    long long groups = (Q.count + 31) / 32;
+    int grid = (int)std::min<long long>(
+        pl.grid, (groups + morse::kSearchWarps - 1) / morse::kSearchWarps);
+    if (grid < 1) grid = 1;
+    r = t_begin(ctx, KT_SEARCH);
+    MORSE_CUDA(ctx, morse::launch_search(Q, false, pl.ep_smem, grid, pl.smem,
+                                         ctx->stream));
+    t_end(ctx, r);
+    Entry *sel = nullptr;
+    int levels = 0;
+    r = t_begin(ctx, KT_MERGE);
+    MORSE_CUDA(ctx, morse::launch_topk_merge((Entry *)(base + pl.off_pa),
+                                             (Entry *)(base + pl.off_pb), grid,
+                                             pl.K, &sel, &levels,
+                                             ctx->stream));
+    MORSE_CUDA(ctx, morse::launch_seed_threshold(sel, pl.K, P.gthr,
+                                                 ctx->stream));
+    t_end(ctx, r);
+    ctx->launches += 2 + (uint64_t)levels;
+  }
+  r = t_begin(ctx, KT_SEARCH);
   MORSE_CUDA(ctx, morse::launch_search(P, false, pl.ep_smem, pl.grid, pl.smem,
                                        ctx->stream));
   t_end(ctx, r);
@@ -533,6 +566,7 @@ morse_status sweep_impl(morse_ctx *ctx, const morse_event *ev,
   grid_params(grid, T, &P);
   P.first = 0;
   P.count = grid_size(grid);
+  P.stride = 1;
   morse_fit *fits = (morse_fit *)(base + pl.off_out);
   MORSE_TRY(hdr_init(ctx, base, pl, &P));
   for (int i = 0; i < n_maps; ++i) {
@@ -699,7 +733,8 @@ morse_status morse_map_from_host(morse_ctx *ctx, const float *A, int npix,
   cudaError_t e = cudaMemcpyAsync(m->A, A, n * sizeof(float),
                                   cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) {
-    e = morse::launch_quads_from_A(m->A, npix, m->quad, ctx->stream);
+    e = morse::launch_quads_from_A(m->A, npix, m->quad, m->qpitch,
+                                   ctx->stream);
     ctx->launches += 1;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -878,6 +913,7 @@ morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
   grid_params(grid, T, &P);
   P.first = 0;
   P.count = grid_size(grid);
+  P.stride = 1;
   morse_fit *fits = (morse_fit *)(base + pl.off_out);
   MORSE_TRY(hdr_init(ctx, base, pl, &P));
   MORSE_TRY(enqueue_topk(ctx, pl, P, base, T, fits));
@@ -920,6 +956,7 @@ morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
   grid_params(grid, T, &P);
   P.first = first;
   P.count = count;
+  P.stride = 1;
   P.top_k = 1;
   P.dchi2 = (double *)(base + pl.off_out);
   P.dFs = P.dchi2 + count;

@@ -40,7 +40,9 @@ struct morse_map {
   bool has_counts;
   uint32_t *counts;         // [npix*npix] ray counts (device)
   float *A;                 // [npix*npix] FP32 magnification (device)
-  float4 *quad;             // [npix*npix] 2x2 texel neighbourhoods (device)
+  float4 *quad;             // [npix rows x qpitch] 2x2 texel neighbourhoods
+  int qpitch;               // quads per row: npix + pad (spreads the rows of
+                            // a steep track over cache sets)
   unsigned long long *tot;  // [2] off-map, lost (device)
   uint64_t off_map, lost;
 };
@@ -77,10 +79,17 @@ constexpr int kRayThreads = 512;  // threads per ray-shooting block
 
 cudaError_t launch_rayshoot(const RayParams &P, bool fp64, int grid,
                             cudaStream_t st);
+// Quad row pitch for an npix map (float4 units).
+#ifndef MORSE_QPITCH_PAD
+#define MORSE_QPITCH_PAD 8
+#endif
+inline int quad_pitch(int npix) { return npix + MORSE_QPITCH_PAD; }
+
 cudaError_t launch_counts_to_map(const uint32_t *counts, int npix, double f,
-                                 float *A, float4 *quad, cudaStream_t st);
+                                 float *A, float4 *quad, int qpitch,
+                                 cudaStream_t st);
 cudaError_t launch_quads_from_A(const float *A, int npix, float4 *quad,
-                                cudaStream_t st);
+                                int qpitch, cudaStream_t st);
 int rayshoot_blocks_per_sm();
 
 // ---------------------------------------------------------------- search
@@ -93,6 +102,7 @@ struct SearchParams {
   // map
   const float4 *quad;
   int npix, half;           // npix, npix/2
+  int qpitch;               // quad row pitch (float4 units)
   float vlo, vhi;           // inside iff vlo < v < vhi (centred coords)
   float vmin;               // -npix/2: clamp to the first texel centre
   float vmax;               // npix - npix/2 - 1: centre of the last texel
@@ -109,7 +119,8 @@ struct SearchParams {
   // grid tables (device, FP64)
   const double *u0v, *ca, *sa, *t0rel, *invtEd;
   int n_u0, n_alpha, n_t0, n_tE;
-  long long first, count;   // trajectory index range
+  long long first, count;   // trajectories first + i * stride, i < count
+  long long stride;
   int top_k;
   // outputs
   Entry *partial;           // [gridDim.x][top_k] (top-K mode)
@@ -142,6 +153,9 @@ cudaError_t launch_search(const SearchParams &P, bool dense, bool ep_smem,
 cudaError_t launch_topk_merge(Entry *a, Entry *b, int lists, int k,
                               Entry **result, int *levels, cudaStream_t st);
 cudaError_t launch_fill(const FillParams &F, cudaStream_t st);
+// gthr <- min(gthr, chi^2 bits of sel[k-1]) when that entry is real
+cudaError_t launch_seed_threshold(const Entry *sel, int k,
+                                  unsigned long long *gthr, cudaStream_t st);
 cudaError_t launch_lightcurve(const SearchParams &P, float ax, float bx,
                               float ay, float by, float kt, float bt,
                               float u02, const float *t, int n, float *A,

@@ -179,6 +179,7 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   morse::SearchParams P;
   memset(&P, 0, sizeof(P));
   P.quad = map->quad;
+  P.qpitch = map->qpitch;
   P.npix = map->npix;
   P.half = map->npix / 2;
   P.vlo = -(float)(map->npix / 2) - 0.5f;
@@ -210,6 +211,7 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   P.top_k = K;
   P.first = 0;
   P.count = count;
+  P.stride = 1;
   P.partial = (morse::Entry *)(base + off_a);
   // status words: the grid-wide pruning threshold (all-ones = +inf) and the
   // error word of the block locks
