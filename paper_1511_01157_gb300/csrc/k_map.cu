@@ -212,8 +212,8 @@ __global__ void __launch_bounds__(kRayThreads)
   }
 }
 
-// counts -> A = count * f (FP64 product rounded to FP32) and 2x2 quads with
-// the last row/column replicated.
+// counts -> A = count * f (FP64 product rounded to FP32) and 2x2 quads of
+// A - 1 with the last row/column replicated.
 __device__ __forceinline__ float mag_of(const uint32_t *c, int npix, int x,
                                         int y, double f) {
   return __double2float_rn(__dmul_rn((double)c[(size_t)y * npix + x], f));
@@ -229,10 +229,11 @@ __global__ void k_counts_to_map(const uint32_t *__restrict__ counts, int npix,
     int x1 = min(x + 1, npix - 1), y1 = min(y + 1, npix - 1);
     float a00 = mag_of(counts, npix, x, y, f);
     A[k] = a00;
-    quad[(size_t)y * qpitch + x] = make_float4(a00,
-                          mag_of(counts, npix, x1, y, f),
-                          mag_of(counts, npix, x, y1, f),
-                          mag_of(counts, npix, x1, y1, f));
+    // the search reads A - 1 (FP32 of the FP32 value: exact for A <= 2)
+    quad[(size_t)y * qpitch + x] =
+        make_float4(a00 - 1.0f, mag_of(counts, npix, x1, y, f) - 1.0f,
+                    mag_of(counts, npix, x, y1, f) - 1.0f,
+                    mag_of(counts, npix, x1, y1, f) - 1.0f);
   }
 }
 
@@ -243,9 +244,9 @@ __global__ void k_quads_from_A(const float *__restrict__ A, int npix,
        k += (size_t)gridDim.x * blockDim.x) {
     int x = (int)(k % npix), y = (int)(k / npix);
     int x1 = min(x + 1, npix - 1), y1 = min(y + 1, npix - 1);
-    quad[(size_t)y * qpitch + x] =
-        make_float4(A[(size_t)y * npix + x], A[(size_t)y * npix + x1],
-                          A[(size_t)y1 * npix + x], A[(size_t)y1 * npix + x1]);
+    quad[(size_t)y * qpitch + x] = make_float4(
+        A[(size_t)y * npix + x] - 1.0f, A[(size_t)y * npix + x1] - 1.0f,
+        A[(size_t)y1 * npix + x] - 1.0f, A[(size_t)y1 * npix + x1] - 1.0f);
   }
 }
 

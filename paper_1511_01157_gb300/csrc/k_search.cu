@@ -51,6 +51,11 @@ namespace morse {
 
 namespace {
 
+#ifndef MORSE_UNROLL
+#define MORSE_UNROLL 4
+#endif
+constexpr int kUnroll = MORSE_UNROLL;  // inside-map epoch loop
+
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned kLockSpinLimit = 1u << 20;
 
@@ -173,31 +178,37 @@ __device__ __forceinline__ float pspl_u2(float u2) {
                    rsqrt_approx(__fmul_rn(u2, __fadd_rn(u2, 4.f))));
 }
 
-// Bilinear magnification at centred coordinates inside the map.  The
-// clamps keep the texel index in [0, npix-1] whatever v is; inside the map
-// they change nothing (below: the clamp to the first texel centre is the
-// lookup rule; above: the last texel's quad repeats its edge values, so
-// v and its clamp give the same value).
-__device__ __forceinline__ float bilinear(const SearchParams &P, float vx,
-                                          float vy) {
-  const float cx = fminf(fmaxf(vx, P.vmin), P.vmax);
-  const float cy = fminf(fmaxf(vy, P.vmin), P.vmax);
+// Bilinear A - 1 at centred coordinates inside the map (the quads store
+// A - 1).  Coordinates below the first texel centre are clamped to it (the
+// lookup rule).  Above the last centre no clamp is needed: the caller only
+// passes epochs strictly inside the map, so floor(v) <= npix - half - 1, and
+// the last texel's quad repeats its edge values.  The bounds-checked build
+// verifies the index range.
+__device__ __forceinline__ float bilinear_m1(const SearchParams &P, float vx,
+                                             float vy) {
+  const float cx = fmaxf(vx, P.vmin);
+  const float cy = fmaxf(vy, P.vmin);
   // floor: adding 1.5 * 2^23 rounding down leaves floor(c) in the low
   // mantissa bits; the fraction c - floor(c) is exact
   const float tx = __fadd_rd(cx, 12582912.f), ty = __fadd_rd(cy, 12582912.f);
-  // floor(c) is in [-half, npix - half - 1]; + half gives [0, npix - 1]
-  const int ix = __float_as_int(tx) - 0x4B400000 + P.half;
-  const int iy = __float_as_int(ty) - 0x4B400000 + P.half;
   const float fx = __fsub_rn(cx, __fsub_rn(tx, 12582912.f));
   const float fy = __fsub_rn(cy, __fsub_rn(ty, 12582912.f));
+  // texel (ix, iy) = floor(c) + half; quad index iy * qpitch + ix, folded
+  // into one multiply-add on the raw bit patterns (mod 2^32, exact because
+  // the index is in [0, npix * qpitch))
+  const unsigned bx = (unsigned)__float_as_int(tx);
+  const unsigned by = (unsigned)__float_as_int(ty);
+  const unsigned idx = by * (unsigned)P.qpitch + bx + P.qidx0;
 #ifdef MORSE_CHECK_BOUNDS
   // checked build: record an out-of-range texel and skip the access
+  const int ix = (int)(bx - 0x4B400000u) + P.half;
+  const int iy = (int)(by - 0x4B400000u) + P.half;
   if ((unsigned)ix >= (unsigned)P.npix || (unsigned)iy >= (unsigned)P.npix) {
     if (P.err) atomicOr(P.err, 2u);
     return 0.f;
   }
 #endif
-  const float4 q = __ldg(&P.quad[iy * P.qpitch + ix]);
+  const float4 q = __ldg(&P.quad[idx]);
   const float r0 = __fmaf_rn(fx, __fsub_rn(q.y, q.x), q.x);
   const float r1 = __fmaf_rn(fx, __fsub_rn(q.w, q.z), q.z);
   return __fmaf_rn(fy, __fsub_rn(r1, r0), r0);
@@ -222,12 +233,11 @@ __device__ __forceinline__ void phase1(const SearchParams &P,
     b = __fmaf_rn(wAc, Ac, b);
     d = __fmaf_rn(v.z, Ac, d);
   }
-#pragma unroll 4
+#pragma unroll (kUnroll)
   for (int e = c.e_in + lane; e < c.e_out; e += 32) {
     const float4 v = ep[e];
-    const float Ac = __fsub_rn(
-        bilinear(P, __fmaf_rn(c.ax, v.x, c.bx), __fmaf_rn(c.ay, v.x, c.by)),
-        1.f);
+    const float Ac = bilinear_m1(P, __fmaf_rn(c.ax, v.x, c.bx),
+                                 __fmaf_rn(c.ay, v.x, c.by));
     const float wAc = __fmul_rn(v.y, Ac);
     a = __fadd_rn(a, wAc);
     b = __fmaf_rn(wAc, Ac, b);
@@ -270,12 +280,11 @@ __device__ __forceinline__ double phase2(const SearchParams &P,
     const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
     chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
   }
-#pragma unroll 4
+#pragma unroll (kUnroll)
   for (int e = c.e_in + lane; e < c.e_out; e += 32) {
     const float4 v = ep[e];
-    const float Ac = __fsub_rn(
-        bilinear(P, __fmaf_rn(c.ax, v.x, c.bx), __fmaf_rn(c.ay, v.x, c.by)),
-        1.f);
+    const float Ac = bilinear_m1(P, __fmaf_rn(c.ax, v.x, c.bx),
+                                 __fmaf_rn(c.ay, v.x, c.by));
     const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
     chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
   }
@@ -488,14 +497,15 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
   }
   __syncthreads();
 
-  const long long n_groups = (P.count + 31) / 32;
+  const int tpg = P.tpg;  // trajectories per warp group (1..32)
+  const long long n_groups = (P.count + tpg - 1) / tpg;
   const long long stride = (long long)gridDim.x * kSearchWarps;
   unsigned long long n_exact = 0;
 
   for (long long g = (long long)blockIdx.x * kSearchWarps + warp;
        g < n_groups; g += stride) {
-    const long long base = g * 32;
-    const int nvalid = (int)min(32LL, P.count - base);
+    const long long base = g * tpg;
+    const int nvalid = (int)min((long long)tpg, P.count - base);
     const long long my =
         P.first + (base + (lane < nvalid ? lane : 0)) * P.stride;
     const TrajC mine = traj_consts(P, ep, my);
@@ -671,7 +681,7 @@ __global__ void k_lightcurve(const SearchParams P, float ax, float bx,
     const bool inside =
         (vx > P.vlo) & (vx < P.vhi) & (vy > P.vlo) & (vy < P.vhi);
     if (inside) {
-      A[i] = bilinear(P, vx, vy);
+      A[i] = __fadd_rn(bilinear_m1(P, vx, vy), 1.f);
     } else {
       const float tau = __fmaf_rn(kt, t[i], bt);
       A[i] = pspl_u2(__fmaf_rn(tau, tau, u02));

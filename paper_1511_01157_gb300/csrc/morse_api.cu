@@ -328,6 +328,8 @@ void map_params(const morse_map *map, morse::SearchParams *P) {
   const double dlt = (2.0 * map->L) / (double)map->npix;
   P->quad = map->quad;
   P->qpitch = map->qpitch;
+  P->qidx0 = (unsigned)(map->npix / 2 - 0x4B400000) *
+             (unsigned)(map->qpitch + 1);
   P->npix = map->npix;
   P->half = map->npix / 2;
   P->vlo = -(float)(map->npix / 2) - 0.5f;
@@ -442,7 +444,7 @@ morse_status plan_search(morse_ctx *ctx, const morse_event *ev,
     return fail(ctx, MORSE_EUNSUPPORTED,
                 "search kernel does not fit (epochs %lld, top_k %d)",
                 (long long)ev->n, K);
-  long long groups = (count + 31) / 32;
+  long long groups = (count + morse::kTpgMain - 1) / morse::kTpgMain;
   long long want = (groups + morse::kSearchWarps - 1) / morse::kSearchWarps;
   int grid = (int)std::min<long long>((long long)bps * ctx->sm_count, want);
   if (grid < 1) grid = 1;
@@ -478,7 +480,8 @@ morse_status enqueue_topk(morse_ctx *ctx, const Plan &pl,
     morse::SearchParams Q = P;
     Q.stride = stride;
     Q.count = (P.count + stride - 1) / stride;
-    long long groups = (Q.count + 31) / 32;
+    Q.tpg = morse::kTpgPilot;
+    long long groups = (Q.count + Q.tpg - 1) / Q.tpg;
     int grid = (int)std::min<long long>(
         pl.grid, (groups + morse::kSearchWarps - 1) / morse::kSearchWarps);
     if (grid < 1) grid = 1;
@@ -567,6 +570,7 @@ morse_status sweep_impl(morse_ctx *ctx, const morse_event *ev,
   P.first = 0;
   P.count = grid_size(grid);
   P.stride = 1;
+  P.tpg = morse::kTpgMain;
   morse_fit *fits = (morse_fit *)(base + pl.off_out);
   MORSE_TRY(hdr_init(ctx, base, pl, &P));
   for (int i = 0; i < n_maps; ++i) {
@@ -914,6 +918,7 @@ morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
   P.first = 0;
   P.count = grid_size(grid);
   P.stride = 1;
+  P.tpg = morse::kTpgMain;
   morse_fit *fits = (morse_fit *)(base + pl.off_out);
   MORSE_TRY(hdr_init(ctx, base, pl, &P));
   MORSE_TRY(enqueue_topk(ctx, pl, P, base, T, fits));
@@ -957,6 +962,7 @@ morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
   P.first = first;
   P.count = count;
   P.stride = 1;
+  P.tpg = morse::kTpgMain;
   P.top_k = 1;
   P.dchi2 = (double *)(base + pl.off_out);
   P.dFs = P.dchi2 + count;

@@ -40,7 +40,7 @@ struct morse_map {
   bool has_counts;
   uint32_t *counts;         // [npix*npix] ray counts (device)
   float *A;                 // [npix*npix] FP32 magnification (device)
-  float4 *quad;             // [npix rows x qpitch] 2x2 texel neighbourhoods
+  float4 *quad;             // [npix rows x qpitch] 2x2 neighbourhoods of A-1
   int qpitch;               // quads per row: npix + pad (spreads the rows of
                             // a steep track over cache sets)
   unsigned long long *tot;  // [2] off-map, lost (device)
@@ -103,6 +103,8 @@ struct SearchParams {
   const float4 *quad;
   int npix, half;           // npix, npix/2
   int qpitch;               // quad row pitch (float4 units)
+  unsigned qidx0;           // quad index offset for the raw floor bits:
+                            // (half - 0x4B400000) (qpitch + 1) mod 2^32
   float vlo, vhi;           // inside iff vlo < v < vhi (centred coords)
   float vmin;               // -npix/2: clamp to the first texel centre
   float vmax;               // npix - npix/2 - 1: centre of the last texel
@@ -121,6 +123,7 @@ struct SearchParams {
   int n_u0, n_alpha, n_t0, n_tE;
   long long first, count;   // trajectories first + i * stride, i < count
   long long stride;
+  int tpg;                  // trajectories per warp group (1..32)
   int top_k;
   // outputs
   Entry *partial;           // [gridDim.x][top_k] (top-K mode)
@@ -142,7 +145,16 @@ struct FillParams {
   morse_fit *out;           // [k]
 };
 
-constexpr int kSearchWarps = 32;
+#ifndef MORSE_SEARCH_WARPS
+#define MORSE_SEARCH_WARPS 32
+#endif
+constexpr int kSearchWarps = MORSE_SEARCH_WARPS;  // one block per SM
+#ifndef MORSE_TPG
+#define MORSE_TPG 32
+#endif
+constexpr int kTpgMain = MORSE_TPG;  // main pass
+constexpr int kTpgPilot = 4;         // pilot: spread a small sample over
+                                     // every SM
 
 size_t search_smem_bytes(int n_ep_smem, int top_k);
 int search_blocks_per_sm(bool dense, bool ep_smem, size_t smem);

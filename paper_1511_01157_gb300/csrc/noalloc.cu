@@ -106,7 +106,7 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   const int bps = morse::search_blocks_per_sm(false, ep_smem, smem);
   if (bps < 1)
     return set_err(ctx, MORSE_EUNSUPPORTED, "search kernel does not fit");
-  long long groups = (count + 31) / 32;
+  long long groups = (count + morse::kTpgMain - 1) / morse::kTpgMain;
   long long want = (groups + morse::kSearchWarps - 1) / morse::kSearchWarps;
   int grid = (int)std::min<long long>((long long)bps * ctx->sm_count, want);
   if (grid < 1) grid = 1;
@@ -180,6 +180,8 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   memset(&P, 0, sizeof(P));
   P.quad = map->quad;
   P.qpitch = map->qpitch;
+  P.qidx0 = (unsigned)(map->npix / 2 - 0x4B400000) *
+            (unsigned)(map->qpitch + 1);
   P.npix = map->npix;
   P.half = map->npix / 2;
   P.vlo = -(float)(map->npix / 2) - 0.5f;
@@ -212,6 +214,7 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   P.first = 0;
   P.count = count;
   P.stride = 1;
+  P.tpg = morse::kTpgMain;
   P.partial = (morse::Entry *)(base + off_a);
   // status words: the grid-wide pruning threshold (all-ones = +inf) and the
   // error word of the block locks
