@@ -497,17 +497,41 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
   }
   __syncthreads();
 
+  // Warp groups.  A strided sample (pilot, stride > 1) is cut into runs of
+  // tpg sample indices.  Otherwise groups are aligned to (u0, alpha) lines
+  // (P.line consecutive trajectories share the track's line), ng_line
+  // groups per line, so that the warps of a block, which take consecutive
+  // groups, walk the same line of the map and share its texels in L1.
   const int tpg = P.tpg;  // trajectories per warp group (1..32)
-  const long long n_groups = (P.count + tpg - 1) / tpg;
-  const long long stride = (long long)gridDim.x * kSearchWarps;
+  const bool lined = P.stride == 1 && P.line > 0;
+  long long n_groups, line0 = 0;
+  if (lined) {
+    line0 = P.first / P.line;
+    const long long line1 = (P.first + P.count - 1) / P.line;
+    n_groups = (line1 - line0 + 1) * P.ng_line;
+  } else {
+    n_groups = (P.count + tpg - 1) / tpg;
+  }
+  const long long gstride = (long long)gridDim.x * kSearchWarps;
   unsigned long long n_exact = 0;
 
   for (long long g = (long long)blockIdx.x * kSearchWarps + warp;
-       g < n_groups; g += stride) {
-    const long long base = g * tpg;
-    const int nvalid = (int)min((long long)tpg, P.count - base);
-    const long long my =
-        P.first + (base + (lane < nvalid ? lane : 0)) * P.stride;
+       g < n_groups; g += gstride) {
+    long long lo, hi;  // absolute indices (lined) or sample indices
+    if (lined) {
+      const long long L = line0 + g / P.ng_line;
+      const long long gi = g % P.ng_line;
+      lo = max(P.first, L * P.line + gi * tpg);
+      hi = min(P.first + P.count, L * P.line + min((gi + 1) * tpg, P.line));
+    } else {
+      lo = g * tpg;
+      hi = min(lo + tpg, P.count);
+    }
+    const int nvalid = (int)max(0LL, hi - lo);
+    if (nvalid == 0) continue;  // warp-uniform
+    const int ml = lane < nvalid ? lane : 0;
+    const long long my = lined ? lo + ml : P.first + (lo + ml) * P.stride;
+    const long long out_off = lined ? lo - P.first : lo;  // dense output
     const TrajC mine = traj_consts(P, ep, my);
     float mA = 0.f, mAA = 0.f, mAF = 0.f;
     for (int k = 0; k < nvalid; ++k) {
@@ -546,7 +570,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
     }
     if (DENSE) {
       if (lane < nvalid) {
-        const long long o = base + lane;
+        const long long o = out_off + lane;
         P.dchi2[o] = my_chi2;
         if (P.dFs) P.dFs[o] = sol.Fs;
         if (P.dFb) P.dFb[o] = sol.Bc + P.Fref - sol.Fs;

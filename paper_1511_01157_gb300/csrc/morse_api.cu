@@ -430,8 +430,9 @@ morse_status hdr_check(morse_ctx *ctx, const Hdr &h) {
 }
 
 morse_status plan_search(morse_ctx *ctx, const morse_event *ev,
-                         const morse_grid *g, long long count, bool dense,
-                         long long n_out, Plan *pl) {
+                         const morse_grid *g, long long first,
+                         long long count, bool dense, long long n_out,
+                         Plan *pl) {
   const int K = dense ? 1 : g->top_k;
   const size_t fixed = morse::search_smem_bytes(0, dense ? 0 : K) -
                        (dense ? sizeof(Entry) * morse::kSearchWarps * 32 : 0);
@@ -444,7 +445,8 @@ morse_status plan_search(morse_ctx *ctx, const morse_event *ev,
     return fail(ctx, MORSE_EUNSUPPORTED,
                 "search kernel does not fit (epochs %lld, top_k %d)",
                 (long long)ev->n, K);
-  long long groups = (count + morse::kTpgMain - 1) / morse::kTpgMain;
+  long long groups =
+      morse::main_groups((long long)g->n_t0 * g->n_tE, first, count);
   long long want = (groups + morse::kSearchWarps - 1) / morse::kSearchWarps;
   int grid = (int)std::min<long long>((long long)bps * ctx->sm_count, want);
   if (grid < 1) grid = 1;
@@ -555,7 +557,8 @@ morse_status sweep_impl(morse_ctx *ctx, const morse_event *ev,
   morse_map *m = ctx->sweep_map;
   m->L = extent;
   Plan pl;
-  MORSE_TRY(plan_search(ctx, ev, grid, grid_size(grid), false, n_maps, &pl));
+  MORSE_TRY(plan_search(ctx, ev, grid, 0, grid_size(grid), false, n_maps,
+                        &pl));
   void *ws = nullptr;
   MORSE_TRY(ws_reserve(ctx, pl.bytes, &ws));
   char *base = (char *)ws;
@@ -570,7 +573,7 @@ morse_status sweep_impl(morse_ctx *ctx, const morse_event *ev,
   P.first = 0;
   P.count = grid_size(grid);
   P.stride = 1;
-  P.tpg = morse::kTpgMain;
+  morse::set_groups(&P);
   morse_fit *fits = (morse_fit *)(base + pl.off_out);
   MORSE_TRY(hdr_init(ctx, base, pl, &P));
   for (int i = 0; i < n_maps; ++i) {
@@ -903,7 +906,7 @@ morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
   MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
   call_begin(ctx);
   Plan pl;
-  MORSE_TRY(plan_search(ctx, ev, grid, grid_size(grid), false, 1, &pl));
+  MORSE_TRY(plan_search(ctx, ev, grid, 0, grid_size(grid), false, 1, &pl));
   void *ws = nullptr;
   MORSE_TRY(ws_reserve(ctx, pl.bytes, &ws));
   char *base = (char *)ws;
@@ -918,7 +921,7 @@ morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
   P.first = 0;
   P.count = grid_size(grid);
   P.stride = 1;
-  P.tpg = morse::kTpgMain;
+  morse::set_groups(&P);
   morse_fit *fits = (morse_fit *)(base + pl.off_out);
   MORSE_TRY(hdr_init(ctx, base, pl, &P));
   MORSE_TRY(enqueue_topk(ctx, pl, P, base, T, fits));
@@ -947,7 +950,7 @@ morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
   MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
   call_begin(ctx);
   Plan pl;
-  MORSE_TRY(plan_search(ctx, ev, grid, count, true, count, &pl));
+  MORSE_TRY(plan_search(ctx, ev, grid, first, count, true, count, &pl));
   void *ws = nullptr;
   MORSE_TRY(ws_reserve(ctx, pl.bytes, &ws));
   char *base = (char *)ws;
@@ -962,7 +965,7 @@ morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
   P.first = first;
   P.count = count;
   P.stride = 1;
-  P.tpg = morse::kTpgMain;
+  morse::set_groups(&P);
   P.top_k = 1;
   P.dchi2 = (double *)(base + pl.off_out);
   P.dFs = P.dchi2 + count;

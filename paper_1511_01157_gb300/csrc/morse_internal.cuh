@@ -124,6 +124,8 @@ struct SearchParams {
   long long first, count;   // trajectories first + i * stride, i < count
   long long stride;
   int tpg;                  // trajectories per warp group (1..32)
+  long long line;           // trajectories per (u0, alpha) line
+  long long ng_line;        // warp groups per line (main pass)
   int top_k;
   // outputs
   Entry *partial;           // [gridDim.x][top_k] (top-K mode)
@@ -152,9 +154,30 @@ constexpr int kSearchWarps = MORSE_SEARCH_WARPS;  // one block per SM
 #ifndef MORSE_TPG
 #define MORSE_TPG 32
 #endif
-constexpr int kTpgMain = MORSE_TPG;  // main pass
+constexpr int kTpgMain = MORSE_TPG;  // main pass, at most
 constexpr int kTpgPilot = 4;         // pilot: spread a small sample over
                                      // every SM
+
+// Line-aligned warp groups for the main pass: about one line per block
+// round (line = n_t0 n_tE trajectories share a track's line).
+inline int line_tpg(long long line) {
+  long long t = (line + kSearchWarps - 1) / kSearchWarps;
+  if (t > kTpgMain) t = kTpgMain;
+  if (t < 8) t = 8 < kTpgMain ? 8 : kTpgMain;
+  return (int)t;
+}
+inline void set_groups(SearchParams *P) {
+  P->line = (long long)P->n_t0 * P->n_tE;
+  P->tpg = line_tpg(P->line);
+  P->ng_line = (P->line + P->tpg - 1) / P->tpg;
+}
+// number of warp groups of the main pass over [first, first + count)
+inline long long main_groups(long long line, long long first,
+                             long long count) {
+  const int t = line_tpg(line);
+  const long long ng = (line + t - 1) / t;
+  return ((first + count - 1) / line - first / line + 1) * ng;
+}
 
 size_t search_smem_bytes(int n_ep_smem, int top_k);
 int search_blocks_per_sm(bool dense, bool ep_smem, size_t smem);

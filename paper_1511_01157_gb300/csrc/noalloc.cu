@@ -106,7 +106,8 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   const int bps = morse::search_blocks_per_sm(false, ep_smem, smem);
   if (bps < 1)
     return set_err(ctx, MORSE_EUNSUPPORTED, "search kernel does not fit");
-  long long groups = (count + morse::kTpgMain - 1) / morse::kTpgMain;
+  long long groups =
+      morse::main_groups((long long)g->n_t0 * g->n_tE, 0, count);
   long long want = (groups + morse::kSearchWarps - 1) / morse::kSearchWarps;
   int grid = (int)std::min<long long>((long long)bps * ctx->sm_count, want);
   if (grid < 1) grid = 1;
@@ -214,7 +215,7 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   P.first = 0;
   P.count = count;
   P.stride = 1;
-  P.tpg = morse::kTpgMain;
+  morse::set_groups(&P);
   P.partial = (morse::Entry *)(base + off_a);
   // status words: the grid-wide pruning threshold (all-ones = +inf) and the
   // error word of the block locks
