@@ -148,7 +148,7 @@ struct FillParams {
 };
 
 #ifndef MORSE_SEARCH_WARPS
-#define MORSE_SEARCH_WARPS 32
+#define MORSE_SEARCH_WARPS 16
 #endif
 constexpr int kSearchWarps = MORSE_SEARCH_WARPS;  // one block per SM
 #ifndef MORSE_TPG
