@@ -214,54 +214,121 @@ __device__ __forceinline__ float bilinear_m1(const SearchParams &P, float vx,
   return __fmaf_rn(fy, __fsub_rn(r1, r0), r0);
 }
 
-// Phase 1: per-lane FP32 sums of S_A = sum w (A-1), S_AA = sum w (A-1)^2,
-// S_AF = sum w (F-Fref)(A-1) over the three epoch ranges (each lane-strided
-// from its start), then an xor butterfly; lane 0's value goes to all lanes
-// so that every caller sees the same rounding.
-__device__ __forceinline__ void phase1(const SearchParams &P,
-                                       const float4 *ep, const TrajC &c,
-                                       const int lane, float &oA, float &oAA,
-                                       float &oAF) {
-  float a = 0.f, b = 0.f, d = 0.f;
-#pragma unroll 2
-  for (int e = lane; e < c.e_in; e += 32) {
+// Lanes own epochs by index mod 32 in every range, so a lane always sums
+// its terms in ascending epoch order whatever the ranges are: the sums of a
+// trajectory do not depend on how its epoch axis is cut into segments (the
+// search pairs trajectories, the fit fill does not; both get the same
+// rounding).
+__device__ __forceinline__ int lane_start(int e0, int lane) {
+  return e0 + ((lane - e0) & 31);
+}
+
+struct Acc {
+  float a, b, d;  // S_A, S_AA, S_AF partial sums of one lane
+};
+
+__device__ __forceinline__ void acc_add(Acc &s, const float4 &v, float Ac) {
+  const float wAc = __fmul_rn(v.y, Ac);
+  s.a = __fadd_rn(s.a, wAc);
+  s.b = __fmaf_rn(wAc, Ac, s.b);
+  s.d = __fmaf_rn(v.z, Ac, s.d);
+}
+
+// A - 1 at time t inside the map (bilinear) or outside (single lens)
+__device__ __forceinline__ float mag_in_m1(const SearchParams &P,
+                                           const TrajC &c, float t) {
+  return bilinear_m1(P, __fmaf_rn(c.ax, t, c.bx), __fmaf_rn(c.ay, t, c.by));
+}
+__device__ __forceinline__ float mag_out_m1(const TrajC &c, float t) {
+  const float tau = __fmaf_rn(c.kt, t, c.bt);
+  return __fsub_rn(pspl_u2(__fmaf_rn(tau, tau, c.u02)), 1.f);
+}
+
+template <bool IN>
+__device__ __forceinline__ void seg1(const SearchParams &P, const float4 *ep,
+                                     const TrajC &c, int lane, int e0, int e1,
+                                     Acc &s) {
+#pragma unroll (IN ? kUnroll : 2)
+  for (int e = lane_start(e0, lane); e < e1; e += 32) {
     const float4 v = ep[e];
-    const float tau = __fmaf_rn(c.kt, v.x, c.bt);
-    const float Ac = __fsub_rn(pspl_u2(__fmaf_rn(tau, tau, c.u02)), 1.f);
-    const float wAc = __fmul_rn(v.y, Ac);
-    a = __fadd_rn(a, wAc);
-    b = __fmaf_rn(wAc, Ac, b);
-    d = __fmaf_rn(v.z, Ac, d);
+    acc_add(s, v, IN ? mag_in_m1(P, c, v.x) : mag_out_m1(c, v.x));
   }
-#pragma unroll (kUnroll)
-  for (int e = c.e_in + lane; e < c.e_out; e += 32) {
+}
+
+// two trajectories over one epoch segment, one epoch load for both
+template <bool INA, bool INB>
+__device__ __forceinline__ void seg2(const SearchParams &P, const float4 *ep,
+                                     const TrajC &ca, const TrajC &cb,
+                                     int lane, int e0, int e1, Acc &sa,
+                                     Acc &sb) {
+#pragma unroll ((INA || INB) ? kUnroll : 2)
+  for (int e = lane_start(e0, lane); e < e1; e += 32) {
     const float4 v = ep[e];
-    const float Ac = bilinear_m1(P, __fmaf_rn(c.ax, v.x, c.bx),
-                                 __fmaf_rn(c.ay, v.x, c.by));
-    const float wAc = __fmul_rn(v.y, Ac);
-    a = __fadd_rn(a, wAc);
-    b = __fmaf_rn(wAc, Ac, b);
-    d = __fmaf_rn(v.z, Ac, d);
+    acc_add(sa, v, INA ? mag_in_m1(P, ca, v.x) : mag_out_m1(ca, v.x));
+    acc_add(sb, v, INB ? mag_in_m1(P, cb, v.x) : mag_out_m1(cb, v.x));
   }
-#pragma unroll 2
-  for (int e = c.e_out + lane; e < P.n_ep; e += 32) {
-    const float4 v = ep[e];
-    const float tau = __fmaf_rn(c.kt, v.x, c.bt);
-    const float Ac = __fsub_rn(pspl_u2(__fmaf_rn(tau, tau, c.u02)), 1.f);
-    const float wAc = __fmul_rn(v.y, Ac);
-    a = __fadd_rn(a, wAc);
-    b = __fmaf_rn(wAc, Ac, b);
-    d = __fmaf_rn(v.z, Ac, d);
-  }
+}
+
+// xor butterfly; lane 0's totals go to every lane
+__device__ __forceinline__ Acc acc_reduce(Acc s) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
-    a = __fadd_rn(a, __shfl_xor_sync(kFull, a, o));
-    b = __fadd_rn(b, __shfl_xor_sync(kFull, b, o));
-    d = __fadd_rn(d, __shfl_xor_sync(kFull, d, o));
+    s.a = __fadd_rn(s.a, __shfl_xor_sync(kFull, s.a, o));
+    s.b = __fadd_rn(s.b, __shfl_xor_sync(kFull, s.b, o));
+    s.d = __fadd_rn(s.d, __shfl_xor_sync(kFull, s.d, o));
   }
-  oA = __shfl_sync(kFull, a, 0);
-  oAA = __shfl_sync(kFull, b, 0);
-  oAF = __shfl_sync(kFull, d, 0);
+  Acc r;
+  r.a = __shfl_sync(kFull, s.a, 0);
+  r.b = __shfl_sync(kFull, s.b, 0);
+  r.d = __shfl_sync(kFull, s.d, 0);
+  return r;
+}
+
+// Phase 1: FP32 sums of S_A = sum w (A-1), S_AA = sum w (A-1)^2 and
+// S_AF = sum w (F-Fref)(A-1) over the epochs before, inside and after the
+// map, reduced across the warp.
+__device__ __forceinline__ Acc phase1(const SearchParams &P, const float4 *ep,
+                                      const TrajC &c, const int lane) {
+  Acc s = {0.f, 0.f, 0.f};
+  seg1<false>(P, ep, c, lane, 0, c.e_in, s);
+  seg1<true>(P, ep, c, lane, c.e_in, c.e_out, s);
+  seg1<false>(P, ep, c, lane, c.e_out, P.n_ep, s);
+  return acc_reduce(s);
+}
+
+// Phase 1 of two trajectories at once: the epoch axis is cut at both
+// trajectories' map entry and exit, and each segment runs the matching
+// inside/outside combination with one epoch load per lane for both.
+__device__ __forceinline__ void phase1_pair(const SearchParams &P,
+                                            const float4 *ep, const TrajC &ca,
+                                            const TrajC &cb, const int lane,
+                                            Acc &ra, Acc &rb) {
+  Acc sa = {0.f, 0.f, 0.f}, sb = {0.f, 0.f, 0.f};
+  // cut points, sorted (warp-uniform)
+  int p1 = ca.e_in, p2 = ca.e_out, p3 = cb.e_in, p4 = cb.e_out, t;
+  if (p1 > p2) { t = p1; p1 = p2; p2 = t; }
+  if (p3 > p4) { t = p3; p3 = p4; p4 = t; }
+  if (p1 > p3) { t = p1; p1 = p3; p3 = t; }
+  if (p2 > p4) { t = p2; p2 = p4; p4 = t; }
+  if (p2 > p3) { t = p2; p2 = p3; p3 = t; }
+  const int cut[6] = {0, p1, p2, p3, p4, P.n_ep};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int e0 = cut[i], e1 = cut[i + 1];
+    if (e0 >= e1) continue;
+    const bool ina = e0 >= ca.e_in && e1 <= ca.e_out;
+    const bool inb = e0 >= cb.e_in && e1 <= cb.e_out;
+    if (ina && inb)
+      seg2<true, true>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+    else if (ina)
+      seg2<true, false>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+    else if (inb)
+      seg2<false, true>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+    else
+      seg2<false, false>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+  }
+  ra = acc_reduce(sa);
+  rb = acc_reduce(sb);
 }
 
 // Phase 2: chi^2 = sum w (F - Fs A - Fb)^2, written with centred values as
@@ -273,26 +340,23 @@ __device__ __forceinline__ double phase2(const SearchParams &P,
                                          const float Bc) {
   float chi = 0.f;
 #pragma unroll 2
-  for (int e = lane; e < c.e_in; e += 32) {
+  for (int e = lane_start(0, lane); e < c.e_in; e += 32) {
     const float4 v = ep[e];
-    const float tau = __fmaf_rn(c.kt, v.x, c.bt);
-    const float Ac = __fsub_rn(pspl_u2(__fmaf_rn(tau, tau, c.u02)), 1.f);
+    const float Ac = mag_out_m1(c, v.x);
     const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
     chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
   }
 #pragma unroll (kUnroll)
-  for (int e = c.e_in + lane; e < c.e_out; e += 32) {
+  for (int e = lane_start(c.e_in, lane); e < c.e_out; e += 32) {
     const float4 v = ep[e];
-    const float Ac = bilinear_m1(P, __fmaf_rn(c.ax, v.x, c.bx),
-                                 __fmaf_rn(c.ay, v.x, c.by));
+    const float Ac = mag_in_m1(P, c, v.x);
     const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
     chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
   }
 #pragma unroll 2
-  for (int e = c.e_out + lane; e < P.n_ep; e += 32) {
+  for (int e = lane_start(c.e_out, lane); e < P.n_ep; e += 32) {
     const float4 v = ep[e];
-    const float tau = __fmaf_rn(c.kt, v.x, c.bt);
-    const float Ac = __fsub_rn(pspl_u2(__fmaf_rn(tau, tau, c.u02)), 1.f);
+    const float Ac = mag_out_m1(c, v.x);
     const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
     chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
   }
@@ -533,18 +597,22 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
     const long long my = lined ? lo + ml : P.first + (lo + ml) * P.stride;
     const long long out_off = lined ? lo - P.first : lo;  // dense output
     const TrajC mine = traj_consts(P, ep, my);
-    float mA = 0.f, mAA = 0.f, mAF = 0.f;
-    for (int k = 0; k < nvalid; ++k) {
-      const TrajC c = shfl_traj(mine, k);
-      float sA, sAA, sAF;
-      phase1(P, ep, c, lane, sA, sAA, sAF);
-      if (lane == k) {
-        mA = sA;
-        mAA = sAA;
-        mAF = sAF;
+    Acc mine_s = {0.f, 0.f, 0.f};
+    for (int k = 0; k < nvalid; k += 2) {
+      const TrajC ca = shfl_traj(mine, k);
+      if (k + 1 < nvalid) {
+        const TrajC cb = shfl_traj(mine, k + 1);
+        Acc ra, rb;
+        phase1_pair(P, ep, ca, cb, lane, ra, rb);
+        if (lane == k) mine_s = ra;
+        if (lane == k + 1) mine_s = rb;
+      } else {
+        const Acc ra = phase1(P, ep, ca, lane);
+        if (lane == k) mine_s = ra;
       }
     }
-    const Solved sol = solve2(P, (double)mA, (double)mAA, (double)mAF);
+    const Solved sol =
+        solve2(P, (double)mine_s.a, (double)mine_s.b, (double)mine_s.d);
     double thr = CUDART_INF;
     if (!DENSE) {
       thr = *T.thr;
@@ -655,9 +723,8 @@ __global__ void k_fill(const FillParams F) {
     return;
   }
   const TrajC c = traj_consts(P, P.ep, e.idx);
-  float sA, sAA, sAF;
-  phase1(P, P.ep, c, lane, sA, sAA, sAF);
-  const Solved sol = solve2(P, (double)sA, (double)sAA, (double)sAF);
+  const Acc s = phase1(P, P.ep, c, lane);
+  const Solved sol = solve2(P, (double)s.a, (double)s.b, (double)s.d);
   const double chi2 = phase2(P, P.ep, c, lane, __double2float_rn(sol.Fs),
                              __double2float_rn(sol.Bc));
   if (lane == 0) {
