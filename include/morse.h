@@ -163,7 +163,10 @@ typedef struct {
   int top_k;
 } morse_grid;
 
-enum { MORSE_FIT_DEGENERATE = 1 }; /* A constant along the track: Fs = 0 */
+enum {
+  MORSE_FIT_DEGENERATE = 1, /* A constant along the track: Fs = 0          */
+  MORSE_FIT_REFINED = 2     /* parameters from morse_refine, off the grid   */
+};
 
 /* One fitted trajectory.  chi2 = sum_i w_i (F_i - Fs A_i - Fb)^2 with
  * (Fs, Fb) the weighted least-squares solution of Eq. 6. */
@@ -263,6 +266,47 @@ morse_status morse_lightcurve(morse_ctx *ctx, const morse_map *map,
                               double t0, double tE, double u0, double alpha,
                               const double *t, int64_t n, double *A_out);
 
+/* ------------------------------------------------------------------ */
+/* Gradient and refinement of trajectories (seeds of §4.4 refined as §5  */
+/* does, here on the same point-source map)                             */
+/* ------------------------------------------------------------------ */
+
+/* chi^2 of n trajectories theta[4 i + (0..3)] = (t0, tE, u0, alpha) (t0
+ * absolute, tE > 0) on the map, with (Fs, Fb) profiled out by the 2x2 solve
+ * of Eq. 6, and its gradient with respect to theta.  Because (Fs, Fb)
+ * minimise chi^2 at every theta, d chi^2/d theta_k = sum_i -2 w_i r_i Fs
+ * dA_i/d theta_k, with dA/d theta through the bilinear lookup (inside the
+ * map) or the single-lens formula (outside).  The bilinear gradient is
+ * piecewise: it jumps where a data point crosses a texel edge.  Host
+ * arrays: chi2[n]; grad[4 n], Fs[n], Fb[n] may be NULL.
+ * Errors: EINVAL (n < 0, non-finite theta, tE <= 0), ENOMEM, ECUDA. */
+morse_status morse_chi2_grad(morse_ctx *ctx, const morse_event *ev,
+                             const morse_map *map, const double *theta,
+                             int64_t n, double *chi2, double *grad,
+                             double *Fs, double *Fb);
+
+/* morse_chi2_grad on DEVICE arrays (theta [4 n], chi2 [n], grad [4 n] or
+ * NULL), queued on the context stream without host synchronisation (for
+ * autograd and other device-side drivers).  theta is not validated on the
+ * host: tE is floored at 1e-6 in the kernel.  Errors: EINVAL, ECUDA. */
+morse_status morse_chi2_grad_dev(morse_ctx *ctx, const morse_event *ev,
+                                 const morse_map *map, const double *theta,
+                                 int64_t n, double *chi2, double *grad);
+
+enum { MORSE_REFINE_LM = 0 };
+
+/* Refine n starting trajectories (e.g. grid top-K records) by batched
+ * Levenberg-Marquardt on chi^2(theta): each iteration evaluates chi^2, its
+ * gradient and the Gauss-Newton matrix sum w Fs^2 dA/dtheta dA/dtheta^T,
+ * accepts the point if chi^2 fell, and steps by (H + lam diag H)^-1 g.
+ * One iteration is captured as a CUDA graph and replayed iters times.
+ * out[n] (host) receives the best point of each, its chi^2, Fs, Fb, the
+ * start's idx and MORSE_FIT_REFINED.  chi^2 never increases from the start.
+ * method: MORSE_REFINE_LM.  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA. */
+morse_status morse_refine(morse_ctx *ctx, const morse_event *ev,
+                          const morse_map *map, const morse_fit *starts,
+                          int n, int iters, int method, morse_fit *out);
+
 /* Merge n_lists top-K lists (each ascending by (chi2, idx), counts[i]
  * entries, entries with idx < 0 ignored) into the k best, ascending, in
  * out[k] (tail padded with idx = -1, chi2 = +inf).  Host-only; used to
@@ -275,7 +319,8 @@ morse_status morse_topk_merge(const morse_fit *const *lists,
 /* Device time of the kernels of the most recent call on this context, in
  * milliseconds (CUDA events on the context stream), summed over every
  * launch of that kind in the call: which = 0 ray shooting, 1 counts-to-map,
- * 2 grid search, 3 top-K merge, 4 fit fill; 5..7 reserved (0). */
+ * 2 grid search, 3 top-K merge, 4 fit fill, 5 adjoint evaluations, 6
+ * refine steps; 7 reserved (0). */
 morse_status morse_last_kernel_ms(const morse_ctx *ctx, int which,
                                   double *ms);
 

@@ -18,6 +18,7 @@ names the passage of McDougall & Albrow (2015) it follows:
 * ``fit_A``           -- §4.1 Eq. 5-6 linear flux fit, chi^2 as a sum of
   per-point contributions (§4.2)
 * ``grid_chi2``/``topk`` -- brute-force grid and the K best seeds (§4.4)
+* ``chi2_theta``      -- chi^2 at an arbitrary trajectory (map or polynomial)
 """
 from __future__ import annotations
 
@@ -80,6 +81,8 @@ def _load():
                                ctypes.c_long, _P, _I, _I, _P, _I, _P, _I,
                                _LL, _LL, _P, _P, _P, _P, _I]),
         "orc_topk": (_I, [_P, _LL, _LL, _I, _P, _P]),
+        "orc_chi2_theta": (_D, [_P, _I, _D, _D, _D, _I, _P, _P, _P,
+                                ctypes.c_long, _D, _D, _D, _D, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -297,6 +300,29 @@ def grid_chi2(grid: Grid, t, F, w, A=None, L=None, s=None, q=None, first=0,
     if rc < 0:
         raise ValueError("orc_grid_chi2 rejected its arguments")
     return chi2, fs, fb, fl
+
+
+def chi2_theta(t, F, w, theta, A=None, L=None, s=None, q=None):
+    """chi^2 of one trajectory theta = (t0, tE, u0, alpha) on the map A
+    (half-width L) or, when A is None, on the polynomial magnification of
+    (s, q); returns (chi2, Fs, Fb)."""
+    t = _f64(t)
+    F = _f64(F)
+    w = _f64(w)
+    fs = ctypes.c_double()
+    fb = ctypes.c_double()
+    if A is not None:
+        A = np.ascontiguousarray(A, dtype=np.float32)
+        c = _load().orc_chi2_theta(_ptr(A), A.shape[0], float(L), 0.0, 0.0,
+                                   0, _ptr(t), _ptr(F), _ptr(w), len(t),
+                                   *[float(x) for x in theta],
+                                   ctypes.byref(fs), ctypes.byref(fb))
+    else:
+        c = _load().orc_chi2_theta(None, 0, 0.0, float(s), float(q), 1,
+                                   _ptr(t), _ptr(F), _ptr(w), len(t),
+                                   *[float(x) for x in theta],
+                                   ctypes.byref(fs), ctypes.byref(fb))
+    return c, fs.value, fb.value
 
 
 def topk(chi2, k, first=0):

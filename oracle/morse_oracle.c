@@ -482,6 +482,26 @@ double orc_fit_A(const double *A, const double *F, const double *w, long n,
   return chi2;
 }
 
+/* chi^2 (and the fitted Fs, Fb) of one trajectory at arbitrary
+ * (t0, tE, u0, alpha): magnifications from the map (mode 0) or from the
+ * point-source polynomial (mode 1), then the linear fit of Eq. 6. */
+double orc_chi2_theta(const float *Amap, int npix, double L, double s,
+                      double q, int mode, const double *t, const double *F,
+                      const double *w, long n, double t0, double tE, double u0,
+                      double alpha, double *Fs, double *Fb) {
+  double *A = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+  for (long i = 0; i < n; ++i) {
+    double y1, y2;
+    orc_traj_point(t[i], t0, tE, u0, alpha, &y1, &y2);
+    A[i] = (mode == 0) ? orc_map_A(Amap, npix, L, y1, y2)
+                       : orc_mag_point(s, q, y1, y2, NULL);
+  }
+  int fl;
+  double c = orc_fit_A(A, F, w, n, Fs, Fb, &fl);
+  free(A);
+  return c;
+}
+
 /* Grid axis values: linear lo + (hi-lo) i/(n-1), or logarithmic
  * lo (hi/lo)^(i/(n-1)); n == 1 gives lo. */
 void orc_axis(double lo, double hi, int n, int logsp, double *out) {

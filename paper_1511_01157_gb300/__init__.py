@@ -40,7 +40,8 @@ _lib = ctypes.CDLL(LIB_PATH)
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEGENERATE, EUNSUPPORTED = range(7)
 DEFLECT_FP64, DEFLECT_FP32 = 0, 1
 STORE_FP32, STORE_FP16LOG = 1, 2
-FIT_DEGENERATE = 1
+FIT_DEGENERATE, FIT_REFINED = 1, 2
+REFINE_LM = 0
 
 
 class MorseError(RuntimeError):
@@ -121,6 +122,9 @@ _SIGS = {
                                 _I64, _P, _P, _P]),
     "morse_lightcurve": (_S, [_P, _P, _D, _D, _D, _D, _P, _I64, _P]),
     "morse_topk_merge": (_S, [_P, _P, _I, _I, _P]),
+    "morse_chi2_grad": (_S, [_P, _P, _P, _P, _I64, _P, _P, _P, _P]),
+    "morse_chi2_grad_dev": (_S, [_P, _P, _P, _P, _I64, _P, _P]),
+    "morse_refine": (_S, [_P, _P, _P, _P, _I, _I, _I, _P]),
     "morse_last_kernel_ms": (_S, [_P, _I, _P]),
     "morse_launch_count": (_S, [_P, _P]),
     "morse_last_search_stats": (_S, [_P, _P]),
@@ -319,6 +323,45 @@ class Context:
         self._check(st, "morse_search_sweep")
         return out
 
+    # ------------------------------------------------------------ gradient
+    def chi2_grad(self, event, map_, theta):
+        """chi^2, d chi^2/d(t0, tE, u0, alpha), Fs, Fb of trajectories
+        theta[n, 4] (morse_chi2_grad)."""
+        th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1, 4)
+        n = th.shape[0]
+        chi2 = np.zeros(n)
+        grad = np.zeros((n, 4))
+        fs = np.zeros(n)
+        fb = np.zeros(n)
+        st = _lib.morse_chi2_grad(self._h, event._h, map_._h, _ptr(th), n,
+                                  _ptr(chi2), _ptr(grad), _ptr(fs), _ptr(fb))
+        self._check(st, "morse_chi2_grad")
+        return chi2, grad, fs, fb
+
+    def chi2_grad_dev(self, event, map_, theta, chi2, grad=None):
+        """Device version on torch float64 CUDA tensors (theta [n, 4],
+        chi2 [n], grad [n, 4] or None), queued on the context's stream."""
+        for x in (theta, chi2) + ((grad,) if grad is not None else ()):
+            if not (x.is_cuda and x.is_contiguous()) or str(x.dtype) != \
+                    "torch.float64":
+                raise ValueError("contiguous float64 CUDA tensors expected")
+        n = theta.shape[0]
+        st = _lib.morse_chi2_grad_dev(
+            self._h, event._h, map_._h, ctypes.c_void_p(theta.data_ptr()), n,
+            ctypes.c_void_p(chi2.data_ptr()),
+            ctypes.c_void_p(grad.data_ptr()) if grad is not None else None)
+        self._check(st, "morse_chi2_grad_dev")
+
+    def refine(self, event, map_, starts, iters=50, method=REFINE_LM):
+        """Batched Levenberg-Marquardt refinement of fit records
+        (morse_refine)."""
+        st_ = np.ascontiguousarray(starts, dtype=FIT_DTYPE)
+        out = np.zeros(len(st_), dtype=FIT_DTYPE)
+        st = _lib.morse_refine(self._h, event._h, map_._h, _ptr(st_),
+                               len(st_), int(iters), int(method), _ptr(out))
+        self._check(st, "morse_refine")
+        return out
+
     def lightcurve(self, map_, t0, tE, u0, alpha, t):
         t = _f64(t)
         out = np.zeros(len(t))
@@ -409,6 +452,41 @@ class Event:
             pass
 
 
+def chi2_function():
+    """torch.autograd.Function computing chi^2(theta) per trajectory with
+    the adjoint gradient (morse_chi2_grad_dev).  Usage:
+        Chi2 = chi2_function(); chi2 = Chi2.apply(theta, ctx, event, map)
+    theta: float64 CUDA tensor [n, 4] (t0, tE, u0, alpha)."""
+    import torch
+
+    class Chi2(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, theta, mctx, event, map_):
+            theta = theta.detach().contiguous()
+            chi2 = torch.empty(theta.shape[0], dtype=torch.float64,
+                               device=theta.device)
+            grad = torch.empty_like(theta)
+            # order the library's stream after the producer of theta
+            cur = torch.cuda.current_stream(theta.device)
+            lib_stream = getattr(mctx, "_stream_ref", None)
+            if lib_stream is not None:
+                lib_stream.wait_stream(cur)
+            mctx.chi2_grad_dev(event, map_, theta, chi2, grad)
+            if lib_stream is not None:
+                cur.wait_stream(lib_stream)
+            else:
+                torch.cuda.synchronize(theta.device)
+            fctx.save_for_backward(grad)
+            return chi2
+
+        @staticmethod
+        def backward(fctx, gout):
+            (grad,) = fctx.saved_tensors
+            return gout[:, None] * grad, None, None, None
+
+    return Chi2
+
+
 def topk_merge(lists, k):
     """Merge sorted top-K lists (FIT_DTYPE arrays) on the host."""
     arrs = [np.ascontiguousarray(a, dtype=FIT_DTYPE) for a in lists]
@@ -423,4 +501,5 @@ def topk_merge(lists, k):
 
 
 __all__ = ["Context", "Map", "Event", "Grid", "Fit", "FIT_DTYPE", "MapOpts",
-           "MorseError", "topk_merge", "version", "LIB_PATH", "EXPORTED"]
+           "MorseError", "topk_merge", "chi2_function", "version",
+           "LIB_PATH", "EXPORTED"]

@@ -341,6 +341,7 @@ void map_params(const morse_map *map, morse::SearchParams *P) {
   P->coff = 0.5 * map->npix - (double)(map->npix / 2) - 0.5;
   P->voff = (float)(-P->coff);
   P->dltf = (float)dlt;
+  P->invDf = (float)(1.0 / dlt);
   P->invD = 1.0 / dlt;
 }
 
@@ -1072,6 +1073,182 @@ morse_status morse_lightcurve(morse_ctx *ctx, const morse_map *map,
   MORSE_TRY(sync_and_collect(ctx, "light curve"));
   for (int64_t i = 0; i < n; ++i) A_out[i] = hA[(size_t)i];
   return MORSE_OK;
+}
+
+// ------------------------------------------------------------------ refine
+static morse_status check_theta(morse_ctx *ctx, const double *theta,
+                                int64_t n) {
+  for (int64_t i = 0; i < n; ++i) {
+    for (int k = 0; k < 4; ++k)
+      if (!is_fin(theta[4 * i + k]))
+        return fail(ctx, MORSE_EINVAL, "theta[%lld] is not finite",
+                    (long long)i);
+    if (!(theta[4 * i + 1] > 0.0))
+      return fail(ctx, MORSE_EINVAL, "theta[%lld]: tE must be > 0",
+                  (long long)i);
+  }
+  return MORSE_OK;
+}
+
+morse_status morse_chi2_grad_dev(morse_ctx *ctx, const morse_event *ev,
+                                 const morse_map *map, const double *theta,
+                                 int64_t n, double *chi2, double *grad) {
+  if (!ctx) return MORSE_EINVAL;
+  MORSE_TRY(check_pair(ctx, ev, map));
+  if (n < 0 || n > 0x7fffffffLL)
+    return fail(ctx, MORSE_EINVAL, "n out of range");
+  if (n == 0) return MORSE_OK;
+  if (!theta || !chi2) return fail(ctx, MORSE_EINVAL, "NULL device array");
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  morse::SearchParams P;
+  memset(&P, 0, sizeof(P));
+  map_params(map, &P);
+  event_params(ev, &P);
+  MORSE_CUDA(ctx, morse::launch_theta(P, theta, (int)n, ev->t_ref, chi2,
+                                      grad, nullptr, nullptr, nullptr,
+                                      nullptr, ctx->stream));
+  ctx->launches += 1;
+  return MORSE_OK;
+}
+
+morse_status morse_chi2_grad(morse_ctx *ctx, const morse_event *ev,
+                             const morse_map *map, const double *theta,
+                             int64_t n, double *chi2, double *grad,
+                             double *Fs, double *Fb) {
+  if (!ctx) return MORSE_EINVAL;
+  MORSE_TRY(check_pair(ctx, ev, map));
+  if (n < 0 || n > 0x7fffffffLL)
+    return fail(ctx, MORSE_EINVAL, "n out of range");
+  if (n == 0) return MORSE_OK;
+  if (!theta || !chi2) return fail(ctx, MORSE_EINVAL, "NULL array");
+  MORSE_TRY(check_theta(ctx, theta, n));
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  call_begin(ctx);
+  // workspace: theta | chi2 | grad | Fs | Fb
+  const size_t nn = (size_t)n;
+  void *ws = nullptr;
+  MORSE_TRY(ws_reserve(ctx, sizeof(double) * nn * 11 + 1024, &ws));
+  double *d_th = (double *)ws, *d_c = d_th + 4 * nn, *d_g = d_c + nn;
+  double *d_fs = d_g + 4 * nn, *d_fb = d_fs + nn;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(d_th, theta, sizeof(double) * 4 * nn,
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  morse::SearchParams P;
+  memset(&P, 0, sizeof(P));
+  map_params(map, &P);
+  event_params(ev, &P);
+  int r = t_begin(ctx, KT_ADJ);
+  MORSE_CUDA(ctx, morse::launch_theta(P, d_th, (int)n, ev->t_ref, d_c, d_g,
+                                      nullptr, d_fs, d_fb, nullptr,
+                                      ctx->stream));
+  t_end(ctx, r);
+  ctx->launches += 1;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(chi2, d_c, sizeof(double) * nn,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  if (grad)
+    MORSE_CUDA(ctx, cudaMemcpyAsync(grad, d_g, sizeof(double) * 4 * nn,
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+  if (Fs)
+    MORSE_CUDA(ctx, cudaMemcpyAsync(Fs, d_fs, sizeof(double) * nn,
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+  if (Fb)
+    MORSE_CUDA(ctx, cudaMemcpyAsync(Fb, d_fb, sizeof(double) * nn,
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+  return sync_and_collect(ctx, "chi2 gradient");
+}
+
+morse_status morse_refine(morse_ctx *ctx, const morse_event *ev,
+                          const morse_map *map, const morse_fit *starts,
+                          int n, int iters, int method, morse_fit *out) {
+  if (!ctx) return MORSE_EINVAL;
+  MORSE_TRY(check_pair(ctx, ev, map));
+  if (method != MORSE_REFINE_LM)
+    return fail(ctx, MORSE_EUNSUPPORTED, "refine method %d", method);
+  if (n < 0 || iters < 0 || iters > 100000)
+    return fail(ctx, MORSE_EINVAL, "n or iters out of range");
+  if (n == 0) return MORSE_OK;
+  if (!starts || !out) return fail(ctx, MORSE_EINVAL, "NULL array");
+  for (int i = 0; i < n; ++i) {
+    const double th[4] = {starts[i].t0, starts[i].tE, starts[i].u0,
+                          starts[i].alpha};
+    MORSE_TRY(check_theta(ctx, th, 1));
+  }
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  call_begin(ctx);
+  const size_t nn = (size_t)n;
+  // workspace: 36 doubles + 1 int per trajectory, starts, records
+  const size_t dbl = nn * 36, bytes = sizeof(double) * dbl + sizeof(int) * nn +
+                                      2 * sizeof(morse_fit) * nn + 4096;
+  void *ws = nullptr;
+  MORSE_TRY(ws_reserve(ctx, bytes, &ws));
+  double *d = (double *)ws;
+  morse::RefineState S;
+  S.th_cur = d;
+  S.th_best = S.th_cur + 4 * nn;
+  S.chi2_cur = S.th_best + 4 * nn;
+  S.chi2_best = S.chi2_cur + nn;
+  S.lam = S.chi2_best + nn;
+  S.g_cur = S.lam + nn;
+  S.g_best = S.g_cur + 4 * nn;
+  S.H_cur = S.g_best + 4 * nn;
+  S.H_best = S.H_cur + 10 * nn;
+  S.Fs = S.H_best + 10 * nn;
+  S.Fb = S.Fs + nn;
+  S.flags = (int *)(S.Fb + nn);
+  morse_fit *d_starts = (morse_fit *)align_up(
+      (size_t)(S.flags + nn), alignof(morse_fit));
+  morse_fit *d_out = d_starts + nn;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(d_starts, starts, sizeof(morse_fit) * nn,
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  morse::SearchParams P;
+  memset(&P, 0, sizeof(P));
+  map_params(map, &P);
+  event_params(ev, &P);
+  MORSE_CUDA(ctx, morse::launch_lm_init(S, d_starts, n, 1e-3, ctx->stream));
+  ctx->launches += 1;
+  if (iters > 0) {
+    // one iteration (evaluate at theta_cur, then step) as a CUDA graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    MORSE_CUDA(ctx, cudaStreamBeginCapture(ctx->stream,
+                                           cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = morse::launch_theta(P, S.th_cur, n, ev->t_ref,
+                                         S.chi2_cur, S.g_cur, S.H_cur,
+                                         nullptr, nullptr, nullptr,
+                                         ctx->stream);
+    cudaError_t e2 = morse::launch_lm_step(S, n, ctx->stream);
+    cudaError_t e3 = cudaStreamEndCapture(ctx->stream, &graph);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(ctx, e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3),
+                       "refine graph capture");
+    }
+    cudaError_t e4 = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e4 != cudaSuccess) return cuda_fail(ctx, e4, "refine graph");
+    int r = t_begin(ctx, KT_LM);
+    for (int it = 0; it < iters; ++it) {
+      cudaError_t e = cudaGraphLaunch(exec, ctx->stream);
+      if (e != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        return cuda_fail(ctx, e, "refine graph launch");
+      }
+    }
+    t_end(ctx, r);
+    ctx->launches += 2 * (uint64_t)iters;
+    MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaGraphExecDestroy(exec);
+  }
+  // evaluate at the best point (the start if no iteration improved on it)
+  int r = t_begin(ctx, KT_ADJ);
+  MORSE_CUDA(ctx, morse::launch_theta(P, S.th_best, n, ev->t_ref, S.chi2_cur,
+                                      nullptr, nullptr, S.Fs, S.Fb, S.flags,
+                                      ctx->stream));
+  t_end(ctx, r);
+  MORSE_CUDA(ctx, morse::launch_lm_finish(S, d_starts, n, d_out, ctx->stream));
+  ctx->launches += 2;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(out, d_out, sizeof(morse_fit) * nn,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  return sync_and_collect(ctx, "refine");
 }
 
 morse_status morse_topk_merge(const morse_fit *const *lists,

@@ -11,7 +11,7 @@
 
 // kernel kinds timed per call (morse_last_kernel_ms)
 enum { KT_RAY = 0, KT_MAP = 1, KT_SEARCH = 2, KT_MERGE = 3, KT_FILL = 4,
-       KT_COUNT = 8 };
+       KT_ADJ = 5, KT_LM = 6, KT_COUNT = 8 };
 
 struct morse_ctx {
   int device;
@@ -110,6 +110,7 @@ struct SearchParams {
   float vmax;               // npix - npix/2 - 1: centre of the last texel
   float voff;               // -coff: y = (v + voff) Delta
   float dltf;               // Delta
+  float invDf;              // 1/Delta
   double invD;              // 1/Delta
   double coff;              // v = y/Delta + coff
   double L, dlt;            // map half-width, Delta (FP64)
@@ -191,6 +192,26 @@ cudaError_t launch_fill(const FillParams &F, cudaStream_t st);
 // gthr <- min(gthr, chi^2 bits of sel[k-1]) when that entry is real
 cudaError_t launch_seed_threshold(const Entry *sel, int k,
                                   unsigned long long *gthr, cudaStream_t st);
+// ---------------------------------------------------------------- refine
+struct RefineState {
+  double *th_cur, *th_best;        // [4 n] (t0, tE, u0, alpha)
+  double *chi2_cur, *chi2_best;    // [n]
+  double *lam;                     // [n] damping
+  double *g_cur, *g_best;          // [4 n]
+  double *H_cur, *H_best;          // [10 n] upper triangles
+  double *Fs, *Fb;                 // [n]
+  int *flags;                      // [n]
+};
+
+cudaError_t launch_theta(const SearchParams &P, const double *theta, int n,
+                         double t_ref, double *chi2, double *grad, double *H,
+                         double *Fs, double *Fb, int *flags, cudaStream_t st);
+cudaError_t launch_lm_init(const RefineState &S, const morse_fit *starts,
+                           int n, double lam0, cudaStream_t st);
+cudaError_t launch_lm_step(const RefineState &S, int n, cudaStream_t st);
+cudaError_t launch_lm_finish(const RefineState &S, const morse_fit *starts,
+                             int n, morse_fit *out, cudaStream_t st);
+
 cudaError_t launch_lightcurve(const SearchParams &P, float ax, float bx,
                               float ay, float by, float kt, float bt,
                               float u02, const float *t, int n, float *A,

@@ -194,6 +194,7 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   P.coff = 0.5 * map->npix - (double)(map->npix / 2) - 0.5;
   P.voff = (float)(-P.coff);
   P.dltf = (float)dlt;
+  P.invDf = (float)(1.0 / dlt);
   P.invD = 1.0 / dlt;
   P.ep = ev->ep;
   P.n_ep = (int)ev->n;

@@ -1,0 +1,401 @@
+// Device functions shared by the search, fit-fill and adjoint kernels: the
+// per-trajectory constants, the map lookup, the two epoch sweeps and the
+// 2x2 solve.  Every kernel that reports a chi^2 uses these same functions,
+// so their results agree to the last bit for the same trajectory.
+//
+// The method (McDougall & Albrow 2015, §4.2): bilinear interpolation of the
+// magnification map along a straight trajectory, the linear flux model
+// F = Fs A + Fb (Eq. 5-6) and chi^2 as the sum of per-point contributions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "morse_internal.cuh"
+
+namespace morse {
+namespace dev {
+
+#ifndef MORSE_UNROLL
+#define MORSE_UNROLL 4
+#endif
+constexpr int kUnroll = MORSE_UNROLL;  // inside-map epoch loop
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned kLockSpinLimit = 1u << 20;
+
+// Per-trajectory constants.
+struct TrajC {
+  float ax, bx, ay, by;  // centred pixel coordinates v = a t + b
+  float kt, bt, u02;     // tau = kt t + bt; u0^2
+  int e_in, e_out;       // epochs [e_in, e_out) lie inside the map
+};
+
+__device__ __forceinline__ bool key_less(const Entry &a, const Entry &b) {
+  return a.chi2 < b.chi2 || (a.chi2 == b.chi2 && a.idx < b.idx);
+}
+__device__ __forceinline__ bool key_less(double ca, long long ia, double cb,
+                                         long long ib) {
+  return ca < cb || (ca == cb && ia < ib);
+}
+
+// first epoch index with t > x (strict) or t >= x (!strict), t ascending
+__device__ __forceinline__ int epoch_search(const float4 *ep, int n, double x,
+                                            bool strict) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const double t = (double)ep[mid].x;
+    const bool right = strict ? (t > x) : (t >= x);
+    if (right)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+// Constants of trajectory j.  The kernel works in centred pixel coordinates
+// v = (y + L)/Delta - 1/2 - floor(npix/2) = y/Delta + coff (coff = -1/2 for
+// even npix, 0 for odd): texel i (from 0 at the map edge) is centred at
+// v = i - floor(npix/2), and the map centre, where the caustics of close and
+// resonant lenses lie, has the finest FP32 resolution.  With
+// y1 = tau cos(alpha) - u0 sin(alpha), y2 = tau sin(alpha) + u0 cos(alpha)
+// and tau = (t - t0)/tE the coordinates are v = a t + b.  The track is
+// inside the map (|y1| < L and |y2| < L) for tau in (tau_lo, tau_hi), i.e.
+// for the epochs [e_in, e_out).
+__device__ __forceinline__ TrajC make_traj(const SearchParams &P,
+                                           const float4 *ep, double u,
+                                           double c, double s, double t0,
+                                           double k) {
+  // u = u0, (c, s) = (cos, sin) alpha, t0 relative to t_ref,
+  // k = 1/(tE Delta)
+  const double ax = __dmul_rn(c, k), ay = __dmul_rn(s, k);
+  const double cx = __dadd_rn(__dmul_rn(-__dmul_rn(u, s), P.invD), P.coff);
+  const double cy = __dadd_rn(__dmul_rn(__dmul_rn(u, c), P.invD), P.coff);
+  const double kt = __dmul_rn(k, P.dlt);  // 1/tE
+  TrajC o;
+  o.ax = __double2float_rn(ax);
+  o.ay = __double2float_rn(ay);
+  o.bx = __double2float_rn(__dsub_rn(cx, __dmul_rn(t0, ax)));
+  o.by = __double2float_rn(__dsub_rn(cy, __dmul_rn(t0, ay)));
+  o.kt = __double2float_rn(kt);
+  o.bt = __double2float_rn(-__dmul_rn(t0, kt));
+  o.u02 = __double2float_rn(__dmul_rn(u, u));
+  // slab intersection of the line with |y1| < L, |y2| < L
+  double lo = -CUDART_INF, hi = CUDART_INF;
+  const double us = u * s, uc = u * c;
+  if (c != 0.0) {
+    const double a0 = (-P.L + us) / c, a1 = (P.L + us) / c;
+    lo = fmax(lo, fmin(a0, a1));
+    hi = fmin(hi, fmax(a0, a1));
+  } else if (!(fabs(us) < P.L)) {
+    hi = lo;
+  }
+  if (s != 0.0) {
+    const double b0 = (-P.L - uc) / s, b1 = (P.L - uc) / s;
+    lo = fmax(lo, fmin(b0, b1));
+    hi = fmin(hi, fmax(b0, b1));
+  } else if (!(fabs(uc) < P.L)) {
+    hi = lo;
+  }
+  if (lo < hi) {
+    const double tE = 1.0 / kt;
+    o.e_in = epoch_search(ep, P.n_ep, t0 + lo * tE, true);
+    o.e_out = epoch_search(ep, P.n_ep, t0 + hi * tE, false);
+    if (o.e_out < o.e_in) o.e_out = o.e_in;
+  } else {
+    o.e_in = P.n_ep;
+    o.e_out = P.n_ep;
+  }
+  return o;
+}
+
+// constants of grid trajectory j from the device tables
+__device__ __forceinline__ TrajC traj_consts(const SearchParams &P,
+                                             const float4 *ep, long long j) {
+  long long r = j;
+  const int itE = (int)(r % P.n_tE);
+  r /= P.n_tE;
+  const int it0 = (int)(r % P.n_t0);
+  r /= P.n_t0;
+  const int ia = (int)(r % P.n_alpha);
+  const int iu = (int)(r / P.n_alpha);
+  return make_traj(P, ep, P.u0v[iu], P.ca[ia], P.sa[ia], P.t0rel[it0],
+                   P.invtEd[itE]);
+}
+
+__device__ __forceinline__ TrajC shfl_traj(const TrajC &m, int k) {
+  TrajC c;
+  c.ax = __shfl_sync(kFull, m.ax, k);
+  c.bx = __shfl_sync(kFull, m.bx, k);
+  c.ay = __shfl_sync(kFull, m.ay, k);
+  c.by = __shfl_sync(kFull, m.by, k);
+  c.kt = __shfl_sync(kFull, m.kt, k);
+  c.bt = __shfl_sync(kFull, m.bt, k);
+  c.u02 = __shfl_sync(kFull, m.u02, k);
+  c.e_in = __shfl_sync(kFull, m.e_in, k);
+  c.e_out = __shfl_sync(kFull, m.e_out, k);
+  return c;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// single-lens magnification from u^2 (outside the map)
+__device__ __forceinline__ float pspl_u2(float u2) {
+  return __fmul_rn(__fadd_rn(u2, 2.f),
+                   rsqrt_approx(__fmul_rn(u2, __fadd_rn(u2, 4.f))));
+}
+
+// Bilinear A - 1 at centred coordinates inside the map (the quads store
+// A - 1).  Coordinates below the first texel centre are clamped to it (the
+// lookup rule).  Above the last centre no clamp is needed: the caller only
+// passes epochs strictly inside the map, so floor(v) <= npix - half - 1, and
+// the last texel's quad repeats its edge values.  The bounds-checked build
+// verifies the index range.
+__device__ __forceinline__ float bilinear_m1(const SearchParams &P, float vx,
+                                             float vy) {
+  const float cx = fmaxf(vx, P.vmin);
+  const float cy = fmaxf(vy, P.vmin);
+  // floor: adding 1.5 * 2^23 rounding down leaves floor(c) in the low
+  // mantissa bits; the fraction c - floor(c) is exact
+  const float tx = __fadd_rd(cx, 12582912.f), ty = __fadd_rd(cy, 12582912.f);
+  const float fx = __fsub_rn(cx, __fsub_rn(tx, 12582912.f));
+  const float fy = __fsub_rn(cy, __fsub_rn(ty, 12582912.f));
+  // texel (ix, iy) = floor(c) + half; quad index iy * qpitch + ix, folded
+  // into one multiply-add on the raw bit patterns (mod 2^32, exact because
+  // the index is in [0, npix * qpitch))
+  const unsigned bx = (unsigned)__float_as_int(tx);
+  const unsigned by = (unsigned)__float_as_int(ty);
+  const unsigned idx = by * (unsigned)P.qpitch + bx + P.qidx0;
+#ifdef MORSE_CHECK_BOUNDS
+  // checked build: record an out-of-range texel and skip the access
+  const int ix = (int)(bx - 0x4B400000u) + P.half;
+  const int iy = (int)(by - 0x4B400000u) + P.half;
+  if ((unsigned)ix >= (unsigned)P.npix || (unsigned)iy >= (unsigned)P.npix) {
+    if (P.err) atomicOr(P.err, 2u);
+    return 0.f;
+  }
+#endif
+  const float4 q = __ldg(&P.quad[idx]);
+  const float r0 = __fmaf_rn(fx, __fsub_rn(q.y, q.x), q.x);
+  const float r1 = __fmaf_rn(fx, __fsub_rn(q.w, q.z), q.z);
+  return __fmaf_rn(fy, __fsub_rn(r1, r0), r0);
+}
+
+// Lanes own epochs by index mod 32 in every range, so a lane always sums
+// its terms in ascending epoch order whatever the ranges are: the sums of a
+// trajectory do not depend on how its epoch axis is cut into segments (the
+// search pairs trajectories, the fit fill does not; both get the same
+// rounding).
+__device__ __forceinline__ int lane_start(int e0, int lane) {
+  return e0 + ((lane - e0) & 31);
+}
+
+struct Acc {
+  float a, b, d;  // S_A, S_AA, S_AF partial sums of one lane
+};
+
+__device__ __forceinline__ void acc_add(Acc &s, const float4 &v, float Ac) {
+  const float wAc = __fmul_rn(v.y, Ac);
+  s.a = __fadd_rn(s.a, wAc);
+  s.b = __fmaf_rn(wAc, Ac, s.b);
+  s.d = __fmaf_rn(v.z, Ac, s.d);
+}
+
+// A - 1 at time t inside the map (bilinear) or outside (single lens)
+__device__ __forceinline__ float mag_in_m1(const SearchParams &P,
+                                           const TrajC &c, float t) {
+  return bilinear_m1(P, __fmaf_rn(c.ax, t, c.bx), __fmaf_rn(c.ay, t, c.by));
+}
+__device__ __forceinline__ float mag_out_m1(const TrajC &c, float t) {
+  const float tau = __fmaf_rn(c.kt, t, c.bt);
+  return __fsub_rn(pspl_u2(__fmaf_rn(tau, tau, c.u02)), 1.f);
+}
+
+template <bool IN>
+__device__ __forceinline__ void seg1(const SearchParams &P, const float4 *ep,
+                                     const TrajC &c, int lane, int e0, int e1,
+                                     Acc &s) {
+#pragma unroll (IN ? kUnroll : 2)
+  for (int e = lane_start(e0, lane); e < e1; e += 32) {
+    const float4 v = ep[e];
+    acc_add(s, v, IN ? mag_in_m1(P, c, v.x) : mag_out_m1(c, v.x));
+  }
+}
+
+// two trajectories over one epoch segment, one epoch load for both
+template <bool INA, bool INB>
+__device__ __forceinline__ void seg2(const SearchParams &P, const float4 *ep,
+                                     const TrajC &ca, const TrajC &cb,
+                                     int lane, int e0, int e1, Acc &sa,
+                                     Acc &sb) {
+#pragma unroll ((INA || INB) ? kUnroll : 2)
+  for (int e = lane_start(e0, lane); e < e1; e += 32) {
+    const float4 v = ep[e];
+    acc_add(sa, v, INA ? mag_in_m1(P, ca, v.x) : mag_out_m1(ca, v.x));
+    acc_add(sb, v, INB ? mag_in_m1(P, cb, v.x) : mag_out_m1(cb, v.x));
+  }
+}
+
+// xor butterfly; lane 0's totals go to every lane
+__device__ __forceinline__ Acc acc_reduce(Acc s) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    s.a = __fadd_rn(s.a, __shfl_xor_sync(kFull, s.a, o));
+    s.b = __fadd_rn(s.b, __shfl_xor_sync(kFull, s.b, o));
+    s.d = __fadd_rn(s.d, __shfl_xor_sync(kFull, s.d, o));
+  }
+  Acc r;
+  r.a = __shfl_sync(kFull, s.a, 0);
+  r.b = __shfl_sync(kFull, s.b, 0);
+  r.d = __shfl_sync(kFull, s.d, 0);
+  return r;
+}
+
+// Phase 1: FP32 sums of S_A = sum w (A-1), S_AA = sum w (A-1)^2 and
+// S_AF = sum w (F-Fref)(A-1) over the epochs before, inside and after the
+// map, reduced across the warp.
+__device__ __forceinline__ Acc phase1(const SearchParams &P, const float4 *ep,
+                                      const TrajC &c, const int lane) {
+  Acc s = {0.f, 0.f, 0.f};
+  seg1<false>(P, ep, c, lane, 0, c.e_in, s);
+  seg1<true>(P, ep, c, lane, c.e_in, c.e_out, s);
+  seg1<false>(P, ep, c, lane, c.e_out, P.n_ep, s);
+  return acc_reduce(s);
+}
+
+// Phase 1 of two trajectories at once: the epoch axis is cut at both
+// trajectories' map entry and exit, and each segment runs the matching
+// inside/outside combination with one epoch load per lane for both.
+__device__ __forceinline__ void phase1_pair(const SearchParams &P,
+                                            const float4 *ep, const TrajC &ca,
+                                            const TrajC &cb, const int lane,
+                                            Acc &ra, Acc &rb) {
+  Acc sa = {0.f, 0.f, 0.f}, sb = {0.f, 0.f, 0.f};
+  // cut points, sorted (warp-uniform)
+  int p1 = ca.e_in, p2 = ca.e_out, p3 = cb.e_in, p4 = cb.e_out, t;
+  if (p1 > p2) { t = p1; p1 = p2; p2 = t; }
+  if (p3 > p4) { t = p3; p3 = p4; p4 = t; }
+  if (p1 > p3) { t = p1; p1 = p3; p3 = t; }
+  if (p2 > p4) { t = p2; p2 = p4; p4 = t; }
+  if (p2 > p3) { t = p2; p2 = p3; p3 = t; }
+  const int cut[6] = {0, p1, p2, p3, p4, P.n_ep};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int e0 = cut[i], e1 = cut[i + 1];
+    if (e0 >= e1) continue;
+    const bool ina = e0 >= ca.e_in && e1 <= ca.e_out;
+    const bool inb = e0 >= cb.e_in && e1 <= cb.e_out;
+    if (ina && inb)
+      seg2<true, true>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+    else if (ina)
+      seg2<true, false>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+    else if (inb)
+      seg2<false, true>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+    else
+      seg2<false, false>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+  }
+  ra = acc_reduce(sa);
+  rb = acc_reduce(sb);
+}
+
+// Phase 2: chi^2 = sum w (F - Fs A - Fb)^2, written with centred values as
+// w (Fc - Fs Ac - Bc)^2, Bc = Fs + Fb - Fref.  FP32 per lane, FP64 across
+// lanes; lane 0's value is returned to all lanes.
+__device__ __forceinline__ double phase2(const SearchParams &P,
+                                         const float4 *ep, const TrajC &c,
+                                         const int lane, const float Fs,
+                                         const float Bc) {
+  float chi = 0.f;
+#pragma unroll 2
+  for (int e = lane_start(0, lane); e < c.e_in; e += 32) {
+    const float4 v = ep[e];
+    const float Ac = mag_out_m1(c, v.x);
+    const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
+    chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
+  }
+#pragma unroll (kUnroll)
+  for (int e = lane_start(c.e_in, lane); e < c.e_out; e += 32) {
+    const float4 v = ep[e];
+    const float Ac = mag_in_m1(P, c, v.x);
+    const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
+    chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
+  }
+#pragma unroll 2
+  for (int e = lane_start(c.e_out, lane); e < P.n_ep; e += 32) {
+    const float4 v = ep[e];
+    const float Ac = mag_out_m1(c, v.x);
+    const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
+    chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
+  }
+  double x = (double)chi;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x = __dadd_rn(x, __shfl_xor_sync(kFull, x, o));
+  return __shfl_sync(kFull, x, 0);
+}
+
+struct Solved {
+  double Fs, Bc;      // Fb = Bc + Fref - Fs
+  double lb;          // rigorous lower bound of the exact chi^2
+  bool degenerate;
+};
+
+// 2x2 weighted least squares (Eq. 6) in FP64 from the centred sums, and a
+// lower bound of the chi^2 the exact residual sweep will give.
+// Degenerate rule: det <= 1e-12 S_AA S_1 (uncentred S_AA) -> Fs = 0,
+// Fb = weighted mean flux.
+//
+// Bound.  With C_FF = S_FF - S_F^2/S_1, C_AA = S_AA - S_A^2/S_1 and
+// C_AF = S_AF - S_A S_F/S_1 the minimum is chi^2 = C_FF - C_AF^2 / C_AA.
+// The FP32 sums carry relative errors of at most gamma of the sums of
+// absolute terms (T_A = sum |w Ac| <= sqrt(S_1 S_AA), T_AF = sum |w Ac Fc|
+// <= sqrt(S_AA S_FF); S_AA has positive terms), so |C_AF| and C_AA are
+// bracketed and C_AF^2 / C_AA <= (|C_AF| + d_AF)^2 / (C_AA - d_AA).  This
+// holds however ill-conditioned (Fs, Fb) is: a nearly flat track explains
+// little of C_FF and is discarded all the same.  C_FF is exact (FP64 sums
+// of the stored values).  gamma is doubled as a margin.
+__device__ __forceinline__ Solved solve2(const SearchParams &P, double SA,
+                                         double SAA, double SAF) {
+  Solved o;
+  const double S1 = P.S1, SF = P.SF, SFF = P.SFF;
+  const double SAAu = SAA + 2.0 * SA + S1;
+  const double det = SAA * S1 - SA * SA;
+  if (!(det > 1e-12 * SAAu * S1)) {
+    o.Fs = 0.0;
+    o.Bc = SF / S1;
+    o.degenerate = true;
+  } else {
+    const double inv = 1.0 / det;
+    o.Fs = (S1 * SAF - SA * SF) * inv;
+    o.Bc = (SAA * SF - SA * SAF) * inv;
+    o.degenerate = false;
+  }
+  const double g = 2.0 * P.gamma;
+  const double CFF = SFF - SF * SF / S1;
+  const double CAA = SAA - SA * SA / S1;
+  const double CAF = SAF - SA * SF / S1;
+  const double TA = sqrt(S1 * SAA), TAF = sqrt(SAA * SFF);
+  const double dAA = g * (SAA + (2.0 * fabs(SA) * TA + g * TA * TA) / S1);
+  const double dAF = g * (TAF + TA * fabs(SF) / S1);
+  double X = CFF;  // upper bound of the part of C_FF the fit explains
+  if (CAA > dAA) {
+    const double num = fabs(CAF) + dAF;
+    X = fmin(CFF, num * num / (CAA - dAA));
+  }
+  o.lb = CFF - X;
+  return o;
+}
+
+__device__ __forceinline__ double bits_to_chi2(unsigned long long b) {
+  return b == ~0ULL ? CUDART_INF : __longlong_as_double((long long)b);
+}
+
+
+}  // namespace dev
+}  // namespace morse

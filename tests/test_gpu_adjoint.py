@@ -1,0 +1,252 @@
+"""GPU parity of the adjoint gradient, the Levenberg-Marquardt refine and the
+torch.autograd.Function, against the CPU oracle.
+
+* chi^2 at grid points equals the grid search's (same device functions).
+* The gradient equals FP64 central differences of the oracle's map chi^2
+  for every component whose +-h evaluations keep every epoch in the same
+  texel and on the same side of the map edge (the bilinear lookup is
+  smooth there; its gradient jumps at texel edges).  h = 1e-6 relative:
+  the FP64 oracle is exact enough for it, and crossings stay rare.
+* Against the FP64 gradient of the point-source polynomial chi^2 (central
+  differences of the oracle's polynomial magnification) on trajectories
+  that stay 5 texels from any caustic, on a dense map: the map's pixel
+  averaging sets the tolerance; the distribution is reported.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+import synth
+
+pytestmark = pytest.mark.gpu
+
+NT = orc.threads_default()
+
+
+@pytest.fixture(scope="module")
+def m():
+    import paper_1511_01157_gb300 as lib
+    return lib
+
+
+@pytest.fixture(scope="module")
+def ctx(m):
+    c = m.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def setup(ctx):
+    c = synth.CFG0
+    A_o, *_ = orc.build_map(c["s"], c["q"], c["L"], c["npix"], c["nray"],
+                            c["X"], nthreads=NT)
+    t = synth.epoch_times(c["n"], c["seed"], c["t0"])
+    At = orc.lightcurve_point(c["s"], c["q"], t, c["t0"], c["tE"], c["u0"],
+                              c["alpha"])
+    F, sig = synth.photometry(c["Fs"] * At + c["Fb"], c["seed"])
+    mp = ctx.map_from_host(A_o, c["L"])
+    ev = ctx.event(t, F, sig)
+    return c, A_o, t, F, sig, mp, ev
+
+
+def _ogrid(g):
+    return orc.Grid(g["n_u0"], g["n_alpha"], g["n_t0"], g["n_tE"],
+                    g["u0_lo"], g["u0_hi"], g["t0_lo"], g["t0_hi"],
+                    g["tE_lo"], g["tE_hi"], g["u0_log"], g["tE_log"])
+
+
+def test_chi2_at_grid_points_equals_search(ctx, m, setup):
+    c, A_o, t, F, sig, mp, ev = setup
+    g = c["grid"]
+    og = _ogrid(g)
+    grid = m.Grid.make(g["n_u0"], g["n_alpha"], g["n_t0"], g["n_tE"],
+                       g["u0_lo"], g["u0_hi"], g["t0_lo"], g["t0_hi"],
+                       g["tE_lo"], g["tE_hi"], True, True, 4)
+    idx = np.random.default_rng(0).choice(og.size, 64, replace=False)
+    theta = np.array([og.params(int(k)) for k in idx])
+    chi2, grad, fs, fb = ctx.chi2_grad(ev, mp, theta)
+    dense, dfs, dfb = ctx.grid_chi2_dense(ev, mp, grid)
+    np.testing.assert_allclose(chi2, dense[idx], rtol=1e-6)
+    w = 1.0 / sig ** 2
+    for j, k in enumerate(idx[:16]):
+        o, ofs, ofb = orc.chi2_theta(t, F, w, theta[j], A=A_o, L=c["L"])
+        assert chi2[j] == pytest.approx(o, rel=1e-5)
+        assert fs[j] == pytest.approx(ofs, rel=1e-3, abs=1e-3)
+
+
+def _pixels(theta, t, L, npix):
+    """FP64 pixel coordinates (lookup convention) and inside flags."""
+    t0, tE, u0, al = theta
+    tau = (t - t0) / tE
+    y1 = tau * math.cos(al) - u0 * math.sin(al)
+    y2 = tau * math.sin(al) + u0 * math.cos(al)
+    d = 2 * L / npix
+    px = np.clip((y1 + L) / d - 0.5, 0, npix - 1)
+    py = np.clip((y2 + L) / d - 0.5, 0, npix - 1)
+    inside = (np.abs(y1) < L) & (np.abs(y2) < L)
+    return np.floor(px), np.floor(py), inside
+
+
+def _steps(theta):
+    t0, tE, u0, al = theta
+    return np.array([1e-6 * tE, 1e-6 * tE, 1e-6 * max(u0, 1e-3), 1e-6])
+
+
+def test_gradient_matches_oracle_central_differences(ctx, setup):
+    c, A_o, t, F, sig, mp, ev = setup
+    w = 1.0 / sig ** 2
+    rng = np.random.default_rng(5)
+    n = 120
+    theta = np.stack([rng.uniform(-1.5, 1.5, n), rng.uniform(8.0, 40.0, n),
+                      rng.uniform(0.01, 0.3, n), rng.uniform(0, 2 * np.pi, n)],
+                     axis=1)
+    chi2, grad, _, _ = ctx.chi2_grad(ev, mp, theta)
+    rel, used = [], 0
+    for i in range(n):
+        h = _steps(theta[i])
+        base = _pixels(theta[i], t, c["L"], c["npix"])
+        for k in range(4):
+            tp = theta[i].copy()
+            tm = theta[i].copy()
+            tp[k] += h[k]
+            tm[k] -= h[k]
+            pp, pm = _pixels(tp, t, c["L"], c["npix"]), \
+                _pixels(tm, t, c["L"], c["npix"])
+            clean = all(np.array_equal(a, b) and np.array_equal(a, cc)
+                        for a, b, cc in zip(base, pp, pm))
+            if not clean:
+                continue
+            fp = orc.chi2_theta(t, F, w, tp, A=A_o, L=c["L"])[0]
+            fm = orc.chi2_theta(t, F, w, tm, A=A_o, L=c["L"])[0]
+            fd = (fp - fm) / (2 * h[k])
+            # scale: the largest of this component's FD and the gradient
+            # magnitude a 1e-3 relative chi^2 change per unit step implies
+            scale = max(abs(fd), 1e-3 * chi2[i] / max(h[k] * 1e6, 1e-12))
+            rel.append(abs(grad[i, k] - fd) / scale)
+            used += 1
+    rel = np.array(rel)
+    print(f"components compared: {used}; rel err median {np.median(rel):.2e}"
+          f" p95 {np.quantile(rel, 0.95):.2e} max {rel.max():.2e}")
+    assert used > 200
+    assert np.median(rel) < 1e-4
+    assert np.quantile(rel, 0.95) < 1e-3
+
+
+def test_gradient_vs_polynomial_point_source(ctx, m):
+    """Map gradient vs the FP64 gradient of the polynomial point-source
+    chi^2, on smooth-region trajectories of a dense map."""
+    s, q, L, npix, nray, X = 1.0, 1e-3, 1.0, 256, 8000, 2.0
+    A_o, *_ = orc.build_map(s, q, L, npix, nray, X, nthreads=NT)
+    mp = ctx.map_from_host(A_o, L)
+    # caustic pixels: the image count changes between neighbours
+    d = 2 * L / npix
+    cnt = np.zeros((npix, npix), dtype=np.int8)
+    for j in range(npix):
+        for i in range(npix):
+            cnt[j, i] = orc.images(s, q, -L + (i + 0.5) * d,
+                                   -L + (j + 0.5) * d)[0]
+    edge = np.zeros_like(cnt, dtype=bool)
+    edge[:, 1:] |= cnt[:, 1:] != cnt[:, :-1]
+    edge[:, :-1] |= cnt[:, 1:] != cnt[:, :-1]
+    edge[1:, :] |= cnt[1:, :] != cnt[:-1, :]
+    edge[:-1, :] |= cnt[1:, :] != cnt[:-1, :]
+    from scipy.ndimage import binary_dilation
+    bad = binary_dilation(edge, iterations=5)
+    t = synth.epoch_times(160, 13)
+    t = t[np.abs(t) < 30]
+    At = orc.lightcurve_point(s, q, t, 0.0, 20.0, 0.1, 0.6)
+    F, sig = synth.photometry(At + 0.2, 13)
+    w = 1.0 / sig ** 2
+    ev = ctx.event(t, F, sig)
+    rng = np.random.default_rng(2)
+    thetas = []
+    while len(thetas) < 150:
+        th = np.array([rng.uniform(-2, 2), rng.uniform(10, 40),
+                       rng.uniform(0.05, 0.6), rng.uniform(0, 2 * np.pi)])
+        px, py, inside = _pixels(th, t, L, npix)
+        if inside.sum() < 10:
+            continue
+        if bad[py[inside].astype(int), px[inside].astype(int)].any():
+            continue
+        thetas.append(th)
+    theta = np.array(thetas)
+    chi2, grad, _, _ = ctx.chi2_grad(ev, mp, theta)
+    rel = []
+    for i in range(len(theta)):
+        h = 1e2 * _steps(theta[i])  # 1e-4 relative on the smooth polynomial
+        g = np.zeros(4)
+        for k in range(4):
+            tp = theta[i].copy()
+            tm = theta[i].copy()
+            tp[k] += h[k]
+            tm[k] -= h[k]
+            g[k] = (orc.chi2_theta(t, F, w, tp, s=s, q=q)[0] -
+                    orc.chi2_theta(t, F, w, tm, s=s, q=q)[0]) / (2 * h[k])
+        rel.append(np.linalg.norm(grad[i] - g) / np.linalg.norm(g))
+    rel = np.array(rel)
+    print(f"map vs polynomial gradient: median rel {np.median(rel):.2e}, "
+          f"p90 {np.quantile(rel, 0.9):.2e}")
+    assert np.median(rel) < 1e-2
+
+
+def test_refine_lowers_chi2_and_matches_oracle(ctx, m, setup):
+    c, A_o, t, F, sig, mp, ev = setup
+    g = c["grid"]
+    grid = m.Grid.make(g["n_u0"], g["n_alpha"], g["n_t0"], g["n_tE"],
+                       g["u0_lo"], g["u0_hi"], g["t0_lo"], g["t0_hi"],
+                       g["tE_lo"], g["tE_hi"], True, True, 16)
+    seeds = ctx.grid_chi2(ev, mp, grid)
+    out = ctx.refine(ev, mp, seeds, iters=40)
+    assert np.all(out["chi2"] <= seeds["chi2"] * (1 + 1e-12))
+    assert out["chi2"].min() < seeds["chi2"].min()
+    assert np.all(out["flags"] & m.FIT_REFINED)
+    assert np.array_equal(out["idx"], seeds["idx"])
+    w = 1.0 / sig ** 2
+    for r in out[:6]:
+        o = orc.chi2_theta(t, F, w, (r["t0"], r["tE"], r["u0"], r["alpha"]),
+                           A=A_o, L=c["L"])[0]
+        assert r["chi2"] == pytest.approx(o, rel=1e-5)
+    # zero iterations return the starts unchanged
+    same = ctx.refine(ev, mp, seeds[:4], iters=0)
+    np.testing.assert_allclose(same["chi2"], seeds["chi2"][:4], rtol=1e-6)
+
+
+def test_autograd_function_and_lbfgs(ctx, m, setup):
+    torch = pytest.importorskip("torch")
+    c, A_o, t, F, sig, mp, ev = setup
+    Chi2 = m.chi2_function()
+    theta0 = np.array([[0.3, 18.0, 0.08, 0.6], [-0.5, 25.0, 0.04, 0.8]])
+    th = torch.tensor(theta0, dtype=torch.float64, device="cuda",
+                      requires_grad=True)
+    y = Chi2.apply(th, ctx, ev, mp)
+    y.sum().backward()
+    chi2, grad, _, _ = ctx.chi2_grad(ev, mp, theta0)
+    np.testing.assert_allclose(y.detach().cpu().numpy(), chi2, rtol=1e-12)
+    np.testing.assert_allclose(th.grad.cpu().numpy(), grad, rtol=1e-12)
+    # L-BFGS through the autograd function lowers chi^2
+    p = torch.tensor(theta0[:1], dtype=torch.float64, device="cuda",
+                     requires_grad=True)
+    opt = torch.optim.LBFGS([p], lr=0.5, max_iter=20,
+                            line_search_fn="strong_wolfe")
+
+    def closure():
+        opt.zero_grad()
+        v = Chi2.apply(p, ctx, ev, mp).sum()
+        v.backward()
+        return v
+
+    before = closure().item()
+    opt.step(closure)
+    after = Chi2.apply(p.detach(), ctx, ev, mp).sum().item()
+    assert after < before
+
+
+def test_gradient_rejects_bad_theta(ctx, m, setup):
+    c, A_o, t, F, sig, mp, ev = setup
+    for bad in ([0.0, -1.0, 0.1, 0.0], [np.nan, 10.0, 0.1, 0.0]):
+        with pytest.raises(m.MorseError) as e:
+            ctx.chi2_grad(ev, mp, np.array([bad]))
+        assert e.value.status == m.EINVAL
