@@ -13,6 +13,7 @@ names the passage of McDougall & Albrow (2015) it follows:
 * ``counts_to_mag``   -- map value = ray count x h^2 / Delta^2
 * ``quintic``/``roots5``/``images``/``mag_point`` -- §3 fifth-order lens
   polynomial, 3 or 5 images, A = sum 1/|det J| (Eq. 3-4)
+* ``poly_map``        -- §4.1 point-source map from the polynomial per texel
 * ``pspl``            -- §4.3 (ii) Paczynski single-lens curve
 * ``traj_point``/``map_A`` -- §4.2 straight trajectory, bilinear map lookup
 * ``fit_A``           -- §4.1 Eq. 5-6 linear flux fit, chi^2 as a sum of
@@ -73,6 +74,7 @@ def _load():
         "orc_images": (_I, [_D, _D, _D, _D, _D, _P, _P, _P, _P]),
         "orc_mag_point": (_D, [_D, _D, _D, _D, _P]),
         "orc_pspl": (_D, [_D]),
+        "orc_poly_map": (None, [_D, _D, _D, _I, _P, _I]),
         "orc_traj_point": (None, [_D, _D, _D, _D, _D, _P, _P]),
         "orc_map_A": (_D, [_P, _I, _D, _D, _D]),
         "orc_fit_A": (_D, [_P, _P, _P, ctypes.c_long, _P, _P, _P]),
@@ -182,6 +184,15 @@ def mag_point(s, q, y1, y2):
     """Point-source magnification sum_j 1/|det J_j| (§3 Eq. 3)."""
     n = ctypes.c_int()
     return _load().orc_mag_point(s, q, y1, y2, ctypes.byref(n))
+
+
+def poly_map(s, q, L, npix, nthreads=1):
+    """Point-source map: the polynomial magnification at texel centres
+    (§4.1), FP32 [npix, npix]."""
+    A = np.zeros((npix, npix), dtype=np.float32)
+    _load().orc_poly_map(float(s), float(q), float(L), int(npix), _ptr(A),
+                         int(nthreads))
+    return A
 
 
 def pspl(u):

@@ -395,6 +395,24 @@ double orc_mag_point(double s, double q, double y1, double y2, int *nimg) {
   return A;
 }
 
+/* Point-source map by the polynomial (§4.1: "solving the fifth-order
+ * polynomial ... for a uniform grid of source positions"): texel (i, j)
+ * holds the magnification at its centre (-L + (i+1/2) Delta, ...), rounded
+ * to FP32.  Rows are independent (OpenMP). */
+void orc_poly_map(double s, double q, double L, int npix, float *A,
+                  int nthreads) {
+  double dlt = (2.0 * L) / (double)npix;
+  if (nthreads < 1) nthreads = 1;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 1)
+#endif
+  for (int j = 0; j < npix; ++j)
+    for (int i = 0; i < npix; ++i)
+      A[(size_t)j * npix + i] = (float)orc_mag_point(
+          s, q, -L + ((double)i + 0.5) * dlt, -L + ((double)j + 0.5) * dlt,
+          NULL);
+}
+
 /* Single-lens (Paczynski) magnification A(u) = (u^2+2)/(u sqrt(u^2+4)). */
 double orc_pspl(double u) {
   return (u * u + 2.0) / (u * sqrt(u * u + 4.0));

@@ -8,9 +8,11 @@ torch.autograd.Function, against the CPU oracle.
   smooth there; its gradient jumps at texel edges).  h = 1e-6 relative:
   the FP64 oracle is exact enough for it, and crossings stay rare.
 * Against the FP64 gradient of the point-source polynomial chi^2 (central
-  differences of the oracle's polynomial magnification) on trajectories
-  that stay 5 texels from any caustic, on a dense map: the map's pixel
-  averaging sets the tolerance; the distribution is reported.
+  differences of the oracle's polynomial magnification) on 1000
+  trajectories that stay 8 texels from any caustic, on a map holding the
+  polynomial at texel centres: the bilinear discretisation sets the
+  tolerance (median relative error <= 1e-2); the distribution is
+  printed.
 """
 import math
 
@@ -137,24 +139,30 @@ def test_gradient_matches_oracle_central_differences(ctx, setup):
 
 def test_gradient_vs_polynomial_point_source(ctx, m):
     """Map gradient vs the FP64 gradient of the polynomial point-source
-    chi^2, on smooth-region trajectories of a dense map."""
-    s, q, L, npix, nray, X = 1.0, 1e-3, 1.0, 256, 8000, 2.0
-    A_o, *_ = orc.build_map(s, q, L, npix, nray, X, nthreads=NT)
-    mp = ctx.map_from_host(A_o, L)
-    # caustic pixels: the image count changes between neighbours
-    d = 2 * L / npix
-    cnt = np.zeros((npix, npix), dtype=np.int8)
-    for j in range(npix):
-        for i in range(npix):
-            cnt[j, i] = orc.images(s, q, -L + (i + 0.5) * d,
-                                   -L + (j + 0.5) * d)[0]
+    chi^2 on 1000 smooth-region trajectories.
+
+    The map holds the polynomial magnification at its texel centres
+    (§4.1's point-source map), so the comparison measures the bilinear
+    lookup's discretisation alone.  A ray-shot map would add the ray
+    sampling's texel-to-texel noise, which differentiation amplifies by
+    1/Delta: finer ray-shot maps agree worse, not better."""
+    s, q, L, npix = 1.0, 1e-3, 1.0, 512
+    P = orc.poly_map(s, q, L, npix, nthreads=NT)
+    mp = ctx.map_from_host(P, L)
+    # caustic texels: the image count changes between neighbours, found on
+    # a 4x coarser grid and dilated by 2 coarse (8 fine) texels
+    nc = npix // 4
+    dc = 2 * L / nc
+    cnt = np.array([[orc.images(s, q, -L + (i + 0.5) * dc,
+                                -L + (j + 0.5) * dc)[0]
+                     for i in range(nc)] for j in range(nc)], dtype=np.int8)
     edge = np.zeros_like(cnt, dtype=bool)
     edge[:, 1:] |= cnt[:, 1:] != cnt[:, :-1]
     edge[:, :-1] |= cnt[:, 1:] != cnt[:, :-1]
     edge[1:, :] |= cnt[1:, :] != cnt[:-1, :]
     edge[:-1, :] |= cnt[1:, :] != cnt[:-1, :]
     from scipy.ndimage import binary_dilation
-    bad = binary_dilation(edge, iterations=5)
+    bad = binary_dilation(edge, iterations=2)
     t = synth.epoch_times(160, 13)
     t = t[np.abs(t) < 30]
     At = orc.lightcurve_point(s, q, t, 0.0, 20.0, 0.1, 0.6)
@@ -163,10 +171,10 @@ def test_gradient_vs_polynomial_point_source(ctx, m):
     ev = ctx.event(t, F, sig)
     rng = np.random.default_rng(2)
     thetas = []
-    while len(thetas) < 150:
+    while len(thetas) < 1000:
         th = np.array([rng.uniform(-2, 2), rng.uniform(10, 40),
                        rng.uniform(0.05, 0.6), rng.uniform(0, 2 * np.pi)])
-        px, py, inside = _pixels(th, t, L, npix)
+        px, py, inside = _pixels(th, t, L, nc)
         if inside.sum() < 10:
             continue
         if bad[py[inside].astype(int), px[inside].astype(int)].any():
@@ -185,11 +193,15 @@ def test_gradient_vs_polynomial_point_source(ctx, m):
             tm[k] -= h[k]
             g[k] = (orc.chi2_theta(t, F, w, tp, s=s, q=q)[0] -
                     orc.chi2_theta(t, F, w, tm, s=s, q=q)[0]) / (2 * h[k])
-        rel.append(np.linalg.norm(grad[i] - g) / np.linalg.norm(g))
+        # components in natural units: t0, tE per tE; u0 per u0; alpha
+        sc = np.array([theta[i, 1], theta[i, 1], theta[i, 2], 1.0])
+        rel.append(np.linalg.norm((grad[i] - g) * sc) /
+                   np.linalg.norm(g * sc))
     rel = np.array(rel)
     print(f"map vs polynomial gradient: median rel {np.median(rel):.2e}, "
-          f"p90 {np.quantile(rel, 0.9):.2e}")
+          f"p90 {np.quantile(rel, 0.9):.2e}, max {rel.max():.2e}")
     assert np.median(rel) < 1e-2
+    assert np.quantile(rel, 0.9) < 1e-1
 
 
 def test_refine_lowers_chi2_and_matches_oracle(ctx, m, setup):

@@ -214,6 +214,32 @@ def test_map_single_lens_is_paczynski():
     assert abs(np.sum((A - P)[m]) / np.sum(P[m])) < 1e-3
 
 
+def test_poly_map_texel_centres():
+    # q -> 0: every texel centre carries the Paczynski closed form of its
+    # distance from the lens (§4.3 (ii)); index order is [row j, column i]
+    L, npix = 1.5, 12
+    P = orc.poly_map(1.0, 1e-12, L, npix, nthreads=4)
+    d = 2 * L / npix
+    for j in range(npix):
+        for i in range(npix):
+            r = math.hypot(-L + (i + 0.5) * d - 0.0, -L + (j + 0.5) * d)
+            assert P[j, i] == pytest.approx(orc.pspl(r), rel=1e-6)
+    # binary lens: agrees with the independent ray-shot map in smooth
+    # texels, to the pixel-averaging and shot-noise level
+    s, q, L, npix = 1.0, 1e-2, 1.0, 32
+    A, c, off, lost = orc.build_map(s, q, L, npix, 6000, 3.0, nthreads=8)
+    Pm = orc.poly_map(s, q, L, npix, nthreads=4)
+    Pa, G = _pixel_average(lambda a, b: orc.mag_point(s, q, a, b), L, npix, 6)
+    m = _smooth_mask(G, 1.1)
+    assert m.mean() > 0.5
+    # centre value vs texel average differ by < 1e-2 where max/min < 1.1
+    assert np.max(np.abs((Pa - Pm) / Pm)[m]) < 1e-2
+    rel = (A - Pm) / Pm
+    assert np.all(np.abs(rel[m]) <= 3.0 / np.sqrt(c[m]) + 1e-2)
+    # transposing the map (rows <-> columns) breaks it: the lens axis is y1
+    assert np.max(np.abs(Pm.T - A)[m]) > 5 * np.max(np.abs(Pm - A)[m])
+
+
 # ------------------------------------------------------------ lookup
 def test_lookup_reproduces_plane():
     npix, L = 16, 2.0
