@@ -45,8 +45,10 @@ UNIT = "traj-epoch evals/s"
 # equation sums 3, residual sweep 2.
 ALG_INSTR_PER_EVAL = 22
 FP32_LANES_PER_SM = 128
-KERNEL_SRC = os.path.join(ROOT, "paper_1511_01157_gb300", "csrc",
-                          "k_search.cu")
+# the search kernel's sources: its traffic record holds while they match
+KERNEL_SRC = [os.path.join(ROOT, "paper_1511_01157_gb300", "csrc", f)
+              for f in ("k_search.cu", "search_common.cuh",
+                        "morse_internal.cuh")]
 PROFILE = os.path.join(ROOT, "profiles", "k_search_cfg1.md")
 
 
@@ -149,12 +151,19 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SRC:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def recorded_traffic():
     """DRAM bytes per launch of the search kernel from the committed ncu
     summary, valid only while the kernel source is unchanged."""
     if not os.path.exists(PROFILE):
         return None
-    src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    src_hash = kernel_source_hash()
     bytes_, h = None, None
     for line in open(PROFILE):
         if line.startswith("traffic_bytes_per_launch:"):

@@ -13,6 +13,9 @@ names the passage of McDougall & Albrow (2015) it follows:
 * ``counts_to_mag``   -- map value = ray count x h^2 / Delta^2
 * ``quintic``/``roots5``/``images``/``mag_point`` -- §3 fifth-order lens
   polynomial, 3 or 5 images, A = sum 1/|det J| (Eq. 3-4)
+* ``mag_point_grad``  -- Eq. 2, 4 differentiated implicitly: dA/dy
+* ``chi2_grad_poly``  -- chi^2 gradient in (t0, tE, u0, alpha) of the
+  polynomial light curve, Fs and Fb profiled (Eq. 5-6, §4.2)
 * ``poly_map``        -- §4.1 point-source map from the polynomial per texel
 * ``pspl``            -- §4.3 (ii) Paczynski single-lens curve
 * ``traj_point``/``map_A`` -- §4.2 straight trajectory, bilinear map lookup
@@ -75,6 +78,9 @@ def _load():
         "orc_mag_point": (_D, [_D, _D, _D, _D, _P]),
         "orc_pspl": (_D, [_D]),
         "orc_poly_map": (None, [_D, _D, _D, _I, _P, _I]),
+        "orc_mag_point_grad": (_D, [_D, _D, _D, _D, _P]),
+        "orc_chi2_grad_poly": (_D, [_D, _D, _P, _P, _P, ctypes.c_long, _D, _D,
+                                    _D, _D, _P, _P, _P]),
         "orc_traj_point": (None, [_D, _D, _D, _D, _D, _P, _P]),
         "orc_map_A": (_D, [_P, _I, _D, _D, _D]),
         "orc_fit_A": (_D, [_P, _P, _P, ctypes.c_long, _P, _P, _P]),
@@ -184,6 +190,30 @@ def mag_point(s, q, y1, y2):
     """Point-source magnification sum_j 1/|det J_j| (§3 Eq. 3)."""
     n = ctypes.c_int()
     return _load().orc_mag_point(s, q, y1, y2, ctypes.byref(n))
+
+
+def mag_point_grad(s, q, y1, y2):
+    """(A, dA/dy1, dA/dy2) of the point source, by implicit differentiation
+    of the lens equation (Eq. 2, 4)."""
+    g = np.zeros(2)
+    a = _load().orc_mag_point_grad(float(s), float(q), float(y1), float(y2),
+                                   _ptr(g))
+    return a, g[0], g[1]
+
+
+def chi2_grad_poly(t, F, w, theta, s, q):
+    """(chi2, grad[4], Fs, Fb) of the polynomial point-source light curve of
+    theta = (t0, tE, u0, alpha), the flux fit profiled out (Eq. 5-6)."""
+    t = _f64(t)
+    F = _f64(F)
+    w = _f64(w)
+    g = np.zeros(4)
+    fs = ctypes.c_double()
+    fb = ctypes.c_double()
+    c = _load().orc_chi2_grad_poly(float(s), float(q), _ptr(t), _ptr(F),
+                                   _ptr(w), len(t), *[float(x) for x in theta],
+                                   _ptr(g), ctypes.byref(fs), ctypes.byref(fb))
+    return c, g, fs.value, fb.value
 
 
 def poly_map(s, q, L, npix, nthreads=1):

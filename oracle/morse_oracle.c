@@ -395,6 +395,41 @@ double orc_mag_point(double s, double q, double y1, double y2, int *nimg) {
   return A;
 }
 
+/* Gradient of the point-source magnification with respect to the source
+ * position, by implicit differentiation of Eq. 2 at each image.  With
+ * D = sum_k eps_k/(conj z - z_k)^2 and E = sum_k eps_k/(conj z - z_k)^3,
+ * Eq. 2 gives d zeta = dz + D d conj(z), so
+ *   dz = (d zeta - D conj(d zeta)) / (1 - |D|^2),
+ * and det J = 1 - |D|^2 (Eq. 4) moves by d det J = 4 Re(D conj(E) dz).
+ * A_j = 1/|det J_j| then changes by -sign(det J_j) d det J_j / det J_j^2.
+ * d zeta = 1 for y1 and i for y2.  Returns A; g[0] = dA/dy1, g[1] = dA/dy2. */
+double orc_mag_point_grad(double s, double q, double y1, double y2,
+                          double *g) {
+  double zre[5], zim[5], dj[5], res[5];
+  double e1, e2, xa, xb;
+  int n = orc_images(s, q, y1, y2, 1e-9, zre, zim, dj, res);
+  g[0] = g[1] = 0.0;
+  if (n < 0) return NAN;
+  orc_lens(s, q, &e1, &e2, &xa, &xb);
+  double A = 0.0;
+  for (int k = 0; k < n; ++k) {
+    cplx zc = zre[k] - I * zim[k];
+    cplx ua = zc - xa, ub = zc - xb;
+    cplx D = e1 / (ua * ua) + e2 / (ub * ub);
+    cplx E = e1 / (ua * ua * ua) + e2 / (ub * ub * ub);
+    double det = 1.0 - creal(D * conj(D));
+    double sg = det > 0.0 ? 1.0 : -1.0;
+    A += 1.0 / fabs(det);
+    for (int c = 0; c < 2; ++c) {
+      cplx dzeta = (c == 0) ? 1.0 : I;
+      cplx dz = (dzeta - D * conj(dzeta)) / det;
+      double ddet = 4.0 * creal(D * conj(E) * dz);
+      g[c] += -sg * ddet / (det * det);
+    }
+  }
+  return A;
+}
+
 /* Point-source map by the polynomial (§4.1: "solving the fifth-order
  * polynomial ... for a uniform grid of source positions"): texel (i, j)
  * holds the magnification at its centre (-L + (i+1/2) Delta, ...), rounded
@@ -517,6 +552,51 @@ double orc_chi2_theta(const float *Amap, int npix, double L, double s,
   int fl;
   double c = orc_fit_A(A, F, w, n, Fs, Fb, &fl);
   free(A);
+  return c;
+}
+
+/* chi^2 of the polynomial point-source light curve of one trajectory and
+ * its gradient in theta = (t0, tE, u0, alpha).  Fs and Fb are the least-
+ * squares solution (Eq. 5-6), so the partial derivatives of chi^2 in them
+ * vanish there and, with r_i = F_i - Fs A_i - Fb,
+ *   d chi^2 / d theta = sum_i -2 w_i r_i Fs (dA/dy1 dy1/dtheta
+ *                                            + dA/dy2 dy2/dtheta),
+ * where tau = (t - t0)/tE, y1 = tau cos(alpha) - u0 sin(alpha),
+ * y2 = tau sin(alpha) + u0 cos(alpha) (§4.2). */
+double orc_chi2_grad_poly(double s, double q, const double *t,
+                          const double *F, const double *w, long n,
+                          double t0, double tE, double u0, double alpha,
+                          double *grad, double *Fs, double *Fb) {
+  size_t m = (size_t)(n > 0 ? n : 1);
+  double *A = (double *)malloc(m * sizeof(double));
+  double *g1 = (double *)malloc(m * sizeof(double));
+  double *g2 = (double *)malloc(m * sizeof(double));
+  double ca = cos(alpha), sa = sin(alpha);
+  for (long i = 0; i < n; ++i) {
+    double y1, y2, g[2];
+    orc_traj_point(t[i], t0, tE, u0, alpha, &y1, &y2);
+    A[i] = orc_mag_point_grad(s, q, y1, y2, g);
+    g1[i] = g[0];
+    g2[i] = g[1];
+  }
+  int fl;
+  double c = orc_fit_A(A, F, w, n, Fs, Fb, &fl);
+  for (int k = 0; k < 4; ++k) grad[k] = 0.0;
+  for (long i = 0; i < n; ++i) {
+    double tau = (t[i] - t0) / tE;
+    double y1 = tau * ca - u0 * sa, y2 = tau * sa + u0 * ca;
+    double r = F[i] - *Fs * A[i] - *Fb;
+    double f = -2.0 * w[i] * r * *Fs;
+    /* d tau/d t0 = -1/tE, d tau/d tE = -tau/tE */
+    double dtau = g1[i] * ca + g2[i] * sa; /* dA/dtau */
+    grad[0] += f * dtau * (-1.0 / tE);
+    grad[1] += f * dtau * (-tau / tE);
+    grad[2] += f * (g1[i] * (-sa) + g2[i] * ca);
+    grad[3] += f * (g1[i] * (-y2) + g2[i] * y1);
+  }
+  free(A);
+  free(g1);
+  free(g2);
   return c;
 }
 

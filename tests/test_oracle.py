@@ -375,3 +375,69 @@ def test_grid_polynomial_mode_matches_lightcurve():
     for k in (0, 5, g.size - 1):
         Ak = orc.lightcurve_point(1.1, 0.01, t, *g.params(k))
         assert orc.fit_A(Ak, F, w)[0] == pytest.approx(chi2[k], rel=1e-12)
+
+
+# ------------------------------------------------------------ gradients
+@pytest.mark.parametrize("u", [0.05, 0.3, 1.0, 2.5])
+def test_mag_point_grad_single_lens_closed_form(u):
+    # q -> 0: grad A = A'(u) y/u with A'(u) = -8 / (u^2 (u^2 + 4)^(3/2))
+    y1, y2 = 0.6 * u, -0.8 * u
+    a, g1, g2 = orc.mag_point_grad(1.0, 1e-12, y1, y2)
+    d = -8.0 / (u * u * (u * u + 4.0) ** 1.5)
+    assert a == pytest.approx(orc.pspl(u), rel=1e-9)
+    assert g1 == pytest.approx(d * 0.6, rel=1e-7)
+    assert g2 == pytest.approx(-d * 0.8, rel=1e-7)
+
+
+@pytest.mark.parametrize("s,q", [(1.0, 1e-3), (0.7, 0.1), (1.3, 1.0)])
+def test_mag_point_grad_matches_differences(s, q):
+    rng = np.random.default_rng(11)
+    n = 0
+    for _ in range(120):
+        y1, y2 = rng.uniform(-1.5, 1.5, 2)
+        h = 1e-6
+        n_img = [orc.images(s, q, y1 + a, y2 + b)[0]
+                 for a, b in ((h, 0), (-h, 0), (0, h), (0, -h))]
+        if len(set(n_img)) != 1:
+            continue  # a caustic between the difference points
+        a, g1, g2 = orc.mag_point_grad(s, q, y1, y2)
+        f1 = (orc.mag_point(s, q, y1 + h, y2) -
+              orc.mag_point(s, q, y1 - h, y2)) / (2 * h)
+        f2 = (orc.mag_point(s, q, y1, y2 + h) -
+              orc.mag_point(s, q, y1, y2 - h)) / (2 * h)
+        assert math.hypot(g1 - f1, g2 - f2) <= 1e-6 * max(
+            math.hypot(f1, f2), 1.0) + 1e-7 * a / h
+        n += 1
+    assert n > 100
+
+
+def test_chi2_grad_poly_matches_differences_and_vanishes_at_truth():
+    s, q = 1.0, 5e-3
+    t = synth.epoch_times(120, 21)
+    t = t[np.abs(t) < 30]
+    truth = np.array([0.3, 18.0, 0.12, 0.9])
+    At = orc.lightcurve_point(s, q, t, *truth)
+    F = 1.3 * At + 0.4
+    w = np.full(len(t), 1e4)
+    c, g, fs, fb = orc.chi2_grad_poly(t, F, w, truth, s, q)
+    # noiseless: chi^2 = 0 and the gradient vanishes at the truth
+    assert c < 1e-16 and fs == pytest.approx(1.3) and fb == pytest.approx(0.4)
+    assert np.all(np.abs(g) < 1e-5)
+    rng = np.random.default_rng(4)
+    for _ in range(6):
+        th = truth * (1 + rng.uniform(-0.05, 0.05, 4))
+        c, g, fs, fb = orc.chi2_grad_poly(t, F, w, th, s, q)
+        assert c == pytest.approx(orc.chi2_theta(t, F, w, th, s=s, q=q)[0],
+                                  rel=1e-12)
+        for k in range(4):
+            h = 1e-6 * abs(th[k])
+            tp, tm = th.copy(), th.copy()
+            tp[k] += h
+            tm[k] -= h
+            fd = (orc.chi2_theta(t, F, w, tp, s=s, q=q)[0] -
+                  orc.chi2_theta(t, F, w, tm, s=s, q=q)[0]) / (2 * h)
+            assert g[k] == pytest.approx(fd, rel=1e-5, abs=1e-6 * c / h)
+        # a small step down the gradient lowers chi^2
+        sc = np.array([th[1], th[1], th[2], 1.0]) ** 2
+        step = 1e-4 * c / np.dot(g, g * sc) * g * sc
+        assert orc.chi2_theta(t, F, w, th - step, s=s, q=q)[0] < c
