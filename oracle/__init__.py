@@ -17,6 +17,8 @@ names the passage of McDougall & Albrow (2015) it follows:
 * ``chi2_grad_poly``  -- chi^2 gradient in (t0, tE, u0, alpha) of the
   polynomial light curve, Fs and Fb profiled (Eq. 5-6, §4.2)
 * ``poly_map``        -- §4.1 point-source map from the polynomial per texel
+* ``half_bits``/``half_value``/``log10_half``/``half_decode`` -- the FP16
+  log10 storage form of a map (IEEE binary16, round to nearest even)
 * ``pspl``            -- §4.3 (ii) Paczynski single-lens curve
 * ``traj_point``/``map_A`` -- §4.2 straight trajectory, bilinear map lookup
 * ``fit_A``           -- §4.1 Eq. 5-6 linear flux fit, chi^2 as a sum of
@@ -79,6 +81,10 @@ def _load():
         "orc_pspl": (_D, [_D]),
         "orc_poly_map": (None, [_D, _D, _D, _I, _P, _I]),
         "orc_mag_point_grad": (_D, [_D, _D, _D, _D, _P]),
+        "orc_half_bits": (ctypes.c_uint16, [_D]),
+        "orc_half_value": (_D, [ctypes.c_uint16]),
+        "orc_log10_half": (None, [_P, ctypes.c_longlong, _D, _P]),
+        "orc_half_decode": (None, [_P, ctypes.c_longlong, _P]),
         "orc_chi2_grad_poly": (_D, [_D, _D, _P, _P, _P, ctypes.c_long, _D, _D,
                                     _D, _D, _P, _P, _P]),
         "orc_traj_point": (None, [_D, _D, _D, _D, _D, _P, _P]),
@@ -214,6 +220,39 @@ def chi2_grad_poly(t, F, w, theta, s, q):
                                    _ptr(w), len(t), *[float(x) for x in theta],
                                    _ptr(g), ctypes.byref(fs), ctypes.byref(fb))
     return c, g, fs.value, fb.value
+
+
+def half_bits(x):
+    """IEEE binary16 bit pattern of x (round to nearest even)."""
+    return int(_load().orc_half_bits(float(x)))
+
+
+def half_value(h):
+    """Value of a binary16 bit pattern."""
+    return _load().orc_half_value(int(h))
+
+
+def log10_half(A, a_floor):
+    """FP16 storage codes of an FP32 map: half(log10(max(A, a_floor)))."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    codes = np.zeros(A.shape, dtype=np.uint16)
+    _load().orc_log10_half(_ptr(A), A.size, float(a_floor), _ptr(codes))
+    return codes
+
+
+def half_decode(codes):
+    """Decoded FP16 map: 10^x per code, rounded to FP32."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint16)
+    A = np.zeros(codes.shape, dtype=np.float32)
+    _load().orc_half_decode(_ptr(codes), codes.size, _ptr(A))
+    return A
+
+
+def half_floor(L, npix, nray, X):
+    """A_floor of a ray-shot map: half a ray, 0.5 h^2 / Delta^2."""
+    h = 2.0 * X / nray
+    d = 2.0 * L / npix
+    return 0.5 * h * h / (d * d)
 
 
 def poly_map(s, q, L, npix, nthreads=1):

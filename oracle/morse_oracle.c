@@ -27,6 +27,9 @@
  *   flux model + fit ...... §4.1 Eq. 5-6 (F = Fs A + Fb, linear in A), chi^2
  *                          as the sum of per-data-point contributions (§4.2)
  *   seeds (top-K) ......... §4.4 (best local minima of the coarse search)
+ *   FP16 log10 map ........ storage form of the map values: log10 A rounded
+ *                          to IEEE binary16 (round to nearest, ties to
+ *                          even), decoded as 10^x
  *
  * Readings where the paper is silent (all mirrored by the CUDA path and
  * listed in the design notes): cell-centred image rays; half-open source
@@ -446,6 +449,63 @@ void orc_poly_map(double s, double q, double L, int npix, float *A,
       A[(size_t)j * npix + i] = (float)orc_mag_point(
           s, q, -L + ((double)i + 0.5) * dlt, -L + ((double)j + 0.5) * dlt,
           NULL);
+}
+
+/* IEEE 754 binary16 encoding of a finite double, round to nearest with
+ * ties to even, from the format's definition: 1 sign bit, 5 exponent bits
+ * (bias 15), 10 fraction bits; normal values (1 + f/1024) 2^(E-15) for
+ * E = 1..30, subnormal values f 2^-24.  Magnitudes from 65520 up round to
+ * infinity.  frexp/ldexp scale exactly and rint rounds to nearest even in
+ * the default rounding mode, so the result is the correctly rounded one. */
+uint16_t orc_half_bits(double x) {
+  uint16_t sign = (signbit(x) ? 0x8000u : 0u);
+  double a = fabs(x);
+  if (a == 0.0) return sign;
+  if (a >= 65520.0) return sign | 0x7C00u;
+  int e;
+  frexp(a, &e); /* a = m 2^e, m in [0.5, 1): binade 2^(e-1) */
+  if (e - 1 >= -14) {
+    double sig = rint(ldexp(a, 11 - e)); /* in [1024, 2048] */
+    if (sig == 2048.0) {
+      sig = 1024.0;
+      e += 1;
+    }
+    int E = e - 1 + 15;
+    if (E >= 31) return sign | 0x7C00u;
+    return sign | (uint16_t)(E << 10) | (uint16_t)(sig - 1024.0);
+  }
+  /* subnormal (a rounded count of 2^-24 reaching 1024 is the smallest
+   * normal, whose bit pattern is that count) */
+  return sign | (uint16_t)rint(ldexp(a, 24));
+}
+
+/* binary16 bits -> double (exact). */
+double orc_half_value(uint16_t h) {
+  int E = (h >> 10) & 31, f = h & 1023;
+  double v;
+  if (E == 0)
+    v = ldexp((double)f, -24);
+  else if (E == 31)
+    v = f ? NAN : INFINITY;
+  else
+    v = ldexp((double)(1024 + f), E - 25);
+  return (h & 0x8000u) ? -v : v;
+}
+
+/* FP16 storage form of a map: code = half(log10(max(A, A_floor))) per
+ * texel, with A the FP32 map value. */
+void orc_log10_half(const float *A, long long n, double a_floor,
+                    uint16_t *codes) {
+  for (long long k = 0; k < n; ++k) {
+    double a = (double)A[k];
+    codes[k] = orc_half_bits(log10(a > a_floor ? a : a_floor));
+  }
+}
+
+/* Decoded FP16 map: A = 10^x of each code, rounded to FP32. */
+void orc_half_decode(const uint16_t *codes, long long n, float *A) {
+  for (long long k = 0; k < n; ++k)
+    A[k] = (float)pow(10.0, orc_half_value(codes[k]));
 }
 
 /* Single-lens (Paczynski) magnification A(u) = (u^2+2)/(u sqrt(u^2+4)). */

@@ -441,3 +441,50 @@ def test_chi2_grad_poly_matches_differences_and_vanishes_at_truth():
         sc = np.array([th[1], th[1], th[2], 1.0]) ** 2
         step = 1e-4 * c / np.dot(g, g * sc) * g * sc
         assert orc.chi2_theta(t, F, w, th - step, s=s, q=q)[0] < c
+
+
+# ------------------------------------------------------------ FP16 storage
+def test_half_bits_definition_points_and_ties():
+    cases = {0.0: 0x0000, 1.0: 0x3C00, -2.0: 0xC000, 65504.0: 0x7BFF,
+             65519.99: 0x7BFF, 65520.0: 0x7C00, 2.0 ** -14: 0x0400,
+             2.0 ** -24: 0x0001, 2.0 ** -25: 0x0000,   # tie -> even (0)
+             1.5 * 2.0 ** -24: 0x0002,                 # tie -> even (2)
+             1.0 + 2.0 ** -11: 0x3C00,                 # tie -> even
+             1.0 + 3 * 2.0 ** -11: 0x3C02,             # tie -> even
+             1.0 + 2.0 ** -11 + 2.0 ** -30: 0x3C01,    # above the tie
+             0.1: 0x2E66, 1.0 / 3.0: 0x3555}
+    for x, b in cases.items():
+        assert orc.half_bits(x) == b, (x, hex(orc.half_bits(x)))
+    for b in (0x0001, 0x03FF, 0x0400, 0x3C00, 0x3C01, 0x7BFF, 0xBC00):
+        assert orc.half_bits(orc.half_value(b)) == b
+
+
+def test_half_bits_match_numpy_float16():
+    # an independent implementation of the same IEEE rounding
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([rng.normal(0, 3, 20000),
+                         rng.uniform(-1e-5, 1e-5, 5000),
+                         10.0 ** rng.uniform(-9, 4.8, 5000)])
+    ours = np.array([orc.half_bits(x) for x in xs], dtype=np.uint16)
+    np.testing.assert_array_equal(ours, xs.astype(np.float16).view(np.uint16))
+
+
+def test_log10_half_quantisation_bound():
+    rng = np.random.default_rng(1)
+    A = (10.0 ** rng.uniform(-0.3, 3.0, 50000)).astype(np.float32)
+    A[:10] = 0.0   # empty texels take the floor
+    codes = orc.log10_half(A, 1e-3)
+    assert np.all(codes[:10] == orc.half_bits(-3.0))
+    dec = orc.half_decode(codes)
+    x = np.log10(A[10:].astype(np.float64))
+    # half rounding moves x by at most half an ulp of x: 2^-11 |x| relative
+    # for normal halves, so A moves by a factor 10^(2^-11 |x|) at most
+    # (plus the FP32 rounding of the decoded value)
+    bound = np.log(10) * np.maximum(2.0 ** -11 * np.abs(x), 2.0 ** -25) + 2e-7
+    rel = np.abs(dec[10:] / A[10:] - 1.0)
+    assert np.all(rel <= bound * 1.0001)
+    assert rel.max() > 0.5 * bound.max() * 0.5  # the bound is not vacuous
+    # A = 10^k for small k is exact in both directions
+    assert orc.half_decode(orc.log10_half(np.array([1.0, 10.0, 100.0],
+                                                   dtype=np.float32),
+                                          1e-3)).tolist() == [1.0, 10.0, 100.0]
