@@ -330,6 +330,7 @@ def run_gpu(args, cfg):
         pick = np.linspace(0, len(S) - 1, args.maps).round().astype(int)
         S, Q = S[pick].copy(), Q[pick].copy()
     n_maps = len(S)
+    fp16 = args.lookup == "fp16log"
     # weak scaling: every rank searches its own event over all 651 maps
     t, F, sig = make_event(ctx, m, cfg, cfg["seed"] + rank)
     ev = ctx.event(t, F, sig)
@@ -342,7 +343,8 @@ def run_gpu(args, cfg):
 
     def step():
         fits = ctx.sweep(ev, S, Q, cfg["L"], cfg["npix"], cfg["nray"], grid,
-                         image_halfwidth=cfg["X"], deflect="fp32")
+                         image_halfwidth=cfg["X"], deflect="fp32",
+                         fp16log=fp16)
         exact.append(ctx.exact_sweeps())
         return fits, [ctx.kernel_ms(i) for i in range(5)]
 
@@ -385,7 +387,7 @@ def run_gpu(args, cfg):
         for k in range(e2e_steps):
             ctx.search_sweep(tp, Fp, sp, 0.0, S, Q, cfg["L"], cfg["npix"],
                              cfg["nray"], grid, image_halfwidth=cfg["X"],
-                             deflect="fp32")
+                             deflect="fp32", fp16log=fp16)
         torch.cuda.synchronize()
         e2e_elapsed = max_over_ranks(time.perf_counter() - t0, world)
 
@@ -409,6 +411,7 @@ def run_gpu(args, cfg):
     if n_maps != cfg["n_s"] * cfg["n_q"]:
         cfg_line["maps_per_step"] = n_maps
         cfg_line["workload"] += f" (SUBSET: {n_maps} maps, profiling only)"
+    cfg_line["lookup"] = "FP16 log10 A table" if fp16 else "FP32 A table"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -473,6 +476,8 @@ def main():
     ap.add_argument("--ref-frac", type=float, default=0.002,
                     help="trajectory fraction per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lookup", default="fp32", choices=["fp32", "fp16log"],
+                    help="map table the search reads (the headline is fp32)")
     ap.add_argument("--maps", type=int, default=0,
                     help="search an evenly spaced subset of the 651 (s,q) "
                     "maps per step (profiling of small cases only)")

@@ -84,7 +84,8 @@ enum {
 };
 enum {
   MORSE_STORE_FP32 = 1,    /* FP32 A (always kept)                        */
-  MORSE_STORE_FP16LOG = 2  /* plus FP16 log10(max(A, A_floor)) texels     */
+  MORSE_STORE_FP16LOG = 2  /* plus FP16 log10(max(A, A_floor)) texels,
+                              which searches then read                    */
 };
 
 typedef struct {
@@ -128,6 +129,32 @@ morse_status morse_map_values(const morse_map *map, float *host_A);
 morse_status morse_map_info(const morse_map *map, int *npix, double *extent,
                             double *s, double *q);
 void morse_map_free(morse_map *map);
+
+/* FP16 storage form.  Next to the FP32 values a map can hold the table
+ * x = half(log10(max(A, A_floor))) per texel (IEEE binary16, round to
+ * nearest even; A_floor = half a ray, 0.5 h^2/Delta^2, for ray-shot maps
+ * and 1e-6 for maps from host values), packed as 2x2 neighbourhoods of
+ * 8 bytes per texel instead of 16.  A search through it decodes the four
+ * texels around each position to A = 10^x in FP32 and interpolates
+ * bilinearly in A, as on the FP32 map; sums and the solve are unchanged.
+ * The paper stores maps in single precision; this is a storage option of
+ * the GPU design, its error is the half quantisation of log10 A (relative
+ * error of A at most ln(10) 2^-11 |log10 A|).
+ *
+ * morse_map_set_lookup selects the table that morse_grid_chi2,
+ * morse_grid_chi2_dense, morse_grid_chi2_noalloc and morse_lightcurve read:
+ * MORSE_STORE_FP32 or MORSE_STORE_FP16LOG (computing the FP16 table from
+ * the current FP32 values if the map has none).  morse_build_map with
+ * opts->store including MORSE_STORE_FP16LOG builds both and selects FP16;
+ * morse_sweep and morse_search_sweep then search every map through its
+ * FP16 table.  The gradient and refine calls always read the FP32 values.
+ * Errors: EINVAL (unknown store value), ENOMEM, ECUDA. */
+morse_status morse_map_set_lookup(morse_map *map, int store);
+
+/* Copy the FP16 table (npix*npix uint16 codes, host, row-major like A) and
+ * A_floor.  Either pointer may be NULL.  Errors: EINVAL (no FP16 table). */
+morse_status morse_map_half(const morse_map *map, uint16_t *host_codes,
+                            double *a_floor);
 
 /* ------------------------------------------------------------------ */
 /* Light curves (§4.1 Eq. 5)                                            */

@@ -109,6 +109,8 @@ _SIGS = {
     "morse_map_values": (_S, [_P, _P]),
     "morse_map_info": (_S, [_P, _P, _P, _P, _P]),
     "morse_map_free": (None, [_P]),
+    "morse_map_set_lookup": (_S, [_P, _I]),
+    "morse_map_half": (_S, [_P, _P, _P]),
     "morse_event_create": (_S, [_P, _P, _P, _P, _I64, _D, _P]),
     "morse_event_free": (None, [_P]),
     "morse_event_info": (_S, [_P, _P, _P]),
@@ -285,15 +287,16 @@ class Context:
         return out
 
     def sweep(self, event, s, q, extent, npix, rays_per_axis, grid: Grid,
-              image_halfwidth=None, deflect="fp32"):
+              image_halfwidth=None, deflect="fp32", fp16log=False):
         """Full (s, q) search of a device-resident event (morse_sweep):
-        returns fits[n_maps, top_k]."""
+        returns fits[n_maps, top_k].  fp16log: search each map through its
+        FP16 log10 table."""
         s, q = _f64(s), _f64(q)
         if len(s) != len(q):
             raise ValueError("s and q lists differ in length")
         opts = MapOpts(float(image_halfwidth or 0.0),
                        DEFLECT_FP64 if deflect == "fp64" else DEFLECT_FP32,
-                       STORE_FP32)
+                       STORE_FP32 | (STORE_FP16LOG if fp16log else 0))
         out = np.zeros((len(s), grid.top_k), dtype=FIT_DTYPE)
         st = _lib.morse_sweep(self._h, event._h, _ptr(s), _ptr(q), len(s),
                               float(extent), int(npix), int(rays_per_axis),
@@ -304,7 +307,7 @@ class Context:
 
     def search_sweep(self, t, flux, sigma, t_ref, s, q, extent, npix,
                      rays_per_axis, grid: Grid, image_halfwidth=None,
-                     deflect="fp32"):
+                     deflect="fp32", fp16log=False):
         """morse_search_sweep: the full (s, q) search from host buffers."""
         t, flux, sigma = _f64(t), _f64(flux), _f64(sigma)
         s, q = _f64(s), _f64(q)
@@ -312,7 +315,7 @@ class Context:
             raise ValueError("s and q lists differ in length")
         opts = MapOpts(float(image_halfwidth or 0.0),
                        DEFLECT_FP64 if deflect == "fp64" else DEFLECT_FP32,
-                       STORE_FP32)
+                       STORE_FP32 | (STORE_FP16LOG if fp16log else 0))
         out = np.zeros((len(s), grid.top_k), dtype=FIT_DTYPE)
         st = _lib.morse_search_sweep(self._h, _ptr(t), _ptr(flux),
                                      _ptr(sigma), len(t), float(t_ref),
@@ -421,6 +424,22 @@ class Map:
         self.ctx._check(_lib.morse_map_values(self._h, _ptr(A)),
                         "morse_map_values")
         return A
+
+    def set_lookup(self, fp16log: bool):
+        """Search through the FP16 log10 table (built on demand) or the
+        FP32 values."""
+        self.ctx._check(_lib.morse_map_set_lookup(
+            self._h, STORE_FP16LOG if fp16log else STORE_FP32),
+            "morse_map_set_lookup")
+
+    def half(self):
+        """(FP16 codes [npix, npix] uint16, A_floor)."""
+        c = np.zeros((self.npix, self.npix), dtype=np.uint16)
+        f = ctypes.c_double()
+        self.ctx._check(_lib.morse_map_half(self._h, _ptr(c),
+                                            ctypes.byref(f)),
+                        "morse_map_half")
+        return c, f.value
 
     def free(self):
         if self._h:

@@ -15,6 +15,7 @@
 // with red.global.add, and the window is flushed with one global add per
 // non-empty bin.  Threads own 8x16-ray sub-blocks so that the 32 lanes of a
 // warp sit 8 rays (~1.2 pixels) apart and rarely hit the same bin.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -250,6 +251,37 @@ __global__ void k_quads_from_A(const float *__restrict__ A, int npix,
   }
 }
 
+// FP16 storage code of one FP32 value: log10 in FP64, rounded once to
+// binary16 (round to nearest even)
+__device__ __forceinline__ uint16_t half_code(float a, double a_floor) {
+  const double v = (double)a;
+  return __half_as_ushort(__double2half(log10(v > a_floor ? v : a_floor)));
+}
+
+__global__ void k_half_codes(const float *__restrict__ A, size_t n,
+                             double a_floor, uint16_t *__restrict__ codes) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x)
+    codes[k] = half_code(A[k], a_floor);
+}
+
+// (x00, x10) in .x and (x01, x11) in .y, low half first
+__global__ void k_half_quads(const uint16_t *__restrict__ codes, int npix,
+                             uint2 *__restrict__ quadh, int qpitch) {
+  size_t n = (size_t)npix * npix;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x) {
+    int x = (int)(k % npix), y = (int)(k / npix);
+    int x1 = min(x + 1, npix - 1), y1 = min(y + 1, npix - 1);
+    const unsigned c00 = codes[(size_t)y * npix + x];
+    const unsigned c10 = codes[(size_t)y * npix + x1];
+    const unsigned c01 = codes[(size_t)y1 * npix + x];
+    const unsigned c11 = codes[(size_t)y1 * npix + x1];
+    quadh[(size_t)y * qpitch + x] = make_uint2(c00 | (c10 << 16),
+                                               c01 | (c11 << 16));
+  }
+}
+
 }  // namespace
 
 static size_t ray_smem() { return sizeof(uint32_t) * kRayWin * kRayWin; }
@@ -302,6 +334,18 @@ cudaError_t launch_quads_from_A(const float *A, int npix, float4 *quad,
                                 int qpitch, cudaStream_t st) {
   size_t n = (size_t)npix * npix;
   k_quads_from_A<<<elementwise_grid(n), 256, 0, st>>>(A, npix, quad, qpitch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_half_from_A(const float *A, int npix, double a_floor,
+                               uint16_t *codes, uint2 *quadh, int qpitch,
+                               cudaStream_t st) {
+  size_t n = (size_t)npix * npix;
+  k_half_codes<<<elementwise_grid(n), 256, 0, st>>>(A, n, a_floor, codes);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_half_quads<<<elementwise_grid(n), 256, 0, st>>>(codes, npix, quadh,
+                                                    qpitch);
   return cudaGetLastError();
 }
 

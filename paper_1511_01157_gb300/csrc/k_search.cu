@@ -155,7 +155,7 @@ __device__ void warp_merge(const SearchParams &P, BlockTopK &T, const int K,
   __syncwarp();
 }
 
-template <bool DENSE, bool EP_SMEM>
+template <bool DENSE, bool EP_SMEM, bool H>
 __global__ void __launch_bounds__(kSearchWarps * 32, 1)
     k_search(const SearchParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -235,11 +235,11 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
       if (k + 1 < nvalid) {
         const TrajC cb = shfl_traj(mine, k + 1);
         Acc ra, rb;
-        phase1_pair(P, ep, ca, cb, lane, ra, rb);
+        phase1_pair<H>(P, ep, ca, cb, lane, ra, rb);
         if (lane == k) mine_s = ra;
         if (lane == k + 1) mine_s = rb;
       } else {
-        const Acc ra = phase1(P, ep, ca, lane);
+        const Acc ra = phase1<H>(P, ep, ca, lane);
         if (lane == k) mine_s = ra;
       }
     }
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
       const TrajC c = shfl_traj(mine, k);
       const float Fs = __shfl_sync(kFull, myFs, k);
       const float Bc = __shfl_sync(kFull, myBc, k);
-      const double chi2 = phase2(P, ep, c, lane, Fs, Bc);
+      const double chi2 = phase2<H>(P, ep, c, lane, Fs, Bc);
       if (lane == k) my_chi2 = isnan(chi2) ? CUDART_INF : chi2;
     }
     if (DENSE) {
@@ -335,6 +335,7 @@ __global__ void k_merge_level(const Entry *__restrict__ in,
 // Fit fill: one warp per selected trajectory recomputes the phase-1 sums,
 // the solve and the phase-2 chi^2 with the same device functions as the
 // search, and writes the public morse_fit record.
+template <bool H>
 __global__ void k_fill(const FillParams F) {
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -355,9 +356,9 @@ __global__ void k_fill(const FillParams F) {
     return;
   }
   const TrajC c = traj_consts(P, P.ep, e.idx);
-  const Acc s = phase1(P, P.ep, c, lane);
+  const Acc s = phase1<H>(P, P.ep, c, lane);
   const Solved sol = solve2(P, (double)s.a, (double)s.b, (double)s.d);
-  const double chi2 = phase2(P, P.ep, c, lane, __double2float_rn(sol.Fs),
+  const double chi2 = phase2<H>(P, P.ep, c, lane, __double2float_rn(sol.Fs),
                              __double2float_rn(sol.Bc));
   if (lane == 0) {
     long long q = e.idx;
@@ -393,6 +394,7 @@ __global__ void k_seed_threshold(const Entry *sel, int k,
 
 // A(t) along one trajectory given by (ax, bx, ay, by) with v = a t + b, and
 // tau = kt t + bt, u0^2 for the single-lens part outside the map.
+template <bool H>
 __global__ void k_lightcurve(const SearchParams P, float ax, float bx,
                              float ay, float by, float kt, float bt, float u02,
                              const float *__restrict__ t, int n,
@@ -404,7 +406,8 @@ __global__ void k_lightcurve(const SearchParams P, float ax, float bx,
     const bool inside =
         (vx > P.vlo) & (vx < P.vhi) & (vy > P.vlo) & (vy < P.vhi);
     if (inside) {
-      A[i] = __fadd_rn(bilinear_m1(P, vx, vy), 1.f);
+      A[i] = __fadd_rn(H ? bilinear_h_m1(P, vx, vy) : bilinear_m1(P, vx, vy),
+                       1.f);
     } else {
       const float tau = __fmaf_rn(kt, t[i], bt);
       A[i] = pspl_u2(__fmaf_rn(tau, tau, u02));
@@ -423,9 +426,9 @@ size_t search_smem_bytes(int n_ep_smem, int top_k) {
 #define MORSE_SMEM_CARVEOUT 1
 #endif
 
-template <bool D, bool E>
+template <bool D, bool E, bool H>
 static int occupancy(size_t smem) {
-  cudaFuncSetAttribute(k_search<D, E>,
+  cudaFuncSetAttribute(k_search<D, E, H>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 #if MORSE_SMEM_CARVEOUT
   // ask for the smallest shared-memory carveout that holds the block, so
@@ -437,37 +440,52 @@ static int occupancy(size_t smem) {
   if (optin > 0) {
     int pct = (int)((100.0 * (double)(smem + 2048)) / (double)optin) + 1;
     if (pct > 100) pct = 100;
-    cudaFuncSetAttribute(k_search<D, E>,
+    cudaFuncSetAttribute(k_search<D, E, H>,
                          cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   }
 #endif
   int b = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &b, k_search<D, E>, kSearchWarps * 32, smem) != cudaSuccess) {
+          &b, k_search<D, E, H>, kSearchWarps * 32, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return b;
 }
 
-int search_blocks_per_sm(bool dense, bool ep_smem, size_t smem) {
-  if (dense && ep_smem) return occupancy<true, true>(smem);
-  if (dense) return occupancy<true, false>(smem);
-  if (ep_smem) return occupancy<false, true>(smem);
-  return occupancy<false, false>(smem);
+template <bool H>
+static int occupancy_h(bool dense, bool ep_smem, size_t smem) {
+  if (dense && ep_smem) return occupancy<true, true, H>(smem);
+  if (dense) return occupancy<true, false, H>(smem);
+  if (ep_smem) return occupancy<false, true, H>(smem);
+  return occupancy<false, false, H>(smem);
+}
+
+int search_blocks_per_sm(bool dense, bool ep_smem, bool h16, size_t smem) {
+  return h16 ? occupancy_h<true>(dense, ep_smem, smem)
+             : occupancy_h<false>(dense, ep_smem, smem);
+}
+
+template <bool H>
+static void launch_search_h(const SearchParams &P, bool dense, bool ep_smem,
+                            int grid, size_t smem, cudaStream_t st) {
+  const int threads = kSearchWarps * 32;
+  if (dense && ep_smem)
+    k_search<true, true, H><<<grid, threads, smem, st>>>(P);
+  else if (dense)
+    k_search<true, false, H><<<grid, threads, smem, st>>>(P);
+  else if (ep_smem)
+    k_search<false, true, H><<<grid, threads, smem, st>>>(P);
+  else
+    k_search<false, false, H><<<grid, threads, smem, st>>>(P);
 }
 
 cudaError_t launch_search(const SearchParams &P, bool dense, bool ep_smem,
                           int grid, size_t smem, cudaStream_t st) {
-  const int threads = kSearchWarps * 32;
-  if (dense && ep_smem)
-    k_search<true, true><<<grid, threads, smem, st>>>(P);
-  else if (dense)
-    k_search<true, false><<<grid, threads, smem, st>>>(P);
-  else if (ep_smem)
-    k_search<false, true><<<grid, threads, smem, st>>>(P);
+  if (P.quadh)
+    launch_search_h<true>(P, dense, ep_smem, grid, smem, st);
   else
-    k_search<false, false><<<grid, threads, smem, st>>>(P);
+    launch_search_h<false>(P, dense, ep_smem, grid, smem, st);
   return cudaGetLastError();
 }
 
@@ -496,7 +514,10 @@ cudaError_t launch_topk_merge(Entry *a, Entry *b, int lists, int k,
 cudaError_t launch_fill(const FillParams &F, cudaStream_t st) {
   const int threads = 256;
   const int blocks = (F.k * 32 + threads - 1) / threads;
-  k_fill<<<blocks, threads, 0, st>>>(F);
+  if (F.S.quadh)
+    k_fill<true><<<blocks, threads, 0, st>>>(F);
+  else
+    k_fill<false><<<blocks, threads, 0, st>>>(F);
   return cudaGetLastError();
 }
 
@@ -513,8 +534,12 @@ cudaError_t launch_lightcurve(const SearchParams &P, float ax, float bx,
   int blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  k_lightcurve<<<blocks, 256, 0, st>>>(P, ax, bx, ay, by, kt, bt, u02, t, n,
-                                       A);
+  if (P.quadh)
+    k_lightcurve<true><<<blocks, 256, 0, st>>>(P, ax, bx, ay, by, kt, bt, u02,
+                                               t, n, A);
+  else
+    k_lightcurve<false><<<blocks, 256, 0, st>>>(P, ax, bx, ay, by, kt, bt,
+                                                u02, t, n, A);
   return cudaGetLastError();
 }
 

@@ -143,6 +143,7 @@ struct BuildSpec {
   int npix;
   int64_t nray;
   bool fp64;
+  bool fp16;  // also write the FP16 log10 table and search through it
 };
 
 morse_status check_build(morse_ctx *ctx, double s, double q, double extent,
@@ -167,8 +168,9 @@ morse_status check_build(morse_ctx *ctx, double s, double q, double extent,
       return fail(ctx, MORSE_EINVAL, "unknown deflect mode %d", deflect);
     if (store & ~(MORSE_STORE_FP32 | MORSE_STORE_FP16LOG))
       return fail(ctx, MORSE_EINVAL, "unknown store flags %d", store);
-    if (store & MORSE_STORE_FP16LOG)
-      return fail(ctx, MORSE_EUNSUPPORTED, "FP16 log10 maps not built yet");
+    b->fp16 = (store & MORSE_STORE_FP16LOG) != 0;
+  } else {
+    b->fp16 = false;
   }
   b->s = s;
   b->q = q;
@@ -207,8 +209,38 @@ morse_map *map_alloc(morse_ctx *ctx, int npix, bool counts) {
   return m;
 }
 
+// FP16 table storage of a map (allocated on first use)
+bool map_ensure_half(morse_map *m) {
+  if (m->quadh) return true;
+  size_t n = (size_t)m->npix * m->npix;
+  if (cudaMalloc(&m->hcodes, n * sizeof(uint16_t)) != cudaSuccess ||
+      cudaMalloc(&m->quadh, (size_t)m->npix * m->qpitch * sizeof(uint2)) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    if (m->hcodes) cudaFree(m->hcodes);
+    m->hcodes = nullptr;
+    m->quadh = nullptr;
+    return false;
+  }
+  return true;
+}
+
+// Queue the FP16 table of the map's current FP32 values.
+morse_status enqueue_half(morse_ctx *ctx, morse_map *m) {
+  if (!map_ensure_half(m))
+    return fail(ctx, MORSE_ENOMEM, "FP16 table of %d^2 texels", m->npix);
+  MORSE_CUDA(ctx, morse::launch_half_from_A(m->A, m->npix, m->a_floor,
+                                            m->hcodes, m->quadh, m->qpitch,
+                                            ctx->stream));
+  ctx->launches += 2;
+  m->half_valid = true;
+  return MORSE_OK;
+}
+
 void map_release(morse_map *m) {
   if (!m) return;
+  if (m->hcodes) cudaFree(m->hcodes);
+  if (m->quadh) cudaFree(m->quadh);
   if (m->A) cudaFree(m->A);
   if (m->quad) cudaFree(m->quad);
   if (m->tot) cudaFree(m->tot);
@@ -266,6 +298,14 @@ morse_status enqueue_build(morse_ctx *ctx, morse_map *m, const BuildSpec &b) {
   MORSE_CUDA(ctx, morse::launch_counts_to_map(m->counts, b.npix, f, m->A,
                                               m->quad, m->qpitch,
                                               ctx->stream));
+  // FP16 floor: half a ray, 0.5 h^2 / Delta^2
+  m->a_floor = 0.5 * f;
+  m->half_valid = false;
+  m->lookup = MORSE_STORE_FP32;
+  if (b.fp16) {
+    MORSE_TRY(enqueue_half(ctx, m));
+    m->lookup = MORSE_STORE_FP16LOG;
+  }
   t_end(ctx, r);
   ctx->launches += 1;
   return MORSE_OK;
@@ -327,6 +367,7 @@ morse_status upload_tables(morse_ctx *ctx, const morse_grid *g, double t_ref,
 void map_params(const morse_map *map, morse::SearchParams *P) {
   const double dlt = (2.0 * map->L) / (double)map->npix;
   P->quad = map->quad;
+  P->quadh = morse::map_h16(map) ? map->quadh : nullptr;
   P->qpitch = map->qpitch;
   P->qidx0 = (unsigned)(map->npix / 2 - 0x4B400000) *
              (unsigned)(map->qpitch + 1);
@@ -432,8 +473,8 @@ morse_status hdr_check(morse_ctx *ctx, const Hdr &h) {
 
 morse_status plan_search(morse_ctx *ctx, const morse_event *ev,
                          const morse_grid *g, long long first,
-                         long long count, bool dense, long long n_out,
-                         Plan *pl) {
+                         long long count, bool dense, bool h16,
+                         long long n_out, Plan *pl) {
   const int K = dense ? 1 : g->top_k;
   const size_t fixed = morse::search_smem_bytes(0, dense ? 0 : K) -
                        (dense ? sizeof(Entry) * morse::kSearchWarps * 32 : 0);
@@ -441,7 +482,7 @@ morse_status plan_search(morse_ctx *ctx, const morse_event *ev,
   const bool ep_smem =
       budget > fixed && (size_t)ev->n <= (budget - fixed) / sizeof(float4);
   const size_t smem = fixed + (ep_smem ? sizeof(float4) * (size_t)ev->n : 0);
-  const int bps = morse::search_blocks_per_sm(dense, ep_smem, smem);
+  const int bps = morse::search_blocks_per_sm(dense, ep_smem, h16, smem);
   if (bps < 1)
     return fail(ctx, MORSE_EUNSUPPORTED,
                 "search kernel does not fit (epochs %lld, top_k %d)",
@@ -557,8 +598,11 @@ morse_status sweep_impl(morse_ctx *ctx, const morse_event *ev,
   }
   morse_map *m = ctx->sweep_map;
   m->L = extent;
+  const bool h16 = n_maps > 0 && specs[0].fp16;
+  if (h16 && !map_ensure_half(m))
+    return fail(ctx, MORSE_ENOMEM, "FP16 table of %d^2 texels", npix);
   Plan pl;
-  MORSE_TRY(plan_search(ctx, ev, grid, 0, grid_size(grid), false, n_maps,
+  MORSE_TRY(plan_search(ctx, ev, grid, 0, grid_size(grid), false, h16, n_maps,
                         &pl));
   void *ws = nullptr;
   MORSE_TRY(ws_reserve(ctx, pl.bytes, &ws));
@@ -569,6 +613,7 @@ morse_status sweep_impl(morse_ctx *ctx, const morse_event *ev,
   morse::SearchParams P;
   memset(&P, 0, sizeof(P));
   map_params(m, &P);
+  P.quadh = h16 ? m->quadh : nullptr;  // written by each build below
   event_params(ev, &P);
   grid_params(grid, T, &P);
   P.first = 0;
@@ -738,6 +783,8 @@ morse_status morse_map_from_host(morse_ctx *ctx, const float *A, int npix,
   morse_map *m = map_alloc(ctx, npix, false);
   if (!m) return fail(ctx, MORSE_ENOMEM, "map of %d^2 texels", npix);
   m->L = extent;
+  m->a_floor = 1e-6;
+  m->lookup = MORSE_STORE_FP32;
   cudaError_t e = cudaMemcpyAsync(m->A, A, n * sizeof(float),
                                   cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) {
@@ -790,6 +837,43 @@ morse_status morse_map_info(const morse_map *map, int *npix, double *extent,
   if (extent) *extent = map->L;
   if (s) *s = map->s;
   if (q) *q = map->q;
+  return MORSE_OK;
+}
+
+morse_status morse_map_set_lookup(morse_map *map, int store) {
+  if (!map) return MORSE_EINVAL;
+  morse_ctx *ctx = map->ctx;
+  if (store == MORSE_STORE_FP32) {
+    map->lookup = MORSE_STORE_FP32;
+    return MORSE_OK;
+  }
+  if (store != MORSE_STORE_FP16LOG)
+    return fail(ctx, MORSE_EINVAL, "lookup must be MORSE_STORE_FP32 or "
+                "MORSE_STORE_FP16LOG, not %d", store);
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (!map->half_valid) {
+    call_begin(ctx);
+    MORSE_TRY(enqueue_half(ctx, map));
+    MORSE_TRY(sync_and_collect(ctx, "FP16 table"));
+  }
+  map->lookup = MORSE_STORE_FP16LOG;
+  return MORSE_OK;
+}
+
+morse_status morse_map_half(const morse_map *map, uint16_t *host_codes,
+                            double *a_floor) {
+  if (!map) return MORSE_EINVAL;
+  morse_ctx *ctx = map->ctx;
+  if (!map->half_valid)
+    return fail(ctx, MORSE_EINVAL, "map has no FP16 table");
+  if (a_floor) *a_floor = map->a_floor;
+  if (host_codes) {
+    size_t n = (size_t)map->npix * map->npix;
+    MORSE_CUDA(ctx, cudaMemcpyAsync(host_codes, map->hcodes,
+                                    n * sizeof(uint16_t),
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+    MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   return MORSE_OK;
 }
 
@@ -907,7 +991,8 @@ morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
   MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
   call_begin(ctx);
   Plan pl;
-  MORSE_TRY(plan_search(ctx, ev, grid, 0, grid_size(grid), false, 1, &pl));
+  MORSE_TRY(plan_search(ctx, ev, grid, 0, grid_size(grid), false,
+                        morse::map_h16(map), 1, &pl));
   void *ws = nullptr;
   MORSE_TRY(ws_reserve(ctx, pl.bytes, &ws));
   char *base = (char *)ws;
@@ -951,7 +1036,8 @@ morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
   MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
   call_begin(ctx);
   Plan pl;
-  MORSE_TRY(plan_search(ctx, ev, grid, first, count, true, count, &pl));
+  MORSE_TRY(plan_search(ctx, ev, grid, first, count, true,
+                        morse::map_h16(map), count, &pl));
   void *ws = nullptr;
   MORSE_TRY(ws_reserve(ctx, pl.bytes, &ws));
   char *base = (char *)ws;

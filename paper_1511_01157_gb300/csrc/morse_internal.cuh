@@ -45,6 +45,14 @@ struct morse_map {
                             // a steep track over cache sets)
   unsigned long long *tot;  // [2] off-map, lost (device)
   uint64_t off_map, lost;
+  // FP16 storage form (present when built with MORSE_STORE_FP16LOG or
+  // selected later): half(log10(max(A, a_floor))) per texel, and the same
+  // 2x2 neighbourhoods as quad packed as four halves (8 bytes)
+  uint16_t *hcodes;         // [npix*npix]
+  uint2 *quadh;             // [npix rows x qpitch]
+  double a_floor;           // half a ray (ray-shot maps), else 1e-6
+  bool half_valid;          // the FP16 table holds the current values
+  int lookup;               // MORSE_STORE_FP32 or MORSE_STORE_FP16LOG
 };
 
 struct morse_event {
@@ -58,6 +66,12 @@ struct morse_event {
 namespace morse {
 
 // ---------------------------------------------------------------- maps
+// searches read the FP16 log10 table
+inline bool map_h16(const morse_map *m) {
+  return m->lookup == MORSE_STORE_FP16LOG && m->quadh != nullptr &&
+         m->half_valid;
+}
+
 struct RayParams {
   double e1, e2, xa, xb;    // lens mass fractions and positions
   double X, h, L, dlt;      // image half-width, ray spacing, map half-width,
@@ -90,6 +104,10 @@ cudaError_t launch_counts_to_map(const uint32_t *counts, int npix, double f,
                                  cudaStream_t st);
 cudaError_t launch_quads_from_A(const float *A, int npix, float4 *quad,
                                 int qpitch, cudaStream_t st);
+// FP16 form from the FP32 values: codes, then their 2x2 quads
+cudaError_t launch_half_from_A(const float *A, int npix, double a_floor,
+                               uint16_t *codes, uint2 *quadh, int qpitch,
+                               cudaStream_t st);
 int rayshoot_blocks_per_sm();
 
 // ---------------------------------------------------------------- search
@@ -99,8 +117,10 @@ struct Entry {
 };
 
 struct SearchParams {
-  // map
+  // map: the lookup reads quadh (FP16 log10 quads) when it is set, else
+  // quad (FP32 A - 1 quads); both share qpitch and the index folding
   const float4 *quad;
+  const uint2 *quadh;
   int npix, half;           // npix, npix/2
   int qpitch;               // quad row pitch (float4 units)
   unsigned qidx0;           // quad index offset for the raw floor bits:
@@ -181,7 +201,8 @@ inline long long main_groups(long long line, long long first,
 }
 
 size_t search_smem_bytes(int n_ep_smem, int top_k);
-int search_blocks_per_sm(bool dense, bool ep_smem, size_t smem);
+int search_blocks_per_sm(bool dense, bool ep_smem, bool h16, size_t smem);
+// (the FP16 kernels are chosen when P.quadh is set)
 cudaError_t launch_search(const SearchParams &P, bool dense, bool ep_smem,
                           int grid, size_t smem, cudaStream_t st);
 // Merge `lists` sorted lists of `k` entries (ping-pong between a and b) into

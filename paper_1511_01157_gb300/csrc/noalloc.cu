@@ -103,7 +103,8 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   const bool ep_smem =
       budget > fixed && (size_t)ev->n <= (budget - fixed) / sizeof(float4);
   const size_t smem = fixed + (ep_smem ? sizeof(float4) * (size_t)ev->n : 0);
-  const int bps = morse::search_blocks_per_sm(false, ep_smem, smem);
+  const bool h16 = morse::map_h16(map);
+  const int bps = morse::search_blocks_per_sm(false, ep_smem, h16, smem);
   if (bps < 1)
     return set_err(ctx, MORSE_EUNSUPPORTED, "search kernel does not fit");
   long long groups =
@@ -180,6 +181,7 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   morse::SearchParams P;
   memset(&P, 0, sizeof(P));
   P.quad = map->quad;
+  P.quadh = h16 ? map->quadh : nullptr;
   P.qpitch = map->qpitch;
   P.qidx0 = (unsigned)(map->npix / 2 - 0x4B400000) *
             (unsigned)(map->qpitch + 1);

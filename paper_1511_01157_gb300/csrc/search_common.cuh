@@ -8,6 +8,7 @@
 // F = Fs A + Fb (Eq. 5-6) and chi^2 as the sum of per-point contributions.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
@@ -152,6 +153,41 @@ __device__ __forceinline__ float pspl_u2(float u2) {
                    rsqrt_approx(__fmul_rn(u2, __fadd_rn(u2, 4.f))));
 }
 
+// Texel-quad index and bilinear fractions of centred coordinates (vx, vy)
+// (clamped below to the first texel centre; the caller keeps them below
+// the last).
+struct TexPos {
+  unsigned idx;
+  float fx, fy;
+};
+
+__device__ __forceinline__ bool tex_pos(const SearchParams &P, float vx,
+                                        float vy, TexPos &o) {
+  const float cx = fmaxf(vx, P.vmin);
+  const float cy = fmaxf(vy, P.vmin);
+  // floor: adding 1.5 * 2^23 rounding down leaves floor(c) in the low
+  // mantissa bits; the fraction c - floor(c) is exact
+  const float tx = __fadd_rd(cx, 12582912.f), ty = __fadd_rd(cy, 12582912.f);
+  o.fx = __fsub_rn(cx, __fsub_rn(tx, 12582912.f));
+  o.fy = __fsub_rn(cy, __fsub_rn(ty, 12582912.f));
+  // texel (ix, iy) = floor(c) + half; quad index iy * qpitch + ix, folded
+  // into one multiply-add on the raw bit patterns (mod 2^32, exact because
+  // the index is in [0, npix * qpitch))
+  const unsigned bx = (unsigned)__float_as_int(tx);
+  const unsigned by = (unsigned)__float_as_int(ty);
+  o.idx = by * (unsigned)P.qpitch + bx + P.qidx0;
+#ifdef MORSE_CHECK_BOUNDS
+  // checked build: record an out-of-range texel and skip the access
+  const int ix = (int)(bx - 0x4B400000u) + P.half;
+  const int iy = (int)(by - 0x4B400000u) + P.half;
+  if ((unsigned)ix >= (unsigned)P.npix || (unsigned)iy >= (unsigned)P.npix) {
+    if (P.err) atomicOr(P.err, 2u);
+    return false;
+  }
+#endif
+  return true;
+}
+
 // Bilinear A - 1 at centred coordinates inside the map (the quads store
 // A - 1).  Coordinates below the first texel centre are clamped to it (the
 // lookup rule).  Above the last centre no clamp is needed: the caller only
@@ -160,29 +196,10 @@ __device__ __forceinline__ float pspl_u2(float u2) {
 // verifies the index range.
 __device__ __forceinline__ float bilinear_m1(const SearchParams &P, float vx,
                                              float vy) {
-  const float cx = fmaxf(vx, P.vmin);
-  const float cy = fmaxf(vy, P.vmin);
-  // floor: adding 1.5 * 2^23 rounding down leaves floor(c) in the low
-  // mantissa bits; the fraction c - floor(c) is exact
-  const float tx = __fadd_rd(cx, 12582912.f), ty = __fadd_rd(cy, 12582912.f);
-  const float fx = __fsub_rn(cx, __fsub_rn(tx, 12582912.f));
-  const float fy = __fsub_rn(cy, __fsub_rn(ty, 12582912.f));
-  // texel (ix, iy) = floor(c) + half; quad index iy * qpitch + ix, folded
-  // into one multiply-add on the raw bit patterns (mod 2^32, exact because
-  // the index is in [0, npix * qpitch))
-  const unsigned bx = (unsigned)__float_as_int(tx);
-  const unsigned by = (unsigned)__float_as_int(ty);
-  const unsigned idx = by * (unsigned)P.qpitch + bx + P.qidx0;
-#ifdef MORSE_CHECK_BOUNDS
-  // checked build: record an out-of-range texel and skip the access
-  const int ix = (int)(bx - 0x4B400000u) + P.half;
-  const int iy = (int)(by - 0x4B400000u) + P.half;
-  if ((unsigned)ix >= (unsigned)P.npix || (unsigned)iy >= (unsigned)P.npix) {
-    if (P.err) atomicOr(P.err, 2u);
-    return 0.f;
-  }
-#endif
-  const float4 q = __ldg(&P.quad[idx]);
+  TexPos t;
+  if (!tex_pos(P, vx, vy, t)) return 0.f;
+  const float fx = t.fx, fy = t.fy;
+  const float4 q = __ldg(&P.quad[t.idx]);
   const float r0 = __fmaf_rn(fx, __fsub_rn(q.y, q.x), q.x);
   const float r1 = __fmaf_rn(fx, __fsub_rn(q.w, q.z), q.z);
   return __fmaf_rn(fy, __fsub_rn(r1, r0), r0);
@@ -208,29 +225,62 @@ __device__ __forceinline__ void acc_add(Acc &s, const float4 &v, float Ac) {
   s.d = __fmaf_rn(v.z, Ac, s.d);
 }
 
+// 10^x for a decoded FP16 log10 texel: one hardware base-2 exponential
+// of x log2(10) (relative error a few FP32 ulps, far below the half
+// quantisation of x)
+__device__ __forceinline__ float exp10_texel(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x * 3.32192809488736234787f));
+  return y;
+}
+
+// FP16 map: the four log10 texels of the quad are decoded to A = 10^x in
+// FP32 and interpolated in A, the same bilinear as the FP32 map; A - 1 is
+// returned as there.
+__device__ __forceinline__ float bilinear_h_m1(const SearchParams &P,
+                                               float vx, float vy) {
+  TexPos t;
+  if (!tex_pos(P, vx, vy, t)) return 0.f;
+  const uint2 q = __ldg(&P.quadh[t.idx]);
+  const float2 lo = __half22float2(
+      __halves2half2(__ushort_as_half((unsigned short)(q.x & 0xffffu)),
+                     __ushort_as_half((unsigned short)(q.x >> 16))));
+  const float2 hi = __half22float2(
+      __halves2half2(__ushort_as_half((unsigned short)(q.y & 0xffffu)),
+                     __ushort_as_half((unsigned short)(q.y >> 16))));
+  const float a00 = exp10_texel(lo.x), a10 = exp10_texel(lo.y);
+  const float a01 = exp10_texel(hi.x), a11 = exp10_texel(hi.y);
+  const float r0 = __fmaf_rn(t.fx, __fsub_rn(a10, a00), a00);
+  const float r1 = __fmaf_rn(t.fx, __fsub_rn(a11, a01), a01);
+  return __fsub_rn(__fmaf_rn(t.fy, __fsub_rn(r1, r0), r0), 1.f);
+}
+
 // A - 1 at time t inside the map (bilinear) or outside (single lens)
+// (H: the FP16 log10 table)
+template <bool H>
 __device__ __forceinline__ float mag_in_m1(const SearchParams &P,
                                            const TrajC &c, float t) {
-  return bilinear_m1(P, __fmaf_rn(c.ax, t, c.bx), __fmaf_rn(c.ay, t, c.by));
+  const float vx = __fmaf_rn(c.ax, t, c.bx), vy = __fmaf_rn(c.ay, t, c.by);
+  return H ? bilinear_h_m1(P, vx, vy) : bilinear_m1(P, vx, vy);
 }
 __device__ __forceinline__ float mag_out_m1(const TrajC &c, float t) {
   const float tau = __fmaf_rn(c.kt, t, c.bt);
   return __fsub_rn(pspl_u2(__fmaf_rn(tau, tau, c.u02)), 1.f);
 }
 
-template <bool IN>
+template <bool H, bool IN>
 __device__ __forceinline__ void seg1(const SearchParams &P, const float4 *ep,
                                      const TrajC &c, int lane, int e0, int e1,
                                      Acc &s) {
 #pragma unroll (IN ? kUnroll : 2)
   for (int e = lane_start(e0, lane); e < e1; e += 32) {
     const float4 v = ep[e];
-    acc_add(s, v, IN ? mag_in_m1(P, c, v.x) : mag_out_m1(c, v.x));
+    acc_add(s, v, IN ? mag_in_m1<H>(P, c, v.x) : mag_out_m1(c, v.x));
   }
 }
 
 // two trajectories over one epoch segment, one epoch load for both
-template <bool INA, bool INB>
+template <bool H, bool INA, bool INB>
 __device__ __forceinline__ void seg2(const SearchParams &P, const float4 *ep,
                                      const TrajC &ca, const TrajC &cb,
                                      int lane, int e0, int e1, Acc &sa,
@@ -238,8 +288,8 @@ __device__ __forceinline__ void seg2(const SearchParams &P, const float4 *ep,
 #pragma unroll ((INA || INB) ? kUnroll : 2)
   for (int e = lane_start(e0, lane); e < e1; e += 32) {
     const float4 v = ep[e];
-    acc_add(sa, v, INA ? mag_in_m1(P, ca, v.x) : mag_out_m1(ca, v.x));
-    acc_add(sb, v, INB ? mag_in_m1(P, cb, v.x) : mag_out_m1(cb, v.x));
+    acc_add(sa, v, INA ? mag_in_m1<H>(P, ca, v.x) : mag_out_m1(ca, v.x));
+    acc_add(sb, v, INB ? mag_in_m1<H>(P, cb, v.x) : mag_out_m1(cb, v.x));
   }
 }
 
@@ -261,18 +311,20 @@ __device__ __forceinline__ Acc acc_reduce(Acc s) {
 // Phase 1: FP32 sums of S_A = sum w (A-1), S_AA = sum w (A-1)^2 and
 // S_AF = sum w (F-Fref)(A-1) over the epochs before, inside and after the
 // map, reduced across the warp.
+template <bool H>
 __device__ __forceinline__ Acc phase1(const SearchParams &P, const float4 *ep,
                                       const TrajC &c, const int lane) {
   Acc s = {0.f, 0.f, 0.f};
-  seg1<false>(P, ep, c, lane, 0, c.e_in, s);
-  seg1<true>(P, ep, c, lane, c.e_in, c.e_out, s);
-  seg1<false>(P, ep, c, lane, c.e_out, P.n_ep, s);
+  seg1<H, false>(P, ep, c, lane, 0, c.e_in, s);
+  seg1<H, true>(P, ep, c, lane, c.e_in, c.e_out, s);
+  seg1<H, false>(P, ep, c, lane, c.e_out, P.n_ep, s);
   return acc_reduce(s);
 }
 
 // Phase 1 of two trajectories at once: the epoch axis is cut at both
 // trajectories' map entry and exit, and each segment runs the matching
 // inside/outside combination with one epoch load per lane for both.
+template <bool H>
 __device__ __forceinline__ void phase1_pair(const SearchParams &P,
                                             const float4 *ep, const TrajC &ca,
                                             const TrajC &cb, const int lane,
@@ -293,13 +345,13 @@ __device__ __forceinline__ void phase1_pair(const SearchParams &P,
     const bool ina = e0 >= ca.e_in && e1 <= ca.e_out;
     const bool inb = e0 >= cb.e_in && e1 <= cb.e_out;
     if (ina && inb)
-      seg2<true, true>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+      seg2<H, true, true>(P, ep, ca, cb, lane, e0, e1, sa, sb);
     else if (ina)
-      seg2<true, false>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+      seg2<H, true, false>(P, ep, ca, cb, lane, e0, e1, sa, sb);
     else if (inb)
-      seg2<false, true>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+      seg2<H, false, true>(P, ep, ca, cb, lane, e0, e1, sa, sb);
     else
-      seg2<false, false>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+      seg2<H, false, false>(P, ep, ca, cb, lane, e0, e1, sa, sb);
   }
   ra = acc_reduce(sa);
   rb = acc_reduce(sb);
@@ -308,6 +360,7 @@ __device__ __forceinline__ void phase1_pair(const SearchParams &P,
 // Phase 2: chi^2 = sum w (F - Fs A - Fb)^2, written with centred values as
 // w (Fc - Fs Ac - Bc)^2, Bc = Fs + Fb - Fref.  FP32 per lane, FP64 across
 // lanes; lane 0's value is returned to all lanes.
+template <bool H>
 __device__ __forceinline__ double phase2(const SearchParams &P,
                                          const float4 *ep, const TrajC &c,
                                          const int lane, const float Fs,
@@ -323,7 +376,7 @@ __device__ __forceinline__ double phase2(const SearchParams &P,
 #pragma unroll (kUnroll)
   for (int e = lane_start(c.e_in, lane); e < c.e_out; e += 32) {
     const float4 v = ep[e];
-    const float Ac = mag_in_m1(P, c, v.x);
+    const float Ac = mag_in_m1<H>(P, c, v.x);
     const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
     chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
   }
