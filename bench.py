@@ -202,6 +202,152 @@ def grid_of(m, cfg):
                        cfg["top_k"])
 
 
+def batch_events(ctx, m, cfg, n_events):
+    """Light curves of the batched workload: lengths log-uniform in
+    [200, 20000], truths from synth.truth_draws, magnification read through
+    the library from a map of each truth lens (self-consistent injection),
+    noise as config 0."""
+    lens = synth.event_lengths(n_events, cfg["seed"], cfg["len_lo"],
+                               cfg["len_hi"])
+    truths = synth.truth_draws(n_events, cfg["seed"])
+    evs = []
+    for i, (n, tr) in enumerate(zip(lens, truths)):
+        mp = ctx.build_map(tr["s"], tr["q"], cfg["L"], cfg["npix"],
+                           cfg["nray"], image_halfwidth=cfg["X"],
+                           deflect="fp32")
+        t = synth.epoch_times(int(n), cfg["seed"] * 1000 + i, tr["t0"])
+        A = ctx.lightcurve(mp, tr["t0"], tr["tE"], tr["u0"], tr["alpha"], t)
+        mp.free()
+        F, sig = synth.photometry(tr["Fs"] * A + tr["Fb"],
+                                  cfg["seed"] * 1000 + i)
+        evs.append(ctx.event(t, F, sig, t_ref=0.0))
+    return evs, lens
+
+
+def run_batched(ctx, m, n_events, n_maps, tune=True):
+    """The batched search (one persistent launch per call, CUDA graph) on a
+    subset of the 256-event x 64-map workload, against one morse_grid_chi2
+    call per (event, map) pair on the same inputs."""
+    import torch
+    cfg = synth.CFG3
+    evs, lens = batch_events(ctx, m, cfg, n_events)
+    S, Q = synth.bank_sq(n_maps, cfg["seed"])
+    maps = [ctx.build_map(S[j], Q[j], cfg["L"], cfg["npix"], cfg["nray"],
+                          image_halfwidth=cfg["X"], deflect="fp32")
+            for j in range(n_maps)]
+    g = cfg["grid"]
+    grid = m.Grid.make(g["n_u0"], g["n_alpha"], g["n_t0"], g["n_tE"],
+                       g["u0_lo"], g["u0_hi"], g["t0_lo"], g["t0_hi"],
+                       g["tE_lo"], g["tE_hi"], g["u0_log"], g["tE_log"],
+                       cfg["top_k"])
+    evals = float(grid.size) * float(np.sum(lens)) * n_maps
+    ctx.batch_tuning(tune)
+    t0 = time.perf_counter()
+    out = ctx.grid_chi2_batch(evs, maps, grid)  # first call tunes
+    first = time.perf_counter() - t0
+    walls, search = [], []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.grid_chi2_batch(evs, maps, grid)
+        walls.append(time.perf_counter() - t0)
+        search.append(ctx.kernel_ms(2))
+    exact = ctx.exact_sweeps()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    same = True
+    for e, ev in enumerate(evs):
+        for j, mp in enumerate(maps):
+            one = ctx.grid_chi2(ev, mp, grid)
+            same &= bool(np.array_equal(one["idx"], out[e, j]["idx"]) and
+                         np.array_equal(one["chi2"], out[e, j]["chi2"]))
+    plain = time.perf_counter() - t0
+    shapes = {}
+    for b in sorted({int(np.log2(n)) for n in lens}):
+        sh = ctx.batch_shape(2 ** b, grid, maps[0])
+        shapes[f"2^{b}"] = f"tpg {sh['tpg']} rounds {sh['rounds']} " \
+                           f"stage {sh['stage']}"
+    for mp in maps:
+        mp.free()
+    for ev in evs:
+        ev.free()
+    return {
+        "workload": f"{n_events} events (lengths log-uniform in [200, 20000]"
+                    f", {int(np.sum(lens))} epochs) x {n_maps} maps of "
+                    f"1024^2 x {grid.size} trajectories per pair, top-K "
+                    f"{cfg['top_k']} (subset of 256 x 64)",
+        "evals_per_call": evals,
+        "batch_s": min(walls), "batch_evals_per_s": evals / min(walls),
+        "batch_search_ms": float(min(search)),
+        "first_call_s_with_tuning": first,
+        "per_pair_calls_s": plain, "per_pair_evals_per_s": evals / plain,
+        "identical_to_per_pair": same,
+        "exact_sweep_fraction": exact / (grid.size * n_events * n_maps),
+        "tuned_shapes": shapes,
+    }
+
+
+def refine_best(ctx, m, cfg, ev, S, Q, fits, n_maps=8, iters=40):
+    """Levenberg-Marquardt refinement (adjoint gradient) of the top seeds
+    of the n_maps maps with the lowest grid chi^2; returns the best chi^2."""
+    best = np.inf
+    for j in np.argsort(fits["chi2"][:, 0])[:n_maps]:
+        mp = ctx.build_map(S[j], Q[j], cfg["L"], cfg["npix"], cfg["nray"],
+                           image_halfwidth=cfg["X"], deflect="fp32")
+        seeds = fits[j][:16]
+        r = ctx.refine(ev, mp, seeds[np.isfinite(seeds["chi2"])], iters=iters)
+        best = min(best, float(r["chi2"].min()))
+        mp.free()
+    return best
+
+
+def time_to_best_fit(ctx, m, cfg, ev, S, Q, plain_s, plain_fits):
+    """Wall time of each form of the (s, q) search and its best chi^2; a
+    form reaches the best fit when its chi^2 is within 1e-3 of the lowest
+    chi^2 any form found.  Forms: the plain FP32 grid (timed above), the
+    same grid on FP16 log10 tables, the plain grid followed by adjoint
+    (Levenberg-Marquardt) refinement of its best seeds, and grids 3.8x and
+    15x coarser followed by the same refinement."""
+    import torch
+    g = cfg["grid"]
+
+    def sweep(grid, fp16=False):
+        return ctx.sweep(ev, S, Q, cfg["L"], cfg["npix"], cfg["nray"], grid,
+                         image_halfwidth=cfg["X"], deflect="fp32",
+                         fp16log=fp16)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        v = fn()
+        torch.cuda.synchronize()
+        return v, time.perf_counter() - t0
+
+    forms = {"plain_fp32_grid": (plain_s, float(plain_fits["chi2"].min()),
+                                 "40x72x25x20 grid, 651 maps")}
+    f16, t = timed(lambda: sweep(grid_of(m, cfg), True))
+    forms["fp16_grid"] = (t, float(f16["chi2"].min()),
+                          "same grid on FP16 log10 tables")
+    b, t = timed(lambda: refine_best(ctx, m, cfg, ev, S, Q, plain_fits))
+    forms["plain_grid_plus_refine"] = (
+        plain_s + t, b, "plain grid, then 40 LM iterations on the 16 best "
+        "seeds of the 8 best maps")
+    for name, dims in (("half_grid_plus_refine", (40, 72, 13, 10)),
+                       ("coarse_grid_plus_refine", (20, 36, 13, 10))):
+        grid = m.Grid.make(*dims, g["u0_lo"], g["u0_hi"], g["t0_lo"],
+                           g["t0_hi"], g["tE_lo"], g["tE_hi"], True, True, 16)
+        b, t = timed(lambda: refine_best(ctx, m, cfg, ev, S, Q,
+                                         sweep(grid)))
+        forms[name] = (t, b, "x".join(map(str, dims)) + " grid, then the "
+                       "same refinement")
+    target = min(v[1] for v in forms.values())
+    return {"target_chi2": target,
+            "rule": "reached: best chi^2 <= target x (1 + 1e-3)",
+            **{k: {"s": v[0], "best_chi2": v[1], "form": v[2],
+                   "reached": v[1] <= target * (1 + 1e-3)}
+               for k, v in forms.items()}}
+
+
 # ---------------------------------------------------------------- dist
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -447,6 +593,11 @@ def run_gpu(args, cfg):
         "best_chi2": best,
         "clocks": clocks,
     }
+    if rank == 0 and not args.no_extras:
+        line["time_to_best_fit"] = time_to_best_fit(
+            ctx, m, cfg, ev, S, Q, elapsed / args.steps, fits)
+        line["batched"] = run_batched(ctx, m, args.batch_events,
+                                      args.batch_maps, not args.no_batch_tune)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nth = os.cpu_count() or 1
         r = oracle_sample(cfg, args.cpu_frac, 7, nth)
@@ -476,6 +627,14 @@ def main():
     ap.add_argument("--ref-frac", type=float, default=0.002,
                     help="trajectory fraction per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the time-to-best-fit and batched sections")
+    ap.add_argument("--no-batch-tune", action="store_true",
+                    help="batched section with the default launch shapes")
+    ap.add_argument("--batch-events", type=int, default=32,
+                    help="events of the batched section (of 256)")
+    ap.add_argument("--batch-maps", type=int, default=8,
+                    help="maps of the batched section (of 64)")
     ap.add_argument("--lookup", default="fp32", choices=["fp32", "fp16log"],
                     help="map table the search reads (the headline is fp32)")
     ap.add_argument("--maps", type=int, default=0,

@@ -242,6 +242,52 @@ morse_status morse_grid_chi2_noalloc(morse_ctx *ctx, const morse_event *ev,
                                      const morse_map *map,
                                      const morse_grid *grid, morse_fit *out);
 
+/* Batched search: n_ev light curves (any lengths) against n_maps maps,
+ * every (event, map) pair searched over the same grid, in one persistent
+ * kernel launch.  The pair (e, m) gets the top_k fits of
+ * morse_grid_chi2(ev[e], maps[m], grid), bit for bit, in
+ * out[(e * n_maps + m) * top_k + r] (host, caller-allocated).  The maps
+ * must share npix, extent and lookup table (FP32 or FP16); grid t0 values
+ * are absolute times, each event's relative to its own t_ref.  The whole
+ * sequence (a strided pilot pass per pair that seeds the pair's pruning
+ * threshold, the main pass, the per-pair merges and the record fill) is
+ * captured in a CUDA graph, which later calls of the same shape update and
+ * replay.  Launch shapes per epoch-count bucket (trajectories per warp
+ * group, groups per work unit, shared-memory staging of the epochs) come
+ * from the autotuner (morse_batch_tuning) or from the default rule.
+ * Errors: EINVAL (mismatched maps, foreign handles, n_ev or n_maps < 1,
+ * more than 2^31 partial lists), ENOMEM, ECUDA, ETIMEOUT. */
+morse_status morse_grid_chi2_batch(morse_ctx *ctx,
+                                   const morse_event *const *ev, int n_ev,
+                                   const morse_map *const *maps, int n_maps,
+                                   const morse_grid *grid, morse_fit *out);
+
+/* Launch shape of the batched search for light curves of one epoch-count
+ * bucket (2^b <= n_ep < 2^(b+1)). */
+typedef struct {
+  int tpg;             /* trajectories per warp group (8, 16 or 32)        */
+  int rounds;          /* warp groups per warp in one work unit             */
+  int stage;           /* 1: epochs staged in shared memory                 */
+  int tuned;           /* 1: picked by timing candidates, 0: default rule   */
+  double ns_per_eval;  /* tuned: time per trajectory-epoch of the winner    */
+} morse_batch_shape;
+
+enum {
+  MORSE_TUNE_OFF = 0, /* default rule (no timing runs)                     */
+  MORSE_TUNE_ON = 1   /* time the candidate shapes of each new bucket once
+                         per context on a sample of the batch (default)    */
+};
+
+/* Select the autotuner mode and forget the shapes tuned so far. */
+morse_status morse_batch_tuning(morse_ctx *ctx, int mode);
+
+/* The shape used for light curves of n_ep epochs with this grid and map
+ * geometry, if a batch call has chosen one (else EINVAL). */
+morse_status morse_batch_shape_of(morse_ctx *ctx, int64_t n_ep,
+                                  const morse_grid *grid,
+                                  const morse_map *map,
+                                  morse_batch_shape *out);
+
 /* chi^2, Fs and Fb of every trajectory with index in [first, first+count)
  * (host arrays of count doubles; Fs/Fb may be NULL).  Same arithmetic as
  * morse_grid_chi2.  Errors: EINVAL, ENOMEM, ECUDA. */

@@ -91,6 +91,15 @@ class MapOpts(ctypes.Structure):
                 ("deflect", ctypes.c_int), ("store", ctypes.c_int)]
 
 
+class BatchShape(ctypes.Structure):
+    """morse_batch_shape: launch shape of one epoch-count bucket."""
+    _fields_ = [("tpg", ctypes.c_int), ("rounds", ctypes.c_int),
+                ("stage", ctypes.c_int), ("tuned", ctypes.c_int),
+                ("ns_per_eval", ctypes.c_double)]
+
+
+TUNE_OFF, TUNE_ON = 0, 1
+
 _P = ctypes.c_void_p
 _D = ctypes.c_double
 _I = ctypes.c_int
@@ -110,6 +119,9 @@ _SIGS = {
     "morse_map_info": (_S, [_P, _P, _P, _P, _P]),
     "morse_map_free": (None, [_P]),
     "morse_map_set_lookup": (_S, [_P, _I]),
+    "morse_grid_chi2_batch": (_S, [_P, _P, _I, _P, _I, _P, _P]),
+    "morse_batch_tuning": (_S, [_P, _I]),
+    "morse_batch_shape_of": (_S, [_P, _I64, _P, _P, _P]),
     "morse_map_half": (_S, [_P, _P, _P]),
     "morse_event_create": (_S, [_P, _P, _P, _P, _I64, _D, _P]),
     "morse_event_free": (None, [_P]),
@@ -245,6 +257,34 @@ class Context:
                                   ctypes.byref(grid), _ptr(out))
         self._check(st, "morse_grid_chi2")
         return out
+
+    def grid_chi2_batch(self, events, maps, grid: Grid) -> np.ndarray:
+        """Batched search of every (event, map) pair in one persistent launch
+        (morse_grid_chi2_batch): fits[n_events, n_maps, top_k]."""
+        ev = (ctypes.c_void_p * len(events))(*[e._h for e in events])
+        mp = (ctypes.c_void_p * len(maps))(*[m._h for m in maps])
+        out = np.zeros((len(events), len(maps), grid.top_k), dtype=FIT_DTYPE)
+        st = _lib.morse_grid_chi2_batch(self._h, ev, len(events), mp,
+                                        len(maps), ctypes.byref(grid),
+                                        _ptr(out))
+        self._check(st, "morse_grid_chi2_batch")
+        return out
+
+    def batch_tuning(self, on: bool):
+        """Autotune batched launch shapes (default) or use the default rule;
+        forgets the shapes chosen so far (morse_batch_tuning)."""
+        self._check(_lib.morse_batch_tuning(self._h,
+                                            TUNE_ON if on else TUNE_OFF),
+                    "morse_batch_tuning")
+
+    def batch_shape(self, n_ep, grid: Grid, map_) -> dict:
+        """The batched launch shape chosen for light curves of n_ep epochs."""
+        sh = BatchShape()
+        self._check(_lib.morse_batch_shape_of(self._h, int(n_ep),
+                                              ctypes.byref(grid), map_._h,
+                                              ctypes.byref(sh)),
+                    "morse_batch_shape_of")
+        return {f: getattr(sh, f) for f, _ in BatchShape._fields_}
 
     def grid_chi2_noalloc(self, event, map_, grid: Grid) -> np.ndarray:
         """Top-K search that allocates no device memory

@@ -73,6 +73,18 @@ void call_begin(morse_ctx *ctx) {
   for (int k = 0; k < KT_COUNT; ++k) ctx->kernel_ms[k] = 0.0;
 }
 
+// Record a timing event on the context stream; while the stream is being
+// captured the record becomes an external event node of the graph, which
+// still timestamps the event when the graph runs.
+void record(morse_ctx *ctx, cudaEvent_t e) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &cs) == cudaSuccess &&
+      cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, ctx->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, ctx->stream);
+}
+
 int t_begin(morse_ctx *ctx, int kind) {
   size_t r = ctx->rec_kind.size();
   while (ctx->evpool.size() < 2 * (r + 1)) {
@@ -84,12 +96,12 @@ int t_begin(morse_ctx *ctx, int kind) {
     ctx->evpool.push_back(e);
   }
   ctx->rec_kind.push_back(kind);
-  cudaEventRecord(ctx->evpool[2 * r], ctx->stream);
+  record(ctx, ctx->evpool[2 * r]);
   return (int)r;
 }
 
 void t_end(morse_ctx *ctx, int r) {
-  if (r >= 0) cudaEventRecord(ctx->evpool[2 * (size_t)r + 1], ctx->stream);
+  if (r >= 0) record(ctx, ctx->evpool[2 * (size_t)r + 1]);
 }
 
 // after the stream has synchronised
@@ -637,6 +649,487 @@ morse_status sweep_impl(morse_ctx *ctx, const morse_event *ev,
   return hdr_check(ctx, h);
 }
 
+// ---------------------------------------------------------------- batch
+// Epoch-count bucket: floor(log2 n_ep).
+int ep_bucket(int64_t n) {
+  int b = 0;
+  while ((int64_t(2) << b) <= n) ++b;
+  return b;
+}
+
+std::string tune_key(int bucket, const morse_grid *g, const morse_map *m) {
+  char buf[128];
+  snprintf(buf, sizeof(buf), "%d|%d|%lld|%lld|%d|%d", bucket, g->top_k,
+           (long long)g->n_t0 * g->n_tE, grid_size(g), m->npix,
+           morse::map_h16(m) ? 1 : 0);
+  return std::string(buf);
+}
+
+// Staging is decided per bucket, so that one shape holds for every light
+// curve of the bucket: the default stages buckets of fewer than 4096
+// epochs, the tuner may try staging up to 8191 (128 KB).
+constexpr int kBatchStageDefault = 4095;
+constexpr int kBatchStageMax = 8191;
+
+int64_t bucket_top(int64_t n_ep) {
+  return (int64_t(2) << ep_bucket(n_ep)) - 1;
+}
+
+morse_batch_shape default_shape(int64_t n_ep, long long line) {
+  morse_batch_shape s;
+  s.tpg = morse::line_tpg(line);
+  s.rounds = 4;
+  s.stage = bucket_top(n_ep) <= kBatchStageDefault ? 1 : 0;
+  s.tuned = 0;
+  s.ns_per_eval = 0.0;
+  return s;
+}
+
+// Host copy of everything a batch launch reads besides the epochs and maps.
+struct BatchHost {
+  std::vector<morse::BatchEvent> ev;
+  std::vector<const void *> tab;
+  std::vector<morse::BatchUnit> pilot, main;
+  std::vector<int> pilot_list0, main_list0;
+  std::vector<double> tables;  // u0 | cos | sin | 1/(tE D) | t0 | tE | t0rel
+  long long pilot_count = 0, pilot_stride = 0;
+  int ep_cap = 0;
+};
+
+// Units of one pass over `pairs` pairs: groups [0, groups(p)) of each pair
+// cut into units of kSearchWarps * rounds groups.
+void batch_units(const std::vector<int> &pair_ids,
+                 const std::vector<morse_batch_shape> &shape_of_pair,
+                 const std::vector<long long> &groups_of_pair, int pairs,
+                 std::vector<morse::BatchUnit> &units,
+                 std::vector<int> &list0) {
+  list0.assign((size_t)pairs + 1, 0);
+  std::vector<long long> per(pairs, 0);
+  for (int p : pair_ids) {
+    const long long ug = (long long)morse::kSearchWarps *
+                         shape_of_pair[(size_t)p].rounds;
+    per[(size_t)p] = (groups_of_pair[(size_t)p] + ug - 1) / ug;
+  }
+  for (int p = 0; p < pairs; ++p)
+    list0[(size_t)p + 1] = list0[(size_t)p] + (int)per[(size_t)p];
+  units.clear();
+  for (int p : pair_ids) {
+    const morse_batch_shape &s = shape_of_pair[(size_t)p];
+    const long long ug = (long long)morse::kSearchWarps * s.rounds;
+    for (long long u = 0; u < per[(size_t)p]; ++u) {
+      morse::BatchUnit U;
+      U.pair = p;
+      U.list = list0[(size_t)p] + (int)u;
+      U.g0 = (int)(u * ug);
+      U.ng = (int)std::min(ug, groups_of_pair[(size_t)p] - u * ug);
+      U.tpg = s.tpg;
+      U.stage = s.stage;
+      units.push_back(U);
+    }
+  }
+}
+
+// Grid tables shared by the pairs, plus each event's t0 - t_ref.
+void batch_tables(const morse_grid *g, const morse_event *const *evs, int n_ev,
+                  double dlt, std::vector<double> &h) {
+  std::vector<double> u0, t0, tE;
+  axis(g->u0_lo, g->u0_hi, g->n_u0, g->u0_log, u0);
+  axis(g->t0_lo, g->t0_hi, g->n_t0, 0, t0);
+  axis(g->tE_lo, g->tE_hi, g->n_tE, g->tE_log, tE);
+  h.clear();
+  h.insert(h.end(), u0.begin(), u0.end());
+  for (int k = 0; k < g->n_alpha; ++k)
+    h.push_back(cos(2.0 * M_PI * (double)k / (double)g->n_alpha));
+  for (int k = 0; k < g->n_alpha; ++k)
+    h.push_back(sin(2.0 * M_PI * (double)k / (double)g->n_alpha));
+  for (double v : tE) h.push_back(1.0 / (v * dlt));
+  h.insert(h.end(), t0.begin(), t0.end());
+  h.insert(h.end(), tE.begin(), tE.end());
+  for (int e = 0; e < n_ev; ++e)
+    for (double v : t0) h.push_back(v - evs[e]->t_ref);
+}
+
+// Device layout of a batch call.
+struct BatchLayout {
+  size_t off_tab, off_ev, off_ptr, off_up, off_um, off_lp, off_lm, off_gthr,
+      off_hdr, off_pa, off_pb, off_res, off_fit, bytes;
+};
+
+struct BatchHdr {
+  unsigned counter[2];
+  unsigned err;
+  unsigned pad;
+  unsigned long long stat_exact;
+};
+
+BatchLayout batch_layout(const BatchHost &H, int pairs, int K) {
+  BatchLayout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes, 256);
+    return at;
+  };
+  L.off_tab = take(sizeof(double) * H.tables.size());
+  L.off_ev = take(sizeof(morse::BatchEvent) * H.ev.size());
+  L.off_ptr = take(sizeof(void *) * H.tab.size());
+  L.off_up = take(sizeof(morse::BatchUnit) * H.pilot.size());
+  L.off_um = take(sizeof(morse::BatchUnit) * H.main.size());
+  L.off_lp = take(sizeof(int) * H.pilot_list0.size());
+  L.off_lm = take(sizeof(int) * H.main_list0.size());
+  L.off_gthr = take(sizeof(unsigned long long) * (size_t)pairs);
+  L.off_hdr = take(sizeof(BatchHdr));
+  const size_t lists = (size_t)std::max(
+      H.pilot_list0.empty() ? 0 : H.pilot_list0.back(), H.main_list0.back());
+  L.off_pa = take(sizeof(Entry) * lists * (size_t)K);
+  L.off_pb = take(sizeof(Entry) * lists * (size_t)K);
+  L.off_res = take(sizeof(Entry) * (size_t)pairs * K);
+  L.off_fit = take(sizeof(morse_fit) * (size_t)pairs * K);
+  L.bytes = o;
+  return L;
+}
+
+// Fill the per-pair arrays of a batch over the given events and maps.
+// shape_of_event: the launch shape of each event.
+morse_status batch_prepare(morse_ctx *ctx, const morse_event *const *evs,
+                           int n_ev, const morse_map *const *maps, int n_maps,
+                           const morse_grid *g,
+                           const std::vector<morse_batch_shape> &shape_ev,
+                           bool with_pilot, BatchHost &H) {
+  const int K = g->top_k;
+  const long long N = grid_size(g);
+  const long long line = (long long)g->n_t0 * g->n_tE;
+  const int pairs = n_ev * n_maps;
+  const double dlt = (2.0 * maps[0]->L) / (double)maps[0]->npix;
+  batch_tables(g, evs, n_ev, dlt, H.tables);
+  H.tab.resize((size_t)n_maps);
+  const bool h16 = morse::map_h16(maps[0]);
+  for (int m = 0; m < n_maps; ++m)
+    H.tab[(size_t)m] = h16 ? (const void *)maps[m]->quadh
+                           : (const void *)maps[m]->quad;
+  H.ev.resize((size_t)n_ev);
+  H.ep_cap = 0;
+  // staged light curves must fit next to the block's top-K lists
+  const size_t lists = morse::batch_smem_bytes(0, K);
+  const long long cap_max =
+      ctx->smem_optin > lists + 2048
+          ? (long long)((ctx->smem_optin - lists - 2048) / sizeof(float4))
+          : 0;
+  for (int e = 0; e < n_ev; ++e) {
+    morse::BatchEvent &E = H.ev[(size_t)e];
+    E.ep = evs[e]->ep;
+    E.n_ep = (int)evs[e]->n;
+    E.S1 = evs[e]->S1;
+    E.SF = evs[e]->SF;
+    E.SFF = evs[e]->SFF;
+    E.Fref = evs[e]->Fref;
+    E.gamma = ((double)((evs[e]->n + 31) / 32) + 10.0) * ldexp(1.0, -24);
+    E.t0rel = nullptr;  // set once the table offset is known
+  }
+  std::vector<morse_batch_shape> shape_fit = shape_ev;
+  for (int e = 0; e < n_ev; ++e) {
+    morse_batch_shape &s = shape_fit[(size_t)e];
+    if (s.stage && evs[e]->n > cap_max) s.stage = 0;
+    if (s.stage) H.ep_cap = std::max(H.ep_cap, (int)evs[e]->n);
+  }
+  // pairs, longest light curve first (they start early; short ones fill
+  // the tail)
+  std::vector<int> order((size_t)pairs);
+  for (int p = 0; p < pairs; ++p) order[(size_t)p] = p;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return evs[a / n_maps]->n > evs[b / n_maps]->n;
+  });
+  std::vector<morse_batch_shape> shape_pair((size_t)pairs);
+  for (int p = 0; p < pairs; ++p)
+    shape_pair[(size_t)p] = shape_fit[(size_t)(p / n_maps)];
+  // pilot: a strided sample of ~sqrt(K N) trajectories per pair
+  const double want = std::max(16.0 * K, std::sqrt((double)K * N));
+  const long long stride = (long long)(N / want);
+  H.pilot.clear();
+  H.pilot_list0.clear();
+  H.pilot_count = 0;
+  H.pilot_stride = 0;
+  if (with_pilot && stride >= 4) {
+    H.pilot_stride = stride;
+    H.pilot_count = (N + stride - 1) / stride;
+    std::vector<morse_batch_shape> sp = shape_pair;
+    std::vector<long long> gp((size_t)pairs);
+    for (int p = 0; p < pairs; ++p) {
+      sp[(size_t)p].tpg = 16;
+      sp[(size_t)p].rounds = 2;
+      gp[(size_t)p] = (H.pilot_count + 15) / 16;
+    }
+    batch_units(order, sp, gp, pairs, H.pilot, H.pilot_list0);
+  }
+  std::vector<long long> gm((size_t)pairs);
+  for (int p = 0; p < pairs; ++p) {
+    const int t = shape_pair[(size_t)p].tpg;
+    gm[(size_t)p] = (N / line) * ((line + t - 1) / t);
+  }
+  batch_units(order, shape_pair, gm, pairs, H.main, H.main_list0);
+  if ((long long)H.main_list0.back() >= 0x7fffffffLL / std::max(K, 1))
+    return fail(ctx, MORSE_EINVAL, "batch needs too many partial lists");
+  return MORSE_OK;
+}
+
+// Upload a prepared batch; returns the kernel parameters of its passes.
+morse_status batch_upload(morse_ctx *ctx, BatchHost &H, const BatchLayout &L,
+                          char *base, const morse_grid *g,
+                          const morse_map *map0, int n_ev,
+                          morse::BatchParams *Bp, morse::BatchParams *Bm,
+                          double **t0abs, double **tEv) {
+  double *tab = (double *)(base + L.off_tab);
+  const size_t o_u0 = 0, o_ca = o_u0 + g->n_u0, o_sa = o_ca + g->n_alpha,
+               o_k = o_sa + g->n_alpha, o_t0 = o_k + g->n_tE,
+               o_tE = o_t0 + g->n_t0, o_rel = o_tE + g->n_tE;
+  for (int e = 0; e < n_ev; ++e)
+    H.ev[(size_t)e].t0rel = tab + o_rel + (size_t)e * g->n_t0;
+  // one staging buffer, one copy, one wait (the host vectors are pageable)
+  std::vector<char> h(L.off_gthr);
+  memcpy(h.data() + L.off_tab, H.tables.data(),
+         sizeof(double) * H.tables.size());
+  memcpy(h.data() + L.off_ev, H.ev.data(),
+         sizeof(morse::BatchEvent) * H.ev.size());
+  memcpy(h.data() + L.off_ptr, H.tab.data(), sizeof(void *) * H.tab.size());
+  if (!H.pilot.empty()) {
+    memcpy(h.data() + L.off_up, H.pilot.data(),
+           sizeof(morse::BatchUnit) * H.pilot.size());
+    memcpy(h.data() + L.off_lp, H.pilot_list0.data(),
+           sizeof(int) * H.pilot_list0.size());
+  }
+  memcpy(h.data() + L.off_um, H.main.data(),
+         sizeof(morse::BatchUnit) * H.main.size());
+  memcpy(h.data() + L.off_lm, H.main_list0.data(),
+         sizeof(int) * H.main_list0.size());
+  MORSE_CUDA(ctx, cudaMemcpyAsync(base, h.data(), h.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  BatchHdr *hd = (BatchHdr *)(base + L.off_hdr);
+  morse::BatchParams B;
+  memset(&B, 0, sizeof(B));
+  map_params(map0, &B.S);
+  B.S.quad = nullptr;
+  B.S.quadh = nullptr;
+  B.S.u0v = tab + o_u0;
+  B.S.ca = tab + o_ca;
+  B.S.sa = tab + o_sa;
+  B.S.invtEd = tab + o_k;
+  B.S.n_u0 = g->n_u0;
+  B.S.n_alpha = g->n_alpha;
+  B.S.n_t0 = g->n_t0;
+  B.S.n_tE = g->n_tE;
+  B.S.top_k = g->top_k;
+  B.S.err = &hd->err;
+  B.S.stat_exact = &hd->stat_exact;
+  B.S.first = 0;
+  B.ev = (const morse::BatchEvent *)(base + L.off_ev);
+  B.tab = (const void *const *)(base + L.off_ptr);
+  B.n_maps = (int)H.tab.size();
+  B.gthr = (unsigned long long *)(base + L.off_gthr);
+  B.partial = (Entry *)(base + L.off_pa);
+  B.ep_cap = H.ep_cap;
+  *Bp = B;
+  Bp->S.count = H.pilot_count;
+  Bp->S.stride = H.pilot_stride;
+  Bp->S.line = 0;
+  Bp->units = (const morse::BatchUnit *)(base + L.off_up);
+  Bp->n_units = (int)H.pilot.size();
+  Bp->counter = &hd->counter[0];
+  *Bm = B;
+  Bm->S.count = grid_size(g);
+  Bm->S.stride = 1;
+  Bm->S.line = (long long)g->n_t0 * g->n_tE;
+  Bm->units = (const morse::BatchUnit *)(base + L.off_um);
+  Bm->n_units = (int)H.main.size();
+  Bm->counter = &hd->counter[1];
+  *t0abs = tab + o_t0;
+  *tEv = tab + o_tE;
+  return MORSE_OK;
+}
+
+// Queue a batch: reset words, pilot pass and seeding, main pass, merges,
+// fill.  No host synchronisation.
+morse_status batch_enqueue(morse_ctx *ctx, const BatchLayout &L, char *base,
+                           const morse::BatchParams &Bp,
+                           const morse::BatchParams &Bm, bool h16, int pairs,
+                           const double *t0abs, const double *tEv,
+                           int grid, size_t smem) {
+  const int K = Bm.S.top_k;
+  MORSE_CUDA(ctx, cudaMemsetAsync(base + L.off_gthr, 0xFF,
+                                  sizeof(unsigned long long) * pairs,
+                                  ctx->stream));
+  MORSE_CUDA(ctx, cudaMemsetAsync(base + L.off_hdr, 0, sizeof(BatchHdr),
+                                  ctx->stream));
+  Entry *pa = (Entry *)(base + L.off_pa), *pb = (Entry *)(base + L.off_pb);
+  Entry *res = (Entry *)(base + L.off_res);
+  int r;
+  if (Bp.n_units > 0) {
+    r = t_begin(ctx, KT_SEARCH);
+    MORSE_CUDA(ctx, morse::launch_batch(
+                        Bp, h16, std::min(grid, Bp.n_units), smem,
+                        ctx->stream));
+    t_end(ctx, r);
+    r = t_begin(ctx, KT_MERGE);
+    MORSE_CUDA(ctx, morse::launch_batch_merge(
+                        pa, pb, (const int *)(base + L.off_lp), pairs, K, res,
+                        Bm.gthr, ctx->stream));
+    t_end(ctx, r);
+    ctx->launches += 2;
+  }
+  r = t_begin(ctx, KT_SEARCH);
+  MORSE_CUDA(ctx, morse::launch_batch(Bm, h16, std::min(grid, Bm.n_units),
+                                      smem, ctx->stream));
+  t_end(ctx, r);
+  r = t_begin(ctx, KT_MERGE);
+  MORSE_CUDA(ctx, morse::launch_batch_merge(pa, pb,
+                                            (const int *)(base + L.off_lm),
+                                            pairs, K, res, nullptr,
+                                            ctx->stream));
+  t_end(ctx, r);
+  ctx->launches += 2;
+  r = t_begin(ctx, KT_FILL);
+  MORSE_CUDA(ctx, morse::launch_batch_fill(Bm, h16, res, pairs, t0abs, tEv,
+                                           (morse_fit *)(base + L.off_fit),
+                                           ctx->stream));
+  t_end(ctx, r);
+  ctx->launches += 1;
+  return MORSE_OK;
+}
+
+morse_status batch_hdr_check(morse_ctx *ctx, const BatchHdr &h) {
+  ctx->last_exact = h.stat_exact;
+  if (h.err & 2u)
+    return fail(ctx, MORSE_ECUDA,
+                "bounds check: a texel index fell outside the map (error "
+                "0x%x); results are invalid", h.err);
+  if (h.err & 1u)
+    return fail(ctx, MORSE_ETIMEOUT,
+                "a search block could not take its top-K lock (error 0x%x); "
+                "results are incomplete", h.err);
+  return MORSE_OK;
+}
+
+// Autotune the launch shape of one bucket on event e (a representative of
+// the bucket) against map 0: after one pilot pass (untimed, shared by the
+// candidates) the main pass runs on a sample of units of that pair for each
+// candidate shape; the fastest per trajectory-epoch wins.
+morse_status batch_tune(morse_ctx *ctx, const morse_event *ev,
+                        const morse_map *map0, const morse_grid *g,
+                        morse_batch_shape *best) {
+  const long long line = (long long)g->n_t0 * g->n_tE;
+  *best = default_shape(ev->n, line);
+  std::vector<morse_batch_shape> cands;
+  for (int tpg : {8, 16, 32})
+    for (int stage : {1, 0})
+      for (int rounds : {2, 8}) {
+        if (stage && bucket_top(ev->n) > kBatchStageMax) continue;
+        morse_batch_shape s;
+        s.tpg = tpg;
+        s.stage = stage;
+        s.rounds = rounds;
+        s.tuned = 1;
+        s.ns_per_eval = 0.0;
+        cands.push_back(s);
+      }
+  const bool h16 = morse::map_h16(map0);
+  const morse_event *evs[1] = {ev};
+  const morse_map *maps[1] = {map0};
+  constexpr long long kTuneTrajs = 300000;
+  double best_ns = 0.0;
+  cudaEvent_t e0, e1;
+  MORSE_CUDA(ctx, cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ctx, ce, "tuner event");
+  }
+  morse_status st = MORSE_OK;
+  for (size_t c = 0; c < cands.size() && st == MORSE_OK; ++c) {
+    std::vector<morse_batch_shape> sh(1, cands[c]);
+    BatchHost H;
+    st = batch_prepare(ctx, evs, 1, maps, 1, g, sh, true, H);
+    if (st != MORSE_OK) break;
+    // time an evenly spaced sample of the pair's units, about
+    // kTuneTrajs trajectories
+    const long long tpg = cands[c].tpg, ngl = (line + tpg - 1) / tpg;
+    auto unit_trajs = [&](const morse::BatchUnit &U) {
+      long long n = 0;
+      for (long long gi = U.g0; gi < (long long)U.g0 + U.ng; ++gi) {
+        const long long j = gi % ngl;
+        n += std::min((j + 1) * tpg, line) - j * tpg;
+      }
+      return n;
+    };
+    const long long per_unit = std::max(1LL, unit_trajs(H.main[0]));
+    const long long want_units = std::max(1LL, kTuneTrajs / per_unit);
+    const size_t step = std::max<size_t>(
+        1, H.main.size() / (size_t)want_units);
+    std::vector<morse::BatchUnit> pick;
+    long long trajs = 0;
+    for (size_t i = 0; i < H.main.size(); i += step) {
+      pick.push_back(H.main[i]);
+      trajs += unit_trajs(H.main[i]);
+    }
+    H.main.swap(pick);
+    BatchLayout L = batch_layout(H, 1, g->top_k);
+    void *ws = nullptr;
+    st = ws_reserve(ctx, L.bytes, &ws);
+    if (st != MORSE_OK) break;
+    char *base = (char *)ws;
+    morse::BatchParams Bp, Bm;
+    double *t0abs, *tEv;
+    st = batch_upload(ctx, H, L, base, g, map0, 1, &Bp, &Bm, &t0abs, &tEv);
+    if (st != MORSE_OK) break;
+    // the pilot pass and its merge, then the timed main pass
+    const size_t smem = morse::batch_smem_bytes(H.ep_cap, g->top_k);
+    const int bps = morse::batch_blocks_per_sm(h16, smem);
+    if (bps < 1) continue;
+    const int grid = bps * ctx->sm_count;
+    cands[c].stage = H.ep_cap > 0 ? 1 : 0;  // as the preparation fitted it
+    cudaMemsetAsync(base + L.off_gthr, 0xFF, sizeof(unsigned long long),
+                    ctx->stream);
+    cudaMemsetAsync(base + L.off_hdr, 0, sizeof(BatchHdr), ctx->stream);
+    Entry *pa = (Entry *)(base + L.off_pa), *pb = (Entry *)(base + L.off_pb);
+    if (Bp.n_units > 0) {
+      morse::launch_batch(Bp, h16, std::min(grid, Bp.n_units), smem,
+                          ctx->stream);
+      morse::launch_batch_merge(pa, pb, (const int *)(base + L.off_lp), 1,
+                                g->top_k, (Entry *)(base + L.off_res),
+                                Bm.gthr, ctx->stream);
+      ctx->launches += 2;
+    }
+    cudaEventRecord(e0, ctx->stream);
+    morse::launch_batch(Bm, h16, std::min(grid, Bm.n_units), smem,
+                        ctx->stream);
+    cudaEventRecord(e1, ctx->stream);
+    ctx->launches += 1;
+    ce = cudaStreamSynchronize(ctx->stream);
+    if (ce != cudaSuccess) {
+      st = cuda_fail(ctx, ce, "tuning run");
+      break;
+    }
+    BatchHdr hh;
+    ce = cudaMemcpy(&hh, base + L.off_hdr, sizeof(hh), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) {
+      st = cuda_fail(ctx, ce, "tuning run");
+      break;
+    }
+    st = batch_hdr_check(ctx, hh);
+    if (st != MORSE_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double ns = 1e6 * (double)ms / ((double)trajs * (double)ev->n);
+    if (best_ns == 0.0 || ns < best_ns) {
+      best_ns = ns;
+      *best = cands[c];
+      best->ns_per_eval = ns;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -682,6 +1175,8 @@ morse_status morse_create(morse_ctx **out, int device, void *cuda_stream) {
     return MORSE_ECUDA;
   }
   c->sm_count = prop.multiProcessorCount;
+  c->tune_mode = MORSE_TUNE_ON;
+  c->batch_exec = nullptr;
   c->smem_optin = prop.sharedMemPerBlockOptin;
   if (cuda_stream) {
     c->stream = (cudaStream_t)cuda_stream;
@@ -704,6 +1199,7 @@ void morse_destroy(morse_ctx *ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->sweep_map) map_release(ctx->sweep_map);
+  if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
   if (ctx->ws) cudaFree(ctx->ws);
   for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -1360,6 +1856,135 @@ morse_status morse_topk_merge(const morse_fit *const *lists,
       out[j].idx = -1;
     }
   }
+  return MORSE_OK;
+}
+
+// ------------------------------------------------------------------ batch
+morse_status morse_grid_chi2_batch(morse_ctx *ctx,
+                                   const morse_event *const *evs, int n_ev,
+                                   const morse_map *const *maps, int n_maps,
+                                   const morse_grid *grid, morse_fit *out) {
+  if (!ctx || !out || !evs || !maps) return MORSE_EINVAL;
+  if (n_ev < 1 || n_maps < 1)
+    return fail(ctx, MORSE_EINVAL, "need at least one event and one map");
+  if ((long long)n_ev * n_maps > 0x7fffffffLL)
+    return fail(ctx, MORSE_EINVAL, "too many (event, map) pairs");
+  MORSE_TRY(check_grid(ctx, grid));
+  for (int e = 0; e < n_ev; ++e)
+    if (!evs[e] || evs[e]->ctx != ctx)
+      return fail(ctx, MORSE_EINVAL, "event %d is NULL or of another ctx", e);
+  for (int m = 0; m < n_maps; ++m) {
+    if (!maps[m] || maps[m]->ctx != ctx)
+      return fail(ctx, MORSE_EINVAL, "map %d is NULL or of another ctx", m);
+    if (maps[m]->npix != maps[0]->npix || maps[m]->L != maps[0]->L ||
+        morse::map_h16(maps[m]) != morse::map_h16(maps[0]))
+      return fail(ctx, MORSE_EINVAL,
+                  "map %d differs from map 0 in npix, extent or lookup "
+                  "table; batch maps must share them", m);
+  }
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int K = grid->top_k;
+  const int pairs = n_ev * n_maps;
+  const bool h16 = morse::map_h16(maps[0]);
+  // launch shapes per light curve, tuned once per bucket and signature
+  std::vector<morse_batch_shape> shape_ev((size_t)n_ev);
+  for (int e = 0; e < n_ev; ++e) {
+    const std::string key = tune_key(ep_bucket(evs[e]->n), grid, maps[0]);
+    auto it = ctx->tune.find(key);
+    if (it == ctx->tune.end()) {
+      morse_batch_shape s =
+          default_shape(evs[e]->n, (long long)grid->n_t0 * grid->n_tE);
+      if (ctx->tune_mode == MORSE_TUNE_ON) {
+        call_begin(ctx);
+        MORSE_TRY(batch_tune(ctx, evs[e], maps[0], grid, &s));
+      }
+      it = ctx->tune.emplace(key, s).first;
+    }
+    shape_ev[(size_t)e] = it->second;
+  }
+  call_begin(ctx);
+  BatchHost H;
+  MORSE_TRY(batch_prepare(ctx, evs, n_ev, maps, n_maps, grid, shape_ev, true,
+                          H));
+  const BatchLayout L = batch_layout(H, pairs, K);
+  void *ws = nullptr;
+  MORSE_TRY(ws_reserve(ctx, L.bytes, &ws));
+  char *base = (char *)ws;
+  morse::BatchParams Bp, Bm;
+  double *t0abs, *tEv;
+  MORSE_TRY(batch_upload(ctx, H, L, base, grid, maps[0], n_ev, &Bp, &Bm,
+                         &t0abs, &tEv));
+  const size_t smem = morse::batch_smem_bytes(H.ep_cap, K);
+  const int bps = morse::batch_blocks_per_sm(h16, smem);
+  if (bps < 1)
+    return fail(ctx, MORSE_EUNSUPPORTED,
+                "batched search kernel does not fit (%d staged epochs, "
+                "top_k %d)", H.ep_cap, K);
+  // timing events exist before the capture records them
+  for (int k = 0; k < 8; ++k) t_end(ctx, t_begin(ctx, KT_SEARCH));
+  call_begin(ctx);
+  // capture the sequence; update the context's executable graph in place
+  // when the shape allows, else instantiate it anew
+  MORSE_CUDA(ctx, cudaStreamBeginCapture(ctx->stream,
+                                         cudaStreamCaptureModeThreadLocal));
+  morse_status st = batch_enqueue(ctx, L, base, Bp, Bm, h16, pairs, t0abs,
+                                  tEv, bps * ctx->sm_count, smem);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+  if (st != MORSE_OK || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    ctx->rec_kind.clear();
+    if (st != MORSE_OK) return st;
+    return cuda_fail(ctx, ce, "batch graph capture");
+  }
+  if (ctx->batch_exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(ctx->batch_exec, graph, &info) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(ctx->batch_exec);
+      ctx->batch_exec = nullptr;
+    }
+  }
+  if (!ctx->batch_exec) {
+    ce = cudaGraphInstantiate(&ctx->batch_exec, graph, 0);
+    if (ce != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      ctx->batch_exec = nullptr;
+      ctx->rec_kind.clear();
+      return cuda_fail(ctx, ce, "batch graph instantiate");
+    }
+  }
+  cudaGraphDestroy(graph);
+  MORSE_CUDA(ctx, cudaGraphLaunch(ctx->batch_exec, ctx->stream));
+  BatchHdr h;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(&h, base + L.off_hdr, sizeof(h),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_CUDA(ctx, cudaMemcpyAsync(out, base + L.off_fit,
+                                  sizeof(morse_fit) * (size_t)pairs * K,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_TRY(sync_and_collect(ctx, "batched search"));
+  return batch_hdr_check(ctx, h);
+}
+
+morse_status morse_batch_tuning(morse_ctx *ctx, int mode) {
+  if (!ctx) return MORSE_EINVAL;
+  if (mode != MORSE_TUNE_OFF && mode != MORSE_TUNE_ON)
+    return fail(ctx, MORSE_EINVAL, "unknown tuning mode %d", mode);
+  ctx->tune_mode = mode;
+  ctx->tune.clear();
+  return MORSE_OK;
+}
+
+morse_status morse_batch_shape_of(morse_ctx *ctx, int64_t n_ep,
+                                  const morse_grid *grid,
+                                  const morse_map *map,
+                                  morse_batch_shape *out) {
+  if (!ctx || !out || !map || n_ep < 1) return MORSE_EINVAL;
+  MORSE_TRY(check_grid(ctx, grid));
+  auto it = ctx->tune.find(tune_key(ep_bucket(n_ep), grid, map));
+  if (it == ctx->tune.end())
+    return fail(ctx, MORSE_EINVAL, "no batch shape chosen for this bucket");
+  *out = it->second;
   return MORSE_OK;
 }
 

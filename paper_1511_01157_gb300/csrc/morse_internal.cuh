@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <string>
 #include <vector>
 
 #include "morse.h"
@@ -30,6 +32,11 @@ struct morse_ctx {
   uint64_t launches;        // kernels launched by this context
   morse_map *sweep_map;     // map storage reused by sweeps
   unsigned long long last_exact;  // exact sweeps in the last search call
+  // batched search: autotuned launch shapes per epoch-count bucket (key:
+  // bucket and the search signature) and the reusable graph
+  std::map<std::string, morse_batch_shape> tune;
+  int tune_mode;            // MORSE_TUNE_*
+  cudaGraphExec_t batch_exec;
 };
 
 struct morse_map {
@@ -213,6 +220,55 @@ cudaError_t launch_fill(const FillParams &F, cudaStream_t st);
 // gthr <- min(gthr, chi^2 bits of sel[k-1]) when that entry is real
 cudaError_t launch_seed_threshold(const Entry *sel, int k,
                                   unsigned long long *gthr, cudaStream_t st);
+// ---------------------------------------------------------------- batch
+// One light curve of a batch, as the batched search reads it.
+struct BatchEvent {
+  const float4 *ep;         // time-sorted epochs (device)
+  int n_ep;
+  double S1, SF, SFF, Fref, gamma;
+  const double *t0rel;      // [n_t0] grid t0 - t_ref of this event
+};
+
+// A unit of work: warp groups [g0, g0 + ng) of one (event, map) pair, run
+// by one block, whose top-K goes to partial list `list`.
+struct BatchUnit {
+  int pair;                 // event * n_maps + map
+  int list;
+  int g0, ng;
+  int tpg;                  // trajectories per warp group
+  int stage;                // 1: the event's epochs are staged in shared
+                            // memory, 0: read from global memory
+};
+
+struct BatchParams {
+  SearchParams S;           // map geometry, grid tables, top_k, pass mode
+                            // (strided sample or line-aligned), err/stats
+  const BatchEvent *ev;     // [n_ev]
+  const void *const *tab;   // [n_maps] lookup tables (float4 or uint2 quads)
+  int n_maps;
+  const BatchUnit *units;   // [n_units] in processing order
+  int n_units;
+  unsigned *counter;        // next unit (zero before the launch)
+  unsigned long long *gthr; // [pairs] pruning thresholds (chi^2 bits)
+  Entry *partial;           // [lists][top_k]
+  int ep_cap;               // staged-epoch capacity of shared memory
+};
+
+size_t batch_smem_bytes(int ep_cap, int top_k);
+int batch_blocks_per_sm(bool h16, size_t smem);
+cudaError_t launch_batch(const BatchParams &B, bool h16, int grid,
+                         size_t smem, cudaStream_t st);
+// per pair: merge lists [list0[p], list0[p+1]) of a and b (ping-pong) into
+// result[p]; with gthr set, also lower gthr[p] to the merged K-th chi^2
+cudaError_t launch_batch_merge(Entry *a, Entry *b, const int *list0,
+                               int pairs, int k, Entry *result,
+                               unsigned long long *gthr, cudaStream_t st);
+// records of result[pairs][k] into out[pairs][k]
+cudaError_t launch_batch_fill(const BatchParams &B, bool h16,
+                              const Entry *result, int pairs,
+                              const double *t0abs, const double *tEv,
+                              morse_fit *out, cudaStream_t st);
+
 // ---------------------------------------------------------------- refine
 struct RefineState {
   double *th_cur, *th_best;        // [4 n] (t0, tE, u0, alpha)

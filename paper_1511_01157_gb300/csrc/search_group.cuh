@@ -1,0 +1,236 @@
+// Shared-memory top-K of a search block and the per-warp-group body of the
+// trajectory search, used by the single-pair search (k_search) and the
+// batched persistent search (k_batch).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "morse_internal.cuh"
+#include "search_common.cuh"
+
+namespace morse {
+namespace dev {
+
+// Block-wide top-K state in shared memory.
+struct BlockTopK {
+  Entry *buf0, *buf1; // the sorted list and its merge target, alternating
+  Entry *wbuf;        // per-warp staging of sorted candidates (32 each)
+  int *cur, *nk, *lock;
+  volatile double *thr;
+};
+
+// Warp-collective: merge this lane's candidate (if any) into the block's
+// sorted top-K under the block lock.  Candidates are first sorted across
+// the warp (bitonic); each existing entry and each candidate then moves to
+// its rank in the union, and the first K are kept.
+__device__ inline void warp_merge(const SearchParams &P, BlockTopK &T, const int K,
+                           const int warp, const int lane, bool has,
+                           double chi2, long long idx) {
+  const unsigned m = __ballot_sync(kFull, has);
+  if (!m) return;
+  const int nc = __popc(m);
+  double key = has ? chi2 : CUDART_INF;
+  long long id = has ? idx : 0x7fffffffffffffffLL;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const double ok = __shfl_xor_sync(kFull, key, j);
+      const long long oi = __shfl_xor_sync(kFull, id, j);
+      const bool keep_min = (((lane & k) == 0) == ((lane & j) == 0));
+      const bool other_less = key_less(ok, oi, key, id);
+      if (keep_min == other_less) {
+        key = ok;
+        id = oi;
+      }
+    }
+  }
+  Entry *wb = T.wbuf + warp * 32;
+  if (lane < nc) {
+    wb[lane].chi2 = key;
+    wb[lane].idx = id;
+  }
+  // acquire the block lock (bounded spin)
+  int ok = 1;
+  if (lane == 0) {
+    unsigned it = 0;
+    while (atomicCAS(T.lock, 0, 1) != 0) {
+      if (++it > kLockSpinLimit) {
+        ok = 0;
+        if (P.err) atomicOr(P.err, 1u);
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence_block();
+  }
+  ok = __shfl_sync(kFull, ok, 0);
+  __syncwarp();
+  if (!ok) return;
+  const int c0 = *T.cur;
+  const int nk = *T.nk;
+  const Entry *cur = c0 ? T.buf1 : T.buf0;
+  Entry *nxt = c0 ? T.buf0 : T.buf1;
+  for (int i = lane; i < nk; i += 32) {
+    const Entry e = cur[i];
+    int lo = 0, hi = nc;  // candidates below e
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (key_less(wb[mid], e))
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    const int r = i + lo;
+    if (r < K) nxt[r] = e;
+  }
+  if (lane < nc) {
+    const Entry e = wb[lane];
+    int lo = 0, hi = nk;  // kept entries below e
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (key_less(cur[mid], e))
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    const int r = lane + lo;
+    if (r < K) nxt[r] = e;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    const int nn = min(K, nk + nc);
+    *T.nk = nn;
+    *T.cur = c0 ^ 1;
+    const double th = (nn == K) ? nxt[K - 1].chi2 : CUDART_INF;
+    *T.thr = th;
+    if (P.gthr && nn == K)
+      atomicMin(P.gthr, (unsigned long long)__double_as_longlong(th));
+    __threadfence_block();
+    atomicExch(T.lock, 0);
+  }
+  __syncwarp();
+}
+
+// One warp group: trajectories [lo, hi) of the line-aligned pass (lined),
+// or sample positions [lo, hi) of a strided pass, each lane owning one.
+// Phase 1 in pairs of trajectories, the FP64 solve, the pruning test
+// against min(block K-th, grid-wide threshold), phase 2 for the survivors,
+// then the dense store or the merge into the block's top-K.
+template <bool DENSE, bool H>
+__device__ __forceinline__ void search_group(const SearchParams &P,
+                                             const float4 *ep, BlockTopK &T,
+                                             const int K, const int warp,
+                                             const int lane, long long lo,
+                                             long long hi, const bool lined,
+                                             unsigned long long &n_exact) {
+  const int nvalid = (int)max(0LL, hi - lo);
+  if (nvalid == 0) return;  // warp-uniform
+  const int ml = lane < nvalid ? lane : 0;
+  const long long my = lined ? lo + ml : P.first + (lo + ml) * P.stride;
+  const long long out_off = lined ? lo - P.first : lo;  // dense output
+  const TrajC mine = traj_consts(P, ep, my);
+  Acc mine_s = {0.f, 0.f, 0.f};
+  for (int k = 0; k < nvalid; k += 2) {
+    const TrajC ca = shfl_traj(mine, k);
+    if (k + 1 < nvalid) {
+      const TrajC cb = shfl_traj(mine, k + 1);
+      Acc ra, rb;
+      phase1_pair<H>(P, ep, ca, cb, lane, ra, rb);
+      if (lane == k) mine_s = ra;
+      if (lane == k + 1) mine_s = rb;
+    } else {
+      const Acc ra = phase1<H>(P, ep, ca, lane);
+      if (lane == k) mine_s = ra;
+    }
+  }
+  const Solved sol =
+      solve2(P, (double)mine_s.a, (double)mine_s.b, (double)mine_s.d);
+  double thr = CUDART_INF;
+  if (!DENSE) {
+    thr = *T.thr;
+    if (P.gthr) thr = fmin(thr, bits_to_chi2(__ldcg(P.gthr)));
+  }
+  bool cand_me = lane < nvalid;
+  // 1e-4: margin for the FP32 rounding of the exact sweep itself
+  if (!DENSE && cand_me && thr < CUDART_INF)
+    cand_me = sol.lb * (1.0 - 1e-4) <= thr;
+  unsigned todo = __ballot_sync(kFull, cand_me);
+  n_exact += __popc(todo);
+  const float myFs = __double2float_rn(sol.Fs);
+  const float myBc = __double2float_rn(sol.Bc);
+  double my_chi2 = CUDART_INF;
+  while (todo) {
+    const int k = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const TrajC c = shfl_traj(mine, k);
+    const float Fs = __shfl_sync(kFull, myFs, k);
+    const float Bc = __shfl_sync(kFull, myBc, k);
+    const double chi2 = phase2<H>(P, ep, c, lane, Fs, Bc);
+    if (lane == k) my_chi2 = isnan(chi2) ? CUDART_INF : chi2;
+  }
+  if (DENSE) {
+    if (lane < nvalid) {
+      const long long o = out_off + lane;
+      P.dchi2[o] = my_chi2;
+      if (P.dFs) P.dFs[o] = sol.Fs;
+      if (P.dFb) P.dFb[o] = sol.Bc + P.Fref - sol.Fs;
+    }
+  } else {
+    const bool keep = lane < nvalid && my_chi2 <= thr && my_chi2 < CUDART_INF;
+    warp_merge(P, T, K, warp, lane, keep, my_chi2, my);
+  }
+}
+
+// Record of one selected trajectory e (warp-collective; lane 0 writes *dst):
+// the phase-1 sums, the solve and the phase-2 chi^2 recomputed with the
+// search's device functions, on the epochs at P.ep.
+template <bool H>
+__device__ __forceinline__ void fill_one(const SearchParams &P, const Entry e,
+                                         const double *t0abs,
+                                         const double *tEv, const int lane,
+                                         morse_fit *dst) {
+  morse_fit r;
+  const long long total = (long long)P.n_u0 * P.n_alpha * P.n_t0 * P.n_tE;
+  if (e.idx < 0 || e.idx >= total) {
+    if (lane == 0) {
+      r.chi2 = CUDART_INF;
+      r.t0 = r.tE = r.u0 = r.alpha = r.Fs = r.Fb = 0.0;
+      r.idx = -1;
+      r.flags = 0;
+      r.reserved = 0;
+      *dst = r;
+    }
+    return;
+  }
+  const TrajC c = traj_consts(P, P.ep, e.idx);
+  const Acc s = phase1<H>(P, P.ep, c, lane);
+  const Solved sol = solve2(P, (double)s.a, (double)s.b, (double)s.d);
+  const double chi2 = phase2<H>(P, P.ep, c, lane, __double2float_rn(sol.Fs),
+                                __double2float_rn(sol.Bc));
+  if (lane == 0) {
+    long long q = e.idx;
+    const int itE = (int)(q % P.n_tE);
+    q /= P.n_tE;
+    const int it0 = (int)(q % P.n_t0);
+    q /= P.n_t0;
+    const int ia = (int)(q % P.n_alpha);
+    const int iu = (int)(q / P.n_alpha);
+    r.chi2 = isnan(chi2) ? CUDART_INF : chi2;
+    r.t0 = t0abs[it0];
+    r.tE = tEv[itE];
+    r.u0 = P.u0v[iu];
+    r.alpha = 2.0 * CUDART_PI * (double)ia / (double)P.n_alpha;
+    r.Fs = sol.Fs;
+    r.Fb = sol.Bc + P.Fref - sol.Fs;
+    r.idx = e.idx;
+    r.flags = sol.degenerate ? MORSE_FIT_DEGENERATE : 0;
+    r.reserved = 0;
+    *dst = r;
+  }
+}
+
+}  // namespace dev
+}  // namespace morse

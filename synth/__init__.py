@@ -134,3 +134,24 @@ def sq_axes(cfg=CFG1):
     q = np.exp(np.linspace(np.log(cfg["q_lo"]), np.log(cfg["q_hi"]),
                            cfg["n_q"]))
     return s, q
+
+
+# Batched workload: 256 events of log-uniform length in [200, 20000] epochs
+# (truths from truth_draws, light curves from the point-source polynomial
+# by the caller), against a bank of 64 maps of 1024^2 texels over [-2, 2]^2
+# with (s, q) log-uniform in [0.3, 3] x [1e-5, 1e-1], 200,000 trajectories
+# per (event, map) pair: 25 u0 x 40 alpha x 20 t0 x 10 tE.
+CFG3 = dict(n_events=256, len_lo=200, len_hi=20000, n_maps=64, L=2.0,
+            npix=1024, nray=10000, X=3.0, seed=3,
+            grid=dict(n_u0=25, n_alpha=40, n_t0=20, n_tE=10, u0_lo=1e-3,
+                      u0_hi=0.5, t0_lo=-2.0, t0_hi=2.0, tE_lo=5.0,
+                      tE_hi=80.0, u0_log=True, tE_log=True),
+            top_k=16)
+
+
+def bank_sq(n_maps: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """(s, q) of a map bank: log-uniform in [0.3, 3] x [1e-5, 1e-1]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    s = np.exp(rng.uniform(np.log(0.3), np.log(3.0), n_maps))
+    q = np.exp(rng.uniform(np.log(1e-5), np.log(1e-1), n_maps))
+    return s, q
