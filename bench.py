@@ -48,7 +48,7 @@ FP32_LANES_PER_SM = 128
 # the search kernel's sources: its traffic record holds while they match
 KERNEL_SRC = [os.path.join(ROOT, "paper_1511_01157_gb300", "csrc", f)
               for f in ("k_search.cu", "search_common.cuh",
-                        "morse_internal.cuh")]
+                        "search_group.cuh", "morse_internal.cuh")]
 PROFILE = os.path.join(ROOT, "profiles", "k_search_cfg1.md")
 
 
