@@ -40,33 +40,21 @@ __device__ __forceinline__ float in_grad(const SearchParams &P, const TrajC &c,
                                          float cs, float sn, float u0,
                                          float t, Deriv &g) {
   const float vx = __fmaf_rn(c.ax, t, c.bx), vy = __fmaf_rn(c.ay, t, c.by);
-  const float cx = fmaxf(vx, P.vmin), cy = fmaxf(vy, P.vmin);
-  const float tx = __fadd_rd(cx, 12582912.f), ty = __fadd_rd(cy, 12582912.f);
-  const float fx = __fsub_rn(cx, __fsub_rn(tx, 12582912.f));
-  const float fy = __fsub_rn(cy, __fsub_rn(ty, 12582912.f));
-  const unsigned bx = (unsigned)__float_as_int(tx);
-  const unsigned by = (unsigned)__float_as_int(ty);
-  const unsigned idx = by * (unsigned)P.qpitch + bx + P.qidx0;
-#ifdef MORSE_CHECK_BOUNDS
-  const int ix = (int)(bx - 0x4B400000u) + P.half;
-  const int iy = (int)(by - 0x4B400000u) + P.half;
-  if ((unsigned)ix >= (unsigned)P.npix || (unsigned)iy >= (unsigned)P.npix) {
-    if (P.err) atomicOr(P.err, 2u);
+  TexPos p;
+  if (!tex_pos(P, vx, vy, p)) {
     g.d[0] = g.d[1] = g.d[2] = g.d[3] = 0.f;
     return 0.f;
   }
-#endif
-  const float4 q = __ldg(&P.quad[idx]);
-  const float dx0 = __fsub_rn(q.y, q.x), dx1 = __fsub_rn(q.w, q.z);
-  const float r0 = __fmaf_rn(fx, dx0, q.x);
-  const float r1 = __fmaf_rn(fx, dx1, q.z);
-  const float am1 = __fmaf_rn(fy, __fsub_rn(r1, r0), r0);
-  // gradient in pixel units; zero along an axis clamped to the first
-  // texel centre (the lookup is constant there)
-  float gx = __fmaf_rn(fy, __fsub_rn(dx1, dx0), dx0);
-  float gy = __fsub_rn(r1, r0);
-  if (vx < P.vmin) gx = 0.f;
-  if (vy < P.vmin) gy = 0.f;
+  const float4 q = __ldg(&P.quad[p.idx]);
+  const float dx0 = q.y, dx1 = q.w;  // x-differences of the cell's rows
+  const float r0 = __fmaf_rn(p.fx, dx0, q.x);
+  const float r1 = __fmaf_rn(p.fx, dx1, q.z);
+  const float am1 = __fmaf_rn(p.fy, __fsub_rn(r1, r0), r0);
+  // gradient in pixel units; the edge cells below and above the map have
+  // zero differences across the edge, so the gradient there is zero along
+  // that axis (the lookup is constant)
+  const float gx = __fmaf_rn(p.fy, __fsub_rn(dx1, dx0), dx0);
+  const float gy = __fsub_rn(r1, r0);
   // per unit of y: divide by Delta
   const float Gx = __fmul_rn(gx, P.invDf), Gy = __fmul_rn(gy, P.invDf);
   const float Gp = __fmaf_rn(Gx, cs, __fmul_rn(Gy, sn));

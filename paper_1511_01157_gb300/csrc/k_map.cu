@@ -213,41 +213,62 @@ __global__ void __launch_bounds__(kRayThreads)
   }
 }
 
-// counts -> A = count * f (FP64 product rounded to FP32) and 2x2 quads of
-// A - 1 with the last row/column replicated.
+// Texel tables.  Quad (c, r), c, r in [0, npix], describes the bilinear
+// cell whose lower corner is texel (c - 1, r - 1): the column and row below
+// the map repeat its edge (so that a lookup below the first texel centre
+// reads the edge value, the clamping rule, without a clamp), and so do the
+// column and row at npix - 1.  The FP32 quad holds
+//   (a00 - 1, (a10 - 1) - (a00 - 1), a01 - 1, (a11 - 1) - (a01 - 1)),
+// the differences rounded in FP32 exactly as the lookup would take them.
+__device__ __forceinline__ int clampi(int v, int n) {
+  return v < 0 ? 0 : (v >= n ? n - 1 : v);
+}
+
+// counts -> A = count * f (FP64 product rounded to FP32)
 __device__ __forceinline__ float mag_of(const uint32_t *c, int npix, int x,
                                         int y, double f) {
   return __double2float_rn(__dmul_rn((double)c[(size_t)y * npix + x], f));
 }
 
+__device__ __forceinline__ float4 quad_of(float a00, float a10, float a01,
+                                          float a11) {
+  // A - 1: FP32 of the FP32 value, exact for A <= 2
+  const float m00 = a00 - 1.0f, m10 = a10 - 1.0f;
+  const float m01 = a01 - 1.0f, m11 = a11 - 1.0f;
+  return make_float4(m00, __fsub_rn(m10, m00), m01, __fsub_rn(m11, m01));
+}
+
 __global__ void k_counts_to_map(const uint32_t *__restrict__ counts, int npix,
                                 double f, float *__restrict__ A,
                                 float4 *__restrict__ quad, int qpitch) {
-  size_t n = (size_t)npix * npix;
+  const int side = npix + 1;
+  const size_t n = (size_t)side * side;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
        k += (size_t)gridDim.x * blockDim.x) {
-    int x = (int)(k % npix), y = (int)(k / npix);
-    int x1 = min(x + 1, npix - 1), y1 = min(y + 1, npix - 1);
-    float a00 = mag_of(counts, npix, x, y, f);
-    A[k] = a00;
-    // the search reads A - 1 (FP32 of the FP32 value: exact for A <= 2)
-    quad[(size_t)y * qpitch + x] =
-        make_float4(a00 - 1.0f, mag_of(counts, npix, x1, y, f) - 1.0f,
-                    mag_of(counts, npix, x, y1, f) - 1.0f,
-                    mag_of(counts, npix, x1, y1, f) - 1.0f);
+    const int c = (int)(k % side), r = (int)(k / side);
+    const int x0 = clampi(c - 1, npix), x1 = clampi(c, npix);
+    const int y0 = clampi(r - 1, npix), y1 = clampi(r, npix);
+    const float a00 = mag_of(counts, npix, x0, y0, f);
+    if (c >= 1 && r >= 1) A[(size_t)(r - 1) * npix + (c - 1)] = a00;
+    quad[(size_t)r * qpitch + c] =
+        quad_of(a00, mag_of(counts, npix, x1, y0, f),
+                mag_of(counts, npix, x0, y1, f),
+                mag_of(counts, npix, x1, y1, f));
   }
 }
 
 __global__ void k_quads_from_A(const float *__restrict__ A, int npix,
                                float4 *__restrict__ quad, int qpitch) {
-  size_t n = (size_t)npix * npix;
+  const int side = npix + 1;
+  const size_t n = (size_t)side * side;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
        k += (size_t)gridDim.x * blockDim.x) {
-    int x = (int)(k % npix), y = (int)(k / npix);
-    int x1 = min(x + 1, npix - 1), y1 = min(y + 1, npix - 1);
-    quad[(size_t)y * qpitch + x] = make_float4(
-        A[(size_t)y * npix + x] - 1.0f, A[(size_t)y * npix + x1] - 1.0f,
-        A[(size_t)y1 * npix + x] - 1.0f, A[(size_t)y1 * npix + x1] - 1.0f);
+    const int c = (int)(k % side), r = (int)(k / side);
+    const int x0 = clampi(c - 1, npix), x1 = clampi(c, npix);
+    const int y0 = clampi(r - 1, npix), y1 = clampi(r, npix);
+    quad[(size_t)r * qpitch + c] = quad_of(
+        A[(size_t)y0 * npix + x0], A[(size_t)y0 * npix + x1],
+        A[(size_t)y1 * npix + x0], A[(size_t)y1 * npix + x1]);
   }
 }
 
@@ -265,19 +286,22 @@ __global__ void k_half_codes(const float *__restrict__ A, size_t n,
     codes[k] = half_code(A[k], a_floor);
 }
 
-// (x00, x10) in .x and (x01, x11) in .y, low half first
+// (x00, x10) in .x and (x01, x11) in .y, low half first; same cells and
+// edge repetition as the FP32 quads, codes undifferenced
 __global__ void k_half_quads(const uint16_t *__restrict__ codes, int npix,
                              uint2 *__restrict__ quadh, int qpitch) {
-  size_t n = (size_t)npix * npix;
+  const int side = npix + 1;
+  const size_t n = (size_t)side * side;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
        k += (size_t)gridDim.x * blockDim.x) {
-    int x = (int)(k % npix), y = (int)(k / npix);
-    int x1 = min(x + 1, npix - 1), y1 = min(y + 1, npix - 1);
-    const unsigned c00 = codes[(size_t)y * npix + x];
-    const unsigned c10 = codes[(size_t)y * npix + x1];
-    const unsigned c01 = codes[(size_t)y1 * npix + x];
+    const int c = (int)(k % side), r = (int)(k / side);
+    const int x0 = clampi(c - 1, npix), x1 = clampi(c, npix);
+    const int y0 = clampi(r - 1, npix), y1 = clampi(r, npix);
+    const unsigned c00 = codes[(size_t)y0 * npix + x0];
+    const unsigned c10 = codes[(size_t)y0 * npix + x1];
+    const unsigned c01 = codes[(size_t)y1 * npix + x0];
     const unsigned c11 = codes[(size_t)y1 * npix + x1];
-    quadh[(size_t)y * qpitch + x] = make_uint2(c00 | (c10 << 16),
+    quadh[(size_t)r * qpitch + c] = make_uint2(c00 | (c10 << 16),
                                                c01 | (c11 << 16));
   }
 }
@@ -314,6 +338,10 @@ cudaError_t launch_rayshoot(const RayParams &P, bool fp64, int grid,
   return cudaGetLastError();
 }
 
+static size_t quad_cells(int npix) {
+  return (size_t)(npix + 1) * (size_t)(npix + 1);
+}
+
 static int elementwise_grid(size_t n) {
   size_t g = (n + 255) / 256;
   if (g > 8192) g = 8192;
@@ -324,16 +352,15 @@ static int elementwise_grid(size_t n) {
 cudaError_t launch_counts_to_map(const uint32_t *counts, int npix, double f,
                                  float *A, float4 *quad, int qpitch,
                                  cudaStream_t st) {
-  size_t n = (size_t)npix * npix;
-  k_counts_to_map<<<elementwise_grid(n), 256, 0, st>>>(counts, npix, f, A,
-                                                       quad, qpitch);
+  k_counts_to_map<<<elementwise_grid(quad_cells(npix)), 256, 0, st>>>(
+      counts, npix, f, A, quad, qpitch);
   return cudaGetLastError();
 }
 
 cudaError_t launch_quads_from_A(const float *A, int npix, float4 *quad,
                                 int qpitch, cudaStream_t st) {
-  size_t n = (size_t)npix * npix;
-  k_quads_from_A<<<elementwise_grid(n), 256, 0, st>>>(A, npix, quad, qpitch);
+  k_quads_from_A<<<elementwise_grid(quad_cells(npix)), 256, 0, st>>>(
+      A, npix, quad, qpitch);
   return cudaGetLastError();
 }
 
@@ -344,8 +371,8 @@ cudaError_t launch_half_from_A(const float *A, int npix, double a_floor,
   k_half_codes<<<elementwise_grid(n), 256, 0, st>>>(A, n, a_floor, codes);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_half_quads<<<elementwise_grid(n), 256, 0, st>>>(codes, npix, quadh,
-                                                    qpitch);
+  k_half_quads<<<elementwise_grid(quad_cells(npix)), 256, 0, st>>>(
+      codes, npix, quadh, qpitch);
   return cudaGetLastError();
 }
 

@@ -203,7 +203,7 @@ morse_map *map_alloc(morse_ctx *ctx, int npix, bool counts) {
   size_t n = (size_t)npix * npix;
   m->qpitch = morse::quad_pitch(npix);
   bool ok = cudaMalloc(&m->A, n * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&m->quad, (size_t)npix * m->qpitch * sizeof(float4)) ==
+            cudaMalloc(&m->quad, morse::quad_count(npix) * sizeof(float4)) ==
                 cudaSuccess &&
             cudaMalloc(&m->tot, 2 * sizeof(unsigned long long)) == cudaSuccess;
   if (ok && counts)
@@ -226,7 +226,7 @@ bool map_ensure_half(morse_map *m) {
   if (m->quadh) return true;
   size_t n = (size_t)m->npix * m->npix;
   if (cudaMalloc(&m->hcodes, n * sizeof(uint16_t)) != cudaSuccess ||
-      cudaMalloc(&m->quadh, (size_t)m->npix * m->qpitch * sizeof(uint2)) !=
+      cudaMalloc(&m->quadh, morse::quad_count(m->npix) * sizeof(uint2)) !=
           cudaSuccess) {
     cudaGetLastError();
     if (m->hcodes) cudaFree(m->hcodes);
@@ -381,14 +381,11 @@ void map_params(const morse_map *map, morse::SearchParams *P) {
   P->quad = map->quad;
   P->quadh = morse::map_h16(map) ? map->quadh : nullptr;
   P->qpitch = map->qpitch;
-  P->qidx0 = (unsigned)(map->npix / 2 - 0x4B400000) *
-             (unsigned)(map->qpitch + 1);
+  P->qidx0 = morse::quad_idx0(map->npix);
   P->npix = map->npix;
   P->half = map->npix / 2;
   P->vlo = -(float)(map->npix / 2) - 0.5f;
   P->vhi = (float)(map->npix - map->npix / 2) - 0.5f;
-  P->vmin = -(float)(map->npix / 2);
-  P->vmax = (float)(map->npix - map->npix / 2 - 1);
   P->L = map->L;
   P->dlt = dlt;
   P->coff = 0.5 * map->npix - (double)(map->npix / 2) - 0.5;
@@ -908,7 +905,7 @@ morse_status batch_upload(morse_ctx *ctx, BatchHost &H, const BatchLayout &L,
   morse::BatchParams B;
   memset(&B, 0, sizeof(B));
   map_params(map0, &B.S);
-  B.S.quad = nullptr;
+  B.S.quad = nullptr;  // per pair, from B.tab
   B.S.quadh = nullptr;
   B.S.u0v = tab + o_u0;
   B.S.ca = tab + o_ca;

@@ -47,7 +47,9 @@ struct morse_map {
   bool has_counts;
   uint32_t *counts;         // [npix*npix] ray counts (device)
   float *A;                 // [npix*npix] FP32 magnification (device)
-  float4 *quad;             // [npix rows x qpitch] 2x2 neighbourhoods of A-1
+  float4 *quad;             // [npix + 1 rows x qpitch] bilinear cells of
+                            // A - 1 (edge rows/columns repeated below and
+                            // above the map), pre-differenced along x
   int qpitch;               // quads per row: npix + pad (spreads the rows of
                             // a steep track over cache sets)
   unsigned long long *tot;  // [2] off-map, lost (device)
@@ -56,7 +58,7 @@ struct morse_map {
   // selected later): half(log10(max(A, a_floor))) per texel, and the same
   // 2x2 neighbourhoods as quad packed as four halves (8 bytes)
   uint16_t *hcodes;         // [npix*npix]
-  uint2 *quadh;             // [npix rows x qpitch]
+  uint2 *quadh;             // [npix + 1 rows x qpitch], cells as quad
   double a_floor;           // half a ray (ray-shot maps), else 1e-6
   bool half_valid;          // the FP16 table holds the current values
   int lookup;               // MORSE_STORE_FP32 or MORSE_STORE_FP16LOG
@@ -100,11 +102,19 @@ constexpr int kRayThreads = 512;  // threads per ray-shooting block
 
 cudaError_t launch_rayshoot(const RayParams &P, bool fp64, int grid,
                             cudaStream_t st);
-// Quad row pitch for an npix map (float4 units).
+// Quad row pitch for an npix map (quads; npix + 1 cells per row are used).
 #ifndef MORSE_QPITCH_PAD
 #define MORSE_QPITCH_PAD 8
 #endif
 inline int quad_pitch(int npix) { return npix + MORSE_QPITCH_PAD; }
+inline size_t quad_count(int npix) {
+  return (size_t)(npix + 1) * (size_t)quad_pitch(npix);
+}
+// quad index offset of the folded floor-bit index (see SearchParams)
+inline unsigned quad_idx0(int npix) {
+  return (unsigned)(npix / 2 + 1 - 0x4B400000) *
+         (unsigned)(quad_pitch(npix) + 1);
+}
 
 cudaError_t launch_counts_to_map(const uint32_t *counts, int npix, double f,
                                  float *A, float4 *quad, int qpitch,
@@ -129,12 +139,10 @@ struct SearchParams {
   const float4 *quad;
   const uint2 *quadh;
   int npix, half;           // npix, npix/2
-  int qpitch;               // quad row pitch (float4 units)
+  int qpitch;               // quad row pitch (quads)
   unsigned qidx0;           // quad index offset for the raw floor bits:
-                            // (half - 0x4B400000) (qpitch + 1) mod 2^32
+                            // (half + 1 - 0x4B400000) (qpitch + 1) mod 2^32
   float vlo, vhi;           // inside iff vlo < v < vhi (centred coords)
-  float vmin;               // -npix/2: clamp to the first texel centre
-  float vmax;               // npix - npix/2 - 1: centre of the last texel
   float voff;               // -coff: y = (v + voff) Delta
   float dltf;               // Delta
   float invDf;              // 1/Delta

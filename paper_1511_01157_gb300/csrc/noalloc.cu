@@ -183,14 +183,11 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   P.quad = map->quad;
   P.quadh = h16 ? map->quadh : nullptr;
   P.qpitch = map->qpitch;
-  P.qidx0 = (unsigned)(map->npix / 2 - 0x4B400000) *
-            (unsigned)(map->qpitch + 1);
+  P.qidx0 = morse::quad_idx0(map->npix);
   P.npix = map->npix;
   P.half = map->npix / 2;
   P.vlo = -(float)(map->npix / 2) - 0.5f;
   P.vhi = (float)(map->npix - map->npix / 2) - 0.5f;
-  P.vmin = -(float)(map->npix / 2);
-  P.vmax = (float)(map->npix - map->npix / 2 - 1);
   P.L = map->L;
   P.dlt = dlt;
   P.coff = 0.5 * map->npix - (double)(map->npix / 2) - 0.5;

@@ -153,9 +153,11 @@ __device__ __forceinline__ float pspl_u2(float u2) {
                    rsqrt_approx(__fmul_rn(u2, __fadd_rn(u2, 4.f))));
 }
 
-// Texel-quad index and bilinear fractions of centred coordinates (vx, vy)
-// (clamped below to the first texel centre; the caller keeps them below
-// the last).
+// Quad index and bilinear fractions of centred coordinates (vx, vy) inside
+// the map.  Inside means vlo < v < vhi, i.e. floor(v) from -half - 1 to
+// npix - half - 1: the cell whose lower corner is texel floor(v) + half,
+// stored at quad (floor(v) + half + 1) in each axis, and the cells of the
+// edge repeat the edge texels, so no coordinate is clamped.
 struct TexPos {
   unsigned idx;
   float fx, fy;
@@ -163,24 +165,22 @@ struct TexPos {
 
 __device__ __forceinline__ bool tex_pos(const SearchParams &P, float vx,
                                         float vy, TexPos &o) {
-  const float cx = fmaxf(vx, P.vmin);
-  const float cy = fmaxf(vy, P.vmin);
-  // floor: adding 1.5 * 2^23 rounding down leaves floor(c) in the low
-  // mantissa bits; the fraction c - floor(c) is exact
-  const float tx = __fadd_rd(cx, 12582912.f), ty = __fadd_rd(cy, 12582912.f);
-  o.fx = __fsub_rn(cx, __fsub_rn(tx, 12582912.f));
-  o.fy = __fsub_rn(cy, __fsub_rn(ty, 12582912.f));
-  // texel (ix, iy) = floor(c) + half; quad index iy * qpitch + ix, folded
-  // into one multiply-add on the raw bit patterns (mod 2^32, exact because
-  // the index is in [0, npix * qpitch))
+  // floor: adding 1.5 * 2^23 rounding down leaves floor(v) in the low
+  // mantissa bits; the fraction v - floor(v) is exact
+  const float tx = __fadd_rd(vx, 12582912.f), ty = __fadd_rd(vy, 12582912.f);
+  o.fx = __fsub_rn(vx, __fsub_rn(tx, 12582912.f));
+  o.fy = __fsub_rn(vy, __fsub_rn(ty, 12582912.f));
+  // quad index (iy + 1) * qpitch + (ix + 1) with i = floor(v) + half,
+  // folded into one multiply-add on the raw bit patterns (mod 2^32, exact
+  // because the index is in [0, (npix + 1) * qpitch))
   const unsigned bx = (unsigned)__float_as_int(tx);
   const unsigned by = (unsigned)__float_as_int(ty);
   o.idx = by * (unsigned)P.qpitch + bx + P.qidx0;
 #ifdef MORSE_CHECK_BOUNDS
-  // checked build: record an out-of-range texel and skip the access
-  const int ix = (int)(bx - 0x4B400000u) + P.half;
-  const int iy = (int)(by - 0x4B400000u) + P.half;
-  if ((unsigned)ix >= (unsigned)P.npix || (unsigned)iy >= (unsigned)P.npix) {
+  // checked build: record an out-of-range cell and skip the access
+  const int cx = (int)(bx - 0x4B400000u) + P.half + 1;
+  const int cy = (int)(by - 0x4B400000u) + P.half + 1;
+  if ((unsigned)cx > (unsigned)P.npix || (unsigned)cy > (unsigned)P.npix) {
     if (P.err) atomicOr(P.err, 2u);
     return false;
   }
@@ -188,21 +188,20 @@ __device__ __forceinline__ bool tex_pos(const SearchParams &P, float vx,
   return true;
 }
 
-// Bilinear A - 1 at centred coordinates inside the map (the quads store
-// A - 1).  Coordinates below the first texel centre are clamped to it (the
-// lookup rule).  Above the last centre no clamp is needed: the caller only
-// passes epochs strictly inside the map, so floor(v) <= npix - half - 1, and
-// the last texel's quad repeats its edge values.  The bounds-checked build
-// verifies the index range.
+// Bilinear A - 1 at centred coordinates inside the map.  The quads store
+// (a00 - 1, a10 - a00, a01 - 1, a11 - a01) of the cell, the differences
+// rounded in FP32 when the table was built, so each row is one FMA.  Below
+// the first texel centre the edge cell repeats the edge values (the
+// clamping rule of the lookup); above the last centre likewise.  The
+// bounds-checked build verifies the index range.
 __device__ __forceinline__ float bilinear_m1(const SearchParams &P, float vx,
                                              float vy) {
   TexPos t;
   if (!tex_pos(P, vx, vy, t)) return 0.f;
-  const float fx = t.fx, fy = t.fy;
   const float4 q = __ldg(&P.quad[t.idx]);
-  const float r0 = __fmaf_rn(fx, __fsub_rn(q.y, q.x), q.x);
-  const float r1 = __fmaf_rn(fx, __fsub_rn(q.w, q.z), q.z);
-  return __fmaf_rn(fy, __fsub_rn(r1, r0), r0);
+  const float r0 = __fmaf_rn(t.fx, q.y, q.x);
+  const float r1 = __fmaf_rn(t.fx, q.w, q.z);
+  return __fmaf_rn(t.fy, __fsub_rn(r1, r0), r0);
 }
 
 // Lanes own epochs by index mod 32 in every range, so a lane always sums
