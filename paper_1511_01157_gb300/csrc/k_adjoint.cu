@@ -135,8 +135,11 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
   double sn, cs;
   sincos(al, &sn, &cs);
   const double tEc = (tE > 1e-6) ? tE : 1e-6;  // the host rejects tE <= 0
+  double tlo, thi;
+  slab_tau(P.L, u0, cs, sn, tlo, thi);
   const TrajC c =
-      make_traj(P, P.ep, u0, cs, sn, t0 - t_ref, 1.0 / (tEc * P.dlt));
+      make_traj(P, P.ep, u0, cs, sn, t0 - t_ref, 1.0 / (tEc * P.dlt), tEc,
+                tlo, thi);
   const Acc s1 = phase1<false>(P, P.ep, c, lane);
   const Solved sol = solve2(P, (double)s1.a, (double)s1.b, (double)s1.d);
   const float fFs = __double2float_rn(sol.Fs);

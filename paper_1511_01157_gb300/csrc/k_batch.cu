@@ -50,6 +50,8 @@ __device__ __forceinline__ SearchParams pair_params(const BatchParams &B,
   Q.SF = E.SF;
   Q.SFF = E.SFF;
   Q.Fref = E.Fref;
+  Q.invS1 = E.invS1;
+  Q.CFF = E.CFF;
   Q.gamma = E.gamma;
   Q.t0rel = E.t0rel;
   return Q;

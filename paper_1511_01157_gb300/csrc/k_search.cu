@@ -188,6 +188,21 @@ __global__ void k_fill(const FillParams F) {
   fill_one<H>(F.S, F.sel[w], F.t0abs, F.tEv, lane, &F.out[w]);
 }
 
+// The tau interval of every (u0, alpha) line inside the map.
+__global__ void k_slab(const double *__restrict__ u0v,
+                       const double *__restrict__ ca,
+                       const double *__restrict__ sa, int n_u0, int n_alpha,
+                       double L, double2 *__restrict__ slab) {
+  const int n = n_u0 * n_alpha;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += gridDim.x * blockDim.x) {
+    const int iu = i / n_alpha, ia = i - iu * n_alpha;
+    double lo, hi;
+    slab_tau(L, u0v[iu], ca[ia], sa[ia], lo, hi);
+    slab[i] = make_double2(lo, hi);
+  }
+}
+
 // Seed the grid-wide threshold with the K-th chi^2 of a pilot search over
 // a subset of the grid: K trajectories at or below it exist, so anything
 // above it cannot enter the global top-K.
@@ -324,6 +339,17 @@ cudaError_t launch_fill(const FillParams &F, cudaStream_t st) {
     k_fill<true><<<blocks, threads, 0, st>>>(F);
   else
     k_fill<false><<<blocks, threads, 0, st>>>(F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slab(const double *u0v, const double *ca, const double *sa,
+                        int n_u0, int n_alpha, double L, double2 *slab,
+                        cudaStream_t st) {
+  const int n = n_u0 * n_alpha;
+  int blocks = (n + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  if (blocks < 1) blocks = 1;
+  k_slab<<<blocks, 256, 0, st>>>(u0v, ca, sa, n_u0, n_alpha, L, slab);
   return cudaGetLastError();
 }
 

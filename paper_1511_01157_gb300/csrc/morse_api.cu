@@ -336,16 +336,21 @@ void axis(double lo, double hi, int n, int logsp, std::vector<double> &out) {
 // Device grid tables: u0, cos/sin alpha, t0 - t_ref, 1/(tE Delta), plus the
 // absolute t0 and tE for the output records.
 struct Tables {
+  double2 *slab;
   double *u0v, *ca, *sa, *t0rel, *invtEd, *t0abs, *tEv;
 };
 
 size_t tables_bytes(const morse_grid *g) {
-  return sizeof(double) *
-         (size_t)(g->n_u0 + 2 * g->n_alpha + 2 * g->n_t0 + 2 * g->n_tE);
+  return sizeof(double2) * (size_t)g->n_u0 * g->n_alpha +
+         sizeof(double) *
+             (size_t)(g->n_u0 + 2 * g->n_alpha + 2 * g->n_t0 + 2 * g->n_tE);
 }
 
+// Grid tables at dev (16-byte aligned): the lines' tau intervals inside
+// the map of half-width L (computed on the device), then u0, cos and sin
+// alpha, t0 - t_ref, 1/(tE Delta), t0, tE.
 morse_status upload_tables(morse_ctx *ctx, const morse_grid *g, double t_ref,
-                           double dlt, void *dev, Tables *T) {
+                           double L, double dlt, void *dev, Tables *T) {
   std::vector<double> u0, t0, tE, h;
   axis(g->u0_lo, g->u0_hi, g->n_u0, g->u0_log, u0);
   axis(g->t0_lo, g->t0_hi, g->n_t0, 0, t0);
@@ -360,7 +365,8 @@ morse_status upload_tables(morse_ctx *ctx, const morse_grid *g, double t_ref,
   for (double v : tE) h.push_back(1.0 / (v * dlt));
   h.insert(h.end(), t0.begin(), t0.end());
   h.insert(h.end(), tE.begin(), tE.end());
-  double *d = (double *)dev;
+  T->slab = (double2 *)dev;
+  double *d = (double *)(T->slab + (size_t)g->n_u0 * g->n_alpha);
   T->u0v = d;
   T->ca = T->u0v + g->n_u0;
   T->sa = T->ca + g->n_alpha;
@@ -370,8 +376,11 @@ morse_status upload_tables(morse_ctx *ctx, const morse_grid *g, double t_ref,
   T->tEv = T->t0abs + g->n_t0;
   // ordered on the context stream, then waited for: the host vector is
   // pageable and dies on return
-  MORSE_CUDA(ctx, cudaMemcpyAsync(dev, h.data(), h.size() * sizeof(double),
+  MORSE_CUDA(ctx, cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double),
                                   cudaMemcpyHostToDevice, ctx->stream));
+  MORSE_CUDA(ctx, morse::launch_slab(T->u0v, T->ca, T->sa, g->n_u0,
+                                     g->n_alpha, L, T->slab, ctx->stream));
+  ctx->launches += 1;
   MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return MORSE_OK;
 }
@@ -402,6 +411,8 @@ void event_params(const morse_event *ev, morse::SearchParams *P) {
   P->SF = ev->SF;
   P->SFF = ev->SFF;
   P->Fref = ev->Fref;
+  P->invS1 = ev->invS1;
+  P->CFF = ev->CFF;
   const double m = (double)((ev->n + 31) / 32);
   P->gamma = (m + 10.0) * ldexp(1.0, -24);
 }
@@ -413,6 +424,8 @@ void grid_params(const morse_grid *g, const Tables &T,
   P->sa = T.sa;
   P->t0rel = T.t0rel;
   P->invtEd = T.invtEd;
+  P->tEv = T.tEv;
+  P->slab = T.slab;
   P->n_u0 = g->n_u0;
   P->n_alpha = g->n_alpha;
   P->n_t0 = g->n_t0;
@@ -618,7 +631,8 @@ morse_status sweep_impl(morse_ctx *ctx, const morse_event *ev,
   char *base = (char *)ws;
   Tables T;
   const double dlt = (2.0 * extent) / (double)npix;
-  MORSE_TRY(upload_tables(ctx, grid, ev->t_ref, dlt, base + pl.off_tab, &T));
+  MORSE_TRY(upload_tables(ctx, grid, ev->t_ref, extent,
+                          dlt, base + pl.off_tab, &T));
   morse::SearchParams P;
   memset(&P, 0, sizeof(P));
   map_params(m, &P);
@@ -726,14 +740,15 @@ void batch_units(const std::vector<int> &pair_ids,
   }
 }
 
-// Grid tables shared by the pairs, plus each event's t0 - t_ref.
+// Grid tables shared by the pairs, plus each event's t0 - t_ref (after
+// the slab table, which the device fills).
 void batch_tables(const morse_grid *g, const morse_event *const *evs, int n_ev,
                   double dlt, std::vector<double> &h) {
   std::vector<double> u0, t0, tE;
   axis(g->u0_lo, g->u0_hi, g->n_u0, g->u0_log, u0);
   axis(g->t0_lo, g->t0_hi, g->n_t0, 0, t0);
   axis(g->tE_lo, g->tE_hi, g->n_tE, g->tE_log, tE);
-  h.clear();
+  h.assign((size_t)2 * g->n_u0 * g->n_alpha, 0.0);  // slab (device)
   h.insert(h.end(), u0.begin(), u0.end());
   for (int k = 0; k < g->n_alpha; ++k)
     h.push_back(cos(2.0 * M_PI * (double)k / (double)g->n_alpha));
@@ -820,6 +835,8 @@ morse_status batch_prepare(morse_ctx *ctx, const morse_event *const *evs,
     E.SF = evs[e]->SF;
     E.SFF = evs[e]->SFF;
     E.Fref = evs[e]->Fref;
+    E.invS1 = evs[e]->invS1;
+    E.CFF = evs[e]->CFF;
     E.gamma = ((double)((evs[e]->n + 31) / 32) + 10.0) * ldexp(1.0, -24);
     E.t0rel = nullptr;  // set once the table offset is known
   }
@@ -876,7 +893,8 @@ morse_status batch_upload(morse_ctx *ctx, BatchHost &H, const BatchLayout &L,
                           morse::BatchParams *Bp, morse::BatchParams *Bm,
                           double **t0abs, double **tEv) {
   double *tab = (double *)(base + L.off_tab);
-  const size_t o_u0 = 0, o_ca = o_u0 + g->n_u0, o_sa = o_ca + g->n_alpha,
+  const size_t o_u0 = (size_t)2 * g->n_u0 * g->n_alpha,
+               o_ca = o_u0 + g->n_u0, o_sa = o_ca + g->n_alpha,
                o_k = o_sa + g->n_alpha, o_t0 = o_k + g->n_tE,
                o_tE = o_t0 + g->n_t0, o_rel = o_tE + g->n_tE;
   for (int e = 0; e < n_ev; ++e)
@@ -900,6 +918,10 @@ morse_status batch_upload(morse_ctx *ctx, BatchHost &H, const BatchLayout &L,
          sizeof(int) * H.main_list0.size());
   MORSE_CUDA(ctx, cudaMemcpyAsync(base, h.data(), h.size(),
                                   cudaMemcpyHostToDevice, ctx->stream));
+  MORSE_CUDA(ctx, morse::launch_slab(tab + o_u0, tab + o_ca, tab + o_sa,
+                                     g->n_u0, g->n_alpha, map0->L,
+                                     (double2 *)tab, ctx->stream));
+  ctx->launches += 1;
   MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   BatchHdr *hd = (BatchHdr *)(base + L.off_hdr);
   morse::BatchParams B;
@@ -911,6 +933,8 @@ morse_status batch_upload(morse_ctx *ctx, BatchHost &H, const BatchLayout &L,
   B.S.ca = tab + o_ca;
   B.S.sa = tab + o_sa;
   B.S.invtEd = tab + o_k;
+  B.S.tEv = tab + o_tE;
+  B.S.slab = (const double2 *)tab;
   B.S.n_u0 = g->n_u0;
   B.S.n_alpha = g->n_alpha;
   B.S.n_t0 = g->n_t0;
@@ -1455,6 +1479,8 @@ morse_status morse_event_create(morse_ctx *ctx, const double *t,
   ev->SF = SF;
   ev->SFF = SFF;
   ev->Fref = Fref;
+  ev->invS1 = 1.0 / S1;
+  ev->CFF = SFF - SF * SF / S1;
   *out = ev;
   return MORSE_OK;
 }
@@ -1491,7 +1517,8 @@ morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
   char *base = (char *)ws;
   Tables T;
   const double dlt = (2.0 * map->L) / (double)map->npix;
-  MORSE_TRY(upload_tables(ctx, grid, ev->t_ref, dlt, base + pl.off_tab, &T));
+  MORSE_TRY(upload_tables(ctx, grid, ev->t_ref, map->L,
+                          dlt, base + pl.off_tab, &T));
   morse::SearchParams P;
   memset(&P, 0, sizeof(P));
   map_params(map, &P);
@@ -1536,7 +1563,8 @@ morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
   char *base = (char *)ws;
   Tables T;
   const double dlt = (2.0 * map->L) / (double)map->npix;
-  MORSE_TRY(upload_tables(ctx, grid, ev->t_ref, dlt, base + pl.off_tab, &T));
+  MORSE_TRY(upload_tables(ctx, grid, ev->t_ref, map->L,
+                          dlt, base + pl.off_tab, &T));
   morse::SearchParams P;
   memset(&P, 0, sizeof(P));
   map_params(map, &P);

@@ -70,6 +70,7 @@ struct morse_event {
   double t_ref;
   float4 *ep;               // [n] (t - t_ref, w, w (F - F_ref), F - F_ref)
   double S1, SF, SFF, Fref; // FP64 sums of the stored FP32 values
+  double invS1, CFF;        // 1/S_1, S_FF - S_F^2/S_1
 };
 
 namespace morse {
@@ -153,9 +154,12 @@ struct SearchParams {
   const float4 *ep;
   int n_ep;
   double S1, SF, SFF, Fref;
+  double invS1, CFF;        // 1/S_1 and S_FF - S_F^2/S_1 (pruning bound)
   double gamma;             // relative bound of the FP32 phase-1 sums
   // grid tables (device, FP64)
-  const double *u0v, *ca, *sa, *t0rel, *invtEd;
+  const double *u0v, *ca, *sa, *t0rel, *invtEd, *tEv;
+  const double2 *slab;      // [n_u0 n_alpha] tau interval of each line
+                            // inside the map (k_slab)
   int n_u0, n_alpha, n_t0, n_tE;
   long long first, count;   // trajectories first + i * stride, i < count
   long long stride;
@@ -228,12 +232,17 @@ cudaError_t launch_fill(const FillParams &F, cudaStream_t st);
 // gthr <- min(gthr, chi^2 bits of sel[k-1]) when that entry is real
 cudaError_t launch_seed_threshold(const Entry *sel, int k,
                                   unsigned long long *gthr, cudaStream_t st);
+// slab[iu n_alpha + ia] = tau interval of line (u0v[iu], alpha_ia) inside
+// the map of half-width L
+cudaError_t launch_slab(const double *u0v, const double *ca, const double *sa,
+                        int n_u0, int n_alpha, double L, double2 *slab,
+                        cudaStream_t st);
 // ---------------------------------------------------------------- batch
 // One light curve of a batch, as the batched search reads it.
 struct BatchEvent {
   const float4 *ep;         // time-sorted epochs (device)
   int n_ep;
-  double S1, SF, SFF, Fref, gamma;
+  double S1, SF, SFF, Fref, invS1, CFF, gamma;
   const double *t0rel;      // [n_t0] grid t0 - t_ref of this event
 };
 

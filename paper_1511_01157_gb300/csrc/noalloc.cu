@@ -113,11 +113,14 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   int grid = (int)std::min<long long>((long long)bps * ctx->sm_count, want);
   if (grid < 1) grid = 1;
 
-  // scratch layout: tables | status words | list A | list B | fits
+  // scratch layout: tables | line slabs | status words | list A | list B |
+  // fits
   const size_t tab_n =
       (size_t)g->n_u0 + 2 * (size_t)g->n_alpha + 2 * (size_t)g->n_t0 +
       2 * (size_t)g->n_tE;
-  const size_t off_w = up256(tab_n * sizeof(double));
+  const size_t off_slab = up256(tab_n * sizeof(double));
+  const size_t off_w =
+      up256(off_slab + sizeof(double2) * (size_t)g->n_u0 * g->n_alpha);
   const size_t off_a = off_w + 256;
   const size_t list = sizeof(morse::Entry) * (size_t)grid * K;
   const size_t off_b = up256(off_a + list);
@@ -177,6 +180,14 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   const double *u0v = d, *ca = u0v + g->n_u0, *sa = ca + g->n_alpha;
   const double *t0rel = sa + g->n_alpha, *invtEd = t0rel + g->n_t0;
   const double *t0abs = invtEd + g->n_tE, *tEabs = t0abs + g->n_t0;
+  double2 *slab = (double2 *)(base + off_slab);
+  e = morse::launch_slab(u0v, ca, sa, g->n_u0, g->n_alpha, map->L, slab,
+                         ctx->stream);
+  if (e != cudaSuccess) {
+    snprintf(ctx->err, sizeof(ctx->err), "line slabs: %s",
+             cudaGetErrorString(e));
+    return MORSE_ECUDA;
+  }
 
   morse::SearchParams P;
   memset(&P, 0, sizeof(P));
@@ -200,6 +211,8 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   P.S1 = ev->S1;
   P.SF = ev->SF;
   P.SFF = ev->SFF;
+  P.invS1 = ev->invS1;
+  P.CFF = ev->CFF;
   P.Fref = ev->Fref;
   P.gamma = ((double)((ev->n + 31) / 32) + 10.0) * ldexp(1.0, -24);
   P.u0v = u0v;
@@ -207,6 +220,8 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   P.sa = sa;
   P.t0rel = t0rel;
   P.invtEd = invtEd;
+  P.tEv = tEabs;
+  P.slab = slab;
   P.n_u0 = g->n_u0;
   P.n_alpha = g->n_alpha;
   P.n_t0 = g->n_t0;
@@ -247,7 +262,7 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
     e = morse::launch_fill(F, ctx->stream);
   }
   if (e == cudaSuccess) {
-    ctx->launches += 2 + (uint64_t)levels;
+    ctx->launches += 3 + (uint64_t)levels;
     e = cudaMemcpyAsync(out, fits, sizeof(morse_fit) * K,
                         cudaMemcpyDeviceToHost, ctx->stream);
   }

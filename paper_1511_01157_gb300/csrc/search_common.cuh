@@ -41,20 +41,52 @@ __device__ __forceinline__ bool key_less(double ca, long long ia, double cb,
   return ca < cb || (ca == cb && ia < ib);
 }
 
-// first epoch index with t > x (strict) or t >= x (!strict), t ascending
+// First epoch index with t > x (strict) or t >= x (!strict), t ascending.
+// The FP32 epoch times are compared with x rounded to FP32 downwards
+// (strict) or upwards: no FP32 value lies strictly between x and that
+// rounding, so t > x <=> t > RD(x) and t >= x <=> t >= RU(x) exactly, and
+// the search needs no FP64 compares.
 __device__ __forceinline__ int epoch_search(const float4 *ep, int n, double x,
                                             bool strict) {
+  const float xf = strict ? __double2float_rd(x) : __double2float_ru(x);
   int lo = 0, hi = n;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    const double t = (double)ep[mid].x;
-    const bool right = strict ? (t > x) : (t >= x);
+    const float t = ep[mid].x;
+    const bool right = strict ? (t > xf) : (t >= xf);
     if (right)
       hi = mid;
     else
       lo = mid + 1;
   }
   return lo;
+}
+
+// The tau interval (lo, hi) in which the line of (u0, alpha) is inside the
+// map, |y1| < L and |y2| < L (slab intersection; lo >= hi when the line
+// misses the map).  It depends on the line only, so the grid searches read
+// it from a table made once per call (k_slab).
+__device__ __forceinline__ void slab_tau(double L, double u, double c,
+                                         double s, double &lo_out,
+                                         double &hi_out) {
+  double lo = -CUDART_INF, hi = CUDART_INF;
+  const double us = u * s, uc = u * c;
+  if (c != 0.0) {
+    const double a0 = (-L + us) / c, a1 = (L + us) / c;
+    lo = fmax(lo, fmin(a0, a1));
+    hi = fmin(hi, fmax(a0, a1));
+  } else if (!(fabs(us) < L)) {
+    hi = lo;
+  }
+  if (s != 0.0) {
+    const double b0 = (-L - uc) / s, b1 = (L - uc) / s;
+    lo = fmax(lo, fmin(b0, b1));
+    hi = fmin(hi, fmax(b0, b1));
+  } else if (!(fabs(uc) < L)) {
+    hi = lo;
+  }
+  lo_out = lo;
+  hi_out = hi;
 }
 
 // Constants of trajectory j.  The kernel works in centred pixel coordinates
@@ -69,9 +101,10 @@ __device__ __forceinline__ int epoch_search(const float4 *ep, int n, double x,
 __device__ __forceinline__ TrajC make_traj(const SearchParams &P,
                                            const float4 *ep, double u,
                                            double c, double s, double t0,
-                                           double k) {
+                                           double k, double tE, double tlo,
+                                           double thi) {
   // u = u0, (c, s) = (cos, sin) alpha, t0 relative to t_ref,
-  // k = 1/(tE Delta)
+  // k = 1/(tE Delta), (tlo, thi) = the line's tau interval in the map
   const double ax = __dmul_rn(c, k), ay = __dmul_rn(s, k);
   const double cx = __dadd_rn(__dmul_rn(-__dmul_rn(u, s), P.invD), P.coff);
   const double cy = __dadd_rn(__dmul_rn(__dmul_rn(u, c), P.invD), P.coff);
@@ -84,27 +117,9 @@ __device__ __forceinline__ TrajC make_traj(const SearchParams &P,
   o.kt = __double2float_rn(kt);
   o.bt = __double2float_rn(-__dmul_rn(t0, kt));
   o.u02 = __double2float_rn(__dmul_rn(u, u));
-  // slab intersection of the line with |y1| < L, |y2| < L
-  double lo = -CUDART_INF, hi = CUDART_INF;
-  const double us = u * s, uc = u * c;
-  if (c != 0.0) {
-    const double a0 = (-P.L + us) / c, a1 = (P.L + us) / c;
-    lo = fmax(lo, fmin(a0, a1));
-    hi = fmin(hi, fmax(a0, a1));
-  } else if (!(fabs(us) < P.L)) {
-    hi = lo;
-  }
-  if (s != 0.0) {
-    const double b0 = (-P.L - uc) / s, b1 = (P.L - uc) / s;
-    lo = fmax(lo, fmin(b0, b1));
-    hi = fmin(hi, fmax(b0, b1));
-  } else if (!(fabs(uc) < P.L)) {
-    hi = lo;
-  }
-  if (lo < hi) {
-    const double tE = 1.0 / kt;
-    o.e_in = epoch_search(ep, P.n_ep, t0 + lo * tE, true);
-    o.e_out = epoch_search(ep, P.n_ep, t0 + hi * tE, false);
+  if (tlo < thi) {
+    o.e_in = epoch_search(ep, P.n_ep, t0 + tlo * tE, true);
+    o.e_out = epoch_search(ep, P.n_ep, t0 + thi * tE, false);
     if (o.e_out < o.e_in) o.e_out = o.e_in;
   } else {
     o.e_in = P.n_ep;
@@ -123,8 +138,9 @@ __device__ __forceinline__ TrajC traj_consts(const SearchParams &P,
   r /= P.n_t0;
   const int ia = (int)(r % P.n_alpha);
   const int iu = (int)(r / P.n_alpha);
+  const double2 sl = P.slab[iu * P.n_alpha + ia];
   return make_traj(P, ep, P.u0v[iu], P.ca[ia], P.sa[ia], P.t0rel[it0],
-                   P.invtEd[itE]);
+                   P.invtEd[itE], P.tEv[itE], sl.x, sl.y);
 }
 
 __device__ __forceinline__ TrajC shfl_traj(const TrajC &m, int k) {
@@ -394,7 +410,8 @@ __device__ __forceinline__ double phase2(const SearchParams &P,
 
 struct Solved {
   double Fs, Bc;      // Fb = Bc + Fref - Fs
-  double lb;          // rigorous lower bound of the exact chi^2
+  double bnum, bden;  // lower bound of the exact chi^2:
+                      // C_FF - min(C_FF, bnum / bden) if bden > 0, else 0
   bool degenerate;
 };
 
@@ -410,12 +427,14 @@ struct Solved {
 // <= sqrt(S_AA S_FF); S_AA has positive terms), so |C_AF| and C_AA are
 // bracketed and C_AF^2 / C_AA <= (|C_AF| + d_AF)^2 / (C_AA - d_AA).  This
 // holds however ill-conditioned (Fs, Fb) is: a nearly flat track explains
-// little of C_FF and is discarded all the same.  C_FF is exact (FP64 sums
-// of the stored values).  gamma is doubled as a margin.
+// little of C_FF and is discarded all the same.  C_FF is exact up to FP64
+// rounding (FP64 sums of the stored values, per event); T_A and T_AF are
+// taken as FP32 square roots rounded up, which only widens the bracket.
+// gamma is doubled as a margin.
 __device__ __forceinline__ Solved solve2(const SearchParams &P, double SA,
                                          double SAA, double SAF) {
   Solved o;
-  const double S1 = P.S1, SF = P.SF, SFF = P.SFF;
+  const double S1 = P.S1, SF = P.SF, iS1 = P.invS1;
   const double SAAu = SAA + 2.0 * SA + S1;
   const double det = SAA * S1 - SA * SA;
   if (!(det > 1e-12 * SAAu * S1)) {
@@ -429,19 +448,27 @@ __device__ __forceinline__ Solved solve2(const SearchParams &P, double SA,
     o.degenerate = false;
   }
   const double g = 2.0 * P.gamma;
-  const double CFF = SFF - SF * SF / S1;
-  const double CAA = SAA - SA * SA / S1;
-  const double CAF = SAF - SA * SF / S1;
-  const double TA = sqrt(S1 * SAA), TAF = sqrt(SAA * SFF);
-  const double dAA = g * (SAA + (2.0 * fabs(SA) * TA + g * TA * TA) / S1);
-  const double dAF = g * (TAF + TA * fabs(SF) / S1);
-  double X = CFF;  // upper bound of the part of C_FF the fit explains
-  if (CAA > dAA) {
-    const double num = fabs(CAF) + dAF;
-    X = fmin(CFF, num * num / (CAA - dAA));
-  }
-  o.lb = CFF - X;
+  const double CAA = SAA - SA * SA * iS1;
+  const double CAF = SAF - SA * SF * iS1;
+  const double TA = (double)__fsqrt_ru(__double2float_ru(S1 * SAA));
+  const double TAF = (double)__fsqrt_ru(__double2float_ru(SAA * P.SFF));
+  const double dAA = g * (SAA + (2.0 * fabs(SA) * TA + g * TA * TA) * iS1);
+  const double dAF = g * (TAF + TA * fabs(SF) * iS1);
+  const double num = fabs(CAF) + dAF;
+  o.bnum = num * num;
+  o.bden = CAA > dAA ? CAA - dAA : 0.0;
   return o;
+}
+
+// Whether the exact chi^2 of a solved trajectory can be at most thr:
+// bound * (1 - 1e-4) <= thr, the 1e-4 a margin for the FP32 rounding of the
+// exact sweep, evaluated as C_FF - bnum/bden <= thr / (1 - 1e-4) without a
+// division.
+__device__ __forceinline__ bool may_reach(const SearchParams &P,
+                                          const Solved &o, double thr) {
+  if (!(o.bden > 0.0)) return true;  // bound 0
+  const double t = thr * 1.0001000100010002;  // >= thr / (1 - 1e-4)
+  return (P.CFF - t) * o.bden <= o.bnum;
 }
 
 __device__ __forceinline__ double bits_to_chi2(unsigned long long b) {

@@ -156,7 +156,7 @@ __device__ __forceinline__ void search_group(const SearchParams &P,
   bool cand_me = lane < nvalid;
   // 1e-4: margin for the FP32 rounding of the exact sweep itself
   if (!DENSE && cand_me && thr < CUDART_INF)
-    cand_me = sol.lb * (1.0 - 1e-4) <= thr;
+    cand_me = may_reach(P, sol, thr);
   unsigned todo = __ballot_sync(kFull, cand_me);
   n_exact += __popc(todo);
   const float myFs = __double2float_rn(sol.Fs);
