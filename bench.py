@@ -44,6 +44,11 @@ UNIT = "traj-epoch evals/s"
 # tau 1, y 2, pixel coords 2, floor/frac/convert 6, bilinear 6, normal-
 # equation sums 3, residual sweep 2.
 ALG_INSTR_PER_EVAL = 22
+# one bilinear gather of a 2x2 FP32 cell per trajectory-epoch
+GATHER_BYTES_PER_EVAL = 16
+# ray shooting, per ray: ray coordinates 2, deflection of Eq. 2 through two
+# lenses 12 (+ 2 reciprocals), binning 6; plus one shared-memory atomic
+ALG_INSTR_PER_RAY = 22
 FP32_LANES_PER_SM = 128
 # the search kernel's sources: its traffic record holds while they match
 KERNEL_SRC = [os.path.join(ROOT, "paper_1511_01157_gb300", "csrc", f)
@@ -482,6 +487,7 @@ def run_gpu(args, cfg):
     ev = ctx.event(t, F, sig)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32,
                         device=f"cuda:{dev}")
+    probes = ctx.measure_peaks()  # measured denominators (before timing)
     evals_step = grid.size * len(t) * n_maps
     rays_step = cfg["nray"] ** 2 * n_maps
 
@@ -549,6 +555,12 @@ def run_gpu(args, cfg):
     peak_instr = props.multi_processor_count * FP32_LANES_PER_SM * \
         sm_max * 1e6 / 1e12
     achieved = evals_step * ALG_INSTR_PER_EVAL / (search_ms * 1e-3) / 1e12
+    evals_per_s_kernel = evals_step / (search_ms * 1e-3)
+    gather_gbs = evals_per_s_kernel * GATHER_BYTES_PER_EVAL / 1e9
+    rays_kernel = rays_step / (ray_ms * 1e-3)
+    ray_alu = probes["fp32_fma_per_s"] / ALG_INSTR_PER_RAY
+    ray_atom = probes["smem_atomics_per_s"]
+    ray_peak = min(ray_alu, ray_atom)
     traffic = recorded_traffic()
     clocks = clk.summary()
     per_launch = evals_step // n_maps
@@ -579,7 +591,27 @@ def run_gpu(args, cfg):
                            f"trajectory-epoch x {per_launch} per launch",
             "peak_source": f"{props.multi_processor_count} SMs x "
                            f"{FP32_LANES_PER_SM} FP32 lanes x {sm_max} MHz "
-                           f"({peak_kind} sm_max_mhz)"},
+                           f"({peak_kind} sm_max_mhz)",
+            "measured_fp32_fma_per_s": probes["fp32_fma_per_s"],
+            "frac_of_measured_fma": achieved * 1e12 /
+            probes["fp32_fma_per_s"],
+            "gather": {
+                "achieved_GBps": gather_gbs,
+                "l1_peak_GBps": probes["l1_gather_bytes_per_s"] / 1e9,
+                "l2_peak_GBps": probes["l2_gather_bytes_per_s"] / 1e9,
+                "frac_l1": gather_gbs * 1e9 / probes["l1_gather_bytes_per_s"],
+                "frac_l2": gather_gbs * 1e9 / probes["l2_gather_bytes_per_s"],
+                "algorithmic": f"{GATHER_BYTES_PER_EVAL} B per "
+                               "trajectory-epoch (one 2x2 FP32 cell)"}},
+        "rayshoot_roofline": {
+            "kernel": "k_rayshoot<FP32>", "rays_per_s": rays_kernel,
+            "bound": "alu" if ray_alu <= ray_atom else "smem_atomic",
+            "peak_rays_per_s": ray_peak, "frac": rays_kernel / ray_peak,
+            "algorithmic": f"{ALG_INSTR_PER_RAY} FP32 instr + 1 shared "
+                           "atomic per ray",
+            "peak_source": "min(measured FP32 FMA/s / instr, measured "
+                           "shared atomics/s)"},
+        "probes": probes,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(tp.nbytes + Fp.nbytes + sp.nbytes),
                 "d2h_bytes_per_step": int(grid.top_k * n_maps *
@@ -601,11 +633,15 @@ def run_gpu(args, cfg):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nth = os.cpu_count() or 1
         r = oracle_sample(cfg, args.cpu_frac, 7, nth)
+        r1 = oracle_sample(cfg, args.cpu_frac / 16, 7, 1)
         line["cpu_baseline"] = {
             "value": r["value"], "unit": UNIT, "cores": nth, "kind": "oracle",
             "sample": r["sample"] + "; one (s,q) map, the 651-map step "
                       "extrapolated linearly",
-            "rays_per_s": r["rays_per_s"]}
+            "rays_per_s": r["rays_per_s"],
+            "single_thread": {"value": r1["value"], "cores": 1,
+                              "rays_per_s": r1["rays_per_s"],
+                              "sample": r1["sample"]}}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()

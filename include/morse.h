@@ -389,6 +389,23 @@ morse_status morse_topk_merge(const morse_fit *const *lists,
                               const int *counts, int n_lists, int k,
                               morse_fit *out);
 
+/* Measured throughput of this GPU for the rooflines of the hot path (not
+ * part of the paper's method): FP32 and FP64 fused multiply-adds (thread
+ * instructions per second, 8 independent chains per thread), shared-memory
+ * atomic adds to pseudo-random bins of a 128 x 128 window (the ray-shooting
+ * histogram), and 16-byte loads from pseudo-random cells of a 64 KB window
+ * (served by L1) and of a 16 MB window (served by L2), in bytes per second.
+ * Each probe runs about 10 ms after one warm-up run.  Uses the context's
+ * workspace.  Errors: EINVAL, ENOMEM, ECUDA. */
+typedef struct {
+  double fp32_fma_per_s;
+  double fp64_fma_per_s;
+  double smem_atomics_per_s;
+  double l1_gather_bytes_per_s;
+  double l2_gather_bytes_per_s;
+} morse_peaks;
+morse_status morse_measure_peaks(morse_ctx *ctx, morse_peaks *out);
+
 /* Device time of the kernels of the most recent call on this context, in
  * milliseconds (CUDA events on the context stream), summed over every
  * launch of that kind in the call: which = 0 ray shooting, 1 counts-to-map,

@@ -91,6 +91,15 @@ class MapOpts(ctypes.Structure):
                 ("deflect", ctypes.c_int), ("store", ctypes.c_int)]
 
 
+class Peaks(ctypes.Structure):
+    """morse_peaks: measured throughput of the GPU for the rooflines."""
+    _fields_ = [("fp32_fma_per_s", ctypes.c_double),
+                ("fp64_fma_per_s", ctypes.c_double),
+                ("smem_atomics_per_s", ctypes.c_double),
+                ("l1_gather_bytes_per_s", ctypes.c_double),
+                ("l2_gather_bytes_per_s", ctypes.c_double)]
+
+
 class BatchShape(ctypes.Structure):
     """morse_batch_shape: launch shape of one epoch-count bucket."""
     _fields_ = [("tpg", ctypes.c_int), ("rounds", ctypes.c_int),
@@ -120,6 +129,7 @@ _SIGS = {
     "morse_map_free": (None, [_P]),
     "morse_map_set_lookup": (_S, [_P, _I]),
     "morse_grid_chi2_batch": (_S, [_P, _P, _I, _P, _I, _P, _P]),
+    "morse_measure_peaks": (_S, [_P, _P]),
     "morse_batch_tuning": (_S, [_P, _I]),
     "morse_batch_shape_of": (_S, [_P, _I64, _P, _P, _P]),
     "morse_map_half": (_S, [_P, _P, _P]),
@@ -269,6 +279,14 @@ class Context:
                                         _ptr(out))
         self._check(st, "morse_grid_chi2_batch")
         return out
+
+    def measure_peaks(self) -> dict:
+        """FP32/FP64 FMA, shared-atomic and L1/L2 gather throughput of this
+        GPU (morse_measure_peaks)."""
+        pk = Peaks()
+        self._check(_lib.morse_measure_peaks(self._h, ctypes.byref(pk)),
+                    "morse_measure_peaks")
+        return {f: getattr(pk, f) for f, _ in Peaks._fields_}
 
     def batch_tuning(self, on: bool):
         """Autotune batched launch shapes (default) or use the default rule;

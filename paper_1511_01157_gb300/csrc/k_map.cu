@@ -250,7 +250,7 @@ __global__ void k_counts_to_map(const uint32_t *__restrict__ counts, int npix,
     const int y0 = clampi(r - 1, npix), y1 = clampi(r, npix);
     const float a00 = mag_of(counts, npix, x0, y0, f);
     if (c >= 1 && r >= 1) A[(size_t)(r - 1) * npix + (c - 1)] = a00;
-    quad[(size_t)r * qpitch + c] =
+    quad[cell_index(c, r, qpitch)] =
         quad_of(a00, mag_of(counts, npix, x1, y0, f),
                 mag_of(counts, npix, x0, y1, f),
                 mag_of(counts, npix, x1, y1, f));
@@ -266,7 +266,7 @@ __global__ void k_quads_from_A(const float *__restrict__ A, int npix,
     const int c = (int)(k % side), r = (int)(k / side);
     const int x0 = clampi(c - 1, npix), x1 = clampi(c, npix);
     const int y0 = clampi(r - 1, npix), y1 = clampi(r, npix);
-    quad[(size_t)r * qpitch + c] = quad_of(
+    quad[cell_index(c, r, qpitch)] = quad_of(
         A[(size_t)y0 * npix + x0], A[(size_t)y0 * npix + x1],
         A[(size_t)y1 * npix + x0], A[(size_t)y1 * npix + x1]);
   }
@@ -301,7 +301,7 @@ __global__ void k_half_quads(const uint16_t *__restrict__ codes, int npix,
     const unsigned c10 = codes[(size_t)y0 * npix + x1];
     const unsigned c01 = codes[(size_t)y1 * npix + x0];
     const unsigned c11 = codes[(size_t)y1 * npix + x1];
-    quadh[(size_t)r * qpitch + c] = make_uint2(c00 | (c10 << 16),
+    quadh[cell_index(c, r, qpitch)] = make_uint2(c00 | (c10 << 16),
                                                c01 | (c11 << 16));
   }
 }

@@ -2013,4 +2013,87 @@ morse_status morse_batch_shape_of(morse_ctx *ctx, int64_t n_ep,
   return MORSE_OK;
 }
 
+// ------------------------------------------------------------------ probes
+morse_status morse_measure_peaks(morse_ctx *ctx, morse_peaks *out) {
+  if (!ctx || !out) return MORSE_EINVAL;
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  const size_t win_bytes = (size_t)16 << 20;  // 16 MB gather window
+  const int threads = morse::probe_threads();
+  const int blocks = 8 * ctx->sm_count;
+  const size_t sink_bytes = sizeof(double) * (size_t)blocks * threads;
+  void *ws = nullptr;
+  MORSE_TRY(ws_reserve(ctx, win_bytes + sink_bytes, &ws));
+  char *base = (char *)ws;
+  MORSE_CUDA(ctx, cudaMemsetAsync(base, 0, win_bytes, ctx->stream));
+  void *sink = base + win_bytes;
+  cudaEvent_t e0, e1;
+  MORSE_CUDA(ctx, cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ctx, ce, "probe events");
+  }
+  // run(n) launches one probe with n iterations per thread; returns ms of
+  // the second of two runs, n grown until that takes about 10 ms
+  auto timed = [&](auto launch, int &n, double *ms_out) -> cudaError_t {
+    for (int round = 0; round < 6; ++round) {
+      cudaError_t e = launch(n);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+      if (e == cudaSuccess) e = launch(n);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) return e;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      *ms_out = ms;
+      ctx->launches += 2;
+      if (ms >= 5.0f || n >= (1 << 24)) break;
+      const double grow = ms > 0.01f ? 10.0 / ms : 64.0;
+      n = (int)std::min<double>((double)(1 << 24), n * grow);
+    }
+    return cudaSuccess;
+  };
+  const double nthr = (double)blocks * threads;
+  double ms = 0.0;
+  int n = 1024;
+  ce = timed([&](int k) { return morse::probe_fma32(blocks, k, (float *)sink,
+                                                    ctx->stream); },
+             n, &ms);
+  if (ce == cudaSuccess)
+    out->fp32_fma_per_s = nthr * n * morse::probe_chains() / (ms * 1e-3);
+  n = 64;
+  if (ce == cudaSuccess)
+    ce = timed([&](int k) { return morse::probe_fma64(blocks, k,
+                                                      (double *)sink,
+                                                      ctx->stream); },
+               n, &ms);
+  if (ce == cudaSuccess)
+    out->fp64_fma_per_s = nthr * n * morse::probe_chains() / (ms * 1e-3);
+  n = 256;
+  if (ce == cudaSuccess)
+    ce = timed([&](int k) { return morse::probe_smem_atomic(
+                                blocks, k, (unsigned *)sink, ctx->stream); },
+               n, &ms);
+  if (ce == cudaSuccess) out->smem_atomics_per_s = nthr * n / (ms * 1e-3);
+  const float4 *win = (const float4 *)base;
+  n = 256;
+  if (ce == cudaSuccess)
+    ce = timed([&](int k) { return morse::probe_gather(
+                                win, (64u << 10) / 16 - 1, blocks, k,
+                                (float *)sink, ctx->stream); },
+               n, &ms);
+  if (ce == cudaSuccess) out->l1_gather_bytes_per_s = nthr * n * 16.0 / (ms * 1e-3);
+  n = 256;
+  if (ce == cudaSuccess)
+    ce = timed([&](int k) { return morse::probe_gather(
+                                win, (unsigned)(win_bytes / 16 - 1), blocks,
+                                k, (float *)sink, ctx->stream); },
+               n, &ms);
+  if (ce == cudaSuccess) out->l2_gather_bytes_per_s = nthr * n * 16.0 / (ms * 1e-3);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ce != cudaSuccess) return cuda_fail(ctx, ce, "throughput probe");
+  return MORSE_OK;
+}
+
 }  // extern "C"

@@ -103,13 +103,45 @@ constexpr int kRayThreads = 512;  // threads per ray-shooting block
 
 cudaError_t launch_rayshoot(const RayParams &P, bool fp64, int grid,
                             cudaStream_t st);
-// Quad row pitch for an npix map (quads; npix + 1 cells per row are used).
+// Cell tables: (npix + 1)^2 bilinear cells, stored either row-major with a
+// row pitch of quad_pitch cells (MORSE_TILE_W = 1), or in tiles of
+// MORSE_TILE_W x MORSE_TILE_H cells (powers of two) laid out row-major, so
+// that the cells a warp gathers along a track of any direction share fewer
+// cache lines.
 #ifndef MORSE_QPITCH_PAD
 #define MORSE_QPITCH_PAD 8
 #endif
-inline int quad_pitch(int npix) { return npix + MORSE_QPITCH_PAD; }
+#ifndef MORSE_TILE_W
+#define MORSE_TILE_W 1
+#endif
+#ifndef MORSE_TILE_H
+#define MORSE_TILE_H 1
+#endif
+constexpr int kTileW = MORSE_TILE_W, kTileH = MORSE_TILE_H;
+constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
+constexpr int kTileLW = ilog2c(kTileW), kTileLH = ilog2c(kTileH);
+static_assert((1 << kTileLW) == kTileW && (1 << kTileLH) == kTileH,
+              "tile sides are powers of two");
+// cells per stored row (a multiple of the tile width)
+inline int quad_pitch(int npix) {
+  const int p = npix + MORSE_QPITCH_PAD;
+  return (p + kTileW - 1) / kTileW * kTileW;
+}
+// stored rows (a multiple of the tile height)
+inline int quad_rows(int npix) {
+  return (npix + 1 + kTileH - 1) / kTileH * kTileH;
+}
 inline size_t quad_count(int npix) {
-  return (size_t)(npix + 1) * (size_t)quad_pitch(npix);
+  return (size_t)quad_rows(npix) * (size_t)quad_pitch(npix);
+}
+// storage index of cell (c, r)
+__host__ __device__ __forceinline__ size_t cell_index(int c, int r,
+                                                      int qpitch) {
+  if (kTileW == 1 && kTileH == 1) return (size_t)r * qpitch + c;
+  const size_t tile = (size_t)(r >> kTileLH) * (size_t)(qpitch >> kTileLW) +
+                      (size_t)(c >> kTileLW);
+  return (tile << (kTileLW + kTileLH)) |
+         (size_t)(((r & (kTileH - 1)) << kTileLW) | (c & (kTileW - 1)));
 }
 // quad index offset of the folded floor-bit index (see SearchParams)
 inline unsigned quad_idx0(int npix) {
@@ -285,6 +317,16 @@ cudaError_t launch_batch_fill(const BatchParams &B, bool h16,
                               const Entry *result, int pairs,
                               const double *t0abs, const double *tEv,
                               morse_fit *out, cudaStream_t st);
+
+// ---------------------------------------------------------------- probes
+cudaError_t probe_fma32(int blocks, int n, float *sink, cudaStream_t st);
+cudaError_t probe_fma64(int blocks, int n, double *sink, cudaStream_t st);
+cudaError_t probe_smem_atomic(int blocks, int n, unsigned *sink,
+                              cudaStream_t st);
+cudaError_t probe_gather(const float4 *win, unsigned mask, int blocks, int n,
+                         float *sink, cudaStream_t st);
+int probe_threads();
+int probe_chains();
 
 // ---------------------------------------------------------------- refine
 struct RefineState {

@@ -191,7 +191,17 @@ __device__ __forceinline__ bool tex_pos(const SearchParams &P, float vx,
   // because the index is in [0, (npix + 1) * qpitch))
   const unsigned bx = (unsigned)__float_as_int(tx);
   const unsigned by = (unsigned)__float_as_int(ty);
-  o.idx = by * (unsigned)P.qpitch + bx + P.qidx0;
+  if (kTileW == 1 && kTileH == 1) {
+    o.idx = by * (unsigned)P.qpitch + bx + P.qidx0;
+  } else {
+    // cell (c, r) = (floor(v) + half + 1) per axis, then the tile index
+    const unsigned c = bx + (unsigned)(P.half + 1 - 0x4B400000);
+    const unsigned r = by + (unsigned)(P.half + 1 - 0x4B400000);
+    o.idx = ((((r >> kTileLH) * ((unsigned)P.qpitch >> kTileLW) +
+               (c >> kTileLW))
+              << (kTileLW + kTileLH)) |
+             ((r & (kTileH - 1)) << kTileLW) | (c & (kTileW - 1)));
+  }
 #ifdef MORSE_CHECK_BOUNDS
   // checked build: record an out-of-range cell and skip the access
   const int cx = (int)(bx - 0x4B400000u) + P.half + 1;
