@@ -306,6 +306,35 @@ def refine_best(ctx, m, cfg, ev, S, Q, fits, n_maps=8, iters=40):
     return best
 
 
+def map_generators(ctx, m, cfg, n_maps=4):
+    """The two map generators on config-1 maps (1024^2 over [-2, 2]^2):
+    inverse ray shooting of 10^8 FP32 rays and the lens polynomial solved
+    in FP64 at every texel centre (the paper's generator), wall time per
+    map with the device synchronised."""
+    import torch
+    S, Q = sq_lists(cfg)
+    pick = np.linspace(0, len(S) - 1, n_maps).round().astype(int)
+    out = {}
+    for gen in ("rays", "poly"):
+        times = []
+        for j in pick:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mp = ctx.build_map(S[j], Q[j], cfg["L"], cfg["npix"], cfg["nray"],
+                               image_halfwidth=cfg["X"], deflect="fp32",
+                               generator=gen)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            mp.free()
+        ms = 1e3 * float(np.median(times[1:] if len(times) > 1 else times))
+        out[gen] = {"ms_per_map": ms,
+                    "texels_per_s": cfg["npix"] ** 2 / (ms * 1e-3)}
+    out["rays"]["rays_per_s"] = cfg["nray"] ** 2 / (out["rays"]["ms_per_map"]
+                                                   * 1e-3)
+    out["maps"] = f"{n_maps} (s, q) of the 651, {cfg['npix']}^2 texels"
+    return out
+
+
 def time_to_best_fit(ctx, m, cfg, ev, S, Q, plain_s, plain_fits):
     """Wall time of each form of the (s, q) search and its best chi^2; a
     form reaches the best fit when its chi^2 is within 1e-3 of the lowest
@@ -628,6 +657,7 @@ def run_gpu(args, cfg):
     if rank == 0 and not args.no_extras:
         line["time_to_best_fit"] = time_to_best_fit(
             ctx, m, cfg, ev, S, Q, elapsed / args.steps, fits)
+        line["map_generators"] = map_generators(ctx, m, cfg)
         line["batched"] = run_batched(ctx, m, args.batch_events,
                                       args.batch_maps, not args.no_batch_tune)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -88,15 +88,26 @@ enum {
                               which searches then read                    */
 };
 
+enum {
+  MORSE_GEN_RAYS = 0, /* inverse ray shooting: texel = area-averaged A    */
+  MORSE_GEN_POLY = 1  /* the lens polynomial per texel (§4.1): texel = the
+                         point-source A at its centre, FP64; no counts     */
+};
+
 typedef struct {
   double image_halfwidth; /* X: rays cover [-X, X]^2; <= 0 means 1.5 L    */
   int deflect;            /* MORSE_DEFLECT_FP64 or MORSE_DEFLECT_FP32     */
   int store;              /* OR of MORSE_STORE_* (FP32 is always kept)     */
+  int generator;          /* MORSE_GEN_RAYS (default) or MORSE_GEN_POLY   */
 } morse_map_opts;
 
 /* Build the magnification map of the binary lens (s, q) by inverse ray
  * shooting (§3 ray-shooting maps; §5 inverse ray shooting) on the source
- * grid of §4.1.  rays_per_axis^2 image-plane rays on the cell-centred grid
+ * grid of §4.1, or, with opts->generator = MORSE_GEN_POLY, by solving the
+ * fifth-order lens polynomial at every texel centre (§4.1; one thread per
+ * texel, FP64 roots polished on Eq. 2, images by Eq. 2 residual; such a map
+ * has no ray counts and ignores rays_per_axis, image_halfwidth and
+ * deflect).  rays_per_axis^2 image-plane rays on the cell-centred grid
  * x = -X + (i+1/2) h, h = 2X/rays_per_axis, are deflected through the real
  * form of Eq. 2,
  *     y = x - eps1 (x - x1)/|x - x1|^2 - eps2 (x - x2)/|x - x2|^2,

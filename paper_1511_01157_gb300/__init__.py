@@ -40,6 +40,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEGENERATE, EUNSUPPORTED = range(7)
 DEFLECT_FP64, DEFLECT_FP32 = 0, 1
 STORE_FP32, STORE_FP16LOG = 1, 2
+GEN_RAYS, GEN_POLY = 0, 1
 FIT_DEGENERATE, FIT_REFINED = 1, 2
 REFINE_LM = 0
 
@@ -88,7 +89,8 @@ assert FIT_DTYPE.itemsize == ctypes.sizeof(Fit)
 
 class MapOpts(ctypes.Structure):
     _fields_ = [("image_halfwidth", ctypes.c_double),
-                ("deflect", ctypes.c_int), ("store", ctypes.c_int)]
+                ("deflect", ctypes.c_int), ("store", ctypes.c_int),
+                ("generator", ctypes.c_int)]
 
 
 class Peaks(ctypes.Structure):
@@ -224,12 +226,15 @@ class Context:
 
     # ------------------------------------------------------------ maps
     def build_map(self, s, q, extent, npix, rays_per_axis,
-                  image_halfwidth=None, deflect="fp64", fp16log=False):
+                  image_halfwidth=None, deflect="fp64", fp16log=False,
+                  generator="rays"):
         """Magnification map of the binary lens (s, q) by inverse ray
-        shooting (morse_build_map)."""
+        shooting, or by the lens polynomial per texel with generator="poly"
+        (morse_build_map)."""
         opts = MapOpts(float(image_halfwidth or 0.0),
                        DEFLECT_FP64 if deflect == "fp64" else DEFLECT_FP32,
-                       STORE_FP32 | (STORE_FP16LOG if fp16log else 0))
+                       STORE_FP32 | (STORE_FP16LOG if fp16log else 0),
+                       GEN_POLY if generator == "poly" else GEN_RAYS)
         h = ctypes.c_void_p()
         st = _lib.morse_build_map(self._h, float(s), float(q), float(extent),
                                   int(npix), int(rays_per_axis),
@@ -345,16 +350,18 @@ class Context:
         return out
 
     def sweep(self, event, s, q, extent, npix, rays_per_axis, grid: Grid,
-              image_halfwidth=None, deflect="fp32", fp16log=False):
+              image_halfwidth=None, deflect="fp32", fp16log=False,
+              generator="rays"):
         """Full (s, q) search of a device-resident event (morse_sweep):
         returns fits[n_maps, top_k].  fp16log: search each map through its
-        FP16 log10 table."""
+        FP16 log10 table; generator="poly": maps from the lens polynomial."""
         s, q = _f64(s), _f64(q)
         if len(s) != len(q):
             raise ValueError("s and q lists differ in length")
         opts = MapOpts(float(image_halfwidth or 0.0),
                        DEFLECT_FP64 if deflect == "fp64" else DEFLECT_FP32,
-                       STORE_FP32 | (STORE_FP16LOG if fp16log else 0))
+                       STORE_FP32 | (STORE_FP16LOG if fp16log else 0),
+                       GEN_POLY if generator == "poly" else GEN_RAYS)
         out = np.zeros((len(s), grid.top_k), dtype=FIT_DTYPE)
         st = _lib.morse_sweep(self._h, event._h, _ptr(s), _ptr(q), len(s),
                               float(extent), int(npix), int(rays_per_axis),
@@ -365,7 +372,7 @@ class Context:
 
     def search_sweep(self, t, flux, sigma, t_ref, s, q, extent, npix,
                      rays_per_axis, grid: Grid, image_halfwidth=None,
-                     deflect="fp32", fp16log=False):
+                     deflect="fp32", fp16log=False, generator="rays"):
         """morse_search_sweep: the full (s, q) search from host buffers."""
         t, flux, sigma = _f64(t), _f64(flux), _f64(sigma)
         s, q = _f64(s), _f64(q)
@@ -373,7 +380,8 @@ class Context:
             raise ValueError("s and q lists differ in length")
         opts = MapOpts(float(image_halfwidth or 0.0),
                        DEFLECT_FP64 if deflect == "fp64" else DEFLECT_FP32,
-                       STORE_FP32 | (STORE_FP16LOG if fp16log else 0))
+                       STORE_FP32 | (STORE_FP16LOG if fp16log else 0),
+                       GEN_POLY if generator == "poly" else GEN_RAYS)
         out = np.zeros((len(s), grid.top_k), dtype=FIT_DTYPE)
         st = _lib.morse_search_sweep(self._h, _ptr(t), _ptr(flux),
                                      _ptr(sigma), len(t), float(t_ref),

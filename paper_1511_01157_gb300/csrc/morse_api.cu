@@ -156,6 +156,7 @@ struct BuildSpec {
   int64_t nray;
   bool fp64;
   bool fp16;  // also write the FP16 log10 table and search through it
+  bool poly;  // the lens polynomial per texel instead of ray shooting
 };
 
 morse_status check_build(morse_ctx *ctx, double s, double q, double extent,
@@ -181,8 +182,13 @@ morse_status check_build(morse_ctx *ctx, double s, double q, double extent,
     if (store & ~(MORSE_STORE_FP32 | MORSE_STORE_FP16LOG))
       return fail(ctx, MORSE_EINVAL, "unknown store flags %d", store);
     b->fp16 = (store & MORSE_STORE_FP16LOG) != 0;
+    if (opts->generator != MORSE_GEN_RAYS && opts->generator != MORSE_GEN_POLY)
+      return fail(ctx, MORSE_EINVAL, "unknown map generator %d",
+                  opts->generator);
+    b->poly = opts->generator == MORSE_GEN_POLY;
   } else {
     b->fp16 = false;
+    b->poly = false;
   }
   b->s = s;
   b->q = q;
@@ -266,6 +272,32 @@ morse_status enqueue_build(morse_ctx *ctx, morse_map *m, const BuildSpec &b) {
   m->L = b.L;
   m->s = b.s;
   m->q = b.q;
+  if (b.poly) {
+    // the lens polynomial at every texel centre: no rays, no counts
+    m->X = 0.0;
+    m->nray = 0;
+    m->has_counts = false;
+    m->a_floor = 1e-6;
+    m->half_valid = false;
+    m->lookup = MORSE_STORE_FP32;
+    MORSE_CUDA(ctx, cudaMemsetAsync(m->tot, 0, 2 * sizeof(unsigned long long),
+                                    ctx->stream));
+    int r = t_begin(ctx, KT_RAY);
+    MORSE_CUDA(ctx, morse::launch_poly_map(b.s, b.q, b.L, b.npix, m->A,
+                                           ctx->sm_count, ctx->stream));
+    t_end(ctx, r);
+    r = t_begin(ctx, KT_MAP);
+    MORSE_CUDA(ctx, morse::launch_quads_from_A(m->A, b.npix, m->quad,
+                                               m->qpitch, ctx->stream));
+    if (b.fp16) {
+      MORSE_TRY(enqueue_half(ctx, m));
+      m->lookup = MORSE_STORE_FP16LOG;
+    }
+    t_end(ctx, r);
+    ctx->launches += 2;
+    return MORSE_OK;
+  }
+  m->has_counts = m->counts != nullptr;
   m->X = b.X;
   m->nray = b.nray;
   morse::RayParams P;

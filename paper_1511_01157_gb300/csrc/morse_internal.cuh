@@ -159,6 +159,9 @@ cudaError_t launch_half_from_A(const float *A, int npix, double a_floor,
                                uint16_t *codes, uint2 *quadh, int qpitch,
                                cudaStream_t st);
 int rayshoot_blocks_per_sm();
+// point-source A at the npix^2 texel centres by the lens polynomial (FP64)
+cudaError_t launch_poly_map(double s, double q, double L, int npix, float *A,
+                            int sm_count, cudaStream_t st);
 
 // ---------------------------------------------------------------- search
 struct Entry {

@@ -41,6 +41,7 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts_match_header():
     m = _lib()
     assert ctypes.sizeof(m.Fit) == 72
+    assert ctypes.sizeof(m.MapOpts) == 8 + 3 * 4 + 4  # padded
     assert ctypes.sizeof(m.Grid) == 4 * 4 + 6 * 8 + 3 * 4 + 4  # padded
     assert m.FIT_DTYPE.itemsize == 72
 
