@@ -17,6 +17,8 @@ names the passage of McDougall & Albrow (2015) it follows:
 * ``chi2_grad_poly``  -- chi^2 gradient in (t0, tE, u0, alpha) of the
   polynomial light curve, Fs and Fb profiled (Eq. 5-6, §4.2)
 * ``poly_map``        -- §4.1 point-source map from the polynomial per texel
+* ``fs_weights``/``fs_convolve`` -- §4.1 finite-source maps: the map
+  convolved with a limb-darkened source profile
 * ``half_bits``/``half_value``/``log10_half``/``half_decode`` -- the FP16
   log10 storage form of a map (IEEE binary16, round to nearest even)
 * ``pspl``            -- §4.3 (ii) Paczynski single-lens curve
@@ -29,6 +31,7 @@ names the passage of McDougall & Albrow (2015) it follows:
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import sys
@@ -82,6 +85,8 @@ def _load():
         "orc_poly_map": (None, [_D, _D, _D, _I, _P, _I]),
         "orc_mag_point_grad": (_D, [_D, _D, _D, _D, _P]),
         "orc_half_bits": (ctypes.c_uint16, [_D]),
+        "orc_fs_weights": (None, [_D, _D, _I, _I, _P]),
+        "orc_fs_convolve": (None, [_P, _I, _D, _P, _I, _P, _I]),
         "orc_half_value": (_D, [ctypes.c_uint16]),
         "orc_log10_half": (None, [_P, ctypes.c_longlong, _D, _P]),
         "orc_half_decode": (None, [_P, ctypes.c_longlong, _P]),
@@ -220,6 +225,32 @@ def chi2_grad_poly(t, F, w, theta, s, q):
                                    _ptr(w), len(t), *[float(x) for x in theta],
                                    _ptr(g), ctypes.byref(fs), ctypes.byref(fb))
     return c, g, fs.value, fb.value
+
+
+def fs_radius(rho_px):
+    """Half-width R (texels) of the finite-source kernel of radius rho_px."""
+    return int(math.ceil(rho_px + 0.5))
+
+
+def fs_weights(rho_px, gamma, sub=8):
+    """Limb-darkened source profile (§4.1) integrated over the texels
+    within R = fs_radius(rho_px), normalised; [2R+1, 2R+1] (dy, dx)."""
+    R = fs_radius(rho_px)
+    W = np.zeros((2 * R + 1, 2 * R + 1))
+    _load().orc_fs_weights(float(rho_px), float(gamma), R, int(sub), _ptr(W))
+    return W
+
+
+def fs_convolve(A, L, W, nthreads=1):
+    """Finite-source map: A convolved with W, the Paczynski curve standing
+    in for the texels outside the map; FP64 [npix, npix]."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    R = (W.shape[0] - 1) // 2
+    out = np.zeros(A.shape)
+    _load().orc_fs_convolve(_ptr(A), A.shape[0], float(L), _ptr(W), R,
+                            _ptr(out), int(nthreads))
+    return out
 
 
 def half_bits(x):

@@ -488,3 +488,70 @@ def test_log10_half_quantisation_bound():
     assert orc.half_decode(orc.log10_half(np.array([1.0, 10.0, 100.0],
                                                    dtype=np.float32),
                                           1e-3)).tolist() == [1.0, 10.0, 100.0]
+
+
+# ------------------------------------------------------------ finite source
+@pytest.mark.parametrize("gamma", [0.0, 0.53, 1.0])
+def test_fs_weights_second_moment_closed_form(gamma):
+    # linear limb darkening in the Gamma form: <r^2> = rho^2 (1/2 - Gamma/10)
+    # for the continuous profile; texel integration adds 1/6 (texel units)
+    rho = 40.0
+    W = orc.fs_weights(rho, gamma)
+    R = (W.shape[0] - 1) // 2
+    d = np.arange(-R, R + 1)
+    assert W.sum() == pytest.approx(1.0, abs=1e-12)
+    assert np.allclose(W, W[::-1, :]) and np.allclose(W, W.T)
+    m2 = (W * (d[None, :] ** 2 + d[:, None] ** 2)).sum()
+    closed = rho ** 2 * (0.5 - gamma / 10.0) + 1.0 / 6.0
+    assert m2 == pytest.approx(closed, rel=1e-4)
+    # the centre of the disc is brighter than its edge for Gamma > 0
+    if gamma > 0:
+        assert W[R, R] > W[R, R + int(rho) - 1]
+
+
+def test_fs_convolve_identity_constant_plane_and_paraboloid():
+    L, npix = 2.0, 96
+    jj, ii = np.meshgrid(np.arange(npix), np.arange(npix), indexing="ij")
+    # a source smaller than a texel: identity
+    A = (2.0 + np.sin(ii * 0.3) * np.cos(jj * 0.2)).astype(np.float32)
+    W0 = orc.fs_weights(0.3, 0.53)
+    assert W0.shape == (3, 3)
+    out = orc.fs_convolve(A, L, W0)
+    np.testing.assert_array_equal(out, A.astype(np.float64))
+    rho = 12.0
+    W = orc.fs_weights(rho, 0.53)
+    R = (W.shape[0] - 1) // 2
+    inner = (slice(R, npix - R), slice(R, npix - R))
+    # constant and plane: reproduced exactly away from the edge (symmetric
+    # kernel, centred on the output texel)
+    Pexact = 1.5 + 0.01 * ii + 0.02 * jj
+    outP = orc.fs_convolve(Pexact.astype(np.float32), L, W)
+    # up to the FP32 rounding of the input texels
+    np.testing.assert_allclose(outP[inner], Pexact[inner], rtol=2e-7)
+    # paraboloid: the second moment is added
+    Q = (1.0 + 1e-3 * ((ii - 40.0) ** 2 + (jj - 50.0) ** 2)).astype(np.float32)
+    outQ = orc.fs_convolve(Q, L, W)
+    d = np.arange(-R, R + 1)
+    m2 = (W * (d[None, :] ** 2 + d[:, None] ** 2)).sum()
+    np.testing.assert_allclose(outQ[inner] - Q[inner], 1e-3 * m2, rtol=1e-6,
+                               atol=1e-6)
+    # outside the map the Paczynski curve stands in
+    out_edge = orc.fs_convolve(np.ones((npix, npix), np.float32), L, W)
+    assert out_edge[0, 0] > 1.0 and out_edge[npix // 2, npix // 2] == \
+        pytest.approx(1.0, abs=1e-12)
+
+
+def test_fs_uniform_disc_on_a_point_lens_centre():
+    # uniform disc centred on a single lens: A = sqrt(1 + 4 / rho^2); the
+    # area-averaged (ray-shot) map resolves the 1/u cusp
+    L, npix, nray = 1.0, 64, 4000
+    A, c, off, lost = orc.build_map(1.0, 1e-12, L, npix, nray, 3.0,
+                                    nthreads=8)
+    dlt = 2 * L / npix
+    rho = 0.4  # Einstein radii
+    W = orc.fs_weights(rho / dlt, 0.0)
+    out = orc.fs_convolve(A, L, W, nthreads=4)
+    # the lens sits on the corner of the four central texels
+    centre = out[npix // 2 - 1:npix // 2 + 1, npix // 2 - 1:npix // 2 + 1]
+    exact = np.sqrt(1 + 4 / rho ** 2)
+    assert centre.mean() == pytest.approx(exact, rel=2e-3)
