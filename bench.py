@@ -335,6 +335,34 @@ def map_generators(ctx, m, cfg, n_maps=4):
     return out
 
 
+def finite_source_maps(ctx, m, cfg, gamma=0.53):
+    """The paper's finite-source set on one config-1 map: seven source
+    radii log-spaced over (0.001, 1) Einstein radii, limb darkening 0.53;
+    wall time per convolution and multiply-adds per second."""
+    import torch
+    mp = ctx.build_map(cfg["s"], cfg["q"], cfg["L"], cfg["npix"], cfg["nray"],
+                       image_halfwidth=cfg["X"], deflect="fp32")
+    dlt = 2.0 * cfg["L"] / cfg["npix"]
+    rows = []
+    for rho in np.exp(np.linspace(np.log(1e-3), np.log(1.0), 7)):
+        times = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fs = mp.finite_source(rho, gamma)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            fs.free()
+        R = int(math.ceil(rho / dlt + 0.5))
+        taps = math.pi * (rho / dlt) ** 2 if rho / dlt > 0.5 else 1.0
+        t = min(times)
+        rows.append({"rho": float(rho), "R_texels": R, "ms": 1e3 * t,
+                     "fma_per_s": taps * cfg["npix"] ** 2 / t})
+    mp.free()
+    return {"map": f"{cfg['npix']}^2 texels, (s, q) = ({cfg['s']}, "
+                   f"{cfg['q']})", "gamma": gamma, "radii": rows}
+
+
 def time_to_best_fit(ctx, m, cfg, ev, S, Q, plain_s, plain_fits):
     """Wall time of each form of the (s, q) search and its best chi^2; a
     form reaches the best fit when its chi^2 is within 1e-3 of the lowest
@@ -366,6 +394,23 @@ def time_to_best_fit(ctx, m, cfg, ev, S, Q, plain_s, plain_fits):
     forms["plain_grid_plus_refine"] = (
         plain_s + t, b, "plain grid, then 40 LM iterations on the 16 best "
         "seeds of the 8 best maps")
+    coarse = m.Grid.make(20, 36, 13, 10, g["u0_lo"], g["u0_hi"], g["t0_lo"],
+                         g["t0_hi"], g["tE_lo"], g["tE_hi"], True, True, 16)
+
+    def screened():
+        # coarse screen of all maps, the full grid on the 16 best, refine
+        first = sweep(coarse)
+        best = np.sort(np.argsort(first["chi2"][:, 0])[:16])
+        fine = ctx.sweep(ev, S[best].copy(), Q[best].copy(), cfg["L"],
+                         cfg["npix"], cfg["nray"], grid_of(m, cfg),
+                         image_halfwidth=cfg["X"], deflect="fp32")
+        return refine_best(ctx, m, cfg, ev, S[best].copy(), Q[best].copy(),
+                           fine)
+    b, t = timed(screened)
+    forms["screen_then_grid_plus_refine"] = (
+        t, b, "20x36x13x10 grid on all 651 maps, the 40x72x25x20 grid on "
+        "the 16 best maps, then 40 LM iterations on the 16 best seeds of "
+        "the 8 best of those")
     for name, dims in (("half_grid_plus_refine", (40, 72, 13, 10)),
                        ("coarse_grid_plus_refine", (20, 36, 13, 10))):
         grid = m.Grid.make(*dims, g["u0_lo"], g["u0_hi"], g["t0_lo"],
@@ -658,6 +703,7 @@ def run_gpu(args, cfg):
         line["time_to_best_fit"] = time_to_best_fit(
             ctx, m, cfg, ev, S, Q, elapsed / args.steps, fits)
         line["map_generators"] = map_generators(ctx, m, cfg)
+        line["finite_source"] = finite_source_maps(ctx, m, cfg)
         line["batched"] = run_batched(ctx, m, args.batch_events,
                                       args.batch_maps, not args.no_batch_tune)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -130,6 +130,7 @@ _SIGS = {
     "morse_map_info": (_S, [_P, _P, _P, _P, _P]),
     "morse_map_free": (None, [_P]),
     "morse_map_set_lookup": (_S, [_P, _I]),
+    "morse_map_finite_source": (_S, [_P, _P, _D, _D, _P]),
     "morse_grid_chi2_batch": (_S, [_P, _P, _I, _P, _I, _P, _P]),
     "morse_measure_peaks": (_S, [_P, _P]),
     "morse_batch_tuning": (_S, [_P, _I]),
@@ -490,6 +491,15 @@ class Map:
         self.ctx._check(_lib.morse_map_values(self._h, _ptr(A)),
                         "morse_map_values")
         return A
+
+    def finite_source(self, rho, gamma=0.53):
+        """New map: this one convolved with a limb-darkened source of radius
+        rho (Einstein radii), morse_map_finite_source."""
+        h = ctypes.c_void_p()
+        self.ctx._check(_lib.morse_map_finite_source(
+            self.ctx._h, self._h, float(rho), float(gamma), ctypes.byref(h)),
+            "morse_map_finite_source")
+        return Map(self.ctx, h)
 
     def set_lookup(self, fp16log: bool):
         """Search through the FP16 log10 table (built on demand) or the

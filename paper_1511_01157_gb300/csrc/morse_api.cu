@@ -1389,6 +1389,93 @@ morse_status morse_map_info(const morse_map *map, int *npix, double *extent,
   return MORSE_OK;
 }
 
+morse_status morse_map_finite_source(morse_ctx *ctx, const morse_map *src,
+                                     double rho, double gamma,
+                                     morse_map **out) {
+  if (!ctx || !src || !out) return MORSE_EINVAL;
+  *out = nullptr;
+  if (src->ctx != ctx) return fail(ctx, MORSE_EINVAL, "map of another ctx");
+  if (!(rho > 0.0) || !is_fin(rho))
+    return fail(ctx, MORSE_EINVAL, "rho must be finite and > 0");
+  if (!(gamma >= 0.0 && gamma <= 1.0))
+    return fail(ctx, MORSE_EINVAL, "gamma must be in [0, 1]");
+  const int npix = src->npix;
+  const double dlt = (2.0 * src->L) / (double)npix;
+  const double rpx = rho / dlt;
+  if (!(rpx + 0.5 <= 1700.0))
+    return fail(ctx, MORSE_EINVAL,
+                "source radius of %.1f texels exceeds the 1700 supported",
+                rpx);
+  const int R = (int)ceil(rpx + 0.5);
+  const int side = 2 * R + 1;
+  // the profile integrated over each texel on 8 x 8 midpoint points
+  constexpr int kSub = 8;
+  std::vector<double> w((size_t)side * side, 0.0);
+  double tot = 0.0;
+  for (int dy = -R; dy <= R; ++dy)
+    for (int dx = -R; dx <= R; ++dx) {
+      double acc = 0.0;
+      for (int b = 0; b < kSub; ++b) {
+        const double y = dy - 0.5 + (b + 0.5) / kSub;
+        for (int a = 0; a < kSub; ++a) {
+          const double x = dx - 0.5 + (a + 0.5) / kSub;
+          const double u2 = (x * x + y * y) / (rpx * rpx);
+          if (u2 < 1.0) acc += 1.0 - gamma * (1.0 - 1.5 * sqrt(1.0 - u2));
+        }
+      }
+      w[(size_t)(dy + R) * side + (dx + R)] = acc;
+      tot += acc;
+    }
+  if (!(tot > 0.0)) {  // sub-texel source: the centre texel alone
+    std::fill(w.begin(), w.end(), 0.0);
+    w[(size_t)R * side + R] = 1.0;
+    tot = 1.0;
+  }
+  std::vector<float> wf(w.size());
+  std::vector<int> hw((size_t)side, -1);
+  for (int dy = 0; dy < side; ++dy)
+    for (int dx = 0; dx < side; ++dx) {
+      const double v = w[(size_t)dy * side + dx] / tot;
+      wf[(size_t)dy * side + dx] = (float)v;
+      if (v != 0.0) hw[(size_t)dy] = std::max(hw[(size_t)dy], std::abs(dx - R));
+    }
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  call_begin(ctx);
+  const size_t wbytes = align_up(sizeof(float) * wf.size(), 256);
+  void *ws = nullptr;
+  MORSE_TRY(ws_reserve(ctx, wbytes + sizeof(int) * hw.size(), &ws));
+  float *dW = (float *)ws;
+  int *dhw = (int *)((char *)ws + wbytes);
+  MORSE_CUDA(ctx, cudaMemcpyAsync(dW, wf.data(), sizeof(float) * wf.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  MORSE_CUDA(ctx, cudaMemcpyAsync(dhw, hw.data(), sizeof(int) * hw.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  morse_map *m = map_alloc(ctx, npix, false);
+  if (!m) return fail(ctx, MORSE_ENOMEM, "map of %d^2 texels", npix);
+  m->L = src->L;
+  m->s = src->s;
+  m->q = src->q;
+  m->a_floor = src->a_floor;
+  m->lookup = MORSE_STORE_FP32;
+  int r = t_begin(ctx, KT_MAP);
+  cudaError_t e = morse::launch_fs_conv(src->A, npix, src->L, R, dW, dhw,
+                                        m->A, ctx->stream);
+  if (e == cudaSuccess)
+    e = morse::launch_quads_from_A(m->A, npix, m->quad, m->qpitch,
+                                   ctx->stream);
+  t_end(ctx, r);
+  ctx->launches += 2;
+  morse_status st = e == cudaSuccess ? sync_and_collect(ctx, "finite source")
+                                     : cuda_fail(ctx, e, "finite source");
+  if (st != MORSE_OK) {
+    cudaStreamSynchronize(ctx->stream);
+    map_release(m);
+    return st;
+  }
+  *out = m;
+  return MORSE_OK;
+}
+
 morse_status morse_map_set_lookup(morse_map *map, int store) {
   if (!map) return MORSE_EINVAL;
   morse_ctx *ctx = map->ctx;

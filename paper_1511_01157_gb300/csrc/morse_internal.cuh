@@ -159,6 +159,12 @@ cudaError_t launch_half_from_A(const float *A, int npix, double a_floor,
                                uint16_t *codes, uint2 *quadh, int qpitch,
                                cudaStream_t st);
 int rayshoot_blocks_per_sm();
+// finite-source map: A convolved with the (2R+1)^2 weights W (rows dy),
+// rowhw[dy + R] = largest |dx| of a nonzero weight in row dy (-1: none)
+size_t fs_smem_bytes(int R);
+cudaError_t launch_fs_conv(const float *A, int npix, double L, int R,
+                           const float *W, const int *rowhw, float *out,
+                           cudaStream_t st);
 // point-source A at the npix^2 texel centres by the lens polynomial (FP64)
 cudaError_t launch_poly_map(double s, double q, double L, int npix, float *A,
                             int sm_count, cudaStream_t st);
