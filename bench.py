@@ -400,7 +400,7 @@ def time_to_best_fit(ctx, m, cfg, ev, S, Q, plain_s, plain_fits):
     def screened():
         # coarse screen of all maps, the full grid on the 16 best, refine
         first = sweep(coarse)
-        best = np.sort(np.argsort(first["chi2"][:, 0])[:16])
+        best = np.sort(np.argsort(first["chi2"][:, 0])[:64])
         fine = ctx.sweep(ev, S[best].copy(), Q[best].copy(), cfg["L"],
                          cfg["npix"], cfg["nray"], grid_of(m, cfg),
                          image_halfwidth=cfg["X"], deflect="fp32")
@@ -409,7 +409,7 @@ def time_to_best_fit(ctx, m, cfg, ev, S, Q, plain_s, plain_fits):
     b, t = timed(screened)
     forms["screen_then_grid_plus_refine"] = (
         t, b, "20x36x13x10 grid on all 651 maps, the 40x72x25x20 grid on "
-        "the 16 best maps, then 40 LM iterations on the 16 best seeds of "
+        "the 64 best maps, then 40 LM iterations on the 16 best seeds of "
         "the 8 best of those")
     for name, dims in (("half_grid_plus_refine", (40, 72, 13, 10)),
                        ("coarse_grid_plus_refine", (20, 36, 13, 10))):

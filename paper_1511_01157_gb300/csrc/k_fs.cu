@@ -27,11 +27,13 @@ namespace {
 constexpr int kFsTX = 64, kFsTY = 16, kFsOut = 4;  // outputs per thread
 constexpr int kFsThreads = (kFsTX / kFsOut) * kFsTY;
 
-__device__ __forceinline__ float pspl_at(int x, int y, double L, double dlt) {
-  const double y1 = -L + ((double)x + 0.5) * dlt;
-  const double y2 = -L + ((double)y + 0.5) * dlt;
-  const double u2 = y1 * y1 + y2 * y2;
-  return (float)((u2 + 2.0) / sqrt(u2 * (u2 + 4.0)));
+// Paczynski A of the centre of texel (x, y) outside the map, in FP32
+// (relative error a few 1e-7; halo texels of a large source are many)
+__device__ __forceinline__ float pspl_at(int x, int y, float L, float dlt) {
+  const float y1 = __fmaf_rn((float)x + 0.5f, dlt, -L);
+  const float y2 = __fmaf_rn((float)y + 0.5f, dlt, -L);
+  const float u2 = __fmaf_rn(y1, y1, y2 * y2);
+  return (u2 + 2.0f) * rsqrtf(u2 * (u2 + 4.0f));
 }
 
 __global__ void __launch_bounds__(kFsThreads)
@@ -45,7 +47,7 @@ __global__ void __launch_bounds__(kFsThreads)
   const int tx = threadIdx.x % (kFsTX / kFsOut);
   const int ty = threadIdx.x / (kFsTX / kFsOut);
   const int x0 = blockIdx.x * kFsTX, y0 = blockIdx.y * kFsTY;
-  const double dlt = (2.0 * L) / (double)npix;
+  const float Lf = (float)L, dltf = (float)((2.0 * L) / (double)npix);
   double acc[kFsOut];
 #pragma unroll
   for (int k = 0; k < kFsOut; ++k) acc[k] = 0.0;
@@ -57,7 +59,7 @@ __global__ void __launch_bounds__(kFsThreads)
       const int x = x0 - R + c, y = y0 + dy + r;
       s_in[t] = (x >= 0 && x < npix && y >= 0 && y < npix)
                     ? A[(size_t)y * npix + x]
-                    : pspl_at(x, y, L, dlt);
+                    : pspl_at(x, y, Lf, dltf);
     }
     for (int t = threadIdx.x; t <= 2 * R; t += blockDim.x)
       s_w[t] = W[(size_t)(dy + R) * (2 * R + 1) + t];

@@ -13,7 +13,9 @@
 //    a quintic in w whose roots contain the images.
 //  * Its five roots are found together by the Aberth-Ehrlich iteration
 //    (each root moves by the Newton step corrected for the other roots),
-//    from starting points on a circle enclosing them.
+//    from starting points on a circle enclosing them: in FP32 to a relative
+//    move of 1e-5 (FP64 is 1/70 of the FP32 rate on this GPU), then in FP64
+//    to 1e-12.
 //  * Each root is polished by Newton's method on Eq. 2 itself (the step dw
 //    solves f + dw + D conj(dw) = 0, D = d zeta / d conj(z)), which
 //    sharpens images next to a low-mass lens where the polynomial's
@@ -32,36 +34,85 @@ namespace morse {
 
 namespace {
 
-struct cd {
-  double re, im;
+template <typename T>
+struct cx {
+  T re, im;
 };
-__device__ __forceinline__ cd mk(double r, double i) { return {r, i}; }
-__device__ __forceinline__ cd add(cd a, cd b) {
+using cd = cx<double>;
+template <typename T>
+__device__ __forceinline__ cx<T> mk(T r, T i) { return {r, i}; }
+template <typename T>
+__device__ __forceinline__ cx<T> add(cx<T> a, cx<T> b) {
   return {a.re + b.re, a.im + b.im};
 }
-__device__ __forceinline__ cd sub(cd a, cd b) {
+template <typename T>
+__device__ __forceinline__ cx<T> sub(cx<T> a, cx<T> b) {
   return {a.re - b.re, a.im - b.im};
 }
-__device__ __forceinline__ cd mul(cd a, cd b) {
+template <typename T>
+__device__ __forceinline__ cx<T> mul(cx<T> a, cx<T> b) {
   return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
-__device__ __forceinline__ cd scl(double s, cd a) { return {s * a.re, s * a.im}; }
-__device__ __forceinline__ cd cnj(cd a) { return {a.re, -a.im}; }
-__device__ __forceinline__ double ab2(cd a) {
+template <typename T>
+__device__ __forceinline__ cx<T> scl(T s, cx<T> a) {
+  return {s * a.re, s * a.im};
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cnj(cx<T> a) { return {a.re, -a.im}; }
+template <typename T>
+__device__ __forceinline__ T ab2(cx<T> a) {
   return a.re * a.re + a.im * a.im;
 }
 __device__ __forceinline__ double ab(cd a) { return hypot(a.re, a.im); }
-__device__ __forceinline__ cd dvd(cd a, cd b) {
-  // a / b by scaling with the larger component of b
+__device__ __forceinline__ float ab(cx<float> a) { return hypotf(a.re, a.im); }
+template <typename T>
+__device__ __forceinline__ cx<T> dvd(cx<T> a, cx<T> b) {
+  // a / b by scaling with the larger component of b (two divisions)
   if (fabs(b.re) >= fabs(b.im)) {
-    const double r = b.im / b.re, den = b.re + b.im * r;
-    return {(a.re + a.im * r) / den, (a.im - a.re * r) / den};
+    const T r = b.im / b.re, id = T(1) / (b.re + b.im * r);
+    return {(a.re + a.im * r) * id, (a.im - a.re * r) * id};
   }
-  const double r = b.re / b.im, den = b.re * r + b.im;
-  return {(a.re * r + a.im) / den, (a.im * r - a.re) / den};
+  const T r = b.re / b.im, id = T(1) / (b.re * r + b.im);
+  return {(a.re * r + a.im) * id, (a.im * r - a.re) * id};
 }
 
-constexpr int kPolyIters = 100;
+// Aberth-Ehrlich iterations on the monic quintic with coefficients b
+// (z^5 + b4 z^4 + ... + b0) in precision T until the largest relative move
+// is below tol or `iters` sweeps are done.
+template <typename T>
+__device__ __forceinline__ void aberth(const cx<T> (&b)[5], cx<T> (&z)[5],
+                                       int iters, T tol) {
+  const cx<T> one = mk<T>(1, 0);
+  for (int it = 0; it < iters; ++it) {
+    T moved = 0;
+    for (int t = 0; t < 5; ++t) {
+      cx<T> p = one, dp = mk<T>(0, 0);  // p and p' by Horner
+      for (int u = 4; u >= 0; --u) {
+        dp = add(mul(dp, z[t]), p);
+        p = add(mul(p, z[t]), b[u]);
+      }
+      if (ab2(p) == T(0)) continue;
+      const cx<T> nw = dvd(p, dp);  // Newton step p/p'
+      cx<T> sum = mk<T>(0, 0);
+      for (int u = 0; u < 5; ++u)
+        if (u != t) sum = add(sum, dvd(one, sub(z[t], z[u])));
+      // Aberth step: nw / (1 - nw * sum)
+      const cx<T> step = dvd(nw, sub(one, mul(nw, sum)));
+      if (isfinite(step.re) && isfinite(step.im)) {
+        z[t] = sub(z[t], step);
+        moved = fmax(moved, ab(step) / (T(1) + ab(z[t])));
+      }
+    }
+    if (moved < tol) break;
+  }
+}
+
+// The roots need only be good starting points for the polish on Eq. 2,
+// which takes each image to full precision: FP32 sweeps stop at a relative
+// move of 1e-5, FP64 sweeps at 1e-12 (a tighter test would sit at the
+// rounding floor of ill-conditioned roots and use up the sweeps).
+constexpr int kPolyIters = 30;    // FP64 sweeps at most
+constexpr int kPolyItersF = 60;   // FP32 sweeps at most
 constexpr int kPolishIters = 8;
 
 // Lens equation in the midpoint frame: omega(w) and D = d omega/d conj(w).
@@ -130,35 +181,30 @@ __global__ void k_poly_map(double s, double q, double L, int npix,
       double R = 0.0;
       for (int t = 0; t < 5; ++t) R = fmax(R, ab(b[t]));
       R = 0.5 * (1.0 + R);
-      cd z[5];
+      // roots to single precision in FP32 from a circle of starting
+      // points, then to double precision in FP64 (a few cubically
+      // converging sweeps)
+      cx<float> bf[5], zf[5];
       for (int t = 0; t < 5; ++t) {
-        double sn, cs;
-        sincos(0.4 + 2.0 * CUDART_PI * t / 5.0, &sn, &cs);
-        z[t] = mk(R * cs, R * sn);
+        bf[t] = mk((float)b[t].re, (float)b[t].im);
+        float sn, cs;
+        sincosf(0.4f + 2.0f * (float)CUDART_PI * t / 5.0f, &sn, &cs);
+        zf[t] = mk((float)R * cs, (float)R * sn);
       }
-      for (int it = 0; it < kPolyIters; ++it) {
-        double moved = 0.0;
+      aberth(bf, zf, kPolyItersF, 1e-5f);
+      cd z[5];
+      bool ok = true;
+      for (int t = 0; t < 5; ++t) {
+        z[t] = mk((double)zf[t].re, (double)zf[t].im);
+        ok = ok && isfinite(z[t].re) && isfinite(z[t].im);
+      }
+      if (!ok)  // FP32 out of range: start the FP64 sweeps from the circle
         for (int t = 0; t < 5; ++t) {
-          // p and p' by Horner
-          cd p = mk(1.0, 0.0), dp = mk(0.0, 0.0);
-          for (int u = 4; u >= 0; --u) {
-            dp = add(mul(dp, z[t]), p);
-            p = add(mul(p, z[t]), b[u]);
-          }
-          if (ab2(p) == 0.0) continue;
-          const cd nw = dvd(p, dp);  // Newton step p/p'
-          cd sum = mk(0.0, 0.0);
-          for (int u = 0; u < 5; ++u)
-            if (u != t) sum = add(sum, dvd(mk(1.0, 0.0), sub(z[t], z[u])));
-          // Aberth step: nw / (1 - nw * sum)
-          const cd step = dvd(nw, sub(mk(1.0, 0.0), mul(nw, sum)));
-          if (isfinite(step.re) && isfinite(step.im)) {
-            z[t] = sub(z[t], step);
-            moved = fmax(moved, ab(step) / (1.0 + ab(z[t])));
-          }
+          double sn, cs;
+          sincos(0.4 + 2.0 * CUDART_PI * t / 5.0, &sn, &cs);
+          z[t] = mk(R * cs, R * sn);
         }
-        if (moved < 1e-15) break;
-      }
+      aberth(b, z, kPolyIters, 1e-12);
       // polish on Eq. 2 and keep the images
       cd img[5];
       int ni = 0;
@@ -180,14 +226,23 @@ __global__ void k_poly_map(double s, double q, double L, int npix,
           lens(w, a, e1, e2, &o, &D);
           const cd f = sub(o, om);
           const double r = ab(f);
-          if (r < best_r) {
-            best_r = r;
-            best = w;
-          }
+          if (!(r < best_r)) break;  // no longer improving: at the floor
+          best_r = r;
+          best = w;
           if (r == 0.0 || it == kPolishIters) break;
           const double det = 1.0 - ab2(D);
           if (det == 0.0) break;
-          w = add(w, scl(1.0 / det, sub(mul(D, cnj(f)), f)));
+          const cd dw = scl(1.0 / det, sub(mul(D, cnj(f)), f));
+          w = add(w, dw);
+          if (ab2(dw) <= 1e-32 * (1.0 + ab2(w))) {  // converged: one check
+            lens(w, a, e1, e2, &o, &D);
+            const double r2 = ab(sub(o, om));
+            if (r2 < best_r) {
+              best_r = r2;
+              best = w;
+            }
+            break;
+          }
         }
         // residual relative to the size of the terms of Eq. 2
         const double sc = ab(best) + ab(om) +
