@@ -153,7 +153,7 @@ void morse_map_free(morse_map *map);
  * log-spaced in (0.001, 1).  A source smaller than a texel leaves the map
  * unchanged.  The new map has the source map's geometry, FP32 values and
  * no ray counts; it is owned by the caller (morse_map_free).
- * Arguments: rho > 0 with R <= 1700 texels, 0 <= gamma <= 1.
+ * Arguments: rho > 0 with R <= 1600 texels, 0 <= gamma <= 1.
  * Errors: EINVAL, ENOMEM, ECUDA. */
 morse_status morse_map_finite_source(morse_ctx *ctx, const morse_map *src,
                                      double rho, double gamma,

@@ -1402,9 +1402,9 @@ morse_status morse_map_finite_source(morse_ctx *ctx, const morse_map *src,
   const int npix = src->npix;
   const double dlt = (2.0 * src->L) / (double)npix;
   const double rpx = rho / dlt;
-  if (!(rpx + 0.5 <= 1700.0))
+  if (!(rpx + 0.5 <= 1600.0))
     return fail(ctx, MORSE_EINVAL,
-                "source radius of %.1f texels exceeds the 1700 supported",
+                "source radius of %.1f texels exceeds the 1600 supported",
                 rpx);
   const int R = (int)ceil(rpx + 0.5);
   const int side = 2 * R + 1;
