@@ -23,6 +23,7 @@ names the passage of McDougall & Albrow (2015) it follows:
   log10 storage form of a map (IEEE binary16, round to nearest even)
 * ``pspl``            -- §4.3 (ii) Paczynski single-lens curve
 * ``traj_point``/``map_A`` -- §4.2 straight trajectory, bilinear map lookup
+* ``line_max``        -- §4.3 (i) largest magnification along a line
 * ``fit_A``           -- §4.1 Eq. 5-6 linear flux fit, chi^2 as a sum of
   per-point contributions (§4.2)
 * ``grid_chi2``/``topk`` -- brute-force grid and the K best seeds (§4.4)
@@ -86,6 +87,7 @@ def _load():
         "orc_mag_point_grad": (_D, [_D, _D, _D, _D, _P]),
         "orc_half_bits": (ctypes.c_uint16, [_D]),
         "orc_fs_weights": (None, [_D, _D, _I, _I, _P]),
+        "orc_line_max": (_D, [_P, _I, _D, _D, _D]),
         "orc_fs_convolve": (None, [_P, _I, _D, _P, _I, _P, _I]),
         "orc_half_value": (_D, [ctypes.c_uint16]),
         "orc_log10_half": (None, [_P, ctypes.c_longlong, _D, _P]),
@@ -314,6 +316,14 @@ def map_A(A, L, y1, y2):
     A = np.ascontiguousarray(A, dtype=np.float32)
     return _load().orc_map_A(_ptr(A), A.shape[0], float(L), float(y1),
                              float(y2))
+
+
+def line_max(A, L, u0, alpha):
+    """Largest magnification on the straight line (u0, alpha): exact for the
+    bilinear lookup inside the map and the Paczynski curve outside (§4.3)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    return _load().orc_line_max(_ptr(A), A.shape[0], float(L), float(u0),
+                                float(alpha))
 
 
 def lightcurve_map(A, L, t, t0, tE, u0, alpha):

@@ -625,6 +625,112 @@ double orc_map_A(const float *A, int npix, double L, double y1, double y2) {
 /* Linear flux fit and chi^2 (§4.1 Eq. 5-6, §4.2)                       */
 /* ------------------------------------------------------------------ */
 
+/* Bilinear interpolant of the map at (y1, y2) with the coordinates clamped
+ * to the outermost texel centres (the lookup inside the map, continued to
+ * the edge). */
+static double bil_clamped(const float *A, int npix, double L, double y1,
+                          double y2) {
+  double dlt = (2.0 * L) / (double)npix;
+  double px = (y1 + L) / dlt - 0.5, py = (y2 + L) / dlt - 0.5;
+  double hi = (double)(npix - 1);
+  px = px < 0.0 ? 0.0 : (px > hi ? hi : px);
+  py = py < 0.0 ? 0.0 : (py > hi ? hi : py);
+  long i0 = (long)floor(px), j0 = (long)floor(py);
+  if (i0 > npix - 2) i0 = npix - 2;
+  if (j0 > npix - 2) j0 = npix - 2;
+  if (i0 < 0) i0 = 0;
+  if (j0 < 0) j0 = 0;
+  long i1 = (i0 + 1 < npix) ? i0 + 1 : i0, j1 = (j0 + 1 < npix) ? j0 + 1 : j0;
+  double fx = px - (double)i0, fy = py - (double)j0;
+  return (1.0 - fy) * ((1.0 - fx) * A[j0 * npix + i0] + fx * A[j0 * npix + i1]) +
+         fy * ((1.0 - fx) * A[j1 * npix + i0] + fx * A[j1 * npix + i1]);
+}
+
+static int cmp_double(const void *a, const void *b) {
+  double x = *(const double *)a, y = *(const double *)b;
+  return (x > y) - (x < y);
+}
+
+/* Largest magnification a source meets anywhere on the straight line
+ * (u0, alpha) (§4.3 (i): the magnification along a trajectory read from
+ * the point-source map).  Inside the map the bilinear interpolant along
+ * the line is a quadratic in tau between consecutive crossings of texel-
+ * centre lines, so its maximum is at a crossing, at an end of the inside
+ * interval, or at the vertex of a piece; outside the map (tau <= tau_lo or
+ * tau >= tau_hi, or everywhere when the line misses the map) the Paczynski
+ * A(|y|), |y|^2 = tau^2 + u0^2, is largest at the outside tau nearest 0. */
+double orc_line_max(const float *A, int npix, double L, double u,
+                    double alpha) {
+  double c = cos(alpha), s = sin(alpha);
+  /* tau interval inside |y1| < L, |y2| < L */
+  double lo = -INFINITY, hi = INFINITY;
+  if (c != 0.0) {
+    double a0 = (-L + u * s) / c, a1 = (L + u * s) / c;
+    lo = fmax(lo, fmin(a0, a1));
+    hi = fmin(hi, fmax(a0, a1));
+  } else if (!(fabs(u * s) < L)) {
+    hi = lo;
+  }
+  if (s != 0.0) {
+    double b0 = (-L - u * c) / s, b1 = (L - u * c) / s;
+    lo = fmax(lo, fmin(b0, b1));
+    hi = fmin(hi, fmax(b0, b1));
+  } else if (!(fabs(u * c) < L)) {
+    hi = lo;
+  }
+  double best;
+  /* outside part */
+  if (!(lo < hi)) {
+    best = orc_pspl(fabs(u));
+    return best;
+  }
+  {
+    double tn = (lo > 0.0 || hi < 0.0) ? 0.0 : (-lo < hi ? lo : hi);
+    best = orc_pspl(sqrt(tn * tn + u * u));
+  }
+  /* inside: breakpoints where a texel-centre coordinate is an integer */
+  double dlt = (2.0 * L) / (double)npix;
+  double ax = c / dlt, bx = (-u * s + L) / dlt - 0.5;
+  double ay = s / dlt, by = (u * c + L) / dlt - 0.5;
+  size_t cap = 2 * (size_t)npix + 4, nb = 0;
+  double *tb = (double *)malloc(cap * sizeof(double));
+  tb[nb++] = lo;
+  tb[nb++] = hi;
+  for (int k = 0; k < npix; ++k) {
+    if (ax != 0.0) {
+      double t = ((double)k - bx) / ax;
+      if (t > lo && t < hi) tb[nb++] = t;
+    }
+    if (ay != 0.0) {
+      double t = ((double)k - by) / ay;
+      if (t > lo && t < hi) tb[nb++] = t;
+    }
+  }
+  qsort(tb, nb, sizeof(double), cmp_double);
+  for (size_t k = 0; k + 1 < nb; ++k) {
+    double ta = tb[k], tc = tb[k + 1];
+    double fa = bil_clamped(A, npix, L, ta * c - u * s, ta * s + u * c);
+    if (fa > best) best = fa;
+    if (!(tc > ta)) continue;
+    double tm = 0.5 * (ta + tc), h = 0.5 * (tc - ta);
+    double fc = bil_clamped(A, npix, L, tc * c - u * s, tc * s + u * c);
+    double fm = bil_clamped(A, npix, L, tm * c - u * s, tm * s + u * c);
+    if (fc > best) best = fc;
+    if (fm > best) best = fm;
+    double g2 = (fa + fc - 2.0 * fm) / (2.0 * h * h); /* curvature / 2 */
+    if (g2 < 0.0) {
+      double g1 = (fc - fa) / (2.0 * h);
+      double tv = tm - g1 / (2.0 * g2);
+      if (tv > ta && tv < tc) {
+        double fv = bil_clamped(A, npix, L, tv * c - u * s, tv * s + u * c);
+        if (fv > best) best = fv;
+      }
+    }
+  }
+  free(tb);
+  return best;
+}
+
 /* Given magnifications A[i] at the epochs, the weighted least-squares
  * (Fs, Fb) of F = Fs A + Fb (normal equations, closed form) and the chi^2
  * as the sum of per-point contributions w (F - Fs A - Fb)^2.

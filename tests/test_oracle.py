@@ -555,3 +555,49 @@ def test_fs_uniform_disc_on_a_point_lens_centre():
     centre = out[npix // 2 - 1:npix // 2 + 1, npix // 2 - 1:npix // 2 + 1]
     exact = np.sqrt(1 + 4 / rho ** 2)
     assert centre.mean() == pytest.approx(exact, rel=2e-3)
+
+
+# ------------------------------------------------------------ line maxima
+def _line_samples(A, L, u, al, n=60001, span=6.0):
+    tau = np.linspace(-span, span, n)
+    return np.array([orc.map_A(A, L, t * math.cos(al) - u * math.sin(al),
+                               t * math.sin(al) + u * math.cos(al))
+                     for t in tau])
+
+
+def test_line_max_bounds_dense_samples():
+    # brute force: no sample along the line exceeds the exact maximum, and
+    # dense samples come close to it
+    A, *_ = orc.build_map(1.0, 1e-2, 2.0, 48, 600, 3.0, nthreads=8)
+    rng = np.random.default_rng(3)
+    for _ in range(12):
+        u = rng.uniform(-0.9, 0.9)
+        al = rng.uniform(0, 2 * np.pi)
+        mx = orc.line_max(A, 2.0, u, al)
+        v = _line_samples(A, 2.0, u, al)
+        assert v.max() <= mx * (1 + 1e-12)
+        assert v.max() >= mx * (1 - 2e-3)
+
+
+def test_line_max_plane_bump_and_outside():
+    L, npix = 1.0, 32
+    jj, ii = np.meshgrid(np.arange(npix), np.arange(npix), indexing="ij")
+    # plane increasing in the first coordinate: a horizontal line peaks at
+    # the last texel centre (the lookup is clamped beyond it)
+    P = (10.0 + 0.5 * ii).astype(np.float32)
+    assert orc.line_max(P, L, 0.3, 0.0) == pytest.approx(10.0 + 0.5 * 31,
+                                                          rel=1e-13)
+    # and transposed: a vertical line sees the constant of its column
+    assert orc.line_max(P.T.copy(), L, 0.3, 0.0) < 10.0 + 0.5 * 31
+    # one bright texel: a line through its centre meets it exactly
+    B = np.ones((npix, npix), np.float32)
+    B[20, 11] = 5.0
+    d = 2 * L / npix
+    y1, y2 = -L + 11.5 * d, -L + 20.5 * d
+    al = 0.3
+    u = -y1 * math.sin(al) + y2 * math.cos(al)  # the line through (y1, y2)
+    assert orc.line_max(B, L, u, al) == pytest.approx(5.0, rel=1e-12)
+    # a line that misses the map sees only the Paczynski curve, at its
+    # closest approach
+    assert orc.line_max(B, L, 3.0, 0.7) == pytest.approx(orc.pspl(3.0),
+                                                         rel=1e-14)
