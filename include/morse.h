@@ -217,7 +217,26 @@ typedef struct {
   double u0_lo, u0_hi, t0_lo, t0_hi, tE_lo, tE_hi;
   int u0_log, tE_log;
   int top_k;
+  /* minimum-magnification cut (§4.3 (i)); 0: off.  Trajectories whose
+   * (u0, alpha) line never reaches a_min (the largest magnification on the
+   * whole line: the map's bilinear lookup inside, Paczynski outside; see
+   * morse_line_max) cannot fit a light curve that needs a_min and are not
+   * searched: top-K results are those of the other trajectories, dense
+   * results give them chi2 = +inf and Fs = Fb = 0.  Supported by
+   * morse_grid_chi2, morse_grid_chi2_dense, morse_sweep and
+   * morse_search_sweep; the batched and allocation-free searches return
+   * EUNSUPPORTED for a_min > 0. */
+  float a_min;
 } morse_grid;
+
+/* Largest magnification on each (u0, alpha) line of the grid (§4.3 (i)):
+ * out[i_u0 * n_alpha + i_alpha] (host, n_u0 * n_alpha doubles) = the
+ * maximum over the whole straight line of the map's bilinear lookup inside
+ * the map (exactly: the lookup is quadratic between texel-centre
+ * crossings) and of the Paczynski curve outside it.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+morse_status morse_line_max(morse_ctx *ctx, const morse_map *map,
+                            const morse_grid *grid, double *out);
 
 enum {
   MORSE_FIT_DEGENERATE = 1, /* A constant along the track: Fs = 0          */

@@ -59,13 +59,14 @@ class Grid(ctypes.Structure):
                 ("t0_lo", ctypes.c_double), ("t0_hi", ctypes.c_double),
                 ("tE_lo", ctypes.c_double), ("tE_hi", ctypes.c_double),
                 ("u0_log", ctypes.c_int), ("tE_log", ctypes.c_int),
-                ("top_k", ctypes.c_int)]
+                ("top_k", ctypes.c_int), ("a_min", ctypes.c_float)]
 
     @classmethod
     def make(cls, n_u0, n_alpha, n_t0, n_tE, u0_lo, u0_hi, t0_lo, t0_hi,
-             tE_lo, tE_hi, u0_log=True, tE_log=True, top_k=16):
+             tE_lo, tE_hi, u0_log=True, tE_log=True, top_k=16, a_min=0.0):
         return cls(n_u0, n_alpha, n_t0, n_tE, u0_lo, u0_hi, t0_lo, t0_hi,
-                   tE_lo, tE_hi, int(bool(u0_log)), int(bool(tE_log)), top_k)
+                   tE_lo, tE_hi, int(bool(u0_log)), int(bool(tE_log)), top_k,
+                   float(a_min))
 
     @property
     def size(self):
@@ -131,6 +132,7 @@ _SIGS = {
     "morse_map_free": (None, [_P]),
     "morse_map_set_lookup": (_S, [_P, _I]),
     "morse_map_finite_source": (_S, [_P, _P, _D, _D, _P]),
+    "morse_line_max": (_S, [_P, _P, _P, _P]),
     "morse_grid_chi2_batch": (_S, [_P, _P, _I, _P, _I, _P, _P]),
     "morse_measure_peaks": (_S, [_P, _P]),
     "morse_batch_tuning": (_S, [_P, _I]),
@@ -284,6 +286,14 @@ class Context:
                                         len(maps), ctypes.byref(grid),
                                         _ptr(out))
         self._check(st, "morse_grid_chi2_batch")
+        return out
+
+    def line_max(self, map_, grid: Grid) -> np.ndarray:
+        """Largest magnification on every (u0, alpha) line of the grid
+        (morse_line_max): [n_u0, n_alpha]."""
+        out = np.zeros((grid.n_u0, grid.n_alpha))
+        self._check(_lib.morse_line_max(self._h, map_._h, ctypes.byref(grid),
+                                        _ptr(out)), "morse_line_max")
         return out
 
     def measure_peaks(self) -> dict:

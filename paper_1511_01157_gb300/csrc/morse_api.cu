@@ -140,6 +140,8 @@ morse_status check_grid(morse_ctx *ctx, const morse_grid *g) {
     return fail(ctx, MORSE_EINVAL, "log-spaced u0 needs positive bounds");
   if (g->top_k < 1 || g->top_k > 4096)
     return fail(ctx, MORSE_EINVAL, "top_k must be in [1, 4096]");
+  if (!(g->a_min >= 0.0f) || !std::isfinite(g->a_min))
+    return fail(ctx, MORSE_EINVAL, "a_min must be finite and >= 0");
   double total = (double)g->n_u0 * g->n_alpha * g->n_t0 * g->n_tE;
   if (total > 9.0e15)
     return fail(ctx, MORSE_EINVAL, "grid has too many trajectories");
@@ -479,7 +481,7 @@ struct Plan {
   bool dense, ep_smem;
   size_t smem;
   int grid;
-  size_t off_tab, off_hdr, off_pa, off_pb, off_out, bytes;
+  size_t off_tab, off_lmax, off_hdr, off_pa, off_pb, off_out, bytes;
 };
 
 // Device words of one search call (in the workspace header): the grid-wide
@@ -552,7 +554,9 @@ morse_status plan_search(morse_ctx *ctx, const morse_event *ev,
   pl->smem = smem;
   pl->grid = grid;
   pl->off_tab = 0;
-  pl->off_hdr = align_up(tables_bytes(g), 256);
+  pl->off_lmax = align_up(tables_bytes(g), 256);
+  pl->off_hdr = align_up(
+      pl->off_lmax + sizeof(double) * (size_t)g->n_u0 * g->n_alpha, 256);
   pl->off_pa = pl->off_hdr + 256;
   size_t list_bytes = dense ? 0 : sizeof(Entry) * (size_t)grid * K;
   pl->off_pb = align_up(pl->off_pa + list_bytes, 256);
@@ -560,6 +564,26 @@ morse_status plan_search(morse_ctx *ctx, const morse_event *ev,
   size_t out_bytes = dense ? sizeof(double) * 3 * (size_t)n_out
                            : sizeof(morse_fit) * (size_t)K * (size_t)n_out;
   pl->bytes = pl->off_out + out_bytes;
+  return MORSE_OK;
+}
+
+// The minimum-magnification cut of a grid on a map: queue the line maxima
+// into the plan's table and point the search at them (no-op for a_min 0).
+morse_status enqueue_cut(morse_ctx *ctx, const morse_map *map,
+                         const morse_grid *g, const Tables &T, const Plan &pl,
+                         char *base, morse::SearchParams *P) {
+  if (!(g->a_min > 0.0f)) {
+    P->linemax = nullptr;
+    P->a_min = 0.0;
+    return MORSE_OK;
+  }
+  double *lm = (double *)(base + pl.off_lmax);
+  MORSE_CUDA(ctx, morse::launch_line_max(map->A, map->npix, map->L, T.u0v,
+                                         T.ca, T.sa, g->n_u0, g->n_alpha, lm,
+                                         ctx->stream));
+  ctx->launches += 1;
+  P->linemax = lm;
+  P->a_min = (double)g->a_min;
   return MORSE_OK;
 }
 
@@ -680,6 +704,7 @@ morse_status sweep_impl(morse_ctx *ctx, const morse_event *ev,
   for (int i = 0; i < n_maps; ++i) {
     MORSE_TRY(enqueue_build(ctx, m, specs[(size_t)i]));
     if (i > 0) MORSE_TRY(hdr_reset_threshold(ctx, base, pl));
+    MORSE_TRY(enqueue_cut(ctx, m, grid, T, pl, base, &P));
     MORSE_TRY(enqueue_topk(ctx, pl, P, base, T, fits + (size_t)i * pl.K));
   }
   Hdr h;
@@ -1389,6 +1414,30 @@ morse_status morse_map_info(const morse_map *map, int *npix, double *extent,
   return MORSE_OK;
 }
 
+morse_status morse_line_max(morse_ctx *ctx, const morse_map *map,
+                            const morse_grid *grid, double *out) {
+  if (!ctx || !map || !out) return MORSE_EINVAL;
+  if (map->ctx != ctx) return fail(ctx, MORSE_EINVAL, "map of another ctx");
+  MORSE_TRY(check_grid(ctx, grid));
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  call_begin(ctx);
+  const size_t n = (size_t)grid->n_u0 * grid->n_alpha;
+  const size_t off = align_up(tables_bytes(grid), 256);
+  void *ws = nullptr;
+  MORSE_TRY(ws_reserve(ctx, off + sizeof(double) * n, &ws));
+  Tables T;
+  const double dlt = (2.0 * map->L) / (double)map->npix;
+  MORSE_TRY(upload_tables(ctx, grid, 0.0, map->L, dlt, ws, &T));
+  double *lm = (double *)((char *)ws + off);
+  MORSE_CUDA(ctx, morse::launch_line_max(map->A, map->npix, map->L, T.u0v,
+                                         T.ca, T.sa, grid->n_u0,
+                                         grid->n_alpha, lm, ctx->stream));
+  ctx->launches += 1;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(out, lm, sizeof(double) * n,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  return sync_and_collect(ctx, "line maxima");
+}
+
 morse_status morse_map_finite_source(morse_ctx *ctx, const morse_map *src,
                                      double rho, double gamma,
                                      morse_map **out) {
@@ -1649,6 +1698,7 @@ morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
   morse::set_groups(&P);
   morse_fit *fits = (morse_fit *)(base + pl.off_out);
   MORSE_TRY(hdr_init(ctx, base, pl, &P));
+  MORSE_TRY(enqueue_cut(ctx, map, grid, T, pl, base, &P));
   MORSE_TRY(enqueue_topk(ctx, pl, P, base, T, fits));
   Hdr h;
   MORSE_CUDA(ctx, cudaMemcpyAsync(&h, base + pl.off_hdr, sizeof(Hdr),
@@ -1698,6 +1748,7 @@ morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
   P.dFs = P.dchi2 + count;
   P.dFb = P.dFs + count;
   MORSE_TRY(hdr_init(ctx, base, pl, &P));
+  MORSE_TRY(enqueue_cut(ctx, map, grid, T, pl, base, &P));
   int r = t_begin(ctx, KT_SEARCH);
   MORSE_CUDA(ctx, morse::launch_search(P, true, pl.ep_smem, pl.grid, pl.smem,
                                        ctx->stream));
@@ -2014,6 +2065,9 @@ morse_status morse_grid_chi2_batch(morse_ctx *ctx,
   if ((long long)n_ev * n_maps > 0x7fffffffLL)
     return fail(ctx, MORSE_EINVAL, "too many (event, map) pairs");
   MORSE_TRY(check_grid(ctx, grid));
+  if (grid->a_min > 0.0f)
+    return fail(ctx, MORSE_EUNSUPPORTED,
+                "the batched search has no minimum-magnification cut");
   for (int e = 0; e < n_ev; ++e)
     if (!evs[e] || evs[e]->ctx != ctx)
       return fail(ctx, MORSE_EINVAL, "event %d is NULL or of another ctx", e);

@@ -207,6 +207,9 @@ struct SearchParams {
   int tpg;                  // trajectories per warp group (1..32)
   long long line;           // trajectories per (u0, alpha) line
   long long ng_line;        // warp groups per line (main pass)
+  const double *linemax;    // [n_u0 n_alpha] largest A of each line, or
+                            // nullptr: no minimum-magnification cut
+  double a_min;             // the cut (with linemax)
   int top_k;
   // outputs
   Entry *partial;           // [gridDim.x][top_k] (top-K mode)
@@ -273,6 +276,11 @@ cudaError_t launch_fill(const FillParams &F, cudaStream_t st);
 // gthr <- min(gthr, chi^2 bits of sel[k-1]) when that entry is real
 cudaError_t launch_seed_threshold(const Entry *sel, int k,
                                   unsigned long long *gthr, cudaStream_t st);
+// out[iu n_alpha + ia] = largest magnification on line (u0v[iu], alpha_ia)
+cudaError_t launch_line_max(const float *A, int npix, double L,
+                            const double *u0v, const double *ca,
+                            const double *sa, int n_u0, int n_alpha,
+                            double *out, cudaStream_t st);
 // slab[iu n_alpha + ia] = tau interval of line (u0v[iu], alpha_ia) inside
 // the map of half-width L
 cudaError_t launch_slab(const double *u0v, const double *ca, const double *sa,

@@ -93,6 +93,10 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
              cudaGetErrorString(e));
     return MORSE_ECUDA;
   }
+  if (g->a_min > 0.0f)
+    return set_err(ctx, MORSE_EUNSUPPORTED,
+                   "the allocation-free search has no minimum-magnification "
+                   "cut");
   const int K = g->top_k;
   const long long count =
       (long long)g->n_u0 * g->n_alpha * g->n_t0 * g->n_tE;

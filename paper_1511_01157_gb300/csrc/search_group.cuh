@@ -128,6 +128,17 @@ __device__ __forceinline__ void search_group(const SearchParams &P,
                                              unsigned long long &n_exact) {
   const int nvalid = (int)max(0LL, hi - lo);
   if (nvalid == 0) return;  // warp-uniform
+  if (P.linemax && lined &&
+      __ldg(&P.linemax[lo / P.line]) < P.a_min) {
+    // minimum-magnification cut: the whole group's line is too faint
+    if (DENSE && lane < nvalid) {
+      const long long o = lo - P.first + lane;
+      P.dchi2[o] = CUDART_INF;
+      if (P.dFs) P.dFs[o] = 0.0;
+      if (P.dFb) P.dFb[o] = 0.0;
+    }
+    return;
+  }
   const int ml = lane < nvalid ? lane : 0;
   const long long my = lined ? lo + ml : P.first + (lo + ml) * P.stride;
   const long long out_off = lined ? lo - P.first : lo;  // dense output
@@ -179,7 +190,10 @@ __device__ __forceinline__ void search_group(const SearchParams &P,
       if (P.dFb) P.dFb[o] = sol.Bc + P.Fref - sol.Fs;
     }
   } else {
-    const bool keep = lane < nvalid && my_chi2 <= thr && my_chi2 < CUDART_INF;
+    bool keep = lane < nvalid && my_chi2 <= thr && my_chi2 < CUDART_INF;
+    // a strided (pilot) sample mixes lines: drop the cut ones here
+    if (keep && P.linemax && !lined)
+      keep = __ldg(&P.linemax[my / P.line]) >= P.a_min;
     warp_merge(P, T, K, warp, lane, keep, my_chi2, my);
   }
 }
