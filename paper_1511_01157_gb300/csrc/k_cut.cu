@@ -10,8 +10,8 @@
 // |y|^2 = tau^2 + u0^2, is largest at the outside tau nearest 0.  The
 // inside interval is cut into 32 equal parts, one per lane; a lane steps
 // through its part's crossings in order (the next x- and y-crossings from
-// integer indices, so that it always advances) and evaluates the pieces in
-// FP64 from the FP32 texels.
+// integer indices, so that it always advances) and evaluates each piece in
+// FP64 from its cell's four FP32 texels, loaded once.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
@@ -24,26 +24,6 @@ namespace morse {
 namespace {
 
 using namespace dev;
-
-// Bilinear interpolant at pixel coordinates (px, py), clamped to the
-// outermost texel centres.
-__device__ __forceinline__ double bil_px(const float *__restrict__ A,
-                                         int npix, double px, double py) {
-  const double hi = (double)(npix - 1);
-  px = fmin(fmax(px, 0.0), hi);
-  py = fmin(fmax(py, 0.0), hi);
-  int i0 = (int)floor(px), j0 = (int)floor(py);
-  i0 = min(max(i0, 0), max(npix - 2, 0));
-  j0 = min(max(j0, 0), max(npix - 2, 0));
-  const int i1 = min(i0 + 1, npix - 1), j1 = min(j0 + 1, npix - 1);
-  const double fx = px - (double)i0, fy = py - (double)j0;
-  const double a00 = __ldg(&A[(size_t)j0 * npix + i0]);
-  const double a10 = __ldg(&A[(size_t)j0 * npix + i1]);
-  const double a01 = __ldg(&A[(size_t)j1 * npix + i0]);
-  const double a11 = __ldg(&A[(size_t)j1 * npix + i1]);
-  return (1.0 - fy) * ((1.0 - fx) * a00 + fx * a10) +
-         fy * ((1.0 - fx) * a01 + fx * a11);
-}
 
 __device__ __forceinline__ double pspl64(double u) {
   return (u * u + 2.0) / (u * sqrt(u * u + 4.0));
@@ -73,7 +53,41 @@ __global__ void k_line_max(const float *__restrict__ A, int npix, double L,
   const double dlt = (2.0 * L) / (double)npix;
   const double ax = c / dlt, bx = (-u * s + L) / dlt - 0.5;
   const double ay = s / dlt, by = (u * c + L) / dlt - 0.5;
-  auto f = [&](double t) { return bil_px(A, npix, ax * t + bx, ay * t + by); };
+  const double pmax = (double)(npix - 1);
+  // One piece [t0, t1] lies in one cell (i0, j0) with the clamping state
+  // fixed, so the lookup is a0 + d1 fx + d2 fy + d3 fx fy with fx, fy
+  // linear in tau: its four texels are loaded once and the ends and the
+  // vertex evaluated from them.
+  auto piece = [&](double t0, double t1) {
+    const double tm = 0.5 * (t0 + t1);
+    const double pxm = ax * tm + bx, pym = ay * tm + by;
+    const bool cx = pxm < 0.0 || pxm > pmax, cy = pym < 0.0 || pym > pmax;
+    const double qx = fmin(fmax(pxm, 0.0), pmax), qy = fmin(fmax(pym, 0.0), pmax);
+    int i0 = (int)floor(qx), j0 = (int)floor(qy);
+    i0 = min(max(i0, 0), max(npix - 2, 0));
+    j0 = min(max(j0, 0), max(npix - 2, 0));
+    const int i1 = min(i0 + 1, npix - 1), j1 = min(j0 + 1, npix - 1);
+    const double a00 = __ldg(&A[(size_t)j0 * npix + i0]);
+    const double a10 = __ldg(&A[(size_t)j0 * npix + i1]);
+    const double a01 = __ldg(&A[(size_t)j1 * npix + i0]);
+    const double a11 = __ldg(&A[(size_t)j1 * npix + i1]);
+    const double d1 = a10 - a00, d2 = a01 - a00, d3 = a00 - a10 - a01 + a11;
+    // fx = ux + vx t, fy = uy + vy t (constant when clamped)
+    const double vx = cx ? 0.0 : ax, ux = cx ? qx - i0 : bx - i0;
+    const double vy = cy ? 0.0 : ay, uy = cy ? qy - j0 : by - j0;
+    auto val = [&](double t) {
+      const double fx = ux + vx * t, fy = uy + vy * t;
+      return a00 + d1 * fx + d2 * fy + d3 * fx * fy;
+    };
+    double m = fmax(val(t0), val(t1));
+    const double c2 = d3 * vx * vy;
+    if (c2 < 0.0) {
+      const double c1 = d1 * vx + d2 * vy + d3 * (ux * vy + uy * vx);
+      const double tv = -c1 / (2.0 * c2);
+      if (tv > t0 && tv < t1) m = fmax(m, val(tv));
+    }
+    return m;
+  };
   const double w = (hi - lo) / 32.0;
   const double ta = lo + lane * w;
   const double tb = lane == 31 ? hi : lo + (lane + 1) * w;
@@ -85,27 +99,15 @@ __global__ void k_line_max(const float *__restrict__ A, int npix, double L,
   const double sx = ax > 0.0 ? 1.0 : -1.0, sy = ay > 0.0 ? 1.0 : -1.0;
   const double iax = ax != 0.0 ? 1.0 / ax : 0.0;
   const double iay = ay != 0.0 ? 1.0 / ay : 0.0;
-  double prev = ta, fprev = f(ta);
-  best = fmax(best, fprev);
+  double prev = ta;
   const int cap = 2 * npix + 8;  // crossings in a lane's part, at most
   for (int it = 0; it < cap; ++it) {
     const double tx = ax != 0.0 ? (kx - bx) * iax : CUDART_INF;
     const double ty = ay != 0.0 ? (ky - by) * iay : CUDART_INF;
-    double cur = fmin(fmin(tx, ty), tb);
-    if (!(cur > prev)) cur = prev;  // a crossing at prev: advance the index
+    const double cur = fmin(fmin(tx, ty), tb);
     if (cur > prev) {
-      const double fc = f(cur);
-      const double tm = 0.5 * (prev + cur), h = 0.5 * (cur - prev);
-      const double fm = f(tm);
-      best = fmax(best, fmax(fc, fm));
-      const double g2 = (fprev + fc - 2.0 * fm) / (2.0 * h * h);
-      if (g2 < 0.0) {
-        const double g1 = (fc - fprev) / (2.0 * h);
-        const double tv = tm - g1 / (2.0 * g2);
-        if (tv > prev && tv < cur) best = fmax(best, f(tv));
-      }
+      best = fmax(best, piece(prev, cur));
       prev = cur;
-      fprev = fc;
     }
     if (prev >= tb) break;
     if (tx <= ty) kx += sx;

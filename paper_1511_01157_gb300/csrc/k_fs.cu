@@ -122,7 +122,39 @@ __global__ void __launch_bounds__(kFsThreads)
   }
 }
 
+// Source profile integrated over texel (dx, dy), |dx|, |dy| <= R, on
+// kSub x kSub midpoint points (unnormalised), one thread per texel.
+constexpr int kFsSub = 8;
+__global__ void k_fs_weights(double rho, double gamma, int R,
+                             double *__restrict__ w) {
+  const int side = 2 * R + 1;
+  const int n = side * side;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += gridDim.x * blockDim.x) {
+    const int dy = k / side - R, dx = k % side - R;
+    double acc = 0.0;
+    for (int b = 0; b < kFsSub; ++b) {
+      const double y = dy - 0.5 + (b + 0.5) / kFsSub;
+      for (int a = 0; a < kFsSub; ++a) {
+        const double x = dx - 0.5 + (a + 0.5) / kFsSub;
+        const double u2 = (x * x + y * y) / (rho * rho);
+        if (u2 < 1.0) acc += 1.0 - gamma * (1.0 - 1.5 * sqrt(1.0 - u2));
+      }
+    }
+    w[k] = acc;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_fs_weights(double rho_px, double gamma, int R, double *w,
+                              cudaStream_t st) {
+  const int n = (2 * R + 1) * (2 * R + 1);
+  int blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_fs_weights<<<blocks, 256, 0, st>>>(rho_px, gamma, R, w);
+  return cudaGetLastError();
+}
 
 size_t fs_smem_bytes(int R) {
   return sizeof(float) *

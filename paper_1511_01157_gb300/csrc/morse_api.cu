@@ -1457,24 +1457,22 @@ morse_status morse_map_finite_source(morse_ctx *ctx, const morse_map *src,
                 rpx);
   const int R = (int)ceil(rpx + 0.5);
   const int side = 2 * R + 1;
-  // the profile integrated over each texel on 8 x 8 midpoint points
-  constexpr int kSub = 8;
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  // the profile integrated over each texel on 8 x 8 midpoint points, on the
+  // device; normalised and rounded to FP32 here
   std::vector<double> w((size_t)side * side, 0.0);
+  {
+    void *ws0 = nullptr;
+    MORSE_TRY(ws_reserve(ctx, sizeof(double) * w.size(), &ws0));
+    MORSE_CUDA(ctx, morse::launch_fs_weights(rpx, gamma, R, (double *)ws0,
+                                             ctx->stream));
+    ctx->launches += 1;
+    MORSE_CUDA(ctx, cudaMemcpyAsync(w.data(), ws0, sizeof(double) * w.size(),
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+    MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   double tot = 0.0;
-  for (int dy = -R; dy <= R; ++dy)
-    for (int dx = -R; dx <= R; ++dx) {
-      double acc = 0.0;
-      for (int b = 0; b < kSub; ++b) {
-        const double y = dy - 0.5 + (b + 0.5) / kSub;
-        for (int a = 0; a < kSub; ++a) {
-          const double x = dx - 0.5 + (a + 0.5) / kSub;
-          const double u2 = (x * x + y * y) / (rpx * rpx);
-          if (u2 < 1.0) acc += 1.0 - gamma * (1.0 - 1.5 * sqrt(1.0 - u2));
-        }
-      }
-      w[(size_t)(dy + R) * side + (dx + R)] = acc;
-      tot += acc;
-    }
+  for (double v : w) tot += v;
   if (!(tot > 0.0)) {  // sub-texel source: the centre texel alone
     std::fill(w.begin(), w.end(), 0.0);
     w[(size_t)R * side + R] = 1.0;
@@ -1488,7 +1486,6 @@ morse_status morse_map_finite_source(morse_ctx *ctx, const morse_map *src,
       wf[(size_t)dy * side + dx] = (float)v;
       if (v != 0.0) hw[(size_t)dy] = std::max(hw[(size_t)dy], std::abs(dx - R));
     }
-  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
   call_begin(ctx);
   const size_t wbytes = align_up(sizeof(float) * wf.size(), 256);
   void *ws = nullptr;

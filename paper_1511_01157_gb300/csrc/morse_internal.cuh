@@ -162,6 +162,10 @@ int rayshoot_blocks_per_sm();
 // finite-source map: A convolved with the (2R+1)^2 weights W (rows dy),
 // rowhw[dy + R] = largest |dx| of a nonzero weight in row dy (-1: none)
 size_t fs_smem_bytes(int R);
+// unnormalised texel weights of a source of radius rho_px texels, limb
+// darkening gamma: w[(dy + R)(2R + 1) + dx + R]
+cudaError_t launch_fs_weights(double rho_px, double gamma, int R, double *w,
+                              cudaStream_t st);
 cudaError_t launch_fs_conv(const float *A, int npix, double L, int R,
                            const float *W, const int *rowhw, float *out,
                            cudaStream_t st);
