@@ -601,3 +601,47 @@ def test_line_max_plane_bump_and_outside():
     # closest approach
     assert orc.line_max(B, L, 3.0, 0.7) == pytest.approx(orc.pspl(3.0),
                                                          rel=1e-14)
+
+
+# ------------------------------------------------------------ caustics
+def test_critical_points_and_caustic_count_by_topology():
+    from oracle import caustics as oc
+    for s, q in [(0.5, 1e-2), (0.7, 0.3), (1.0, 1.0), (1.0, 1e-3),
+                 (1.6, 1e-3), (2.5, 5e-4), (0.9, 0.1)]:
+        z = oc.critical_points(s, q, 360)
+        e1, e2, x1, x2 = orc.lens(s, q)
+        D = e1 / (np.conj(z) - x1) ** 2 + e2 / (np.conj(z) - x2) ** 2
+        assert np.allclose(np.abs(D), 1.0, atol=1e-9)
+        cs = oc.caustics(s, q, 720)
+        assert len(cs) == oc.topology_count(s, q), (s, q, cs)
+        # mirror symmetry about the lens axis
+        ys = sorted(round(c[1], 6) for c in cs)
+        assert np.allclose(ys, sorted(-y for y in ys), atol=1e-6)
+
+
+def test_caustic_positions_and_image_count_change():
+    from oracle import caustics as oc
+    # equal masses, s = 1: one caustic centred on the origin
+    (c,) = oc.caustics(1.0, 1.0, 720)
+    assert abs(c[0]) < 1e-9 and abs(c[1]) < 1e-9
+    # wide, small q: the planetary caustic near s - 1/s from the primary
+    s, q = 2.5, 5e-4
+    e1, e2, x1, x2 = orc.lens(s, q)
+    cs = oc.caustics(s, q, 720)
+    planet = max(cs, key=lambda t: t[0])
+    assert planet[0] - x1 == pytest.approx(s - 1.0 / s, rel=0.02)
+    assert planet[2] < 0.05
+    # across a caustic the number of images changes by two
+    z = oc.critical_points(1.2, 0.05, 720)
+    zeta = oc.caustic_of(1.2, 0.05, z[:, 0])
+    changed = 0
+    for k in range(10, 720, 37):
+        tang = zeta[k + 1] - zeta[k - 1]
+        nrm = 1j * tang / abs(tang)
+        eps = 1e-4 * abs(tang)
+        a = orc.images(1.2, 0.05, (zeta[k] + eps * nrm).real,
+                       (zeta[k] + eps * nrm).imag, 1e-9)[0]
+        b = orc.images(1.2, 0.05, (zeta[k] - eps * nrm).real,
+                       (zeta[k] - eps * nrm).imag, 1e-9)[0]
+        changed += {a, b} == {3, 5}
+    assert changed >= 17  # of 20 (cusps excepted)
