@@ -238,6 +238,39 @@ typedef struct {
 morse_status morse_line_max(morse_ctx *ctx, const morse_map *map,
                             const morse_grid *grid, double *out);
 
+/* Caustics of the binary lens (s, q) (§4.2: trajectory grids about the
+ * central regions of the caustics, scaled by their sizes).  The critical
+ * points solve, for psi_k = 2 pi k / n_psi, the quartic in w = conj(z)
+ *     eps1 (w - x2)^2 + eps2 (w - x1)^2 = exp(-i psi) (w - x1)^2 (w - x2)^2
+ * (det J = 0, Eq. 4), on the device; their images by Eq. 2 are the caustic
+ * points.  The four branches are followed across psi by the pairing of
+ * least total distance and a full turn's permutation groups them into
+ * closed critical curves, one caustic each (1, 2 or 3 by topology).  A
+ * caustic's centre is the mean of its points and its size the largest
+ * distance from the centre to one of them.  out receives up to 3 records,
+ * sorted by (c1, c2); *n_out their number.  Arguments: s, q > 0,
+ * 16 <= n_psi <= 1 << 20.  Errors: EINVAL, ENOMEM, ECUDA. */
+typedef struct {
+  double c1, c2;    /* centre (Einstein radii, centre-of-mass origin)     */
+  double size;      /* largest distance from the centre to the caustic    */
+  int32_t n_points; /* caustic points of the caustic                      */
+  int32_t reserved;
+} morse_caustic;
+morse_status morse_caustics(morse_ctx *ctx, double s, double q, int n_psi,
+                            morse_caustic out[3], int *n_out);
+
+/* The lines of an (r, phi) grid about caustics: for caustic c (centre C,
+ * size R), impact r = (r_lo + (r_hi - r_lo) i / (n_r - 1)) R from C
+ * (i < n_r), direction phi_k = 2 pi k / n_phi, in the order (c, i, k).
+ * lines[3 j + 0 .. 2] = (u, alpha, shift): the same line about the origin
+ * has impact u = r + C.n and direction alpha = phi, and its closest
+ * approach to C comes tau = shift = C.d after its closest approach to the
+ * origin (d = (cos phi, sin phi), n = (-sin phi, cos phi)).  Host only.
+ * Errors: EINVAL. */
+morse_status morse_rphi_lines(const morse_caustic *caustics, int n_caustics,
+                              int n_r, double r_lo, double r_hi, int n_phi,
+                              double *lines);
+
 enum {
   MORSE_FIT_DEGENERATE = 1, /* A constant along the track: Fs = 0          */
   MORSE_FIT_REFINED = 2     /* parameters from morse_refine, off the grid   */
@@ -261,6 +294,21 @@ typedef struct {
 morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
                              const morse_map *map, const morse_grid *grid,
                              morse_fit *out);
+
+/* morse_grid_chi2 over a grid of arbitrary lines: trajectory
+ * (j, i_t0, i_tE), index (j n_t0 + i_t0) n_tE + i_tE, follows line j of
+ * lines[3 j .. 3 j + 2] = (u, alpha, shift) (morse_rphi_lines) with t0 the
+ * time of its closest approach to the line's reference point, i.e. the
+ * (u0, alpha, t0, tE) trajectory (u, alpha, t0 - shift tE, tE).  grid gives
+ * n_u0 = the number of lines, n_alpha = 1, the t0 and tE axes and top_k
+ * (its u0 range is not used).  The records are in the (u0, alpha, t0, tE)
+ * convention of morse_grid_chi2, so they seed morse_refine directly.
+ * Errors: EINVAL (n_alpha != 1, non-finite lines), EUNSUPPORTED
+ * (a_min > 0), ENOMEM, ECUDA, ETIMEOUT. */
+morse_status morse_grid_chi2_lines(morse_ctx *ctx, const morse_event *ev,
+                                   const morse_map *map,
+                                   const morse_grid *grid,
+                                   const double *lines, morse_fit *out);
 
 /* morse_grid_chi2 without any device allocation.  The paper has no
  * counterpart: this is a deployment variant of the same search.

@@ -94,6 +94,25 @@ class MapOpts(ctypes.Structure):
                 ("generator", ctypes.c_int)]
 
 
+class Caustic(ctypes.Structure):
+    """morse_caustic: centre, size and point count of one caustic."""
+    _fields_ = [("c1", ctypes.c_double), ("c2", ctypes.c_double),
+                ("size", ctypes.c_double), ("n_points", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+def rphi_lines(caustics, n_r, r_lo, r_hi, n_phi) -> np.ndarray:
+    """Lines (u, alpha, shift) of an (r, phi) grid about the caustics
+    (morse_rphi_lines): [n_caustics * n_r * n_phi, 3]."""
+    arr = (Caustic * len(caustics))(*caustics)
+    out = np.zeros((len(caustics) * n_r * n_phi, 3))
+    st = _lib.morse_rphi_lines(arr, len(caustics), int(n_r), float(r_lo),
+                               float(r_hi), int(n_phi), _ptr(out))
+    if st != OK:
+        raise MorseError(st, "morse_rphi_lines")
+    return out
+
+
 class Peaks(ctypes.Structure):
     """morse_peaks: measured throughput of the GPU for the rooflines."""
     _fields_ = [("fp32_fma_per_s", ctypes.c_double),
@@ -133,6 +152,9 @@ _SIGS = {
     "morse_map_set_lookup": (_S, [_P, _I]),
     "morse_map_finite_source": (_S, [_P, _P, _D, _D, _P]),
     "morse_line_max": (_S, [_P, _P, _P, _P]),
+    "morse_caustics": (_S, [_P, _D, _D, _I, _P, _P]),
+    "morse_rphi_lines": (_S, [_P, _I, _I, _D, _D, _I, _P]),
+    "morse_grid_chi2_lines": (_S, [_P, _P, _P, _P, _P, _P]),
     "morse_grid_chi2_batch": (_S, [_P, _P, _I, _P, _I, _P, _P]),
     "morse_measure_peaks": (_S, [_P, _P]),
     "morse_batch_tuning": (_S, [_P, _I]),
@@ -286,6 +308,26 @@ class Context:
                                         len(maps), ctypes.byref(grid),
                                         _ptr(out))
         self._check(st, "morse_grid_chi2_batch")
+        return out
+
+    def caustics(self, s, q, n_psi=720):
+        """Caustics of the lens (s, q) (morse_caustics): list of Caustic."""
+        out = (Caustic * 3)()
+        n = ctypes.c_int()
+        self._check(_lib.morse_caustics(self._h, float(s), float(q),
+                                        int(n_psi), out, ctypes.byref(n)),
+                    "morse_caustics")
+        return [out[i] for i in range(n.value)]
+
+    def grid_chi2_lines(self, event, map_, grid: Grid, lines) -> np.ndarray:
+        """Top-K over a grid of lines (morse_grid_chi2_lines): grid.n_u0 =
+        len(lines), grid.n_alpha = 1."""
+        lines = np.ascontiguousarray(lines, dtype=np.float64)
+        out = np.zeros(grid.top_k, dtype=FIT_DTYPE)
+        st = _lib.morse_grid_chi2_lines(self._h, event._h, map_._h,
+                                        ctypes.byref(grid), _ptr(lines),
+                                        _ptr(out))
+        self._check(st, "morse_grid_chi2_lines")
         return out
 
     def line_max(self, map_, grid: Grid) -> np.ndarray:
@@ -606,5 +648,6 @@ def topk_merge(lists, k):
 
 
 __all__ = ["Context", "Map", "Event", "Grid", "Fit", "FIT_DTYPE", "MapOpts",
+           "Caustic", "rphi_lines",
            "MorseError", "topk_merge", "chi2_function", "version",
            "LIB_PATH", "EXPORTED"]

@@ -342,6 +342,28 @@ cudaError_t launch_fill(const FillParams &F, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+__global__ void k_slab_lines(const double *__restrict__ u,
+                             const double *__restrict__ c,
+                             const double *__restrict__ s, int n, double L,
+                             double2 *__restrict__ slab) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += gridDim.x * blockDim.x) {
+    double lo, hi;
+    slab_tau(L, u[i], c[i], s[i], lo, hi);
+    slab[i] = make_double2(lo, hi);
+  }
+}
+
+cudaError_t launch_slab_lines(const double *u, const double *c,
+                              const double *s, int n, double L, double2 *slab,
+                              cudaStream_t st) {
+  int blocks = (n + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  if (blocks < 1) blocks = 1;
+  k_slab_lines<<<blocks, 256, 0, st>>>(u, c, s, n, L, slab);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_slab(const double *u0v, const double *ca, const double *sa,
                         int n_u0, int n_alpha, double L, double2 *slab,
                         cudaStream_t st) {

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <new>
 #include <vector>
@@ -2264,6 +2265,205 @@ morse_status morse_measure_peaks(morse_ctx *ctx, morse_peaks *out) {
   cudaEventDestroy(e1);
   if (ce != cudaSuccess) return cuda_fail(ctx, ce, "throughput probe");
   return MORSE_OK;
+}
+
+// ------------------------------------------------------------------ lines
+morse_status morse_caustics(morse_ctx *ctx, double s, double q, int n_psi,
+                            morse_caustic out[3], int *n_out) {
+  if (!ctx || !out || !n_out) return MORSE_EINVAL;
+  if (!(s > 0.0) || !is_fin(s) || !(q > 0.0) || !is_fin(q))
+    return fail(ctx, MORSE_EINVAL, "s and q must be finite and > 0");
+  if (n_psi < 16 || n_psi > (1 << 20))
+    return fail(ctx, MORSE_EINVAL, "n_psi must be in [16, 2^20]");
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  call_begin(ctx);
+  const size_t n = (size_t)4 * n_psi;
+  void *ws = nullptr;
+  MORSE_TRY(ws_reserve(ctx, 2 * n * sizeof(double2), &ws));
+  double2 *dz = (double2 *)ws, *dzeta = dz + n;
+  MORSE_CUDA(ctx, morse::launch_critical(s, q, n_psi, dz, dzeta,
+                                         ctx->stream));
+  ctx->launches += 1;
+  std::vector<double2> z(n), zeta(n);
+  MORSE_CUDA(ctx, cudaMemcpyAsync(z.data(), dz, n * sizeof(double2),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_CUDA(ctx, cudaMemcpyAsync(zeta.data(), dzeta, n * sizeof(double2),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_TRY(sync_and_collect(ctx, "critical curves"));
+  // the 24 orderings of four roots
+  std::vector<std::array<int, 4>> perms;
+  {
+    std::array<int, 4> p = {0, 1, 2, 3};
+    do perms.push_back(p);
+    while (std::next_permutation(p.begin(), p.end()));
+  }
+  auto dist = [](double2 a, double2 b) { return hypot(a.x - b.x, a.y - b.y); };
+  // the ordering of set b that best continues set a
+  auto best_perm = [&](const double2 *a, const double2 *b) {
+    int bi = 0;
+    double bd = INFINITY;
+    for (int i = 0; i < (int)perms.size(); ++i) {
+      double d = 0.0;
+      for (int t = 0; t < 4; ++t) d += dist(b[perms[i][t]], a[t]);
+      if (d < bd) {
+        bd = d;
+        bi = i;
+      }
+    }
+    return perms[bi];
+  };
+  for (int k = 1; k < n_psi; ++k) {
+    const std::array<int, 4> p = best_perm(&z[4 * (k - 1)], &z[4 * k]);
+    double2 tz[4], tc[4];
+    for (int t = 0; t < 4; ++t) {
+      tz[t] = z[4 * k + p[t]];
+      tc[t] = zeta[4 * k + p[t]];
+    }
+    for (int t = 0; t < 4; ++t) {
+      z[4 * k + t] = tz[t];
+      zeta[4 * k + t] = tc[t];
+    }
+  }
+  // after a full turn branch t continues as branch wrap[t]: its cycles are
+  // the closed critical curves
+  const std::array<int, 4> wrap = best_perm(&z[4 * (n_psi - 1)], &z[0]);
+  bool seen[4] = {false, false, false, false};
+  int nc = 0;
+  morse_caustic res[4];
+  for (int t = 0; t < 4; ++t) {
+    if (seen[t]) continue;
+    std::vector<int> cyc;
+    for (int j = t; !seen[j]; j = wrap[j]) {
+      seen[j] = true;
+      cyc.push_back(j);
+    }
+    double sx = 0.0, sy = 0.0;
+    long np = 0;
+    for (int k = 0; k < n_psi; ++k)
+      for (int j : cyc) {
+        sx += zeta[4 * k + j].x;
+        sy += zeta[4 * k + j].y;
+        ++np;
+      }
+    const double cx = sx / np, cy = sy / np;
+    double size = 0.0;
+    for (int k = 0; k < n_psi; ++k)
+      for (int j : cyc)
+        size = fmax(size, hypot(zeta[4 * k + j].x - cx,
+                                zeta[4 * k + j].y - cy));
+    res[nc].c1 = cx;
+    res[nc].c2 = cy;
+    res[nc].size = size;
+    res[nc].n_points = (int32_t)np;
+    res[nc].reserved = 0;
+    ++nc;
+  }
+  if (nc > 3) return fail(ctx, MORSE_ECUDA, "%d critical curves", nc);
+  std::sort(res, res + nc, [](const morse_caustic &a, const morse_caustic &b) {
+    const double ax = std::round(a.c1 * 1e9), bx = std::round(b.c1 * 1e9);
+    if (ax != bx) return ax < bx;
+    return std::round(a.c2 * 1e9) < std::round(b.c2 * 1e9);
+  });
+  for (int i = 0; i < nc; ++i) out[i] = res[i];
+  *n_out = nc;
+  return MORSE_OK;
+}
+
+morse_status morse_rphi_lines(const morse_caustic *cs, int n_caustics,
+                              int n_r, double r_lo, double r_hi, int n_phi,
+                              double *lines) {
+  if (!cs || !lines || n_caustics < 1 || n_r < 1 || n_phi < 1 ||
+      !is_fin(r_lo) || !is_fin(r_hi))
+    return MORSE_EINVAL;
+  size_t j = 0;
+  for (int c = 0; c < n_caustics; ++c)
+    for (int i = 0; i < n_r; ++i) {
+      const double f = n_r > 1 ? (double)i / (double)(n_r - 1) : 0.0;
+      const double r = (r_lo + (r_hi - r_lo) * f) * cs[c].size;
+      for (int k = 0; k < n_phi; ++k) {
+        const double phi = 2.0 * M_PI * (double)k / (double)n_phi;
+        const double dc = cos(phi), ds = sin(phi);
+        lines[3 * j + 0] = r + cs[c].c1 * -ds + cs[c].c2 * dc;
+        lines[3 * j + 1] = phi;
+        lines[3 * j + 2] = cs[c].c1 * dc + cs[c].c2 * ds;
+        ++j;
+      }
+    }
+  return MORSE_OK;
+}
+
+morse_status morse_grid_chi2_lines(morse_ctx *ctx, const morse_event *ev,
+                                   const morse_map *map,
+                                   const morse_grid *grid,
+                                   const double *lines, morse_fit *out) {
+  if (!ctx || !out || !lines || !grid) return MORSE_EINVAL;
+  MORSE_TRY(check_pair(ctx, ev, map));
+  if (grid->n_alpha != 1)
+    return fail(ctx, MORSE_EINVAL, "a line grid has n_alpha = 1");
+  if (grid->a_min > 0.0f)
+    return fail(ctx, MORSE_EUNSUPPORTED,
+                "line grids have no minimum-magnification cut");
+  // the u0 axis is replaced by the lines: give it valid placeholder bounds
+  morse_grid g = *grid;
+  g.u0_lo = 1.0;
+  g.u0_hi = 1.0;
+  g.u0_log = 0;
+  MORSE_TRY(check_grid(ctx, &g));
+  const int nl = g.n_u0;
+  for (int j = 0; j < 3 * nl; ++j)
+    if (!is_fin(lines[j])) return fail(ctx, MORSE_EINVAL, "line %d", j / 3);
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  call_begin(ctx);
+  Plan pl;
+  MORSE_TRY(plan_search(ctx, ev, &g, 0, grid_size(&g), false,
+                        morse::map_h16(map), 1, &pl));
+  const size_t off_lines = align_up(pl.bytes, 256);
+  void *ws = nullptr;
+  MORSE_TRY(ws_reserve(ctx, off_lines + 5 * sizeof(double) * (size_t)nl, &ws));
+  char *base = (char *)ws;
+  Tables T;
+  const double dlt = (2.0 * map->L) / (double)map->npix;
+  MORSE_TRY(upload_tables(ctx, &g, ev->t_ref, map->L, dlt, base + pl.off_tab,
+                          &T));
+  // per line: u, cos, sin, shift, alpha
+  std::vector<double> h((size_t)5 * nl);
+  for (int j = 0; j < nl; ++j) {
+    h[(size_t)j] = lines[3 * j];
+    h[(size_t)nl + j] = cos(lines[3 * j + 1]);
+    h[(size_t)2 * nl + j] = sin(lines[3 * j + 1]);
+    h[(size_t)3 * nl + j] = lines[3 * j + 2];
+    h[(size_t)4 * nl + j] = lines[3 * j + 1];
+  }
+  double *dl = (double *)(base + off_lines);
+  MORSE_CUDA(ctx, cudaMemcpyAsync(dl, h.data(), h.size() * sizeof(double),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  MORSE_CUDA(ctx, morse::launch_slab_lines(dl, dl + nl, dl + 2 * nl, nl,
+                                           map->L, T.slab, ctx->stream));
+  ctx->launches += 1;
+  morse::SearchParams P;
+  memset(&P, 0, sizeof(P));
+  map_params(map, &P);
+  event_params(ev, &P);
+  grid_params(&g, T, &P);
+  P.lu = dl;
+  P.lc = dl + nl;
+  P.ls = dl + 2 * nl;
+  P.lsh = dl + 3 * nl;
+  P.la = dl + 4 * nl;
+  P.first = 0;
+  P.count = grid_size(&g);
+  P.stride = 1;
+  morse::set_groups(&P);
+  morse_fit *fits = (morse_fit *)(base + pl.off_out);
+  MORSE_TRY(hdr_init(ctx, base, pl, &P));
+  MORSE_TRY(enqueue_topk(ctx, pl, P, base, T, fits));
+  Hdr hd;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(&hd, base + pl.off_hdr, sizeof(Hdr),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_CUDA(ctx, cudaMemcpyAsync(out, fits, sizeof(morse_fit) * pl.K,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_TRY(sync_and_collect(ctx, "line-grid search"));
+  return hdr_check(ctx, hd);
 }
 
 }  // extern "C"

@@ -205,6 +205,11 @@ struct SearchParams {
   const double *u0v, *ca, *sa, *t0rel, *invtEd, *tEv;
   const double2 *slab;      // [n_u0 n_alpha] tau interval of each line
                             // inside the map (k_slab)
+  // line grids (n_alpha = 1, line = i_u0), else nullptr: per line the
+  // impact u about the origin, cos and sin of the direction, the tau of the
+  // closest approach to the line's reference point past that to the origin
+  // (grid t0 is the time of the former), and the direction alpha
+  const double *lu, *lc, *ls, *lsh, *la;
   int n_u0, n_alpha, n_t0, n_tE;
   long long first, count;   // trajectories first + i * stride, i < count
   long long stride;
@@ -285,6 +290,14 @@ cudaError_t launch_line_max(const float *A, int npix, double L,
                             const double *u0v, const double *ca,
                             const double *sa, int n_u0, int n_alpha,
                             double *out, cudaStream_t st);
+// slab[i] = tau interval of line i of a line grid (u[i], c[i], s[i])
+cudaError_t launch_slab_lines(const double *u, const double *c,
+                              const double *s, int n, double L, double2 *slab,
+                              cudaStream_t st);
+// critical points of the binary lens (s, q): z[k][4] for psi_k = 2 pi k/n
+// (unordered within k), as (re, im) pairs, and their caustic points zeta
+cudaError_t launch_critical(double s, double q, int n_psi, double2 *z,
+                            double2 *zeta, cudaStream_t st);
 // slab[iu n_alpha + ia] = tau interval of line (u0v[iu], alpha_ia) inside
 // the map of half-width L
 cudaError_t launch_slab(const double *u0v, const double *ca, const double *sa,

@@ -139,8 +139,13 @@ __device__ __forceinline__ TrajC traj_consts(const SearchParams &P,
   const int ia = (int)(r % P.n_alpha);
   const int iu = (int)(r / P.n_alpha);
   const double2 sl = P.slab[iu * P.n_alpha + ia];
+  const double tE = P.tEv[itE];
+  if (P.lu)  // line grid: t0 of the closest approach to the reference point
+    return make_traj(P, ep, P.lu[iu], P.lc[iu], P.ls[iu],
+                     P.t0rel[it0] - P.lsh[iu] * tE, P.invtEd[itE], tE, sl.x,
+                     sl.y);
   return make_traj(P, ep, P.u0v[iu], P.ca[ia], P.sa[ia], P.t0rel[it0],
-                   P.invtEd[itE], P.tEv[itE], sl.x, sl.y);
+                   P.invtEd[itE], tE, sl.x, sl.y);
 }
 
 __device__ __forceinline__ TrajC shfl_traj(const TrajC &m, int k) {

@@ -233,10 +233,16 @@ __device__ __forceinline__ void fill_one(const SearchParams &P, const Entry e,
     const int ia = (int)(q % P.n_alpha);
     const int iu = (int)(q / P.n_alpha);
     r.chi2 = isnan(chi2) ? CUDART_INF : chi2;
-    r.t0 = t0abs[it0];
     r.tE = tEv[itE];
-    r.u0 = P.u0v[iu];
-    r.alpha = 2.0 * CUDART_PI * (double)ia / (double)P.n_alpha;
+    if (P.lu) {  // line grid: the record in the (u0, alpha) convention
+      r.t0 = t0abs[it0] - P.lsh[iu] * r.tE;
+      r.u0 = P.lu[iu];
+      r.alpha = P.la[iu];
+    } else {
+      r.t0 = t0abs[it0];
+      r.u0 = P.u0v[iu];
+      r.alpha = 2.0 * CUDART_PI * (double)ia / (double)P.n_alpha;
+    }
     r.Fs = sol.Fs;
     r.Fb = sol.Bc + P.Fref - sol.Fs;
     r.idx = e.idx;
