@@ -88,17 +88,17 @@ struct GradAcc {
 };
 
 template <bool WITH_H>
-__device__ __forceinline__ void grad_add(GradAcc &a, const float4 &v,
+__device__ __forceinline__ void grad_add(GradAcc &a, float w, float fc,
                                          float Ac, const Deriv &d, float Fs,
                                          float Bc) {
-  const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
-  const float wr = __fmul_rn(v.y, r);
+  const float r = __fsub_rn(fc, __fmaf_rn(Fs, Ac, Bc));
+  const float wr = __fmul_rn(w, r);
   a.chi = __fmaf_rn(wr, r, a.chi);
   const float s = __fmul_rn(-2.f, __fmul_rn(wr, Fs));
 #pragma unroll
   for (int k = 0; k < 4; ++k) a.g[k] = __fmaf_rn(s, d.d[k], a.g[k]);
   if (WITH_H) {
-    const float wf2 = __fmul_rn(v.y, __fmul_rn(Fs, Fs));
+    const float wf2 = __fmul_rn(w, __fmul_rn(Fs, Fs));
     int m = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -137,10 +137,11 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
   const double tEc = (tE > 1e-6) ? tE : 1e-6;  // the host rejects tE <= 0
   double tlo, thi;
   slab_tau(P.L, u0, cs, sn, tlo, thi);
+  const Epochs ep = epochs_at(P.ep, P.n_ep);
   const TrajC c =
-      make_traj(P, P.ep, u0, cs, sn, t0 - t_ref, 1.0 / (tEc * P.dlt), tEc,
+      make_traj(P, ep, u0, cs, sn, t0 - t_ref, 1.0 / (tEc * P.dlt), tEc,
                 tlo, thi);
-  const Acc s1 = phase1<false>(P, P.ep, c, lane);
+  const Acc s1 = phase1<false>(P, ep, c, lane);
   const Solved sol = solve2(P, (double)s1.a, (double)s1.b, (double)s1.d);
   const float fFs = __double2float_rn(sol.Fs);
   const float fBc = __double2float_rn(sol.Bc);
@@ -151,23 +152,22 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
   for (int k = 0; k < 4; ++k) a.g[k] = 0.f;
 #pragma unroll
   for (int k = 0; k < 10; ++k) a.h[k] = 0.f;
-  const float4 *ep = P.ep;
   Deriv d;
   for (int e = lane_start(0, lane); e < c.e_in; e += 32) {
-    const float4 v = ep[e];
+    const float2 v = ep.tw[e];
     const float Ac = out_grad(c, fu0, v.x, d);
-    grad_add<WITH_H>(a, v, Ac, d, fFs, fBc);
+    grad_add<WITH_H>(a, v.y, ep.fc[e], Ac, d, fFs, fBc);
   }
 #pragma unroll 2
   for (int e = lane_start(c.e_in, lane); e < c.e_out; e += 32) {
-    const float4 v = ep[e];
+    const float2 v = ep.tw[e];
     const float Ac = in_grad(P, c, fcs, fsn, fu0, v.x, d);
-    grad_add<WITH_H>(a, v, Ac, d, fFs, fBc);
+    grad_add<WITH_H>(a, v.y, ep.fc[e], Ac, d, fFs, fBc);
   }
   for (int e = lane_start(c.e_out, lane); e < P.n_ep; e += 32) {
-    const float4 v = ep[e];
+    const float2 v = ep.tw[e];
     const float Ac = out_grad(c, fu0, v.x, d);
-    grad_add<WITH_H>(a, v, Ac, d, fFs, fBc);
+    grad_add<WITH_H>(a, v.y, ep.fc[e], Ac, d, fFs, fBc);
   }
   const double x2 = warp_sum_f64(a.chi);
   double gg[4];

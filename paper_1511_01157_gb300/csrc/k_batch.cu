@@ -69,7 +69,7 @@ __device__ __forceinline__ void run_unit(const BatchParams &B,
   Q.tpg = U.tpg;
   Q.ng_line = (Q.line + U.tpg - 1) / U.tpg;
   Q.gthr = B.gthr + U.pair;
-  const float4 *ep = STAGE ? sep : E.ep;
+  const Epochs ep = epochs_at(STAGE ? sep : E.ep, E.n_ep);
   const bool lined = Q.stride == 1 && Q.line > 0;
   for (;;) {
     int gi = 0;

@@ -12,7 +12,7 @@
 // GB300 design.
 //  * One 16-warp block per SM.  The light curve (t, w, wF, F per epoch,
 //    time-sorted) is staged once per block in shared memory.
-//  * Warps take groups of 32 trajectories.  For each, the lanes walk
+//  * Warps take groups of up to 32 trajectories from a block counter.  For each, the lanes walk
 //    consecutive epochs, so the 32 bilinear gathers of a warp fall within a
 //    few texels (one 16-byte float4 load fetches a texel's 2x2
 //    neighbourhood) and the L2-resident map is served mostly from L1.
@@ -63,16 +63,16 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
   const int warp = threadIdx.x >> 5;
   const int K = P.top_k;
 
-  const float4 *ep = P.ep;
+  const float4 *blk = P.ep;
   BlockTopK T;
-  __shared__ int s_cur, s_nk, s_lock;
+  __shared__ int s_cur, s_nk, s_lock, s_next;
   __shared__ double s_thr;
   {
     unsigned char *p = smem;
     if (EP_SMEM) {
       float4 *s = reinterpret_cast<float4 *>(p);
       for (int e = threadIdx.x; e < P.n_ep; e += blockDim.x) s[e] = P.ep[e];
-      ep = s;
+      blk = s;
       p += sizeof(float4) * (size_t)P.n_ep;
     }
     if (!DENSE) {
@@ -89,9 +89,11 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
     s_cur = 0;
     s_nk = 0;
     s_lock = 0;
+    s_next = 0;
     s_thr = CUDART_INF;
   }
   __syncthreads();
+  const Epochs ep = epochs_at(blk, P.n_ep);
 
   // Warp groups.  A strided sample (pilot, stride > 1) is cut into runs of
   // tpg sample indices.  Otherwise groups are aligned to (u0, alpha) lines
@@ -111,8 +113,19 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
   const long long gstride = (long long)gridDim.x * kSearchWarps;
   unsigned long long n_exact = 0;
 
-  for (long long g = (long long)blockIdx.x * kSearchWarps + warp;
-       g < n_groups; g += gstride) {
+  // The block's groups come in rounds of kSearchWarps consecutive groups,
+  // round r starting at blockIdx.x kSearchWarps + r gstride.  Its warps
+  // take them one at a time, in order, from a shared counter: a warp whose
+  // groups were cheap takes more, so the warps finish together, and the
+  // warps of a block still walk neighbouring groups.
+  for (;;) {
+    int k = 0;
+    if (lane == 0) k = atomicAdd(&s_next, 1);
+    k = __shfl_sync(kFull, k, 0);
+    const long long g = (long long)blockIdx.x * kSearchWarps +
+                        (long long)(k / kSearchWarps) * gstride +
+                        k % kSearchWarps;
+    if (g >= n_groups) break;  // g grows with k: every later k is out too
     long long lo, hi;  // absolute indices (lined) or sample indices
     if (lined) {
       const long long L = line0 + g / P.ng_line;

@@ -1592,7 +1592,12 @@ morse_status morse_event_create(morse_ctx *ctx, const double *t,
                    [t](int64_t a, int64_t b) { return t[a] < t[b]; });
   // weights, weighted mean flux, FP32 storage; the FP64 constants are sums
   // of the stored FP32 values so that the device data is self-consistent
+  // device layout: n float4 slots holding the arrays (t - t_ref, w)[n],
+  // w Fc[n] and Fc[n] (structure of arrays, read as such by the sweeps)
   std::vector<float4> h((size_t)n);
+  float2 *h_tw = reinterpret_cast<float2 *>(h.data());
+  float *h_wf = reinterpret_cast<float *>(h_tw + n);
+  float *h_fc = h_wf + n;
   double sw = 0.0, swf = 0.0;
   for (int64_t i = 0; i < n; ++i) {
     double w = 1.0 / (sigma[i] * sigma[i]);
@@ -1614,7 +1619,9 @@ morse_status morse_event_create(morse_ctx *ctx, const double *t,
       return fail(ctx, MORSE_EINVAL,
                   "epoch %lld: weight 1/sigma^2 outside FP32 range",
                   (long long)i);
-    h[(size_t)k] = v;
+    h_tw[k] = make_float2(v.x, v.y);
+    h_wf[k] = v.z;
+    h_fc[k] = v.w;
     // constants of the quadratic the exact sweep evaluates: sum w Fc and
     // sum w Fc^2 with the stored w and Fc
     S1 += (double)v.y;

@@ -68,7 +68,9 @@ struct morse_event {
   morse_ctx *ctx;
   int64_t n;
   double t_ref;
-  float4 *ep;               // [n] (t - t_ref, w, w (F - F_ref), F - F_ref)
+  float4 *ep;               // n float4 slots holding, as arrays,
+                            // (t - t_ref, w)[n], w (F - F_ref)[n],
+                            // (F - F_ref)[n]
   double S1, SF, SFF, Fref; // FP64 sums of the stored FP32 values
   double invS1, CFF;        // 1/S_1, S_FF - S_F^2/S_1
 };

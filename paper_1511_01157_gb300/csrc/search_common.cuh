@@ -33,6 +33,25 @@ struct TrajC {
   int e_in, e_out;       // epochs [e_in, e_out) lie inside the map
 };
 
+// The epochs of one event: a block of n float4 slots (so that it is copied
+// to shared memory in 16-byte pieces) holding, in structure-of-arrays
+// order, tw[n] = (t - t_ref, w), wf[n] = w (F - F_ref) and fc[n] = F - F_ref.
+// A warp reading 32 consecutive epochs of a sweep takes two shared-memory
+// wavefronts for (t, w) and one for w Fc or Fc: three, where one float4
+// per epoch takes four.
+struct Epochs {
+  const float2 *tw;
+  const float *wf, *fc;
+};
+
+__device__ __forceinline__ Epochs epochs_at(const float4 *blk, int n) {
+  Epochs E;
+  E.tw = reinterpret_cast<const float2 *>(blk);
+  E.wf = reinterpret_cast<const float *>(E.tw + n);
+  E.fc = E.wf + n;
+  return E;
+}
+
 __device__ __forceinline__ bool key_less(const Entry &a, const Entry &b) {
   return a.chi2 < b.chi2 || (a.chi2 == b.chi2 && a.idx < b.idx);
 }
@@ -46,13 +65,13 @@ __device__ __forceinline__ bool key_less(double ca, long long ia, double cb,
 // (strict) or upwards: no FP32 value lies strictly between x and that
 // rounding, so t > x <=> t > RD(x) and t >= x <=> t >= RU(x) exactly, and
 // the search needs no FP64 compares.
-__device__ __forceinline__ int epoch_search(const float4 *ep, int n, double x,
+__device__ __forceinline__ int epoch_search(const Epochs &ep, int n, double x,
                                             bool strict) {
   const float xf = strict ? __double2float_rd(x) : __double2float_ru(x);
   int lo = 0, hi = n;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    const float t = ep[mid].x;
+    const float t = ep.tw[mid].x;
     const bool right = strict ? (t > xf) : (t >= xf);
     if (right)
       hi = mid;
@@ -99,7 +118,7 @@ __device__ __forceinline__ void slab_tau(double L, double u, double c,
 // inside the map (|y1| < L and |y2| < L) for tau in (tau_lo, tau_hi), i.e.
 // for the epochs [e_in, e_out).
 __device__ __forceinline__ TrajC make_traj(const SearchParams &P,
-                                           const float4 *ep, double u,
+                                           const Epochs &ep, double u,
                                            double c, double s, double t0,
                                            double k, double tE, double tlo,
                                            double thi) {
@@ -130,7 +149,7 @@ __device__ __forceinline__ TrajC make_traj(const SearchParams &P,
 
 // constants of grid trajectory j from the device tables
 __device__ __forceinline__ TrajC traj_consts(const SearchParams &P,
-                                             const float4 *ep, long long j) {
+                                             const Epochs &ep, long long j) {
   long long r = j;
   const int itE = (int)(r % P.n_tE);
   r /= P.n_tE;
@@ -248,11 +267,11 @@ struct Acc {
   float a, b, d;  // S_A, S_AA, S_AF partial sums of one lane
 };
 
-__device__ __forceinline__ void acc_add(Acc &s, const float4 &v, float Ac) {
-  const float wAc = __fmul_rn(v.y, Ac);
+__device__ __forceinline__ void acc_add(Acc &s, float w, float wf, float Ac) {
+  const float wAc = __fmul_rn(w, Ac);
   s.a = __fadd_rn(s.a, wAc);
   s.b = __fmaf_rn(wAc, Ac, s.b);
-  s.d = __fmaf_rn(v.z, Ac, s.d);
+  s.d = __fmaf_rn(wf, Ac, s.d);
 }
 
 // 10^x for a decoded FP16 log10 texel: one hardware base-2 exponential
@@ -299,27 +318,29 @@ __device__ __forceinline__ float mag_out_m1(const TrajC &c, float t) {
 }
 
 template <bool H, bool IN>
-__device__ __forceinline__ void seg1(const SearchParams &P, const float4 *ep,
+__device__ __forceinline__ void seg1(const SearchParams &P, const Epochs &ep,
                                      const TrajC &c, int lane, int e0, int e1,
                                      Acc &s) {
 #pragma unroll (IN ? kUnroll : 2)
   for (int e = lane_start(e0, lane); e < e1; e += 32) {
-    const float4 v = ep[e];
-    acc_add(s, v, IN ? mag_in_m1<H>(P, c, v.x) : mag_out_m1(c, v.x));
+    const float2 v = ep.tw[e];
+    const float wf = ep.wf[e];
+    acc_add(s, v.y, wf, IN ? mag_in_m1<H>(P, c, v.x) : mag_out_m1(c, v.x));
   }
 }
 
 // two trajectories over one epoch segment, one epoch load for both
 template <bool H, bool INA, bool INB>
-__device__ __forceinline__ void seg2(const SearchParams &P, const float4 *ep,
+__device__ __forceinline__ void seg2(const SearchParams &P, const Epochs &ep,
                                      const TrajC &ca, const TrajC &cb,
                                      int lane, int e0, int e1, Acc &sa,
                                      Acc &sb) {
 #pragma unroll ((INA || INB) ? kUnroll : 2)
   for (int e = lane_start(e0, lane); e < e1; e += 32) {
-    const float4 v = ep[e];
-    acc_add(sa, v, INA ? mag_in_m1<H>(P, ca, v.x) : mag_out_m1(ca, v.x));
-    acc_add(sb, v, INB ? mag_in_m1<H>(P, cb, v.x) : mag_out_m1(cb, v.x));
+    const float2 v = ep.tw[e];
+    const float wf = ep.wf[e];
+    acc_add(sa, v.y, wf, INA ? mag_in_m1<H>(P, ca, v.x) : mag_out_m1(ca, v.x));
+    acc_add(sb, v.y, wf, INB ? mag_in_m1<H>(P, cb, v.x) : mag_out_m1(cb, v.x));
   }
 }
 
@@ -342,7 +363,7 @@ __device__ __forceinline__ Acc acc_reduce(Acc s) {
 // S_AF = sum w (F-Fref)(A-1) over the epochs before, inside and after the
 // map, reduced across the warp.
 template <bool H>
-__device__ __forceinline__ Acc phase1(const SearchParams &P, const float4 *ep,
+__device__ __forceinline__ Acc phase1(const SearchParams &P, const Epochs &ep,
                                       const TrajC &c, const int lane) {
   Acc s = {0.f, 0.f, 0.f};
   seg1<H, false>(P, ep, c, lane, 0, c.e_in, s);
@@ -356,7 +377,7 @@ __device__ __forceinline__ Acc phase1(const SearchParams &P, const float4 *ep,
 // inside/outside combination with one epoch load per lane for both.
 template <bool H>
 __device__ __forceinline__ void phase1_pair(const SearchParams &P,
-                                            const float4 *ep, const TrajC &ca,
+                                            const Epochs &ep, const TrajC &ca,
                                             const TrajC &cb, const int lane,
                                             Acc &ra, Acc &rb) {
   Acc sa = {0.f, 0.f, 0.f}, sb = {0.f, 0.f, 0.f};
@@ -392,29 +413,29 @@ __device__ __forceinline__ void phase1_pair(const SearchParams &P,
 // lanes; lane 0's value is returned to all lanes.
 template <bool H>
 __device__ __forceinline__ double phase2(const SearchParams &P,
-                                         const float4 *ep, const TrajC &c,
+                                         const Epochs &ep, const TrajC &c,
                                          const int lane, const float Fs,
                                          const float Bc) {
   float chi = 0.f;
 #pragma unroll 2
   for (int e = lane_start(0, lane); e < c.e_in; e += 32) {
-    const float4 v = ep[e];
+    const float2 v = ep.tw[e];
     const float Ac = mag_out_m1(c, v.x);
-    const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
+    const float r = __fsub_rn(ep.fc[e], __fmaf_rn(Fs, Ac, Bc));
     chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
   }
 #pragma unroll (kUnroll)
   for (int e = lane_start(c.e_in, lane); e < c.e_out; e += 32) {
-    const float4 v = ep[e];
+    const float2 v = ep.tw[e];
     const float Ac = mag_in_m1<H>(P, c, v.x);
-    const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
+    const float r = __fsub_rn(ep.fc[e], __fmaf_rn(Fs, Ac, Bc));
     chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
   }
 #pragma unroll 2
   for (int e = lane_start(c.e_out, lane); e < P.n_ep; e += 32) {
-    const float4 v = ep[e];
+    const float2 v = ep.tw[e];
     const float Ac = mag_out_m1(c, v.x);
-    const float r = __fsub_rn(v.w, __fmaf_rn(Fs, Ac, Bc));
+    const float r = __fsub_rn(ep.fc[e], __fmaf_rn(Fs, Ac, Bc));
     chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
   }
   double x = (double)chi;

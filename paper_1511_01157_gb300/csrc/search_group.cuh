@@ -121,7 +121,7 @@ __device__ inline void warp_merge(const SearchParams &P, BlockTopK &T, const int
 // then the dense store or the merge into the block's top-K.
 template <bool DENSE, bool H>
 __device__ __forceinline__ void search_group(const SearchParams &P,
-                                             const float4 *ep, BlockTopK &T,
+                                             const Epochs &ep, BlockTopK &T,
                                              const int K, const int warp,
                                              const int lane, long long lo,
                                              long long hi, const bool lined,
@@ -200,7 +200,7 @@ __device__ __forceinline__ void search_group(const SearchParams &P,
 
 // Record of one selected trajectory e (warp-collective; lane 0 writes *dst):
 // the phase-1 sums, the solve and the phase-2 chi^2 recomputed with the
-// search's device functions, on the epochs at P.ep.
+// search's device functions, on the epochs at P.ep (global memory).
 template <bool H>
 __device__ __forceinline__ void fill_one(const SearchParams &P, const Entry e,
                                          const double *t0abs,
@@ -219,10 +219,11 @@ __device__ __forceinline__ void fill_one(const SearchParams &P, const Entry e,
     }
     return;
   }
-  const TrajC c = traj_consts(P, P.ep, e.idx);
-  const Acc s = phase1<H>(P, P.ep, c, lane);
+  const Epochs ep = epochs_at(P.ep, P.n_ep);
+  const TrajC c = traj_consts(P, ep, e.idx);
+  const Acc s = phase1<H>(P, ep, c, lane);
   const Solved sol = solve2(P, (double)s.a, (double)s.b, (double)s.d);
-  const double chi2 = phase2<H>(P, P.ep, c, lane, __double2float_rn(sol.Fs),
+  const double chi2 = phase2<H>(P, ep, c, lane, __double2float_rn(sol.Fs),
                                 __double2float_rn(sol.Bc));
   if (lane == 0) {
     long long q = e.idx;
