@@ -24,6 +24,10 @@ names the passage of McDougall & Albrow (2015) it follows:
 * ``pspl``            -- §4.3 (ii) Paczynski single-lens curve
 * ``traj_point``/``map_A`` -- §4.2 straight trajectory, bilinear map lookup
 * ``line_max``        -- §4.3 (i) largest magnification along a line
+* ``line_peaks``      -- §4.3 (iii) peak library: peaks of the map along a
+  line (count, positions, heights)
+* ``peak_lines``      -- §4.3 (iv)-(v) Eq. 7-8: the trajectories aligned
+  with one or two given peak times
 * ``fit_A``           -- §4.1 Eq. 5-6 linear flux fit, chi^2 as a sum of
   per-point contributions (§4.2)
 * ``grid_chi2``/``topk`` -- brute-force grid and the K best seeds (§4.4)
@@ -88,6 +92,8 @@ def _load():
         "orc_half_bits": (ctypes.c_uint16, [_D]),
         "orc_fs_weights": (None, [_D, _D, _I, _I, _P]),
         "orc_line_max": (_D, [_P, _I, _D, _D, _D]),
+        "orc_line_peaks": (_I, [_P, _I, _D, _D, _D, _D, _D, _I, _D, _I, _P,
+                                _P]),
         "orc_fs_convolve": (None, [_P, _I, _D, _P, _I, _P, _I]),
         "orc_half_value": (_D, [ctypes.c_uint16]),
         "orc_log10_half": (None, [_P, ctypes.c_longlong, _D, _P]),
@@ -324,6 +330,74 @@ def line_max(A, L, u0, alpha):
     A = np.ascontiguousarray(A, dtype=np.float32)
     return _load().orc_line_max(_ptr(A), A.shape[0], float(L), float(u0),
                                 float(alpha))
+
+
+def line_peaks(A, L, lines, sub=2, delta=0.0, max_peaks=8):
+    """§4.3 (iii): the peak library of the map A along lines[j] = (u,
+    alpha, shift) (shift: the line's reference point lies tau = shift past
+    its closest approach to the origin).  Returns (count[n] int32,
+    pos[n, max_peaks], height[n, max_peaks]); pos in Einstein radii from the
+    reference point, the max_peaks highest peaks in increasing tau, NaN in
+    unused slots."""
+    lib = _load()
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    lines = np.asarray(lines, dtype=np.float64).reshape(-1, 3)
+    n = len(lines)
+    count = np.zeros(n, dtype=np.int32)
+    pos = np.zeros((n, max_peaks))
+    height = np.zeros((n, max_peaks))
+    pb = np.zeros(max_peaks)
+    hb = np.zeros(max_peaks)
+    for j, (u, al, sh) in enumerate(lines):
+        count[j] = lib.orc_line_peaks(_ptr(A), A.shape[0], L, float(u),
+                                      math.cos(al), math.sin(al), float(sh),
+                                      sub, delta, max_peaks, _ptr(pb),
+                                      _ptr(hb))
+        pos[j] = pb
+        height[j] = hb
+    return count, pos, height
+
+
+def peak_lines(lines, count, pos, tp, min_peaks=0):
+    """§4.3 (iv)-(v): the trajectory families aligned with the given peak
+    times, as line-grid entries.
+
+    Entry slots per line: 1 (no peak time: the line itself), max_peaks (one
+    time t_p: the line's m-th kept peak at t_p, Eq. 7 t0 = t_p - M_p tE) or
+    max_peaks (max_peaks - 1) / 2 (two times t_p1 < t_p2: its peaks a < b
+    at them, Eq. 8 tE = (t_p2 - t_p1) / (M_b - M_a), then Eq. 7 with peak
+    a).  A slot is used when the line has at least max(min_peaks, len(tp))
+    peaks and the slot's peaks are among its kept ones.
+    Returns rows (u, alpha, shift, tE, used) per slot, line-major: the
+    trajectory with grid t0 value t0_g (the t0 axis then runs about t_p1)
+    is (u, alpha, t0_g - shift tE, tE); tE is NaN where the tE axis
+    applies (fewer than two peak times)."""
+    lines = np.asarray(lines, dtype=np.float64).reshape(-1, 3)
+    P = pos.shape[1]
+    ntp = len(tp)
+    need = max(min_peaks, ntp)
+    out = []
+    for j, (u, al, sh) in enumerate(lines):
+        kept = int(min(count[j], P))
+        ok = count[j] >= need
+        if ntp == 0:
+            out.append((u, al, sh, math.nan, 1.0 if ok else 0.0))
+        elif ntp == 1:
+            for m in range(P):
+                used = ok and m < kept
+                M = pos[j, m] + sh if used else 0.0
+                out.append((u, al, M, math.nan, 1.0 if used else 0.0))
+        else:
+            for a in range(P):
+                for b in range(a + 1, P):
+                    used = ok and b < kept
+                    if used:
+                        M = pos[j, a] + sh
+                        tE = (tp[1] - tp[0]) / (pos[j, b] - pos[j, a])
+                    else:
+                        M, tE = 0.0, 1.0
+                    out.append((u, al, M, tE, 1.0 if used else 0.0))
+    return np.array(out).reshape(-1, 5)
 
 
 def lightcurve_map(A, L, t, t0, tE, u0, alpha):

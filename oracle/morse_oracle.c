@@ -27,6 +27,8 @@
  *   flux model + fit ...... §4.1 Eq. 5-6 (F = Fs A + Fb, linear in A), chi^2
  *                          as the sum of per-data-point contributions (§4.2)
  *   seeds (top-K) ......... §4.4 (best local minima of the coarse search)
+ *   peak library .......... §4.3 (iii) (peaks along a line: the
+ *                          magnification turning from rising to falling)
  *   FP16 log10 map ........ storage form of the map values: log10 A rounded
  *                          to IEEE binary16 (round to nearest, ties to
  *                          even), decoded as 10^x
@@ -729,6 +731,127 @@ double orc_line_max(const float *A, int npix, double L, double u,
   }
   free(tb);
   return best;
+}
+
+/* ------------------------------------------------------------------ */
+/* Peak library along a line (§4.3 (iii)-(v))                           */
+/* ------------------------------------------------------------------ */
+
+/* Peaks of the map along the line of impact u and direction (c, s) =
+ * (cos alpha, sin alpha) about the origin, positions measured from the
+ * line's reference point, which lies tau = shift past the closest approach
+ * to the origin.
+ *
+ * A peak is where the magnification turns from rising to falling (§4.3
+ * (iii)).  The profile it is read from (the paper does not say how the
+ * library samples a line):
+ *   - samples at tau_k = k h, h = Delta / sub, k = -sub npix .. sub npix;
+ *   - the sample's texel coordinates p = a tau_k + b (the line's constants
+ *     a, b taken in FP64, then everything in FP32), and the sample is kept
+ *     if it lies inside the map, -1/2 < p < npix - 1/2 on both axes;
+ *   - its value is the bilinear lookup between texel centres, coordinates
+ *     clamped to the outermost centres, in FP32.
+ * FP32 decides the count, so both implementations take it in FP32 with
+ * the same operations.
+ * Peaks are counted with a relative threshold r = 1 + delta: a rise is
+ * confirmed when a value exceeds r times the lowest value since the last
+ * peak, and the highest value after it is a peak once a later value lies
+ * below it by the factor r (delta = 0: every turn from rising to falling,
+ * a plateau counting once).  The profile must rise before its first peak:
+ * its first sample is never one.
+ *
+ * Returns the number of peaks.  pos / height receive the max_peaks highest
+ * (ties: the earlier one), in increasing tau, as (k h - shift, value);
+ * unused slots are NaN. */
+int orc_line_peaks(const float *A, int npix, double L, double u, double c,
+                   double s, double shift, int sub, double delta,
+                   int max_peaks, double *pos, double *height) {
+  double dlt = (2.0 * L) / (double)npix;
+  double h = dlt / (double)sub;
+  double ax = c / dlt, ay = s / dlt;
+  double bx = (L - u * s) / dlt - 0.5;
+  double by = (L + u * c) / dlt - 0.5;
+  float axf = (float)ax, ayf = (float)ay, bxf = (float)bx, byf = (float)by;
+  float hf = (float)h, r = (float)(1.0 + delta);
+  float lo = -0.5f, hi = (float)npix - 0.5f, pmax = (float)(npix - 1);
+  int K = sub * npix;
+  /* the kept peaks, highest first */
+  float *kh = (float *)malloc((size_t)(max_peaks > 0 ? max_peaks : 1) *
+                              sizeof(float));
+  int *kk = (int *)malloc((size_t)(max_peaks > 0 ? max_peaks : 1) *
+                          sizeof(int));
+  int nkept = 0, count = 0, look_max = 0, kmx = 0;
+  float mn = INFINITY, mx = -INFINITY;
+  for (int k = -K; k <= K; ++k) {
+    float tk = (float)k * hf;
+    float px = axf * tk + bxf;
+    float py = ayf * tk + byf;
+    if (!(px > lo && px < hi && py > lo && py < hi)) continue;
+    float qx = px < 0.0f ? 0.0f : px;
+    float qy = py < 0.0f ? 0.0f : py;
+    if (qx > pmax) qx = pmax;
+    if (qy > pmax) qy = pmax;
+    int i0 = (int)floorf(qx), j0 = (int)floorf(qy);
+    if (i0 > npix - 2) i0 = npix - 2;
+    if (j0 > npix - 2) j0 = npix - 2;
+    float fx = qx - (float)i0, fy = qy - (float)j0;
+    float a00 = A[(size_t)j0 * npix + i0], a10 = A[(size_t)j0 * npix + i0 + 1];
+    float a01 = A[(size_t)(j0 + 1) * npix + i0];
+    float a11 = A[(size_t)(j0 + 1) * npix + i0 + 1];
+    float gx = 1.0f - fx, gy = 1.0f - fy;
+    float r0 = gx * a00 + fx * a10;
+    float r1 = gx * a01 + fx * a11;
+    float v = gy * r0 + fy * r1;
+    if (look_max) {
+      if (v > mx) {
+        mx = v;
+        kmx = k;
+      } else if (mx > r * v) {
+        /* a peak: keep it if it is among the max_peaks highest */
+        ++count;
+        int at = nkept;
+        while (at > 0 && mx > kh[at - 1]) --at;
+        if (at < max_peaks) {
+          int last = nkept < max_peaks ? nkept : max_peaks - 1;
+          for (int m = last; m > at; --m) {
+            kh[m] = kh[m - 1];
+            kk[m] = kk[m - 1];
+          }
+          kh[at] = mx;
+          kk[at] = kmx;
+          if (nkept < max_peaks) ++nkept;
+        }
+        look_max = 0;
+        mn = v;
+      }
+    } else {
+      if (v < mn) {
+        mn = v;
+      } else if (v > r * mn) {
+        look_max = 1;
+        mx = v;
+        kmx = k;
+      }
+    }
+  }
+  /* kept peaks in increasing tau */
+  for (int a = 1; a < nkept; ++a)
+    for (int b = a; b > 0 && kk[b] < kk[b - 1]; --b) {
+      int ti = kk[b]; kk[b] = kk[b - 1]; kk[b - 1] = ti;
+      float tf = kh[b]; kh[b] = kh[b - 1]; kh[b - 1] = tf;
+    }
+  for (int m = 0; m < max_peaks; ++m) {
+    if (m < nkept) {
+      pos[m] = (double)kk[m] * h - shift;
+      height[m] = (double)kh[m];
+    } else {
+      pos[m] = NAN;
+      height[m] = NAN;
+    }
+  }
+  free(kh);
+  free(kk);
+  return count;
 }
 
 /* Given magnifications A[i] at the epochs, the weighted least-squares

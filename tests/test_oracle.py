@@ -603,6 +603,140 @@ def test_line_max_plane_bump_and_outside():
                                                          rel=1e-14)
 
 
+# ------------------------------------------------------------ peak library
+def _interior_maxima(v):
+    """Brute force: indices i (0 < i < n - 1) with v[i] above both
+    neighbours, for values with no two neighbours equal."""
+    return [i for i in range(1, len(v) - 1) if v[i] > v[i - 1] and v[i] > v[i + 1]]
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_line_peaks_profile_maxima_brute_force(axis):
+    # A map constant across the line: along a horizontal (vertical) line the
+    # profile interpolates the column (row) values, sampled at every texel
+    # centre and midpoint (sub = 2), so with delta = 0 its peaks are the
+    # interior strict maxima of those values, at the centres' tau.
+    L, npix = 2.0, 96
+    rng = np.random.default_rng(11 + axis)
+    col = rng.permutation(np.linspace(1.0, 9.0, npix)).astype(np.float32)
+    A = np.tile(col, (npix, 1)) if axis == 0 else np.tile(col[:, None], (1, npix))
+    A = np.ascontiguousarray(A)
+    al = 0.0 if axis == 0 else math.pi / 2
+    d = 2 * L / npix
+    idx = _interior_maxima(col)
+    count, pos, height = orc.line_peaks(A, L, [(0.3, al, 0.0)], sub=2,
+                                        max_peaks=npix)
+    assert count[0] == len(idx)
+    got = pos[0][~np.isnan(pos[0])]
+    want = np.array([-L + (i + 0.5) * d for i in idx])
+    assert np.allclose(got, want, rtol=0, atol=1e-12)
+    assert np.allclose(height[0][: len(idx)], col[idx], rtol=1e-4)
+    # the three highest, in increasing tau; a shift moves every position
+    top = sorted(sorted(idx, key=lambda i: -col[i])[:3])
+    count, pos, height = orc.line_peaks(A, L, [(0.3, al, 0.25)], sub=2,
+                                        max_peaks=3)
+    assert count[0] == len(idx)
+    assert np.allclose(pos[0], [-L + (i + 0.5) * d - 0.25 for i in top],
+                       atol=1e-12)
+    # the reversed direction sees the same peaks at -tau
+    count, pos, _ = orc.line_peaks(A, L, [(-0.3, al + math.pi, 0.0)], sub=2,
+                                   max_peaks=npix)
+    assert count[0] == len(idx)
+    assert np.allclose(np.sort(pos[0][~np.isnan(pos[0])]), np.sort(-want),
+                       atol=1e-6)
+
+
+def _bumps(L, npix, centres, heights, sigma):
+    d = 2 * L / npix
+    c = -L + (np.arange(npix) + 0.5) * d
+    Y1, Y2 = np.meshgrid(c, c)  # Y1 varies along a row (first coordinate)
+    A = np.ones((npix, npix))
+    for (x, y), h in zip(centres, heights):
+        A += h * np.exp(-((Y1 - x) ** 2 + (Y2 - y) ** 2) / (2 * sigma ** 2))
+    return A.astype(np.float32)
+
+
+def test_line_peaks_bumps_positions_heights_and_threshold():
+    L, npix = 2.0, 256
+    h = 2 * L / npix / 2
+    # one round bump at the origin: every line through the map has one peak,
+    # at its closest approach to the origin (tau = 0)
+    A = _bumps(L, npix, [(0.0, 0.0)], [5.0], 0.3)
+    lines = [(u, al, sh) for u in (-0.7, 0.0, 0.45) for al in (0.0, 0.9, 2.5)
+             for sh in (0.0, 0.3)]
+    count, pos, height = orc.line_peaks(A, L, lines, max_peaks=2)
+    for j, (u, al, sh) in enumerate(lines):
+        assert count[j] == 1
+        assert abs(pos[j, 0] + sh) <= h
+        assert height[j, 0] == pytest.approx(1 + 5 * math.exp(-u * u / 0.18),
+                                             rel=2e-3)
+        assert np.isnan(pos[j, 1])
+    # a line that misses the map has no peak
+    count, pos, _ = orc.line_peaks(A, L, [(3.0, 0.4, 0.0)])
+    assert count[0] == 0 and np.isnan(pos[0]).all()
+    # three bumps on the line y2 = 0.2 (alpha = 0: tau = y1)
+    A = _bumps(L, npix, [(-1.0, 0.2), (0.0, 0.2), (0.8, 0.2)],
+               [3.0, 6.0, 4.0], 0.12)
+    count, pos, height = orc.line_peaks(A, L, [(0.2, 0.0, 0.0)], max_peaks=8)
+    assert count[0] == 3
+    assert np.allclose(pos[0, :3], [-1.0, 0.0, 0.8], atol=h)
+    assert np.allclose(height[0, :3], [4.0, 7.0, 5.0], rtol=5e-3)
+    # the two highest, in increasing tau
+    count, pos, _ = orc.line_peaks(A, L, [(0.2, 0.0, 0.0)], max_peaks=2)
+    assert np.allclose(pos[0], [0.0, 0.8], atol=h)
+    # threshold: two close bumps with a shallow dip count once when the dip
+    # is within the factor 1 + delta, twice with delta = 0
+    A = _bumps(L, npix, [(-0.15, 0.0), (0.15, 0.0)], [5.0, 4.8], 0.1)
+    prof = [orc.map_A(A, L, t, 0.0) for t in np.linspace(-0.3, 0.3, 601)]
+    dip = min(prof[150:451])
+    assert 1.3 < max(prof) / dip < 1.6  # the dip lies within the factor 1.6
+    assert orc.line_peaks(A, L, [(0.0, 0.0, 0.0)], delta=0.0)[0][0] == 2
+    assert orc.line_peaks(A, L, [(0.0, 0.0, 0.0)], delta=0.3)[0][0] == 2
+    c1, p1, h1 = orc.line_peaks(A, L, [(0.0, 0.0, 0.0)], delta=0.6)
+    assert c1[0] == 1
+    assert abs(p1[0, 0] + 0.15) <= 2 * h and h1[0, 0] > 5.5
+
+
+def test_peak_alignment_eq7_eq8_puts_model_peaks_at_the_given_times():
+    # Eq. 7: the trajectory t0 = t_p - M_p tE peaks at t_p; Eq. 8: with two
+    # peaks, tE = (t_p2 - t_p1)/(M_b - M_a) puts them at t_p1 and t_p2.
+    L, npix = 2.0, 256
+    # (bump centres off the midpoints between texel centres, so that each
+    # top is one texel centre, not a flat stretch between two)
+    A = _bumps(L, npix, [(-0.905, 0.2), (0.53, 0.2)], [4.0, 6.0], 0.1)
+    line = [(0.2, 0.0, 0.1)]
+    count, pos, _ = orc.line_peaks(A, L, line, max_peaks=4)
+    assert count[0] == 2
+    t = np.linspace(50.0, 200.0, 30001)
+
+    def peaks_of(row):
+        u, al, M, tE = row[:4]
+        t0 = tp0 - M * tE
+        lc = np.array(orc.lightcurve_map(A, L, t, t0, tE, u, al))
+        # maxima of the sampled light curve (a top may be two equal samples)
+        return [t[i] for i in range(1, len(lc) - 1)
+                if lc[i] >= lc[i - 1] and lc[i] > lc[i + 1] and lc[i] > 2.0]
+
+    tp0 = 120.0
+    rows = orc.peak_lines(line, count, pos, [tp0])
+    assert rows.shape == (4, 5) and list(rows[:, 4]) == [1, 1, 0, 0]
+    for m in range(2):
+        r = rows[m].copy()
+        r[3] = 25.0  # a tE from the grid axis
+        pk = peaks_of(r)
+        assert min(abs(p - tp0) for p in pk) < 0.2 * 25.0 * 2 * L / npix
+    rows = orc.peak_lines(line, count, pos, [tp0, 160.0], min_peaks=2)
+    assert rows.shape == (6, 5) and rows[0, 4] == 1 and rows[1:, 4].sum() == 0
+    r = rows[0]
+    assert r[3] == pytest.approx(40.0 / 1.435, rel=2e-2)
+    pk = peaks_of(r)
+    assert len(pk) == 2
+    assert abs(pk[0] - 120.0) < 0.2 and abs(pk[1] - 160.0) < 0.2
+    # a line with fewer peaks than required contributes no trajectory
+    rows = orc.peak_lines(line, count, pos, [tp0], min_peaks=3)
+    assert rows[:, 4].sum() == 0
+
+
 # ------------------------------------------------------------ caustics
 def test_critical_points_and_caustic_count_by_topology():
     from oracle import caustics as oc
