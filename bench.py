@@ -363,14 +363,15 @@ def finite_source_maps(ctx, m, cfg, gamma=0.53):
                    f"{cfg['q']})", "gamma": gamma, "radii": rows}
 
 
-def time_to_best_fit(ctx, m, cfg, ev, S, Q, plain_s, plain_fits, ev_flux,
-                     ev_sigma):
+def time_to_best_fit(ctx, m, cfg, ev, S, Q, plain_s, plain_fits, ev_t,
+                     ev_flux, ev_sigma):
     """Wall time of each form of the (s, q) search and its best chi^2; a
     form reaches the best fit when its chi^2 is within 1e-3 of the lowest
     chi^2 any form found.  Forms: the plain FP32 grid (timed above), the
     same grid on FP16 log10 tables, the plain grid followed by adjoint
     (Levenberg-Marquardt) refinement of its best seeds, a coarse screen of
-    the maps, the grid under the minimum-magnification cut, and grids 3.8x
+    the maps, the grid under the minimum-magnification cut, trajectories
+    aligned with the light curve's peak by the peak library, and grids 3.8x
     and 15x coarser, each followed by the same refinement."""
     import torch
     g = cfg["grid"]
@@ -436,6 +437,40 @@ def time_to_best_fit(ctx, m, cfg, ev, S, Q, plain_s, plain_fits, ev_flux,
         f"magnification is below {a_min:.2f} (peak over baseline flux; "
         f"{100 * np.mean(shares):.1f}% of the lines on 8 sample maps), then "
         "the same refinement")
+    # §4.3 (iii)-(iv): the peak time read off the light curve (the largest
+    # running median of 7 epochs), and on every (u0, alpha) line of the grid
+    # the trajectories whose two highest peaks come at it (Eq. 7), 3 t0
+    # offsets within +-0.05 d and the grid's 20 tE
+    order = np.argsort(np.asarray(ev_t))
+    tt, ff = np.asarray(ev_t)[order], Fs_[order]
+    med = np.array([np.median(ff[max(0, i - 3): i + 4])
+                    for i in range(len(tt))])
+    t_peak = float(tt[np.argmax(med)])
+    u0v = np.exp(np.linspace(np.log(g["u0_lo"]), np.log(g["u0_hi"]),
+                             g["n_u0"]))
+    lines = np.array([(u, 2 * np.pi * k / g["n_alpha"], 0.0) for u in u0v
+                      for k in range(g["n_alpha"])])
+    pgrid = m.Grid.make(2 * len(lines), 1, 3, g["n_tE"], 1.0, 1.0, -0.05,
+                        0.05, g["tE_lo"], g["tE_hi"], False, g["tE_log"], 16)
+
+    def aligned():
+        fits = []
+        for j in range(len(S)):
+            mp = ctx.build_map(S[j], Q[j], cfg["L"], cfg["npix"], cfg["nray"],
+                               image_halfwidth=cfg["X"], deflect="fp32")
+            fits.append(ctx.peak_search(ev, mp, pgrid, lines, tp=[t_peak],
+                                        min_peaks=1, sub=2, max_peaks=2,
+                                        delta=0.1))
+            mp.free()
+        return refine_best(ctx, m, cfg, ev, S, Q, np.stack(fits))
+    b, t = timed(aligned)
+    forms["peak_aligned_plus_refine"] = (
+        t, b, f"peak time {t_peak:.3f} d from the light curve; on each of "
+        f"the 2880 (u0, alpha) lines the trajectories whose two highest "
+        f"map peaks (threshold 10%) come at it (Eq. 7), 3 t0 offsets x 20 "
+        f"tE ({pgrid.size} trajectories per map, "
+        f"{pgrid.size / grid_of(m, cfg).size:.0%} of the grid), then the "
+        f"same refinement")
     for name, dims in (("half_grid_plus_refine", (40, 72, 13, 10)),
                        ("coarse_grid_plus_refine", (20, 36, 13, 10))):
         grid = m.Grid.make(*dims, g["u0_lo"], g["u0_hi"], g["t0_lo"],
@@ -726,7 +761,7 @@ def run_gpu(args, cfg):
     }
     if rank == 0 and not args.no_extras:
         line["time_to_best_fit"] = time_to_best_fit(
-            ctx, m, cfg, ev, S, Q, elapsed / args.steps, fits, F, sig)
+            ctx, m, cfg, ev, S, Q, elapsed / args.steps, fits, t, F, sig)
         line["map_generators"] = map_generators(ctx, m, cfg)
         line["finite_source"] = finite_source_maps(ctx, m, cfg)
         line["batched"] = run_batched(ctx, m, args.batch_events,

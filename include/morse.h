@@ -310,6 +310,56 @@ morse_status morse_grid_chi2_lines(morse_ctx *ctx, const morse_event *ev,
                                    const morse_grid *grid,
                                    const double *lines, morse_fit *out);
 
+/* Peak library (§4.3 (iii)): the peaks of the map along each line, a peak
+ * being where the magnification turns from rising to falling.
+ * lines[3 j .. 3 j + 2] = (u, alpha, shift) as in morse_grid_chi2_lines
+ * (a (u0, alpha) grid line has shift 0).  The profile: samples every
+ * h = Delta / sub along the part of the line inside the map, tau_k = k h
+ * from the closest approach to the origin, each the bilinear lookup
+ * between texel centres (clamped to the outermost centres) in FP32.  With
+ * r = 1 + delta, a rise counts once a value exceeds r times the lowest
+ * value since the last peak, and the highest value after it is a peak once
+ * a later value is below it by the factor r (delta = 0: every turn; on a
+ * ray-shot map that includes the Poisson noise, which delta > 0 ignores).
+ * The profile's first sample is never a peak.
+ * Outputs (host): count[j] = the number of peaks; pos[j max_peaks + m] and
+ * height[...] = the max_peaks highest peaks (ties: the earlier) in
+ * increasing tau, as (tau_k - shift, value); NaN in unused slots.
+ * Errors: EINVAL (sub outside 1..16, max_peaks outside 1..16, delta < 0,
+ * non-finite lines), ENOMEM, ECUDA. */
+typedef struct {
+  int sub;        /* samples per texel width along the line (2)           */
+  int max_peaks;  /* peaks kept per line, the highest (8)                  */
+  double delta;   /* relative threshold of a rise or fall, >= 0           */
+} morse_peak_opts;
+morse_status morse_line_peaks(morse_ctx *ctx, const morse_map *map,
+                              const double *lines, int n_lines,
+                              const morse_peak_opts *opts, int32_t *count,
+                              double *pos, double *height);
+
+/* Search of the trajectories the peak library allows (§4.3 (iii)-(v)).
+ * Lines with fewer than max(min_peaks, n_tp) peaks are not searched.
+ *  n_tp = 0: the line grid of morse_grid_chi2_lines over lines[n_lines];
+ *  n_tp = 1: for each kept peak m of each line (tau_m from the origin's
+ *    closest approach), the trajectories whose peak m comes at t_p + dt0:
+ *    t0 = t_p + dt0 - tau_m tE (Eq. 7), dt0 on the grid's t0 axis (an
+ *    offset: n_t0 = 1, t0_lo = 0 gives Eq. 7 itself), tE on its tE axis;
+ *  n_tp = 2 (t_p1 < t_p2): for each pair of kept peaks a < b, tE =
+ *    (t_p2 - t_p1) / (tau_b - tau_a) (Eq. 8) and peak a at t_p1 + dt0; the
+ *    grid must have n_tE = 1 (its tE values are not used).
+ * Index of a trajectory: ((j S + slot) n_t0 + i_t0) n_tE + i_tE, S = 1,
+ * max_peaks or max_peaks (max_peaks - 1) / 2 slots per line (slot m, or
+ * the pairs (a, b) in the order (0,1), (0,2) .. (1,2) ..); slots a line
+ * does not use are skipped like cut lines.  grid: n_alpha = 1, the t0 and
+ * tE axes and top_k are used (n_u0, the u0 range and a_min are not).
+ * Records (top_k, host) are in the (u0, alpha, t0, tE) convention.
+ * Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
+morse_status morse_peak_search(morse_ctx *ctx, const morse_event *ev,
+                               const morse_map *map, const morse_grid *grid,
+                               const double *lines, int n_lines,
+                               const morse_peak_opts *opts, int min_peaks,
+                               const double *tp, int n_tp, morse_fit *out);
+
 /* morse_grid_chi2 without any device allocation.  The paper has no
  * counterpart: this is a deployment variant of the same search.
  *

@@ -101,6 +101,12 @@ class Caustic(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class PeakOpts(ctypes.Structure):
+    """morse_peak_opts: samples per texel, peaks kept per line, threshold."""
+    _fields_ = [("sub", ctypes.c_int), ("max_peaks", ctypes.c_int),
+                ("delta", ctypes.c_double)]
+
+
 def rphi_lines(caustics, n_r, r_lo, r_hi, n_phi) -> np.ndarray:
     """Lines (u, alpha, shift) of an (r, phi) grid about the caustics
     (morse_rphi_lines): [n_caustics * n_r * n_phi, 3]."""
@@ -155,6 +161,8 @@ _SIGS = {
     "morse_caustics": (_S, [_P, _D, _D, _I, _P, _P]),
     "morse_rphi_lines": (_S, [_P, _I, _I, _D, _D, _I, _P]),
     "morse_grid_chi2_lines": (_S, [_P, _P, _P, _P, _P, _P]),
+    "morse_line_peaks": (_S, [_P, _P, _P, _I, _P, _P, _P, _P]),
+    "morse_peak_search": (_S, [_P, _P, _P, _P, _P, _I, _P, _I, _P, _I, _P]),
     "morse_grid_chi2_batch": (_S, [_P, _P, _I, _P, _I, _P, _P]),
     "morse_measure_peaks": (_S, [_P, _P]),
     "morse_batch_tuning": (_S, [_P, _I]),
@@ -328,6 +336,39 @@ class Context:
                                         ctypes.byref(grid), _ptr(lines),
                                         _ptr(out))
         self._check(st, "morse_grid_chi2_lines")
+        return out
+
+    def line_peaks(self, map_, lines, sub=2, max_peaks=8, delta=0.0):
+        """Peak library of the map along lines (u, alpha, shift)
+        (morse_line_peaks): (count[n], pos[n, max_peaks],
+        height[n, max_peaks])."""
+        lines = np.ascontiguousarray(lines, dtype=np.float64).reshape(-1, 3)
+        n = len(lines)
+        count = np.zeros(n, dtype=np.int32)
+        pos = np.zeros((n, max_peaks))
+        height = np.zeros((n, max_peaks))
+        o = PeakOpts(int(sub), int(max_peaks), float(delta))
+        self._check(_lib.morse_line_peaks(self._h, map_._h, _ptr(lines), n,
+                                          ctypes.byref(o), _ptr(count),
+                                          _ptr(pos), _ptr(height)),
+                    "morse_line_peaks")
+        return count, pos, height
+
+    def peak_search(self, event, map_, grid: Grid, lines, tp=(),
+                    min_peaks=0, sub=2, max_peaks=8, delta=0.0) -> np.ndarray:
+        """Top-K over the trajectories the peak library allows, aligned
+        with the peak times tp (0, 1 or 2 of them) (morse_peak_search)."""
+        lines = np.ascontiguousarray(lines, dtype=np.float64).reshape(-1, 3)
+        tpa = np.ascontiguousarray(tp, dtype=np.float64)
+        out = np.zeros(grid.top_k, dtype=FIT_DTYPE)
+        o = PeakOpts(int(sub), int(max_peaks), float(delta))
+        st = _lib.morse_peak_search(self._h, event._h, map_._h,
+                                    ctypes.byref(grid), _ptr(lines),
+                                    len(lines), ctypes.byref(o),
+                                    int(min_peaks),
+                                    _ptr(tpa) if len(tpa) else None,
+                                    len(tpa), _ptr(out))
+        self._check(st, "morse_peak_search")
         return out
 
     def line_max(self, map_, grid: Grid) -> np.ndarray:

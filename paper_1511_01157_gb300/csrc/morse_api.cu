@@ -2474,3 +2474,233 @@ morse_status morse_grid_chi2_lines(morse_ctx *ctx, const morse_event *ev,
 }
 
 }  // extern "C"
+
+namespace {
+
+morse_status check_peak_opts(morse_ctx *ctx, const morse_peak_opts *o) {
+  if (!o) return fail(ctx, MORSE_EINVAL, "peak options");
+  if (o->sub < 1 || o->sub > 16)
+    return fail(ctx, MORSE_EINVAL, "sub %d outside 1..16", o->sub);
+  if (o->max_peaks < 1 || o->max_peaks > morse::kPeakMax)
+    return fail(ctx, MORSE_EINVAL, "max_peaks %d outside 1..%d", o->max_peaks,
+                morse::kPeakMax);
+  if (!(o->delta >= 0.0) || !is_fin(o->delta))
+    return fail(ctx, MORSE_EINVAL, "delta must be finite and >= 0");
+  return MORSE_OK;
+}
+
+// lines[3 j ..] = (u, alpha, shift) -> device arrays u, cos, sin, shift,
+// alpha of n doubles each at d (cos and sin taken here, in FP64)
+morse_status upload_lines(morse_ctx *ctx, const double *lines, int n,
+                          double *d) {
+  for (int j = 0; j < 3 * n; ++j)
+    if (!is_fin(lines[j])) return fail(ctx, MORSE_EINVAL, "line %d", j / 3);
+  std::vector<double> h((size_t)5 * n);
+  for (int j = 0; j < n; ++j) {
+    h[(size_t)j] = lines[3 * j];
+    h[(size_t)n + j] = cos(lines[3 * j + 1]);
+    h[(size_t)2 * n + j] = sin(lines[3 * j + 1]);
+    h[(size_t)3 * n + j] = lines[3 * j + 2];
+    h[(size_t)4 * n + j] = lines[3 * j + 1];
+  }
+  MORSE_CUDA(ctx, cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  // the staging vector must outlive the copy
+  MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return MORSE_OK;
+}
+
+// Device layout of a peak library of n lines, P peaks each, at base + off.
+struct PeakLib {
+  double *lines;  // 5 n: u, cos, sin, shift, alpha
+  int *count;     // n
+  double *pos, *height;  // n P each
+  unsigned *err;
+  size_t bytes;
+};
+
+PeakLib peak_lib_layout(char *base, size_t off, int n, int P) {
+  PeakLib L;
+  size_t o = align_up(off, 256);
+  L.lines = (double *)(base + o);
+  o = align_up(o + sizeof(double) * 5 * (size_t)n, 256);
+  L.count = (int *)(base + o);
+  o = align_up(o + sizeof(int) * (size_t)n, 256);
+  L.pos = (double *)(base + o);
+  o = align_up(o + sizeof(double) * (size_t)n * P, 256);
+  L.height = (double *)(base + o);
+  o = align_up(o + sizeof(double) * (size_t)n * P, 256);
+  L.err = (unsigned *)(base + o);
+  L.bytes = o + 256 - off;
+  return L;
+}
+
+morse_status enqueue_peak_lib(morse_ctx *ctx, const morse_map *map,
+                              const PeakLib &L, int n,
+                              const morse_peak_opts *o) {
+  MORSE_CUDA(ctx, cudaMemsetAsync(L.err, 0, sizeof(unsigned), ctx->stream));
+  const float r = (float)(1.0 + o->delta);
+  MORSE_CUDA(ctx, morse::launch_line_peaks(
+                      map->A, map->npix, map->L, L.lines, L.lines + n,
+                      L.lines + 2 * (size_t)n, L.lines + 3 * (size_t)n, n,
+                      o->sub, r, o->max_peaks, L.count, L.pos, L.height,
+                      L.err, ctx->stream));
+  ctx->launches += 1;
+  return MORSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+morse_status morse_line_peaks(morse_ctx *ctx, const morse_map *map,
+                              const double *lines, int n_lines,
+                              const morse_peak_opts *opts, int32_t *count,
+                              double *pos, double *height) {
+  if (!ctx || !map || !lines || !count || !pos || !height || n_lines < 1)
+    return MORSE_EINVAL;
+  if (map->ctx != ctx) return fail(ctx, MORSE_EINVAL, "map of another ctx");
+  MORSE_TRY(check_peak_opts(ctx, opts));
+  if (map->npix < 2) return fail(ctx, MORSE_EINVAL, "map of one texel");
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  call_begin(ctx);
+  const int P = opts->max_peaks;
+  const size_t bytes = peak_lib_layout(nullptr, 0, n_lines, P).bytes;
+  void *ws = nullptr;
+  MORSE_TRY(ws_reserve(ctx, bytes, &ws));
+  const PeakLib L = peak_lib_layout((char *)ws, 0, n_lines, P);
+  MORSE_TRY(upload_lines(ctx, lines, n_lines, L.lines));
+  MORSE_TRY(enqueue_peak_lib(ctx, map, L, n_lines, opts));
+  unsigned err = 0;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(count, L.count, sizeof(int) * n_lines,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_CUDA(ctx, cudaMemcpyAsync(pos, L.pos,
+                                  sizeof(double) * (size_t)n_lines * P,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_CUDA(ctx, cudaMemcpyAsync(height, L.height,
+                                  sizeof(double) * (size_t)n_lines * P,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_CUDA(ctx, cudaMemcpyAsync(&err, L.err, sizeof(unsigned),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_TRY(sync_and_collect(ctx, "peak library"));
+  if (err) return fail(ctx, MORSE_ECUDA, "peak library: sample run clipped");
+  return MORSE_OK;
+}
+
+morse_status morse_peak_search(morse_ctx *ctx, const morse_event *ev,
+                               const morse_map *map, const morse_grid *grid,
+                               const double *lines, int n_lines,
+                               const morse_peak_opts *opts, int min_peaks,
+                               const double *tp, int n_tp, morse_fit *out) {
+  if (!ctx || !out || !lines || !grid || n_lines < 1) return MORSE_EINVAL;
+  MORSE_TRY(check_pair(ctx, ev, map));
+  MORSE_TRY(check_peak_opts(ctx, opts));
+  if (map->npix < 2) return fail(ctx, MORSE_EINVAL, "map of one texel");
+  if (n_tp < 0 || n_tp > 2 || (n_tp > 0 && !tp))
+    return fail(ctx, MORSE_EINVAL, "n_tp must be 0, 1 or 2");
+  for (int i = 0; i < n_tp; ++i)
+    if (!is_fin(tp[i])) return fail(ctx, MORSE_EINVAL, "peak time %d", i);
+  if (n_tp == 2 && !(tp[1] > tp[0]))
+    return fail(ctx, MORSE_EINVAL, "peak times must increase");
+  if (min_peaks < 0) return fail(ctx, MORSE_EINVAL, "min_peaks < 0");
+  if (grid->n_alpha != 1)
+    return fail(ctx, MORSE_EINVAL, "a line grid has n_alpha = 1");
+  if (n_tp == 2 && grid->n_tE != 1)
+    return fail(ctx, MORSE_EINVAL, "two peak times fix tE: n_tE = 1");
+  const int P = opts->max_peaks;
+  const int mode = n_tp;
+  const int S = mode == 0 ? 1 : mode == 1 ? P : P * (P - 1) / 2;
+  if (S < 1)
+    return fail(ctx, MORSE_EINVAL, "two peak times need max_peaks >= 2");
+  const long long ne = (long long)n_lines * S;
+  if (ne > (1LL << 30)) return fail(ctx, MORSE_EINVAL, "too many entries");
+  const int E = (int)ne;
+  // the entries replace the u0 axis; the t0 axis runs about t_p1
+  morse_grid g = *grid;
+  g.n_u0 = E;
+  g.u0_lo = 1.0;
+  g.u0_hi = 1.0;
+  g.u0_log = 0;
+  g.a_min = 0.0f;
+  if (n_tp >= 1) {
+    g.t0_lo += tp[0];
+    g.t0_hi += tp[0];
+  }
+  if (n_tp == 2) {  // tE per entry; the axis is a placeholder
+    g.tE_lo = 1.0;
+    g.tE_hi = 1.0;
+    g.tE_log = 0;
+  }
+  MORSE_TRY(check_grid(ctx, &g));
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  call_begin(ctx);
+  Plan pl;
+  MORSE_TRY(plan_search(ctx, ev, &g, 0, grid_size(&g), false,
+                        morse::map_h16(map), 1, &pl));
+  const size_t off_lib = align_up(pl.bytes, 256);
+  const size_t lib_bytes = peak_lib_layout(nullptr, off_lib, n_lines, P).bytes;
+  const size_t off_ent = align_up(off_lib + lib_bytes, 256);
+  const size_t ent_bytes = sizeof(double) * 7 * (size_t)E;
+  void *ws = nullptr;
+  MORSE_TRY(ws_reserve(ctx, off_ent + ent_bytes, &ws));
+  char *base = (char *)ws;
+  Tables T;
+  const double dlt = (2.0 * map->L) / (double)map->npix;
+  MORSE_TRY(upload_tables(ctx, &g, ev->t_ref, map->L, dlt, base + pl.off_tab,
+                          &T));
+  const PeakLib L = peak_lib_layout(base, off_lib, n_lines, P);
+  MORSE_TRY(upload_lines(ctx, lines, n_lines, L.lines));
+  MORSE_TRY(enqueue_peak_lib(ctx, map, L, n_lines, opts));
+  double *de = (double *)(base + off_ent);
+  morse::PeakEntries PE;
+  PE.u = de;
+  PE.c = de + (size_t)E;
+  PE.s = de + 2 * (size_t)E;
+  PE.shift = de + 3 * (size_t)E;
+  PE.alpha = de + 4 * (size_t)E;
+  PE.keep = de + 5 * (size_t)E;
+  PE.tE = mode == 2 ? de + 6 * (size_t)E : nullptr;
+  const int need = std::max(min_peaks, n_tp);
+  const size_t n = (size_t)n_lines;
+  MORSE_CUDA(ctx, morse::launch_peak_entries(
+                      n_lines, L.lines, L.lines + n, L.lines + 2 * n,
+                      L.lines + 3 * n, L.lines + 4 * n, L.count, L.pos, P,
+                      mode, need, n_tp >= 1 ? tp[0] : 0.0,
+                      n_tp == 2 ? tp[1] : 0.0, PE, ctx->stream));
+  MORSE_CUDA(ctx, morse::launch_slab_lines(PE.u, PE.c, PE.s, E, map->L,
+                                           T.slab, ctx->stream));
+  ctx->launches += 2;
+  morse::SearchParams Q;
+  memset(&Q, 0, sizeof(Q));
+  map_params(map, &Q);
+  event_params(ev, &Q);
+  grid_params(&g, T, &Q);
+  Q.lu = PE.u;
+  Q.lc = PE.c;
+  Q.ls = PE.s;
+  Q.lsh = PE.shift;
+  Q.la = PE.alpha;
+  Q.ltE = PE.tE;
+  Q.linemax = PE.keep;  // the peak-count cut: entries not in use
+  Q.a_min = 0.5f;
+  Q.first = 0;
+  Q.count = grid_size(&g);
+  Q.stride = 1;
+  morse::set_groups(&Q);
+  morse_fit *fits = (morse_fit *)(base + pl.off_out);
+  MORSE_TRY(hdr_init(ctx, base, pl, &Q));
+  MORSE_TRY(enqueue_topk(ctx, pl, Q, base, T, fits));
+  Hdr hd;
+  unsigned err = 0;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(&hd, base + pl.off_hdr, sizeof(Hdr),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_CUDA(ctx, cudaMemcpyAsync(&err, L.err, sizeof(unsigned),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_CUDA(ctx, cudaMemcpyAsync(out, fits, sizeof(morse_fit) * pl.K,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_TRY(sync_and_collect(ctx, "peak-aligned search"));
+  if (err) return fail(ctx, MORSE_ECUDA, "peak library: sample run clipped");
+  return hdr_check(ctx, hd);
+}
+
+}  // extern "C"

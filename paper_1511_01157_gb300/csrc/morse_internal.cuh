@@ -212,6 +212,7 @@ struct SearchParams {
   // closest approach to the line's reference point past that to the origin
   // (grid t0 is the time of the former), and the direction alpha
   const double *lu, *lc, *ls, *lsh, *la;
+  const double *ltE;        // line grid: tE per line (Eq. 8), else null
   int n_u0, n_alpha, n_t0, n_tE;
   long long first, count;   // trajectories first + i * stride, i < count
   long long stride;
@@ -296,6 +297,30 @@ cudaError_t launch_line_max(const float *A, int npix, double L,
 cudaError_t launch_slab_lines(const double *u, const double *c,
                               const double *s, int n, double L, double2 *slab,
                               cudaStream_t st);
+// ---------------------------------------------------------------- peaks
+constexpr int kPeakMax = 16;  // peaks kept per line, at most
+// Peak library of lines (lu, lc, ls) with reference shifts lsh (§4.3
+// (iii)): count[j], and the max_peaks highest peaks as pos[j max_peaks + m]
+// (tau from the reference point) and height[...], NaN in unused slots;
+// err |= 1 if the sample run was clipped (never expected)
+cudaError_t launch_line_peaks(const float *A, int npix, double L,
+                              const double *lu, const double *lc,
+                              const double *ls, const double *lsh,
+                              int n_lines, int sub, float r, int max_peaks,
+                              int *count, double *pos, double *height,
+                              unsigned *err, cudaStream_t st);
+// Peak-aligned line-grid entries (§4.3 (iv)-(v)), n_lines x slots
+struct PeakEntries {
+  double *u, *c, *s, *shift, *alpha;
+  double *tE;    // mode 2 only (else null)
+  double *keep;  // 1 in use, 0 not
+};
+cudaError_t launch_peak_entries(int n_lines, const double *lu,
+                                const double *lc, const double *ls,
+                                const double *lsh, const double *la,
+                                const int *count, const double *pos, int P,
+                                int mode, int need, double tp0, double tp1,
+                                const PeakEntries &E, cudaStream_t st);
 // critical points of the binary lens (s, q): z[k][4] for psi_k = 2 pi k/n
 // (unordered within k), as (re, im) pairs, and their caustic points zeta
 cudaError_t launch_critical(double s, double q, int n_psi, double2 *z,

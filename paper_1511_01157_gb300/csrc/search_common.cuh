@@ -159,10 +159,17 @@ __device__ __forceinline__ TrajC traj_consts(const SearchParams &P,
   const int iu = (int)(r / P.n_alpha);
   const double2 sl = P.slab[iu * P.n_alpha + ia];
   const double tE = P.tEv[itE];
-  if (P.lu)  // line grid: t0 of the closest approach to the reference point
+  if (P.lu) {  // line grid: t0 of the closest approach to the reference point
+    if (P.ltE) {  // tE of the line (Eq. 8)
+      const double tl = P.ltE[iu];
+      return make_traj(P, ep, P.lu[iu], P.lc[iu], P.ls[iu],
+                       P.t0rel[it0] - P.lsh[iu] * tl, 1.0 / (tl * P.dlt), tl,
+                       sl.x, sl.y);
+    }
     return make_traj(P, ep, P.lu[iu], P.lc[iu], P.ls[iu],
                      P.t0rel[it0] - P.lsh[iu] * tE, P.invtEd[itE], tE, sl.x,
                      sl.y);
+  }
   return make_traj(P, ep, P.u0v[iu], P.ca[ia], P.sa[ia], P.t0rel[it0],
                    P.invtEd[itE], tE, sl.x, sl.y);
 }

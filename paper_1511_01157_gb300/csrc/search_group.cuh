@@ -234,7 +234,7 @@ __device__ __forceinline__ void fill_one(const SearchParams &P, const Entry e,
     const int ia = (int)(q % P.n_alpha);
     const int iu = (int)(q / P.n_alpha);
     r.chi2 = isnan(chi2) ? CUDART_INF : chi2;
-    r.tE = tEv[itE];
+    r.tE = (P.lu && P.ltE) ? P.ltE[iu] : tEv[itE];
     if (P.lu) {  // line grid: the record in the (u0, alpha) convention
       r.t0 = t0abs[it0] - P.lsh[iu] * r.tE;
       r.u0 = P.lu[iu];

@@ -44,6 +44,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(m.MapOpts) == 8 + 3 * 4 + 4  # padded
     assert ctypes.sizeof(m.Grid) == 4 * 4 + 6 * 8 + 3 * 4 + 4  # padded
     assert m.FIT_DTYPE.itemsize == 72
+    assert ctypes.sizeof(m.PeakOpts) == 2 * 4 + 8
 
 
 def test_status_strings_and_version():
