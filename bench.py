@@ -207,6 +207,58 @@ def grid_of(m, cfg):
                        cfg["top_k"])
 
 
+def grid_lines(cfg):
+    """The (u0, alpha) lines of the config-1 grid as (u, alpha, shift)."""
+    g = cfg["grid"]
+    u0v = np.exp(np.linspace(np.log(g["u0_lo"]), np.log(g["u0_hi"]),
+                             g["n_u0"]))
+    return np.array([(u, 2 * np.pi * k / g["n_alpha"], 0.0) for u in u0v
+                     for k in range(g["n_alpha"])])
+
+
+def inside_samples(lines, L, h):
+    """Samples every h of each line's part inside the map |y1|, |y2| < L
+    (the peak library's work), from the slab geometry."""
+    tot = 0.0
+    for u, al, _ in lines:
+        c, s = math.cos(al), math.sin(al)
+        lo, hi = -math.inf, math.inf
+        for a, b in ((c, -u * s), (s, u * c)):  # |a tau + b| < L
+            if abs(a) > 1e-15:
+                t0, t1 = (-L - b) / a, (L - b) / a
+                lo, hi = max(lo, min(t0, t1)), min(hi, max(t0, t1))
+            elif abs(b) >= L:
+                hi = lo
+        tot += max(0.0, hi - lo) / h
+    return tot
+
+
+def peak_library(ctx, m, cfg, delta=0.1, max_peaks=8):
+    """§4.3 (iii) peak library of one config-1 map over the grid's 2880
+    (u0, alpha) lines, two samples per texel: time per library (the C-ABI
+    call, device synchronised) and samples per second."""
+    import torch
+    mp = ctx.build_map(cfg["s"], cfg["q"], cfg["L"], cfg["npix"], cfg["nray"],
+                       image_halfwidth=cfg["X"], deflect="fp32")
+    lines = grid_lines(cfg)
+    times = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        count, _, _ = ctx.line_peaks(mp, lines, sub=2, max_peaks=max_peaks,
+                                     delta=delta)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    mp.free()
+    h = 2.0 * cfg["L"] / cfg["npix"] / 2
+    n = inside_samples(lines, cfg["L"], h)
+    t = min(times)
+    return {"lines": len(lines), "ms": 1e3 * t, "samples": n,
+            "samples_per_s": n / t, "delta": delta,
+            "median_peaks_per_line": float(np.median(count)),
+            "max_peaks_per_line": int(count.max())}
+
+
 def batch_events(ctx, m, cfg, n_events):
     """Light curves of the batched workload: lengths log-uniform in
     [200, 20000], truths from synth.truth_draws, magnification read through
@@ -363,6 +415,40 @@ def finite_source_maps(ctx, m, cfg, gamma=0.53):
                    f"{cfg['q']})", "gamma": gamma, "radii": rows}
 
 
+def peak_time(t, F):
+    """The peak time read off a light curve: the largest running median of
+    7 epochs."""
+    order = np.argsort(np.asarray(t))
+    tt, ff = np.asarray(t)[order], np.asarray(F)[order]
+    med = np.array([np.median(ff[max(0, i - 3): i + 4])
+                    for i in range(len(tt))])
+    return float(tt[np.argmax(med)])
+
+
+def peak_grid(m, cfg, n_lines):
+    g = cfg["grid"]
+    return m.Grid.make(2 * n_lines, 1, 3, g["n_tE"], 1.0, 1.0, -0.05, 0.05,
+                       g["tE_lo"], g["tE_hi"], False, g["tE_log"], 16)
+
+
+def peak_aligned_fits(ctx, m, cfg, ev, S, Q, t_peak):
+    """§4.3 (iii)-(iv): on every (u0, alpha) line of the grid the
+    trajectories whose two highest map peaks (threshold 10%) come at t_peak
+    (Eq. 7), 3 t0 offsets within +-0.05 d and the grid's 20 tE, on each
+    map; [n_maps, 16] records."""
+    lines = grid_lines(cfg)
+    pgrid = peak_grid(m, cfg, len(lines))
+    fits = []
+    for j in range(len(S)):
+        mp = ctx.build_map(S[j], Q[j], cfg["L"], cfg["npix"], cfg["nray"],
+                           image_halfwidth=cfg["X"], deflect="fp32")
+        fits.append(ctx.peak_search(ev, mp, pgrid, lines, tp=[t_peak],
+                                    min_peaks=1, sub=2, max_peaks=2,
+                                    delta=0.1))
+        mp.free()
+    return np.stack(fits)
+
+
 def time_to_best_fit(ctx, m, cfg, ev, S, Q, plain_s, plain_fits, ev_t,
                      ev_flux, ev_sigma):
     """Wall time of each form of the (s, q) search and its best chi^2; a
@@ -441,29 +527,12 @@ def time_to_best_fit(ctx, m, cfg, ev, S, Q, plain_s, plain_fits, ev_t,
     # running median of 7 epochs), and on every (u0, alpha) line of the grid
     # the trajectories whose two highest peaks come at it (Eq. 7), 3 t0
     # offsets within +-0.05 d and the grid's 20 tE
-    order = np.argsort(np.asarray(ev_t))
-    tt, ff = np.asarray(ev_t)[order], Fs_[order]
-    med = np.array([np.median(ff[max(0, i - 3): i + 4])
-                    for i in range(len(tt))])
-    t_peak = float(tt[np.argmax(med)])
-    u0v = np.exp(np.linspace(np.log(g["u0_lo"]), np.log(g["u0_hi"]),
-                             g["n_u0"]))
-    lines = np.array([(u, 2 * np.pi * k / g["n_alpha"], 0.0) for u in u0v
-                      for k in range(g["n_alpha"])])
-    pgrid = m.Grid.make(2 * len(lines), 1, 3, g["n_tE"], 1.0, 1.0, -0.05,
-                        0.05, g["tE_lo"], g["tE_hi"], False, g["tE_log"], 16)
-
-    def aligned():
-        fits = []
-        for j in range(len(S)):
-            mp = ctx.build_map(S[j], Q[j], cfg["L"], cfg["npix"], cfg["nray"],
-                               image_halfwidth=cfg["X"], deflect="fp32")
-            fits.append(ctx.peak_search(ev, mp, pgrid, lines, tp=[t_peak],
-                                        min_peaks=1, sub=2, max_peaks=2,
-                                        delta=0.1))
-            mp.free()
-        return refine_best(ctx, m, cfg, ev, S, Q, np.stack(fits))
-    b, t = timed(aligned)
+    t_peak = peak_time(ev_t, Fs_)
+    lines = grid_lines(cfg)
+    pgrid = peak_grid(m, cfg, len(lines))
+    b, t = timed(lambda: refine_best(
+        ctx, m, cfg, ev, S, Q,
+        peak_aligned_fits(ctx, m, cfg, ev, S, Q, t_peak)))
     forms["peak_aligned_plus_refine"] = (
         t, b, f"peak time {t_peak:.3f} d from the light curve; on each of "
         f"the 2880 (u0, alpha) lines the trajectories whose two highest "
@@ -621,6 +690,16 @@ def run_gpu(args, cfg):
     ev = ctx.event(t, F, sig)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32,
                         device=f"cuda:{dev}")
+    if args.peak_only:  # profiling of the peak-aligned form alone
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fits = peak_aligned_fits(ctx, m, cfg, ev, S, Q, peak_time(t, F))
+        torch.cuda.synchronize()
+        print(json.dumps({"profiling": "peak-aligned form", "maps": len(S),
+                          "s": time.perf_counter() - t0,
+                          "best_chi2": float(fits["chi2"][:, 0].min()),
+                          "peak_library": peak_library(ctx, m, cfg)}))
+        return 0
     probes = ctx.measure_peaks()  # measured denominators (before timing)
     evals_step = grid.size * len(t) * n_maps
     rays_step = cfg["nray"] ** 2 * n_maps
@@ -764,6 +843,7 @@ def run_gpu(args, cfg):
             ctx, m, cfg, ev, S, Q, elapsed / args.steps, fits, t, F, sig)
         line["map_generators"] = map_generators(ctx, m, cfg)
         line["finite_source"] = finite_source_maps(ctx, m, cfg)
+        line["peak_library"] = peak_library(ctx, m, cfg)
         line["batched"] = run_batched(ctx, m, args.batch_events,
                                       args.batch_maps, not args.no_batch_tune)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -809,6 +889,9 @@ def main():
                     help="maps of the batched section (of 64)")
     ap.add_argument("--lookup", default="fp32", choices=["fp32", "fp16log"],
                     help="map table the search reads (the headline is fp32)")
+    ap.add_argument("--peak-only", action="store_true",
+                    help="run only the peak-aligned search over the maps "
+                    "and the peak library section (profiling)")
     ap.add_argument("--maps", type=int, default=0,
                     help="search an evenly spaced subset of the 651 (s,q) "
                     "maps per step (profiling of small cases only)")

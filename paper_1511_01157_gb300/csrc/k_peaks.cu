@@ -18,12 +18,14 @@
 //
 // GB300 design: one warp per line.  The lanes evaluate 32 consecutive
 // samples at once (the line's texels stream through L1/L2, the map having
-// just been built), then lane 0 runs the sequential peak detector over
-// them from shared memory and keeps the highest peaks in a short sorted
-// list there.  A line has at most 2 sub npix sqrt(2) samples inside the
-// map, so a line costs a few tens of microseconds and every line of a grid
-// runs at once.  The expansion into trajectory entries is one thread per
-// (line, slot).
+// just been built); the sequential peak detector then steps through them
+// with every lane holding the same state: a warp scan of the running
+// maximum (or minimum) finds the first sample of the 32 that changes the
+// state, everything before it moves only the running extreme, and the
+// scan resumes after it -- a few warp instructions per sample, no shared
+// memory, no divergence.  The highest peaks are kept one per lane, the
+// list shifted by a warp shuffle on the rare insertion.  The expansion into trajectory
+// entries is one thread per (line, slot).
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
@@ -44,11 +46,8 @@ __global__ void __launch_bounds__(kPkWarps * 32)
                  int n_lines, int sub, float r, int max_peaks,
                  int *__restrict__ count, double *__restrict__ pos,
                  double *__restrict__ height, unsigned *__restrict__ err) {
-  __shared__ float s_v[kPkWarps][32];
-  __shared__ float s_kh[kPkWarps][kPeakMax];
-  __shared__ int s_kk[kPkWarps][kPeakMax];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int line = blockIdx.x * kPkWarps + w;
+  const int lane = threadIdx.x & 31;
+  const int line = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (line >= n_lines) return;  // warp-uniform; the kernel has no barrier
   const double u = lu[line], c = lc[line], s = ls[line], sh = lsh[line];
   // the line in texel coordinates, p = a tau + b, in FP64 then FP32
@@ -82,9 +81,14 @@ __global__ void __launch_bounds__(kPkWarps * 32)
   };
   clip(ax, bx, bxf);
   clip(ay, by, byf);
+  // The detector's state is the same in every lane (each step reads one
+  // broadcast sample), so its branches are warp-uniform.  Kept peak q
+  // (highest first) lives in lane q.
   int cnt = 0, nkept = 0, kmx = 0;
   bool look_max = false;
   float mn = CUDART_INF_F, mx = -CUDART_INF_F;
+  float kh = -CUDART_INF_F;
+  int kk = 0;
   for (int kb = k0; kb <= k1; kb += 32) {
     const int k = kb + lane;
     float v = 0.f;
@@ -120,68 +124,93 @@ __global__ void __launch_bounds__(kPkWarps * 32)
       if (k1 - kb < 32 && ((m >> (k1 - kb)) & 1u) && k1 < K)
         atomicOr(err, 1u);
     }
-    s_v[w][lane] = v;
-    __syncwarp();
-    if (lane == 0) {
-      for (unsigned mm = m; mm; mm &= mm - 1) {
-        const int i = __ffs(mm) - 1;
-        const float x = s_v[w][i];
-        if (look_max) {
-          if (x > mx) {
-            mx = x;
-            kmx = kb + i;
-          } else if (mx > __fmul_rn(r, x)) {
-            // a peak; kept if among the max_peaks highest (ties: earlier)
-            ++cnt;
-            int at = nkept;
-            while (at > 0 && mx > s_kh[w][at - 1]) --at;
-            if (at < max_peaks) {
-              const int last = nkept < max_peaks ? nkept : max_peaks - 1;
-              for (int q = last; q > at; --q) {
-                s_kh[w][q] = s_kh[w][q - 1];
-                s_kk[w][q] = s_kk[w][q - 1];
-              }
-              s_kh[w][at] = mx;
-              s_kk[w][at] = kmx;
-              if (nkept < max_peaks) ++nkept;
-            }
-            look_max = false;
-            mn = x;
-          }
-        } else {
-          if (x < mn) {
-            mn = x;
-          } else if (x > __fmul_rn(r, mn)) {
-            look_max = true;
-            mx = x;
-            kmx = kb + i;
+    if (m == 0u) continue;
+    // The chunk's samples in order, a run at a time.  With the inclusive
+    // running maximum pm_i (of mx and the run's samples up to i), sample i
+    // ends a peak exactly when pm_i > r x_i (a sample above the running
+    // maximum has pm_i = x_i <= r x_i); with the running minimum pn_i, a
+    // rise starts exactly when x_i > r pn_i.  Up to the first such sample
+    // j only the running extreme (and its position) moves; j changes the
+    // state, and the next run starts after it.
+    unsigned act = m;  // inside lanes not yet stepped through
+    for (int guard = 0; act != 0u && guard < 33; ++guard) {
+      const bool a = (act >> lane) & 1u;
+      if (look_max) {
+        float pm = a ? v : -CUDART_INF_F;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const float y = __shfl_up_sync(kFull, pm, o);
+          if (lane >= o) pm = fmaxf(pm, y);
+        }
+        pm = fmaxf(pm, mx);
+        const unsigned f = __ballot_sync(kFull, a && pm > __fmul_rn(r, v));
+        const int j = f ? __ffs(f) - 1 : 32;
+        const unsigned before = act & (j < 32 ? (1u << j) - 1u : kFull);
+        if (before) {
+          const float cm = __shfl_sync(kFull, pm, 31 - __clz(before));
+          if (cm > mx) {
+            kmx = kb + __ffs(__ballot_sync(
+                           kFull, ((before >> lane) & 1u) && v == cm)) - 1;
+            mx = cm;
           }
         }
+        if (j == 32) break;
+        // a peak (mx at kmx) ends at sample j; kept if among the max_peaks
+        // highest (ties: the earlier)
+        ++cnt;
+        const int at = __popc(__ballot_sync(kFull, lane < nkept && kh >= mx));
+        if (at < max_peaks) {
+          const float kh_up = __shfl_up_sync(kFull, kh, 1);
+          const int kk_up = __shfl_up_sync(kFull, kk, 1);
+          if (lane == at) {
+            kh = mx;
+            kk = kmx;
+          } else if (lane > at && lane < max_peaks) {
+            kh = kh_up;
+            kk = kk_up;
+          }
+          if (nkept < max_peaks) ++nkept;
+        }
+        look_max = false;
+        mn = __shfl_sync(kFull, v, j);
+        act &= j < 31 ? ~((2u << j) - 1u) : 0u;
+      } else {
+        float pn = a ? v : CUDART_INF_F;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const float y = __shfl_up_sync(kFull, pn, o);
+          if (lane >= o) pn = fminf(pn, y);
+        }
+        pn = fminf(pn, mn);
+        const unsigned f = __ballot_sync(kFull, a && v > __fmul_rn(r, pn));
+        const int j = f ? __ffs(f) - 1 : 32;
+        const unsigned before = act & (j < 32 ? (1u << j) - 1u : kFull);
+        if (before) mn = __shfl_sync(kFull, pn, 31 - __clz(before));
+        if (j == 32) break;
+        // a rise confirmed at sample j: the peak search starts there
+        look_max = true;
+        mx = __shfl_sync(kFull, v, j);
+        kmx = kb + j;
+        act &= j < 31 ? ~((2u << j) - 1u) : 0u;
       }
     }
-    __syncwarp();
   }
-  if (lane == 0) {
-    // kept peaks in increasing tau
-    for (int a = 1; a < nkept; ++a)
-      for (int b = a; b > 0 && s_kk[w][b] < s_kk[w][b - 1]; --b) {
-        const int ti = s_kk[w][b];
-        s_kk[w][b] = s_kk[w][b - 1];
-        s_kk[w][b - 1] = ti;
-        const float tf = s_kh[w][b];
-        s_kh[w][b] = s_kh[w][b - 1];
-        s_kh[w][b - 1] = tf;
-      }
-    count[line] = cnt;
-    for (int q = 0; q < max_peaks; ++q) {
-      const size_t o = (size_t)line * max_peaks + q;
-      if (q < nkept) {
-        pos[o] = __dsub_rn(__dmul_rn((double)s_kk[w][q], h), sh);
-        height[o] = (double)s_kh[w][q];
-      } else {
-        pos[o] = CUDART_NAN;
-        height[o] = CUDART_NAN;
-      }
+  // kept peaks in increasing tau: lane q's rank among the kept k
+  int rank = 0;
+  for (int p = 0; p < nkept; ++p) {
+    const int kp = __shfl_sync(kFull, kk, p);
+    rank += (kp < kk) ? 1 : 0;
+  }
+  if (lane == 0) count[line] = cnt;
+  if (lane < max_peaks) {
+    if (lane < nkept) {
+      const size_t o = (size_t)line * max_peaks + rank;
+      pos[o] = __dsub_rn(__dmul_rn((double)kk, h), sh);
+      height[o] = (double)kh;
+    } else {
+      const size_t o = (size_t)line * max_peaks + lane;
+      pos[o] = CUDART_NAN;
+      height[o] = CUDART_NAN;
     }
   }
 }
