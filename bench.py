@@ -259,6 +259,63 @@ def peak_library(ctx, m, cfg, delta=0.1, max_peaks=8):
             "max_peaks_per_line": int(count.max())}
 
 
+def adjoint_section(ctx, m, cfg, ev, n_ep, stream, probes, peak_instr_s,
+                    n=4096, iters=50):
+    """Adjoint gradient and refinement on the truth map of the config-1
+    event: n = 4096 trajectories scattered about the truth (the refinement
+    workload's start count).  chi^2 and its gradient by morse_chi2_grad_dev
+    (device buffers, CUDA events on the context's stream), evals/s against
+    the FP32-issue roofline (22 + 14 instructions per evaluation) and the
+    L1 gather roofline (16 B); then `iters` Levenberg-Marquardt iterations of
+    all n (morse_refine, a CUDA graph per iteration) timed end to end."""
+    import torch
+    mp = ctx.build_map(cfg["s"], cfg["q"], cfg["L"], cfg["npix"], cfg["nray"],
+                       image_halfwidth=cfg["X"], deflect="fp32")
+    rng = np.random.default_rng(5)
+    th = np.stack([cfg["t0"] + rng.uniform(-1.0, 1.0, n),
+                   cfg["tE"] * np.exp(rng.uniform(-0.3, 0.3, n)),
+                   cfg["u0"] * np.exp(rng.uniform(-0.5, 0.5, n)),
+                   cfg["alpha"] + rng.uniform(-0.2, 0.2, n)], axis=1)
+    theta = torch.tensor(th, dtype=torch.float64, device="cuda")
+    chi2 = torch.empty(n, dtype=torch.float64, device="cuda")
+    grad = torch.empty((n, 4), dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            ctx.chi2_grad_dev(ev, mp, theta, chi2, grad)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 10
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.chi2_grad_dev(ev, mp, theta, chi2, grad)
+        e1.record(stream)
+        e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    evals = n * n_ep / (ms * 1e-3)
+    peak_instr = peak_instr_s / 36.0
+    peak_gather = probes["l1_gather_bytes_per_s"] / 16.0
+    starts = np.zeros(n, dtype=m.FIT_DTYPE)
+    starts["t0"], starts["tE"], starts["u0"], starts["alpha"] = th.T
+    starts["chi2"] = np.inf
+    ctx.refine(ev, mp, starts[:64], iters=2)  # warm (graph capture)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = ctx.refine(ev, mp, starts, iters=iters)
+    torch.cuda.synchronize()
+    t_ref = time.perf_counter() - t0
+    mp.free()
+    return {"trajectories": n, "epochs": n_ep, "grad_ms": ms,
+            "grad_evals_per_s": evals,
+            "frac_fp32_issue": evals / peak_instr,
+            "frac_l1_gather": evals / peak_gather,
+            "roofline_note": "36 FP32 instr (22 + 14 for the gradient) and "
+                             "16 B per evaluation; peaks: the search's FP32 "
+                             "issue peak and the measured L1 gather",
+            "refine_iters": iters, "refine_s": t_ref,
+            "refine_iters_per_s": n * iters / t_ref,
+            "refine_median_chi2": float(np.median(out["chi2"]))}
+
+
 def batch_events(ctx, m, cfg, n_events):
     """Light curves of the batched workload: lengths log-uniform in
     [200, 20000], truths from synth.truth_draws, magnification read through
@@ -844,6 +901,8 @@ def run_gpu(args, cfg):
         line["map_generators"] = map_generators(ctx, m, cfg)
         line["finite_source"] = finite_source_maps(ctx, m, cfg)
         line["peak_library"] = peak_library(ctx, m, cfg)
+        line["adjoint"] = adjoint_section(ctx, m, cfg, ev, len(t), stream,
+                                          probes, peak_instr * 1e12)
         line["batched"] = run_batched(ctx, m, args.batch_events,
                                       args.batch_maps, not args.no_batch_tune)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

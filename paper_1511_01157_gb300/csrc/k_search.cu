@@ -65,8 +65,12 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
 
   const float4 *blk = P.ep;
   BlockTopK T;
+  float4 *tabs = nullptr;  // two band tables (P.tab_n entries each)
   __shared__ int s_cur, s_nk, s_lock, s_next;
   __shared__ double s_thr;
+  // band table words: ((round + 1) << 7) | (ready << 6) | users; 0 = empty
+  __shared__ unsigned s_tw[2];
+  __shared__ int s_tb[2];  // orientation (1: x-major, 2: y-major)
   {
     unsigned char *p = smem;
     if (EP_SMEM) {
@@ -79,7 +83,9 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
       T.buf0 = reinterpret_cast<Entry *>(p);
       T.buf1 = T.buf0 + K;
       T.wbuf = T.buf1 + K;
+      p += sizeof(Entry) * ((size_t)2 * K + kSearchWarps * 32);
     }
+    if (!H && P.tab_n > 0) tabs = reinterpret_cast<float4 *>(p);
     T.cur = &s_cur;
     T.nk = &s_nk;
     T.lock = &s_lock;
@@ -91,6 +97,8 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
     s_lock = 0;
     s_next = 0;
     s_thr = CUDART_INF;
+    s_tw[0] = 0u;
+    s_tw[1] = 0u;
   }
   __syncthreads();
   const Epochs ep = epochs_at(blk, P.n_ep);
@@ -112,6 +120,86 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
   }
   const long long gstride = (long long)gridDim.x * kSearchWarps;
   unsigned long long n_exact = 0;
+
+  // Band tables.  With kSearchWarps groups per line (the host enables the
+  // tables only then) the block's round r is one line; its table lives in
+  // buffer r & 1.  A warp that claims a group of round r builds the tables
+  // of rounds r and r + 1 when their buffers are free (no user left of the
+  // round two back) and nobody has; it reads round r's table only after
+  // taking a user count on a ready word, and otherwise uses the global
+  // table.  Nothing ever waits: every step falls back to the global path.
+  const bool use_tab = tabs != nullptr && lined &&
+                       P.ng_line == (long long)kSearchWarps;
+  auto round_line = [&](long long r, double &cx, double &cy, double &c,
+                        double &s) -> bool {
+    const long long g0 = (long long)blockIdx.x * kSearchWarps + r * gstride;
+    if (g0 >= n_groups) return false;
+    const long long L = line0 + g0 / P.ng_line;
+    const long long iu = L / P.n_alpha;
+    const int ia = (int)(L - iu * P.n_alpha);
+    double u;
+    if (P.lu) {
+      u = P.lu[iu];
+      c = P.lc[iu];
+      s = P.ls[iu];
+    } else {
+      u = P.u0v[iu];
+      c = P.ca[ia];
+      s = P.sa[ia];
+    }
+    cx = -u * s * P.invD + P.coff;
+    cy = u * c * P.invD + P.coff;
+    return true;
+  };
+  auto try_build = [&](long long r) {  // warp-collective
+    double cx, cy, c, s;
+    if (!round_line(r, cx, cy, c, s)) return;
+    const int b = (int)(r & 1);
+    const unsigned want = (unsigned)(r + 1) << 7;
+    int got = 0;
+    if (lane == 0) {
+      const unsigned w = *(volatile unsigned *)&s_tw[b];
+      const bool idle = w == 0u || (w & 0x40u);  // empty or ready
+      if (idle && (w & 0x3Fu) == 0u && (w >> 7) < (unsigned)(r + 1))
+        got = atomicCAS(&s_tw[b], w, want) == w;
+    }
+    got = __shfl_sync(kFull, got, 0);
+    if (!got) return;
+    const int tb = build_band(P, tabs + (size_t)b * P.tab_n, cx, cy, c, s,
+                              lane);
+    __threadfence_block();
+    __syncwarp();
+    if (lane == 0) {
+      s_tb[b] = tb;
+      __threadfence_block();
+      atomicExch(&s_tw[b], want | 0x40u);
+    }
+    __syncwarp();
+  };
+  auto try_acquire = [&](long long r) -> int {  // warp-collective; 0: none
+    const int b = (int)(r & 1);
+    const unsigned want = ((unsigned)(r + 1) << 7) | 0x40u;
+    int ok = 0;
+    if (lane == 0) {
+      for (int it = 0; it < 16; ++it) {
+        const unsigned w = *(volatile unsigned *)&s_tw[b];
+        if ((w & ~0x3Fu) != want) break;
+        if (atomicCAS(&s_tw[b], w, w + 1u) == w) {
+          ok = 1;
+          break;
+        }
+      }
+      if (ok) {
+        __threadfence_block();
+        ok = *(volatile int *)&s_tb[b];
+      }
+    }
+    return __shfl_sync(kFull, ok, 0);
+  };
+  if (use_tab) {  // the first two rounds' tables before any group starts
+    if (warp < 2) try_build(warp);
+    __syncthreads();
+  }
 
   // The block's groups come in rounds of kSearchWarps consecutive groups,
   // round r starting at blockIdx.x kSearchWarps + r gstride.  Its warps
@@ -136,7 +224,24 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
       lo = g * tpg;
       hi = min(lo + tpg, P.count);
     }
-    search_group<DENSE, H>(P, ep, T, K, warp, lane, lo, hi, lined, n_exact);
+    int tb = 0;
+    const long long r = k / kSearchWarps;
+    if (use_tab) {
+      try_build(r);
+      try_build(r + 1);
+      tb = try_acquire(r);
+    }
+    const float4 *tab = tabs + (size_t)(r & 1) * (use_tab ? P.tab_n : 0);
+    if (tb == 1)
+      search_group<DENSE, H, 1>(P, ep, T, K, warp, lane, lo, hi, lined,
+                                n_exact, tab);
+    else if (tb == 2)
+      search_group<DENSE, H, 2>(P, ep, T, K, warp, lane, lo, hi, lined,
+                                n_exact, tab);
+    else
+      search_group<DENSE, H>(P, ep, T, K, warp, lane, lo, hi, lined,
+                             n_exact);
+    if (tb != 0 && lane == 0) atomicSub(&s_tw[(int)(r & 1)], 1u);
   }
   if (P.stat_exact && lane == 0 && n_exact)
     atomicAdd(P.stat_exact, n_exact);

@@ -483,7 +483,32 @@ struct Plan {
   size_t smem;
   int grid;
   size_t off_tab, off_lmax, off_hdr, off_pa, off_pb, off_out, bytes;
+  int tab_n;  // band-table entries (0: the search reads the global table)
 };
+
+// What the line-aligned pass needs to read its map cells from shared-memory
+// band tables: the map size and a bound on the trajectories' pixel
+// coordinates' terms, B = (max|t - t_ref| + max|t0 - t_ref|) / (min tE
+// Delta) + (max|u| + max|shift|) / Delta.  FP32 rounding moves a position
+// by at most 2^-24 (3 B), and the band keeps 1/4 texel to spare, so the
+// tables are used only while B <= 1e5 (0.018 texel).
+struct BandSpec {
+  int npix = 0;  // 0: no band tables
+  double L = 0.0, u_max = 0.0, shift_max = 0.0;
+};
+
+double grid_umax(const morse_grid *g) {
+  return std::max(std::fabs(g->u0_lo), std::fabs(g->u0_hi));
+}
+
+BandSpec band_spec(int npix, double L, double u_max, double shift_max) {
+  BandSpec b;
+  b.npix = npix;
+  b.L = L;
+  b.u_max = u_max;
+  b.shift_max = shift_max;
+  return b;
+}
 
 // Device words of one search call (in the workspace header): the grid-wide
 // pruning threshold, the error word and the exact-sweep counter.
@@ -521,6 +546,10 @@ morse_status hdr_check(morse_ctx *ctx, const Hdr &h) {
     return fail(ctx, MORSE_ECUDA,
                 "bounds check: a texel index fell outside the map (error "
                 "0x%x); results are invalid", h.err);
+  if (h.err & 4u)
+    return fail(ctx, MORSE_ECUDA,
+                "bounds check: a band-table lookup read another cell than "
+                "the map's (error 0x%x); results are invalid", h.err);
   if (h.err & 1u)
     return fail(ctx, MORSE_ETIMEOUT,
                 "a search block could not take its top-K lock (error 0x%x); "
@@ -531,14 +560,35 @@ morse_status hdr_check(morse_ctx *ctx, const Hdr &h) {
 morse_status plan_search(morse_ctx *ctx, const morse_event *ev,
                          const morse_grid *g, long long first,
                          long long count, bool dense, bool h16,
-                         long long n_out, Plan *pl) {
+                         long long n_out, Plan *pl,
+                         const BandSpec &band = BandSpec()) {
   const int K = dense ? 1 : g->top_k;
   const size_t fixed = morse::search_smem_bytes(0, dense ? 0 : K) -
                        (dense ? sizeof(Entry) * morse::kSearchWarps * 32 : 0);
   const size_t budget = ctx->smem_optin > 4096 ? ctx->smem_optin - 2048 : 0;
   const bool ep_smem =
       budget > fixed && (size_t)ev->n <= (budget - fixed) / sizeof(float4);
-  const size_t smem = fixed + (ep_smem ? sizeof(float4) * (size_t)ev->n : 0);
+  size_t smem = fixed + (ep_smem ? sizeof(float4) * (size_t)ev->n : 0);
+  // band tables: FP32 cells, one line per block round (kSearchWarps groups
+  // per line), two tables in the remaining shared memory, bounded motion
+  pl->tab_n = 0;
+  if (band.npix >= 2 && !h16) {
+    const long long line = (long long)g->n_t0 * g->n_tE;
+    const int tpg = morse::line_tpg(line);
+    const double dlt = 2.0 * band.L / band.npix;
+    const double tE_min = std::min(g->tE_lo, g->tE_hi);
+    const double t0_max = std::max(std::fabs(g->t0_lo - ev->t_ref),
+                                   std::fabs(g->t0_hi - ev->t_ref));
+    const double B = (ev->t_span + t0_max) / (tE_min * dlt) +
+                     (band.u_max + band.shift_max) / dlt + 1.0;
+    const int n = 4 * (band.npix + 1);
+    const size_t tb = 2 * sizeof(float4) * (size_t)n;
+    if ((line + tpg - 1) / tpg == morse::kSearchWarps && tE_min > 0.0 &&
+        B <= 1e5 && smem + tb <= budget) {
+      pl->tab_n = n;
+      smem += tb;
+    }
+  }
   const int bps = morse::search_blocks_per_sm(dense, ep_smem, h16, smem);
   if (bps < 1)
     return fail(ctx, MORSE_EUNSUPPORTED,
@@ -594,6 +644,8 @@ morse_status enqueue_topk(morse_ctx *ctx, const Plan &pl,
                           morse::SearchParams P, char *base,
                           const Tables &T, morse_fit *fits_dev) {
   P.partial = (Entry *)(base + pl.off_pa);
+  P.tab_n = pl.tab_n;
+  P.tab_c = (unsigned)(P.half + 1) - 0x4B400000u;
   int r;
   // pilot: a strided subset of ~sqrt(K N) trajectories (at least 16 K)
   // seeds the grid-wide pruning threshold
@@ -682,7 +734,7 @@ morse_status sweep_impl(morse_ctx *ctx, const morse_event *ev,
     return fail(ctx, MORSE_ENOMEM, "FP16 table of %d^2 texels", npix);
   Plan pl;
   MORSE_TRY(plan_search(ctx, ev, grid, 0, grid_size(grid), false, h16, n_maps,
-                        &pl));
+                        &pl, band_spec(npix, extent, grid_umax(grid), 0.0)));
   void *ws = nullptr;
   MORSE_TRY(ws_reserve(ctx, pl.bytes, &ws));
   char *base = (char *)ws;
@@ -1654,6 +1706,9 @@ morse_status morse_event_create(morse_ctx *ctx, const double *t,
   ev->Fref = Fref;
   ev->invS1 = 1.0 / S1;
   ev->CFF = SFF - SF * SF / S1;
+  ev->t_span = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    ev->t_span = std::max(ev->t_span, std::fabs(t[i] - t_ref));
   *out = ev;
   return MORSE_OK;
 }
@@ -1684,7 +1739,8 @@ morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
   call_begin(ctx);
   Plan pl;
   MORSE_TRY(plan_search(ctx, ev, grid, 0, grid_size(grid), false,
-                        morse::map_h16(map), 1, &pl));
+                        morse::map_h16(map), 1, &pl,
+                        band_spec(map->npix, map->L, grid_umax(grid), 0.0)));
   void *ws = nullptr;
   MORSE_TRY(ws_reserve(ctx, pl.bytes, &ws));
   char *base = (char *)ws;
@@ -1731,7 +1787,8 @@ morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
   call_begin(ctx);
   Plan pl;
   MORSE_TRY(plan_search(ctx, ev, grid, first, count, true,
-                        morse::map_h16(map), count, &pl));
+                        morse::map_h16(map), count, &pl,
+                        band_spec(map->npix, map->L, grid_umax(grid), 0.0)));
   void *ws = nullptr;
   MORSE_TRY(ws_reserve(ctx, pl.bytes, &ws));
   char *base = (char *)ws;
@@ -1752,6 +1809,8 @@ morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,
   P.dchi2 = (double *)(base + pl.off_out);
   P.dFs = P.dchi2 + count;
   P.dFb = P.dFs + count;
+  P.tab_n = pl.tab_n;
+  P.tab_c = (unsigned)(P.half + 1) - 0x4B400000u;
   MORSE_TRY(hdr_init(ctx, base, pl, &P));
   MORSE_TRY(enqueue_cut(ctx, map, grid, T, pl, base, &P));
   int r = t_begin(ctx, KT_SEARCH);
@@ -2421,9 +2480,15 @@ morse_status morse_grid_chi2_lines(morse_ctx *ctx, const morse_event *ev,
     if (!is_fin(lines[j])) return fail(ctx, MORSE_EINVAL, "line %d", j / 3);
   MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
   call_begin(ctx);
+  double l_umax = 0.0, l_smax = 0.0;
+  for (int j = 0; j < nl; ++j) {
+    l_umax = std::max(l_umax, std::fabs(lines[3 * j]));
+    l_smax = std::max(l_smax, std::fabs(lines[3 * j + 2]));
+  }
   Plan pl;
   MORSE_TRY(plan_search(ctx, ev, &g, 0, grid_size(&g), false,
-                        morse::map_h16(map), 1, &pl));
+                        morse::map_h16(map), 1, &pl,
+                        band_spec(map->npix, map->L, l_umax, l_smax)));
   const size_t off_lines = align_up(pl.bytes, 256);
   void *ws = nullptr;
   MORSE_TRY(ws_reserve(ctx, off_lines + 5 * sizeof(double) * (size_t)nl, &ws));
@@ -2634,9 +2699,20 @@ morse_status morse_peak_search(morse_ctx *ctx, const morse_event *ev,
   MORSE_TRY(check_grid(ctx, &g));
   MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
   call_begin(ctx);
+  // band tables unless tE varies per entry (two peak times); positions
+  // along a line lie within 2 sqrt(2) L of its reference point
+  BandSpec band;
+  if (n_tp < 2) {
+    double umax = 0.0, smax = 0.0;
+    for (int j = 0; j < n_lines; ++j) {
+      umax = std::max(umax, std::fabs(lines[3 * j]));
+      smax = std::max(smax, std::fabs(lines[3 * j + 2]));
+    }
+    band = band_spec(map->npix, map->L, umax, smax + 3.0 * map->L);
+  }
   Plan pl;
   MORSE_TRY(plan_search(ctx, ev, &g, 0, grid_size(&g), false,
-                        morse::map_h16(map), 1, &pl));
+                        morse::map_h16(map), 1, &pl, band));
   const size_t off_lib = align_up(pl.bytes, 256);
   const size_t lib_bytes = peak_lib_layout(nullptr, off_lib, n_lines, P).bytes;
   const size_t off_ent = align_up(off_lib + lib_bytes, 256);

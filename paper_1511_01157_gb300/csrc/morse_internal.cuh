@@ -73,6 +73,7 @@ struct morse_event {
                             // (F - F_ref)[n]
   double S1, SF, SFF, Fref; // FP64 sums of the stored FP32 values
   double invS1, CFF;        // 1/S_1, S_FF - S_F^2/S_1
+  double t_span;            // max |t - t_ref| over the epochs
 };
 
 namespace morse {
@@ -230,9 +231,14 @@ struct SearchParams {
   unsigned long long *gthr; // grid-wide pruning threshold (chi^2 bits),
                             // all-ones = +inf
   unsigned int *err;        // bit 0: a block lock spin gave up;
-                            // bit 1: texel index out of range (checked
-                            // build only)
+                            // bit 1: texel index out of range, bit 2: a
+                            // band-table cell differs from the map's
+                            // (checked build only)
   unsigned long long *stat_exact;  // trajectories given the exact sweep
+  // Shared-memory band tables of the line-aligned pass (k_search only;
+  // 0 = off): entries per table, 4 (npix + 1), two tables after the lists.
+  int tab_n;
+  unsigned tab_c;           // half + 1 - 0x4B400000: floor bits -> cell
 };
 
 struct FillParams {

@@ -261,6 +261,82 @@ __device__ __forceinline__ float bilinear_m1(const SearchParams &P, float vx,
   return __fmaf_rn(t.fy, __fsub_rn(r1, r0), r0);
 }
 
+// Band table of one line of the line-aligned pass, in shared memory.  For
+// a line closer to the first axis (|cos alpha| >= |sin alpha|, TB = 1) the
+// table holds, for every cell column X, the cells of rows row0(X) ..
+// row0(X) + 3 around the line, at key X + (npix + 1) ((Y + C) & 3) with C
+// the floor bits' offset: four consecutive rows have distinct low bits, so
+// the key is the cell's own, and neighbouring columns are neighbouring
+// entries (a warp's lookups along the line fall in distinct banks).  The line meets at most rows floor(yc - 1/2) ..
+// floor(yc + 1/2) of a column (|slope| <= 1, yc its height at the column
+// centre), and row0 = floor(yc) - 1 takes them with 1/4 texel to spare on
+// each side, far beyond the FP32 rounding of a trajectory's position
+// (below 1e-2 texel for |a t| < 1e5 texels, which the host checks).  So a
+// band lookup reads the same 16 bytes as the global table, from shared
+// memory.  TB = 2: rows and columns swapped.
+template <int TB>
+__device__ __forceinline__ float bilinear_tab_m1(const SearchParams &P,
+                                                 const float4 *tab, float vx,
+                                                 float vy) {
+  const float tx = __fadd_rd(vx, 12582912.f), ty = __fadd_rd(vy, 12582912.f);
+  const float fx = __fsub_rn(vx, __fsub_rn(tx, 12582912.f));
+  const float fy = __fsub_rn(vy, __fsub_rn(ty, 12582912.f));
+  const unsigned bx = (unsigned)__float_as_int(tx);
+  const unsigned by = (unsigned)__float_as_int(ty);
+  const unsigned S = (unsigned)P.npix + 1u;
+  const unsigned key = TB == 1 ? (bx + P.tab_c) + S * (by & 3u)
+                               : (by + P.tab_c) + S * (bx & 3u);
+#ifdef MORSE_CHECK_BOUNDS
+  // checked build: the band entry must be the global table's cell
+  TexPos t;
+  if (!tex_pos(P, vx, vy, t)) return 0.f;
+  if (key >= (unsigned)P.tab_n) {
+    if (P.err) atomicOr(P.err, 4u);
+    return 0.f;
+  }
+  {
+    const float4 g = __ldg(&P.quad[t.idx]), b = tab[key];
+    if (g.x != b.x || g.y != b.y || g.z != b.z || g.w != b.w)
+      if (P.err) atomicOr(P.err, 4u);
+  }
+#endif
+  const float4 q = tab[key];
+  const float r0 = __fmaf_rn(fx, q.y, q.x);
+  const float r1 = __fmaf_rn(fx, q.w, q.z);
+  return __fmaf_rn(fy, __fsub_rn(r1, r0), r0);
+}
+
+// Fill the band table of the line through the centred point (cx, cy) with
+// direction (c, s) (warp-collective); returns TB (1 or 2).
+__device__ inline int build_band(const SearchParams &P, float4 *tab,
+                                 double cx, double cy, double c, double s,
+                                 int lane) {
+  const bool xm = fabs(c) >= fabs(s);
+  const int n = P.npix;
+  // along the major axis m, the minor coordinate of the line is
+  // w(m) = w0 + slope (m - m0)
+  const float slope = (float)(xm ? s / c : c / s);
+  const float m0 = (float)(xm ? cx : cy), w0 = (float)(xm ? cy : cx);
+  const unsigned C = 0x4B400000u - (unsigned)(P.half + 1);
+  const float lim = 4.f * (float)n + 8.f;
+  for (int M = lane; M <= n; M += 32) {
+    const float mc = (float)(M - P.half) - 0.5f;  // centre of cell M
+    float wc = __fmaf_rn(slope, mc - m0, w0);
+    wc = fminf(fmaxf(wc, -lim), lim);
+    const int r0 = (int)floorf(wc) + P.half;  // cell of the centre, less 1
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const int W = r0 + d;
+      const int Wc = min(max(W, 0), n);
+      const unsigned key =
+          (unsigned)M + (unsigned)(n + 1) * (((unsigned)W + C) & 3u);
+      tab[key] = xm ? P.quad[cell_index(M, Wc, P.qpitch)]
+                    : P.quad[cell_index(Wc, M, P.qpitch)];
+    }
+  }
+  return xm ? 1 : 2;
+}
+
 // Lanes own epochs by index mod 32 in every range, so a lane always sums
 // its terms in ascending epoch order whatever the ranges are: the sums of a
 // trajectory do not depend on how its epoch axis is cut into segments (the
@@ -313,10 +389,12 @@ __device__ __forceinline__ float bilinear_h_m1(const SearchParams &P,
 
 // A - 1 at time t inside the map (bilinear) or outside (single lens)
 // (H: the FP16 log10 table)
-template <bool H>
+template <bool H, int TB = 0>
 __device__ __forceinline__ float mag_in_m1(const SearchParams &P,
-                                           const TrajC &c, float t) {
+                                           const TrajC &c, float t,
+                                           const float4 *tab = nullptr) {
   const float vx = __fmaf_rn(c.ax, t, c.bx), vy = __fmaf_rn(c.ay, t, c.by);
+  if (TB != 0) return bilinear_tab_m1<TB>(P, tab, vx, vy);
   return H ? bilinear_h_m1(P, vx, vy) : bilinear_m1(P, vx, vy);
 }
 __device__ __forceinline__ float mag_out_m1(const TrajC &c, float t) {
@@ -324,30 +402,33 @@ __device__ __forceinline__ float mag_out_m1(const TrajC &c, float t) {
   return __fsub_rn(pspl_u2(__fmaf_rn(tau, tau, c.u02)), 1.f);
 }
 
-template <bool H, bool IN>
+template <bool H, bool IN, int TB = 0>
 __device__ __forceinline__ void seg1(const SearchParams &P, const Epochs &ep,
                                      const TrajC &c, int lane, int e0, int e1,
-                                     Acc &s) {
+                                     Acc &s, const float4 *tab = nullptr) {
 #pragma unroll (IN ? kUnroll : 2)
   for (int e = lane_start(e0, lane); e < e1; e += 32) {
     const float2 v = ep.tw[e];
     const float wf = ep.wf[e];
-    acc_add(s, v.y, wf, IN ? mag_in_m1<H>(P, c, v.x) : mag_out_m1(c, v.x));
+    acc_add(s, v.y, wf,
+            IN ? mag_in_m1<H, TB>(P, c, v.x, tab) : mag_out_m1(c, v.x));
   }
 }
 
 // two trajectories over one epoch segment, one epoch load for both
-template <bool H, bool INA, bool INB>
+template <bool H, bool INA, bool INB, int TB = 0>
 __device__ __forceinline__ void seg2(const SearchParams &P, const Epochs &ep,
                                      const TrajC &ca, const TrajC &cb,
                                      int lane, int e0, int e1, Acc &sa,
-                                     Acc &sb) {
+                                     Acc &sb, const float4 *tab = nullptr) {
 #pragma unroll ((INA || INB) ? kUnroll : 2)
   for (int e = lane_start(e0, lane); e < e1; e += 32) {
     const float2 v = ep.tw[e];
     const float wf = ep.wf[e];
-    acc_add(sa, v.y, wf, INA ? mag_in_m1<H>(P, ca, v.x) : mag_out_m1(ca, v.x));
-    acc_add(sb, v.y, wf, INB ? mag_in_m1<H>(P, cb, v.x) : mag_out_m1(cb, v.x));
+    acc_add(sa, v.y, wf,
+            INA ? mag_in_m1<H, TB>(P, ca, v.x, tab) : mag_out_m1(ca, v.x));
+    acc_add(sb, v.y, wf,
+            INB ? mag_in_m1<H, TB>(P, cb, v.x, tab) : mag_out_m1(cb, v.x));
   }
 }
 
@@ -369,12 +450,13 @@ __device__ __forceinline__ Acc acc_reduce(Acc s) {
 // Phase 1: FP32 sums of S_A = sum w (A-1), S_AA = sum w (A-1)^2 and
 // S_AF = sum w (F-Fref)(A-1) over the epochs before, inside and after the
 // map, reduced across the warp.
-template <bool H>
+template <bool H, int TB = 0>
 __device__ __forceinline__ Acc phase1(const SearchParams &P, const Epochs &ep,
-                                      const TrajC &c, const int lane) {
+                                      const TrajC &c, const int lane,
+                                      const float4 *tab = nullptr) {
   Acc s = {0.f, 0.f, 0.f};
   seg1<H, false>(P, ep, c, lane, 0, c.e_in, s);
-  seg1<H, true>(P, ep, c, lane, c.e_in, c.e_out, s);
+  seg1<H, true, TB>(P, ep, c, lane, c.e_in, c.e_out, s, tab);
   seg1<H, false>(P, ep, c, lane, c.e_out, P.n_ep, s);
   return acc_reduce(s);
 }
@@ -382,11 +464,12 @@ __device__ __forceinline__ Acc phase1(const SearchParams &P, const Epochs &ep,
 // Phase 1 of two trajectories at once: the epoch axis is cut at both
 // trajectories' map entry and exit, and each segment runs the matching
 // inside/outside combination with one epoch load per lane for both.
-template <bool H>
+template <bool H, int TB = 0>
 __device__ __forceinline__ void phase1_pair(const SearchParams &P,
                                             const Epochs &ep, const TrajC &ca,
                                             const TrajC &cb, const int lane,
-                                            Acc &ra, Acc &rb) {
+                                            Acc &ra, Acc &rb,
+                                            const float4 *tab = nullptr) {
   Acc sa = {0.f, 0.f, 0.f}, sb = {0.f, 0.f, 0.f};
   // cut points, sorted (warp-uniform)
   int p1 = ca.e_in, p2 = ca.e_out, p3 = cb.e_in, p4 = cb.e_out, t;
@@ -403,11 +486,11 @@ __device__ __forceinline__ void phase1_pair(const SearchParams &P,
     const bool ina = e0 >= ca.e_in && e1 <= ca.e_out;
     const bool inb = e0 >= cb.e_in && e1 <= cb.e_out;
     if (ina && inb)
-      seg2<H, true, true>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+      seg2<H, true, true, TB>(P, ep, ca, cb, lane, e0, e1, sa, sb, tab);
     else if (ina)
-      seg2<H, true, false>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+      seg2<H, true, false, TB>(P, ep, ca, cb, lane, e0, e1, sa, sb, tab);
     else if (inb)
-      seg2<H, false, true>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+      seg2<H, false, true, TB>(P, ep, ca, cb, lane, e0, e1, sa, sb, tab);
     else
       seg2<H, false, false>(P, ep, ca, cb, lane, e0, e1, sa, sb);
   }
@@ -418,11 +501,12 @@ __device__ __forceinline__ void phase1_pair(const SearchParams &P,
 // Phase 2: chi^2 = sum w (F - Fs A - Fb)^2, written with centred values as
 // w (Fc - Fs Ac - Bc)^2, Bc = Fs + Fb - Fref.  FP32 per lane, FP64 across
 // lanes; lane 0's value is returned to all lanes.
-template <bool H>
+template <bool H, int TB = 0>
 __device__ __forceinline__ double phase2(const SearchParams &P,
                                          const Epochs &ep, const TrajC &c,
                                          const int lane, const float Fs,
-                                         const float Bc) {
+                                         const float Bc,
+                                         const float4 *tab = nullptr) {
   float chi = 0.f;
 #pragma unroll 2
   for (int e = lane_start(0, lane); e < c.e_in; e += 32) {
@@ -434,7 +518,7 @@ __device__ __forceinline__ double phase2(const SearchParams &P,
 #pragma unroll (kUnroll)
   for (int e = lane_start(c.e_in, lane); e < c.e_out; e += 32) {
     const float2 v = ep.tw[e];
-    const float Ac = mag_in_m1<H>(P, c, v.x);
+    const float Ac = mag_in_m1<H, TB>(P, c, v.x, tab);
     const float r = __fsub_rn(ep.fc[e], __fmaf_rn(Fs, Ac, Bc));
     chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
   }

@@ -119,13 +119,14 @@ __device__ inline void warp_merge(const SearchParams &P, BlockTopK &T, const int
 // Phase 1 in pairs of trajectories, the FP64 solve, the pruning test
 // against min(block K-th, grid-wide threshold), phase 2 for the survivors,
 // then the dense store or the merge into the block's top-K.
-template <bool DENSE, bool H>
+template <bool DENSE, bool H, int TB = 0>
 __device__ __forceinline__ void search_group(const SearchParams &P,
                                              const Epochs &ep, BlockTopK &T,
                                              const int K, const int warp,
                                              const int lane, long long lo,
                                              long long hi, const bool lined,
-                                             unsigned long long &n_exact) {
+                                             unsigned long long &n_exact,
+                                             const float4 *tab = nullptr) {
   const int nvalid = (int)max(0LL, hi - lo);
   if (nvalid == 0) return;  // warp-uniform
   if (P.linemax && lined &&
@@ -149,11 +150,11 @@ __device__ __forceinline__ void search_group(const SearchParams &P,
     if (k + 1 < nvalid) {
       const TrajC cb = shfl_traj(mine, k + 1);
       Acc ra, rb;
-      phase1_pair<H>(P, ep, ca, cb, lane, ra, rb);
+      phase1_pair<H, TB>(P, ep, ca, cb, lane, ra, rb, tab);
       if (lane == k) mine_s = ra;
       if (lane == k + 1) mine_s = rb;
     } else {
-      const Acc ra = phase1<H>(P, ep, ca, lane);
+      const Acc ra = phase1<H, TB>(P, ep, ca, lane, tab);
       if (lane == k) mine_s = ra;
     }
   }
@@ -179,7 +180,7 @@ __device__ __forceinline__ void search_group(const SearchParams &P,
     const TrajC c = shfl_traj(mine, k);
     const float Fs = __shfl_sync(kFull, myFs, k);
     const float Bc = __shfl_sync(kFull, myBc, k);
-    const double chi2 = phase2<H>(P, ep, c, lane, Fs, Bc);
+    const double chi2 = phase2<H, TB>(P, ep, c, lane, Fs, Bc, tab);
     if (lane == k) my_chi2 = isnan(chi2) ? CUDART_INF : chi2;
   }
   if (DENSE) {

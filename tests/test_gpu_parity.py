@@ -205,6 +205,33 @@ def test_ragged_grids_and_k_beyond_size(ctx, m, dims, k):
     assert np.max(_rel(chi2, o_chi2)) <= CHI2_RTOL
 
 
+def test_band_tables_equal_global_lookups(ctx, m):
+    """A grid with 16 warp groups per line (20 t0 x 10 tE) reads its cells
+    from the shared-memory band tables: dense chi^2 and top-K equal the
+    oracle's, and the top-K records equal, bit for bit, those of the batched
+    search of the same pair, which reads the global table.  The lines
+    include the axis-parallel and diagonal directions (alpha = k pi / 4) and
+    an odd map size."""
+    c = synth.CFG0
+    for npix, L in ((96, 2.0), (127, 1.5)):
+        A_o, *_ = orc.build_map(0.9, 0.02, L, npix, 900, 3.0, nthreads=NT)
+        mp = ctx.map_from_host(A_o, L)
+        t, F, sig = _event(c, n=180, seed=11)
+        ev = ctx.event(t, F, sig)
+        g = m.Grid.make(3, 8, 20, 10, 0.02, 0.6, -1.5, 1.5, 6.0, 50.0, True,
+                        True, 24)
+        og = orc.Grid(3, 8, 20, 10, 0.02, 0.6, -1.5, 1.5, 6.0, 50.0)
+        o_chi2, *_ = orc.grid_chi2(og, t, F, 1.0 / sig ** 2, A=A_o, L=L,
+                                   nthreads=NT)
+        chi2, fs, fb = ctx.grid_chi2_dense(ev, mp, g)
+        assert np.max(_rel(chi2, o_chi2)) <= CHI2_RTOL
+        got = ctx.grid_chi2(ev, mp, g)
+        assert _check_topk(got, o_chi2, 24) == 0
+        bat = ctx.grid_chi2_batch([ev], [mp], g)[0, 0]
+        for f in ("chi2", "t0", "tE", "u0", "alpha", "Fs", "Fb", "idx"):
+            np.testing.assert_array_equal(got[f], bat[f])
+
+
 def test_dense_subrange(ctx, m, cfg0_maps, cfg0_event):
     mp, A_o, *_ = cfg0_maps
     t, F, sig, ev = cfg0_event
