@@ -276,22 +276,28 @@ def adjoint_section(ctx, m, cfg, ev, n_ep, stream, probes, peak_instr_s,
                    cfg["tE"] * np.exp(rng.uniform(-0.3, 0.3, n)),
                    cfg["u0"] * np.exp(rng.uniform(-0.5, 0.5, n)),
                    cfg["alpha"] + rng.uniform(-0.2, 0.2, n)], axis=1)
-    theta = torch.tensor(th, dtype=torch.float64, device="cuda")
-    chi2 = torch.empty(n, dtype=torch.float64, device="cuda")
-    grad = torch.empty((n, 4), dtype=torch.float64, device="cuda")
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            ctx.chi2_grad_dev(ev, mp, theta, chi2, grad)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        reps = 10
-        e0.record(stream)
-        for _ in range(reps):
-            ctx.chi2_grad_dev(ev, mp, theta, chi2, grad)
-        e1.record(stream)
-        e1.synchronize()
-    ms = e0.elapsed_time(e1) / reps
+    def grad_ms(th_):
+        theta = torch.tensor(th_, dtype=torch.float64, device="cuda")
+        nn = theta.shape[0]
+        chi2 = torch.empty(nn, dtype=torch.float64, device="cuda")
+        grad = torch.empty((nn, 4), dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                ctx.chi2_grad_dev(ev, mp, theta, chi2, grad)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            reps = 10
+            e0.record(stream)
+            for _ in range(reps):
+                ctx.chi2_grad_dev(ev, mp, theta, chi2, grad)
+            e1.record(stream)
+            e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+    ms = grad_ms(th)
     evals = n * n_ep / (ms * 1e-3)
+    # the same trajectories 32 times over: enough warps to fill the GPU
+    ms_big = grad_ms(np.tile(th, (32, 1)))
+    evals_big = 32 * n * n_ep / (ms_big * 1e-3)
     peak_instr = peak_instr_s / 36.0
     peak_gather = probes["l1_gather_bytes_per_s"] / 16.0
     starts = np.zeros(n, dtype=m.FIT_DTYPE)
@@ -308,6 +314,8 @@ def adjoint_section(ctx, m, cfg, ev, n_ep, stream, probes, peak_instr_s,
             "grad_evals_per_s": evals,
             "frac_fp32_issue": evals / peak_instr,
             "frac_l1_gather": evals / peak_gather,
+            "grad_evals_per_s_131072": evals_big,
+            "frac_fp32_issue_131072": evals_big / peak_instr,
             "roofline_note": "36 FP32 instr (22 + 14 for the gradient) and "
                              "16 B per evaluation; peaks: the search's FP32 "
                              "issue peak and the measured L1 gather",
