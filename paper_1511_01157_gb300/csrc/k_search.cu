@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
       T.wbuf = T.buf1 + K;
       p += sizeof(Entry) * ((size_t)2 * K + kSearchWarps * 32);
     }
-    if (!H && P.tab_n > 0) tabs = reinterpret_cast<float4 *>(p);
+    if (P.tab_n > 0) tabs = reinterpret_cast<float4 *>(p);
     T.cur = &s_cur;
     T.nk = &s_nk;
     T.lock = &s_lock;
@@ -165,8 +165,8 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
     }
     got = __shfl_sync(kFull, got, 0);
     if (!got) return;
-    const int tb = build_band(P, tabs + (size_t)b * P.tab_n, cx, cy, c, s,
-                              lane);
+    const int tb = build_band<H>(P, tabs + (size_t)b * P.tab_n, cx, cy, c,
+                                 s, lane);
     __threadfence_block();
     __syncwarp();
     if (lane == 0) {

@@ -550,6 +550,7 @@ morse_status hdr_check(morse_ctx *ctx, const Hdr &h) {
     return fail(ctx, MORSE_ECUDA,
                 "bounds check: a band-table lookup read another cell than "
                 "the map's (error 0x%x); results are invalid", h.err);
+
   if (h.err & 1u)
     return fail(ctx, MORSE_ETIMEOUT,
                 "a search block could not take its top-K lock (error 0x%x); "
@@ -569,10 +570,11 @@ morse_status plan_search(morse_ctx *ctx, const morse_event *ev,
   const bool ep_smem =
       budget > fixed && (size_t)ev->n <= (budget - fixed) / sizeof(float4);
   size_t smem = fixed + (ep_smem ? sizeof(float4) * (size_t)ev->n : 0);
-  // band tables: FP32 cells, one line per block round (kSearchWarps groups
-  // per line), two tables in the remaining shared memory, bounded motion
+  // band tables: FP32 cells (decoded from the FP16 table when the search
+  // reads that one), one line per block round (kSearchWarps groups per
+  // line), two tables in the remaining shared memory, bounded motion
   pl->tab_n = 0;
-  if (band.npix >= 2 && !h16) {
+  if (band.npix >= 2) {
     const long long line = (long long)g->n_t0 * g->n_tE;
     const int tpg = morse::line_tpg(line);
     const double dlt = 2.0 * band.L / band.npix;

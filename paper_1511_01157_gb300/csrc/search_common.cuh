@@ -261,82 +261,6 @@ __device__ __forceinline__ float bilinear_m1(const SearchParams &P, float vx,
   return __fmaf_rn(t.fy, __fsub_rn(r1, r0), r0);
 }
 
-// Band table of one line of the line-aligned pass, in shared memory.  For
-// a line closer to the first axis (|cos alpha| >= |sin alpha|, TB = 1) the
-// table holds, for every cell column X, the cells of rows row0(X) ..
-// row0(X) + 3 around the line, at key X + (npix + 1) ((Y + C) & 3) with C
-// the floor bits' offset: four consecutive rows have distinct low bits, so
-// the key is the cell's own, and neighbouring columns are neighbouring
-// entries (a warp's lookups along the line fall in distinct banks).  The line meets at most rows floor(yc - 1/2) ..
-// floor(yc + 1/2) of a column (|slope| <= 1, yc its height at the column
-// centre), and row0 = floor(yc) - 1 takes them with 1/4 texel to spare on
-// each side, far beyond the FP32 rounding of a trajectory's position
-// (below 1e-2 texel for |a t| < 1e5 texels, which the host checks).  So a
-// band lookup reads the same 16 bytes as the global table, from shared
-// memory.  TB = 2: rows and columns swapped.
-template <int TB>
-__device__ __forceinline__ float bilinear_tab_m1(const SearchParams &P,
-                                                 const float4 *tab, float vx,
-                                                 float vy) {
-  const float tx = __fadd_rd(vx, 12582912.f), ty = __fadd_rd(vy, 12582912.f);
-  const float fx = __fsub_rn(vx, __fsub_rn(tx, 12582912.f));
-  const float fy = __fsub_rn(vy, __fsub_rn(ty, 12582912.f));
-  const unsigned bx = (unsigned)__float_as_int(tx);
-  const unsigned by = (unsigned)__float_as_int(ty);
-  const unsigned S = (unsigned)P.npix + 1u;
-  const unsigned key = TB == 1 ? (bx + P.tab_c) + S * (by & 3u)
-                               : (by + P.tab_c) + S * (bx & 3u);
-#ifdef MORSE_CHECK_BOUNDS
-  // checked build: the band entry must be the global table's cell
-  TexPos t;
-  if (!tex_pos(P, vx, vy, t)) return 0.f;
-  if (key >= (unsigned)P.tab_n) {
-    if (P.err) atomicOr(P.err, 4u);
-    return 0.f;
-  }
-  {
-    const float4 g = __ldg(&P.quad[t.idx]), b = tab[key];
-    if (g.x != b.x || g.y != b.y || g.z != b.z || g.w != b.w)
-      if (P.err) atomicOr(P.err, 4u);
-  }
-#endif
-  const float4 q = tab[key];
-  const float r0 = __fmaf_rn(fx, q.y, q.x);
-  const float r1 = __fmaf_rn(fx, q.w, q.z);
-  return __fmaf_rn(fy, __fsub_rn(r1, r0), r0);
-}
-
-// Fill the band table of the line through the centred point (cx, cy) with
-// direction (c, s) (warp-collective); returns TB (1 or 2).
-__device__ inline int build_band(const SearchParams &P, float4 *tab,
-                                 double cx, double cy, double c, double s,
-                                 int lane) {
-  const bool xm = fabs(c) >= fabs(s);
-  const int n = P.npix;
-  // along the major axis m, the minor coordinate of the line is
-  // w(m) = w0 + slope (m - m0)
-  const float slope = (float)(xm ? s / c : c / s);
-  const float m0 = (float)(xm ? cx : cy), w0 = (float)(xm ? cy : cx);
-  const unsigned C = 0x4B400000u - (unsigned)(P.half + 1);
-  const float lim = 4.f * (float)n + 8.f;
-  for (int M = lane; M <= n; M += 32) {
-    const float mc = (float)(M - P.half) - 0.5f;  // centre of cell M
-    float wc = __fmaf_rn(slope, mc - m0, w0);
-    wc = fminf(fmaxf(wc, -lim), lim);
-    const int r0 = (int)floorf(wc) + P.half;  // cell of the centre, less 1
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      const int W = r0 + d;
-      const int Wc = min(max(W, 0), n);
-      const unsigned key =
-          (unsigned)M + (unsigned)(n + 1) * (((unsigned)W + C) & 3u);
-      tab[key] = xm ? P.quad[cell_index(M, Wc, P.qpitch)]
-                    : P.quad[cell_index(Wc, M, P.qpitch)];
-    }
-  }
-  return xm ? 1 : 2;
-}
-
 // Lanes own epochs by index mod 32 in every range, so a lane always sums
 // its terms in ascending epoch order whatever the ranges are: the sums of a
 // trajectory do not depend on how its epoch axis is cut into segments (the
@@ -387,6 +311,104 @@ __device__ __forceinline__ float bilinear_h_m1(const SearchParams &P,
   return __fsub_rn(__fmaf_rn(t.fy, __fsub_rn(r1, r0), r0), 1.f);
 }
 
+// An FP16 cell decoded as the FP16 bilinear reads it: the four texels
+// 10^x and the two differences along the first axis.
+__device__ __forceinline__ float4 band_cell_h(const uint2 q) {
+  const float2 lo = __half22float2(
+      __halves2half2(__ushort_as_half((unsigned short)(q.x & 0xffffu)),
+                     __ushort_as_half((unsigned short)(q.x >> 16))));
+  const float2 hi = __half22float2(
+      __halves2half2(__ushort_as_half((unsigned short)(q.y & 0xffffu)),
+                     __ushort_as_half((unsigned short)(q.y >> 16))));
+  const float a00 = exp10_texel(lo.x), a10 = exp10_texel(lo.y);
+  const float a01 = exp10_texel(hi.x), a11 = exp10_texel(hi.y);
+  return make_float4(a00, __fsub_rn(a10, a00), a01, __fsub_rn(a11, a01));
+}
+
+// Band table of one line of the line-aligned pass, in shared memory.  For
+// a line closer to the first axis (|cos alpha| >= |sin alpha|, TB = 1) the
+// table holds, for every cell column X, the cells of rows row0(X) ..
+// row0(X) + 3 around the line, at key X + (npix + 1) ((Y + C) & 3) with C
+// the floor bits' offset: four consecutive rows have distinct low bits, so
+// the key is the cell's own, and neighbouring columns are neighbouring
+// entries (a warp's lookups along the line fall in distinct banks).  The line meets at most rows floor(yc - 1/2) ..
+// floor(yc + 1/2) of a column (|slope| <= 1, yc its height at the column
+// centre), and row0 = floor(yc) - 1 takes them with 1/4 texel to spare on
+// each side, far beyond the FP32 rounding of a trajectory's position
+// (below 1e-2 texel for |a t| < 1e5 texels, which the host checks).  So a
+// band lookup reads the same 16 bytes as the global table, from shared
+// memory.  TB = 2: rows and columns swapped.  For the FP16 log10 table
+// (H) the band holds the decoded texels in the same pre-differenced form,
+// (a00, a10 - a00, a01, a11 - a01), so the four exponentials of a lookup
+// are taken once per cell when the band is built, and the lookup is the
+// FP16 bilinear's own arithmetic.
+template <int TB, bool H>
+__device__ __forceinline__ float bilinear_tab_m1(const SearchParams &P,
+                                                 const float4 *tab, float vx,
+                                                 float vy) {
+  const float tx = __fadd_rd(vx, 12582912.f), ty = __fadd_rd(vy, 12582912.f);
+  const float fx = __fsub_rn(vx, __fsub_rn(tx, 12582912.f));
+  const float fy = __fsub_rn(vy, __fsub_rn(ty, 12582912.f));
+  const unsigned bx = (unsigned)__float_as_int(tx);
+  const unsigned by = (unsigned)__float_as_int(ty);
+  const unsigned S = (unsigned)P.npix + 1u;
+  const unsigned key = TB == 1 ? (bx + P.tab_c) + S * (by & 3u)
+                               : (by + P.tab_c) + S * (bx & 3u);
+#ifdef MORSE_CHECK_BOUNDS
+  // checked build: the band entry must be the global table's cell
+  TexPos t;
+  if (!tex_pos(P, vx, vy, t)) return 0.f;
+  if (key >= (unsigned)P.tab_n) {
+    if (P.err) atomicOr(P.err, 4u);
+    return 0.f;
+  }
+  {
+    const float4 g = H ? band_cell_h(P.quadh[t.idx]) : __ldg(&P.quad[t.idx]);
+    const float4 b = tab[key];
+    if (g.x != b.x || g.y != b.y || g.z != b.z || g.w != b.w)
+      if (P.err) atomicOr(P.err, 4u);
+  }
+#endif
+  const float4 q = tab[key];
+  const float r0 = __fmaf_rn(fx, q.y, q.x);
+  const float r1 = __fmaf_rn(fx, q.w, q.z);
+  const float a = __fmaf_rn(fy, __fsub_rn(r1, r0), r0);
+  return H ? __fsub_rn(a, 1.f) : a;
+}
+
+// Fill the band table of the line through the centred point (cx, cy) with
+// direction (c, s) (warp-collective); returns TB (1 or 2).
+template <bool H>
+__device__ inline int build_band(const SearchParams &P, float4 *tab,
+                                 double cx, double cy, double c, double s,
+                                 int lane) {
+  const bool xm = fabs(c) >= fabs(s);
+  const int n = P.npix;
+  // along the major axis m, the minor coordinate of the line is
+  // w(m) = w0 + slope (m - m0)
+  const float slope = (float)(xm ? s / c : c / s);
+  const float m0 = (float)(xm ? cx : cy), w0 = (float)(xm ? cy : cx);
+  const unsigned C = 0x4B400000u - (unsigned)(P.half + 1);
+  const float lim = 4.f * (float)n + 8.f;
+  for (int M = lane; M <= n; M += 32) {
+    const float mc = (float)(M - P.half) - 0.5f;  // centre of cell M
+    float wc = __fmaf_rn(slope, mc - m0, w0);
+    wc = fminf(fmaxf(wc, -lim), lim);
+    const int r0 = (int)floorf(wc) + P.half;  // cell of the centre, less 1
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const int W = r0 + d;
+      const int Wc = min(max(W, 0), n);
+      const unsigned key =
+          (unsigned)M + (unsigned)(n + 1) * (((unsigned)W + C) & 3u);
+      const size_t ci = xm ? cell_index(M, Wc, P.qpitch)
+                           : cell_index(Wc, M, P.qpitch);
+      tab[key] = H ? band_cell_h(P.quadh[ci]) : P.quad[ci];
+    }
+  }
+  return xm ? 1 : 2;
+}
+
 // A - 1 at time t inside the map (bilinear) or outside (single lens)
 // (H: the FP16 log10 table)
 template <bool H, int TB = 0>
@@ -394,7 +416,7 @@ __device__ __forceinline__ float mag_in_m1(const SearchParams &P,
                                            const TrajC &c, float t,
                                            const float4 *tab = nullptr) {
   const float vx = __fmaf_rn(c.ax, t, c.bx), vy = __fmaf_rn(c.ay, t, c.by);
-  if (TB != 0) return bilinear_tab_m1<TB>(P, tab, vx, vy);
+  if (TB != 0) return bilinear_tab_m1<TB, H>(P, tab, vx, vy);
   return H ? bilinear_h_m1(P, vx, vy) : bilinear_m1(P, vx, vy);
 }
 __device__ __forceinline__ float mag_out_m1(const TrajC &c, float t) {
