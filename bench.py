@@ -265,9 +265,13 @@ def adjoint_section(ctx, m, cfg, ev, n_ep, stream, probes, peak_instr_s,
     event: n = 4096 trajectories scattered about the truth (the refinement
     workload's start count).  chi^2 and its gradient by morse_chi2_grad_dev
     (device buffers, CUDA events on the context's stream), evals/s against
-    the FP32-issue roofline (22 + 14 instructions per evaluation) and the
-    L1 gather roofline (16 B); then `iters` Levenberg-Marquardt iterations of
-    all n (morse_refine, a CUDA graph per iteration) timed end to end."""
+    the FP32-issue roofline and the L1 gather roofline.  The adjoint sweeps
+    the epochs twice (the sums of the 2x2 solve, then the residuals and the
+    gradient: the residual form keeps the gradient exact near the minimum,
+    where sums of large terms would cancel), so an evaluation is 22 + 36
+    FP32 instructions and two 16-byte gathers.  Then `iters`
+    Levenberg-Marquardt iterations of all n (morse_refine, a CUDA graph per
+    iteration) timed end to end."""
     import torch
     mp = ctx.build_map(cfg["s"], cfg["q"], cfg["L"], cfg["npix"], cfg["nray"],
                        image_halfwidth=cfg["X"], deflect="fp32")
@@ -298,8 +302,8 @@ def adjoint_section(ctx, m, cfg, ev, n_ep, stream, probes, peak_instr_s,
     # the same trajectories 32 times over: enough warps to fill the GPU
     ms_big = grad_ms(np.tile(th, (32, 1)))
     evals_big = 32 * n * n_ep / (ms_big * 1e-3)
-    peak_instr = peak_instr_s / 36.0
-    peak_gather = probes["l1_gather_bytes_per_s"] / 16.0
+    peak_instr = peak_instr_s / 58.0
+    peak_gather = probes["l1_gather_bytes_per_s"] / 32.0
     starts = np.zeros(n, dtype=m.FIT_DTYPE)
     starts["t0"], starts["tE"], starts["u0"], starts["alpha"] = th.T
     starts["chi2"] = np.inf
@@ -316,9 +320,9 @@ def adjoint_section(ctx, m, cfg, ev, n_ep, stream, probes, peak_instr_s,
             "frac_l1_gather": evals / peak_gather,
             "grad_evals_per_s_131072": evals_big,
             "frac_fp32_issue_131072": evals_big / peak_instr,
-            "roofline_note": "36 FP32 instr (22 + 14 for the gradient) and "
-                             "16 B per evaluation; peaks: the search's FP32 "
-                             "issue peak and the measured L1 gather",
+            "roofline_note": "two sweeps per evaluation: 22 + 36 FP32 instr "
+                             "and 2 x 16 B; peaks: the search's FP32 issue "
+                             "peak and the measured L1 gather",
             "refine_iters": iters, "refine_s": t_ref,
             "refine_iters_per_s": n * iters / t_ref,
             "refine_median_chi2": float(np.median(out["chi2"]))}
