@@ -585,8 +585,12 @@ morse_status plan_search(morse_ctx *ctx, const morse_event *ev,
                      (band.u_max + band.shift_max) / dlt + 1.0;
     const int n = 4 * (band.npix + 1);
     const size_t tb = 2 * sizeof(float4) * (size_t)n;
+    // a band costs one warp about the time of 4 (npix + 1) L2 reads (some
+    // ten microseconds); a round must be long enough to hide it: at least
+    // 4e5 trajectory-epochs per line (a group of config 1 is 1.5e5)
+    const bool worth = (double)line * (double)ev->n >= 4e5;
     if ((line + tpg - 1) / tpg == morse::kSearchWarps && tE_min > 0.0 &&
-        B <= 1e5 && smem + tb <= budget) {
+        B <= 1e5 && smem + tb <= budget && worth) {
       pl->tab_n = n;
       smem += tb;
     }

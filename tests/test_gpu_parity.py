@@ -216,7 +216,7 @@ def test_band_tables_equal_global_lookups(ctx, m):
     for npix, L in ((96, 2.0), (127, 1.5)):
         A_o, *_ = orc.build_map(0.9, 0.02, L, npix, 900, 3.0, nthreads=NT)
         mp = ctx.map_from_host(A_o, L)
-        t, F, sig = _event(c, n=180, seed=11)
+        t, F, sig = _event(c, n=2000, seed=11)  # 4e5 per line: tables on
         ev = ctx.event(t, F, sig)
         g = m.Grid.make(3, 8, 20, 10, 0.02, 0.6, -1.5, 1.5, 6.0, 50.0, True,
                         True, 24)
