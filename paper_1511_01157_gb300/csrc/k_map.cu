@@ -66,6 +66,13 @@ __device__ __forceinline__ int deflect64(const RayParams &P, long long i,
 }
 
 // FP32 deflection: one approximate reciprocal of r1 r2 serves both lenses.
+// The bin of v by one add rounded down: adding 1.5 * 2^23 leaves floor(v)
+// in the low mantissa bits for |v| < 2^22; any other v (far off the map,
+// infinite, NaN) gives a value that the unsigned range test rejects.
+__device__ __forceinline__ unsigned bin_of(float v) {
+  return (unsigned)__float_as_int(__fadd_rd(v, 12582912.f)) - 0x4B400000u;
+}
+
 __device__ __forceinline__ int deflect32(const RayParams &P, float x1,
                                          float x2, float x2sq, int *ix,
                                          int *iy) {
@@ -80,23 +87,24 @@ __device__ __forceinline__ int deflect32(const RayParams &P, float x1,
   float a2 = P.e2f * (r1 * inv);
   float y1 = fmaf(-a2, d2, fmaf(-a1, d1, x1));
   float y2 = fmaf(-(a1 + a2), x2, x2);
-  float v1 = fmaf(y1, P.invdf, P.offf);
-  float v2 = fmaf(y2, P.invdf, P.offf);
-  if (!(v1 >= 0.0f && v1 < P.npixf && v2 >= 0.0f && v2 < P.npixf)) return 1;
-  int a = (int)v1, b = (int)v2;
-  if (a >= P.npix || b >= P.npix) return 1;
-  *ix = a;
-  *iy = b;
+  const unsigned a = bin_of(fmaf(y1, P.invdf, P.offf));
+  const unsigned b = bin_of(fmaf(y2, P.invdf, P.offf));
+  if (a >= (unsigned)P.npix || b >= (unsigned)P.npix) return 1;
+  *ix = (int)a;
+  *iy = (int)b;
   return 0;
 }
 
 // Bin of a sample ray (FP64), clamped into the map; used only to place the
 // shared-memory window, never to count.
+// Bin of ray (i, j) for placing a tile's window (a cache: where a ray is
+// binned does not change the counts), in FP32 for both paths.
 __device__ bool sample_bin(const RayParams &P, long long i, long long j,
                            int *bx, int *by) {
-  double x2 = -P.X + ((double)j + 0.5) * P.h;
+  const float x2 = fmaf((float)j, P.hf, P.x0f);
+  const float x1 = fmaf((float)i, P.hf, P.x0f);
   int ix = 0, iy = 0;
-  int st = deflect64(P, i, x2, x2 * x2, &ix, &iy);
+  const int st = deflect32(P, x1, x2, x2 * x2, &ix, &iy);
   if (st != 0) return false;
   *bx = ix;
   *by = iy;
@@ -152,6 +160,9 @@ __global__ void __launch_bounds__(kRayThreads)
     const int wx0 = s_wx, wy0 = s_wy;
     const long long ib = i0 + sx * kSubX;
     const long long jb = j0 + sy * kSubY;
+    // rays of the sub-block row inside the grid, and the first one's x1
+    const int na = (int)max(0LL, min((long long)kSubX, P.nray - ib));
+    const float x1b = fmaf((float)ib, P.hf, P.x0f);
 #pragma unroll 1
     for (int b = 0; b < kSubY; ++b) {
       const long long j = jb + b;
@@ -167,13 +178,12 @@ __global__ void __launch_bounds__(kRayThreads)
       }
 #pragma unroll
       for (int a = 0; a < kSubX; ++a) {
-        const long long i = ib + a;
-        if (i < P.nray) {
+        if (a < na) {
           int ix = 0, iy = 0, st;
           if (FP64)
-            st = deflect64(P, i, x2d, x2sqd, &ix, &iy);
+            st = deflect64(P, ib + a, x2d, x2sqd, &ix, &iy);
           else
-            st = deflect32(P, fmaf((float)i, P.hf, P.x0f), x2f, x2sqf, &ix,
+            st = deflect32(P, fmaf((float)a, P.hf, x1b), x2f, x2sqf, &ix,
                            &iy);
           if (st == 0) {
             unsigned lx = (unsigned)(ix - wx0), ly = (unsigned)(iy - wy0);
