@@ -38,7 +38,7 @@
 //    minimum of K-th values (atomicMin on the bit pattern) are the pruning
 //    threshold.  The grid-wide value is seeded by a pilot search over a
 //    strided subset of about sqrt(K N) trajectories, so that it is tight
-//    from the start.  A tree of pairwise merges gives the global
+//    from the start.  A tree of 4-way merges gives the global
 //    top-K and k_fill recomputes the winners' records with the same device
 //    functions.
 #include <cuda_runtime.h>
@@ -263,35 +263,37 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
   }
 }
 
-// One level of the merge tree: list pairs (2p, 2p+1) -> list p, keeping the
-// first k of each merged pair.  An odd last list is copied.
+// One level of the merge tree: lists 4p .. 4p + 3 -> list p, keeping the
+// first k of their union (a short last group merges what it has).
+constexpr int kMergeWays = 4;  // lists merged into one per level
+
 __global__ void k_merge_level(const Entry *__restrict__ in,
                               Entry *__restrict__ out, int lists, int k) {
-  const int pairs = (lists + 1) / 2;
-  const long long total = (long long)pairs * 2 * k;
+  // one thread per input entry: its rank in its group of kMergeWays lists
+  // is its index plus the entries of the group's other lists below it
+  // (keys are unique across lists), and the first k ranks are kept
+  const long long total = (long long)lists * k;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
        t < total; t += (long long)gridDim.x * blockDim.x) {
-    const int p = (int)(t / (2 * k));
-    const int side = (int)((t / k) & 1);
-    const int i = (int)(t % k);
-    const int la = 2 * p, lb = 2 * p + 1;
-    if (lb >= lists) {  // odd list out: copy
-      if (side == 0) out[(size_t)p * k + i] = in[(size_t)la * k + i];
-      continue;
+    const int l = (int)(t / k), i = (int)(t % k);
+    const int grp = l / kMergeWays, l0 = grp * kMergeWays;
+    const int l1 = min(l0 + kMergeWays, lists);
+    const Entry e = in[(size_t)l * k + i];
+    int r = i;
+    for (int m = l0; m < l1; ++m) {
+      if (m == l) continue;
+      const Entry *B = in + (size_t)m * k;
+      int lo = 0, hi = k;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (key_less(B[mid], e))
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      r += lo;
     }
-    const Entry *A = in + (size_t)(side ? lb : la) * k;
-    const Entry *B = in + (size_t)(side ? la : lb) * k;
-    const Entry e = A[i];
-    int lo = 0, hi = k;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (key_less(B[mid], e))
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    const int r = i + lo;
-    if (r < k) out[(size_t)p * k + r] = e;
+    if (r < k) out[(size_t)grp * k + r] = e;
   }
 }
 
@@ -433,15 +435,14 @@ cudaError_t launch_topk_merge(Entry *a, Entry *b, int lists, int k,
   Entry *in = a, *out = b;
   *levels = 0;
   while (lists > 1) {
-    const int pairs = (lists + 1) / 2;
-    const long long total = (long long)pairs * 2 * k;
+    const long long total = (long long)lists * k;
     long long g = (total + 255) / 256;
     if (g > 65535) g = 65535;
     k_merge_level<<<(int)g, 256, 0, st>>>(in, out, lists, k);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ++*levels;
-    lists = pairs;
+    lists = (lists + kMergeWays - 1) / kMergeWays;
     Entry *t = in;
     in = out;
     out = t;
