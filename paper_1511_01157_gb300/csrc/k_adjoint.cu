@@ -46,15 +46,15 @@ __device__ __forceinline__ float in_grad(const SearchParams &P, const TrajC &c,
     return 0.f;
   }
   const float4 q = __ldg(&P.quad[p.idx]);
-  const float dx0 = q.y, dx1 = q.w;  // x-differences of the cell's rows
-  const float r0 = __fmaf_rn(p.fx, dx0, q.x);
-  const float r1 = __fmaf_rn(p.fx, dx1, q.z);
-  const float am1 = __fmaf_rn(p.fy, __fsub_rn(r1, r0), r0);
+  // q = (m00, m10 - m00, m01 - m00, second difference)
+  const float r0 = __fmaf_rn(p.fx, q.y, q.x);
+  const float dr = __fmaf_rn(p.fx, q.w, q.z);  // row difference at fx
+  const float am1 = __fmaf_rn(p.fy, dr, r0);
   // gradient in pixel units; the edge cells below and above the map have
   // zero differences across the edge, so the gradient there is zero along
   // that axis (the lookup is constant)
-  const float gx = __fmaf_rn(p.fy, __fsub_rn(dx1, dx0), dx0);
-  const float gy = __fsub_rn(r1, r0);
+  const float gx = __fmaf_rn(p.fy, q.w, q.y);
+  const float gy = dr;
   // per unit of y: divide by Delta
   const float Gx = __fmul_rn(gx, P.invDf), Gy = __fmul_rn(gy, P.invDf);
   const float Gp = __fmaf_rn(Gx, cs, __fmul_rn(Gy, sn));

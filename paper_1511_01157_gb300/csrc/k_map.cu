@@ -227,9 +227,10 @@ __global__ void __launch_bounds__(kRayThreads)
 // cell whose lower corner is texel (c - 1, r - 1): the column and row below
 // the map repeat its edge (so that a lookup below the first texel centre
 // reads the edge value, the clamping rule, without a clamp), and so do the
-// column and row at npix - 1.  The FP32 quad holds
-//   (a00 - 1, (a10 - 1) - (a00 - 1), a01 - 1, (a11 - 1) - (a01 - 1)),
-// the differences rounded in FP32 exactly as the lookup would take them.
+// column and row at npix - 1.  With m = A - 1 the FP32 quad holds
+//   (m00, m10 - m00, m01 - m00, (m11 - m01) - (m10 - m00)),
+// rounded in FP32, so that a lookup is three FMAs: the first row at fx,
+// the row difference at fx, and the value at fy.
 __device__ __forceinline__ int clampi(int v, int n) {
   return v < 0 ? 0 : (v >= n ? n - 1 : v);
 }
@@ -245,7 +246,8 @@ __device__ __forceinline__ float4 quad_of(float a00, float a10, float a01,
   // A - 1: FP32 of the FP32 value, exact for A <= 2
   const float m00 = a00 - 1.0f, m10 = a10 - 1.0f;
   const float m01 = a01 - 1.0f, m11 = a11 - 1.0f;
-  return make_float4(m00, __fsub_rn(m10, m00), m01, __fsub_rn(m11, m01));
+  const float d0 = __fsub_rn(m10, m00), d1 = __fsub_rn(m11, m01);
+  return make_float4(m00, d0, __fsub_rn(m01, m00), __fsub_rn(d1, d0));
 }
 
 __global__ void k_counts_to_map(const uint32_t *__restrict__ counts, int npix,

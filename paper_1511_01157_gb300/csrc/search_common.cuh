@@ -18,8 +18,11 @@
 namespace morse {
 namespace dev {
 
+// Inside-map epoch loops are unrolled twice: the band tables' shared
+// loads need little latency hiding, and the search's code must stay within
+// the instruction cache (unroll 4 measured 33 % slower, unroll 1 10 %).
 #ifndef MORSE_UNROLL
-#define MORSE_UNROLL 4
+#define MORSE_UNROLL 2
 #endif
 constexpr int kUnroll = MORSE_UNROLL;  // inside-map epoch loop
 
@@ -245,9 +248,11 @@ __device__ __forceinline__ bool tex_pos(const SearchParams &P, float vx,
   return true;
 }
 
-// Bilinear A - 1 at centred coordinates inside the map.  The quads store
-// (a00 - 1, a10 - a00, a01 - 1, a11 - a01) of the cell, the differences
-// rounded in FP32 when the table was built, so each row is one FMA.  Below
+// Bilinear A - 1 at centred coordinates inside the map.  The quads store,
+// with m = A - 1, (m00, m10 - m00, m01 - m00, (m11 - m01) - (m10 - m00))
+// of the cell, rounded in FP32 when the table was built: the first row at
+// fx, the difference of the rows at fx and the value at fy are one FMA
+// each.  Below
 // the first texel centre the edge cell repeats the edge values (the
 // clamping rule of the lookup); above the last centre likewise.  The
 // bounds-checked build verifies the index range.
@@ -257,8 +262,8 @@ __device__ __forceinline__ float bilinear_m1(const SearchParams &P, float vx,
   if (!tex_pos(P, vx, vy, t)) return 0.f;
   const float4 q = __ldg(&P.quad[t.idx]);
   const float r0 = __fmaf_rn(t.fx, q.y, q.x);
-  const float r1 = __fmaf_rn(t.fx, q.w, q.z);
-  return __fmaf_rn(t.fy, __fsub_rn(r1, r0), r0);
+  const float dr = __fmaf_rn(t.fx, q.w, q.z);
+  return __fmaf_rn(t.fy, dr, r0);
 }
 
 // Lanes own epochs by index mod 32 in every range, so a lane always sums
@@ -306,13 +311,14 @@ __device__ __forceinline__ float bilinear_h_m1(const SearchParams &P,
                      __ushort_as_half((unsigned short)(q.y >> 16))));
   const float a00 = exp10_texel(lo.x), a10 = exp10_texel(lo.y);
   const float a01 = exp10_texel(hi.x), a11 = exp10_texel(hi.y);
-  const float r0 = __fmaf_rn(t.fx, __fsub_rn(a10, a00), a00);
-  const float r1 = __fmaf_rn(t.fx, __fsub_rn(a11, a01), a01);
-  return __fsub_rn(__fmaf_rn(t.fy, __fsub_rn(r1, r0), r0), 1.f);
+  const float d0 = __fsub_rn(a10, a00), d1 = __fsub_rn(a11, a01);
+  const float r0 = __fmaf_rn(t.fx, d0, a00);
+  const float dr = __fmaf_rn(t.fx, __fsub_rn(d1, d0), __fsub_rn(a01, a00));
+  return __fsub_rn(__fmaf_rn(t.fy, dr, r0), 1.f);
 }
 
-// An FP16 cell decoded as the FP16 bilinear reads it: the four texels
-// 10^x and the two differences along the first axis.
+// An FP16 cell decoded as the FP16 bilinear reads it: with the texels
+// a = 10^x, (a00, a10 - a00, a01 - a00, (a11 - a01) - (a10 - a00)).
 __device__ __forceinline__ float4 band_cell_h(const uint2 q) {
   const float2 lo = __half22float2(
       __halves2half2(__ushort_as_half((unsigned short)(q.x & 0xffffu)),
@@ -322,7 +328,8 @@ __device__ __forceinline__ float4 band_cell_h(const uint2 q) {
                      __ushort_as_half((unsigned short)(q.y >> 16))));
   const float a00 = exp10_texel(lo.x), a10 = exp10_texel(lo.y);
   const float a01 = exp10_texel(hi.x), a11 = exp10_texel(hi.y);
-  return make_float4(a00, __fsub_rn(a10, a00), a01, __fsub_rn(a11, a01));
+  const float d0 = __fsub_rn(a10, a00), d1 = __fsub_rn(a11, a01);
+  return make_float4(a00, d0, __fsub_rn(a01, a00), __fsub_rn(d1, d0));
 }
 
 // Band table of one line of the line-aligned pass, in shared memory.  For
@@ -371,8 +378,8 @@ __device__ __forceinline__ float bilinear_tab_m1(const SearchParams &P,
 #endif
   const float4 q = tab[key];
   const float r0 = __fmaf_rn(fx, q.y, q.x);
-  const float r1 = __fmaf_rn(fx, q.w, q.z);
-  const float a = __fmaf_rn(fy, __fsub_rn(r1, r0), r0);
+  const float dr = __fmaf_rn(fx, q.w, q.z);
+  const float a = __fmaf_rn(fy, dr, r0);
   return H ? __fsub_rn(a, 1.f) : a;
 }
 
