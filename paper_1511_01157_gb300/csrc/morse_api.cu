@@ -583,7 +583,7 @@ morse_status plan_search(morse_ctx *ctx, const morse_event *ev,
                                    std::fabs(g->t0_hi - ev->t_ref));
     const double B = (ev->t_span + t0_max) / (tE_min * dlt) +
                      (band.u_max + band.shift_max) / dlt + 1.0;
-    const int n = 4 * (band.npix + 1);
+    const int n = 4 * morse::band_stride(band.npix);
     const size_t tb = 2 * sizeof(float4) * (size_t)n;
     // a band costs one warp about the time of 4 (npix + 1) L2 reads (some
     // ten microseconds); a round must be long enough to hide it: at least

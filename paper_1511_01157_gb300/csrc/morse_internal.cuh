@@ -146,6 +146,14 @@ __host__ __device__ __forceinline__ size_t cell_index(int c, int r,
   return (tile << (kTileLW + kTileLH)) |
          (size_t)(((r & (kTileH - 1)) << kTileLW) | (c & (kTileW - 1)));
 }
+// Row stride of a band table (entries): npix + 1 cells rounded up to 4 mod 8.
+// A warp's 16-byte loads are served eight lanes at a time, one bank group
+// (of eight) per entry; with a stride of 4 mod 8 the cells one row and up
+// to three columns apart, which neighbouring epochs read where the line
+// crosses a row, fall in distinct bank groups.
+__host__ __device__ __forceinline__ int band_stride(int npix) {
+  return (npix + 1) + ((4 - (npix + 1)) & 7);
+}
 // quad index offset of the folded floor-bit index (see SearchParams)
 inline unsigned quad_idx0(int npix) {
   return (unsigned)(npix / 2 + 1 - 0x4B400000) *
@@ -236,7 +244,8 @@ struct SearchParams {
                             // (checked build only)
   unsigned long long *stat_exact;  // trajectories given the exact sweep
   // Shared-memory band tables of the line-aligned pass (k_search only;
-  // 0 = off): entries per table, 4 (npix + 1), two tables after the lists.
+  // 0 = off): entries per table, 4 band_stride(npix), two tables after the
+  // lists.
   int tab_n;
   unsigned tab_c;           // half + 1 - 0x4B400000: floor bits -> cell
 };

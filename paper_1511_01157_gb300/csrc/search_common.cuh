@@ -335,10 +335,12 @@ __device__ __forceinline__ float4 band_cell_h(const uint2 q) {
 // Band table of one line of the line-aligned pass, in shared memory.  For
 // a line closer to the first axis (|cos alpha| >= |sin alpha|, TB = 1) the
 // table holds, for every cell column X, the cells of rows row0(X) ..
-// row0(X) + 3 around the line, at key X + (npix + 1) ((Y + C) & 3) with C
-// the floor bits' offset: four consecutive rows have distinct low bits, so
-// the key is the cell's own, and neighbouring columns are neighbouring
-// entries (a warp's lookups along the line fall in distinct banks).  The line meets at most rows floor(yc - 1/2) ..
+// row0(X) + 3 around the line, at key X + S ((Y + C) & 3) with S =
+// band_stride(npix) and C the floor bits' offset: four consecutive rows
+// have distinct low bits, so the key is the cell's own, and neighbouring
+// columns are neighbouring entries (a warp's lookups along the line fall in
+// distinct bank groups, also across a row step).  The line meets at most
+// rows floor(yc - 1/2) ..
 // floor(yc + 1/2) of a column (|slope| <= 1, yc its height at the column
 // centre), and row0 = floor(yc) - 1 takes them with 1/4 texel to spare on
 // each side, far beyond the FP32 rounding of a trajectory's position
@@ -349,16 +351,17 @@ __device__ __forceinline__ float4 band_cell_h(const uint2 q) {
 // (a00, a10 - a00, a01, a11 - a01), so the four exponentials of a lookup
 // are taken once per cell when the band is built, and the lookup is the
 // FP16 bilinear's own arithmetic.
+// The band-table lookup from the floor sums t = RD(v + 1.5 2^23) and the
+// fractions f = v - floor(v) of both axes; (vx, vy) only serve the
+// bounds-checked build.
 template <int TB, bool H>
-__device__ __forceinline__ float bilinear_tab_m1(const SearchParams &P,
-                                                 const float4 *tab, float vx,
-                                                 float vy) {
-  const float tx = __fadd_rd(vx, 12582912.f), ty = __fadd_rd(vy, 12582912.f);
-  const float fx = __fsub_rn(vx, __fsub_rn(tx, 12582912.f));
-  const float fy = __fsub_rn(vy, __fsub_rn(ty, 12582912.f));
+__device__ __forceinline__ float tab_cell_m1(const SearchParams &P,
+                                             const float4 *tab, float tx,
+                                             float ty, float fx, float fy,
+                                             float vx, float vy) {
   const unsigned bx = (unsigned)__float_as_int(tx);
   const unsigned by = (unsigned)__float_as_int(ty);
-  const unsigned S = (unsigned)P.npix + 1u;
+  const unsigned S = (unsigned)band_stride(P.npix);
   const unsigned key = TB == 1 ? (bx + P.tab_c) + S * (by & 3u)
                                : (by + P.tab_c) + S * (bx & 3u);
 #ifdef MORSE_CHECK_BOUNDS
@@ -379,7 +382,17 @@ __device__ __forceinline__ float bilinear_tab_m1(const SearchParams &P,
   const float4 q = tab[key];
   const float r0 = __fmaf_rn(fx, q.y, q.x);
   const float dr = __fmaf_rn(fx, q.w, q.z);
-  const float a = __fmaf_rn(fy, dr, r0);
+  return __fmaf_rn(fy, dr, r0);
+}
+
+template <int TB, bool H>
+__device__ __forceinline__ float bilinear_tab_m1(const SearchParams &P,
+                                                 const float4 *tab, float vx,
+                                                 float vy) {
+  const float tx = __fadd_rd(vx, 12582912.f), ty = __fadd_rd(vy, 12582912.f);
+  const float fx = __fsub_rn(vx, __fsub_rn(tx, 12582912.f));
+  const float fy = __fsub_rn(vy, __fsub_rn(ty, 12582912.f));
+  const float a = tab_cell_m1<TB, H>(P, tab, tx, ty, fx, fy, vx, vy);
   return H ? __fsub_rn(a, 1.f) : a;
 }
 
@@ -407,7 +420,7 @@ __device__ inline int build_band(const SearchParams &P, float4 *tab,
       const int W = r0 + d;
       const int Wc = min(max(W, 0), n);
       const unsigned key =
-          (unsigned)M + (unsigned)(n + 1) * (((unsigned)W + C) & 3u);
+          (unsigned)M + (unsigned)band_stride(n) * (((unsigned)W + C) & 3u);
       const size_t ci = xm ? cell_index(M, Wc, P.qpitch)
                            : cell_index(Wc, M, P.qpitch);
       tab[key] = H ? band_cell_h(P.quadh[ci]) : P.quad[ci];
@@ -444,20 +457,93 @@ __device__ __forceinline__ void seg1(const SearchParams &P, const Epochs &ep,
   }
 }
 
+// Two trajectories side by side in packed FP32 pairs (x: trajectory a,
+// y: trajectory b): each packed operation rounds both halves exactly as
+// the scalar operation does, so the sums are bit-identical to the scalar
+// sweep (seg1, the fit records), with one instruction for both.
+struct TrajP {
+  float2 ax, bx, ay, by, kt, bt, u02;
+};
+struct Acc2 {
+  float2 a, b, d;  // Acc of trajectory a in .x, of b in .y
+};
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ TrajP pack_traj(const TrajC &a, const TrajC &b) {
+  TrajP p;
+  p.ax = make_float2(a.ax, b.ax);
+  p.bx = make_float2(a.bx, b.bx);
+  p.ay = make_float2(a.ay, b.ay);
+  p.by = make_float2(a.by, b.by);
+  p.kt = make_float2(a.kt, b.kt);
+  p.bt = make_float2(a.bt, b.bt);
+  p.u02 = make_float2(a.u02, b.u02);
+  return p;
+}
+
+// A - 1 of both inside the map: packed coordinates, floor sums and
+// fractions (as in bilinear_tab_m1), then one lookup each
+template <bool H, int TB>
+__device__ __forceinline__ float2 mag2_in_m1(const SearchParams &P,
+                                             const TrajP &c, const float2 tt,
+                                             const float4 *tab) {
+  const float2 vx = __ffma2_rn(c.ax, tt, c.bx);
+  const float2 vy = __ffma2_rn(c.ay, tt, c.by);
+  if (TB == 0)
+    return make_float2(
+        H ? bilinear_h_m1(P, vx.x, vy.x) : bilinear_m1(P, vx.x, vy.x),
+        H ? bilinear_h_m1(P, vx.y, vy.y) : bilinear_m1(P, vx.y, vy.y));
+  const float2 tx = __fadd2_rd(vx, f2(12582912.f));
+  const float2 ty = __fadd2_rd(vy, f2(12582912.f));
+  // v - (t - 1.5 2^23): the subtraction as an FMA with -1 (exact product)
+  const float2 fx = __ffma2_rn(__fadd2_rn(tx, f2(-12582912.f)), f2(-1.f), vx);
+  const float2 fy = __ffma2_rn(__fadd2_rn(ty, f2(-12582912.f)), f2(-1.f), vy);
+  const float2 a =
+      make_float2(tab_cell_m1<TB, H>(P, tab, tx.x, ty.x, fx.x, fy.x, vx.x, vy.x),
+                  tab_cell_m1<TB, H>(P, tab, tx.y, ty.y, fx.y, fy.y, vx.y, vy.y));
+  return H ? __fadd2_rn(a, f2(-1.f)) : a;
+}
+
+// A - 1 of both outside the map (single lens, as mag_out_m1)
+__device__ __forceinline__ float2 mag2_out_m1(const TrajP &c, const float2 tt) {
+  const float2 tau = __ffma2_rn(c.kt, tt, c.bt);
+  const float2 u2 = __ffma2_rn(tau, tau, c.u02);
+  const float2 r = __fmul2_rn(u2, __fadd2_rn(u2, f2(4.f)));
+  const float2 A = __fmul2_rn(__fadd2_rn(u2, f2(2.f)),
+                              make_float2(rsqrt_approx(r.x), rsqrt_approx(r.y)));
+  return __fadd2_rn(A, f2(-1.f));
+}
+
+__device__ __forceinline__ void acc2_add(Acc2 &s, float2 w, float2 wf,
+                                         float2 Ac) {
+  const float2 wAc = __fmul2_rn(w, Ac);
+  s.a = __fadd2_rn(s.a, wAc);
+  s.b = __ffma2_rn(wAc, Ac, s.b);
+  s.d = __ffma2_rn(wf, Ac, s.d);
+}
+
 // two trajectories over one epoch segment, one epoch load for both
 template <bool H, bool INA, bool INB, int TB = 0>
 __device__ __forceinline__ void seg2(const SearchParams &P, const Epochs &ep,
                                      const TrajC &ca, const TrajC &cb,
-                                     int lane, int e0, int e1, Acc &sa,
-                                     Acc &sb, const float4 *tab = nullptr) {
+                                     const TrajP &cp, int lane, int e0, int e1,
+                                     Acc2 &s, const float4 *tab = nullptr) {
 #pragma unroll ((INA || INB) ? kUnroll : 2)
   for (int e = lane_start(e0, lane); e < e1; e += 32) {
     const float2 v = ep.tw[e];
     const float wf = ep.wf[e];
-    acc_add(sa, v.y, wf,
-            INA ? mag_in_m1<H, TB>(P, ca, v.x, tab) : mag_out_m1(ca, v.x));
-    acc_add(sb, v.y, wf,
-            INB ? mag_in_m1<H, TB>(P, cb, v.x, tab) : mag_out_m1(cb, v.x));
+    const float2 tt = f2(v.x);
+    float2 Ac;
+    if (INA && INB)
+      Ac = mag2_in_m1<H, TB>(P, cp, tt, tab);
+    else if (!INA && !INB)
+      Ac = mag2_out_m1(cp, tt);
+    else
+      Ac = make_float2(
+          INA ? mag_in_m1<H, TB>(P, ca, v.x, tab) : mag_out_m1(ca, v.x),
+          INB ? mag_in_m1<H, TB>(P, cb, v.x, tab) : mag_out_m1(cb, v.x));
+    acc2_add(s, f2(v.y), f2(wf), Ac);
   }
 }
 
@@ -499,7 +585,8 @@ __device__ __forceinline__ void phase1_pair(const SearchParams &P,
                                             const TrajC &cb, const int lane,
                                             Acc &ra, Acc &rb,
                                             const float4 *tab = nullptr) {
-  Acc sa = {0.f, 0.f, 0.f}, sb = {0.f, 0.f, 0.f};
+  Acc2 s = {f2(0.f), f2(0.f), f2(0.f)};
+  const TrajP cp = pack_traj(ca, cb);
   // cut points, sorted (warp-uniform)
   int p1 = ca.e_in, p2 = ca.e_out, p3 = cb.e_in, p4 = cb.e_out, t;
   if (p1 > p2) { t = p1; p1 = p2; p2 = t; }
@@ -515,14 +602,15 @@ __device__ __forceinline__ void phase1_pair(const SearchParams &P,
     const bool ina = e0 >= ca.e_in && e1 <= ca.e_out;
     const bool inb = e0 >= cb.e_in && e1 <= cb.e_out;
     if (ina && inb)
-      seg2<H, true, true, TB>(P, ep, ca, cb, lane, e0, e1, sa, sb, tab);
+      seg2<H, true, true, TB>(P, ep, ca, cb, cp, lane, e0, e1, s, tab);
     else if (ina)
-      seg2<H, true, false, TB>(P, ep, ca, cb, lane, e0, e1, sa, sb, tab);
+      seg2<H, true, false, TB>(P, ep, ca, cb, cp, lane, e0, e1, s, tab);
     else if (inb)
-      seg2<H, false, true, TB>(P, ep, ca, cb, lane, e0, e1, sa, sb, tab);
+      seg2<H, false, true, TB>(P, ep, ca, cb, cp, lane, e0, e1, s, tab);
     else
-      seg2<H, false, false>(P, ep, ca, cb, lane, e0, e1, sa, sb);
+      seg2<H, false, false>(P, ep, ca, cb, cp, lane, e0, e1, s);
   }
+  const Acc sa = {s.a.x, s.b.x, s.d.x}, sb = {s.a.y, s.b.y, s.d.y};
   ra = acc_reduce(sa);
   rb = acc_reduce(sb);
 }
