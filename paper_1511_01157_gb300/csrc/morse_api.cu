@@ -655,7 +655,9 @@ morse_status enqueue_topk(morse_ctx *ctx, const Plan &pl,
   int r;
   // pilot: a strided subset of ~sqrt(K N) trajectories (at least 16 K)
   // seeds the grid-wide pruning threshold
-  const double want = std::max(16.0 * pl.K, std::sqrt((double)pl.K * P.count));
+  const double want =
+      std::max(morse::kPilotMinK * pl.K,
+               morse::kPilotSqrt * std::sqrt((double)pl.K * P.count));
   const long long stride = (long long)(P.count / want);
   if (P.gthr && stride >= 4) {
     morse::SearchParams Q = P;
@@ -973,7 +975,8 @@ morse_status batch_prepare(morse_ctx *ctx, const morse_event *const *evs,
   for (int p = 0; p < pairs; ++p)
     shape_pair[(size_t)p] = shape_fit[(size_t)(p / n_maps)];
   // pilot: a strided sample of ~sqrt(K N) trajectories per pair
-  const double want = std::max(16.0 * K, std::sqrt((double)K * N));
+  const double want = std::max(morse::kPilotMinK * K,
+                               morse::kPilotSqrt * std::sqrt((double)K * N));
   const long long stride = (long long)(N / want);
   H.pilot.clear();
   H.pilot_list0.clear();

@@ -266,8 +266,19 @@ constexpr int kSearchWarps = MORSE_SEARCH_WARPS;  // one block per SM
 #define MORSE_TPG 32
 #endif
 constexpr int kTpgMain = MORSE_TPG;  // main pass, at most
-constexpr int kTpgPilot = 4;         // pilot: spread a small sample over
-                                     // every SM
+#ifndef MORSE_TPG_PILOT
+#define MORSE_TPG_PILOT 4
+#endif
+constexpr int kTpgPilot = MORSE_TPG_PILOT;  // pilot: spread a small sample
+                                            // over every SM
+// pilot sample: max(kPilotMinK K, kPilotSqrt sqrt(K N)) trajectories
+#ifndef MORSE_PILOT_SQRT
+#define MORSE_PILOT_SQRT 1.0
+#endif
+#ifndef MORSE_PILOT_MIN_K
+#define MORSE_PILOT_MIN_K 16.0
+#endif
+constexpr double kPilotSqrt = MORSE_PILOT_SQRT, kPilotMinK = MORSE_PILOT_MIN_K;
 
 // Line-aligned warp groups for the main pass: about one line per block
 // round (line = n_t0 n_tE trajectories share a track's line).
