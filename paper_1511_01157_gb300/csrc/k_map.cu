@@ -111,8 +111,89 @@ __device__ bool sample_bin(const RayParams &P, long long i, long long j,
   return true;
 }
 
+__device__ __forceinline__ float2 f2r(float v) { return make_float2(v, v); }
+
+// Bin one FP32 ray from its floor sums tx, ty = RD(v + 1.5 2^23) (the bin
+// of v in the low mantissa bits, as bin_of).  cx, cy: the window's corner
+// plus the bit offset 0x4B400000, so one unsigned compare per axis tests
+// "on the map and in the window" (the window lies inside the map; W is its
+// side, the map's side when the map is smaller).
+__device__ __forceinline__ void bin_ray(const RayParams &P, uint32_t *win,
+                                        unsigned cx, unsigned cy, unsigned W,
+                                        float tx, float ty, bool lost,
+                                        unsigned &n_off, unsigned &n_lost) {
+  const unsigned ux = (unsigned)__float_as_int(tx);
+  const unsigned uy = (unsigned)__float_as_int(ty);
+  const unsigned lx = ux - cx, ly = uy - cy;
+  if (lost) {
+    ++n_lost;
+  } else if (lx < W && ly < W) {
+    atomicAdd(&win[ly * kRayWin + lx], 1u);
+  } else {
+    const unsigned a = ux - 0x4B400000u, b = uy - 0x4B400000u;
+    if (a >= (unsigned)P.npix || b >= (unsigned)P.npix)
+      ++n_off;
+    else
+      atomicAdd(&P.counts[(size_t)b * P.npix + a], 1u);
+  }
+}
+
+// The FP32 rays of one thread's sub-block: columns ib .. ib + na - 1
+// (FULL: na = kSubX), rows jb .. jb + kSubY - 1, two columns per packed
+// FP32 instruction.  The column terms x1, x1 - xa and x1 - xb are taken
+// once per sub-block.  Every operation is that of deflect32, rounded the
+// same way (the mass terms with -e1, -e2, exact negations), so each ray
+// lands in the same bin as there.
+template <bool FULL>
+__device__ __forceinline__ void shoot_f32(const RayParams &P, uint32_t *win,
+                                          int wx0, int wy0, long long jb,
+                                          int na, float x1b, unsigned &n_off,
+                                          unsigned &n_lost) {
+  constexpr int NP = kSubX / 2;
+  float2 x1[NP], d1[NP], d2[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    x1[p] = make_float2(fmaf((float)(2 * p), P.hf, x1b),
+                        fmaf((float)(2 * p + 1), P.hf, x1b));
+    d1[p] = __fadd2_rn(x1[p], f2r(-P.xaf));
+    d2[p] = __fadd2_rn(x1[p], f2r(-P.xbf));
+  }
+  const float2 ne1 = f2r(-P.e1f), ne2 = f2r(-P.e2f);
+  const float2 invd = f2r(P.invdf), off = f2r(P.offf);
+  const float2 M = f2r(12582912.f);
+  const unsigned W = (unsigned)min(kRayWin, P.npix);
+  const unsigned cx = 0x4B400000u + (unsigned)wx0;
+  const unsigned cy = 0x4B400000u + (unsigned)wy0;
+#pragma unroll 1
+  for (int b = 0; b < kSubY; ++b) {
+    const long long j = jb + b;
+    if (j >= P.nray) break;
+    const float x2 = fmaf((float)j, P.hf, P.x0f);
+    const float2 x2p = f2r(x2), x2sq = f2r(x2 * x2);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      if (!FULL && 2 * p >= na) break;
+      const float2 r1 = __ffma2_rn(d1[p], d1[p], x2sq);
+      const float2 r2 = __ffma2_rn(d2[p], d2[p], x2sq);
+      const float2 rr = __fmul2_rn(r1, r2);
+      const float2 inv = make_float2(rcp_approx(rr.x), rcp_approx(rr.y));
+      const float2 a1 = __fmul2_rn(ne1, __fmul2_rn(r2, inv));  // -e1 r2/rr
+      const float2 a2 = __fmul2_rn(ne2, __fmul2_rn(r1, inv));  // -e2 r1/rr
+      const float2 y1 = __ffma2_rn(a2, d2[p], __ffma2_rn(a1, d1[p], x1[p]));
+      const float2 y2 = __ffma2_rn(__fadd2_rn(a1, a2), x2p, x2p);
+      const float2 tx = __fadd2_rd(__ffma2_rn(y1, invd, off), M);
+      const float2 ty = __fadd2_rd(__ffma2_rn(y2, invd, off), M);
+      bin_ray(P, win, cx, cy, W, tx.x, ty.x, rr.x == 0.0f, n_off, n_lost);
+      if (FULL || 2 * p + 1 < na)
+        bin_ray(P, win, cx, cy, W, tx.y, ty.y, rr.y == 0.0f, n_off, n_lost);
+    }
+  }
+}
+
+// FP32: two blocks per SM (at most 64 registers: the packed sub-block loop
+// keeps its twelve column pairs in registers).
 template <bool FP64>
-__global__ void __launch_bounds__(kRayThreads)
+__global__ void __launch_bounds__(kRayThreads, FP64 ? 1 : 2)
     k_rayshoot(const RayParams P) {
   extern __shared__ uint32_t win[];  // kRayWin * kRayWin bins
   __shared__ int s_wx, s_wy;
@@ -163,38 +244,34 @@ __global__ void __launch_bounds__(kRayThreads)
     // rays of the sub-block row inside the grid, and the first one's x1
     const int na = (int)max(0LL, min((long long)kSubX, P.nray - ib));
     const float x1b = fmaf((float)ib, P.hf, P.x0f);
+    if (!FP64) {
+      if (na == kSubX)
+        shoot_f32<true>(P, win, wx0, wy0, jb, na, x1b, n_off, n_lost);
+      else if (na > 0)
+        shoot_f32<false>(P, win, wx0, wy0, jb, na, x1b, n_off, n_lost);
+    } else {
 #pragma unroll 1
-    for (int b = 0; b < kSubY; ++b) {
-      const long long j = jb + b;
-      if (j >= P.nray) break;
-      double x2d = 0.0, x2sqd = 0.0;
-      float x2f = 0.f, x2sqf = 0.f;
-      if (FP64) {
-        x2d = __dadd_rn(-P.X, __dmul_rn(__dadd_rn((double)j, 0.5), P.h));
-        x2sqd = __dmul_rn(x2d, x2d);
-      } else {
-        x2f = fmaf((float)j, P.hf, P.x0f);
-        x2sqf = x2f * x2f;
-      }
+      for (int b = 0; b < kSubY; ++b) {
+        const long long j = jb + b;
+        if (j >= P.nray) break;
+        const double x2d = __dadd_rn(-P.X, __dmul_rn(__dadd_rn((double)j, 0.5), P.h));
+        const double x2sqd = __dmul_rn(x2d, x2d);
 #pragma unroll
-      for (int a = 0; a < kSubX; ++a) {
-        if (a < na) {
-          int ix = 0, iy = 0, st;
-          if (FP64)
-            st = deflect64(P, ib + a, x2d, x2sqd, &ix, &iy);
-          else
-            st = deflect32(P, fmaf((float)a, P.hf, x1b), x2f, x2sqf, &ix,
-                           &iy);
-          if (st == 0) {
-            unsigned lx = (unsigned)(ix - wx0), ly = (unsigned)(iy - wy0);
-            if (lx < (unsigned)kRayWin && ly < (unsigned)kRayWin)
-              atomicAdd(&win[ly * kRayWin + lx], 1u);
-            else
-              atomicAdd(&P.counts[(size_t)iy * P.npix + ix], 1u);
-          } else if (st == 1) {
-            ++n_off;
-          } else {
-            ++n_lost;
+        for (int a = 0; a < kSubX; ++a) {
+          if (a < na) {
+            int ix = 0, iy = 0;
+            const int st = deflect64(P, ib + a, x2d, x2sqd, &ix, &iy);
+            if (st == 0) {
+              unsigned lx = (unsigned)(ix - wx0), ly = (unsigned)(iy - wy0);
+              if (lx < (unsigned)kRayWin && ly < (unsigned)kRayWin)
+                atomicAdd(&win[ly * kRayWin + lx], 1u);
+              else
+                atomicAdd(&P.counts[(size_t)iy * P.npix + ix], 1u);
+            } else if (st == 1) {
+              ++n_off;
+            } else {
+              ++n_lost;
+            }
           }
         }
       }
