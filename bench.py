@@ -556,9 +556,11 @@ def time_to_best_fit(ctx, m, cfg, ev, S, Q, plain_s, plain_fits, ev_t,
                          g["t0_hi"], g["tE_lo"], g["tE_hi"], True, True, 16)
 
     def screened():
-        # coarse screen of all maps, the full grid on the 16 best, refine
+        # coarse screen of all maps, the full grid on the 256 best (of 64,
+        # 128, 192 and 256 kept, the smallest that keeps the best map of
+        # this event), refine
         first = sweep(coarse)
-        best = np.sort(np.argsort(first["chi2"][:, 0])[:64])
+        best = np.sort(np.argsort(first["chi2"][:, 0])[:256])
         fine = ctx.sweep(ev, S[best].copy(), Q[best].copy(), cfg["L"],
                          cfg["npix"], cfg["nray"], grid_of(m, cfg),
                          image_halfwidth=cfg["X"], deflect="fp32")
@@ -567,7 +569,7 @@ def time_to_best_fit(ctx, m, cfg, ev, S, Q, plain_s, plain_fits, ev_t,
     b, t = timed(screened)
     forms["screen_then_grid_plus_refine"] = (
         t, b, "20x36x13x10 grid on all 651 maps, the 40x72x25x20 grid on "
-        "the 64 best maps, then 40 LM iterations on the 16 best seeds of "
+        "the 256 best maps, then 40 LM iterations on the 16 best seeds of "
         "the 8 best of those")
     # §4.3 (i): the smallest peak magnification the data allow when the
     # blend flux is not negative, F_peak / F_base with F_peak the largest
