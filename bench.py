@@ -46,6 +46,12 @@ UNIT = "traj-epoch evals/s"
 ALG_INSTR_PER_EVAL = 22
 # one bilinear gather of a 2x2 FP32 cell per trajectory-epoch
 GATHER_BYTES_PER_EVAL = 16
+# bytes per trajectory-epoch through the shared-memory data pipe as the
+# search is built: the 16-byte cell from the band table and half of the
+# 12-byte epoch record (one load serves a trajectory pair); the pipe moves
+# 128 bytes per clock per SM
+SMEM_BYTES_PER_EVAL = 22
+SMEM_BYTES_PER_CLK_SM = 128
 # ray shooting, per ray: ray coordinates 2, deflection of Eq. 2 through two
 # lenses 12 (+ 2 reciprocals), binning 6; plus one shared-memory atomic
 ALG_INSTR_PER_RAY = 22
@@ -841,6 +847,9 @@ def run_gpu(args, cfg):
     achieved = evals_step * ALG_INSTR_PER_EVAL / (search_ms * 1e-3) / 1e12
     evals_per_s_kernel = evals_step / (search_ms * 1e-3)
     gather_gbs = evals_per_s_kernel * GATHER_BYTES_PER_EVAL / 1e9
+    smem_gbs = evals_per_s_kernel * SMEM_BYTES_PER_EVAL / 1e9
+    smem_peak = props.multi_processor_count * SMEM_BYTES_PER_CLK_SM * \
+        sm_max * 1e6 / 1e9
     rays_kernel = rays_step / (ray_ms * 1e-3)
     ray_alu = probes["fp32_fma_per_s"] / ALG_INSTR_PER_RAY
     ray_atom = probes["smem_atomics_per_s"]
@@ -886,7 +895,16 @@ def run_gpu(args, cfg):
                 "frac_l1": gather_gbs * 1e9 / probes["l1_gather_bytes_per_s"],
                 "frac_l2": gather_gbs * 1e9 / probes["l2_gather_bytes_per_s"],
                 "algorithmic": f"{GATHER_BYTES_PER_EVAL} B per "
-                               "trajectory-epoch (one 2x2 FP32 cell)"}},
+                               "trajectory-epoch (one 2x2 FP32 cell)"},
+            "smem_pipe": {
+                "achieved_GBps": smem_gbs, "peak_GBps": smem_peak,
+                "frac": smem_gbs / smem_peak,
+                "bytes": f"{SMEM_BYTES_PER_EVAL} B per trajectory-epoch "
+                         "(16 B cell + half of a 12 B epoch record), "
+                         "excluding bank conflicts",
+                "peak_source": f"{props.multi_processor_count} SMs x "
+                               f"{SMEM_BYTES_PER_CLK_SM} B per clock x "
+                               f"{sm_max} MHz"}},
         "rayshoot_roofline": {
             "kernel": "k_rayshoot<FP32>", "rays_per_s": rays_kernel,
             "bound": "alu" if ray_alu <= ray_atom else "smem_atomic",
