@@ -18,9 +18,10 @@
 namespace morse {
 namespace dev {
 
-// Inside-map epoch loops are unrolled twice: the band tables' shared
-// loads need little latency hiding, and the search's code must stay within
-// the instruction cache (unroll 4 measured 33 % slower, unroll 1 10 %).
+// Inside-map epoch loops are unrolled twice by default (a source file may
+// set MORSE_UNROLL first): the code must stay within the instruction cache
+// (before the trajectory pairs were packed, unroll 4 made the search 33 %
+// slower; k_search.cu now sets 4).
 #ifndef MORSE_UNROLL
 #define MORSE_UNROLL 2
 #endif
