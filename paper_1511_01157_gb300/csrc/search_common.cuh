@@ -25,7 +25,13 @@ namespace dev {
 #ifndef MORSE_UNROLL
 #define MORSE_UNROLL 2
 #endif
-constexpr int kUnroll = MORSE_UNROLL;  // inside-map epoch loop
+// the FP16-table kernels keep two (their band builds add code; four made
+// the FP16 sweep 5 % slower)
+#ifndef MORSE_UNROLL_H
+#define MORSE_UNROLL_H 2
+#endif
+constexpr int kUnroll = MORSE_UNROLL;     // inside-map epoch loop
+constexpr int kUnrollH = MORSE_UNROLL_H;  // the same, FP16 tables
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned kLockSpinLimit = 1u << 20;
@@ -449,7 +455,7 @@ template <bool H, bool IN, int TB = 0>
 __device__ __forceinline__ void seg1(const SearchParams &P, const Epochs &ep,
                                      const TrajC &c, int lane, int e0, int e1,
                                      Acc &s, const float4 *tab = nullptr) {
-#pragma unroll (IN ? kUnroll : 2)
+#pragma unroll (IN ? (H ? kUnrollH : kUnroll) : 2)
   for (int e = lane_start(e0, lane); e < e1; e += 32) {
     const float2 v = ep.tw[e];
     const float wf = ep.wf[e];
@@ -530,7 +536,7 @@ __device__ __forceinline__ void seg2(const SearchParams &P, const Epochs &ep,
                                      const TrajC &ca, const TrajC &cb,
                                      const TrajP &cp, int lane, int e0, int e1,
                                      Acc2 &s, const float4 *tab = nullptr) {
-#pragma unroll ((INA || INB) ? kUnroll : 2)
+#pragma unroll ((INA || INB) ? (H ? kUnrollH : kUnroll) : 2)
   for (int e = lane_start(e0, lane); e < e1; e += 32) {
     const float2 v = ep.tw[e];
     const float wf = ep.wf[e];
@@ -633,7 +639,7 @@ __device__ __forceinline__ double phase2(const SearchParams &P,
     const float r = __fsub_rn(ep.fc[e], __fmaf_rn(Fs, Ac, Bc));
     chi = __fmaf_rn(__fmul_rn(v.y, r), r, chi);
   }
-#pragma unroll (kUnroll)
+#pragma unroll (H ? kUnrollH : kUnroll)
   for (int e = lane_start(c.e_in, lane); e < c.e_out; e += 32) {
     const float2 v = ep.tw[e];
     const float Ac = mag_in_m1<H, TB>(P, c, v.x, tab);
