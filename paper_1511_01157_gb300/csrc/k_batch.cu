@@ -19,6 +19,12 @@
 //  * Every trajectory's chi^2 is computed by the same device functions as
 //    the single-pair search (k_search), so the results of a batch are those
 //    of one morse_grid_chi2 call per pair, bit for bit.
+// Inside-map epoch loops (global-table lookups from L2) unrolled four
+// times for the FP32 table: more independent loads in flight, 4 % faster
+// on the 32-event x 8-map batch than twice (FP16-table variants: twice).
+#ifndef MORSE_UNROLL
+#define MORSE_UNROLL 4
+#endif
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
