@@ -114,6 +114,25 @@ def test_fp32_map_relative_l1(ctx):
     assert int(c.sum(dtype=np.uint64)) + off + lost == nray * nray
 
 
+@pytest.mark.parametrize("nray,npix", [(2003, 128), (1029, 64)])
+def test_fp32_map_ragged_ray_grid(ctx, nray, npix):
+    """FP32 ray shooting with a ray grid that is not a multiple of a
+    thread's 8 columns or a tile's 256: the last sub-blocks are partial.
+    Every ray is counted once, and the map matches the FP64 oracle."""
+    s, q, L, X = 1.1, 3e-3, 2.0, 3.0
+    mp = ctx.build_map(s, q, L, npix, nray, image_halfwidth=X,
+                       deflect="fp32")
+    A_o, co, offo, losto = orc.build_map(s, q, L, npix, nray, X, nthreads=NT)
+    c, off, lost = mp.counts()
+    assert int(c.sum(dtype=np.uint64)) + off + lost == nray * nray
+    assert abs(int(off) - int(offo)) <= 1e-4 * nray * nray
+    A = mp.values()
+    sel = co >= 100
+    assert sel.sum() > 500
+    rel_l1 = np.abs(A[sel] - A_o[sel]).sum() / np.abs(A_o[sel]).sum()
+    assert rel_l1 <= 1e-3, rel_l1
+
+
 # ------------------------------------------------------------------ search
 @pytest.fixture(scope="module")
 def cfg0_event(ctx):
