@@ -18,7 +18,10 @@
  *                          source grid of §4.1
  *   quintic + roots ....... §3 (inversion of Eq. 2 gives a fifth-order
  *                          polynomial with 3 or 5 image solutions); roots by
- *                          Laguerre's method with deflation and polishing
+ *                          Laguerre's iteration (derived from the root sums
+ *                          of p'/p and its derivative), damped and
+ *                          restarted, with deflation and re-convergence on
+ *                          the full polynomial
  *   magnification ......... §3 Eq. 3-4 (A_j = 1/det J, J = d zeta / d z,
  *                          total = sum over images; absolute value taken)
  *   Paczynski curve ....... §4.3 (ii) single-lens light curve
@@ -224,65 +227,114 @@ int orc_quintic(double s, double q, double y1, double y2, double *cre,
   return (cabs(c6[5]) == 0.0) ? -1 : 0;
 }
 
-/* One root of sum_k a[k] z^k (degree m) by Laguerre's method, starting from
- * *x.  Laguerre step: with G = p'/p and H = G^2 - p''/p,
- *     dx = m / (G +- sqrt((m-1)(m H - G^2))),
- * sign chosen to make the denominator largest.  A stalled iteration is
- * nudged by a fractional step every tenth iteration. */
-static int laguerre(const cplx *a, int m, cplx *x) {
-  static const double frac[] = {0.0, 0.5, 0.25, 0.75, 0.13, 0.38,
-                                0.62, 0.88, 1.0};
-  const double eps = 1e-15;
-  for (int it = 1; it <= 80; ++it) {
-    cplx p = a[m], dp = 0.0, ddp = 0.0; /* ddp accumulates p''/2 */
-    double err = cabs(p), ax = cabs(*x);
-    for (int j = m - 1; j >= 0; --j) {
-      ddp = (*x) * ddp + dp;
-      dp = (*x) * dp + p;
-      p = (*x) * p + a[j];
-      err = cabs(p) + ax * err;
+/* Value, first and second derivative of p(z) = sum_k a[k] z^k (degree m)
+ * at x by Horner's scheme, and the scale b = sum_k |a[k]| |x|^k of the
+ * terms: the rounding error of the computed p(x) is at most about
+ * 2 m 2^-53 b, so |p(x)| below that is indistinguishable from zero. */
+static cplx poly_eval(const cplx *a, int m, cplx x, cplx *d1, cplx *d2,
+                      double *scale) {
+  cplx p = a[m], q = 0.0, r = 0.0;
+  double b = cabs(a[m]), ax = cabs(x);
+  for (int j = m - 1; j >= 0; --j) {
+    r = r * x + q;  /* p''/2 */
+    q = q * x + p;  /* p'    */
+    p = p * x + a[j];
+    b = b * ax + cabs(a[j]);
+  }
+  *d1 = q;
+  *d2 = 2.0 * r;
+  *scale = b;
+  return p;
+}
+
+/* One root of p (degree m >= 1) by Laguerre's iteration from *x.
+ *
+ * Derivation: with roots r_i, G = p'/p = sum 1/(x - r_i) and H = G^2 -
+ * p''/p = sum 1/(x - r_i)^2.  Supposing the nearest root at distance d and
+ * the other m - 1 all at one distance e, G = 1/d + (m-1)/e and H = 1/d^2 +
+ * (m-1)/e^2; eliminating e gives d = m / (G +- sqrt((m-1)(m H - G^2))),
+ * the sign that makes the denominator larger in modulus (the nearer root).
+ *
+ * Safeguards of this implementation:
+ *  - damping: the step is taken only if it lowers |p|; otherwise it is
+ *    halved, up to six times, and the trial with the smallest |p| is kept;
+ *  - restart: after three steps in a row that could not lower |p|, or a
+ *    vanishing denominator, the iterate moves to a point of the circle of
+ *    radius |x| + R/4 (R = 1 + max_k |a_k / a_m|, a bound on every root's
+ *    modulus) at the angle j * 2.39996 rad (the golden angle: restarts
+ *    never repeat a direction);
+ *  - stop: |p(x)| at the rounding floor 2 m 2^-53 sum |a_k| |x|^k, or a
+ *    step below 2^-52 |x|, or 200 iterations (returns -1 then; the caller
+ *    keeps the last iterate, which the Eq. 2 residual test then judges).
+ * Returns the iterations used. */
+static int laguerre_root(const cplx *a, int m, cplx *x) {
+  const double u = 1.1102230246251565e-16; /* 2^-53 */
+  double R = 0.0;
+  for (int k = 0; k < m; ++k) {
+    double t = cabs(a[k]) / cabs(a[m]);
+    if (t > R) R = t;
+  }
+  R += 1.0;
+  int stalls = 0, restarts = 0;
+  for (int it = 1; it <= 200; ++it) {
+    cplx d1, d2;
+    double b;
+    cplx p = poly_eval(a, m, *x, &d1, &d2, &b);
+    double ap = cabs(p);
+    if (ap <= 2.0 * m * u * b) return it;
+    cplx G = d1 / p;
+    cplx H = G * G - d2 / p;
+    cplx root = csqrt((double)(m - 1) * ((double)m * H - G * G));
+    cplx den = cabs(G + root) >= cabs(G - root) ? G + root : G - root;
+    if (cabs(den) == 0.0 || !isfinite(creal(den)) ||
+        !isfinite(cimag(den)) || stalls >= 3) {
+      ++restarts;
+      double ang = 2.39996322972865332 * (double)restarts;
+      *x = (cabs(*x) + 0.25 * R) * (cos(ang) + I * sin(ang));
+      stalls = 0;
+      continue;
     }
-    if (cabs(p) <= eps * err) return it; /* at the rounding floor */
-    cplx G = dp / p;
-    cplx H = G * G - 2.0 * ddp / p;
-    cplx sq = csqrt((double)(m - 1) * ((double)m * H - G * G));
-    cplx gp = G + sq, gm = G - sq;
-    double ap = cabs(gp), am = cabs(gm);
-    if (ap < am) {
-      gp = gm;
-      ap = am;
+    cplx dx = (double)m / den;
+    if (cabs(dx) <= 2.0 * u * cabs(*x)) return it;
+    cplx best = *x - dx;
+    double best_ap = cabs(poly_eval(a, m, best, &d1, &d2, &b));
+    for (int h = 0; h < 6 && !(best_ap < ap); ++h) {
+      dx = 0.5 * dx;
+      cplx trial = *x - dx;
+      double t = cabs(poly_eval(a, m, trial, &d1, &d2, &b));
+      if (t < best_ap) {
+        best = trial;
+        best_ap = t;
+      }
     }
-    cplx dx = (ap > 0.0) ? (double)m / gp
-                         : (1.0 + ax) * (cos((double)it) + I * sin((double)it));
-    cplx x1 = *x - dx;
-    if (x1 == *x) return it;
-    if (it % 10 != 0)
-      *x = x1;
-    else
-      *x = *x - frac[(it / 10) % 9] * dx;
+    stalls = (best_ap < ap) ? 0 : stalls + 1;
+    *x = best;
   }
   return -1;
 }
 
-/* All 5 roots: Laguerre on the deflated polynomial from z = 0, synthetic
- * division after each root, then each root polished on the full polynomial. */
+/* All 5 roots of the quintic: each by laguerre_root on the polynomial
+ * deflated by the roots found so far (starting from z = 0, so the smaller
+ * roots come off first and the deflation stays well conditioned), the
+ * deflation being synthetic division by (z - root); then every root is
+ * re-converged on the undeflated polynomial, which removes the error the
+ * deflated coefficients carried. */
 int orc_roots5(const double *cre, const double *cim, double *rre,
                double *rim) {
   cplx a[6], d[6], r[5];
   for (int k = 0; k < 6; ++k) a[k] = d[k] = cre[k] + I * cim[k];
   for (int m = 5; m >= 1; --m) {
     cplx x = 0.0;
-    laguerre(d, m, &x);
+    laguerre_root(d, m, &x);
     r[m - 1] = x;
-    /* divide d by (z - x) */
-    cplx carry = d[m];
+    cplx carry = d[m]; /* d(z) = (z - x) d'(z) + remainder */
     for (int j = m - 1; j >= 0; --j) {
       cplx t = d[j];
       d[j] = carry;
       carry = t + x * carry;
     }
   }
-  for (int k = 0; k < 5; ++k) laguerre(a, 5, &r[k]);
+  for (int k = 0; k < 5; ++k) laguerre_root(a, 5, &r[k]);
   for (int k = 0; k < 5; ++k) {
     rre[k] = creal(r[k]);
     rim[k] = cimag(r[k]);
