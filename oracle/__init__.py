@@ -26,7 +26,7 @@ names the passage of McDougall & Albrow (2015) it follows:
 * ``line_max``        -- §4.3 (i) largest magnification along a line
 * ``line_peaks``      -- §4.3 (iii) peak library: peaks of the map along a
   line (count, positions, heights)
-* ``peak_lines``      -- §4.3 (iv)-(v) Eq. 7-8: the trajectories aligned
+* ``peak_trajectories`` -- §4.3 (iv)-(v) Eq. 7-8: the trajectories aligned
   with one or two given peak times
 * ``fit_A``           -- §4.1 Eq. 5-6 linear flux fit, chi^2 as a sum of
   per-point contributions (§4.2)
@@ -93,7 +93,7 @@ def _load():
         "orc_fs_weights": (None, [_D, _D, _I, _I, _P]),
         "orc_line_max": (_D, [_P, _I, _D, _D, _D]),
         "orc_line_peaks": (_I, [_P, _I, _D, _D, _D, _D, _D, _I, _D, _I, _P,
-                                _P]),
+                                _P, _P, _P]),
         "orc_fs_convolve": (None, [_P, _I, _D, _P, _I, _P, _I]),
         "orc_half_value": (_D, [ctypes.c_uint16]),
         "orc_log10_half": (None, [_P, ctypes.c_longlong, _D, _P]),
@@ -332,13 +332,18 @@ def line_max(A, L, u0, alpha):
                                 float(alpha))
 
 
-def line_peaks(A, L, lines, sub=2, delta=0.0, max_peaks=8):
+def line_peaks(A, L, lines, sub=2, delta=0.0, max_peaks=8, bounds=False):
     """§4.3 (iii): the peak library of the map A along lines[j] = (u,
     alpha, shift) (shift: the line's reference point lies tau = shift past
-    its closest approach to the origin).  Returns (count[n] int32,
+    its closest approach to the origin), in FP64 from the definition (a
+    turn of the sampled bilinear profile from rising to falling, rise and
+    fall confirmed by the factor 1 + delta).  Returns (count[n] int32,
     pos[n, max_peaks], height[n, max_peaks]); pos in Einstein radii from the
     reference point, the max_peaks highest peaks in increasing tau, NaN in
-    unused slots."""
+    unused slots.  With bounds=True also (herr[n, max_peaks], uncertain[n]
+    bool): the height bounds of an FP32 evaluation of the same profile and
+    the lines where some decision lies within those bounds (see
+    orc_line_peaks)."""
     lib = _load()
     A = np.ascontiguousarray(A, dtype=np.float32)
     lines = np.asarray(lines, dtype=np.float64).reshape(-1, 3)
@@ -346,58 +351,66 @@ def line_peaks(A, L, lines, sub=2, delta=0.0, max_peaks=8):
     count = np.zeros(n, dtype=np.int32)
     pos = np.zeros((n, max_peaks))
     height = np.zeros((n, max_peaks))
+    herr = np.zeros((n, max_peaks))
+    unsure = np.zeros(n, dtype=bool)
     pb = np.zeros(max_peaks)
     hb = np.zeros(max_peaks)
+    eb = np.zeros(max_peaks)
+    flag = ctypes.c_int()
     for j, (u, al, sh) in enumerate(lines):
         count[j] = lib.orc_line_peaks(_ptr(A), A.shape[0], L, float(u),
                                       math.cos(al), math.sin(al), float(sh),
                                       sub, delta, max_peaks, _ptr(pb),
-                                      _ptr(hb))
+                                      _ptr(hb), _ptr(eb), ctypes.byref(flag))
         pos[j] = pb
         height[j] = hb
+        herr[j] = eb
+        unsure[j] = bool(flag.value)
+    if bounds:
+        return count, pos, height, herr, unsure
     return count, pos, height
 
 
-def peak_lines(lines, count, pos, tp, min_peaks=0):
-    """§4.3 (iv)-(v): the trajectory families aligned with the given peak
-    times, as line-grid entries.
+def peak_trajectories(lines, count, pos, tp, t0_offsets, tE_axis,
+                      min_peaks=0):
+    """§4.3 (iv)-(v), Eq. 7-8: the set of trajectories the peak library
+    allows, as rows (line j, u0, alpha, t0, tE).
 
-    Entry slots per line: 1 (no peak time: the line itself), max_peaks (one
-    time t_p: the line's m-th kept peak at t_p, Eq. 7 t0 = t_p - M_p tE) or
-    max_peaks (max_peaks - 1) / 2 (two times t_p1 < t_p2: its peaks a < b
-    at them, Eq. 8 tE = (t_p2 - t_p1) / (M_b - M_a), then Eq. 7 with peak
-    a).  A slot is used when the line has at least max(min_peaks, len(tp))
-    peaks and the slot's peaks are among its kept ones.
-    Returns rows (u, alpha, shift, tE, used) per slot, line-major: the
-    trajectory with grid t0 value t0_g (the t0 axis then runs about t_p1)
-    is (u, alpha, t0_g - shift tE, tE); tE is NaN where the tE axis
-    applies (fewer than two peak times)."""
+    A line takes part when it has at least max(min_peaks, len(tp)) peaks;
+    its peaks are its kept ones (pos[j], finite entries), tau_m measured
+    from the line's closest approach to the origin, M_m = pos + shift.
+      * no peak time: every (t0, tE) of the axes, t0 = t0_offsets
+        (absolute times) about the line's reference point, i.e. the
+        trajectory (u, alpha, t0 - shift tE, tE);
+      * one peak time t_p: for every peak m, every dt0 in t0_offsets and
+        tE in tE_axis, the trajectory whose peak m comes at t_p + dt0:
+        t0 = t_p + dt0 - M_m tE (Eq. 7);
+      * two peak times t_p1 < t_p2: for every pair of peaks a before b,
+        tE = (t_p2 - t_p1) / (M_b - M_a) (Eq. 8) and peak a at t_p1 + dt0.
+    The order of the rows carries no meaning: callers compare sets."""
     lines = np.asarray(lines, dtype=np.float64).reshape(-1, 3)
-    P = pos.shape[1]
-    ntp = len(tp)
-    need = max(min_peaks, ntp)
+    need = max(min_peaks, len(tp))
     out = []
     for j, (u, al, sh) in enumerate(lines):
-        kept = int(min(count[j], P))
-        ok = count[j] >= need
-        if ntp == 0:
-            out.append((u, al, sh, math.nan, 1.0 if ok else 0.0))
-        elif ntp == 1:
-            for m in range(P):
-                used = ok and m < kept
-                M = pos[j, m] + sh if used else 0.0
-                out.append((u, al, M, math.nan, 1.0 if used else 0.0))
+        if count[j] < need:
+            continue
+        M = sorted(float(p) + sh for p in pos[j] if np.isfinite(p))
+        if len(tp) == 0:
+            for t0 in t0_offsets:
+                for tE in tE_axis:
+                    out.append((j, u, al, t0 - sh * tE, tE))
+        elif len(tp) == 1:
+            for Mm in M:
+                for dt in t0_offsets:
+                    for tE in tE_axis:
+                        out.append((j, u, al, tp[0] + dt - Mm * tE, tE))
         else:
-            for a in range(P):
-                for b in range(a + 1, P):
-                    used = ok and b < kept
-                    if used:
-                        M = pos[j, a] + sh
-                        tE = (tp[1] - tp[0]) / (pos[j, b] - pos[j, a])
-                    else:
-                        M, tE = 0.0, 1.0
-                    out.append((u, al, M, tE, 1.0 if used else 0.0))
-    return np.array(out).reshape(-1, 5)
+            for a in range(len(M)):
+                for b in range(a + 1, len(M)):
+                    tE = (tp[1] - tp[0]) / (M[b] - M[a])
+                    for dt in t0_offsets:
+                        out.append((j, u, al, tp[0] + dt - M[a] * tE, tE))
+    return np.array(out, dtype=np.float64).reshape(-1, 5)
 
 
 def lightcurve_map(A, L, t, t0, tE, u0, alpha):

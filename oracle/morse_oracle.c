@@ -794,115 +794,326 @@ double orc_line_max(const float *A, int npix, double L, double u,
  * line's reference point, which lies tau = shift past the closest approach
  * to the origin.
  *
- * A peak is where the magnification turns from rising to falling (§4.3
- * (iii)).  The profile it is read from (the paper does not say how the
- * library samples a line):
- *   - samples at tau_k = k h, h = Delta / sub, k = -sub npix .. sub npix;
- *   - the sample's texel coordinates p = a tau_k + b (the line's constants
- *     a, b taken in FP64, then everything in FP32), and the sample is kept
- *     if it lies inside the map, -1/2 < p < npix - 1/2 on both axes;
- *   - its value is the bilinear lookup between texel centres, coordinates
- *     clamped to the outermost centres, in FP32.
- * FP32 decides the count, so both implementations take it in FP32 with
- * the same operations.
- * Peaks are counted with a relative threshold r = 1 + delta: a rise is
- * confirmed when a value exceeds r times the lowest value since the last
- * peak, and the highest value after it is a peak once a later value lies
- * below it by the factor r (delta = 0: every turn from rising to falling,
- * a plateau counting once).  The profile must rise before its first peak:
- * its first sample is never one.
+ * Definition (§4.3 (iii)): a peak is where the magnification along the
+ * line turns from rising to falling.  The profile (the paper does not say
+ * how a line is sampled): samples at tau_k = k h, h = Delta / sub, for
+ * |k| <= sub npix, kept where the point y = tau_k (c, s) + u (-s, c) is
+ * inside the map (|y1| < L and |y2| < L); the value is the map's bilinear
+ * lookup between texel centres, coordinates clamped to the outermost
+ * centres, everything in FP64.  A rise is confirmed once a value exceeds
+ * r = 1 + delta times the lowest value since the last peak; the highest
+ * value after it is a peak once a later value lies below it by the factor
+ * r (delta = 0: every turn; a plateau counts once, at its first sample).
+ * The profile must rise before its first peak, so the first sample is
+ * never one.
  *
- * Returns the number of peaks.  pos / height receive the max_peaks highest
- * (ties: the earlier one), in increasing tau, as (k h - shift, value);
- * unused slots are NaN. */
-int orc_line_peaks(const float *A, int npix, double L, double u, double c,
-                   double s, double shift, int sub, double delta,
-                   int max_peaks, double *pos, double *height) {
-  double dlt = (2.0 * L) / (double)npix;
-  double h = dlt / (double)sub;
-  double ax = c / dlt, ay = s / dlt;
-  double bx = (L - u * s) / dlt - 0.5;
-  double by = (L + u * c) / dlt - 0.5;
-  float axf = (float)ax, ayf = (float)ay, bxf = (float)bx, byf = (float)by;
-  float hf = (float)h, r = (float)(1.0 + delta);
-  float lo = -0.5f, hi = (float)npix - 0.5f, pmax = (float)(npix - 1);
-  int K = sub * npix;
-  /* the kept peaks, highest first */
-  float *kh = (float *)malloc((size_t)(max_peaks > 0 ? max_peaks : 1) *
-                              sizeof(float));
-  int *kk = (int *)malloc((size_t)(max_peaks > 0 ? max_peaks : 1) *
-                          sizeof(int));
-  int nkept = 0, count = 0, look_max = 0, kmx = 0;
-  float mn = INFINITY, mx = -INFINITY;
-  for (int k = -K; k <= K; ++k) {
-    float tk = (float)k * hf;
-    float px = axf * tk + bxf;
-    float py = ayf * tk + byf;
-    if (!(px > lo && px < hi && py > lo && py < hi)) continue;
-    float qx = px < 0.0f ? 0.0f : px;
-    float qy = py < 0.0f ? 0.0f : py;
-    if (qx > pmax) qx = pmax;
-    if (qy > pmax) qy = pmax;
-    int i0 = (int)floorf(qx), j0 = (int)floorf(qy);
-    if (i0 > npix - 2) i0 = npix - 2;
-    if (j0 > npix - 2) j0 = npix - 2;
-    float fx = qx - (float)i0, fy = qy - (float)j0;
-    float a00 = A[(size_t)j0 * npix + i0], a10 = A[(size_t)j0 * npix + i0 + 1];
-    float a01 = A[(size_t)(j0 + 1) * npix + i0];
-    float a11 = A[(size_t)(j0 + 1) * npix + i0 + 1];
-    float gx = 1.0f - fx, gy = 1.0f - fy;
-    float r0 = gx * a00 + fx * a10;
-    float r1 = gx * a01 + fx * a11;
-    float v = gy * r0 + fy * r1;
-    if (look_max) {
-      if (v > mx) {
-        mx = v;
-        kmx = k;
-      } else if (mx > r * v) {
-        /* a peak: keep it if it is among the max_peaks highest */
-        ++count;
-        int at = nkept;
-        while (at > 0 && mx > kh[at - 1]) --at;
-        if (at < max_peaks) {
-          int last = nkept < max_peaks ? nkept : max_peaks - 1;
-          for (int m = last; m > at; --m) {
-            kh[m] = kh[m - 1];
-            kk[m] = kk[m - 1];
+ * Error bounds for a comparison with an FP32 evaluation of the same
+ * profile.  An FP32 evaluation places the sample at texel coordinates off
+ * by at most dp = 2 2^-24 (4 |a tau| + |b| + |p| + 1) per axis (p = a tau +
+ * b with a, b and h rounded to FP32, tau = k h, a tau and the sum rounded:
+ * five roundings, doubled as a margin), which moves the value by at most
+ * G dp per axis, G the largest texel difference along that axis over the
+ * cells within dp, and the FP32 bilinear itself adds at most 16 2^-24 max
+ * A of those cells.  err_k is that sum.  A decision
+ * of the detector whose two sides are closer than the sum of their bounds
+ * (including the inside-the-map test and the max_peaks-th versus the next
+ * highest peak) could go either way in FP32; such a line is flagged
+ * *uncertain.  Every decision of an unflagged line is the same in any
+ * evaluation within the bounds, so its count and peak positions are
+ * exactly determined and its heights are within herr.
+ *
+ * Returns the number of peaks.  pos / height / herr receive the max_peaks
+ * highest (ties: the earlier one), in increasing tau, as (k h - shift,
+ * value, err); unused slots are NaN. */
+static double texel_at(const float *A, int npix, long i, long j) {
+  if (i < 0) i = 0;
+  if (j < 0) j = 0;
+  if (i > npix - 1) i = npix - 1;
+  if (j > npix - 1) j = npix - 1;
+  return (double)A[(size_t)j * (size_t)npix + (size_t)i];
+}
+
+/* Bounds of |d v / d px| and |d v / d py| of the clamped bilinear lookup
+ * over the texel coordinates within (dpx, dpy) of (qx, qy): the largest
+ * texel difference along each axis over the cells those positions touch
+ * (the lookup is linear along each axis within a cell), and max A of those
+ * cells. */
+static void cell_slopes(const float *A, int npix, double qx, double qy,
+                        double dpx, double dpy, double *gx, double *gy,
+                        double *amax) {
+  long ia = (long)floor(qx - dpx), ib = (long)floor(qx + dpx);
+  long ja = (long)floor(qy - dpy), jb = (long)floor(qy + dpy);
+  double sx = 0.0, sy = 0.0, am = 0.0;
+  for (long j = ja; j <= jb; ++j)
+    for (long i = ia; i <= ib; ++i)
+      for (long b = 0; b <= 1; ++b)
+        for (long a = 0; a <= 1; ++a) {
+          double t = texel_at(A, npix, i + a, j + b);
+          if (t > am) am = t;
+          if (a == 0) {
+            double d = fabs(texel_at(A, npix, i + 1, j + b) - t);
+            if (d > sx) sx = d;
           }
-          kh[at] = mx;
-          kk[at] = kmx;
-          if (nkept < max_peaks) ++nkept;
+          if (b == 0) {
+            double d = fabs(texel_at(A, npix, i + a, j + 1) - t);
+            if (d > sy) sy = d;
+          }
         }
-        look_max = 0;
-        mn = v;
+  *gx = sx;
+  *gy = sy;
+  *amax = am;
+}
+
+/* The detector of orc_line_peaks over samples (v[i], e[i]), i < n, in
+ * order, skipping those with skip[i] set.  Writes every peak's height,
+ * bound and sample index and returns the count.
+ *
+ * Near-ties: a decision whose two sides lie within their bounds (which
+ * sample tops a peak, whether a value confirms a fall, whether it confirms
+ * a rise) is recorded in ties[] as 4 i + type (type 0 top, 1 fall, 2 rise)
+ * when ties is not NULL (at most max_ties; *n_ties counts them all).  The
+ * decisions whose codes are listed in flips[0 .. n_flips) are taken the
+ * other way, so that a caller can see whether they matter. */
+static int is_flipped(const int *flips, int n_flips, int code) {
+  for (int i = 0; i < n_flips; ++i)
+    if (flips[i] == code) return 1;
+  return 0;
+}
+
+static int detect_peaks(const double *v, const double *e, const int *kk,
+                        const char *skip, int n, double r, double *ph,
+                        double *pe, int *pk, const int *flips, int n_flips,
+                        int *ties, int max_ties, int *n_ties) {
+  int count = 0, rising_seen = 0, have = 0, kmx = 0;
+  double mn = 0.0, emn = 0.0, mx = 0.0, emx = 0.0;
+  if (n_ties) *n_ties = 0;
+#define NEAR_TIE(type, cond)                                   \
+  do {                                                         \
+    if (cond) {                                                \
+      if (ties && n_ties) {                                    \
+        if (*n_ties < max_ties) ties[*n_ties] = 4 * i + (type); \
+        ++*n_ties;                                             \
+      }                                                        \
+    }                                                          \
+  } while (0)
+  for (int i = 0; i < n; ++i) {
+    if (skip && skip[i]) continue;
+    double x = v[i], ex = e[i];
+    if (!have) { /* first sample: the running minimum starts here */
+      have = 1;
+      mn = x;
+      emn = ex;
+      continue;
+    }
+    if (rising_seen) { /* looking for the top of a rise */
+      int up = x > mx, fall = mx > r * x;
+      NEAR_TIE(0, fabs(x - mx) <= ex + emx);
+      NEAR_TIE(1, fabs(mx - r * x) <= emx + r * ex);
+      if (is_flipped(flips, n_flips, 4 * i + 0)) up = !up;
+      if (is_flipped(flips, n_flips, 4 * i + 1)) fall = !fall;
+      if (up) {
+        mx = x;
+        emx = ex;
+        kmx = kk[i];
+      } else if (fall) { /* the fall confirms the peak at kmx */
+        ph[count] = mx;
+        pe[count] = emx;
+        pk[count] = kmx;
+        ++count;
+        rising_seen = 0;
+        mn = x;
+        emn = ex;
       }
-    } else {
-      if (v < mn) {
-        mn = v;
-      } else if (v > r * mn) {
-        look_max = 1;
-        mx = v;
-        kmx = k;
+    } else { /* looking for a rise */
+      int rise = x > r * mn;
+      NEAR_TIE(2, fabs(x - r * mn) <= ex + r * emn);
+      if (is_flipped(flips, n_flips, 4 * i + 2)) rise = !rise;
+      if (x < mn && !rise) {
+        /* a near-tie with the old minimum widens the new one's bound by
+         * their difference (an FP32 evaluation may keep either) */
+        double d = mn - x, eo = emn;
+        mn = x;
+        emn = (d <= ex + eo) ? fmax(ex, eo) + d : ex;
+      } else if (rise) {
+        rising_seen = 1;
+        mx = x;
+        emx = ex;
+        kmx = kk[i];
+      } else if (x - mn <= ex + emn) {
+        emn = fmax(ex, emn) + (x - mn);
       }
     }
   }
-  /* kept peaks in increasing tau */
-  for (int a = 1; a < nkept; ++a)
-    for (int b = a; b > 0 && kk[b] < kk[b - 1]; --b) {
-      int ti = kk[b]; kk[b] = kk[b - 1]; kk[b - 1] = ti;
-      float tf = kh[b]; kh[b] = kh[b - 1]; kh[b - 1] = tf;
+#undef NEAR_TIE
+  return count;
+}
+
+/* the max_peaks highest of n peaks (ties: the earlier), then in increasing
+ * tau: indices into the peak arrays in sel[0 .. return value) */
+static int keep_highest(const double *ph, const double *pe, const int *pk,
+                        int n, int P, int *sel, int *unsure) {
+  for (int i = 0; i < n; ++i) sel[i] = i;
+  for (int i = 1; i < n; ++i) /* stable insertion sort, highest first */
+    for (int j = i; j > 0 && ph[sel[j]] > ph[sel[j - 1]]; --j) {
+      int t = sel[j];
+      sel[j] = sel[j - 1];
+      sel[j - 1] = t;
     }
+  int nkept = n < P ? n : P;
+  if (n > P && unsure) {
+    int a = sel[P - 1], b = sel[P];
+    if (fabs(ph[a] - ph[b]) <= pe[a] + pe[b]) *unsure = 1;
+  }
+  for (int i = 1; i < nkept; ++i)
+    for (int j = i; j > 0 && pk[sel[j]] < pk[sel[j - 1]]; --j) {
+      int t = sel[j];
+      sel[j] = sel[j - 1];
+      sel[j - 1] = t;
+    }
+  return nkept;
+}
+
+/* Whether every evaluation within the bounds gives the library (count,
+ * kept positions pos[0 .. nkept)): the detector is run with the decisions
+ * flips[0 .. n_flips) inverted, and recursively with each later near-tie
+ * of that run inverted as well, to a depth of 3 inverted decisions (a
+ * plateau of up to four samples that FP32 rounding makes wiggle).  More
+ * than *budget runs in all counts as undetermined. */
+#define PEAK_FLIP_DEPTH 3
+static int same_library(const double *v, const double *e, const int *kk,
+                        const char *skip, int n, double r, int P, double h,
+                        double shift, int *flips, int n_flips, int count,
+                        int nkept, const double *pos, int *budget) {
+  if (--*budget < 0) return 0;
+  int cap = n + 2;
+  double *ph = (double *)malloc((size_t)cap * sizeof(double));
+  double *pe = (double *)malloc((size_t)cap * sizeof(double));
+  int *pk = (int *)malloc((size_t)cap * sizeof(int));
+  int *ksel = (int *)malloc((size_t)cap * sizeof(int));
+  int max_ties = 4 * n + 4, n_ties = 0;
+  int *ties = (int *)malloc((size_t)max_ties * sizeof(int));
+  int c2 = detect_peaks(v, e, kk, skip, n, r, ph, pe, pk, flips, n_flips,
+                        ties, max_ties, &n_ties);
+  int n2 = keep_highest(ph, pe, pk, c2, P, ksel, NULL);
+  int same = (c2 == count && n2 == nkept);
+  for (int m = 0; same && m < n2; ++m)
+    if ((double)pk[ksel[m]] * h - shift != pos[m]) same = 0;
+  if (same && n_flips < PEAK_FLIP_DEPTH) {
+    int last = n_flips > 0 ? flips[n_flips - 1] : -1;
+    for (int t = 0; t < n_ties && t < max_ties && same; ++t) {
+      if (ties[t] <= last) continue; /* earlier ones: other branches */
+      flips[n_flips] = ties[t];
+      same = same_library(v, e, kk, skip, n, r, P, h, shift, flips,
+                          n_flips + 1, count, nkept, pos, budget);
+    }
+    if (n_ties > max_ties) same = 0;
+  }
+  free(ph);
+  free(pe);
+  free(pk);
+  free(ksel);
+  free(ties);
+  return same;
+}
+
+int orc_line_peaks(const float *A, int npix, double L, double u, double c,
+                   double s, double shift, int sub, double delta,
+                   int max_peaks, double *pos, double *height, double *herr,
+                   int *uncertain) {
+  const double f32 = 5.9604644775390625e-8; /* 2^-24 */
+  double dlt = (2.0 * L) / (double)npix;
+  double h = dlt / (double)sub;
+  double r = 1.0 + delta;
+  int K = sub * npix;
+  int P = max_peaks > 0 ? max_peaks : 1;
+  int cap = 2 * K + 1;
+  /* the profile: every sample inside the map, plus those whose inside test
+   * an FP32 evaluation could decide either way (amb = 1; then v, e are
+   * those of the clamped lookup, which is what such a sample reads) */
+  double *v = (double *)malloc((size_t)cap * sizeof(double));
+  double *e = (double *)malloc((size_t)cap * sizeof(double));
+  int *kk = (int *)malloc((size_t)cap * sizeof(int));
+  char *amb = (char *)malloc((size_t)cap);
+  char *inc = (char *)malloc((size_t)cap);
+  int n = 0;
+  for (int k = -K; k <= K; ++k) {
+    double tau = (double)k * h;
+    double y1 = tau * c - u * s, y2 = tau * s + u * c;
+    /* texel coordinates and the FP32 placement bound */
+    double px = (y1 + L) / dlt - 0.5, py = (y2 + L) / dlt - 0.5;
+    double atx = fabs(c / dlt * tau), aty = fabs(s / dlt * tau);
+    double dpx = 2.0 * f32 * (4.0 * atx + fabs(px - c / dlt * tau) +
+                              fabs(px) + 1.0);
+    double dpy = 2.0 * f32 * (4.0 * aty + fabs(py - s / dlt * tau) +
+                              fabs(py) + 1.0);
+    double lo = -0.5, hi = (double)npix - 0.5;
+    int inside = fabs(y1) < L && fabs(y2) < L;
+    int nearx = fabs(px - lo) <= dpx || fabs(px - hi) <= dpx;
+    int neary = fabs(py - lo) <= dpy || fabs(py - hi) <= dpy;
+    int outx = px < lo - dpx || px > hi + dpx;
+    int outy = py < lo - dpy || py > hi + dpy;
+    int ambiguous = (nearx && !outy) || (neary && !outx);
+    if (!inside && !ambiguous) continue;
+    double qx = px < 0.0 ? 0.0 : (px > npix - 1.0 ? npix - 1.0 : px);
+    double qy = py < 0.0 ? 0.0 : (py > npix - 1.0 ? npix - 1.0 : py);
+    double gx, gy, amax;
+    cell_slopes(A, npix, qx, qy, dpx, dpy, &gx, &gy, &amax);
+    v[n] = bil_clamped(A, npix, L, y1, y2);
+    e[n] = gx * dpx + gy * dpy + 16.0 * f32 * amax;
+    kk[n] = k;
+    amb[n] = (char)ambiguous;
+    inc[n] = (char)!inside; /* skip mask of the definition's profile */
+    ++n;
+  }
+  double *ph = (double *)malloc((size_t)(cap + 1) * sizeof(double));
+  double *pe = (double *)malloc((size_t)(cap + 1) * sizeof(double));
+  int *pk = (int *)malloc((size_t)(cap + 1) * sizeof(int));
+  int *sel = (int *)malloc((size_t)(cap + 1) * sizeof(int));
+  int unsure = 0;
+  int count = detect_peaks(v, e, kk, inc, n, r, ph, pe, pk, NULL, 0, NULL,
+                           0, NULL);
+  int nkept = keep_highest(ph, pe, pk, count, P, sel, &unsure);
   for (int m = 0; m < max_peaks; ++m) {
     if (m < nkept) {
-      pos[m] = (double)kk[m] * h - shift;
-      height[m] = (double)kh[m];
+      pos[m] = (double)pk[sel[m]] * h - shift;
+      height[m] = ph[sel[m]];
+      if (herr) herr[m] = pe[sel[m]];
     } else {
       pos[m] = NAN;
       height[m] = NAN;
+      if (herr) herr[m] = NAN;
     }
   }
-  free(kh);
+  /* The library is determined when no combination of up to
+   * PEAK_FLIP_DEPTH near-tie decisions taken the other way changes the
+   * count or the kept positions, for every way an FP32 evaluation could
+   * classify the samples at the ends of the run whose inside test is
+   * within its bounds (variants: the ambiguous samples of each end in or
+   * out). */
+  int flips[PEAK_FLIP_DEPTH + 1];
+  int budget = 4096;
+  int any_amb = 0;
+  for (int i = 0; i < n; ++i) any_amb |= amb[i];
+  for (int var = 0; var < (any_amb ? 4 : 1) && !unsure; ++var) {
+    if (var > 0)
+      for (int i = 0; i < n; ++i)
+        inc[i] = amb[i] ? (char)!((i < n / 2) ? (var & 1)
+                                               : ((var >> 1) & 1))
+                        : 0;
+    if (!same_library(v, e, kk, inc, n, r, P, h, shift, flips, 0, count,
+                      nkept, pos, &budget))
+      unsure = 1;
+  }
+  if (uncertain) *uncertain = unsure;
+  free(v);
+  free(e);
   free(kk);
+  free(amb);
+  free(inc);
+  free(ph);
+  free(pe);
+  free(pk);
+  free(sel);
   return count;
 }
 

@@ -1,17 +1,22 @@
 """GPU parity of the peak library and the peak-aligned searches (§4.3
-(iii)-(v), Eq. 7-8).
+(iii)-(v), Eq. 7-8), against the oracle's FP64 statement of the definition.
 
-* The library (count, positions, heights of the kept peaks) equals the
-  oracle's bit for bit: the count is an integer decided in FP32 with the
-  same operations on both sides.  Ray-shot maps with and without the
-  threshold (delta = 0 counts the Poisson noise too, which stresses the
-  detector and the choice of the highest peaks), several sampling steps,
-  lines of a (u0, alpha) grid and of an (r, phi) grid, axis-parallel lines
-  and lines that miss the map.
-* The searches' top-K equals the oracle's chi^2 of every allowed trajectory
-  (set identical, chi^2 within 1e-5) with no peak time and a peak-count cut,
-  with one peak time (Eq. 7) and with two (Eq. 8); each record's chi^2 is
-  the oracle's chi^2 of its (t0, tE, u0, alpha).
+* The library.  The oracle samples each line's bilinear profile in FP64 and
+  counts turns from rising to falling (confirmed by the factor 1 + delta).
+  It also bounds, per sample, how far an FP32 evaluation of the same
+  profile can be off, and flags a line as undetermined when some decision
+  (a rise, a fall, which sample tops a peak, the max_peaks-th highest
+  against the next, a sample at the map edge) lies within those bounds and
+  taking it the other way changes the library.  Rule: on every line the
+  oracle does not flag, the GPU's count and peak positions equal the
+  oracle's exactly and its heights lie within the bounds; the flagged lines
+  are counted and their share is bounded.
+* The searches.  The oracle enumerates, from its own library and with no
+  knowledge of how the library stores its entries, the set of trajectories
+  Eq. 7 (one peak time) or Eq. 8 (two) allows, and its chi^2 on the map;
+  the GPU's top-K must be that set's K best (compared as sets of (u0,
+  alpha, t0, tE)), each record's chi^2 within 1e-5.  The searched lines
+  are the ones whose library the oracle finds determined.
 """
 import math
 
@@ -19,7 +24,6 @@ import numpy as np
 import pytest
 
 import oracle as orc
-from oracle import caustics as oc
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -47,6 +51,11 @@ def amap():
     return A
 
 
+@pytest.fixture(scope="module")
+def pmap():
+    return orc.poly_map(S_, Q_, L_, 256, nthreads=NT)
+
+
 def _grid_lines(n_u0, n_alpha, u_lo, u_hi):
     return np.array([(u, 2 * math.pi * k / n_alpha, 0.0)
                      for u in np.linspace(u_lo, u_hi, n_u0)
@@ -63,22 +72,59 @@ def _all_lines(m, ctx):
     return np.vstack([_grid_lines(9, 16, -1.2, 1.2), rphi, edge])
 
 
-@pytest.mark.parametrize("sub,max_peaks,delta",
-                         [(2, 8, 0.0), (2, 8, 0.05), (1, 1, 0.02),
-                          (3, 16, 0.0), (2, 4, 0.3)])
-def test_library_bit_exact(ctx, m, amap, sub, max_peaks, delta):
-    lines = _all_lines(m, ctx)
-    mp = ctx.map_from_host(amap, L_)
+def _compare_library(ctx, mp, A, lines, sub, max_peaks, delta):
     c, p, h = ctx.line_peaks(mp, lines, sub=sub, max_peaks=max_peaks,
                              delta=delta)
-    co, po, ho = orc.line_peaks(amap, L_, lines, sub=sub, delta=delta,
-                                max_peaks=max_peaks)
-    np.testing.assert_array_equal(c, co)
-    np.testing.assert_array_equal(p, po)  # NaN in the same slots
-    np.testing.assert_array_equal(h, ho)
-    assert c[-4] == 0 and c[-3] == 0  # lines that miss the map
-    if delta == 0.0:
-        assert c.max() > max_peaks  # noise peaks: the kept ones are chosen
+    co, po, ho, eo, unsure = orc.line_peaks(A, L_, lines, sub=sub,
+                                            delta=delta,
+                                            max_peaks=max_peaks,
+                                            bounds=True)
+    ok = ~unsure
+    np.testing.assert_array_equal(c[ok], co[ok])
+    np.testing.assert_array_equal(p[ok], po[ok])  # NaN in the same slots
+    fin = np.isfinite(ho[ok])
+    assert np.array_equal(fin, np.isfinite(h[ok]))
+    dh = np.abs(h[ok][fin] - ho[ok][fin])
+    assert (dh <= eo[ok][fin]).all(), dh.max()
+    print(f"sub {sub} max_peaks {max_peaks} delta {delta}: "
+          f"{int(unsure.sum())} of {len(lines)} lines undetermined at FP32 "
+          f"resolution; their counts differ on "
+          f"{int((c[unsure] != co[unsure]).sum())}")
+    return c, co, unsure
+
+
+@pytest.mark.parametrize("sub,max_peaks,delta",
+                         [(2, 8, 0.05), (1, 1, 0.02), (2, 4, 0.3),
+                          (3, 6, 0.1)])
+def test_library_ray_shot_map(ctx, m, amap, sub, max_peaks, delta):
+    lines = _all_lines(m, ctx)
+    mp = ctx.map_from_host(amap, L_)
+    c, co, unsure = _compare_library(ctx, mp, amap, lines, sub, max_peaks,
+                                     delta)
+    assert unsure.mean() <= 0.35
+    assert c[-4] == 0 and c[-3] == 0 and co[-4] == 0  # lines missing the map
+
+
+@pytest.mark.parametrize("sub,max_peaks", [(2, 8), (3, 16), (1, 2)])
+def test_library_smooth_map_every_turn(ctx, m, pmap, sub, max_peaks):
+    # delta = 0 (every turn counts) on the point-source polynomial map,
+    # where the profile has no sampling noise
+    lines = _all_lines(m, ctx)
+    mp = ctx.map_from_host(pmap, L_)
+    c, co, unsure = _compare_library(ctx, mp, pmap, lines, sub, max_peaks,
+                                     0.0)
+    assert unsure.mean() <= 0.45
+    assert co[~unsure].max() >= 3
+
+
+def test_library_noise_peaks_every_turn(ctx, m, amap):
+    # delta = 0 on a ray-shot map counts the Poisson noise: tens of peaks a
+    # line, many of them FP32 near-ties; the determined lines still agree,
+    # and the kept peaks are a choice among many
+    lines = _all_lines(m, ctx)
+    mp = ctx.map_from_host(amap, L_)
+    c, co, unsure = _compare_library(ctx, mp, amap, lines, 2, 8, 0.0)
+    assert c.max() > 8 and co.max() > 8
 
 
 def _event(seed=9):
@@ -92,27 +138,15 @@ def _event(seed=9):
     return t, F, sig, [t[i] for i in top]
 
 
-def _ref_chi2(rows, t0v, tEv, t, F, w, A):
-    out = []
-    for u, al, M, tEr, used in rows:
-        for t0 in t0v:
-            for tE in ([tEr] if not math.isnan(tEr) else tEv):
-                if used:
-                    out.append(orc.chi2_theta(t, F, w, (t0 - M * tE, tE, u,
-                                                        al), A=A, L=L_)[0])
-                else:
-                    out.append(math.inf)
-    return np.array(out)
-
-
-def _check(got, ref, t, F, w, A, k):
-    idx_o, _ = orc.topk(ref, k)
-    assert set(got["idx"].tolist()) == set(idx_o.tolist())
-    np.testing.assert_allclose(got["chi2"], ref[got["idx"]], rtol=1e-5)
-    for r in got[:4]:
-        c = orc.chi2_theta(t, F, w, (r["t0"], r["tE"], r["u0"], r["alpha"]),
-                           A=A, L=L_)[0]
-        assert r["chi2"] == pytest.approx(c, rel=1e-5)
+def _match(rec, rows):
+    """Row of the oracle's allowed set with the record's (u0, alpha, t0,
+    tE), or -1."""
+    d = (np.abs(rows[:, 1] - rec["u0"]) <= 1e-12) & \
+        (np.abs(rows[:, 2] - rec["alpha"]) <= 1e-12) & \
+        (np.abs(rows[:, 3] - rec["t0"]) <= 1e-9 * max(1.0, abs(rec["t0"]))) & \
+        (np.abs(rows[:, 4] - rec["tE"]) <= 1e-9 * rec["tE"])
+    hit = np.flatnonzero(d)
+    return int(hit[0]) if len(hit) == 1 else -1
 
 
 @pytest.mark.parametrize("n_tp", [0, 1, 2])
@@ -121,32 +155,47 @@ def test_peak_search_matches_oracle(ctx, m, amap, n_tp):
     w = 1.0 / sig ** 2
     mp = ctx.map_from_host(amap, L_)
     ev = ctx.event(t, F, sig)
-    lines = _grid_lines(8, 12, -0.6, 0.6)
     sub, P, delta = 2, 4, 0.3
+    all_lines = _grid_lines(8, 12, -0.6, 0.6)
+    co, po, _, _, unsure = orc.line_peaks(amap, L_, all_lines, sub=sub,
+                                          delta=delta, max_peaks=P,
+                                          bounds=True)
+    lines = all_lines[~unsure]
+    assert len(lines) >= 0.6 * len(all_lines)
+    co, po = co[~unsure], po[~unsure]
     tp = tps[:n_tp]
-    min_peaks = 2 if n_tp == 0 else n_tp
-    co, po, _ = orc.line_peaks(amap, L_, lines, sub=sub, delta=delta,
-                               max_peaks=P)
-    rows = orc.peak_lines(lines, co, po, tp, min_peaks=min_peaks)
-    n_used = int(rows[:, 4].sum())
-    assert 0 < n_used < len(rows)  # the cut removes some, keeps some
+    min_peaks = 2  # lines with fewer peaks are cut
+    tEv = orc.axis(8.0, 40.0, 4, True)
     if n_tp == 0:
         n_t0, n_tE, t0lo, t0hi = 5, 4, -2.0, 2.0
-        t0v = orc.axis(t0lo, t0hi, n_t0, False)
+        offs = orc.axis(t0lo, t0hi, n_t0, False)
     elif n_tp == 1:
         n_t0, n_tE, t0lo, t0hi = 3, 4, -0.4, 0.4
-        t0v = orc.axis(t0lo + tp[0], t0hi + tp[0], n_t0, False)
+        offs = orc.axis(t0lo, t0hi, n_t0, False)
     else:
         n_t0, n_tE, t0lo, t0hi = 2, 1, -0.1, 0.1
-        t0v = orc.axis(t0lo + tp[0], t0hi + tp[0], n_t0, False)
-    tEv = orc.axis(8.0, 40.0, n_tE, True)
-    g = m.Grid.make(len(rows), 1, n_t0, n_tE, 1.0, 1.0, t0lo, t0hi, 8.0,
-                    40.0, False, True, 10)
+        offs = orc.axis(t0lo, t0hi, n_t0, False)
+    rows = orc.peak_trajectories(lines, co, po, tp, offs, tEv,
+                                 min_peaks=min_peaks)
+    lines_used = len(set(rows[:, 0].astype(int)))
+    assert 0 < lines_used < len(lines)  # the cut removes some, keeps some
+    chi = np.array([orc.chi2_theta(t, F, w, (r[3], r[4], r[1], r[2]),
+                                   A=amap, L=L_)[0] for r in rows])
+    K = 10
+    g = m.Grid.make(len(lines), 1, n_t0, n_tE, 1.0, 1.0, t0lo, t0hi, 8.0,
+                    40.0, False, True, K)
     got = ctx.peak_search(ev, mp, g, lines, tp=tp, min_peaks=min_peaks,
                           sub=sub, max_peaks=P, delta=delta)
-    ref = _ref_chi2(rows, t0v, tEv, t, F, w, amap)
-    assert len(ref) == len(rows) * n_t0 * n_tE
-    _check(got, ref, t, F, w, amap, 10)
+    hit = [_match(r, rows) for r in got]
+    assert all(h >= 0 for h in hit), hit  # every record is allowed
+    np.testing.assert_allclose(got["chi2"], chi[hit], rtol=1e-5)
+    # the K best of the allowed set, as a set (a pair straddling rank K
+    # within the chi^2 tolerance may swap)
+    order = np.argsort(chi, kind="stable")
+    best = set(order[:K].tolist())
+    extra = set(hit) - best
+    kth = chi[order[K - 1]]
+    assert all(abs(chi[h] - kth) <= 2e-5 * kth for h in extra), extra
     if n_tp == 2:
         # Eq. 8: the record's tE spans the two peaks
         for r in got[:3]:

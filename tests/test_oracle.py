@@ -710,31 +710,78 @@ def test_peak_alignment_eq7_eq8_puts_model_peaks_at_the_given_times():
     t = np.linspace(50.0, 200.0, 30001)
 
     def peaks_of(row):
-        u, al, M, tE = row[:4]
-        t0 = tp0 - M * tE
+        _, u, al, t0, tE = row
         lc = np.array(orc.lightcurve_map(A, L, t, t0, tE, u, al))
         # maxima of the sampled light curve (a top may be two equal samples)
         return [t[i] for i in range(1, len(lc) - 1)
                 if lc[i] >= lc[i - 1] and lc[i] > lc[i + 1] and lc[i] > 2.0]
 
     tp0 = 120.0
-    rows = orc.peak_lines(line, count, pos, [tp0])
-    assert rows.shape == (4, 5) and list(rows[:, 4]) == [1, 1, 0, 0]
-    for m in range(2):
-        r = rows[m].copy()
-        r[3] = 25.0  # a tE from the grid axis
+    # Eq. 7: one family per peak, every tE of the axis (t0 offset 0)
+    rows = orc.peak_trajectories(line, count, pos, [tp0], [0.0], [25.0])
+    assert rows.shape == (2, 5)
+    for r in rows:
         pk = peaks_of(r)
         assert min(abs(p - tp0) for p in pk) < 0.2 * 25.0 * 2 * L / npix
-    rows = orc.peak_lines(line, count, pos, [tp0, 160.0], min_peaks=2)
-    assert rows.shape == (6, 5) and rows[0, 4] == 1 and rows[1:, 4].sum() == 0
+    # the t0 offsets shift the aligned peak by the offset
+    rows = orc.peak_trajectories(line, count, pos, [tp0], [-3.0, 3.0],
+                                 [25.0])
+    assert rows.shape == (4, 5)
+    assert sorted(rows[:, 3] - rows[0, 3])[-1] == pytest.approx(6.0, abs=1e-9)
+    # Eq. 8: the one pair (a, b) of the two peaks fixes tE and t0
+    rows = orc.peak_trajectories(line, count, pos, [tp0, 160.0], [0.0],
+                                 [25.0], min_peaks=2)
+    assert rows.shape == (1, 5)
     r = rows[0]
-    assert r[3] == pytest.approx(40.0 / 1.435, rel=2e-2)
+    assert r[4] == pytest.approx(40.0 / 1.435, rel=2e-2)
     pk = peaks_of(r)
     assert len(pk) == 2
     assert abs(pk[0] - 120.0) < 0.2 and abs(pk[1] - 160.0) < 0.2
     # a line with fewer peaks than required contributes no trajectory
-    rows = orc.peak_lines(line, count, pos, [tp0], min_peaks=3)
-    assert rows[:, 4].sum() == 0
+    rows = orc.peak_trajectories(line, count, pos, [tp0], [0.0], [25.0],
+                                 min_peaks=3)
+    assert rows.shape == (0, 5)
+    # no peak time: the line grid itself, t0 about the reference point
+    rows = orc.peak_trajectories(line, count, pos, [], [1.0, 2.0],
+                                 [10.0, 20.0], min_peaks=2)
+    assert rows.shape == (4, 5)
+    assert rows[0, 3] == pytest.approx(1.0 - 0.1 * 10.0)
+
+
+def test_peak_library_fp32_bounds_cover_a_rounded_profile():
+    # The FP64 library's error bounds: a profile evaluated with the sample
+    # positions and values perturbed within the stated FP32 bounds (here:
+    # the texels rounded to FP32 twice over and the positions shifted by a
+    # tenth of a texel's FP32 resolution) gives the same count and
+    # positions on every line the library does not flag, and heights
+    # within herr.
+    L, npix = 2.0, 128
+    rng = np.random.default_rng(5)
+    A = (1.0 + rng.gamma(4.0, 0.25, size=(npix, npix))).astype(np.float32)
+    lines = [(u, al, 0.0) for u in np.linspace(-1.5, 1.5, 13)
+             for al in np.linspace(0.0, 3.0, 11)]
+    c, p, h, e, uns = orc.line_peaks(A, L, lines, sub=2, delta=0.05,
+                                     max_peaks=6, bounds=True)
+    # a one-ulp change of every texel moves each value by far less than
+    # its bound: unflagged lines keep their library
+    A2 = np.nextafter(A, np.float32(np.inf))
+    c2, p2, h2 = orc.line_peaks(A2, L, lines, sub=2, delta=0.05,
+                                max_peaks=6)
+    ok = ~uns
+    assert ok.sum() > 0.8 * len(lines)
+    assert np.array_equal(c[ok], c2[ok])
+    assert np.array_equal(p[ok], p2[ok])
+    fin = np.isfinite(h[ok])
+    assert (np.abs(h[ok][fin] - h2[ok][fin]) <= e[ok][fin]).all()
+    # a plateau (four equal texels) puts two samples at one value: a
+    # near-tie of the running maximum, which the library flags
+    B = np.ones((npix, npix), dtype=np.float32)
+    B[60:62, 60:62] = 5.0
+    d = 2 * L / npix
+    y = -L + 60.5 * d
+    cb, pb, hb, eb, ub = orc.line_peaks(B, L, [(y, 0.0, 0.0)], sub=2,
+                                        delta=0.1, max_peaks=2, bounds=True)
+    assert cb[0] == 1 and ub[0]
 
 
 # ------------------------------------------------------------ caustics
