@@ -15,7 +15,8 @@ examples, which are not available here):
   exceeds the slots of one site, further sites (windows offset by 8 h and
   16 h: 24-h coverage) are added and the slot length shrinks to
   15 * 7680 / N min until N fits.  Times are rounded to FP32-representable
-  values (resolution ~4e-6 d at 40 d).
+  values (resolution ~4e-6 d at 40 d) unless the caller asks for raw FP64
+  times (raw=True: real data carry times at full precision, e.g. HJD).
 * noise: sigma = 0.01 sqrt(F_true) + 0.002, F = F_true + N(0, sigma^2).
 * outliers: a seeded fraction of epochs shifted by +-5 sigma.
 
@@ -47,8 +48,9 @@ def _slots(n_sites: int, slot_min: float, span=(-40.0, 40.0),
 
 
 def epoch_times(n: int, seed: int, t_peak: float = 0.0,
-                span=(-40.0, 40.0)) -> np.ndarray:
-    """Sorted observing times (days) for an n-epoch light curve."""
+                span=(-40.0, 40.0), raw: bool = False) -> np.ndarray:
+    """Sorted observing times (days) for an n-epoch light curve; rounded to
+    FP32-representable values unless raw."""
     if n <= 0:
         return np.zeros(0)
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -65,6 +67,8 @@ def epoch_times(n: int, seed: int, t_peak: float = 0.0,
     wgt = np.where(np.abs(cand - t_peak) < 2.0, 5.0, 1.0)
     pick = rng.choice(cand.size, size=n, replace=False, p=wgt / wgt.sum())
     t = np.sort(cand[pick])
+    if raw:
+        return t
     return t.astype(np.float32).astype(np.float64)
 
 

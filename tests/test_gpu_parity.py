@@ -367,36 +367,34 @@ def test_cfg1_full_size_fp32_map(ctx, cfg1_setup):
     assert int(cg.sum(dtype=np.uint64)) + off + lost == c["nray"] ** 2
 
 
-def test_cfg1_full_size_search_sampled(ctx, m, cfg1_setup):
-    """1.44 M trajectories x 3000 epochs, top-K = 256, in the launch
-    configuration the benchmark times; checked on the reported fits and a
-    seeded sample of trajectories the oracle evaluates one by one."""
+@pytest.mark.parametrize("s,q", [(0.9, 5e-4), (1.0, 1e-2)])
+def test_cfg1_full_size_search_dense_oracle(ctx, m, cfg1_setup, s, q):
+    """Config 1 at full size, in the launch configuration the benchmark
+    times: the map of 10^8 FP32-deflected rays built on the GPU, 1.44 M
+    trajectories x 3000 epochs, top-K = 256.  The oracle computes the dense
+    chi^2 of every trajectory on the same FP32 map values (the event's truth
+    map and a resonant-caustic map); bars: every trajectory's chi^2 within
+    1e-5 (GPU dense sweep), the top-256 set identical to the oracle's full
+    sort (pairs within the tolerance straddling rank K may swap; counted),
+    and every record's chi^2 within 1e-5."""
     c, A_o, co, t, F, sig = cfg1_setup
-    mp = ctx.map_from_host(A_o, c["L"])
+    mp = ctx.build_map(s, q, c["L"], c["npix"], c["nray"],
+                       image_halfwidth=c["X"], deflect="fp32")
+    A = mp.values()
     ev = ctx.event(t, F, sig)
     g = _grid(m, c["grid"], c["top_k"])
     og = _ogrid(c["grid"])
-    got = ctx.grid_chi2(ev, mp, g)
     w = 1.0 / sig ** 2
-    assert np.all(np.diff(got["chi2"]) >= 0)
-    assert len(set(got["idx"].tolist())) == c["top_k"]
-    for rec in got[::16]:
-        o, *_ = orc.grid_chi2(og, t, F, w, A=A_o, L=c["L"],
-                              first=int(rec["idx"]), count=1)
-        assert rec["chi2"] == pytest.approx(o[0], rel=CHI2_RTOL)
-    rng = np.random.default_rng(42)
-    kth = got["chi2"][-1]
-    for start in rng.integers(0, og.size - 64, 6):
-        o, *_ = orc.grid_chi2(og, t, F, w, A=A_o, L=c["L"], first=int(start),
-                              count=64, nthreads=NT)
-        d, _, _ = ctx.grid_chi2_dense(ev, mp, g, int(start), 64)
-        assert np.max(_rel(d, o)) <= CHI2_RTOL
-        # validity of the top-K on the sample: nothing sampled beats rank K
-        # unless it is in the list
-        listed = set(got["idx"].tolist())
-        for j in range(64):
-            if o[j] < kth * (1 - 2 * CHI2_RTOL):
-                assert int(start) + j in listed
+    o_chi2, *_ = orc.grid_chi2(og, t, F, w, A=A, L=c["L"], nthreads=NT)
+    got = ctx.grid_chi2(ev, mp, g)
+    swaps = _check_topk(got, o_chi2, c["top_k"])
+    d, _, _ = ctx.grid_chi2_dense(ev, mp, g)
+    rel = _rel(d, o_chi2)
+    assert np.max(rel) <= CHI2_RTOL, (np.max(rel), int(np.argmax(rel)))
+    print(f"(s, q) = ({s}, {q}): {og.size} trajectories, max chi^2 relative "
+          f"error {np.max(rel):.2e}, top-{c['top_k']} swaps at rank K: "
+          f"{swaps}")
+    assert swaps <= 2
 
 
 def test_sweep_equals_per_map_searches(ctx, m):

@@ -1,14 +1,34 @@
-"""Precision study of the map storage forms on resonant-caustic maps
-(4096^2 texels over [-2, 2]^2 from 1.6e9 FP32-deflected rays; FP16
-log10(A) and FP32 A tables) against the FP64 CPU oracle on a seeded ~1 %
-subsample of the 200,000-trajectory grid of the batched workload.
+"""Precision study of the map storage forms (configuration 4): 16 (s, q)
+pairs near resonant caustics (s log-spaced in [0.8, 1.25], q log-spaced in
+[1e-4, 1e-2]), maps of 4096^2 texels over [-2, 2]^2 from 1.6e9
+FP32-deflected rays, stored as FP32 A and as FP16 log10(A); light curves
+from the 256-event batch of configuration 3 (lengths log-uniform in
+[200, 20000]); FP32 lookups and sums, FP64 solve; per-trajectory chi^2 and
+top-16 against the FP64 CPU oracle on a seeded 1 % subsample of the
+200,000-trajectory grid (20 runs of 100 consecutive trajectories per map).
 
-Reported per (s, q): the relative chi^2 error of each table against the
-oracle's FP64 map and the overlap of the subsample's top-16.  Bars: the
-FP32 table within 1e-3 relative at the median (the FP32 deflection moves a
-few rays between bins: map relative L1 <= 1e-3), the FP16 table within
-5e-3 at every trajectory and 1e-3 at the median against the same FP32
-map's chi^2 (the half quantisation of log10 A).
+Bars, per (s, q) and event:
+* FP32 table against the oracle on the same FP32 texel values: every
+  trajectory within 5e-5, the subsample's top-16 identical.  The 1e-5 of
+  the smaller maps (met at 1024^2 on all 1.44 M trajectories of config 1)
+  does not hold at 4096^2: a data point's centred pixel coordinate v =
+  a t + b is an FP32 value of up to 2048 texels, built from terms of up to
+  ~4000 texels, so it is resolved to about 2^-24 (|v| + |a t| + |b|) ~
+  3e-4 texel (4x coarser than at 1024^2), which moved chi^2 by up to
+  2.0e-5 on the worst of 8000 trajectories per map;
+* FP16 table against the oracle on the decoded FP16 texels (10^x of every
+  half code): the same bar, the top-16 identical;
+* FP16 table against the FP32 table of the same map (the half quantisation
+  of log10 A, a relative error of A up to ln(10) 2^-12 |log10 A|, 2.2e-3
+  at A = 1e4, which the high-magnification epochs of a well-fitted event
+  carry into chi^2 at their signal-to-noise): every trajectory within
+  1e-2, median within 1e-3 (the maxima per map are printed; 5.8e-3 to
+  7.0e-3 on the most magnified events);
+* both tables against the oracle's own map (FP64 deflection of the same
+  rays): median within 1e-3, 99th percentile within 1e-2, every trajectory
+  within 5e-2; the FP32 deflection moves rays between bins (map relative
+  L1 <= 1e-3, a few rays of the ~40 per texel near the lenses), so these
+  are the two maps' difference, printed with the top-16 overlap.
 """
 import numpy as np
 import pytest
@@ -19,7 +39,10 @@ import synth
 pytestmark = pytest.mark.gpu
 
 NT = orc.threads_default()
-PAIRS = [(0.9, 1e-3), (1.1, 3e-3), (1.0, 1e-2)]
+S_AX = np.exp(np.linspace(np.log(0.8), np.log(1.25), 4))
+Q_AX = np.exp(np.linspace(np.log(1e-4), np.log(1e-2), 4))
+PAIRS = [(float(s), float(q)) for s in S_AX for q in Q_AX]
+N_EVENTS = 4  # of the 256-event batch, per map (seeded)
 
 
 @pytest.fixture(scope="module")
@@ -35,13 +58,44 @@ def ctx(m):
     c.close()
 
 
-@pytest.mark.parametrize("s,q", PAIRS)
-def test_fp16_and_fp32_tables_against_fp64_oracle(ctx, m, s, q):
+@pytest.fixture(scope="module")
+def batch():
     cfg = synth.CFG3
+    lens = synth.event_lengths(cfg["n_events"], cfg["seed"], cfg["len_lo"],
+                               cfg["len_hi"])
+    truths = synth.truth_draws(cfg["n_events"], cfg["seed"])
+    return cfg, lens, truths
+
+
+def _event(cfg, lens, truths, i):
+    tr = truths[i]
+    seed = cfg["seed"] * 1000 + i
+    t = synth.epoch_times(int(lens[i]), seed, tr["t0"])
+    At = orc.lightcurve_point(tr["s"], tr["q"], t, tr["t0"], tr["tE"],
+                              tr["u0"], tr["alpha"])
+    F, sig = synth.photometry(tr["Fs"] * At + tr["Fb"], seed)
+    return t, F, sig
+
+
+def _topk_same(x, o, k=16, tol=1e-5):
+    """The k best of x and of o are the same set, except pairs whose chi^2
+    lie within the tolerance of o's k-th (which may swap)."""
+    a = set(np.argsort(x, kind="stable")[:k].tolist())
+    b = set(np.argsort(o, kind="stable")[:k].tolist())
+    kth = np.sort(o)[k - 1]
+    return all(abs(o[j] - kth) <= 2 * tol * kth for j in a ^ b)
+
+
+@pytest.mark.parametrize("s,q", PAIRS)
+def test_storage_forms_against_fp64_oracle(ctx, m, batch, s, q):
+    cfg, lens, truths = batch
     L, npix, nray, X = 2.0, 4096, 40000, 3.0
     mp = ctx.build_map(s, q, L, npix, nray, image_halfwidth=X,
                        deflect="fp32", fp16log=True)
-    A_o, *_ = orc.build_map(s, q, L, npix, nray, X, nthreads=NT)
+    A32 = mp.values()
+    codes, _ = mp.half()
+    A16 = orc.half_decode(codes)
+    A64, *_ = orc.build_map(s, q, L, npix, nray, X, nthreads=NT)
     g = cfg["grid"]
     grid = m.Grid.make(g["n_u0"], g["n_alpha"], g["n_t0"], g["n_tE"],
                        g["u0_lo"], g["u0_hi"], g["t0_lo"], g["t0_hi"],
@@ -49,36 +103,49 @@ def test_fp16_and_fp32_tables_against_fp64_oracle(ctx, m, s, q):
     og = orc.Grid(g["n_u0"], g["n_alpha"], g["n_t0"], g["n_tE"], g["u0_lo"],
                   g["u0_hi"], g["t0_lo"], g["t0_hi"], g["tE_lo"],
                   g["tE_hi"], g["u0_log"], g["tE_log"])
-    rng = np.random.default_rng(41)
-    # 20 seeded runs of 100 consecutive trajectories (1 % of the grid)
+    rng = np.random.default_rng(int(1e6 * s) ^ int(1e8 * q))
+    events = rng.choice(cfg["n_events"], N_EVENTS, replace=False)
     starts = np.sort(rng.choice(og.size // 100, 20, replace=False)) * 100
-    tr = synth.truth_draws(1, 7)[0]
-    t = synth.epoch_times(2000, 7, 0.0)
-    At = orc.lightcurve_point(s, q, t, 0.0, tr["tE"], tr["u0"], tr["alpha"])
-    F, sig = synth.photometry(tr["Fs"] * At + tr["Fb"], 7)
-    ev = ctx.event(t, F, sig)
-    c16, c32, co = [], [], []
-    for st in starts:
-        mp.set_lookup(True)
-        a, *_ = ctx.grid_chi2_dense(ev, mp, grid, int(st), 100)
-        c16.append(a)
-        mp.set_lookup(False)
-        b, *_ = ctx.grid_chi2_dense(ev, mp, grid, int(st), 100)
-        c32.append(b)
-        o, *_ = orc.grid_chi2(og, t, F, 1.0 / sig ** 2, A=A_o, L=L,
-                              first=int(st), count=100, nthreads=NT)
-        co.append(o)
-    c16, c32, co = map(np.concatenate, (c16, c32, co))
-    r32 = np.abs(c32 - co) / co
-    r16 = np.abs(c16 - co) / co
-    q16 = np.abs(c16 - c32) / c32
-    top = [set(np.argsort(x, kind="stable")[:16].tolist())
-           for x in (c16, c32, co)]
-    print(f"(s, q) = ({s}, {q}): FP32 vs oracle median {np.median(r32):.2e} "
-          f"p99 {np.quantile(r32, 0.99):.2e} max {r32.max():.2e}; FP16 vs "
-          f"oracle median {np.median(r16):.2e} p99 {np.quantile(r16, 0.99):.2e}"
-          f" max {r16.max():.2e}; FP16 vs FP32 max {q16.max():.2e}; top-16 "
-          f"overlap with the oracle FP32 {len(top[1] & top[2])}/16, FP16 "
-          f"{len(top[0] & top[2])}/16")
-    assert np.median(r32) <= 1e-3
-    assert q16.max() <= 5e-3 and np.median(q16) <= 1e-3
+    rows = []
+    for i in events:
+        t, F, sig = _event(cfg, lens, truths, int(i))
+        w = 1.0 / sig ** 2
+        ev = ctx.event(t, F, sig)
+        c16, c32, o32, o16, o64 = [], [], [], [], []
+        for st in starts:
+            mp.set_lookup(True)
+            c16.append(ctx.grid_chi2_dense(ev, mp, grid, int(st), 100)[0])
+            mp.set_lookup(False)
+            c32.append(ctx.grid_chi2_dense(ev, mp, grid, int(st), 100)[0])
+            for A, out in ((A32, o32), (A16, o16), (A64, o64)):
+                out.append(orc.grid_chi2(og, t, F, w, A=A, L=L,
+                                         first=int(st), count=100,
+                                         nthreads=NT)[0])
+        c16, c32, o32, o16, o64 = map(np.concatenate,
+                                      (c16, c32, o32, o16, o64))
+        r32 = np.abs(c32 - o32) / o32
+        r16 = np.abs(c16 - o16) / o16
+        q16 = np.abs(c16 - c32) / c32
+        d32 = np.abs(c32 - o64) / o64
+        d16 = np.abs(c16 - o64) / o64
+        assert r32.max() <= 5e-5, r32.max()
+        assert r16.max() <= 5e-5, r16.max()
+        assert _topk_same(c32, o32, tol=5e-5)
+        assert _topk_same(c16, o16, tol=5e-5)
+        assert q16.max() <= 1e-2 and np.median(q16) <= 1e-3
+        assert np.median(d32) <= 1e-3 and np.median(d16) <= 1e-3
+        assert np.quantile(d32, 0.99) <= 1e-2 and np.quantile(d16, 0.99) <= 1e-2
+        assert d32.max() <= 5e-2 and d16.max() <= 5e-2
+        ov32 = len(set(np.argsort(c32)[:16]) & set(np.argsort(o64)[:16]))
+        ov16 = len(set(np.argsort(c16)[:16]) & set(np.argsort(o64)[:16]))
+        rows.append((int(i), len(t), r32.max(), r16.max(), q16.max(),
+                     np.median(d32), d32.max(), np.median(d16), d16.max(),
+                     ov32, ov16))
+        ev.free()
+    mp.free()
+    for r in rows:
+        print(f"(s, q) = ({s:.3f}, {q:.2e}) event {r[0]} ({r[1]} epochs): "
+              f"same-map FP32 {r[2]:.1e} FP16 {r[3]:.1e}; FP16 vs FP32 max "
+              f"{r[4]:.1e}; vs FP64 map FP32 median {r[5]:.1e} max "
+              f"{r[6]:.1e}, FP16 median {r[7]:.1e} max {r[8]:.1e}; top-16 "
+              f"overlap with the FP64 map FP32 {r[9]}/16 FP16 {r[10]}/16")
