@@ -192,9 +192,11 @@ morse_status morse_map_half(const morse_map *map, uint16_t *host_codes,
 /* Copy a light curve to the device: n epochs with times t (days), fluxes
  * and 1-sigma errors (w = 1/sigma^2), in any order (stored sorted by time,
  * which the search relies on).  Times are stored as FP32 offsets
- * t - t_ref, so t_ref should lie within the data (resolution ~4e-6 d for
- * offsets up to 40 d); grid t0 values are absolute times in the same frame
- * as t.  Requires n >= 3, every value finite, sigma > 0.
+ * t - t_ref, computed in FP64 on the host, so t_ref should lie within the
+ * data (resolution ~4e-6 d for offsets up to 40 d; real data in HJD go
+ * through the same path); grid t0 values are absolute times in the same
+ * frame as t.  Requires n >= 3, every value finite, sigma > 0, and
+ * |t - t_ref| <= 1e5 d for every epoch (FP32 offsets resolve 0.004 d there).
  * Errors: EINVAL, ENOMEM, ECUDA. */
 morse_status morse_event_create(morse_ctx *ctx, const double *t,
                                 const double *flux, const double *sigma,
@@ -295,6 +297,20 @@ morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
                              const morse_map *map, const morse_grid *grid,
                              morse_fit *out);
 
+/* morse_grid_chi2 restricted to the trajectories with index in
+ * [first, first + count): the top_k smallest chi^2 among them, ordered by
+ * (chi2, idx), idx the index in the whole grid (tail idx = -1, chi2 = +inf
+ * if the range has fewer than top_k).  Each trajectory's chi^2 does not
+ * depend on the range, so the top-K lists of ranges that partition the grid,
+ * merged by morse_topk_merge, equal the whole grid's list bit for bit: the
+ * shard of one map's search that a GPU (or a call) takes when the grid is
+ * split across several.  Errors: EINVAL (range outside the grid), ENOMEM,
+ * ECUDA, ETIMEOUT. */
+morse_status morse_grid_chi2_range(morse_ctx *ctx, const morse_event *ev,
+                                   const morse_map *map,
+                                   const morse_grid *grid, int64_t first,
+                                   int64_t count, morse_fit *out);
+
 /* morse_grid_chi2 over a grid of arbitrary lines: trajectory
  * (j, i_t0, i_tE), index (j n_t0 + i_t0) n_tE + i_tE, follows line j of
  * lines[3 j .. 3 j + 2] = (u, alpha, shift) (morse_rphi_lines) with t0 the
@@ -363,27 +379,31 @@ morse_status morse_peak_search(morse_ctx *ctx, const morse_event *ev,
 /* morse_grid_chi2 without any device allocation.  The paper has no
  * counterpart: this is a deployment variant of the same search.
  *
- * For callers that must not let the library call cudaMalloc or cudaFree in
- * their hot loop -- cudaFree waits for the whole device and so stalls every
- * other stream of a latency-bound pipeline, allocation is not available
- * while a stream is being captured, and some applications run under a
- * fixed, pre-reserved memory budget.  Such callers create the context,
+ * For callers that must not let the library call cudaMalloc or cudaFree
+ * once set-up is over: cudaFree waits for the whole device and so stalls
+ * every other stream of a latency-bound pipeline, and some applications run
+ * under a fixed memory budget reserved at start-up, where a workspace that
+ * grows on demand is not acceptable.  Such callers create the context,
  * event and map at set-up and then call this function, which keeps its
  * scratch (grid tables, per-block top-K lists, fit records) in one static
  * device array of 4 MiB that every GPU loading the library holds until the
  * process exits, instead of the context's growable workspace.  Inputs,
  * output and results are exactly those of morse_grid_chi2 (same kernels,
- * same arithmetic); out is caller-allocated host memory of top_k records.
+ * same arithmetic, same parameter set-up); out is caller-allocated host
+ * memory of top_k records.  Like morse_grid_chi2 the call is synchronous:
+ * it returns once the records are on the host.
  *
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call in the process shares the array:
- * calls that overlap on the same GPU (other streams, other host threads)
- * race on it; each call rewrites every byte it reads, so nothing carries
- * over.  Returns MORSE_EINVAL, with a message naming the sizes, when the
- * search needs more than 4 MiB of scratch (top_k above about 850 on a
- * 152-SM GPU) or more than 4096 grid-table values (n_u0 + 2 n_alpha +
- * 2 n_t0 + 2 n_tE).  Errors otherwise as morse_grid_chi2. */
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the
+ * life of the process, so the library must not be used across a
+ * cudaDeviceReset of that device; make that first call before any stream
+ * capture.  Every call in the process shares the array: calls that overlap
+ * on the same GPU (other streams, other host threads) race on it; each
+ * call rewrites every byte it reads, so nothing carries over.  Returns
+ * MORSE_EINVAL, with a message naming the sizes, when the search needs
+ * more than 4 MiB of scratch (top_k above about 850 on a 152-SM GPU) or
+ * more than 4096 grid-table values (n_u0 + 2 n_alpha + 2 n_t0 + 2 n_tE).
+ * Errors otherwise as morse_grid_chi2. */
 morse_status morse_grid_chi2_noalloc(morse_ctx *ctx, const morse_event *ev,
                                      const morse_map *map,
                                      const morse_grid *grid, morse_fit *out);
@@ -569,6 +589,27 @@ morse_status morse_last_search_stats(const morse_ctx *ctx,
 
 /* Number of CUDA kernels this context has launched since morse_create. */
 morse_status morse_launch_count(const morse_ctx *ctx, uint64_t *n);
+
+/* Fault injection for tests of the error paths (not part of the paper's
+ * method).  Each fault makes a bounded failure happen on purpose, on the
+ * host or as a device wait that gives up; none faults or hangs the GPU, and
+ * the context stays usable afterwards.
+ *  MORSE_FAULT_NONE: clear every injected fault (arg ignored).
+ *  MORSE_FAULT_LOCK_HELD: until cleared, the top-K searches of this context
+ *    (morse_grid_chi2 and the calls built on it, the batched and the
+ *    allocation-free search) start with every block's top-K lock taken, and
+ *    a wait for it gives up after arg spins of ~64 ns (1 <= arg <= 2^20;
+ *    the default limit is 2^20): the call returns MORSE_ETIMEOUT.
+ *  MORSE_FAULT_ALLOC: the arg-th device allocation from now (arg >= 1)
+ *    fails as cudaMalloc would when out of memory, without allocating; the
+ *    call that makes it returns MORSE_ENOMEM.  One shot.
+ * Errors: EINVAL (unknown fault, arg out of range). */
+enum {
+  MORSE_FAULT_NONE = 0,
+  MORSE_FAULT_LOCK_HELD = 1,
+  MORSE_FAULT_ALLOC = 2
+};
+morse_status morse_inject_fault(morse_ctx *ctx, int fault, int64_t arg);
 
 #ifdef __cplusplus
 }

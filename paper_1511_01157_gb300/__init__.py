@@ -38,6 +38,8 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDEGENERATE, EUNSUPPORTED = range(7)
+# morse_inject_fault kinds (tests of the error paths)
+FAULT_NONE, FAULT_LOCK_HELD, FAULT_ALLOC = range(3)
 DEFLECT_FP64, DEFLECT_FP32 = 0, 1
 STORE_FP32, STORE_FP16LOG = 1, 2
 GEN_RAYS, GEN_POLY = 0, 1
@@ -187,6 +189,8 @@ _SIGS = {
     "morse_last_kernel_ms": (_S, [_P, _I, _P]),
     "morse_launch_count": (_S, [_P, _P]),
     "morse_last_search_stats": (_S, [_P, _P]),
+    "morse_inject_fault": (_S, [_P, _I, _I64]),
+    "morse_grid_chi2_range": (_S, [_P, _P, _P, _P, _I64, _I64, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -304,6 +308,16 @@ class Context:
         st = _lib.morse_grid_chi2(self._h, event._h, map_._h,
                                   ctypes.byref(grid), _ptr(out))
         self._check(st, "morse_grid_chi2")
+        return out
+
+    def grid_chi2_range(self, event, map_, grid: Grid, first, count):
+        """Top-K of trajectories [first, first + count) of the grid
+        (morse_grid_chi2_range): one shard of a split search."""
+        out = np.zeros(grid.top_k, dtype=FIT_DTYPE)
+        st = _lib.morse_grid_chi2_range(self._h, event._h, map_._h,
+                                        ctypes.byref(grid), int(first),
+                                        int(count), _ptr(out))
+        self._check(st, "morse_grid_chi2_range")
         return out
 
     def grid_chi2_batch(self, events, maps, grid: Grid) -> np.ndarray:
@@ -541,6 +555,14 @@ class Context:
         self._check(_lib.morse_last_search_stats(self._h, ctypes.byref(v)),
                     "morse_last_search_stats")
         return int(v.value)
+
+    def inject_fault(self, kind: int, arg: int = 0):
+        """Make a bounded failure happen on purpose (morse_inject_fault):
+        FAULT_LOCK_HELD (arg: spin limit) makes top-K searches give up their
+        lock waits (ETIMEOUT); FAULT_ALLOC (arg: n) fails the n-th device
+        allocation from now (ENOMEM); FAULT_NONE clears."""
+        self._check(_lib.morse_inject_fault(self._h, int(kind), int(arg)),
+                    "morse_inject_fault")
 
     def launch_count(self) -> int:
         v = ctypes.c_uint64()

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
       if (stage) s_ev = e;
       s_cur = 0;
       s_nk = 0;
-      s_lock = 0;
+      s_lock = B.S.lock0;
       s_thr = CUDART_INF;
       s_next = 0;
     }

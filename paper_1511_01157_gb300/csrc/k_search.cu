@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
   if (threadIdx.x == 0) {
     s_cur = 0;
     s_nk = 0;
-    s_lock = 0;
+    s_lock = P.lock0;
     s_next = 0;
     s_thr = CUDART_INF;
     s_tw[0] = 0u;

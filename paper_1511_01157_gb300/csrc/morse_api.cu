@@ -20,6 +20,9 @@ using morse::Entry;
 
 namespace {
 
+// spins (of ~64 ns) before a block top-K lock wait gives up: ~67 ms
+constexpr unsigned kDefaultSpinLimit = 1u << 20;
+
 morse_status fail(morse_ctx *ctx, morse_status st, const char *fmt, ...) {
   if (ctx) {
     va_list ap;
@@ -56,7 +59,7 @@ morse_status ws_reserve(morse_ctx *ctx, size_t bytes, void **out) {
       ctx->ws_bytes = 0;
     }
     size_t want = bytes + bytes / 4 + 4096;
-    if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+    if (morse::dev_alloc(ctx, &ctx->ws, want) != cudaSuccess) {
       cudaGetLastError();
       return fail(ctx, MORSE_ENOMEM, "workspace of %zu bytes", want);
     }
@@ -211,12 +214,17 @@ morse_map *map_alloc(morse_ctx *ctx, int npix, bool counts) {
   m->npix = npix;
   size_t n = (size_t)npix * npix;
   m->qpitch = morse::quad_pitch(npix);
-  bool ok = cudaMalloc(&m->A, n * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&m->quad, morse::quad_count(npix) * sizeof(float4)) ==
-                cudaSuccess &&
-            cudaMalloc(&m->tot, 2 * sizeof(unsigned long long)) == cudaSuccess;
+  bool ok =
+      morse::dev_alloc(ctx, (void **)&m->A, n * sizeof(float)) ==
+          cudaSuccess &&
+      morse::dev_alloc(ctx, (void **)&m->quad,
+                       morse::quad_count(npix) * sizeof(float4)) ==
+          cudaSuccess &&
+      morse::dev_alloc(ctx, (void **)&m->tot,
+                       2 * sizeof(unsigned long long)) == cudaSuccess;
   if (ok && counts)
-    ok = cudaMalloc(&m->counts, n * sizeof(uint32_t)) == cudaSuccess;
+    ok = morse::dev_alloc(ctx, (void **)&m->counts,
+                          n * sizeof(uint32_t)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     if (m->A) cudaFree(m->A);
@@ -234,8 +242,10 @@ morse_map *map_alloc(morse_ctx *ctx, int npix, bool counts) {
 bool map_ensure_half(morse_map *m) {
   if (m->quadh) return true;
   size_t n = (size_t)m->npix * m->npix;
-  if (cudaMalloc(&m->hcodes, n * sizeof(uint16_t)) != cudaSuccess ||
-      cudaMalloc(&m->quadh, morse::quad_count(m->npix) * sizeof(uint2)) !=
+  if (morse::dev_alloc(m->ctx, (void **)&m->hcodes, n * sizeof(uint16_t)) !=
+          cudaSuccess ||
+      morse::dev_alloc(m->ctx, (void **)&m->quadh,
+                       morse::quad_count(m->npix) * sizeof(uint2)) !=
           cudaSuccess) {
     cudaGetLastError();
     if (m->hcodes) cudaFree(m->hcodes);
@@ -368,38 +378,59 @@ void axis(double lo, double hi, int n, int logsp, std::vector<double> &out) {
   }
 }
 
-// Device grid tables: u0, cos/sin alpha, t0 - t_ref, 1/(tE Delta), plus the
-// absolute t0 and tE for the output records.
-struct Tables {
-  double2 *slab;
-  double *u0v, *ca, *sa, *t0rel, *invtEd, *t0abs, *tEv;
-};
-
-size_t tables_bytes(const morse_grid *g) {
-  return sizeof(double2) * (size_t)g->n_u0 * g->n_alpha +
-         sizeof(double) *
-             (size_t)(g->n_u0 + 2 * g->n_alpha + 2 * g->n_t0 + 2 * g->n_tE);
-}
+using morse::Tables;
+using morse::tables_bytes;
 
 // Grid tables at dev (16-byte aligned): the lines' tau intervals inside
 // the map of half-width L (computed on the device), then u0, cos and sin
 // alpha, t0 - t_ref, 1/(tE Delta), t0, tE.
 morse_status upload_tables(morse_ctx *ctx, const morse_grid *g, double t_ref,
                            double L, double dlt, void *dev, Tables *T) {
-  std::vector<double> u0, t0, tE, h;
+  std::vector<double> h(morse::table_values(g));
+  morse::table_host(g, t_ref, dlt, h.data());
+  morse::tables_at(g, dev, T);
+  // ordered on the context stream, then waited for: the host vector is
+  // pageable and dies on return
+  MORSE_CUDA(ctx, cudaMemcpyAsync(T->u0v, h.data(), h.size() * sizeof(double),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  MORSE_CUDA(ctx, morse::launch_slab(T->u0v, T->ca, T->sa, g->n_u0,
+                                     g->n_alpha, L, T->slab, ctx->stream));
+  ctx->launches += 1;
+  MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return MORSE_OK;
+}
+
+}  // namespace
+
+namespace morse {
+
+size_t table_values(const morse_grid *g) {
+  return (size_t)(g->n_u0 + 2 * g->n_alpha + 2 * g->n_t0 + 2 * g->n_tE);
+}
+
+size_t tables_bytes(const morse_grid *g) {
+  return sizeof(double2) * (size_t)g->n_u0 * g->n_alpha +
+         sizeof(double) * table_values(g);
+}
+
+void table_host(const morse_grid *g, double t_ref, double dlt, double *h) {
+  std::vector<double> u0, t0, tE;
   axis(g->u0_lo, g->u0_hi, g->n_u0, g->u0_log, u0);
   axis(g->t0_lo, g->t0_hi, g->n_t0, 0, t0);
   axis(g->tE_lo, g->tE_hi, g->n_tE, g->tE_log, tE);
-  h.reserve(tables_bytes(g) / sizeof(double));
-  h.insert(h.end(), u0.begin(), u0.end());
-  for (int k = 0; k < g->n_alpha; ++k)
-    h.push_back(cos(2.0 * M_PI * (double)k / (double)g->n_alpha));
-  for (int k = 0; k < g->n_alpha; ++k)
-    h.push_back(sin(2.0 * M_PI * (double)k / (double)g->n_alpha));
-  for (double v : t0) h.push_back(v - t_ref);
-  for (double v : tE) h.push_back(1.0 / (v * dlt));
-  h.insert(h.end(), t0.begin(), t0.end());
-  h.insert(h.end(), tE.begin(), tE.end());
+  size_t k = 0;
+  for (double v : u0) h[k++] = v;
+  for (int i = 0; i < g->n_alpha; ++i)
+    h[k++] = cos(2.0 * M_PI * (double)i / (double)g->n_alpha);
+  for (int i = 0; i < g->n_alpha; ++i)
+    h[k++] = sin(2.0 * M_PI * (double)i / (double)g->n_alpha);
+  for (double v : t0) h[k++] = v - t_ref;
+  for (double v : tE) h[k++] = 1.0 / (v * dlt);
+  for (double v : t0) h[k++] = v;
+  for (double v : tE) h[k++] = v;
+}
+
+void tables_at(const morse_grid *g, void *dev, Tables *T) {
   T->slab = (double2 *)dev;
   double *d = (double *)(T->slab + (size_t)g->n_u0 * g->n_alpha);
   T->u0v = d;
@@ -409,18 +440,16 @@ morse_status upload_tables(morse_ctx *ctx, const morse_grid *g, double t_ref,
   T->invtEd = T->t0rel + g->n_t0;
   T->t0abs = T->invtEd + g->n_tE;
   T->tEv = T->t0abs + g->n_t0;
-  // ordered on the context stream, then waited for: the host vector is
-  // pageable and dies on return
-  MORSE_CUDA(ctx, cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double),
-                                  cudaMemcpyHostToDevice, ctx->stream));
-  MORSE_CUDA(ctx, morse::launch_slab(T->u0v, T->ca, T->sa, g->n_u0,
-                                     g->n_alpha, L, T->slab, ctx->stream));
-  ctx->launches += 1;
-  MORSE_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  return MORSE_OK;
 }
 
-void map_params(const morse_map *map, morse::SearchParams *P) {
+cudaError_t dev_alloc(morse_ctx *ctx, void **p, size_t bytes) {
+  *p = nullptr;
+  if (ctx && ctx->fault_alloc > 0 && --ctx->fault_alloc == 0)
+    return cudaErrorMemoryAllocation;  // injected: nothing allocated
+  return cudaMalloc(p, bytes);
+}
+
+void map_params(const morse_map *map, SearchParams *P) {
   const double dlt = (2.0 * map->L) / (double)map->npix;
   P->quad = map->quad;
   P->quadh = morse::map_h16(map) ? map->quadh : nullptr;
@@ -437,9 +466,15 @@ void map_params(const morse_map *map, morse::SearchParams *P) {
   P->dltf = (float)dlt;
   P->invDf = (float)(1.0 / dlt);
   P->invD = 1.0 / dlt;
+  ctx_params(map->ctx, P);
 }
 
-void event_params(const morse_event *ev, morse::SearchParams *P) {
+void ctx_params(const morse_ctx *ctx, SearchParams *P) {
+  P->spin_limit = ctx ? ctx->spin_limit : 0u;
+  P->lock0 = ctx ? ctx->fault_lock_held : 0;
+}
+
+void event_params(const morse_event *ev, SearchParams *P) {
   P->ep = ev->ep;
   P->n_ep = (int)ev->n;
   P->S1 = ev->S1;
@@ -452,8 +487,7 @@ void event_params(const morse_event *ev, morse::SearchParams *P) {
   P->gamma = (m + 10.0) * ldexp(1.0, -24);
 }
 
-void grid_params(const morse_grid *g, const Tables &T,
-                 morse::SearchParams *P) {
+void grid_params(const morse_grid *g, const Tables &T, SearchParams *P) {
   P->u0v = T.u0v;
   P->ca = T.ca;
   P->sa = T.sa;
@@ -467,6 +501,16 @@ void grid_params(const morse_grid *g, const Tables &T,
   P->n_tE = g->n_tE;
   P->top_k = g->top_k;
 }
+
+}  // namespace morse
+
+namespace {
+
+using morse::ctx_params;
+using morse::dev_alloc;
+using morse::event_params;
+using morse::grid_params;
+using morse::map_params;
 
 morse_status check_pair(morse_ctx *ctx, const morse_event *ev,
                         const morse_map *map) {
@@ -1316,6 +1360,9 @@ morse_status morse_create(morse_ctx **out, int device, void *cuda_stream) {
   }
   c->sm_count = prop.multiProcessorCount;
   c->tune_mode = MORSE_TUNE_ON;
+  c->spin_limit = kDefaultSpinLimit;
+  c->fault_lock_held = 0;
+  c->fault_alloc = 0;
   c->batch_exec = nullptr;
   c->smem_optin = prop.sharedMemPerBlockOptin;
   if (cuda_stream) {
@@ -1368,6 +1415,32 @@ morse_status morse_launch_count(const morse_ctx *ctx, uint64_t *n) {
   if (!ctx || !n) return MORSE_EINVAL;
   *n = ctx->launches;
   return MORSE_OK;
+}
+
+morse_status morse_inject_fault(morse_ctx *ctx, int fault, int64_t arg) {
+  if (!ctx) return MORSE_EINVAL;
+  switch (fault) {
+    case MORSE_FAULT_NONE:
+      ctx->spin_limit = kDefaultSpinLimit;
+      ctx->fault_lock_held = 0;
+      ctx->fault_alloc = 0;
+      return MORSE_OK;
+    case MORSE_FAULT_LOCK_HELD:
+      if (arg < 1 || arg > (int64_t)kDefaultSpinLimit)
+        return fail(ctx, MORSE_EINVAL, "spin limit %lld outside 1..%u",
+                    (long long)arg, kDefaultSpinLimit);
+      ctx->spin_limit = (unsigned)arg;
+      ctx->fault_lock_held = 1;
+      return MORSE_OK;
+    case MORSE_FAULT_ALLOC:
+      if (arg < 1)
+        return fail(ctx, MORSE_EINVAL, "allocation index %lld < 1",
+                    (long long)arg);
+      ctx->fault_alloc = arg;
+      return MORSE_OK;
+    default:
+      return fail(ctx, MORSE_EINVAL, "unknown fault %d", fault);
+  }
 }
 
 // ------------------------------------------------------------------ maps
@@ -1645,6 +1718,18 @@ morse_status morse_event_create(morse_ctx *ctx, const double *t,
       return fail(ctx, MORSE_EINVAL, "epoch %lld has sigma <= 0",
                   (long long)i);
   }
+  // Times are stored as FP32 offsets from t_ref: at |t - t_ref| = 1e5 d
+  // they resolve 0.004 d, beyond that the offsets no longer locate a data
+  // point on a trajectory (JD-scale times with t_ref = 0 would resolve
+  // 0.25 d), so such a t_ref is rejected.
+  double t_span = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    t_span = std::max(t_span, std::fabs(t[i] - t_ref));
+  if (t_span > 1e5)
+    return fail(ctx, MORSE_EINVAL,
+                "times lie up to %.6g d from t_ref: their FP32 offsets would "
+                "resolve only %.3g d; pass a t_ref within the data",
+                t_span, t_span * 5.9604644775390625e-8);
   // the search needs the epochs in time order (a straight track crosses the
   // map in one time interval): store them sorted, ties in input order
   std::vector<int64_t> order((size_t)n);
@@ -1692,7 +1777,8 @@ morse_status morse_event_create(morse_ctx *ctx, const double *t,
   MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
   morse_event *ev = (morse_event *)calloc(1, sizeof(morse_event));
   if (!ev) return fail(ctx, MORSE_ENOMEM, "event");
-  if (cudaMalloc(&ev->ep, sizeof(float4) * (size_t)n) != cudaSuccess) {
+  if (morse::dev_alloc(ctx, (void **)&ev->ep, sizeof(float4) * (size_t)n) !=
+      cudaSuccess) {
     cudaGetLastError();
     free(ev);
     return fail(ctx, MORSE_ENOMEM, "event of %lld epochs", (long long)n);
@@ -1715,9 +1801,7 @@ morse_status morse_event_create(morse_ctx *ctx, const double *t,
   ev->Fref = Fref;
   ev->invS1 = 1.0 / S1;
   ev->CFF = SFF - SF * SF / S1;
-  ev->t_span = 0.0;
-  for (int64_t i = 0; i < n; ++i)
-    ev->t_span = std::max(ev->t_span, std::fabs(t[i] - t_ref));
+  ev->t_span = t_span;
   *out = ev;
   return MORSE_OK;
 }
@@ -1738,16 +1822,15 @@ morse_status morse_event_info(const morse_event *ev, int64_t *n,
 }
 
 // ------------------------------------------------------------------ search
-morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
-                             const morse_map *map, const morse_grid *grid,
-                             morse_fit *out) {
-  if (!ctx || !out) return MORSE_EINVAL;
-  MORSE_TRY(check_pair(ctx, ev, map));
-  MORSE_TRY(check_grid(ctx, grid));
+// The top-K of trajectories [first, first + count) of the grid.
+static morse_status grid_chi2_impl(morse_ctx *ctx, const morse_event *ev,
+                                   const morse_map *map,
+                                   const morse_grid *grid, long long first,
+                                   long long count, morse_fit *out) {
   MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
   call_begin(ctx);
   Plan pl;
-  MORSE_TRY(plan_search(ctx, ev, grid, 0, grid_size(grid), false,
+  MORSE_TRY(plan_search(ctx, ev, grid, first, count, false,
                         morse::map_h16(map), 1, &pl,
                         band_spec(map->npix, map->L, grid_umax(grid), 0.0)));
   void *ws = nullptr;
@@ -1762,8 +1845,8 @@ morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
   map_params(map, &P);
   event_params(ev, &P);
   grid_params(grid, T, &P);
-  P.first = 0;
-  P.count = grid_size(grid);
+  P.first = first;
+  P.count = count;
   P.stride = 1;
   morse::set_groups(&P);
   morse_fit *fits = (morse_fit *)(base + pl.off_out);
@@ -1777,6 +1860,31 @@ morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
                                   cudaMemcpyDeviceToHost, ctx->stream));
   MORSE_TRY(sync_and_collect(ctx, "grid search"));
   return hdr_check(ctx, h);
+}
+
+morse_status morse_grid_chi2(morse_ctx *ctx, const morse_event *ev,
+                             const morse_map *map, const morse_grid *grid,
+                             morse_fit *out) {
+  if (!ctx || !out) return MORSE_EINVAL;
+  MORSE_TRY(check_pair(ctx, ev, map));
+  MORSE_TRY(check_grid(ctx, grid));
+  return grid_chi2_impl(ctx, ev, map, grid, 0, grid_size(grid), out);
+}
+
+morse_status morse_grid_chi2_range(morse_ctx *ctx, const morse_event *ev,
+                                   const morse_map *map,
+                                   const morse_grid *grid, int64_t first,
+                                   int64_t count, morse_fit *out) {
+  if (!ctx || !out) return MORSE_EINVAL;
+  MORSE_TRY(check_pair(ctx, ev, map));
+  MORSE_TRY(check_grid(ctx, grid));
+  const long long n = grid_size(grid);
+  if (first < 0 || count < 1 || first > n || count > n - first)
+    return fail(ctx, MORSE_EINVAL,
+                "trajectory range [%lld, %lld + %lld) outside the grid of "
+                "%lld", (long long)first, (long long)first, (long long)count,
+                n);
+  return grid_chi2_impl(ctx, ev, map, grid, first, count, out);
 }
 
 morse_status morse_grid_chi2_dense(morse_ctx *ctx, const morse_event *ev,

@@ -37,6 +37,11 @@ struct morse_ctx {
   std::map<std::string, morse_batch_shape> tune;
   int tune_mode;            // MORSE_TUNE_*
   cudaGraphExec_t batch_exec;
+  // injected faults (morse_inject_fault; tests of the error paths)
+  unsigned spin_limit;      // spins before a block top-K lock wait gives up
+  int fault_lock_held;      // searches start with every block lock taken
+  long long fault_alloc;    // > 0: the fault_alloc-th device allocation
+                            // from now fails (then the count is spent)
 };
 
 struct morse_map {
@@ -243,12 +248,39 @@ struct SearchParams {
                             // band-table cell differs from the map's
                             // (checked build only)
   unsigned long long *stat_exact;  // trajectories given the exact sweep
+  unsigned spin_limit;      // block top-K lock: spins before giving up
+  int lock0;                // initial lock word (1: held, an injected fault)
   // Shared-memory band tables of the line-aligned pass (k_search only;
   // 0 = off): entries per table, 4 band_stride(npix), two tables after the
   // lists.
   int tab_n;
   unsigned tab_c;           // half + 1 - 0x4B400000: floor bits -> cell
 };
+
+// ------------------------------------------- host set-up of a search
+// Grid tables in device memory: the lines' tau intervals inside the map,
+// then u0, cos and sin alpha, t0 - t_ref, 1/(tE Delta), and the absolute t0
+// and tE of the output records.
+struct Tables {
+  double2 *slab;
+  double *u0v, *ca, *sa, *t0rel, *invtEd, *t0abs, *tEv;
+};
+// bytes of the tables of grid g (slabs first, 16-byte aligned)
+size_t tables_bytes(const morse_grid *g);
+// number of FP64 table values after the slabs
+size_t table_values(const morse_grid *g);
+// the table values of g in device order, written to h[table_values(g)]
+void table_host(const morse_grid *g, double t_ref, double dlt, double *h);
+// the table pointers of g laid out at dev
+void tables_at(const morse_grid *g, void *dev, Tables *T);
+// search parameters from the handles (every search path sets them alike)
+void map_params(const morse_map *map, SearchParams *P);
+void event_params(const morse_event *ev, SearchParams *P);
+void grid_params(const morse_grid *g, const Tables &T, SearchParams *P);
+void ctx_params(const morse_ctx *ctx, SearchParams *P);
+// device allocation through the context: cudaMalloc, or the injected
+// failure of morse_inject_fault (cudaErrorMemoryAllocation, nothing made)
+cudaError_t dev_alloc(morse_ctx *ctx, void **p, size_t bytes);
 
 struct FillParams {
   SearchParams S;

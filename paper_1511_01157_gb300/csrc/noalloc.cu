@@ -1,12 +1,11 @@
 // morse_grid_chi2_noalloc: the top-K trajectory search without any device
 // allocation.
 //
-// Some callers cannot let the library call cudaMalloc or cudaFree inside
-// their hot loop: cudaFree waits for the whole device, which stalls every
-// stream of a latency-bound pipeline; allocation is unavailable while a
-// stream is being captured; and some applications run under a fixed,
-// pre-reserved memory budget where a workspace that grows on demand is not
-// acceptable.  They create their context, event and map handles at set-up
+// Some callers cannot let the library call cudaMalloc or cudaFree once
+// set-up is over: cudaFree waits for the whole device, which stalls every
+// stream of a latency-bound pipeline, and some applications run under a
+// fixed, pre-reserved memory budget where a workspace that grows on demand
+// is not acceptable.  They create their context, event and map handles at set-up
 // (where allocation is fine) and then search with this entry point, which
 // keeps its scratch -- the grid tables, two status words, the two
 // per-block top-K lists of the merge tree and the fit records -- in one
@@ -41,8 +40,9 @@ std::mutex g_setup_mutex;
 void *g_scratch_ptr[kMaxDevices];
 
 // Device address of g_noalloc_scratch on `device` (which must be current).
-// Looked up once per device; the host-side symbol is only a stand-in and
-// must never be passed to a kernel.
+// Looked up once per device and kept for the life of the process (a
+// cudaDeviceReset would invalidate it); the host-side symbol is only a
+// stand-in and must never be passed to a kernel.
 cudaError_t scratch_address(int device, void **out) {
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
@@ -117,14 +117,10 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   int grid = (int)std::min<long long>((long long)bps * ctx->sm_count, want);
   if (grid < 1) grid = 1;
 
-  // scratch layout: tables | line slabs | status words | list A | list B |
-  // fits
-  const size_t tab_n =
-      (size_t)g->n_u0 + 2 * (size_t)g->n_alpha + 2 * (size_t)g->n_t0 +
-      2 * (size_t)g->n_tE;
-  const size_t off_slab = up256(tab_n * sizeof(double));
-  const size_t off_w =
-      up256(off_slab + sizeof(double2) * (size_t)g->n_u0 * g->n_alpha);
+  // scratch layout: grid tables (line slabs, then the FP64 values) |
+  // status words | list A | list B | fits
+  const size_t tab_n = morse::table_values(g);
+  const size_t off_w = up256(morse::tables_bytes(g));
   const size_t off_a = off_w + 256;
   const size_t list = sizeof(morse::Entry) * (size_t)grid * K;
   const size_t off_b = up256(off_a + list);
@@ -141,7 +137,8 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
   }
   char *base = (char *)scratch;
 
-  // grid tables (same values as the allocating path), staged on the stack
+  // grid tables (the allocating path's values, from the same helper),
+  // staged on the stack
   constexpr size_t kMaxTable = 4096;
   if (tab_n > kMaxTable) {
     snprintf(ctx->err, sizeof(ctx->err),
@@ -152,85 +149,33 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
     return MORSE_EINVAL;
   }
   double h[kMaxTable];
-  size_t nh = 0;
-  auto axis = [&](double lo, double hi, int n, int logsp, double shift) {
-    for (int i = 0; i < n; ++i) {
-      double f = (n > 1) ? (double)i / (double)(n - 1) : 0.0;
-      h[nh++] = (logsp ? exp(log(lo) + (log(hi) - log(lo)) * f)
-                       : lo + (hi - lo) * f) - shift;
-    }
-  };
   const double dlt = (2.0 * map->L) / (double)map->npix;
-  axis(g->u0_lo, g->u0_hi, g->n_u0, g->u0_log, 0.0);
-  for (int k = 0; k < g->n_alpha; ++k)
-    h[nh++] = cos(2.0 * M_PI * (double)k / (double)g->n_alpha);
-  for (int k = 0; k < g->n_alpha; ++k)
-    h[nh++] = sin(2.0 * M_PI * (double)k / (double)g->n_alpha);
-  axis(g->t0_lo, g->t0_hi, g->n_t0, 0, ev->t_ref);            // t0 - t_ref
-  const size_t at_tE = nh;
-  axis(g->tE_lo, g->tE_hi, g->n_tE, g->tE_log, 0.0);          // tE ...
-  for (int i = 0; i < g->n_tE; ++i) h[at_tE + i] = 1.0 / (h[at_tE + i] * dlt);
-  axis(g->t0_lo, g->t0_hi, g->n_t0, 0, 0.0);                  // t0
-  axis(g->tE_lo, g->tE_hi, g->n_tE, g->tE_log, 0.0);          // tE
-  e = cudaMemcpyAsync(base, h, nh * sizeof(double), cudaMemcpyHostToDevice,
-                      ctx->stream);
+  morse::table_host(g, ev->t_ref, dlt, h);
+  morse::Tables T;
+  morse::tables_at(g, base, &T);
+  e = cudaMemcpyAsync(T.u0v, h, tab_n * sizeof(double),
+                      cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     snprintf(ctx->err, sizeof(ctx->err), "table upload: %s",
              cudaGetErrorString(e));
     return MORSE_ECUDA;
   }
-  double *d = (double *)base;
-  const double *u0v = d, *ca = u0v + g->n_u0, *sa = ca + g->n_alpha;
-  const double *t0rel = sa + g->n_alpha, *invtEd = t0rel + g->n_t0;
-  const double *t0abs = invtEd + g->n_tE, *tEabs = t0abs + g->n_t0;
-  double2 *slab = (double2 *)(base + off_slab);
-  e = morse::launch_slab(u0v, ca, sa, g->n_u0, g->n_alpha, map->L, slab,
-                         ctx->stream);
+  e = morse::launch_slab(T.u0v, T.ca, T.sa, g->n_u0, g->n_alpha, map->L,
+                         T.slab, ctx->stream);
   if (e != cudaSuccess) {
     snprintf(ctx->err, sizeof(ctx->err), "line slabs: %s",
              cudaGetErrorString(e));
     return MORSE_ECUDA;
   }
 
+  // search parameters from the same setters as morse_grid_chi2
   morse::SearchParams P;
   memset(&P, 0, sizeof(P));
-  P.quad = map->quad;
+  morse::map_params(map, &P);
   P.quadh = h16 ? map->quadh : nullptr;
-  P.qpitch = map->qpitch;
-  P.qidx0 = morse::quad_idx0(map->npix);
-  P.npix = map->npix;
-  P.half = map->npix / 2;
-  P.vlo = -(float)(map->npix / 2) - 0.5f;
-  P.vhi = (float)(map->npix - map->npix / 2) - 0.5f;
-  P.L = map->L;
-  P.dlt = dlt;
-  P.coff = 0.5 * map->npix - (double)(map->npix / 2) - 0.5;
-  P.voff = (float)(-P.coff);
-  P.dltf = (float)dlt;
-  P.invDf = (float)(1.0 / dlt);
-  P.invD = 1.0 / dlt;
-  P.ep = ev->ep;
-  P.n_ep = (int)ev->n;
-  P.S1 = ev->S1;
-  P.SF = ev->SF;
-  P.SFF = ev->SFF;
-  P.invS1 = ev->invS1;
-  P.CFF = ev->CFF;
-  P.Fref = ev->Fref;
-  P.gamma = ((double)((ev->n + 31) / 32) + 10.0) * ldexp(1.0, -24);
-  P.u0v = u0v;
-  P.ca = ca;
-  P.sa = sa;
-  P.t0rel = t0rel;
-  P.invtEd = invtEd;
-  P.tEv = tEabs;
-  P.slab = slab;
-  P.n_u0 = g->n_u0;
-  P.n_alpha = g->n_alpha;
-  P.n_t0 = g->n_t0;
-  P.n_tE = g->n_tE;
-  P.top_k = K;
+  morse::event_params(ev, &P);
+  morse::grid_params(g, T, &P);
   P.first = 0;
   P.count = count;
   P.stride = 1;
@@ -260,8 +205,8 @@ extern "C" morse_status morse_grid_chi2_noalloc(morse_ctx *ctx,
     F.S = P;
     F.sel = sel;
     F.k = K;
-    F.t0abs = t0abs;
-    F.tEv = tEabs;
+    F.t0abs = T.t0abs;
+    F.tEv = T.tEv;
     F.out = fits;
     e = morse::launch_fill(F, ctx->stream);
   }

@@ -34,7 +34,6 @@ constexpr int kUnroll = MORSE_UNROLL;     // inside-map epoch loop
 constexpr int kUnrollH = MORSE_UNROLL_H;  // the same, FP16 tables
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr unsigned kLockSpinLimit = 1u << 20;
 
 // Per-trajectory constants.
 struct TrajC {

@@ -52,12 +52,13 @@ __device__ inline void warp_merge(const SearchParams &P, BlockTopK &T, const int
     wb[lane].chi2 = key;
     wb[lane].idx = id;
   }
-  // acquire the block lock (bounded spin)
+  // acquire the block lock (bounded spin: P.spin_limit waits of ~64 ns)
   int ok = 1;
   if (lane == 0) {
+    const unsigned lim = P.spin_limit ? P.spin_limit : (1u << 20);
     unsigned it = 0;
     while (atomicCAS(T.lock, 0, 1) != 0) {
-      if (++it > kLockSpinLimit) {
+      if (++it > lim) {
         ok = 0;
         if (P.err) atomicOr(P.err, 1u);
         break;

@@ -1,9 +1,12 @@
 """The sharded search's host logic on two CPU ranks (gloo, world size 2).
 
-The grid is split by trajectory index across ranks; each rank keeps the
-top-K of its shard (here computed by the oracle, on the CPU), the lists are
-gathered with torch.distributed and merged by morse_topk_merge.  The merged
-list must equal the unsharded top-K, and the bench's max-over-ranks timing
+Each rank runs the library's shard code (paper_1511_01157_gb300.shard:
+the contiguous split of the trajectory index, the gather over
+torch.distributed, morse_topk_merge).  With no GPU here, the per-shard
+search it calls is a CPU stand-in that returns the top-K of the shard's
+range (the oracle's chi^2, written as records); on a GPU the same code calls
+morse_grid_chi2_range.  The oracle's unsharded top-K is the check: every
+rank's merged list must equal it, and the bench's max-over-ranks timing
 helper must return the slowest rank's time on every rank.
 """
 import os
@@ -46,23 +49,19 @@ def _rank(rank, world, port, k, out_q):
     w_, r_, _ = bench.dist_setup()
     assert (w_, r_) == (world, rank)
     orc, A, g, t, F, w = _problem()
-    n = g.size
-    first = rank * n // world
-    count = (rank + 1) * n // world - first
-    chi2, fs, fb, fl = orc.grid_chi2(g, t, F, w, A=A, L=2.0, first=first,
-                                     count=count)
-    idx, val = orc.topk(chi2, k, first=first)
-    mine = np.zeros(k, dtype=m.FIT_DTYPE)
-    mine["chi2"] = np.inf
-    mine["idx"] = -1
-    mine["chi2"][:len(idx)] = val
-    mine["idx"][:len(idx)] = idx
-    # gather the shard lists (fixed-size byte buffers)
-    buf = torch.from_numpy(mine.view(np.uint8).copy())
-    parts = [torch.zeros_like(buf) for _ in range(world)]
-    dist.all_gather(parts, buf)
-    lists = [p.numpy().view(m.FIT_DTYPE) for p in parts]
-    merged = m.topk_merge(lists, k)
+    from paper_1511_01157_gb300 import shard
+
+    def search_range(first, count):  # CPU stand-in for the GPU shard
+        chi2, fs, fb, fl = orc.grid_chi2(g, t, F, w, A=A, L=2.0,
+                                         first=first, count=count)
+        idx, val = orc.topk(chi2, k, first=first)
+        mine = shard.empty_fits(k)
+        mine["chi2"][:len(idx)] = val
+        mine["idx"][:len(idx)] = idx
+        return mine
+
+    merged = shard.sharded_topk(search_range, g.size, k, rank, world,
+                                shard.torch_gather())
     # slowest rank's time everywhere
     tmax = bench.max_over_ranks(1.0 + rank, world)
     bench.barrier(world)
