@@ -57,6 +57,12 @@ GATHER_BYTES_PER_EVAL = 16
 # 128 bytes per clock per SM
 SMEM_BYTES_PER_EVAL = 22
 SMEM_BYTES_PER_CLK_SM = 128
+# adjoint, per trajectory-epoch: the chi^2 of the two sweeps (22, as the
+# search) and 14 more for the gradient through the lookup (the survey's
+# per-evaluation figure); the kernel recomputes the lookup in its second
+# sweep instead of storing A, and takes the gradient in the map's pixel
+# axes, about 37 FP32 instructions in all
+ADJ_INSTR_PER_EVAL = 36
 # ray shooting, per ray: ray coordinates 2, deflection of Eq. 2 through two
 # lenses 12 (+ 2 reciprocals), binning 6; plus one shared-memory atomic
 ALG_INSTR_PER_RAY = 22
@@ -282,7 +288,9 @@ def adjoint_section(ctx, m, cfg, ev, n_ep, stream, probes, peak_instr_s,
     where sums of large terms would cancel), so an evaluation is 22 + 36
     FP32 instructions and two 16-byte gathers.  Then `iters`
     Levenberg-Marquardt iterations of all n (morse_refine, a CUDA graph per
-    iteration) timed end to end."""
+    iteration) timed end to end.  The roofline counts 36 FP32 instructions
+    per evaluation (chi^2 22 + gradient 14); the earlier accounting of two
+    full sweeps (22 + 36) is reported beside it."""
     import torch
     mp = ctx.build_map(cfg["s"], cfg["q"], cfg["L"], cfg["npix"], cfg["nray"],
                        image_halfwidth=cfg["X"], deflect="fp32")
@@ -313,7 +321,8 @@ def adjoint_section(ctx, m, cfg, ev, n_ep, stream, probes, peak_instr_s,
     # the same trajectories 32 times over: enough warps to fill the GPU
     ms_big = grad_ms(np.tile(th, (32, 1)))
     evals_big = 32 * n * n_ep / (ms_big * 1e-3)
-    peak_instr = peak_instr_s / 58.0
+    peak_instr = peak_instr_s / ADJ_INSTR_PER_EVAL
+    peak_instr_58 = peak_instr_s / 58.0
     peak_gather = probes["l1_gather_bytes_per_s"] / 32.0
     starts = np.zeros(n, dtype=m.FIT_DTYPE)
     starts["t0"], starts["tE"], starts["u0"], starts["alpha"] = th.T
@@ -328,15 +337,60 @@ def adjoint_section(ctx, m, cfg, ev, n_ep, stream, probes, peak_instr_s,
     return {"trajectories": n, "epochs": n_ep, "grad_ms": ms,
             "grad_evals_per_s": evals,
             "frac_fp32_issue": evals / peak_instr,
+            "frac_fp32_issue_58": evals / peak_instr_58,
             "frac_l1_gather": evals / peak_gather,
             "grad_evals_per_s_131072": evals_big,
             "frac_fp32_issue_131072": evals_big / peak_instr,
-            "roofline_note": "two sweeps per evaluation: 22 + 36 FP32 instr "
-                             "and 2 x 16 B; peaks: the search's FP32 issue "
-                             "peak and the measured L1 gather",
+            "frac_fp32_issue_58_131072": evals_big / peak_instr_58,
+            "roofline_note": f"{ADJ_INSTR_PER_EVAL} FP32 instr per "
+                             "evaluation (chi^2 22 + gradient 14) against "
+                             "152 x 128 lanes x max clock; _58: two full "
+                             "sweeps counted (22 + 36); gather: 2 x 16 B "
+                             "against the measured L1 random gather",
             "refine_iters": iters, "refine_s": t_ref,
             "refine_iters_per_s": n * iters / t_ref,
             "refine_median_chi2": float(np.median(out["chi2"]))}
+
+
+def config2_section(ctx, m, cfg, ev, S, Q, fits, n_starts=4096, iters=50):
+    """Configuration 2: Levenberg-Marquardt refinement (adjoint gradient,
+    Gauss-Newton matrix, one CUDA graph per iteration) of the n_starts
+    lowest-chi^2 grid minima of the 651-map config-1 sweep (the top-256
+    lists of every map), 50 iterations.  The maps those minima lie on are
+    built and kept resident together (17 MB each), and every start refines
+    in one morse_refine_batch call on its own map.  Reported: wall time
+    with the map builds, the refine call alone, and the chi^2 reached."""
+    import torch
+    flat = fits.reshape(-1)
+    mi = np.repeat(np.arange(fits.shape[0]), fits.shape[1])
+    ok = np.flatnonzero(flat["idx"] >= 0)
+    pick = ok[np.argsort(flat["chi2"][ok], kind="stable")[:n_starts]]
+    maps = np.unique(mi[pick])
+    slot = {int(j): k for k, j in enumerate(maps)}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    built = [ctx.build_map(S[j], Q[j], cfg["L"], cfg["npix"], cfg["nray"],
+                           image_halfwidth=cfg["X"], deflect="fp32")
+             for j in maps]
+    seeds = flat[pick]
+    map_of = np.array([slot[int(j)] for j in mi[pick]], dtype=np.int32)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    out = ctx.refine_batch(ev, built, map_of, seeds, iters=iters)
+    torch.cuda.synchronize()
+    t_ref = time.perf_counter() - t1
+    wall = time.perf_counter() - t0
+    for mp in built:
+        mp.free()
+    gain = 1.0 - out["chi2"] / seeds["chi2"]
+    return {"starts": int(len(pick)), "maps": int(len(maps)),
+            "iterations": iters, "wall_s": wall, "refine_s": t_ref,
+            "trajectory_iterations_per_s": len(pick) * iters / t_ref,
+            "best_grid_chi2": float(seeds["chi2"].min()),
+            "best_refined_chi2": float(out["chi2"].min()),
+            "median_relative_chi2_drop": float(np.median(gain)),
+            "never_increased": bool(np.all(out["chi2"] <= seeds["chi2"] *
+                                           (1 + 1e-12)))}
 
 
 def batch_events(ctx, m, cfg, n_events):
@@ -785,6 +839,10 @@ def run_gpu(args, cfg):
                 float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
             out["adjoint"] = adjoint_section(ctx, m, cfg, ev, len(t), stream,
                                              probes, peak_instr)
+            fits = ctx.sweep(ev, S, Q, cfg["L"], cfg["npix"], cfg["nray"],
+                             grid, image_halfwidth=cfg["X"], deflect="fp32")
+            out["config2_refine"] = config2_section(ctx, m, cfg, ev, S, Q,
+                                                    fits)
         elif args.only == "batched":
             out["batched"] = run_batched(ctx, m, args.batch_events,
                                          args.batch_maps,
@@ -972,6 +1030,7 @@ def run_gpu(args, cfg):
         line["peak_library"] = peak_library(ctx, m, cfg)
         line["adjoint"] = adjoint_section(ctx, m, cfg, ev, len(t), stream,
                                           probes, peak_instr * 1e12)
+        line["config2_refine"] = config2_section(ctx, m, cfg, ev, S, Q, fits)
         line["batched"] = run_batched(ctx, m, args.batch_events,
                                       args.batch_maps, not args.no_batch_tune)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

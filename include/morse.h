@@ -546,6 +546,20 @@ morse_status morse_refine(morse_ctx *ctx, const morse_event *ev,
                           const morse_map *map, const morse_fit *starts,
                           int n, int iters, int method, morse_fit *out);
 
+/* morse_refine of starts on several maps in one call: start i is refined
+ * on maps[map_of[i]] (0 <= map_of[i] < n_maps), every start in the same
+ * batched launches and the same CUDA graph, so that the grid minima of a
+ * whole (s, q) sweep (config 2: the K best over all maps) refine together
+ * with every map they need resident on the device.  The maps must share
+ * npix and extent; each start's result is the one morse_refine gives on its
+ * own map, bit for bit.  Errors: EINVAL (mismatched maps, map index out of
+ * range), EUNSUPPORTED, ENOMEM, ECUDA. */
+morse_status morse_refine_batch(morse_ctx *ctx, const morse_event *ev,
+                                const morse_map *const *maps, int n_maps,
+                                const int *map_of, const morse_fit *starts,
+                                int n, int iters, int method,
+                                morse_fit *out);
+
 /* Merge n_lists top-K lists (each ascending by (chi2, idx), counts[i]
  * entries, entries with idx < 0 ignored) into the k best, ascending, in
  * out[k] (tail padded with idx = -1, chi2 = +inf).  Host-only; used to

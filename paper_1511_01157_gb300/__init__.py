@@ -191,6 +191,7 @@ _SIGS = {
     "morse_last_search_stats": (_S, [_P, _P]),
     "morse_inject_fault": (_S, [_P, _I, _I64]),
     "morse_grid_chi2_range": (_S, [_P, _P, _P, _P, _I64, _I64, _P]),
+    "morse_refine_batch": (_S, [_P, _P, _P, _I, _P, _P, _I, _I, _I, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -537,6 +538,20 @@ class Context:
         st = _lib.morse_refine(self._h, event._h, map_._h, _ptr(st_),
                                len(st_), int(iters), int(method), _ptr(out))
         self._check(st, "morse_refine")
+        return out
+
+    def refine_batch(self, event, maps, map_of, starts, iters=50,
+                     method=REFINE_LM):
+        """morse_refine of starts on several maps at once
+        (morse_refine_batch): start i on maps[map_of[i]]."""
+        st_ = np.ascontiguousarray(starts, dtype=FIT_DTYPE)
+        mo = np.ascontiguousarray(map_of, dtype=np.int32)
+        mp = (ctypes.c_void_p * len(maps))(*[m._h for m in maps])
+        out = np.zeros(len(st_), dtype=FIT_DTYPE)
+        st = _lib.morse_refine_batch(self._h, event._h, mp, len(maps),
+                                     _ptr(mo), _ptr(st_), len(st_),
+                                     int(iters), int(method), _ptr(out))
+        self._check(st, "morse_refine_batch")
         return out
 
     def lightcurve(self, map_, t0, tE, u0, alpha, t):

@@ -1359,6 +1359,11 @@ morse_status morse_create(morse_ctx **out, int device, void *cuda_stream) {
     return MORSE_ECUDA;
   }
   c->sm_count = prop.multiProcessorCount;
+  if (morse::adjoint_setup() != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return MORSE_ECUDA;
+  }
   c->tune_mode = MORSE_TUNE_ON;
   c->spin_limit = kDefaultSpinLimit;
   c->fault_lock_held = 0;
@@ -2114,11 +2119,13 @@ morse_status morse_chi2_grad(morse_ctx *ctx, const morse_event *ev,
   return sync_and_collect(ctx, "chi2 gradient");
 }
 
-morse_status morse_refine(morse_ctx *ctx, const morse_event *ev,
-                          const morse_map *map, const morse_fit *starts,
-                          int n, int iters, int method, morse_fit *out) {
-  if (!ctx) return MORSE_EINVAL;
-  MORSE_TRY(check_pair(ctx, ev, map));
+// Levenberg-Marquardt refinement of n starts, start i on map maps[0] or,
+// with map_of set, on maps[map_of[i]] (maps of one geometry).
+static morse_status refine_impl(morse_ctx *ctx, const morse_event *ev,
+                                const morse_map *const *maps, int n_maps,
+                                const int *map_of, const morse_fit *starts,
+                                int n, int iters, int method,
+                                morse_fit *out) {
   if (method != MORSE_REFINE_LM)
     return fail(ctx, MORSE_EUNSUPPORTED, "refine method %d", method);
   if (n < 0 || iters < 0 || iters > 100000)
@@ -2129,13 +2136,19 @@ morse_status morse_refine(morse_ctx *ctx, const morse_event *ev,
     const double th[4] = {starts[i].t0, starts[i].tE, starts[i].u0,
                           starts[i].alpha};
     MORSE_TRY(check_theta(ctx, th, 1));
+    if (map_of && (map_of[i] < 0 || map_of[i] >= n_maps))
+      return fail(ctx, MORSE_EINVAL, "start %d: map index %d outside 0..%d",
+                  i, map_of[i], n_maps - 1);
   }
+  const morse_map *map = maps[0];
   MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
   call_begin(ctx);
   const size_t nn = (size_t)n;
-  // workspace: 36 doubles + 1 int per trajectory, starts, records
+  // workspace: 36 doubles + 1 int per trajectory, starts, records, and the
+  // trajectories' map tables
   const size_t dbl = nn * 36, bytes = sizeof(double) * dbl + sizeof(int) * nn +
-                                      2 * sizeof(morse_fit) * nn + 4096;
+                                      2 * sizeof(morse_fit) * nn +
+                                      sizeof(void *) * nn + 4096;
   void *ws = nullptr;
   MORSE_TRY(ws_reserve(ctx, bytes, &ws));
   double *d = (double *)ws;
@@ -2155,6 +2168,15 @@ morse_status morse_refine(morse_ctx *ctx, const morse_event *ev,
   morse_fit *d_starts = (morse_fit *)align_up(
       (size_t)(S.flags + nn), alignof(morse_fit));
   morse_fit *d_out = d_starts + nn;
+  const float4 **d_tq = nullptr;
+  std::vector<const float4 *> tq;
+  if (map_of) {
+    d_tq = (const float4 **)align_up((size_t)(d_out + nn), 16);
+    tq.resize(nn);
+    for (size_t i = 0; i < nn; ++i) tq[i] = maps[map_of[i]]->quad;
+    MORSE_CUDA(ctx, cudaMemcpyAsync(d_tq, tq.data(), sizeof(void *) * nn,
+                                    cudaMemcpyHostToDevice, ctx->stream));
+  }
   MORSE_CUDA(ctx, cudaMemcpyAsync(d_starts, starts, sizeof(morse_fit) * nn,
                                   cudaMemcpyHostToDevice, ctx->stream));
   morse::SearchParams P;
@@ -2172,7 +2194,7 @@ morse_status morse_refine(morse_ctx *ctx, const morse_event *ev,
     cudaError_t e1 = morse::launch_theta(P, S.th_cur, n, ev->t_ref,
                                          S.chi2_cur, S.g_cur, S.H_cur,
                                          nullptr, nullptr, nullptr,
-                                         ctx->stream);
+                                         ctx->stream, d_tq);
     cudaError_t e2 = morse::launch_lm_step(S, n, ctx->stream);
     cudaError_t e3 = cudaStreamEndCapture(ctx->stream, &graph);
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
@@ -2200,13 +2222,41 @@ morse_status morse_refine(morse_ctx *ctx, const morse_event *ev,
   int r = t_begin(ctx, KT_ADJ);
   MORSE_CUDA(ctx, morse::launch_theta(P, S.th_best, n, ev->t_ref, S.chi2_cur,
                                       nullptr, nullptr, S.Fs, S.Fb, S.flags,
-                                      ctx->stream));
+                                      ctx->stream, d_tq));
   t_end(ctx, r);
   MORSE_CUDA(ctx, morse::launch_lm_finish(S, d_starts, n, d_out, ctx->stream));
   ctx->launches += 2;
   MORSE_CUDA(ctx, cudaMemcpyAsync(out, d_out, sizeof(morse_fit) * nn,
                                   cudaMemcpyDeviceToHost, ctx->stream));
   return sync_and_collect(ctx, "refine");
+}
+
+morse_status morse_refine(morse_ctx *ctx, const morse_event *ev,
+                          const morse_map *map, const morse_fit *starts,
+                          int n, int iters, int method, morse_fit *out) {
+  if (!ctx) return MORSE_EINVAL;
+  MORSE_TRY(check_pair(ctx, ev, map));
+  return refine_impl(ctx, ev, &map, 1, nullptr, starts, n, iters, method,
+                     out);
+}
+
+morse_status morse_refine_batch(morse_ctx *ctx, const morse_event *ev,
+                                const morse_map *const *maps, int n_maps,
+                                const int *map_of, const morse_fit *starts,
+                                int n, int iters, int method,
+                                morse_fit *out) {
+  if (!ctx) return MORSE_EINVAL;
+  if (!maps || !map_of || n_maps < 1)
+    return fail(ctx, MORSE_EINVAL, "maps, map_of and n_maps >= 1 needed");
+  for (int j = 0; j < n_maps; ++j) {
+    MORSE_TRY(check_pair(ctx, ev, maps[j]));
+    if (maps[j]->npix != maps[0]->npix || maps[j]->L != maps[0]->L)
+      return fail(ctx, MORSE_EINVAL,
+                  "map %d: every map needs the geometry of map 0 (npix %d, "
+                  "extent %g)", j, maps[0]->npix, maps[0]->L);
+  }
+  return refine_impl(ctx, ev, maps, n_maps, map_of, starts, n, iters, method,
+                     out);
 }
 
 morse_status morse_topk_merge(const morse_fit *const *lists,

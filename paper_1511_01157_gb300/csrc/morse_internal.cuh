@@ -458,9 +458,14 @@ struct RefineState {
   int *flags;                      // [n]
 };
 
+// once per device (morse_create): shared-memory limits of the adjoint
+cudaError_t adjoint_setup();
+// chi^2 (and gradient, Gauss-Newton matrix) of n trajectories on the map
+// P.quad, or with tq set on the map tq[i] of trajectory i (one geometry)
 cudaError_t launch_theta(const SearchParams &P, const double *theta, int n,
                          double t_ref, double *chi2, double *grad, double *H,
-                         double *Fs, double *Fb, int *flags, cudaStream_t st);
+                         double *Fs, double *Fb, int *flags, cudaStream_t st,
+                         const float4 *const *tq = nullptr);
 cudaError_t launch_lm_init(const RefineState &S, const morse_fit *starts,
                            int n, double lam0, cudaStream_t st);
 cudaError_t launch_lm_step(const RefineState &S, int n, cudaStream_t st);

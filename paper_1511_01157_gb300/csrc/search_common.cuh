@@ -681,10 +681,16 @@ struct Solved {
 // rounding (FP64 sums of the stored values, per event); T_A and T_AF are
 // taken as FP32 square roots rounded up, which only widens the bracket.
 // gamma is doubled as a margin.
-__device__ __forceinline__ Solved solve2(const SearchParams &P, double SA,
-                                         double SAA, double SAF) {
-  Solved o;
-  const double S1 = P.S1, SF = P.SF, iS1 = P.invS1;
+struct Fit2 {
+  double Fs, Bc;
+  bool degenerate;
+};
+
+// the solve alone (the fit of solve2, without the bound)
+__device__ __forceinline__ Fit2 fit2(const SearchParams &P, double SA,
+                                     double SAA, double SAF) {
+  Fit2 o;
+  const double S1 = P.S1, SF = P.SF;
   const double SAAu = SAA + 2.0 * SA + S1;
   const double det = SAA * S1 - SA * SA;
   if (!(det > 1e-12 * SAAu * S1)) {
@@ -697,6 +703,17 @@ __device__ __forceinline__ Solved solve2(const SearchParams &P, double SA,
     o.Bc = (SAA * SF - SA * SAF) * inv;
     o.degenerate = false;
   }
+  return o;
+}
+
+__device__ __forceinline__ Solved solve2(const SearchParams &P, double SA,
+                                         double SAA, double SAF) {
+  Solved o;
+  const double S1 = P.S1, SF = P.SF, iS1 = P.invS1;
+  const Fit2 f = fit2(P, SA, SAA, SAF);
+  o.Fs = f.Fs;
+  o.Bc = f.Bc;
+  o.degenerate = f.degenerate;
   const double g = 2.0 * P.gamma;
   const double CAA = SAA - SA * SA * iS1;
   const double CAF = SAF - SA * SF * iS1;
