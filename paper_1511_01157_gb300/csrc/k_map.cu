@@ -140,26 +140,31 @@ __device__ __forceinline__ void bin_ray(const RayParams &P, uint32_t *win,
 
 // The FP32 rays of one thread's sub-block: columns ib .. ib + na - 1
 // (FULL: na = kSubX), rows jb .. jb + kSubY - 1, two columns per packed
-// FP32 instruction.  The column terms x1, x1 - xa and x1 - xb are taken
-// once per sub-block.  Every operation is that of deflect32, rounded the
-// same way (the mass terms with -e1, -e2, exact negations), so each ray
-// lands in the same bin as there.
+// FP32 instruction.  The deflection works in bin units: with x' = x/Delta +
+// L/Delta and e' = e/Delta (taken once per sub-block and per row), the
+// bin coordinates are
+//     v1 = x1' - e1' d1 r2/(r1 r2) - e2' d2 r1/(r1 r2),
+//     v2 = x2' - (e1' r2 + e2' r1)/(r1 r2) x2,
+// d_k = x1 - x_k, r_k = d_k^2 + x2^2, one approximate reciprocal of r1 r2
+// for both lenses.  The lens terms are those of deflect32 (the window's
+// sample rays); the ray coordinates start from the sub-block, so a ray's
+// bin may differ from deflect32's by the last rounding.
 template <bool FULL>
 __device__ __forceinline__ void shoot_f32(const RayParams &P, uint32_t *win,
                                           int wx0, int wy0, long long jb,
                                           int na, float x1b, unsigned &n_off,
                                           unsigned &n_lost) {
   constexpr int NP = kSubX / 2;
-  float2 x1[NP], d1[NP], d2[NP];
+  float2 x1s[NP], d1[NP], d2[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    x1[p] = make_float2(fmaf((float)(2 * p), P.hf, x1b),
-                        fmaf((float)(2 * p + 1), P.hf, x1b));
-    d1[p] = __fadd2_rn(x1[p], f2r(-P.xaf));
-    d2[p] = __fadd2_rn(x1[p], f2r(-P.xbf));
+    const float2 x1 = make_float2(fmaf((float)(2 * p), P.hf, x1b),
+                                  fmaf((float)(2 * p + 1), P.hf, x1b));
+    d1[p] = __fadd2_rn(x1, f2r(-P.xaf));
+    d2[p] = __fadd2_rn(x1, f2r(-P.xbf));
+    x1s[p] = __ffma2_rn(x1, f2r(P.invdf), f2r(P.offf));
   }
-  const float2 ne1 = f2r(-P.e1f), ne2 = f2r(-P.e2f);
-  const float2 invd = f2r(P.invdf), off = f2r(P.offf);
+  const float2 ne1 = f2r(-P.e1f * P.invdf), ne2 = f2r(-P.e2f * P.invdf);
   const float2 M = f2r(12582912.f);
   const unsigned W = (unsigned)min(kRayWin, P.npix);
   const unsigned cx = 0x4B400000u + (unsigned)wx0;
@@ -170,6 +175,7 @@ __device__ __forceinline__ void shoot_f32(const RayParams &P, uint32_t *win,
     if (j >= P.nray) break;
     const float x2 = fmaf((float)j, P.hf, P.x0f);
     const float2 x2p = f2r(x2), x2sq = f2r(x2 * x2);
+    const float2 x2s = f2r(fmaf(x2, P.invdf, P.offf));
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       if (!FULL && 2 * p >= na) break;
@@ -177,12 +183,12 @@ __device__ __forceinline__ void shoot_f32(const RayParams &P, uint32_t *win,
       const float2 r2 = __ffma2_rn(d2[p], d2[p], x2sq);
       const float2 rr = __fmul2_rn(r1, r2);
       const float2 inv = make_float2(rcp_approx(rr.x), rcp_approx(rr.y));
-      const float2 a1 = __fmul2_rn(ne1, __fmul2_rn(r2, inv));  // -e1 r2/rr
-      const float2 a2 = __fmul2_rn(ne2, __fmul2_rn(r1, inv));  // -e2 r1/rr
-      const float2 y1 = __ffma2_rn(a2, d2[p], __ffma2_rn(a1, d1[p], x1[p]));
-      const float2 y2 = __ffma2_rn(__fadd2_rn(a1, a2), x2p, x2p);
-      const float2 tx = __fadd2_rd(__ffma2_rn(y1, invd, off), M);
-      const float2 ty = __fadd2_rd(__ffma2_rn(y2, invd, off), M);
+      const float2 a1 = __fmul2_rn(ne1, __fmul2_rn(r2, inv));  // -e1' / r1
+      const float2 a2 = __fmul2_rn(ne2, __fmul2_rn(r1, inv));  // -e2' / r2
+      const float2 v1 = __ffma2_rn(a2, d2[p], __ffma2_rn(a1, d1[p], x1s[p]));
+      const float2 v2 = __ffma2_rn(__fadd2_rn(a1, a2), x2p, x2s);
+      const float2 tx = __fadd2_rd(v1, M);
+      const float2 ty = __fadd2_rd(v2, M);
       bin_ray(P, win, cx, cy, W, tx.x, ty.x, rr.x == 0.0f, n_off, n_lost);
       if (FULL || 2 * p + 1 < na)
         bin_ray(P, win, cx, cy, W, tx.y, ty.y, rr.y == 0.0f, n_off, n_lost);
