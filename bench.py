@@ -352,6 +352,39 @@ def adjoint_section(ctx, m, cfg, ev, n_ep, stream, probes, peak_instr_s,
             "refine_median_chi2": float(np.median(out["chi2"]))}
 
 
+def fp16_section(ctx, m, cfg, ev, sizes=(1024, 2048, 4096), reps=3):
+    """FP16 log10(A) against FP32 A tables: the config-1 search (one map of
+    the truth lens, 1.44 M trajectories x 3000 epochs, top-256) at three
+    map sizes over [-2, 2]^2, rays scaled with the texel count (10^8 at
+    1024^2).  Device time of the search kernels per call (CUDA events on
+    the context stream), best of `reps`, and the best chi^2 of each."""
+    out = {}
+    grid = grid_of(m, cfg)
+    for npix in sizes:
+        nray = int(cfg["nray"] * npix / 1024)
+        mp = ctx.build_map(cfg["s"], cfg["q"], cfg["L"], npix, nray,
+                           image_halfwidth=cfg["X"], deflect="fp32",
+                           fp16log=True)
+        row = {}
+        for name, h16 in (("fp32", False), ("fp16", True)):
+            mp.set_lookup(h16)
+            ctx.grid_chi2(ev, mp, grid)  # warm
+            best, chi = None, None
+            for _ in range(reps):
+                r = ctx.grid_chi2(ev, mp, grid)
+                ms = ctx.kernel_ms(2)
+                best = ms if best is None else min(best, ms)
+                chi = float(r["chi2"][0])
+            row[name] = {"search_ms": best, "best_chi2": chi}
+        row["fp16_over_fp32_time"] = row["fp16"]["search_ms"] / \
+            row["fp32"]["search_ms"]
+        row["table_MB"] = {"fp32": 16 * (npix + 1) * (npix + 8) / 1e6,
+                           "fp16": 8 * (npix + 1) * (npix + 8) / 1e6}
+        out[f"{npix}^2"] = row
+        mp.free()
+    return out
+
+
 def config2_section(ctx, m, cfg, ev, S, Q, fits, n_starts=4096, iters=50):
     """Configuration 2: Levenberg-Marquardt refinement (adjoint gradient,
     Gauss-Newton matrix, one CUDA graph per iteration) of the n_starts
@@ -847,6 +880,8 @@ def run_gpu(args, cfg):
             out["batched"] = run_batched(ctx, m, args.batch_events,
                                          args.batch_maps,
                                          not args.no_batch_tune)
+        elif args.only == "fp16":
+            out["fp16_vs_fp32"] = fp16_section(ctx, m, cfg, ev)
         else:
             out["map_generators"] = map_generators(ctx, m, cfg)
         print(json.dumps(out))
@@ -1031,6 +1066,7 @@ def run_gpu(args, cfg):
         line["adjoint"] = adjoint_section(ctx, m, cfg, ev, len(t), stream,
                                           probes, peak_instr * 1e12)
         line["config2_refine"] = config2_section(ctx, m, cfg, ev, S, Q, fits)
+        line["fp16_vs_fp32"] = fp16_section(ctx, m, cfg, ev)
         line["batched"] = run_batched(ctx, m, args.batch_events,
                                       args.batch_maps, not args.no_batch_tune)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1079,7 +1115,7 @@ def main():
                     help="run only the peak-aligned search over the maps "
                     "and the peak library section (profiling)")
     ap.add_argument("--only", default="",
-                    choices=["", "adjoint", "batched", "rayshoot"],
+                    choices=["", "adjoint", "batched", "rayshoot", "fp16"],
                     help="run one section alone on its own workload "
                     "(profiling): the adjoint on the config-1 event, the "
                     "batched search subset, or the config-1 map builds")

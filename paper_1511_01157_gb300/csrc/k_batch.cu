@@ -5,8 +5,9 @@
 // GB300 design.
 //  * One 16-warp block per SM loops over work units taken from a global
 //    counter.  A unit is a run of warp groups of one (event, map) pair; the
-//    host lists the units longest event first, so the long light curves
-//    start early and the short ones fill the tail.
+//    host lists the units map by map (one map at a time is read from HBM
+//    into L2) and within a map longest event first, so the long light
+//    curves start early and the short ones fill the tail.
 //  * Within a unit the warps take groups from a shared-memory counter, so a
 //    warp that drew cheap trajectories (mostly outside the map) takes more.
 //  * The event's epochs are staged in shared memory when the unit's shape
@@ -19,9 +20,13 @@
 //  * Every trajectory's chi^2 is computed by the same device functions as
 //    the single-pair search (k_search), so the results of a batch are those
 //    of one morse_grid_chi2 call per pair, bit for bit.
-// Inside-map epoch loops (global-table lookups from L2) unrolled four
-// times for the FP32 table: more independent loads in flight, 4 % faster
-// on the 32-event x 8-map batch than twice (FP16-table variants: twice).
+// Inside-map epoch loops unrolled four times for the FP32 table (as
+// k_search; FP16-table variants: twice).  The map cells come from the
+// global table through L1: light curves of more than 4096 epochs, which
+// carry about 80 % of a batch's evaluations, cannot be staged in shared
+// memory and stream their epochs through L1 too, and the 131 KB of
+// k_search's band tables would take that L1 away (tried: 9.75e11 ->
+// 9.2e11 evaluations/s, L1 hit rate 90 % -> 41 %).
 #ifndef MORSE_UNROLL
 #define MORSE_UNROLL 4
 #endif

@@ -131,81 +131,24 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
 
   // Band tables.  With kSearchWarps groups per line (the host enables the
   // tables only then) the block's round r is one line; its table lives in
-  // buffer r & 1.  A warp that claims a group of round r builds the tables
-  // of rounds r and r + 1 when their buffers are free (no user left of the
-  // round two back) and nobody has; it reads round r's table only after
-  // taking a user count on a ready word, and otherwise uses the global
-  // table.  Nothing ever waits: every step falls back to the global path.
+  // buffer r & 1 (search_group.cuh: band_try_build, band_try_acquire).
   const bool use_tab = tabs != nullptr && lined &&
                        P.ng_line == (long long)kSearchWarps;
-  auto round_line = [&](long long r, double &cx, double &cy, double &c,
-                        double &s) -> bool {
+  BandTabs B;
+  B.tabs = tabs;
+  B.tw = s_tw;
+  B.tb = s_tb;
+  // the line of block round r, or -1 past the block's last group
+  auto round_line = [&](long long r) -> long long {
     const long long g0 = (long long)blockIdx.x * kSearchWarps + r * gstride;
-    if (g0 >= n_groups) return false;
-    const long long L = line0 + g0 / P.ng_line;
-    const long long iu = L / P.n_alpha;
-    const int ia = (int)(L - iu * P.n_alpha);
-    double u;
-    if (P.lu) {
-      u = P.lu[iu];
-      c = P.lc[iu];
-      s = P.ls[iu];
-    } else {
-      u = P.u0v[iu];
-      c = P.ca[ia];
-      s = P.sa[ia];
-    }
-    cx = -u * s * P.invD + P.coff;
-    cy = u * c * P.invD + P.coff;
-    return true;
-  };
-  auto try_build = [&](long long r) {  // warp-collective
-    double cx, cy, c, s;
-    if (!round_line(r, cx, cy, c, s)) return;
-    const int b = (int)(r & 1);
-    const unsigned want = (unsigned)(r + 1) << 7;
-    int got = 0;
-    if (lane == 0) {
-      const unsigned w = *(volatile unsigned *)&s_tw[b];
-      const bool idle = w == 0u || (w & 0x40u);  // empty or ready
-      if (idle && (w & 0x3Fu) == 0u && (w >> 7) < (unsigned)(r + 1))
-        got = atomicCAS(&s_tw[b], w, want) == w;
-    }
-    got = __shfl_sync(kFull, got, 0);
-    if (!got) return;
-    const int tb = build_band<H>(P, tabs + (size_t)b * P.tab_n, cx, cy, c,
-                                 s, lane);
-    __threadfence_block();
-    __syncwarp();
-    if (lane == 0) {
-      s_tb[b] = tb;
-      __threadfence_block();
-      atomicExch(&s_tw[b], want | 0x40u);
-    }
-    __syncwarp();
-  };
-  auto try_acquire = [&](long long r) -> int {  // warp-collective; 0: none
-    const int b = (int)(r & 1);
-    const unsigned want = ((unsigned)(r + 1) << 7) | 0x40u;
-    int ok = 0;
-    if (lane == 0) {
-      for (int it = 0; it < 16; ++it) {
-        const unsigned w = *(volatile unsigned *)&s_tw[b];
-        if ((w & ~0x3Fu) != want) break;
-        if (atomicCAS(&s_tw[b], w, w + 1u) == w) {
-          ok = 1;
-          break;
-        }
-      }
-      if (ok) {
-        __threadfence_block();
-        ok = *(volatile int *)&s_tb[b];
-      }
-    }
-    return __shfl_sync(kFull, ok, 0);
+    if (g0 >= n_groups) return -1;
+    return line0 + g0 / P.ng_line;
   };
   if (use_tab) {  // the first two rounds' tables before any group starts
-    if (warp < 2) try_build(warp);
+    if (warp < 2) {
+      const long long L = round_line(warp);
+      if (L >= 0) band_try_build<H>(P, B, warp, L, lane);
+    }
     __syncthreads();
   }
 
@@ -235,9 +178,10 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
     int tb = 0;
     const long long r = k / kSearchWarps;
     if (use_tab) {
-      try_build(r);
-      try_build(r + 1);
-      tb = try_acquire(r);
+      band_try_build<H>(P, B, r, round_line(r), lane);
+      const long long L1 = round_line(r + 1);
+      if (L1 >= 0) band_try_build<H>(P, B, r + 1, L1, lane);
+      tb = band_try_acquire(B, r, lane);
     }
     const float4 *tab = tabs + (size_t)(r & 1) * (use_tab ? P.tab_n : 0);
     if (tb == 1)
@@ -249,7 +193,7 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
     else
       search_group<DENSE, H>(P, ep, T, K, warp, lane, lo, hi, lined,
                              n_exact);
-    if (tb != 0 && lane == 0) atomicSub(&s_tw[(int)(r & 1)], 1u);
+    if (tb != 0) band_release(B, r, lane);
   }
   if (P.stat_exact && lane == 0 && n_exact)
     atomicAdd(P.stat_exact, n_exact);

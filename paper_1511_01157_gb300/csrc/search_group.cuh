@@ -200,6 +200,101 @@ __device__ __forceinline__ void search_group(const SearchParams &P,
   }
 }
 
+// Shared-memory band tables of the line-aligned pass (build_band), two of
+// them, alternating by block round (round r in buffer r & 1, one line per
+// round).  A warp that claims a group of round r builds the tables of
+// rounds r and r + 1 when their buffers are free (no user left of the
+// round two back) and nobody has; it reads round r's table only after
+// taking a user count on a ready word, and otherwise uses the global table
+// (same bits).  Nothing ever waits.  Words: ((round + 1) << 7) | (ready <<
+// 6) | users; 0 = empty.
+struct BandTabs {
+  float4 *tabs;  // 2 tables of P.tab_n entries
+  unsigned *tw;  // [2] words
+  int *tb;       // [2] orientations (1: x-major, 2: y-major)
+};
+
+// Centred coordinates of the point of line L nearest the origin, and its
+// direction (the line's row of the grid tables, or of a line grid).
+__device__ __forceinline__ void band_line(const SearchParams &P, long long L,
+                                          double &cx, double &cy, double &c,
+                                          double &s) {
+  const long long iu = L / P.n_alpha;
+  const int ia = (int)(L - iu * P.n_alpha);
+  double u;
+  if (P.lu) {
+    u = P.lu[iu];
+    c = P.lc[iu];
+    s = P.ls[iu];
+  } else {
+    u = P.u0v[iu];
+    c = P.ca[ia];
+    s = P.sa[ia];
+  }
+  cx = -u * s * P.invD + P.coff;
+  cy = u * c * P.invD + P.coff;
+}
+
+// warp-collective: build the table of round r (line L) if its buffer is
+// free and nobody has
+template <bool H>
+__device__ __forceinline__ void band_try_build(const SearchParams &P,
+                                               BandTabs &B, long long r,
+                                               long long L, int lane) {
+  const int b = (int)(r & 1);
+  const unsigned want = (unsigned)(r + 1) << 7;
+  int got = 0;
+  if (lane == 0) {
+    const unsigned w = *(volatile unsigned *)&B.tw[b];
+    const bool idle = w == 0u || (w & 0x40u);  // empty or ready
+    if (idle && (w & 0x3Fu) == 0u && (w >> 7) < (unsigned)(r + 1))
+      got = atomicCAS(&B.tw[b], w, want) == w;
+  }
+  got = __shfl_sync(kFull, got, 0);
+  if (!got) return;
+  double cx, cy, c, s;
+  band_line(P, L, cx, cy, c, s);
+  const int tb = build_band<H>(P, B.tabs + (size_t)b * P.tab_n, cx, cy, c, s,
+                               lane);
+  __threadfence_block();
+  __syncwarp();
+  if (lane == 0) {
+    B.tb[b] = tb;
+    __threadfence_block();
+    atomicExch(&B.tw[b], want | 0x40u);
+  }
+  __syncwarp();
+}
+
+// warp-collective: a user count on round r's table; returns its
+// orientation, or 0 (not ready: use the global table)
+__device__ __forceinline__ int band_try_acquire(BandTabs &B, long long r,
+                                                int lane) {
+  const int b = (int)(r & 1);
+  const unsigned want = ((unsigned)(r + 1) << 7) | 0x40u;
+  int ok = 0;
+  if (lane == 0) {
+    for (int it = 0; it < 16; ++it) {
+      const unsigned w = *(volatile unsigned *)&B.tw[b];
+      if ((w & ~0x3Fu) != want) break;
+      if (atomicCAS(&B.tw[b], w, w + 1u) == w) {
+        ok = 1;
+        break;
+      }
+    }
+    if (ok) {
+      __threadfence_block();
+      ok = *(volatile int *)&B.tb[b];
+    }
+  }
+  return __shfl_sync(kFull, ok, 0);
+}
+
+__device__ __forceinline__ void band_release(BandTabs &B, long long r,
+                                             int lane) {
+  if (lane == 0) atomicSub(&B.tw[(int)(r & 1)], 1u);
+}
+
 // Record of one selected trajectory e (warp-collective; lane 0 writes *dst):
 // the phase-1 sums, the solve and the phase-2 chi^2 recomputed with the
 // search's device functions, on the epochs at P.ep (global memory).
