@@ -216,12 +216,12 @@ def make_event(ctx, m, cfg, seed):
     return t, F, sig
 
 
-def grid_of(m, cfg):
+def grid_of(m, cfg, top_k=None):
     g = cfg["grid"]
     return m.Grid.make(g["n_u0"], g["n_alpha"], g["n_t0"], g["n_tE"],
                        g["u0_lo"], g["u0_hi"], g["t0_lo"], g["t0_hi"],
                        g["tE_lo"], g["tE_hi"], g["u0_log"], g["tE_log"],
-                       cfg["top_k"])
+                       cfg["top_k"] if top_k is None else top_k)
 
 
 def grid_lines(cfg):
@@ -270,10 +270,31 @@ def peak_library(ctx, m, cfg, delta=0.1, max_peaks=8):
     h = 2.0 * cfg["L"] / cfg["npix"] / 2
     n = inside_samples(lines, cfg["L"], h)
     t = min(times)
+    # the libraries of 64 maps of the (s, q) grid in one launch
+    S, Q = sq_lists(cfg)
+    pick = np.linspace(0, len(S) - 1, 64).round().astype(int)
+    maps = [ctx.build_map(S[j], Q[j], cfg["L"], cfg["npix"], cfg["nray"],
+                          image_halfwidth=cfg["X"], deflect="fp32")
+            for j in pick]
+    tb = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.line_peaks_batch(maps, lines, sub=2, max_peaks=max_peaks,
+                             delta=delta)
+        torch.cuda.synchronize()
+        tb.append(time.perf_counter() - t0)
+    for mp in maps:
+        mp.free()
     return {"lines": len(lines), "ms": 1e3 * t, "samples": n,
             "samples_per_s": n / t, "delta": delta,
             "median_peaks_per_line": float(np.median(count)),
-            "max_peaks_per_line": int(count.max())}
+            "max_peaks_per_line": int(count.max()),
+            "batch_64_maps_ms": 1e3 * min(tb),
+            "batch_samples_per_s": 64 * n / min(tb),
+            "note": "samples of the lines inside the map, every half "
+                    "texel; the batch is one launch over 64 maps' lines "
+                    "(C-ABI call, device synchronised)"}
 
 
 def adjoint_section(ctx, m, cfg, ev, n_ep, stream, probes, peak_instr_s,
@@ -669,6 +690,33 @@ def time_to_best_fit(ctx, m, cfg, ev, S, Q, plain_s, plain_fits, ev_t,
         t, b, "20x36x13x10 grid on all 651 maps, the 40x72x25x20 grid on "
         "the 256 best maps, then 40 LM iterations on the 16 best seeds of "
         "the 8 best of those")
+    def resident_batched():
+        # every map built once and kept resident (about 25 MB each, 16 GB
+        # for the 651), the coarse screen of all of them and the full grid
+        # on the 256 best each as one batched launch, then the 16 best
+        # seeds of the 8 best maps refined in one call
+        built = [ctx.build_map(S[j], Q[j], cfg["L"], cfg["npix"],
+                               cfg["nray"], image_halfwidth=cfg["X"],
+                               deflect="fp32") for j in range(len(S))]
+        first = ctx.grid_chi2_batch([ev], built, coarse)[0]
+        best = np.sort(np.argsort(first["chi2"][:, 0])[:256])
+        sub = [built[j] for j in best]
+        fine = ctx.grid_chi2_batch([ev], sub, grid_of(m, cfg, top_k=16))[0]
+        top = np.argsort(fine["chi2"][:, 0])[:8]
+        seeds = np.concatenate([fine[j][:16] for j in top])
+        map_of = np.repeat(np.arange(len(top)), 16).astype(np.int32)
+        keep = np.isfinite(seeds["chi2"])
+        r = ctx.refine_batch(ev, [sub[j] for j in top], map_of[keep],
+                             seeds[keep], iters=40)
+        for mp in built:
+            mp.free()
+        return float(r["chi2"].min())
+    b, t = timed(resident_batched)
+    forms["resident_batched_screen_grid_refine"] = (
+        t, b, "all 651 maps built and kept resident; the 20x36x13x10 "
+        "screen of all of them in one batched launch, the 40x72x25x20 grid "
+        "on the 256 best in one batched launch, then 40 LM iterations of "
+        "the 16 best seeds of the 8 best maps in one batched refine")
     # §4.3 (i): the smallest peak magnification the data allow when the
     # blend flux is not negative, F_peak / F_base with F_peak the largest
     # flux less 3 sigma and F_base the median of the faintest fifth

@@ -353,6 +353,20 @@ morse_status morse_line_peaks(morse_ctx *ctx, const morse_map *map,
                               const morse_peak_opts *opts, int32_t *count,
                               double *pos, double *height);
 
+/* morse_line_peaks of the same lines on n_maps maps of one geometry in one
+ * launch (the libraries of a whole (s, q) grid: enough lines to fill the
+ * GPU, where one map's few thousand lines leave it latency-bound).  Map m's
+ * results are those morse_line_peaks gives for it, bit for bit, at
+ * count[m n_lines + j], pos[(m n_lines + j) max_peaks + k] and height[...].
+ * Errors: EINVAL (as morse_line_peaks; maps of another npix or extent),
+ * ENOMEM, ECUDA. */
+morse_status morse_line_peaks_batch(morse_ctx *ctx,
+                                    const morse_map *const *maps, int n_maps,
+                                    const double *lines, int n_lines,
+                                    const morse_peak_opts *opts,
+                                    int32_t *count, double *pos,
+                                    double *height);
+
 /* Search of the trajectories the peak library allows (§4.3 (iii)-(v)).
  * Lines with fewer than max(min_peaks, n_tp) peaks are not searched.
  *  n_tp = 0: the line grid of morse_grid_chi2_lines over lines[n_lines];

@@ -192,6 +192,7 @@ _SIGS = {
     "morse_inject_fault": (_S, [_P, _I, _I64]),
     "morse_grid_chi2_range": (_S, [_P, _P, _P, _P, _I64, _I64, _P]),
     "morse_refine_batch": (_S, [_P, _P, _P, _I, _P, _P, _I, _I, _I, _P]),
+    "morse_line_peaks_batch": (_S, [_P, _P, _I, _P, _I, _P, _P, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -367,6 +368,22 @@ class Context:
                                           ctypes.byref(o), _ptr(count),
                                           _ptr(pos), _ptr(height)),
                     "morse_line_peaks")
+        return count, pos, height
+
+    def line_peaks_batch(self, maps, lines, sub=2, max_peaks=8, delta=0.0):
+        """Peak libraries of several maps along the same lines in one
+        launch (morse_line_peaks_batch): (count[n_maps, n],
+        pos[n_maps, n, max_peaks], height[n_maps, n, max_peaks])."""
+        lines = np.ascontiguousarray(lines, dtype=np.float64).reshape(-1, 3)
+        n, nm = len(lines), len(maps)
+        count = np.zeros((nm, n), dtype=np.int32)
+        pos = np.zeros((nm, n, max_peaks))
+        height = np.zeros((nm, n, max_peaks))
+        o = PeakOpts(int(sub), int(max_peaks), float(delta))
+        mp = (ctypes.c_void_p * nm)(*[m._h for m in maps])
+        self._check(_lib.morse_line_peaks_batch(
+            self._h, mp, nm, _ptr(lines), n, ctypes.byref(o), _ptr(count),
+            _ptr(pos), _ptr(height)), "morse_line_peaks_batch")
         return count, pos, height
 
     def peak_search(self, event, map_, grid: Grid, lines, tp=(),

@@ -39,16 +39,25 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPkWarps = 4;
 
+// Warp w takes line w % n_lines of map w / n_lines: the map A0, or As[m]
+// of a batch of maps of one geometry (more warps per SM than one map's
+// lines give).  Outputs of map m, line j at index m n_lines + j.
 __global__ void __launch_bounds__(kPkWarps * 32)
-    k_line_peaks(const float *__restrict__ A, int npix, double L,
-                 const double *__restrict__ lu, const double *__restrict__ lc,
+    k_line_peaks(const float *__restrict__ A0,
+                 const float *const *__restrict__ As, int n_maps, int npix,
+                 double L, const double *__restrict__ lu,
+                 const double *__restrict__ lc,
                  const double *__restrict__ ls, const double *__restrict__ lsh,
                  int n_lines, int sub, float r, int max_peaks,
                  int *__restrict__ count, double *__restrict__ pos,
                  double *__restrict__ height, unsigned *__restrict__ err) {
   const int lane = threadIdx.x & 31;
-  const int line = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (line >= n_lines) return;  // warp-uniform; the kernel has no barrier
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= (long long)n_lines * n_maps) return;  // warp-uniform, no barrier
+  const int mi = (int)(w / n_lines);
+  const int line = (int)(w - (long long)mi * n_lines);
+  const float *__restrict__ A = As ? As[mi] : A0;
+  const long long out = w;  // mi n_lines + line
   const double u = lu[line], c = lc[line], s = ls[line], sh = lsh[line];
   // the line in texel coordinates, p = a tau + b, in FP64 then FP32
   const double dlt = __ddiv_rn(__dmul_rn(2.0, L), (double)npix);
@@ -201,14 +210,14 @@ __global__ void __launch_bounds__(kPkWarps * 32)
     const int kp = __shfl_sync(kFull, kk, p);
     rank += (kp < kk) ? 1 : 0;
   }
-  if (lane == 0) count[line] = cnt;
+  if (lane == 0) count[out] = cnt;
   if (lane < max_peaks) {
     if (lane < nkept) {
-      const size_t o = (size_t)line * max_peaks + rank;
+      const size_t o = (size_t)out * max_peaks + rank;
       pos[o] = __dsub_rn(__dmul_rn((double)kk, h), sh);
       height[o] = (double)kh;
     } else {
-      const size_t o = (size_t)line * max_peaks + lane;
+      const size_t o = (size_t)out * max_peaks + lane;
       pos[o] = CUDART_NAN;
       height[o] = CUDART_NAN;
     }
@@ -272,17 +281,19 @@ __global__ void k_peak_entries(int n_lines, const double *__restrict__ lu,
 
 }  // namespace
 
-cudaError_t launch_line_peaks(const float *A, int npix, double L,
+cudaError_t launch_line_peaks(const float *A, const float *const *As,
+                              int n_maps, int npix, double L,
                               const double *lu, const double *lc,
                               const double *ls, const double *lsh,
                               int n_lines, int sub, float r, int max_peaks,
                               int *count, double *pos, double *height,
                               unsigned *err, cudaStream_t st) {
-  if (n_lines <= 0) return cudaSuccess;
-  const int blocks = (n_lines + kPkWarps - 1) / kPkWarps;
-  k_line_peaks<<<blocks, kPkWarps * 32, 0, st>>>(A, npix, L, lu, lc, ls, lsh,
-                                                 n_lines, sub, r, max_peaks,
-                                                 count, pos, height, err);
+  const long long warps = (long long)n_lines * n_maps;
+  if (warps <= 0) return cudaSuccess;
+  const long long blocks = (warps + kPkWarps - 1) / kPkWarps;
+  k_line_peaks<<<(unsigned)blocks, kPkWarps * 32, 0, st>>>(
+      A, As, n_maps, npix, L, lu, lc, ls, lsh, n_lines, sub, r, max_peaks,
+      count, pos, height, err);
   return cudaGetLastError();
 }
 

@@ -839,10 +839,14 @@ std::string tune_key(int bucket, const morse_grid *g, const morse_map *m) {
 }
 
 // Staging is decided per bucket, so that one shape holds for every light
-// curve of the bucket: the default stages buckets of fewer than 4096
-// epochs, the tuner may try staging up to 8191 (128 KB).
+// curve of the bucket: buckets of fewer than 4096 epochs (64 KB) may be
+// staged.  Staging larger ones looks faster when a bucket is timed alone,
+// but the batch's one launch then reserves that shared memory on every
+// SM, and the long light curves, which stream their epochs through L1 and
+// carry most of the evaluations, lose the L1 (tuned with up to 8191
+// staged: 9.1e11 evaluations/s against 9.75e11).
 constexpr int kBatchStageDefault = 4095;
-constexpr int kBatchStageMax = 8191;
+constexpr int kBatchStageMax = 4095;
 
 int64_t bucket_top(int64_t n_ep) {
   return (int64_t(2) << ep_bucket(n_ep)) - 1;
@@ -1224,7 +1228,12 @@ morse_status batch_tune(morse_ctx *ctx, const morse_event *ev,
   const bool h16 = morse::map_h16(map0);
   const morse_event *evs[1] = {ev};
   const morse_map *maps[1] = {map0};
-  constexpr long long kTuneTrajs = 300000;
+  // a sample of about 2e8 trajectory-epochs (a few hundred microseconds,
+  // long enough to time), the whole pair if it has fewer; each candidate
+  // timed three times, the fastest run counting
+  const long long kTuneTrajs =
+      std::max(300000LL, (long long)(2e8 / (double)std::max<int64_t>(
+                                              ev->n, 1)));
   double best_ns = 0.0;
   cudaEvent_t e0, e1;
   MORSE_CUDA(ctx, cudaEventCreate(&e0));
@@ -1276,24 +1285,33 @@ morse_status batch_tune(morse_ctx *ctx, const morse_event *ev,
     if (bps < 1) continue;
     const int grid = bps * ctx->sm_count;
     cands[c].stage = H.ep_cap > 0 ? 1 : 0;  // as the preparation fitted it
-    cudaMemsetAsync(base + L.off_gthr, 0xFF, sizeof(unsigned long long),
-                    ctx->stream);
-    cudaMemsetAsync(base + L.off_hdr, 0, sizeof(BatchHdr), ctx->stream);
     Entry *pa = (Entry *)(base + L.off_pa), *pb = (Entry *)(base + L.off_pb);
-    if (Bp.n_units > 0) {
-      morse::launch_batch(Bp, h16, std::min(grid, Bp.n_units), smem,
+    float ms = 0.f;
+    ce = cudaSuccess;
+    for (int rep = 0; rep < 3 && ce == cudaSuccess; ++rep) {
+      // every run starts from the pilot's threshold (the main pass lowers
+      // it), so the candidates are timed on the same pruning
+      cudaMemsetAsync(base + L.off_gthr, 0xFF, sizeof(unsigned long long),
+                      ctx->stream);
+      cudaMemsetAsync(base + L.off_hdr, 0, sizeof(BatchHdr), ctx->stream);
+      if (Bp.n_units > 0) {
+        morse::launch_batch(Bp, h16, std::min(grid, Bp.n_units), smem,
+                            ctx->stream);
+        morse::launch_batch_merge(pa, pb, (const int *)(base + L.off_lp), 1,
+                                  g->top_k, (Entry *)(base + L.off_res),
+                                  Bm.gthr, ctx->stream);
+        ctx->launches += 2;
+      }
+      cudaEventRecord(e0, ctx->stream);
+      morse::launch_batch(Bm, h16, std::min(grid, Bm.n_units), smem,
                           ctx->stream);
-      morse::launch_batch_merge(pa, pb, (const int *)(base + L.off_lp), 1,
-                                g->top_k, (Entry *)(base + L.off_res),
-                                Bm.gthr, ctx->stream);
-      ctx->launches += 2;
+      cudaEventRecord(e1, ctx->stream);
+      ctx->launches += 1;
+      ce = cudaStreamSynchronize(ctx->stream);
+      float r = 0.f;
+      if (ce == cudaSuccess) cudaEventElapsedTime(&r, e0, e1);
+      if (rep == 0 || r < ms) ms = r;
     }
-    cudaEventRecord(e0, ctx->stream);
-    morse::launch_batch(Bm, h16, std::min(grid, Bm.n_units), smem,
-                        ctx->stream);
-    cudaEventRecord(e1, ctx->stream);
-    ctx->launches += 1;
-    ce = cudaStreamSynchronize(ctx->stream);
     if (ce != cudaSuccess) {
       st = cuda_fail(ctx, ce, "tuning run");
       break;
@@ -1306,8 +1324,6 @@ morse_status batch_tune(morse_ctx *ctx, const morse_event *ev,
     }
     st = batch_hdr_check(ctx, hh);
     if (st != MORSE_OK) break;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
     const double ns = 1e6 * (double)ms / ((double)trajs * (double)ev->n) *
                       (c == 0 ? 0.95 : 1.0);
     if (best_ns == 0.0 || ns < best_ns) {
@@ -2752,25 +2768,33 @@ morse_status upload_lines(morse_ctx *ctx, const double *lines, int n,
 // Device layout of a peak library of n lines, P peaks each, at base + off.
 struct PeakLib {
   double *lines;  // 5 n: u, cos, sin, shift, alpha
-  int *count;     // n
-  double *pos, *height;  // n P each
+  int *count;     // n (per map)
+  double *pos, *height;  // n P each (per map)
   unsigned *err;
+  const float **maps;    // the maps' values (batched library)
   size_t bytes;
 };
 
-PeakLib peak_lib_layout(char *base, size_t off, int n, int P) {
+// (n_maps > 1: counts and peaks of every map, map-major; then the maps'
+// value pointers)
+PeakLib peak_lib_layout(char *base, size_t off, int n, int P,
+                        int n_maps = 1) {
   PeakLib L;
+  const size_t nm = (size_t)n * (size_t)n_maps;
   size_t o = align_up(off, 256);
   L.lines = (double *)(base + o);
   o = align_up(o + sizeof(double) * 5 * (size_t)n, 256);
   L.count = (int *)(base + o);
-  o = align_up(o + sizeof(int) * (size_t)n, 256);
+  o = align_up(o + sizeof(int) * nm, 256);
   L.pos = (double *)(base + o);
-  o = align_up(o + sizeof(double) * (size_t)n * P, 256);
+  o = align_up(o + sizeof(double) * nm * P, 256);
   L.height = (double *)(base + o);
-  o = align_up(o + sizeof(double) * (size_t)n * P, 256);
+  o = align_up(o + sizeof(double) * nm * P, 256);
   L.err = (unsigned *)(base + o);
-  L.bytes = o + 256 - off;
+  o += 256;
+  L.maps = (const float **)(base + o);
+  o = align_up(o + sizeof(void *) * (size_t)n_maps, 256);
+  L.bytes = o - off;
   return L;
 }
 
@@ -2780,10 +2804,10 @@ morse_status enqueue_peak_lib(morse_ctx *ctx, const morse_map *map,
   MORSE_CUDA(ctx, cudaMemsetAsync(L.err, 0, sizeof(unsigned), ctx->stream));
   const float r = (float)(1.0 + o->delta);
   MORSE_CUDA(ctx, morse::launch_line_peaks(
-                      map->A, map->npix, map->L, L.lines, L.lines + n,
-                      L.lines + 2 * (size_t)n, L.lines + 3 * (size_t)n, n,
-                      o->sub, r, o->max_peaks, L.count, L.pos, L.height,
-                      L.err, ctx->stream));
+                      map->A, nullptr, 1, map->npix, map->L, L.lines,
+                      L.lines + n, L.lines + 2 * (size_t)n,
+                      L.lines + 3 * (size_t)n, n, o->sub, r, o->max_peaks,
+                      L.count, L.pos, L.height, L.err, ctx->stream));
   ctx->launches += 1;
   return MORSE_OK;
 }
@@ -2818,6 +2842,63 @@ morse_status morse_line_peaks(morse_ctx *ctx, const morse_map *map,
                                   cudaMemcpyDeviceToHost, ctx->stream));
   MORSE_CUDA(ctx, cudaMemcpyAsync(height, L.height,
                                   sizeof(double) * (size_t)n_lines * P,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_CUDA(ctx, cudaMemcpyAsync(&err, L.err, sizeof(unsigned),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_TRY(sync_and_collect(ctx, "peak library"));
+  if (err) return fail(ctx, MORSE_ECUDA, "peak library: sample run clipped");
+  return MORSE_OK;
+}
+
+morse_status morse_line_peaks_batch(morse_ctx *ctx,
+                                    const morse_map *const *maps, int n_maps,
+                                    const double *lines, int n_lines,
+                                    const morse_peak_opts *opts,
+                                    int32_t *count, double *pos,
+                                    double *height) {
+  if (!ctx || !maps || !lines || !count || !pos || !height || n_lines < 1 ||
+      n_maps < 1)
+    return MORSE_EINVAL;
+  if ((long long)n_lines * n_maps > 0x7fffffffLL)
+    return fail(ctx, MORSE_EINVAL, "too many (map, line) pairs");
+  for (int m = 0; m < n_maps; ++m) {
+    if (!maps[m] || maps[m]->ctx != ctx)
+      return fail(ctx, MORSE_EINVAL, "map %d is NULL or of another ctx", m);
+    if (maps[m]->npix != maps[0]->npix || maps[m]->L != maps[0]->L)
+      return fail(ctx, MORSE_EINVAL,
+                  "map %d differs from map 0 in npix or extent", m);
+  }
+  MORSE_TRY(check_peak_opts(ctx, opts));
+  if (maps[0]->npix < 2) return fail(ctx, MORSE_EINVAL, "map of one texel");
+  MORSE_CUDA(ctx, cudaSetDevice(ctx->device));
+  call_begin(ctx);
+  const int P = opts->max_peaks;
+  const size_t nm = (size_t)n_lines * (size_t)n_maps;
+  const size_t bytes = peak_lib_layout(nullptr, 0, n_lines, P, n_maps).bytes;
+  void *ws = nullptr;
+  MORSE_TRY(ws_reserve(ctx, bytes, &ws));
+  const PeakLib L = peak_lib_layout((char *)ws, 0, n_lines, P, n_maps);
+  std::vector<const float *> ptr((size_t)n_maps);
+  for (int m = 0; m < n_maps; ++m) ptr[(size_t)m] = maps[m]->A;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(L.maps, ptr.data(),
+                                  sizeof(void *) * (size_t)n_maps,
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  MORSE_TRY(upload_lines(ctx, lines, n_lines, L.lines));  // synchronises
+  MORSE_CUDA(ctx, cudaMemsetAsync(L.err, 0, sizeof(unsigned), ctx->stream));
+  const float r = (float)(1.0 + opts->delta);
+  const int n = n_lines;
+  MORSE_CUDA(ctx, morse::launch_line_peaks(
+                      nullptr, L.maps, n_maps, maps[0]->npix, maps[0]->L,
+                      L.lines, L.lines + n, L.lines + 2 * (size_t)n,
+                      L.lines + 3 * (size_t)n, n, opts->sub, r, P, L.count,
+                      L.pos, L.height, L.err, ctx->stream));
+  ctx->launches += 1;
+  unsigned err = 0;
+  MORSE_CUDA(ctx, cudaMemcpyAsync(count, L.count, sizeof(int) * nm,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_CUDA(ctx, cudaMemcpyAsync(pos, L.pos, sizeof(double) * nm * P,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  MORSE_CUDA(ctx, cudaMemcpyAsync(height, L.height, sizeof(double) * nm * P,
                                   cudaMemcpyDeviceToHost, ctx->stream));
   MORSE_CUDA(ctx, cudaMemcpyAsync(&err, L.err, sizeof(unsigned),
                                   cudaMemcpyDeviceToHost, ctx->stream));

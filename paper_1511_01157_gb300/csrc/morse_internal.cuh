@@ -361,7 +361,10 @@ constexpr int kPeakMax = 16;  // peaks kept per line, at most
 // (iii)): count[j], and the max_peaks highest peaks as pos[j max_peaks + m]
 // (tau from the reference point) and height[...], NaN in unused slots;
 // err |= 1 if the sample run was clipped (never expected)
-cudaError_t launch_line_peaks(const float *A, int npix, double L,
+// (of the map A, or with As set of the n_maps maps As[m] of one geometry:
+// outputs of map m, line j at index m n_lines + j)
+cudaError_t launch_line_peaks(const float *A, const float *const *As,
+                              int n_maps, int npix, double L,
                               const double *lu, const double *lc,
                               const double *ls, const double *lsh,
                               int n_lines, int sub, float r, int max_peaks,

@@ -221,3 +221,25 @@ def test_peak_search_all_cut_and_errors(ctx, m, amap):
     with pytest.raises(m.MorseError) as e:  # two peak times fix tE
         ctx.peak_search(ev, mp, g, lines, tp=tps)
     assert e.value.status == m.EINVAL
+
+
+def test_library_batch_over_maps_equals_per_map(ctx, m):
+    # the libraries of several maps in one launch are those of one call per
+    # map, bit for bit
+    lines = _grid_lines(7, 18, -1.2, 1.2)
+    maps = [ctx.build_map(s, q, L_, 192, 900, image_halfwidth=3.0,
+                          deflect="fp32")
+            for s, q in ((0.8, 1e-3), (1.1, 1e-2), (1.6, 3e-4))]
+    cb, pb, hb = ctx.line_peaks_batch(maps, lines, sub=2, max_peaks=5,
+                                      delta=0.05)
+    for k, mp in enumerate(maps):
+        c, p, h = ctx.line_peaks(mp, lines, sub=2, max_peaks=5, delta=0.05)
+        np.testing.assert_array_equal(cb[k], c)
+        np.testing.assert_array_equal(pb[k], p)
+        np.testing.assert_array_equal(hb[k], h)
+    other = ctx.build_map(1.0, 1e-3, L_, 128, 400)
+    with pytest.raises(m.MorseError) as e:
+        ctx.line_peaks_batch([maps[0], other], lines)
+    assert e.value.status == m.EINVAL
+    for mp in maps + [other]:
+        mp.free()
