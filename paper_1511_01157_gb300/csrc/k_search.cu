@@ -53,6 +53,8 @@
 #include <math_constants.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "morse_internal.cuh"
 #include "search_common.cuh"
 #include "search_group.cuh"
@@ -249,9 +251,83 @@ __global__ void k_merge_level(const Entry *__restrict__ in,
   }
 }
 
-// Fit fill: one warp per selected trajectory recomputes the phase-1 sums,
-// the solve and the phase-2 chi^2 with the same device functions as the
-// search, and writes the public morse_fit record.
+// The same merge, W = 4 or 16 lists at a time, with one block per input
+// list: the block stages its group's lists in shared memory (so the binary
+// searches of the ranks cost shared-memory latency, not L2 latency), ranks
+// its own list's entries against the others and writes those of rank < k
+// to the group's output list.  With `seed` on the last level, the entry of
+// final rank k - 1 lowers *seed to its chi^2 (as k_seed_threshold).
+__device__ __forceinline__ int lower_rank(const Entry *B, int k,
+                                          const Entry &e) {
+  int lo = 0, hi = k;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (key_less(B[mid], e))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// S = ways / 4 consecutive threads rank one entry, each against a quarter
+// of the group's other lists; their counts are summed by shuffles.
+__global__ void __launch_bounds__(1024)
+    k_merge_rank(const Entry *__restrict__ in, Entry *__restrict__ out,
+                 int lists, int k, int ways, unsigned long long *seed) {
+  extern __shared__ __align__(16) unsigned char msm[];
+  Entry *grp = reinterpret_cast<Entry *>(msm);
+  const int l = blockIdx.x;
+  const int g = l / ways, l0 = g * ways;
+  const int n = min(ways, lists - l0);
+  {
+    // the group's lists, four independent 16-byte loads per thread in
+    // flight (the copy is bound by L2 latency otherwise)
+    const float4 *src = reinterpret_cast<const float4 *>(in + (size_t)l0 * k);
+    float4 *dst = reinterpret_cast<float4 *>(grp);
+    const int nv = n * k * (int)(sizeof(Entry) / sizeof(float4));
+    const int st = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < nv; i0 += 4 * st) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + u * st < nv) v[u] = __ldcg(src + i0 + u * st);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + u * st < nv) dst[i0 + u * st] = v[u];
+    }
+  }
+  __syncthreads();
+  const int me = l - l0;
+  const int S = ways >= 16 ? 4 : 1;  // threads per entry (a power of 2)
+  const int part = threadIdx.x & (S - 1);
+  const int per = blockDim.x / S;
+  for (int i0 = 0; i0 < k; i0 += per) {  // block-uniform trip count
+    const int i = i0 + (int)threadIdx.x / S;
+    const bool has = i < k;
+    Entry e;
+    e.chi2 = 0.0;
+    e.idx = 0;
+    int r = 0;
+    if (has) {
+      e = grp[(size_t)me * k + i];
+      for (int m = part; m < n; m += S)
+        if (m != me) r += lower_rank(grp + (size_t)m * k, k, e);
+    }
+    for (int o = 1; o < S; o <<= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    r += i;
+    if (has && part == 0 && r < k) {
+      out[(size_t)g * k + r] = e;
+      if (seed && r == k - 1 && e.chi2 < CUDART_INF && e.idx >= 0 &&
+          e.idx < 0x7fff000000000000LL)
+        atomicMin(seed, (unsigned long long)__double_as_longlong(e.chi2));
+    }
+  }
+}
+
+// Fit fill: one warp per selected trajectory recomputes the phase-1 sums
+// and the solve with the same device functions as the search, and writes
+// the public morse_fit record with the search's chi^2.
 template <bool H>
 __global__ void k_fill(const FillParams F) {
   const int lane = threadIdx.x & 31;
@@ -383,28 +459,67 @@ cudaError_t launch_search(const SearchParams &P, bool dense, bool ep_smem,
 }
 
 cudaError_t launch_topk_merge(Entry *a, Entry *b, int lists, int k,
-                              Entry **result, int *levels, cudaStream_t st) {
+                              Entry **result, int *levels, cudaStream_t st,
+                              unsigned long long *seed) {
   Entry *in = a, *out = b;
   *levels = 0;
+  // the device's shared-memory limit, and the rank kernel's limit raised
+  // to it, once per device
+  static int optin_of[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int optin = dev < 64 ? optin_of[dev] : 0;
+  if (optin == 0) {
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                           dev);
+    cudaFuncSetAttribute(k_merge_rank,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (dev < 64) optin_of[dev] = optin;
+  }
+  bool seeded = false;
   while (lists > 1) {
-    const long long total = (long long)lists * k;
-    long long g = (total + 255) / 256;
-    if (g > 65535) g = 65535;
-    k_merge_level<<<(int)g, 256, 0, st>>>(in, out, lists, k);
+    // 16 lists per group when they fit in shared memory (k <= 908 at
+    // 227 KB), else 4 (k <= 3632), else the global-memory 4-way levels
+    const size_t per = sizeof(Entry) * (size_t)k;
+    const int ways = lists > kMergeWays && 16 * per <= (size_t)optin ? 16
+                     : kMergeWays * per <= (size_t)optin ? kMergeWays : 0;
+    const int next = (lists + (ways ? ways : kMergeWays) - 1) /
+                     (ways ? ways : kMergeWays);
+    if (ways > 0) {
+      const size_t sm = (size_t)min(ways, lists) * per;
+      unsigned long long *sd = next == 1 ? seed : nullptr;
+      // threads: S per entry for up to all k entries at once, whole warps
+      const int S = ways >= 16 ? 4 : 1;
+      const int threads = std::min(1024, ((k * S + 31) / 32) * 32);
+      k_merge_rank<<<lists, threads, sm, st>>>(in, out, lists, k, ways, sd);
+      seeded = sd != nullptr;
+    } else {
+      const long long total = (long long)lists * k;
+      long long g = (total + 255) / 256;
+      if (g > 65535) g = 65535;
+      k_merge_level<<<(int)g, 256, 0, st>>>(in, out, lists, k);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ++*levels;
-    lists = (lists + kMergeWays - 1) / kMergeWays;
+    lists = next;
     Entry *t = in;
     in = out;
     out = t;
   }
   *result = in;
+  if (seed && !seeded) {
+    cudaError_t e = launch_seed_threshold(in, k, seed, st);
+    if (e != cudaSuccess) return e;
+    ++*levels;
+  }
   return cudaSuccess;
 }
 
 cudaError_t launch_fill(const FillParams &F, cudaStream_t st) {
-  const int threads = 256;
+  // two warps per block: the records' warps spread over the SMs (each
+  // warp's walk over the epochs is latency-bound)
+  const int threads = 64;
   const int blocks = (F.k * 32 + threads - 1) / threads;
   if (F.S.quadh)
     k_fill<true><<<blocks, threads, 0, st>>>(F);

@@ -526,7 +526,7 @@ struct Plan {
   bool dense, ep_smem;
   size_t smem;
   int grid;
-  size_t off_tab, off_lmax, off_hdr, off_pa, off_pb, off_out, bytes;
+  size_t off_tab, off_lmax, off_hdr, off_pub, off_pa, off_pb, off_out, bytes;
   int tab_n;  // band-table entries (0: the search reads the global table)
 };
 
@@ -565,7 +565,8 @@ struct Hdr {
 morse_status hdr_init(morse_ctx *ctx, char *base, const Plan &pl,
                       morse::SearchParams *P) {
   Hdr *h = (Hdr *)(base + pl.off_hdr);
-  MORSE_CUDA(ctx, cudaMemsetAsync(h, 0, sizeof(Hdr), ctx->stream));
+  // the header and the published block quantiles (tag 0: none)
+  MORSE_CUDA(ctx, cudaMemsetAsync(h, 0, pl.off_pa - pl.off_hdr, ctx->stream));
   MORSE_CUDA(ctx, cudaMemsetAsync(&h->gthr, 0xFF, sizeof(h->gthr),
                                   ctx->stream));
   P->gthr = &h->gthr;
@@ -658,7 +659,12 @@ morse_status plan_search(morse_ctx *ctx, const morse_event *ev,
   pl->off_lmax = align_up(tables_bytes(g), 256);
   pl->off_hdr = align_up(
       pl->off_lmax + sizeof(double) * (size_t)g->n_u0 * g->n_alpha, 256);
-  pl->off_pa = pl->off_hdr + 256;
+  pl->off_pub = pl->off_hdr + 256;
+  pl->off_pa = align_up(
+      pl->off_pub + (dense ? 0
+                           : sizeof(unsigned long long) * morse::kPubLevels *
+                                 (size_t)grid),
+      256);
   size_t list_bytes = dense ? 0 : sizeof(Entry) * (size_t)grid * K;
   pl->off_pb = align_up(pl->off_pa + list_bytes, 256);
   pl->off_out = align_up(pl->off_pb + list_bytes, 256);
@@ -688,12 +694,20 @@ morse_status enqueue_cut(morse_ctx *ctx, const morse_map *map,
   return MORSE_OK;
 }
 
+// A fresh tag for a search launch's published block quantiles (never 0,
+// the value of a cleared word).
+unsigned next_pub_tag(morse_ctx *ctx) {
+  if (++ctx->pub_tag == 0) ctx->pub_tag = 1;
+  return ctx->pub_tag;
+}
+
 // Queue the top-K search of one map: search kernel, merge tree, fit fill
 // into fits_dev[0..K).  No host synchronisation.
 morse_status enqueue_topk(morse_ctx *ctx, const Plan &pl,
                           morse::SearchParams P, char *base,
                           const Tables &T, morse_fit *fits_dev) {
   P.partial = (Entry *)(base + pl.off_pa);
+  P.pub = (unsigned long long *)(base + pl.off_pub);
   P.tab_n = pl.tab_n;
   P.tab_c = (unsigned)(P.half + 1) - 0x4B400000u;
   int r;
@@ -702,7 +716,8 @@ morse_status enqueue_topk(morse_ctx *ctx, const Plan &pl,
   const double want =
       std::max(morse::kPilotMinK * pl.K,
                morse::kPilotSqrt * std::sqrt((double)pl.K * P.count));
-  const long long stride = (long long)(P.count / want);
+  // (no pilot when the sample would be under one trajectory)
+  const long long stride = want >= 1.0 ? (long long)(P.count / want) : 0;
   if (P.gthr && stride >= 4) {
     morse::SearchParams Q = P;
     Q.stride = stride;
@@ -712,6 +727,8 @@ morse_status enqueue_topk(morse_ctx *ctx, const Plan &pl,
     int grid = (int)std::min<long long>(
         pl.grid, (groups + morse::kSearchWarps - 1) / morse::kSearchWarps);
     if (grid < 1) grid = 1;
+    Q.pub_tag = next_pub_tag(ctx);
+    Q.pub_nb = grid;
     r = t_begin(ctx, KT_SEARCH);
     MORSE_CUDA(ctx, morse::launch_search(Q, false, pl.ep_smem, grid, pl.smem,
                                          ctx->stream));
@@ -722,12 +739,12 @@ morse_status enqueue_topk(morse_ctx *ctx, const Plan &pl,
     MORSE_CUDA(ctx, morse::launch_topk_merge((Entry *)(base + pl.off_pa),
                                              (Entry *)(base + pl.off_pb), grid,
                                              pl.K, &sel, &levels,
-                                             ctx->stream));
-    MORSE_CUDA(ctx, morse::launch_seed_threshold(sel, pl.K, P.gthr,
-                                                 ctx->stream));
+                                             ctx->stream, P.gthr));
     t_end(ctx, r);
-    ctx->launches += 2 + (uint64_t)levels;
+    ctx->launches += 1 + (uint64_t)levels;
   }
+  P.pub_tag = next_pub_tag(ctx);
+  P.pub_nb = pl.grid;
   r = t_begin(ctx, KT_SEARCH);
   MORSE_CUDA(ctx, morse::launch_search(P, false, pl.ep_smem, pl.grid, pl.smem,
                                        ctx->stream));
@@ -1028,7 +1045,7 @@ morse_status batch_prepare(morse_ctx *ctx, const morse_event *const *evs,
   // pilot: a strided sample of ~sqrt(K N) trajectories per pair
   const double want = std::max(morse::kPilotMinK * K,
                                morse::kPilotSqrt * std::sqrt((double)K * N));
-  const long long stride = (long long)(N / want);
+  const long long stride = want >= 1.0 ? (long long)(N / want) : 0;
   H.pilot.clear();
   H.pilot_list0.clear();
   H.pilot_count = 0;

@@ -42,6 +42,7 @@ struct morse_ctx {
   int fault_lock_held;      // searches start with every block lock taken
   long long fault_alloc;    // > 0: the fault_alloc-th device allocation
                             // from now fails (then the count is spent)
+  unsigned pub_tag;         // tag of the last top-K search launch
 };
 
 struct morse_map {
@@ -195,6 +196,9 @@ struct Entry {
   long long idx;
 };
 
+// levels of published block quantiles (search_group.cuh: pub_update)
+constexpr int kPubLevels = 3;
+
 struct SearchParams {
   // map: the lookup reads quadh (FP16 log10 quads) when it is set, else
   // quad (FP32 A - 1 quads); both share qpitch and the index folding
@@ -250,6 +254,12 @@ struct SearchParams {
   unsigned long long *stat_exact;  // trajectories given the exact sweep
   unsigned spin_limit;      // block top-K lock: spins before giving up
   int lock0;                // initial lock word (1: held, an injected fault)
+  // Published block quantiles (nullptr: off): kPubLevels rows of pub_nb
+  // words (launch tag << 32 | FP32 bits of the block's j-th chi^2, rounded
+  // up), pub_nb = gridDim.x; words of another tag are ignored.
+  unsigned long long *pub;
+  unsigned pub_tag;
+  int pub_nb;
   // Shared-memory band tables of the line-aligned pass (k_search only;
   // 0 = off): entries per table, 4 band_stride(npix), two tables after the
   // lists.
@@ -305,10 +315,10 @@ constexpr int kTpgPilot = MORSE_TPG_PILOT;  // pilot: spread a small sample
                                             // over every SM
 // pilot sample: max(kPilotMinK K, kPilotSqrt sqrt(K N)) trajectories
 #ifndef MORSE_PILOT_SQRT
-#define MORSE_PILOT_SQRT 1.0
+#define MORSE_PILOT_SQRT 0.25
 #endif
 #ifndef MORSE_PILOT_MIN_K
-#define MORSE_PILOT_MIN_K 16.0
+#define MORSE_PILOT_MIN_K 4.0
 #endif
 constexpr double kPilotSqrt = MORSE_PILOT_SQRT, kPilotMinK = MORSE_PILOT_MIN_K;
 
@@ -339,9 +349,11 @@ int search_blocks_per_sm(bool dense, bool ep_smem, bool h16, size_t smem);
 cudaError_t launch_search(const SearchParams &P, bool dense, bool ep_smem,
                           int grid, size_t smem, cudaStream_t st);
 // Merge `lists` sorted lists of `k` entries (ping-pong between a and b) into
-// one; returns the buffer that holds the result.
+// one; returns the buffer that holds the result and the launches queued.
+// With `seed`, also seed *seed from the result as launch_seed_threshold.
 cudaError_t launch_topk_merge(Entry *a, Entry *b, int lists, int k,
-                              Entry **result, int *levels, cudaStream_t st);
+                              Entry **result, int *levels, cudaStream_t st,
+                              unsigned long long *seed = nullptr);
 cudaError_t launch_fill(const FillParams &F, cudaStream_t st);
 // gthr <- min(gthr, chi^2 bits of sel[k-1]) when that entry is real
 cudaError_t launch_seed_threshold(const Entry *sel, int k,

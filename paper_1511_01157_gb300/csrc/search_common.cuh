@@ -476,6 +476,45 @@ struct Acc2 {
 
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
+// The packed FP32 pair operations as PTX with explicit rounding modes.
+// Instructions with an explicit rounding mode are never fused with their
+// neighbours, so each pair operation rounds both halves exactly as the
+// scalar __fmul_rn / __fadd_rn / __fmaf_rn do.  (The compiler's own
+// __fmul2_rn and __fadd2_rn may be contracted into one fused multiply-add:
+// the single-lens term (u^2 + 2) rsqrt(...) - 1 of a pair was, so paired
+// sweeps rounded it once where single sweeps rounded it twice.)
+#define MORSE_PK2(OP, a, b)                                             \
+  asm("{\n\t.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\t"         \
+      "mov.b64 pb, {%4, %5};\n\t" OP " pd, pa, pb;\n\t"                  \
+      "mov.b64 {%0, %1}, pd;\n\t}"                                       \
+      : "=f"(d.x), "=f"(d.y)                                            \
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y))
+__device__ __forceinline__ float2 pk_add(float2 a, float2 b) {
+  float2 d;
+  MORSE_PK2("add.rn.f32x2", a, b);
+  return d;
+}
+__device__ __forceinline__ float2 pk_add_rd(float2 a, float2 b) {
+  float2 d;
+  MORSE_PK2("add.rm.f32x2", a, b);
+  return d;
+}
+__device__ __forceinline__ float2 pk_mul(float2 a, float2 b) {
+  float2 d;
+  MORSE_PK2("mul.rn.f32x2", a, b);
+  return d;
+}
+#undef MORSE_PK2
+__device__ __forceinline__ float2 pk_fma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 pa, pb, pc, pd;\n\tmov.b64 pa, {%2, %3};\n\t"
+      "mov.b64 pb, {%4, %5};\n\tmov.b64 pc, {%6, %7};\n\t"
+      "fma.rn.f32x2 pd, pa, pb, pc;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
 __device__ __forceinline__ TrajP pack_traj(const TrajC &a, const TrajC &b) {
   TrajP p;
   p.ax = make_float2(a.ax, b.ax);
@@ -494,39 +533,39 @@ template <bool H, int TB>
 __device__ __forceinline__ float2 mag2_in_m1(const SearchParams &P,
                                              const TrajP &c, const float2 tt,
                                              const float4 *tab) {
-  const float2 vx = __ffma2_rn(c.ax, tt, c.bx);
-  const float2 vy = __ffma2_rn(c.ay, tt, c.by);
+  const float2 vx = pk_fma(c.ax, tt, c.bx);
+  const float2 vy = pk_fma(c.ay, tt, c.by);
   if (TB == 0)
     return make_float2(
         H ? bilinear_h_m1(P, vx.x, vy.x) : bilinear_m1(P, vx.x, vy.x),
         H ? bilinear_h_m1(P, vx.y, vy.y) : bilinear_m1(P, vx.y, vy.y));
-  const float2 tx = __fadd2_rd(vx, f2(12582912.f));
-  const float2 ty = __fadd2_rd(vy, f2(12582912.f));
+  const float2 tx = pk_add_rd(vx, f2(12582912.f));
+  const float2 ty = pk_add_rd(vy, f2(12582912.f));
   // v - (t - 1.5 2^23): the subtraction as an FMA with -1 (exact product)
-  const float2 fx = __ffma2_rn(__fadd2_rn(tx, f2(-12582912.f)), f2(-1.f), vx);
-  const float2 fy = __ffma2_rn(__fadd2_rn(ty, f2(-12582912.f)), f2(-1.f), vy);
+  const float2 fx = pk_fma(pk_add(tx, f2(-12582912.f)), f2(-1.f), vx);
+  const float2 fy = pk_fma(pk_add(ty, f2(-12582912.f)), f2(-1.f), vy);
   const float2 a =
       make_float2(tab_cell_m1<TB, H>(P, tab, tx.x, ty.x, fx.x, fy.x, vx.x, vy.x),
                   tab_cell_m1<TB, H>(P, tab, tx.y, ty.y, fx.y, fy.y, vx.y, vy.y));
-  return H ? __fadd2_rn(a, f2(-1.f)) : a;
+  return H ? pk_add(a, f2(-1.f)) : a;
 }
 
 // A - 1 of both outside the map (single lens, as mag_out_m1)
 __device__ __forceinline__ float2 mag2_out_m1(const TrajP &c, const float2 tt) {
-  const float2 tau = __ffma2_rn(c.kt, tt, c.bt);
-  const float2 u2 = __ffma2_rn(tau, tau, c.u02);
-  const float2 r = __fmul2_rn(u2, __fadd2_rn(u2, f2(4.f)));
-  const float2 A = __fmul2_rn(__fadd2_rn(u2, f2(2.f)),
+  const float2 tau = pk_fma(c.kt, tt, c.bt);
+  const float2 u2 = pk_fma(tau, tau, c.u02);
+  const float2 r = pk_mul(u2, pk_add(u2, f2(4.f)));
+  const float2 A = pk_mul(pk_add(u2, f2(2.f)),
                               make_float2(rsqrt_approx(r.x), rsqrt_approx(r.y)));
-  return __fadd2_rn(A, f2(-1.f));
+  return pk_add(A, f2(-1.f));
 }
 
 __device__ __forceinline__ void acc2_add(Acc2 &s, float2 w, float2 wf,
                                          float2 Ac) {
-  const float2 wAc = __fmul2_rn(w, Ac);
-  s.a = __fadd2_rn(s.a, wAc);
-  s.b = __ffma2_rn(wAc, Ac, s.b);
-  s.d = __ffma2_rn(wf, Ac, s.d);
+  const float2 wAc = pk_mul(w, Ac);
+  s.a = pk_add(s.a, wAc);
+  s.b = pk_fma(wAc, Ac, s.b);
+  s.d = pk_fma(wf, Ac, s.d);
 }
 
 // two trajectories over one epoch segment, one epoch load for both

@@ -21,6 +21,52 @@ struct BlockTopK {
   volatile double *thr;
 };
 
+// Published block quantiles: the grid-wide threshold's second source.  A
+// block whose list holds j entries at or below v, with c - 1 other blocks
+// whose published j-th values are at most v, makes c j distinct
+// trajectories (blocks search disjoint sets) of chi^2 at most v; when
+// c j >= K, v bounds the K-th best and may lower the threshold.  Level q
+// (1..kPubLevels) publishes the ceil(K / 4^q)-th best and needs c >= 4^q;
+// the block's K-th (c = 1) lowers the threshold directly.  Early in a pass
+// each block has seen a small share of the grid, so its K-th is far above
+// the global K-th while its first few entries are not.
+__device__ __forceinline__ int pub_groups(int q) { return 1 << (2 * q); }
+
+// Warp-collective, outside the block lock: publish this block's level
+// values (lane q holds level q's, +inf if the list is shorter) and lower
+// the grid-wide threshold where enough blocks agree.
+static __device__ __noinline__ void pub_update(const SearchParams &P, double pv,
+                                        const int lane) {
+  const int nb = P.pub_nb;
+  unsigned fb[kPubLevels];
+#pragma unroll
+  for (int q = 1; q <= kPubLevels; ++q) {
+    const double v = __shfl_sync(kFull, pv, q);
+    const float f = __double2float_ru(v);
+    fb[q - 1] = (pub_groups(q) <= nb && f < CUDART_INF_F)
+                    ? __float_as_uint(f) : 0xFFFFFFFFu;
+    if (lane == 0 && fb[q - 1] != 0xFFFFFFFFu)
+      __stcg(&P.pub[(size_t)(q - 1) * nb + blockIdx.x],
+             ((unsigned long long)P.pub_tag << 32) | fb[q - 1]);
+  }
+  int c[kPubLevels] = {};
+  for (int b = lane; b < nb; b += 32) {
+    if (b == (int)blockIdx.x) continue;  // counted below
+#pragma unroll
+    for (int q = 0; q < kPubLevels; ++q) {
+      const unsigned long long w = __ldcg(&P.pub[(size_t)q * nb + b]);
+      c[q] += ((unsigned)(w >> 32) == P.pub_tag) && ((unsigned)w <= fb[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kPubLevels; ++q) {
+    const int n = __reduce_add_sync(kFull, (unsigned)c[q]) + 1;
+    if (lane == 0 && fb[q] != 0xFFFFFFFFu && n >= pub_groups(q + 1))
+      atomicMin(P.gthr, (unsigned long long)__double_as_longlong(
+                            (double)__uint_as_float(fb[q])));
+  }
+}
+
 // Warp-collective: merge this lane's candidate (if any) into the block's
 // sorted top-K under the block lock.  Candidates are first sorted across
 // the warp (bitonic); each existing entry and each candidate then moves to
@@ -101,6 +147,12 @@ __device__ inline void warp_merge(const SearchParams &P, BlockTopK &T, const int
     if (r < K) nxt[r] = e;
   }
   __syncwarp();
+  // the published levels' values, read while the lock is held
+  double pv = CUDART_INF;
+  if (P.pub && lane >= 1 && lane <= kPubLevels) {
+    const int j = (K + pub_groups(lane) - 1) / pub_groups(lane);
+    if (min(K, nk + nc) >= j) pv = nxt[j - 1].chi2;
+  }
   if (lane == 0) {
     const int nn = min(K, nk + nc);
     *T.nk = nn;
@@ -113,6 +165,7 @@ __device__ inline void warp_merge(const SearchParams &P, BlockTopK &T, const int
     atomicExch(T.lock, 0);
   }
   __syncwarp();
+  if (P.pub && P.gthr) pub_update(P, pv, lane);
 }
 
 // One warp group: trajectories [lo, hi) of the line-aligned pass (lined),
@@ -296,8 +349,9 @@ __device__ __forceinline__ void band_release(BandTabs &B, long long r,
 }
 
 // Record of one selected trajectory e (warp-collective; lane 0 writes *dst):
-// the phase-1 sums, the solve and the phase-2 chi^2 recomputed with the
-// search's device functions, on the epochs at P.ep (global memory).
+// (Fs, Fb) from the phase-1 sums and the solve, recomputed with the search's
+// device functions on the epochs at P.ep (global memory), so the same bits;
+// chi^2 is the search's own phase-2 value, the key e was ranked by.
 template <bool H>
 __device__ __forceinline__ void fill_one(const SearchParams &P, const Entry e,
                                          const double *t0abs,
@@ -320,8 +374,6 @@ __device__ __forceinline__ void fill_one(const SearchParams &P, const Entry e,
   const TrajC c = traj_consts(P, ep, e.idx);
   const Acc s = phase1<H>(P, ep, c, lane);
   const Solved sol = solve2(P, (double)s.a, (double)s.b, (double)s.d);
-  const double chi2 = phase2<H>(P, ep, c, lane, __double2float_rn(sol.Fs),
-                                __double2float_rn(sol.Bc));
   if (lane == 0) {
     long long q = e.idx;
     const int itE = (int)(q % P.n_tE);
@@ -330,7 +382,7 @@ __device__ __forceinline__ void fill_one(const SearchParams &P, const Entry e,
     q /= P.n_t0;
     const int ia = (int)(q % P.n_alpha);
     const int iu = (int)(q / P.n_alpha);
-    r.chi2 = isnan(chi2) ? CUDART_INF : chi2;
+    r.chi2 = e.chi2;
     r.tE = (P.lu && P.ltE) ? P.ltE[iu] : tEv[itE];
     if (P.lu) {  // line grid: the record in the (u0, alpha) convention
       r.t0 = t0abs[it0] - P.lsh[iu] * r.tE;

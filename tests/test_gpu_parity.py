@@ -224,6 +224,29 @@ def test_ragged_grids_and_k_beyond_size(ctx, m, dims, k):
     assert np.max(_rel(chi2, o_chi2)) <= CHI2_RTOL
 
 
+@pytest.mark.parametrize("k", [1, 5, 256, 640, 641, 2048, 4096])
+def test_topk_merge_equals_dense_order(ctx, m, k):
+    """The top-K of a 152-block search (merged 16 or 4 lists at a time in
+    shared memory, or in global memory when k > 3632) is, record for
+    record, the k smallest (chi^2, idx) of the dense chi^2 of the same
+    grid: the same phase-2 value, so bit for bit, and the fill's chi^2 is
+    that key."""
+    c = synth.CFG0
+    A_o, *_ = orc.build_map(0.9, 0.01, 2.0, 128, 900, 3.0, nthreads=NT)
+    mp = ctx.map_from_host(A_o, 2.0)
+    t, F, sig = _event(c, n=300, seed=5)
+    ev = ctx.event(t, F, sig)
+    g = m.Grid.make(20, 36, 13, 10, 0.01, 0.5, -2.0, 2.0, 5.0, 80.0, True,
+                    True, k)
+    got = ctx.grid_chi2(ev, mp, g)
+    chi2, fs, fb = ctx.grid_chi2_dense(ev, mp, g)
+    order = np.lexsort((np.arange(chi2.size), chi2))[:k]
+    np.testing.assert_array_equal(got["idx"], order)
+    np.testing.assert_array_equal(got["chi2"], chi2[order])
+    np.testing.assert_array_equal(got["Fs"], fs[order])
+    np.testing.assert_array_equal(got["Fb"], fb[order])
+
+
 def test_band_tables_equal_global_lookups(ctx, m):
     """A grid with 16 warp groups per line (20 t0 x 10 tE) reads its cells
     from the shared-memory band tables: dense chi^2 and top-K equal the
