@@ -476,13 +476,13 @@ struct Acc2 {
 
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
-// The packed FP32 pair operations as PTX with explicit rounding modes.
-// Instructions with an explicit rounding mode are never fused with their
-// neighbours, so each pair operation rounds both halves exactly as the
-// scalar __fmul_rn / __fadd_rn / __fmaf_rn do.  (The compiler's own
-// __fmul2_rn and __fadd2_rn may be contracted into one fused multiply-add:
-// the single-lens term (u^2 + 2) rsqrt(...) - 1 of a pair was, so paired
-// sweeps rounded it once where single sweeps rounded it twice.)
+// The packed FP32 pair operations (FADD2, FMUL2, FFMA2) as PTX with
+// explicit rounding modes; each rounds both halves as the scalar __fadd_rn,
+// __fmul_rn and __fmaf_rn do.  One exception was measured: a packed add of
+// a constant to a packed product (the "- 1" of the single-lens term) gave
+// other bits than the scalar sweep in the second half, so that step is
+// taken per half (mag2_out_m1); a GPU test checks that paired and single
+// sweeps agree bit for bit.
 #define MORSE_PK2(OP, a, b)                                             \
   asm("{\n\t.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\t"         \
       "mov.b64 pb, {%4, %5};\n\t" OP " pd, pa, pb;\n\t"                  \
@@ -547,7 +547,7 @@ __device__ __forceinline__ float2 mag2_in_m1(const SearchParams &P,
   const float2 a =
       make_float2(tab_cell_m1<TB, H>(P, tab, tx.x, ty.x, fx.x, fy.x, vx.x, vy.x),
                   tab_cell_m1<TB, H>(P, tab, tx.y, ty.y, fx.y, fy.y, vx.y, vy.y));
-  return H ? pk_add(a, f2(-1.f)) : a;
+  return H ? make_float2(__fsub_rn(a.x, 1.f), __fsub_rn(a.y, 1.f)) : a;
 }
 
 // A - 1 of both outside the map (single lens, as mag_out_m1)
@@ -557,7 +557,8 @@ __device__ __forceinline__ float2 mag2_out_m1(const TrajP &c, const float2 tt) {
   const float2 r = pk_mul(u2, pk_add(u2, f2(4.f)));
   const float2 A = pk_mul(pk_add(u2, f2(2.f)),
                               make_float2(rsqrt_approx(r.x), rsqrt_approx(r.y)));
-  return pk_add(A, f2(-1.f));
+  // A - 1 per half (not as a packed add: see pk_add)
+  return make_float2(__fsub_rn(A.x, 1.f), __fsub_rn(A.y, 1.f));
 }
 
 __device__ __forceinline__ void acc2_add(Acc2 &s, float2 w, float2 wf,

@@ -247,6 +247,36 @@ def test_topk_merge_equals_dense_order(ctx, m, k):
     np.testing.assert_array_equal(got["Fb"], fb[order])
 
 
+@pytest.mark.parametrize("case", ["outside", "inside", "mixed", "band"])
+def test_paired_and_single_sweeps_identical(ctx, m, case):
+    """The search sweeps trajectories two at a time in packed FP32 and the
+    fit fill one at a time; both must give the same bits (the records' Fs
+    and Fb come from the single sweep, their chi^2 from the paired one).
+    A trajectory searched alone (a range of one) is compared with the same
+    trajectory searched among its grid neighbours: tracks that never enter
+    the map, tracks inside it at every epoch, mixed, and a grid that reads
+    the cells from the shared-memory band tables."""
+    A_o, *_ = orc.build_map(0.9, 0.01, 2.0, 128, 900, 3.0, nthreads=NT)
+    mp = ctx.map_from_host(A_o, 2.0)
+    n = 2000 if case == "band" else 300
+    t = synth.epoch_times(n, 5, 0.0)
+    F, sig = synth.photometry(1.0 + 0.3 / np.sqrt(0.05 + (t / 20.0) ** 2), 5)
+    ev = ctx.event(t, F, sig)
+    g = {"outside": m.Grid.make(4, 8, 6, 10, 3.0, 3.5, -5.0, 5.0, 5.0, 80.0,
+                                False, True, 4),
+         "inside": m.Grid.make(4, 8, 6, 10, 0.01, 0.5, -5.0, 5.0, 4000.0,
+                               8000.0, True, True, 4),
+         "mixed": m.Grid.make(4, 8, 6, 10, 0.01, 0.5, -5.0, 5.0, 5.0, 80.0,
+                              True, True, 4),
+         "band": m.Grid.make(3, 8, 20, 10, 0.02, 0.6, -1.5, 1.5, 6.0, 50.0,
+                             True, True, 4)}[case]
+    chi2, fs, fb = ctx.grid_chi2_dense(ev, mp, g)
+    rng = np.random.default_rng(7)
+    for j in rng.choice(chi2.size, 120, replace=False):
+        c1, f1, b1 = ctx.grid_chi2_dense(ev, mp, g, int(j), 1)
+        assert (c1[0], f1[0], b1[0]) == (chi2[j], fs[j], fb[j]), (case, j)
+
+
 def test_band_tables_equal_global_lookups(ctx, m):
     """A grid with 16 warp groups per line (20 t0 x 10 tE) reads its cells
     from the shared-memory band tables: dense chi^2 and top-K equal the
