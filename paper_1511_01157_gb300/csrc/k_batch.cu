@@ -80,6 +80,12 @@ __device__ __forceinline__ void run_unit(const BatchParams &B,
   Q.tpg = U.tpg;
   Q.ng_line = (Q.line + U.tpg - 1) / U.tpg;
   Q.gthr = B.gthr + U.pair;
+  if (Q.pub) {  // the pair's lists' published quantiles
+    const int l0 = B.list0[U.pair];
+    Q.pub += l0;
+    Q.pub_nb = B.list0[U.pair + 1] - l0;
+    Q.pub_me = U.list - l0;
+  }
   const Epochs ep = epochs_at(STAGE ? sep : E.ep, E.n_ep);
   const bool lined = Q.stride == 1 && Q.line > 0;
   for (;;) {

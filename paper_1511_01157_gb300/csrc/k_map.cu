@@ -13,8 +13,9 @@
 // shared-memory window placed on the deflected tile, using shared-memory
 // atomics; rays that fall outside the window go straight to the global map
 // with red.global.add, and the window is flushed with one global add per
-// non-empty bin.  Threads own 8x16-ray sub-blocks so that the 32 lanes of a
-// warp sit 8 rays (~1.2 pixels) apart and rarely hit the same bin.
+// non-empty bin (four bins per 16-byte read).  Threads own 8x16-ray
+// sub-blocks so that the 32 lanes of a warp sit 8 rays (~1.2 pixels) apart
+// and rarely hit the same bin.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -25,10 +26,13 @@ namespace morse {
 
 namespace {
 
-constexpr int kSubX = 8;    // rays per thread sub-block along x
-constexpr int kSubY = 16;   // rays per thread sub-block along y
-static_assert(kRayThreads == (kRayTile / kSubX) * (kRayTile / kSubY),
+constexpr int kSubX = 8;    // rays per thread sub-block along x (the
+                            // rows along y, RayParams::sub_rows, are chosen
+                            // per launch)
+static_assert(kRayThreads == (kRayTileX / kSubX) * kRayWarps,
               "one sub-block per thread");
+static_assert(kSubX == 8 && kRayTileX / kSubX == 32,
+              "a warp is one row of sub-blocks across the tile");
 
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
@@ -139,7 +143,7 @@ __device__ __forceinline__ void bin_ray(const RayParams &P, uint32_t *win,
 }
 
 // The FP32 rays of one thread's sub-block: columns ib .. ib + na - 1
-// (FULL: na = kSubX), rows jb .. jb + kSubY - 1, two columns per packed
+// (FULL: na = kSubX), rows jb .. jb + P.sub_rows - 1, two columns per packed
 // FP32 instruction.  The deflection works in bin units: with x' = x/Delta +
 // L/Delta and e' = e/Delta (taken once per sub-block and per row), the
 // bin coordinates are
@@ -170,7 +174,7 @@ __device__ __forceinline__ void shoot_f32(const RayParams &P, uint32_t *win,
   const unsigned cx = 0x4B400000u + (unsigned)wx0;
   const unsigned cy = 0x4B400000u + (unsigned)wy0;
 #pragma unroll 1
-  for (int b = 0; b < kSubY; ++b) {
+  for (int b = 0; b < P.sub_rows; ++b) {
     const long long j = jb + b;
     if (j >= P.nray) break;
     const float x2 = fmaf((float)j, P.hf, P.x0f);
@@ -189,9 +193,24 @@ __device__ __forceinline__ void shoot_f32(const RayParams &P, uint32_t *win,
       const float2 v2 = __ffma2_rn(__fadd2_rn(a1, a2), x2p, x2s);
       const float2 tx = __fadd2_rd(v1, M);
       const float2 ty = __fadd2_rd(v2, M);
-      bin_ray(P, win, cx, cy, W, tx.x, ty.x, rr.x == 0.0f, n_off, n_lost);
-      if (FULL || 2 * p + 1 < na)
+      if (FULL || 2 * p + 1 < na) {
+        // both rays in the window (the common case): one test for the
+        // pair; a lost ray (rr = 0) has an infinite or NaN bin sum and
+        // fails it
+        const unsigned lx0 = (unsigned)__float_as_int(tx.x) - cx;
+        const unsigned ly0 = (unsigned)__float_as_int(ty.x) - cy;
+        const unsigned lx1 = (unsigned)__float_as_int(tx.y) - cx;
+        const unsigned ly1 = (unsigned)__float_as_int(ty.y) - cy;
+        if (max(max(lx0, ly0), max(lx1, ly1)) < W) {
+          atomicAdd(&win[ly0 * kRayWin + lx0], 1u);
+          atomicAdd(&win[ly1 * kRayWin + lx1], 1u);
+          continue;
+        }
+        bin_ray(P, win, cx, cy, W, tx.x, ty.x, rr.x == 0.0f, n_off, n_lost);
         bin_ray(P, win, cx, cy, W, tx.y, ty.y, rr.y == 0.0f, n_off, n_lost);
+      } else {
+        bin_ray(P, win, cx, cy, W, tx.x, ty.x, rr.x == 0.0f, n_off, n_lost);
+      }
     }
   }
 }
@@ -201,26 +220,33 @@ __device__ __forceinline__ void shoot_f32(const RayParams &P, uint32_t *win,
 template <bool FP64>
 __global__ void __launch_bounds__(kRayThreads, FP64 ? 1 : 2)
     k_rayshoot(const RayParams P) {
-  extern __shared__ uint32_t win[];  // kRayWin * kRayWin bins
-  __shared__ int s_wx, s_wy;
+  extern __shared__ __align__(16) uint32_t win[];  // kRayWin^2 bins
+  __shared__ int s_wx, s_wy, s_tile;
   const int tid = threadIdx.x;
-  for (int k = tid; k < kRayWin * kRayWin; k += kRayThreads) win[k] = 0u;
+  uint4 *win4 = reinterpret_cast<uint4 *>(win);
+  for (int k = tid; k < kRayWin * kRayWin / 4; k += kRayThreads)
+    win4[k] = make_uint4(0u, 0u, 0u, 0u);
   unsigned int n_off = 0, n_lost = 0;
   const int ntiles = P.tiles_x * P.tiles_y;
   const int sx = tid & 31;   // sub-block column (lane)
   const int sy = tid >> 5;   // sub-block row (warp)
 
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long i0 = (long long)(tile % P.tiles_x) * kRayTile;
-    const long long j0 = (long long)(tile / P.tiles_x) * kRayTile;
+  const long long tile_h = (long long)kRayWarps * P.sub_rows;
+  for (;;) {
+    // tiles from a counter: blocks whose tiles were cheap take more
+    if (tid == 0) s_tile = (int)atomicAdd(&P.tot[2], 1ULL);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= ntiles) break;  // block-uniform
+    const long long i0 = (long long)(tile % P.tiles_x) * kRayTileX;
+    const long long j0 = (long long)(tile / P.tiles_x) * tile_h;
     if (tid < 32) {
       // place the window on the bounding box of 9 deflected sample rays
       int bx = 0, by = 0;
       bool ok = false;
       if (tid < 9) {
-        long long span = kRayTile - 1;
-        long long ii = i0 + (tid % 3) * span / 2;
-        long long jj = j0 + (tid / 3) * span / 2;
+        long long ii = i0 + (tid % 3) * (long long)(kRayTileX - 1) / 2;
+        long long jj = j0 + (tid / 3) * (tile_h - 1) / 2;
         if (ii >= P.nray) ii = P.nray - 1;
         if (jj >= P.nray) jj = P.nray - 1;
         ok = sample_bin(P, ii, jj, &bx, &by);
@@ -246,7 +272,7 @@ __global__ void __launch_bounds__(kRayThreads, FP64 ? 1 : 2)
     __syncthreads();
     const int wx0 = s_wx, wy0 = s_wy;
     const long long ib = i0 + sx * kSubX;
-    const long long jb = j0 + sy * kSubY;
+    const long long jb = j0 + sy * P.sub_rows;
     // rays of the sub-block row inside the grid, and the first one's x1
     const int na = (int)max(0LL, min((long long)kSubX, P.nray - ib));
     const float x1b = fmaf((float)ib, P.hf, P.x0f);
@@ -257,7 +283,7 @@ __global__ void __launch_bounds__(kRayThreads, FP64 ? 1 : 2)
         shoot_f32<false>(P, win, wx0, wy0, jb, na, x1b, n_off, n_lost);
     } else {
 #pragma unroll 1
-      for (int b = 0; b < kSubY; ++b) {
+      for (int b = 0; b < P.sub_rows; ++b) {
         const long long j = jb + b;
         if (j >= P.nray) break;
         const double x2d = __dadd_rn(-P.X, __dmul_rn(__dadd_rn((double)j, 0.5), P.h));
@@ -283,14 +309,20 @@ __global__ void __launch_bounds__(kRayThreads, FP64 ? 1 : 2)
       }
     }
     __syncthreads();
-    // flush the window: one global add per non-empty bin, then clear
-    for (int k = tid; k < kRayWin * kRayWin; k += kRayThreads) {
-      uint32_t v = win[k];
-      if (v) {
-        win[k] = 0u;
-        int gx = wx0 + (k % kRayWin), gy = wy0 + (k / kRayWin);
-        atomicAdd(&P.counts[(size_t)gy * P.npix + gx], v);
-      }
+    // flush the window: four bins per read, one global add per non-empty
+    // bin, then clear (a bin beyond a map narrower than the window is
+    // never counted, so it is zero and skipped)
+    for (int k4 = tid; k4 < kRayWin * kRayWin / 4; k4 += kRayThreads) {
+      const uint4 v = win4[k4];
+      if ((v.x | v.y | v.z | v.w) == 0u) continue;
+      win4[k4] = make_uint4(0u, 0u, 0u, 0u);
+      const int k = 4 * k4;
+      const int gx = wx0 + (k % kRayWin), gy = wy0 + (k / kRayWin);
+      uint32_t *dst = &P.counts[(size_t)gy * P.npix + gx];
+      if (v.x) atomicAdd(dst, v.x);
+      if (v.y) atomicAdd(dst + 1, v.y);
+      if (v.z) atomicAdd(dst + 2, v.z);
+      if (v.w) atomicAdd(dst + 3, v.w);
     }
     __syncthreads();
   }

@@ -221,7 +221,7 @@ morse_map *map_alloc(morse_ctx *ctx, int npix, bool counts) {
                        morse::quad_count(npix) * sizeof(float4)) ==
           cudaSuccess &&
       morse::dev_alloc(ctx, (void **)&m->tot,
-                       2 * sizeof(unsigned long long)) == cudaSuccess;
+                       4 * sizeof(unsigned long long)) == cudaSuccess;
   if (ok && counts)
     ok = morse::dev_alloc(ctx, (void **)&m->counts,
                           n * sizeof(uint32_t)) == cudaSuccess;
@@ -334,18 +334,41 @@ morse_status enqueue_build(morse_ctx *ctx, morse_map *m, const BuildSpec &b) {
   P.npixf = (float)b.npix;
   P.npix = b.npix;
   P.nray = b.nray;
-  P.tiles_x = (int)((b.nray + morse::kRayTile - 1) / morse::kRayTile);
-  P.tiles_y = P.tiles_x;
+  P.tiles_x = (int)((b.nray + morse::kRayTileX - 1) / morse::kRayTileX);
+  // Tile height: the persistent blocks take tiles from a counter, and a
+  // last round with few tiles leaves SMs idle, so pick the sub-block rows r
+  // (tile height 16 r) that minimise rounds x (tile rays + a per-tile cost
+  // of about 2000 rays: window placement, flush, barriers).
+  const long long blocks =
+      (long long)morse::rayshoot_blocks_per_sm() * ctx->sm_count;
+  {
+    double best = 0.0;
+    P.sub_rows = morse::kRaySubRowsMax;
+    for (int r = morse::kRaySubRowsMax; r >= morse::kRaySubRowsMax * 5 / 8;
+         --r) {
+      const long long th = (long long)morse::kRayWarps * r;
+      const long long tiles =
+          (long long)P.tiles_x * ((b.nray + th - 1) / th);
+      const long long rounds = (tiles + blocks - 1) / blocks;
+      const double cost =
+          (double)rounds * ((double)morse::kRayTileX * th + 2000.0);
+      if (best == 0.0 || cost < best * 0.995) {
+        best = cost;
+        P.sub_rows = r;
+      }
+    }
+  }
+  const long long th = (long long)morse::kRayWarps * P.sub_rows;
+  P.tiles_y = (int)((b.nray + th - 1) / th);
   P.counts = m->counts;
   P.tot = m->tot;
   size_t n = (size_t)b.npix * b.npix;
   MORSE_CUDA(ctx, cudaMemsetAsync(m->counts, 0, n * sizeof(uint32_t),
                                   ctx->stream));
-  MORSE_CUDA(ctx, cudaMemsetAsync(m->tot, 0, 2 * sizeof(unsigned long long),
+  MORSE_CUDA(ctx, cudaMemsetAsync(m->tot, 0, 3 * sizeof(unsigned long long),
                                   ctx->stream));
   long long tiles = (long long)P.tiles_x * P.tiles_y;
-  int grid = (int)std::min<long long>(
-      tiles, (long long)morse::rayshoot_blocks_per_sm() * ctx->sm_count);
+  int grid = (int)std::min<long long>(tiles, blocks);
   int r = t_begin(ctx, KT_RAY);
   MORSE_CUDA(ctx, morse::launch_rayshoot(P, b.fp64, grid, ctx->stream));
   t_end(ctx, r);
@@ -729,6 +752,8 @@ morse_status enqueue_topk(morse_ctx *ctx, const Plan &pl,
     if (grid < 1) grid = 1;
     Q.pub_tag = next_pub_tag(ctx);
     Q.pub_nb = grid;
+    Q.pub_me = -1;
+    Q.pub_stride = grid;
     r = t_begin(ctx, KT_SEARCH);
     MORSE_CUDA(ctx, morse::launch_search(Q, false, pl.ep_smem, grid, pl.smem,
                                          ctx->stream));
@@ -745,6 +770,8 @@ morse_status enqueue_topk(morse_ctx *ctx, const Plan &pl,
   }
   P.pub_tag = next_pub_tag(ctx);
   P.pub_nb = pl.grid;
+  P.pub_me = -1;
+  P.pub_stride = pl.grid;
   r = t_begin(ctx, KT_SEARCH);
   MORSE_CUDA(ctx, morse::launch_search(P, false, pl.ep_smem, pl.grid, pl.smem,
                                        ctx->stream));
@@ -947,7 +974,8 @@ void batch_tables(const morse_grid *g, const morse_event *const *evs, int n_ev,
 // Device layout of a batch call.
 struct BatchLayout {
   size_t off_tab, off_ev, off_ptr, off_up, off_um, off_lp, off_lm, off_gthr,
-      off_hdr, off_pa, off_pb, off_res, off_fit, bytes;
+      off_hdr, off_pub, off_pa, off_pb, off_res, off_fit, bytes;
+  size_t lists;  // top-K lists of the larger pass
 };
 
 struct BatchHdr {
@@ -976,6 +1004,8 @@ BatchLayout batch_layout(const BatchHost &H, int pairs, int K) {
   L.off_hdr = take(sizeof(BatchHdr));
   const size_t lists = (size_t)std::max(
       H.pilot_list0.empty() ? 0 : H.pilot_list0.back(), H.main_list0.back());
+  L.lists = lists;
+  L.off_pub = take(sizeof(unsigned long long) * morse::kPubLevels * lists);
   L.off_pa = take(sizeof(Entry) * lists * (size_t)K);
   L.off_pb = take(sizeof(Entry) * lists * (size_t)K);
   L.off_res = take(sizeof(Entry) * (size_t)pairs * K);
@@ -1043,8 +1073,8 @@ morse_status batch_prepare(morse_ctx *ctx, const morse_event *const *evs,
   for (int p = 0; p < pairs; ++p)
     shape_pair[(size_t)p] = shape_fit[(size_t)(p / n_maps)];
   // pilot: a strided sample of ~sqrt(K N) trajectories per pair
-  const double want = std::max(morse::kPilotMinK * K,
-                               morse::kPilotSqrt * std::sqrt((double)K * N));
+  const double want = std::max(morse::kBatchPilotMinK * K,
+                               morse::kBatchPilotSqrt * std::sqrt((double)K * N));
   const long long stride = want >= 1.0 ? (long long)(N / want) : 0;
   H.pilot.clear();
   H.pilot_list0.clear();
@@ -1136,7 +1166,15 @@ morse_status batch_upload(morse_ctx *ctx, BatchHost &H, const BatchLayout &L,
   B.gthr = (unsigned long long *)(base + L.off_gthr);
   B.partial = (Entry *)(base + L.off_pa);
   B.ep_cap = H.ep_cap;
+  // published list quantiles: rows of the larger pass's list count, cleared
+  // by every call (a graph replay reuses the tags); tags 1 and 2
+  B.S.pub = MORSE_BATCH_PUB ? (unsigned long long *)(base + L.off_pub)
+                            : nullptr;
+  B.S.pub_stride = (int)L.lists;
+  B.n_lists = (int)L.lists;
   *Bp = B;
+  Bp->S.pub_tag = 1;
+  Bp->list0 = (const int *)(base + L.off_lp);
   Bp->S.count = H.pilot_count;
   Bp->S.stride = H.pilot_stride;
   Bp->S.line = 0;
@@ -1144,6 +1182,8 @@ morse_status batch_upload(morse_ctx *ctx, BatchHost &H, const BatchLayout &L,
   Bp->n_units = (int)H.pilot.size();
   Bp->counter = &hd->counter[0];
   *Bm = B;
+  Bm->S.pub_tag = 2;
+  Bm->list0 = (const int *)(base + L.off_lm);
   Bm->S.count = grid_size(g);
   Bm->S.stride = 1;
   Bm->S.line = (long long)g->n_t0 * g->n_tE;
@@ -1168,6 +1208,10 @@ morse_status batch_enqueue(morse_ctx *ctx, const BatchLayout &L, char *base,
                                   ctx->stream));
   MORSE_CUDA(ctx, cudaMemsetAsync(base + L.off_hdr, 0, sizeof(BatchHdr),
                                   ctx->stream));
+  MORSE_CUDA(ctx, cudaMemsetAsync(
+                      base + L.off_pub, 0,
+                      sizeof(unsigned long long) * morse::kPubLevels * L.lists,
+                      ctx->stream));
   Entry *pa = (Entry *)(base + L.off_pa), *pb = (Entry *)(base + L.off_pb);
   Entry *res = (Entry *)(base + L.off_res);
   int r;
@@ -1311,6 +1355,9 @@ morse_status batch_tune(morse_ctx *ctx, const morse_event *ev,
       cudaMemsetAsync(base + L.off_gthr, 0xFF, sizeof(unsigned long long),
                       ctx->stream);
       cudaMemsetAsync(base + L.off_hdr, 0, sizeof(BatchHdr), ctx->stream);
+      cudaMemsetAsync(base + L.off_pub, 0,
+                      sizeof(unsigned long long) * morse::kPubLevels * L.lists,
+                      ctx->stream);
       if (Bp.n_units > 0) {
         morse::launch_batch(Bp, h16, std::min(grid, Bp.n_units), smem,
                             ctx->stream);

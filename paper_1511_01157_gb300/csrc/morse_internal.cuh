@@ -102,11 +102,18 @@ struct RayParams {
   int npix;
   int64_t nray;
   int tiles_x, tiles_y;
+  int sub_rows;             // rays per thread sub-block along y (tile
+                            // height kRayWarps * sub_rows)
   uint32_t *counts;
-  unsigned long long *tot;
+  unsigned long long *tot;  // [0] off-map rays, [1] lost rays, [2] next
+                            // tile (all zero before the launch)
 };
 
-constexpr int kRayTile = 256;     // rays per tile side
+constexpr int kRayTileX = 256;    // rays per tile along x
+constexpr int kRayWarps = 16;     // sub-block rows per tile (warps per block)
+constexpr int kRaySubRowsMax = 16;  // tile height at most 256 rays (512:
+                                    // 10 % slower, more rays land outside
+                                    // the window)
 constexpr int kRayWin = 128;      // shared-memory window side (bins)
 constexpr int kRayThreads = 512;  // threads per ray-shooting block
 
@@ -254,12 +261,13 @@ struct SearchParams {
   unsigned long long *stat_exact;  // trajectories given the exact sweep
   unsigned spin_limit;      // block top-K lock: spins before giving up
   int lock0;                // initial lock word (1: held, an injected fault)
-  // Published block quantiles (nullptr: off): kPubLevels rows of pub_nb
-  // words (launch tag << 32 | FP32 bits of the block's j-th chi^2, rounded
-  // up), pub_nb = gridDim.x; words of another tag are ignored.
+  // Published block quantiles (nullptr: off): kPubLevels rows, pub_stride
+  // words apart, of pub_nb words (launch tag << 32 | FP32 bits of a list's
+  // j-th chi^2, rounded up), one per top-K list of the search; this list's
+  // word is pub_me (-1: blockIdx.x).  Words of another tag are ignored.
   unsigned long long *pub;
   unsigned pub_tag;
-  int pub_nb;
+  int pub_nb, pub_me, pub_stride;
   // Shared-memory band tables of the line-aligned pass (k_search only;
   // 0 = off): entries per table, 4 band_stride(npix), two tables after the
   // lists.
@@ -321,6 +329,19 @@ constexpr int kTpgPilot = MORSE_TPG_PILOT;  // pilot: spread a small sample
 #define MORSE_PILOT_MIN_K 4.0
 #endif
 constexpr double kPilotSqrt = MORSE_PILOT_SQRT, kPilotMinK = MORSE_PILOT_MIN_K;
+// the batched search's pilot (its own launch shapes and merge)
+#ifndef MORSE_BATCH_PILOT_SQRT
+#define MORSE_BATCH_PILOT_SQRT 1.0
+#endif
+#ifndef MORSE_BATCH_PILOT_MIN_K
+#define MORSE_BATCH_PILOT_MIN_K 16.0
+#endif
+constexpr double kBatchPilotSqrt = MORSE_BATCH_PILOT_SQRT,
+                 kBatchPilotMinK = MORSE_BATCH_PILOT_MIN_K;
+// published list quantiles in the batched search (1: on)
+#ifndef MORSE_BATCH_PUB
+#define MORSE_BATCH_PUB 1
+#endif
 
 // Line-aligned warp groups for the main pass: about one line per block
 // round (line = n_t0 n_tE trajectories share a track's line).
@@ -433,6 +454,9 @@ struct BatchParams {
   int n_units;
   unsigned *counter;        // next unit (zero before the launch)
   unsigned long long *gthr; // [pairs] pruning thresholds (chi^2 bits)
+  const int *list0;         // [pairs + 1] first list of each pair (this
+                            // pass); S.pub: kPubLevels rows of n_lists
+  int n_lists;
   Entry *partial;           // [lists][top_k]
   int ep_cap;               // staged-epoch capacity of shared memory
 };

@@ -22,9 +22,9 @@ struct BlockTopK {
 };
 
 // Published block quantiles: the grid-wide threshold's second source.  A
-// block whose list holds j entries at or below v, with c - 1 other blocks
+// block whose list holds j entries at or below v, with c - 1 other lists
 // whose published j-th values are at most v, makes c j distinct
-// trajectories (blocks search disjoint sets) of chi^2 at most v; when
+// trajectories (lists hold disjoint sets) of chi^2 at most v; when
 // c j >= K, v bounds the K-th best and may lower the threshold.  Level q
 // (1..kPubLevels) publishes the ceil(K / 4^q)-th best and needs c >= 4^q;
 // the block's K-th (c = 1) lowers the threshold directly.  Early in a pass
@@ -38,6 +38,8 @@ __device__ __forceinline__ int pub_groups(int q) { return 1 << (2 * q); }
 static __device__ __noinline__ void pub_update(const SearchParams &P, double pv,
                                         const int lane) {
   const int nb = P.pub_nb;
+  const int me = P.pub_me >= 0 ? P.pub_me : (int)blockIdx.x;
+  const size_t row = (size_t)P.pub_stride;
   unsigned fb[kPubLevels];
 #pragma unroll
   for (int q = 1; q <= kPubLevels; ++q) {
@@ -46,15 +48,15 @@ static __device__ __noinline__ void pub_update(const SearchParams &P, double pv,
     fb[q - 1] = (pub_groups(q) <= nb && f < CUDART_INF_F)
                     ? __float_as_uint(f) : 0xFFFFFFFFu;
     if (lane == 0 && fb[q - 1] != 0xFFFFFFFFu)
-      __stcg(&P.pub[(size_t)(q - 1) * nb + blockIdx.x],
+      __stcg(&P.pub[(size_t)(q - 1) * row + me],
              ((unsigned long long)P.pub_tag << 32) | fb[q - 1]);
   }
   int c[kPubLevels] = {};
   for (int b = lane; b < nb; b += 32) {
-    if (b == (int)blockIdx.x) continue;  // counted below
+    if (b == me) continue;  // counted below
 #pragma unroll
     for (int q = 0; q < kPubLevels; ++q) {
-      const unsigned long long w = __ldcg(&P.pub[(size_t)q * nb + b]);
+      const unsigned long long w = __ldcg(&P.pub[(size_t)q * row + b]);
       c[q] += ((unsigned)(w >> 32) == P.pub_tag) && ((unsigned)w <= fb[q]);
     }
   }
