@@ -49,6 +49,9 @@
 #ifndef MORSE_UNROLL
 #define MORSE_UNROLL 4
 #endif
+#ifndef MORSE_PK_ASM
+#define MORSE_PK_ASM 1  // packed pair operations as inline PTX (faster here)
+#endif
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>

@@ -476,13 +476,19 @@ struct Acc2 {
 
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
-// The packed FP32 pair operations (FADD2, FMUL2, FFMA2) as PTX with
-// explicit rounding modes; each rounds both halves as the scalar __fadd_rn,
-// __fmul_rn and __fmaf_rn do.  One exception was measured: a packed add of
-// a constant to a packed product (the "- 1" of the single-lens term) gave
-// other bits than the scalar sweep in the second half, so that step is
-// taken per half (mag2_out_m1); a GPU test checks that paired and single
-// sweeps agree bit for bit.
+// The packed FP32 pair operations (FADD2, FMUL2, FFMA2); each rounds both
+// halves as the scalar __fadd_rn, __fmul_rn and __fmaf_rn do.  A
+// translation unit that defines MORSE_PK_ASM 1 gets them as inline PTX
+// with explicit rounding modes (k_search: 0.8 % faster; k_batch: 8 %
+// slower), else as the compiler's __fadd2_rn etc.  One step was measured to
+// break the equality in both forms: a packed add of the constant -1 to the
+// packed single-lens product gave other bits than the scalar sweep in the
+// second half, so that step is taken per half (mag2_out_m1); GPU tests
+// check that paired and single sweeps agree bit for bit.
+#ifndef MORSE_PK_ASM
+#define MORSE_PK_ASM 0
+#endif
+#if MORSE_PK_ASM
 #define MORSE_PK2(OP, a, b)                                             \
   asm("{\n\t.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\t"         \
       "mov.b64 pb, {%4, %5};\n\t" OP " pd, pa, pb;\n\t"                  \
@@ -514,6 +520,20 @@ __device__ __forceinline__ float2 pk_fma(float2 a, float2 b, float2 c) {
       : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
   return d;
 }
+#else
+__device__ __forceinline__ float2 pk_add(float2 a, float2 b) {
+  return __fadd2_rn(a, b);
+}
+__device__ __forceinline__ float2 pk_add_rd(float2 a, float2 b) {
+  return __fadd2_rd(a, b);
+}
+__device__ __forceinline__ float2 pk_mul(float2 a, float2 b) {
+  return __fmul2_rn(a, b);
+}
+__device__ __forceinline__ float2 pk_fma(float2 a, float2 b, float2 c) {
+  return __ffma2_rn(a, b, c);
+}
+#endif
 
 __device__ __forceinline__ TrajP pack_traj(const TrajC &a, const TrajC &b) {
   TrajP p;
@@ -557,7 +577,7 @@ __device__ __forceinline__ float2 mag2_out_m1(const TrajP &c, const float2 tt) {
   const float2 r = pk_mul(u2, pk_add(u2, f2(4.f)));
   const float2 A = pk_mul(pk_add(u2, f2(2.f)),
                               make_float2(rsqrt_approx(r.x), rsqrt_approx(r.y)));
-  // A - 1 per half (not as a packed add: see pk_add)
+  // A - 1 per half (not as a packed add: see the pk_ operations)
   return make_float2(__fsub_rn(A.x, 1.f), __fsub_rn(A.y, 1.f));
 }
 
