@@ -163,9 +163,9 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
       Entry en;
       if (i < nk) {
         en = cur[i];
-      } else {  // unique sentinel keys sort after real ones
+      } else {  // unique sentinel keys after the real ones, ascending
         en.chi2 = CUDART_INF;
-        en.idx = 0x7fffffffffffffffLL - ((long long)U.list * K + i);
+        en.idx = 0x7fff000000000000LL + ((long long)U.list * K + i);
       }
       out[i] = en;
     }

@@ -212,8 +212,8 @@ __global__ void __launch_bounds__(kSearchWarps * 32, 1)
       if (i < nk) {
         e = cur[i];
       } else {
-        e.chi2 = CUDART_INF;  // unique sentinel keys sort after real ones
-        e.idx = 0x7fffffffffffffffLL - ((long long)blockIdx.x * K + i);
+        e.chi2 = CUDART_INF;  // unique sentinel keys, ascending
+        e.idx = 0x7fff000000000000LL + ((long long)blockIdx.x * K + i);
       }
       out[i] = e;
     }
@@ -260,35 +260,60 @@ __global__ void k_merge_level(const Entry *__restrict__ in,
 // its own list's entries against the others and writes those of rank < k
 // to the group's output list.  With `seed` on the last level, the entry of
 // final rank k - 1 lowers *seed to its chi^2 (as k_seed_threshold).
-__device__ __forceinline__ int lower_rank(const Entry *B, int k,
-                                          const Entry &e) {
+// Rank of key (kb, id) in a sorted list of k keys: the entries of smaller
+// chi^2 (bit patterns of non-negative doubles order as integers), plus
+// those of equal chi^2 and smaller index.
+__device__ __forceinline__ int lower_rank(const unsigned long long *K,
+                                          const long long *I, int k,
+                                          unsigned long long kb,
+                                          long long id) {
   int lo = 0, hi = k;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (key_less(B[mid], e))
+    if (K[mid] < kb)
       lo = mid + 1;
     else
       hi = mid;
+  }
+  if (lo < k && K[lo] == kb) {  // a tie in chi^2 (rare but for sentinels)
+    int e = lo + 1, top = k;
+    while (e < top) {  // end of the tie run
+      const int mid = (e + top) >> 1;
+      if (K[mid] == kb)
+        e = mid + 1;
+      else
+        top = mid;
+    }
+    hi = e;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (I[mid] < id)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
   }
   return lo;
 }
 
 // S = ways / 4 consecutive threads rank one entry, each against a quarter
-// of the group's other lists; their counts are summed by shuffles.
+// of the group's other lists; their counts are summed by shuffles.  The
+// lists are staged as separate key and index arrays, so a step of the
+// binary search reads 8 bytes.
 __global__ void __launch_bounds__(1024)
     k_merge_rank(const Entry *__restrict__ in, Entry *__restrict__ out,
                  int lists, int k, int ways, unsigned long long *seed) {
   extern __shared__ __align__(16) unsigned char msm[];
-  Entry *grp = reinterpret_cast<Entry *>(msm);
   const int l = blockIdx.x;
   const int g = l / ways, l0 = g * ways;
   const int n = min(ways, lists - l0);
+  unsigned long long *ky = reinterpret_cast<unsigned long long *>(msm);
+  long long *id = reinterpret_cast<long long *>(ky + (size_t)n * k);
   {
     // the group's lists, four independent 16-byte loads per thread in
     // flight (the copy is bound by L2 latency otherwise)
     const float4 *src = reinterpret_cast<const float4 *>(in + (size_t)l0 * k);
-    float4 *dst = reinterpret_cast<float4 *>(grp);
-    const int nv = n * k * (int)(sizeof(Entry) / sizeof(float4));
+    const int nv = n * k;
     const int st = blockDim.x;
     for (int i0 = threadIdx.x; i0 < nv; i0 += 4 * st) {
       float4 v[4];
@@ -297,7 +322,11 @@ __global__ void __launch_bounds__(1024)
         if (i0 + u * st < nv) v[u] = __ldcg(src + i0 + u * st);
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (i0 + u * st < nv) dst[i0 + u * st] = v[u];
+        if (i0 + u * st < nv) {
+          const double2 d = *reinterpret_cast<const double2 *>(&v[u]);
+          ky[i0 + u * st] = (unsigned long long)__double_as_longlong(d.x);
+          id[i0 + u * st] = __double_as_longlong(d.y);
+        }
     }
   }
   __syncthreads();
@@ -308,22 +337,26 @@ __global__ void __launch_bounds__(1024)
   for (int i0 = 0; i0 < k; i0 += per) {  // block-uniform trip count
     const int i = i0 + (int)threadIdx.x / S;
     const bool has = i < k;
-    Entry e;
-    e.chi2 = 0.0;
-    e.idx = 0;
+    unsigned long long kb = 0;
+    long long ie = 0;
     int r = 0;
     if (has) {
-      e = grp[(size_t)me * k + i];
+      kb = ky[(size_t)me * k + i];
+      ie = id[(size_t)me * k + i];
       for (int m = part; m < n; m += S)
-        if (m != me) r += lower_rank(grp + (size_t)m * k, k, e);
+        if (m != me)
+          r += lower_rank(ky + (size_t)m * k, id + (size_t)m * k, k, kb, ie);
     }
     for (int o = 1; o < S; o <<= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
     r += i;
     if (has && part == 0 && r < k) {
+      Entry e;
+      e.chi2 = __longlong_as_double((long long)kb);
+      e.idx = ie;
       out[(size_t)g * k + r] = e;
       if (seed && r == k - 1 && e.chi2 < CUDART_INF && e.idx >= 0 &&
           e.idx < 0x7fff000000000000LL)
-        atomicMin(seed, (unsigned long long)__double_as_longlong(e.chi2));
+        atomicMin(seed, kb);
     }
   }
 }
