@@ -215,58 +215,13 @@ __device__ __forceinline__ void shoot_f32(const RayParams &P, uint32_t *win,
   }
 }
 
-// Warp-collective (one warp): take the next tile from the counter and
-// place its window on the bounding box of 9 deflected sample rays; lane 0
-// writes the tile and the window's corner.
-__device__ __forceinline__ void next_tile(const RayParams &P, int ntiles,
-                                          long long tile_h, int lane,
-                                          int *tile_out, int *wx_out,
-                                          int *wy_out) {
-  int tile = 0;
-  if (lane == 0) tile = (int)atomicAdd(&P.tot[2], 1ULL);
-  tile = __shfl_sync(0xffffffffu, tile, 0);
-  if (tile >= ntiles) {
-    if (lane == 0) *tile_out = tile;
-    return;
-  }
-  const long long i0 = (long long)(tile % P.tiles_x) * kRayTileX;
-  const long long j0 = (long long)(tile / P.tiles_x) * tile_h;
-  int bx = 0, by = 0;
-  bool ok = false;
-  if (lane < 9) {
-    long long ii = i0 + (lane % 3) * (long long)(kRayTileX - 1) / 2;
-    long long jj = j0 + (lane / 3) * (tile_h - 1) / 2;
-    if (ii >= P.nray) ii = P.nray - 1;
-    if (jj >= P.nray) jj = P.nray - 1;
-    ok = sample_bin(P, ii, jj, &bx, &by);
-  }
-  int lo_x = ok ? bx : 0x7fffffff, hi_x = ok ? bx : -1;
-  int lo_y = ok ? by : 0x7fffffff, hi_y = ok ? by : -1;
-  for (int o = 16; o; o >>= 1) {
-    lo_x = min(lo_x, __shfl_xor_sync(0xffffffffu, lo_x, o));
-    hi_x = max(hi_x, __shfl_xor_sync(0xffffffffu, hi_x, o));
-    lo_y = min(lo_y, __shfl_xor_sync(0xffffffffu, lo_y, o));
-    hi_y = max(hi_y, __shfl_xor_sync(0xffffffffu, hi_y, o));
-  }
-  if (lane == 0) {
-    const int cx = (hi_x >= 0) ? (lo_x + hi_x) / 2 : P.npix / 2;
-    const int cy = (hi_y >= 0) ? (lo_y + hi_y) / 2 : P.npix / 2;
-    int wmax = P.npix - kRayWin;
-    if (wmax < 0) wmax = 0;
-    *tile_out = tile;
-    *wx_out = min(max(cx - kRayWin / 2, 0), wmax);
-    *wy_out = min(max(cy - kRayWin / 2, 0), wmax);
-  }
-}
-
 // FP32: two blocks per SM (at most 64 registers: the packed sub-block loop
 // keeps its twelve column pairs in registers).
 template <bool FP64>
 __global__ void __launch_bounds__(kRayThreads, FP64 ? 1 : 2)
     k_rayshoot(const RayParams P) {
   extern __shared__ __align__(16) uint32_t win[];  // kRayWin^2 bins
-  // the tile in work and the next one, with their windows' corners
-  __shared__ int s_tile[2], s_wx[2], s_wy[2];
+  __shared__ int s_wx, s_wy, s_tile;
   const int tid = threadIdx.x;
   uint4 *win4 = reinterpret_cast<uint4 *>(win);
   for (int k = tid; k < kRayWin * kRayWin / 4; k += kRayThreads)
@@ -275,20 +230,47 @@ __global__ void __launch_bounds__(kRayThreads, FP64 ? 1 : 2)
   const int ntiles = P.tiles_x * P.tiles_y;
   const int sx = tid & 31;   // sub-block column (lane)
   const int sy = tid >> 5;   // sub-block row (warp)
-  const long long tile_h = (long long)kRayWarps * P.sub_rows;
 
-  // Tiles come from a counter (blocks whose tiles were cheap take more).
-  // Warp 0 takes the next tile and places its window after its own rays of
-  // the current tile, while the other warps still shoot theirs.
-  if (tid < 32) next_tile(P, ntiles, tile_h, tid, &s_tile[0], &s_wx[0],
-                          &s_wy[0]);
-  __syncthreads();
-  for (int cur = 0;; cur ^= 1) {
-    const int tile = s_tile[cur];
+  const long long tile_h = (long long)kRayWarps * P.sub_rows;
+  for (;;) {
+    // tiles from a counter: blocks whose tiles were cheap take more
+    if (tid == 0) s_tile = (int)atomicAdd(&P.tot[2], 1ULL);
+    __syncthreads();
+    const int tile = s_tile;
     if (tile >= ntiles) break;  // block-uniform
     const long long i0 = (long long)(tile % P.tiles_x) * kRayTileX;
     const long long j0 = (long long)(tile / P.tiles_x) * tile_h;
-    const int wx0 = s_wx[cur], wy0 = s_wy[cur];
+    if (tid < 32) {
+      // place the window on the bounding box of 9 deflected sample rays
+      int bx = 0, by = 0;
+      bool ok = false;
+      if (tid < 9) {
+        long long ii = i0 + (tid % 3) * (long long)(kRayTileX - 1) / 2;
+        long long jj = j0 + (tid / 3) * (tile_h - 1) / 2;
+        if (ii >= P.nray) ii = P.nray - 1;
+        if (jj >= P.nray) jj = P.nray - 1;
+        ok = sample_bin(P, ii, jj, &bx, &by);
+      }
+      int lo_x = ok ? bx : 0x7fffffff, hi_x = ok ? bx : -1;
+      int lo_y = ok ? by : 0x7fffffff, hi_y = ok ? by : -1;
+      for (int o = 16; o; o >>= 1) {
+        lo_x = min(lo_x, __shfl_xor_sync(0xffffffffu, lo_x, o));
+        hi_x = max(hi_x, __shfl_xor_sync(0xffffffffu, hi_x, o));
+        lo_y = min(lo_y, __shfl_xor_sync(0xffffffffu, lo_y, o));
+        hi_y = max(hi_y, __shfl_xor_sync(0xffffffffu, hi_y, o));
+      }
+      if (tid == 0) {
+        int cx = (hi_x >= 0) ? (lo_x + hi_x) / 2 : P.npix / 2;
+        int cy = (hi_y >= 0) ? (lo_y + hi_y) / 2 : P.npix / 2;
+        int wx = cx - kRayWin / 2, wy = cy - kRayWin / 2;
+        int wmax = P.npix - kRayWin;
+        if (wmax < 0) wmax = 0;
+        s_wx = min(max(wx, 0), wmax);
+        s_wy = min(max(wy, 0), wmax);
+      }
+    }
+    __syncthreads();
+    const int wx0 = s_wx, wy0 = s_wy;
     const long long ib = i0 + sx * kSubX;
     const long long jb = j0 + sy * P.sub_rows;
     // rays of the sub-block row inside the grid, and the first one's x1
@@ -326,9 +308,6 @@ __global__ void __launch_bounds__(kRayThreads, FP64 ? 1 : 2)
         }
       }
     }
-    if (tid < 32)
-      next_tile(P, ntiles, tile_h, tid, &s_tile[cur ^ 1], &s_wx[cur ^ 1],
-                &s_wy[cur ^ 1]);
     __syncthreads();
     // flush the window: four bins per read, one global add per non-empty
     // bin, then clear (a bin beyond a map narrower than the window is
