@@ -410,10 +410,10 @@ morse_status morse_peak_search(morse_ctx *ctx, const morse_event *ev,
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current) and keeps it for the
  * life of the process, so the library must not be used across a
- * cudaDeviceReset of that device; make that first call before any stream
- * capture.  Every call in the process shares the array: calls that overlap
- * on the same GPU (other streams, other host threads) race on it; each
- * call rewrites every byte it reads, so nothing carries over.  Returns
+ * cudaDeviceReset of that device.  Every call in the process shares the
+ * array: calls that overlap on the same GPU (other streams, other host
+ * threads) race on it; each call rewrites every byte it reads, so nothing
+ * carries over.  Returns
  * MORSE_EINVAL, with a message naming the sizes, when the search needs
  * more than 4 MiB of scratch (top_k above about 850 on a 152-SM GPU) or
  * more than 4096 grid-table values (n_u0 + 2 n_alpha + 2 n_t0 + 2 n_tE).
