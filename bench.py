@@ -930,6 +930,8 @@ def run_gpu(args, cfg):
                                          not args.no_batch_tune)
         elif args.only == "fp16":
             out["fp16_vs_fp32"] = fp16_section(ctx, m, cfg, ev)
+        elif args.only == "peaks":
+            out["peak_library"] = peak_library(ctx, m, cfg)
         else:
             out["map_generators"] = map_generators(ctx, m, cfg)
         print(json.dumps(out))
@@ -1163,7 +1165,8 @@ def main():
                     help="run only the peak-aligned search over the maps "
                     "and the peak library section (profiling)")
     ap.add_argument("--only", default="",
-                    choices=["", "adjoint", "batched", "rayshoot", "fp16"],
+                    choices=["", "adjoint", "batched", "rayshoot", "fp16",
+                             "peaks"],
                     help="run one section alone on its own workload "
                     "(profiling): the adjoint on the config-1 event, the "
                     "batched search subset, or the config-1 map builds")

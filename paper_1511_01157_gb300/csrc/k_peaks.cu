@@ -19,11 +19,12 @@
 // GB300 design: one warp per line.  The lanes evaluate 32 consecutive
 // samples at once (the line's texels stream through L1/L2, the map having
 // just been built); the sequential peak detector then steps through them
-// with every lane holding the same state: a warp scan of the running
+// with every lane holding the same state: a chunk whose extremes show
+// that it cannot change the state (most chunks: a line has a few peaks)
+// only moves the running extreme; otherwise a warp scan of the running
 // maximum (or minimum) finds the first sample of the 32 that changes the
 // state, everything before it moves only the running extreme, and the
-// scan resumes after it -- a few warp instructions per sample, no shared
-// memory, no divergence.  The highest peaks are kept one per lane, the
+// scan resumes after it -- no shared memory, no divergence.  The highest peaks are kept one per lane, the
 // list shifted by a warp shuffle on the rare insertion.  The expansion into trajectory
 // entries is one thread per (line, slot).
 #include <cuda_runtime.h>
@@ -134,6 +135,37 @@ __global__ void __launch_bounds__(kPkWarps * 32)
         atomicOr(err, 1u);
     }
     if (m == 0u) continue;
+    // Most chunks cannot change the detector's state, which the chunk's
+    // extremes show (one integer reduction each: the samples are
+    // non-negative, so their bit patterns order as the values): looking
+    // for a maximum, no sample ends a peak if max(mx, chunk max) <=
+    // r x (chunk min), since every running maximum is at most the former
+    // and every r x_i at least the latter (rounding is monotone); looking
+    // for a rise, none starts one if chunk max <= r x min(mn, chunk min).
+    // Such a chunk only moves the running extreme, exactly as the scan
+    // below would.
+    {
+      const unsigned vb = __float_as_uint(v);
+      const float cmax =
+          __uint_as_float(__reduce_max_sync(kFull, in ? vb : 0u));
+      const float cmin =
+          __uint_as_float(__reduce_min_sync(kFull, in ? vb : 0x7f800000u));
+      if (look_max) {
+        if (fmaxf(mx, cmax) <= __fmul_rn(r, cmin)) {
+          if (cmax > mx) {
+            kmx = kb + __ffs(__ballot_sync(kFull, in && v == cmax)) - 1;
+            mx = cmax;
+          }
+          continue;
+        }
+      } else {
+        const float low = fminf(mn, cmin);
+        if (cmax <= __fmul_rn(r, low)) {
+          mn = low;
+          continue;
+        }
+      }
+    }
     // The chunk's samples in order, a run at a time.  With the inclusive
     // running maximum pm_i (of mx and the run's samples up to i), sample i
     // ends a peak exactly when pm_i > r x_i (a sample above the running
