@@ -350,11 +350,6 @@ __device__ __forceinline__ int clampi(int v, int n) {
   return v < 0 ? 0 : (v >= n ? n - 1 : v);
 }
 
-// counts -> A = count * f (FP64 product rounded to FP32)
-__device__ __forceinline__ float mag_of(const uint32_t *c, int npix, int x,
-                                        int y, double f) {
-  return __double2float_rn(__dmul_rn((double)c[(size_t)y * npix + x], f));
-}
 
 __device__ __forceinline__ float4 quad_of(float a00, float a10, float a01,
                                           float a11) {
@@ -365,23 +360,15 @@ __device__ __forceinline__ float4 quad_of(float a00, float a10, float a01,
   return make_float4(m00, d0, __fsub_rn(m01, m00), __fsub_rn(d1, d0));
 }
 
-__global__ void k_counts_to_map(const uint32_t *__restrict__ counts, int npix,
-                                double f, float *__restrict__ A,
-                                float4 *__restrict__ quad, int qpitch) {
-  const int side = npix + 1;
-  const size_t n = (size_t)side * side;
+// counts -> A, one FP64 product per texel (the cells are then built from A
+// by k_quads_from_A: one product per texel instead of four per cell, the
+// FP64 pipe being the limiter of a fused form)
+__global__ void k_counts_to_A(const uint32_t *__restrict__ counts, int npix,
+                              double f, float *__restrict__ A) {
+  const size_t n = (size_t)npix * npix;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
-       k += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(k % side), r = (int)(k / side);
-    const int x0 = clampi(c - 1, npix), x1 = clampi(c, npix);
-    const int y0 = clampi(r - 1, npix), y1 = clampi(r, npix);
-    const float a00 = mag_of(counts, npix, x0, y0, f);
-    if (c >= 1 && r >= 1) A[(size_t)(r - 1) * npix + (c - 1)] = a00;
-    quad[cell_index(c, r, qpitch)] =
-        quad_of(a00, mag_of(counts, npix, x1, y0, f),
-                mag_of(counts, npix, x0, y1, f),
-                mag_of(counts, npix, x1, y1, f));
-  }
+       k += (size_t)gridDim.x * blockDim.x)
+    A[k] = __double2float_rn(__dmul_rn((double)counts[k], f));
 }
 
 __global__ void k_quads_from_A(const float *__restrict__ A, int npix,
@@ -479,8 +466,12 @@ static int elementwise_grid(size_t n) {
 cudaError_t launch_counts_to_map(const uint32_t *counts, int npix, double f,
                                  float *A, float4 *quad, int qpitch,
                                  cudaStream_t st) {
-  k_counts_to_map<<<elementwise_grid(quad_cells(npix)), 256, 0, st>>>(
-      counts, npix, f, A, quad, qpitch);
+  k_counts_to_A<<<elementwise_grid((size_t)npix * npix), 256, 0, st>>>(
+      counts, npix, f, A);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_quads_from_A<<<elementwise_grid(quad_cells(npix)), 256, 0, st>>>(
+      A, npix, quad, qpitch);
   return cudaGetLastError();
 }
 

@@ -364,12 +364,22 @@ __global__ void __launch_bounds__(1024)
 // Fit fill: one warp per selected trajectory recomputes the phase-1 sums
 // and the solve with the same device functions as the search, and writes
 // the public morse_fit record with the search's chi^2.
-template <bool H>
+// With EPS the block first stages the light curve in shared memory, so a
+// warp's walk over the epochs waits only on the cell gathers.
+template <bool H, bool EPS>
 __global__ void k_fill(const FillParams F) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const float4 *blk = nullptr;
+  if (EPS) {
+    float4 *s = reinterpret_cast<float4 *>(fsm);
+    for (int e = threadIdx.x; e < F.S.n_ep; e += blockDim.x) s[e] = F.S.ep[e];
+    __syncthreads();
+    blk = s;
+  }
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= F.k) return;
-  fill_one<H>(F.S, F.sel[w], F.t0abs, F.tEv, lane, &F.out[w]);
+  if (w >= F.k) return;  // after the block's only barrier
+  fill_one<H>(F.S, F.sel[w], F.t0abs, F.tEv, lane, &F.out[w], blk);
 }
 
 // The tau interval of every (u0, alpha) line inside the map.
@@ -553,14 +563,38 @@ cudaError_t launch_topk_merge(Entry *a, Entry *b, int lists, int k,
 }
 
 cudaError_t launch_fill(const FillParams &F, cudaStream_t st) {
-  // two warps per block: the records' warps spread over the SMs (each
-  // warp's walk over the epochs is latency-bound)
-  const int threads = 64;
-  const int blocks = (F.k * 32 + threads - 1) / threads;
-  if (F.S.quadh)
-    k_fill<true><<<blocks, threads, 0, st>>>(F);
-  else
-    k_fill<false><<<blocks, threads, 0, st>>>(F);
+  // Each record's warp walks the epochs once (latency-bound).  Light curves
+  // that fit are staged in shared memory by blocks of eight warps; others
+  // are read from global memory by blocks of two warps, spread over the SMs.
+  static int optin_of[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int optin = dev < 64 ? optin_of[dev] : 0;
+  if (optin == 0) {
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                           dev);
+    cudaFuncSetAttribute(k_fill<true, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    cudaFuncSetAttribute(k_fill<false, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (dev < 64) optin_of[dev] = optin;
+  }
+  const size_t sm = sizeof(float4) * (size_t)F.S.n_ep;
+  if (sm <= (size_t)optin) {
+    const int threads = 256;
+    const int blocks = (F.k * 32 + threads - 1) / threads;
+    if (F.S.quadh)
+      k_fill<true, true><<<blocks, threads, sm, st>>>(F);
+    else
+      k_fill<false, true><<<blocks, threads, sm, st>>>(F);
+  } else {
+    const int threads = 64;
+    const int blocks = (F.k * 32 + threads - 1) / threads;
+    if (F.S.quadh)
+      k_fill<true, false><<<blocks, threads, 0, st>>>(F);
+    else
+      k_fill<false, false><<<blocks, threads, 0, st>>>(F);
+  }
   return cudaGetLastError();
 }
 

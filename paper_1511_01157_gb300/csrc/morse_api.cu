@@ -387,7 +387,7 @@ morse_status enqueue_build(morse_ctx *ctx, morse_map *m, const BuildSpec &b) {
     m->lookup = MORSE_STORE_FP16LOG;
   }
   t_end(ctx, r);
-  ctx->launches += 1;
+  ctx->launches += 2;  // counts -> A, A -> cells
   return MORSE_OK;
 }
 

@@ -352,13 +352,15 @@ __device__ __forceinline__ void band_release(BandTabs &B, long long r,
 
 // Record of one selected trajectory e (warp-collective; lane 0 writes *dst):
 // (Fs, Fb) from the phase-1 sums and the solve, recomputed with the search's
-// device functions on the epochs at P.ep (global memory), so the same bits;
+// device functions on the epochs at ep_blk (a shared-memory copy) or P.ep,
+// so the same bits;
 // chi^2 is the search's own phase-2 value, the key e was ranked by.
 template <bool H>
 __device__ __forceinline__ void fill_one(const SearchParams &P, const Entry e,
                                          const double *t0abs,
                                          const double *tEv, const int lane,
-                                         morse_fit *dst) {
+                                         morse_fit *dst,
+                                         const float4 *ep_blk = nullptr) {
   morse_fit r;
   const long long total = (long long)P.n_u0 * P.n_alpha * P.n_t0 * P.n_tE;
   if (e.idx < 0 || e.idx >= total) {
@@ -372,7 +374,7 @@ __device__ __forceinline__ void fill_one(const SearchParams &P, const Entry e,
     }
     return;
   }
-  const Epochs ep = epochs_at(P.ep, P.n_ep);
+  const Epochs ep = epochs_at(ep_blk ? ep_blk : P.ep, P.n_ep);
   const TrajC c = traj_consts(P, ep, e.idx);
   const Acc s = phase1<H>(P, ep, c, lane);
   const Solved sol = solve2(P, (double)s.a, (double)s.b, (double)s.d);
