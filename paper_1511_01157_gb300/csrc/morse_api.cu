@@ -801,6 +801,9 @@ morse_status enqueue_topk(morse_ctx *ctx, const Plan &pl,
 }
 
 // The (s, q) sweep behind morse_sweep and morse_search_sweep.
+#ifndef MORSE_SWEEP_OVERLAP
+#define MORSE_SWEEP_OVERLAP 1
+#endif
 morse_status sweep_impl(morse_ctx *ctx, const morse_event *ev,
                         const double *s, const double *q, int n_maps,
                         double extent, int npix, int64_t rays_per_axis,
@@ -813,21 +816,39 @@ morse_status sweep_impl(morse_ctx *ctx, const morse_event *ev,
   for (int i = 0; i < n_maps; ++i)
     MORSE_TRY(check_build(ctx, s[i], q[i], extent, npix, rays_per_axis, opts,
                           &specs[(size_t)i]));
-  if (ctx->sweep_map && ctx->sweep_map->npix != npix) {
-    cudaStreamSynchronize(ctx->stream);
-    map_release(ctx->sweep_map);
-    ctx->sweep_map = nullptr;
+  // Two map buffers: map i + 1 is built on a second stream while map i is
+  // searched, so the ray shooting fills the SMs that the merges, the fill
+  // and the search's last blocks leave idle.  The results do not depend on
+  // the overlap (each search waits for its map; each build for the search
+  // that last read its buffer).
+  const bool two = MORSE_SWEEP_OVERLAP && n_maps > 1;
+  morse_map **bufs[2] = {&ctx->sweep_map, &ctx->sweep_map2};
+  for (int b = 0; b < (two ? 2 : 1); ++b) {
+    morse_map *&mb = *bufs[b];
+    if (mb && mb->npix != npix) {
+      cudaStreamSynchronize(ctx->stream);
+      map_release(mb);
+      mb = nullptr;
+    }
+    if (!mb) {
+      mb = map_alloc(ctx, npix, true);
+      if (!mb)
+        return fail(ctx, MORSE_ENOMEM, "sweep map of %d^2 texels", npix);
+    }
+    mb->L = extent;
   }
-  if (!ctx->sweep_map) {
-    ctx->sweep_map = map_alloc(ctx, npix, true);
-    if (!ctx->sweep_map)
-      return fail(ctx, MORSE_ENOMEM, "sweep map of %d^2 texels", npix);
+  const bool h16 = n_maps > 0 && specs[0].fp16;
+  for (int b = 0; b < (two ? 2 : 1); ++b)
+    if (h16 && !map_ensure_half(*bufs[b]))
+      return fail(ctx, MORSE_ENOMEM, "FP16 table of %d^2 texels", npix);
+  if (two && !ctx->build_stream) {
+    MORSE_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->build_stream,
+                                              cudaStreamNonBlocking));
+    for (int k = 0; k < 4; ++k)
+      MORSE_CUDA(ctx, cudaEventCreateWithFlags(&ctx->sweep_ev[k],
+                                               cudaEventDisableTiming));
   }
   morse_map *m = ctx->sweep_map;
-  m->L = extent;
-  const bool h16 = n_maps > 0 && specs[0].fp16;
-  if (h16 && !map_ensure_half(m))
-    return fail(ctx, MORSE_ENOMEM, "FP16 table of %d^2 texels", npix);
   Plan pl;
   MORSE_TRY(plan_search(ctx, ev, grid, 0, grid_size(grid), false, h16, n_maps,
                         &pl, band_spec(npix, extent, grid_umax(grid), 0.0)));
@@ -850,11 +871,33 @@ morse_status sweep_impl(morse_ctx *ctx, const morse_event *ev,
   morse::set_groups(&P);
   morse_fit *fits = (morse_fit *)(base + pl.off_out);
   MORSE_TRY(hdr_init(ctx, base, pl, &P));
+  cudaStream_t s0 = ctx->stream;
+  cudaEvent_t *built = ctx->sweep_ev, *freed = ctx->sweep_ev + 2;
+  if (two) {  // the builds follow everything queued so far
+    MORSE_CUDA(ctx, cudaEventRecord(built[0], s0));
+    MORSE_CUDA(ctx, cudaStreamWaitEvent(ctx->build_stream, built[0], 0));
+  }
   for (int i = 0; i < n_maps; ++i) {
-    MORSE_TRY(enqueue_build(ctx, m, specs[(size_t)i]));
+    const int b = two ? (i & 1) : 0;
+    m = *bufs[b];
+    if (two) {
+      if (i >= 2)  // the search of map i - 2 has read this buffer
+        MORSE_CUDA(ctx, cudaStreamWaitEvent(ctx->build_stream, freed[b], 0));
+      ctx->stream = ctx->build_stream;
+      const morse_status bs = enqueue_build(ctx, m, specs[(size_t)i]);
+      ctx->stream = s0;
+      MORSE_TRY(bs);
+      MORSE_CUDA(ctx, cudaEventRecord(built[b], ctx->build_stream));
+      MORSE_CUDA(ctx, cudaStreamWaitEvent(s0, built[b], 0));
+    } else {
+      MORSE_TRY(enqueue_build(ctx, m, specs[(size_t)i]));
+    }
+    P.quad = m->quad;
+    P.quadh = h16 ? m->quadh : nullptr;
     if (i > 0) MORSE_TRY(hdr_reset_threshold(ctx, base, pl));
     MORSE_TRY(enqueue_cut(ctx, m, grid, T, pl, base, &P));
     MORSE_TRY(enqueue_topk(ctx, pl, P, base, T, fits + (size_t)i * pl.K));
+    if (two) MORSE_CUDA(ctx, cudaEventRecord(freed[b], s0));
   }
   Hdr h;
   MORSE_CUDA(ctx, cudaMemcpyAsync(&h, base + pl.off_hdr, sizeof(Hdr),
@@ -1477,7 +1520,13 @@ void morse_destroy(morse_ctx *ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->build_stream) {
+    cudaStreamSynchronize(ctx->build_stream);
+    cudaStreamDestroy(ctx->build_stream);
+    for (cudaEvent_t e : ctx->sweep_ev) cudaEventDestroy(e);
+  }
   if (ctx->sweep_map) map_release(ctx->sweep_map);
+  if (ctx->sweep_map2) map_release(ctx->sweep_map2);
   if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
   if (ctx->ws) cudaFree(ctx->ws);
   for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);

@@ -31,6 +31,10 @@ struct morse_ctx {
   double kernel_ms[KT_COUNT];
   uint64_t launches;        // kernels launched by this context
   morse_map *sweep_map;     // map storage reused by sweeps
+  morse_map *sweep_map2;    // the second buffer: map i + 1 is built (on
+                            // build_stream) while map i is searched
+  cudaStream_t build_stream;  // created on a sweep's first use
+  cudaEvent_t sweep_ev[4];    // built[2], free[2] of the two buffers
   unsigned long long last_exact;  // exact sweeps in the last search call
   // batched search: autotuned launch shapes per epoch-count bucket (key:
   // bucket and the search signature) and the reusable graph
