@@ -5,7 +5,8 @@
   it gives up after a few spins (~64 ns each) and sets the block's error
   bit; the host reads it after the stream has synchronised and returns
   MORSE_ETIMEOUT.  Nothing waits without a bound, so nothing hangs.  The
-  same context then searches normally and gets the same results as before.
+  same context then searches normally and gets the same results as before
+  (single searches, the allocation-free search, the batch and a sweep).
 * An allocation that fails: the next device allocation is made to fail on
   the host (as cudaMalloc does when the device is out of memory, but with
   nothing allocated); the call returns MORSE_ENOMEM and the context stays
@@ -47,10 +48,16 @@ def setup(m):
 def test_lock_wait_gives_up_and_context_recovers(m, setup):
     ctx, ev, mp, grid = setup
     ref = ctx.grid_chi2(ev, mp, grid)
+    # a sweep of three maps (builds on a second stream, searches on the
+    # sweep's own stream) before the fault, for the comparison after it
+    S, Q = np.array([0.9, 1.0, 1.1]), np.array([1e-3, 3e-3, 1e-2])
+    sw_ref = ctx.sweep(ev, S, Q, 2.0, 128, 600, grid, image_halfwidth=3.0)
     ctx.inject_fault(m.FAULT_LOCK_HELD, 4)
     for call in (lambda: ctx.grid_chi2(ev, mp, grid),
                  lambda: ctx.grid_chi2_noalloc(ev, mp, grid),
-                 lambda: ctx.grid_chi2_batch([ev], [mp], grid)):
+                 lambda: ctx.grid_chi2_batch([ev], [mp], grid),
+                 lambda: ctx.sweep(ev, S, Q, 2.0, 128, 600, grid,
+                                   image_halfwidth=3.0)):
         with pytest.raises(m.MorseError) as e:
             call()
         assert e.value.status == m.ETIMEOUT
@@ -59,6 +66,9 @@ def test_lock_wait_gives_up_and_context_recovers(m, setup):
     again = ctx.grid_chi2(ev, mp, grid)
     for f in ("idx", "chi2", "Fs", "Fb"):
         assert np.array_equal(again[f], ref[f]), f
+    sw = ctx.sweep(ev, S, Q, 2.0, 128, 600, grid, image_halfwidth=3.0)
+    for f in ("idx", "chi2", "Fs", "Fb"):
+        assert np.array_equal(sw[f], sw_ref[f]), f
     batch = ctx.grid_chi2_batch([ev], [mp], grid)
     assert np.array_equal(batch[0, 0]["idx"], ref["idx"])
 
