@@ -717,6 +717,10 @@ morse_status enqueue_cut(morse_ctx *ctx, const morse_map *map,
   return MORSE_OK;
 }
 
+#ifndef MORSE_PILOT_UB
+#define MORSE_PILOT_UB 1  // the pilot keys its samples by chi2_upper
+#endif
+
 // A fresh tag for a search launch's published block quantiles (never 0,
 // the value of a cleared word).
 unsigned next_pub_tag(morse_ctx *ctx) {
@@ -750,6 +754,7 @@ morse_status enqueue_topk(morse_ctx *ctx, const Plan &pl,
     int grid = (int)std::min<long long>(
         pl.grid, (groups + morse::kSearchWarps - 1) / morse::kSearchWarps);
     if (grid < 1) grid = 1;
+    Q.pilot_ub = MORSE_PILOT_UB;
     Q.pub_tag = next_pub_tag(ctx);
     Q.pub_nb = grid;
     Q.pub_me = -1;

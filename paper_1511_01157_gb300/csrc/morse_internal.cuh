@@ -263,6 +263,8 @@ struct SearchParams {
                             // band-table cell differs from the map's
                             // (checked build only)
   unsigned long long *stat_exact;  // trajectories given the exact sweep
+  int pilot_ub;             // 1: key the candidates by chi2_upper instead
+                            // of the exact sweep (the pilot pass)
   unsigned spin_limit;      // block top-K lock: spins before giving up
   int lock0;                // initial lock word (1: held, an injected fault)
   // Published block quantiles (nullptr: off): kPubLevels rows, pub_stride

@@ -798,6 +798,32 @@ __device__ __forceinline__ bool may_reach(const SearchParams &P,
   return (P.CFF - t) * o.bden <= o.bnum;
 }
 
+// An upper bound of the chi^2 the exact residual sweep gives at the FP32
+// (Fs, Bc) = (a, b) of a solved trajectory, from its phase-1 sums alone
+// (the pilot seeds the grid-wide threshold from these, without the sweep:
+// K real trajectories have exact chi^2 at or below the K-th bound).  The
+// residual sum is S_FF - 2a S_AF - 2b S_F + a^2 S_AA + 2ab S_A + b^2 S_1;
+// the FP32 sums are bracketed as in solve2 (S_AA within g S_AA, S_A within
+// g T_A, S_AF within g T_AF), each term taken at its worst, plus the FP64
+// rounding of the sum of the terms, times 1 + 1e-4 for the FP32 rounding
+// of the sweep (the margin may_reach allows it).
+__device__ __forceinline__ double chi2_upper(const SearchParams &P, double SA,
+                                            double SAA, double SAF, double a,
+                                            double b) {
+  const double g = 2.0 * P.gamma;
+  const double TA = (double)__fsqrt_ru(__double2float_ru(P.S1 * SAA));
+  const double TAF = (double)__fsqrt_ru(__double2float_ru(SAA * P.SFF));
+  const double q = P.SFF - 2.0 * a * SAF - 2.0 * b * P.SF + a * a * SAA +
+                   2.0 * a * b * SA + b * b * P.S1;
+  const double absum = P.SFF + 2.0 * fabs(a * SAF) + 2.0 * fabs(b * P.SF) +
+                       a * a * SAA + 2.0 * fabs(a * b * SA) + b * b * P.S1;
+  const double slack = g * (2.0 * fabs(a) * TAF + a * a * SAA +
+                            2.0 * fabs(a * b) * TA) +
+                       16.0 * 1.1102230246251565e-16 * absum;
+  const double ub = (q + slack) * 1.0001000100010002;
+  return ub == ub ? ub : CUDART_INF;  // NaN sums: no bound
+}
+
 __device__ __forceinline__ double bits_to_chi2(unsigned long long b) {
   return b == ~0ULL ? CUDART_INF : __longlong_as_double((long long)b);
 }

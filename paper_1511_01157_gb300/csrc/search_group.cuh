@@ -225,11 +225,18 @@ __device__ __forceinline__ void search_group(const SearchParams &P,
   // 1e-4: margin for the FP32 rounding of the exact sweep itself
   if (!DENSE && cand_me && thr < CUDART_INF)
     cand_me = may_reach(P, sol, thr);
-  unsigned todo = __ballot_sync(kFull, cand_me);
-  n_exact += __popc(todo);
   const float myFs = __double2float_rn(sol.Fs);
   const float myBc = __double2float_rn(sol.Bc);
   double my_chi2 = CUDART_INF;
+  if (!DENSE && P.pilot_ub) {
+    // pilot: the bound from the sums, no sweep
+    if (cand_me)
+      my_chi2 = chi2_upper(P, (double)mine_s.a, (double)mine_s.b,
+                           (double)mine_s.d, (double)myFs, (double)myBc);
+    cand_me = false;
+  }
+  unsigned todo = __ballot_sync(kFull, cand_me);
+  n_exact += __popc(todo);
   while (todo) {
     const int k = __ffs(todo) - 1;
     todo &= todo - 1;
