@@ -1222,6 +1222,7 @@ morse_status batch_upload(morse_ctx *ctx, BatchHost &H, const BatchLayout &L,
   B.n_lists = (int)L.lists;
   *Bp = B;
   Bp->S.pub_tag = 1;
+  Bp->S.pilot_ub = MORSE_PILOT_UB;  // the pilot keys samples by chi2_upper
   Bp->list0 = (const int *)(base + L.off_lp);
   Bp->S.count = H.pilot_count;
   Bp->S.stride = H.pilot_stride;
