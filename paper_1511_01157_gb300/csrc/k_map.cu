@@ -206,6 +206,18 @@ __device__ __forceinline__ void shoot_f32(const RayParams &P, uint32_t *win,
           atomicAdd(&win[ly1 * kRayWin + lx1], 1u);
           continue;
         }
+        // both rays off the map (the next most common case: 38 % of the
+        // rays of [-3, 3]^2 miss the [-2, 2]^2 map): one test for the pair
+        // on the map-relative floor bits, unless a ray is lost
+        const unsigned ax0 = (unsigned)__float_as_int(tx.x) - 0x4B400000u;
+        const unsigned ay0 = (unsigned)__float_as_int(ty.x) - 0x4B400000u;
+        const unsigned ax1 = (unsigned)__float_as_int(tx.y) - 0x4B400000u;
+        const unsigned ay1 = (unsigned)__float_as_int(ty.y) - 0x4B400000u;
+        if (min(max(ax0, ay0), max(ax1, ay1)) >= (unsigned)P.npix &&
+            rr.x != 0.0f && rr.y != 0.0f) {
+          n_off += 2;
+          continue;
+        }
         bin_ray(P, win, cx, cy, W, tx.x, ty.x, rr.x == 0.0f, n_off, n_lost);
         bin_ray(P, win, cx, cy, W, tx.y, ty.y, rr.y == 0.0f, n_off, n_lost);
       } else {
