@@ -58,8 +58,8 @@ GATHER_BYTES_PER_EVAL = 16
 SMEM_BYTES_PER_EVAL = 22
 SMEM_BYTES_PER_CLK_SM = 128
 # adjoint, per trajectory-epoch: the chi^2 of the two sweeps (22, as the
-# search) and 14 more for the gradient through the lookup (the survey's
-# per-evaluation figure); the kernel recomputes the lookup in its second
+# search) and 14 more for the gradient through the lookup (four FP32 sums
+# in the map's pixel axes); the kernel recomputes the lookup in its second
 # sweep instead of storing A, and takes the gradient in the map's pixel
 # axes, about 37 FP32 instructions in all
 ADJ_INSTR_PER_EVAL = 36
