@@ -109,7 +109,9 @@ __device__ __forceinline__ void run_unit(const BatchParams &B,
   }
 }
 
-template <bool H>
+// V only names a second copy of the kernel (V = 1: the launch of unstaged
+// light curves), so that each launch has its own shared-memory carveout.
+template <bool H, int V>
 __global__ void __launch_bounds__(kSearchWarps * 32, 1)
     k_batch(const BatchParams B) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -249,10 +251,10 @@ size_t batch_smem_bytes(int ep_cap, int top_k) {
          sizeof(Entry) * ((size_t)2 * top_k + kSearchWarps * 32);
 }
 
-template <bool H>
+template <bool H, int V>
 static int batch_occupancy(size_t smem) {
-  cudaFuncSetAttribute(k_batch<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
+  cudaFuncSetAttribute(k_batch<H, V>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   // smallest shared-memory carveout that holds the block: the rest of the
   // SM's 256 KB serves as L1 for the map gathers
   int dev = 0, per_sm = 0;
@@ -262,29 +264,38 @@ static int batch_occupancy(size_t smem) {
   if (per_sm > 0) {
     int pct = (int)((100.0 * (double)(smem + 2048)) / (double)per_sm) + 1;
     if (pct > 100) pct = 100;
-    cudaFuncSetAttribute(k_batch<H>,
+    cudaFuncSetAttribute(k_batch<H, V>,
                          cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   }
   int b = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &b, k_batch<H>, kSearchWarps * 32, smem) != cudaSuccess) {
+          &b, k_batch<H, V>, kSearchWarps * 32, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return b;
 }
 
-int batch_blocks_per_sm(bool h16, size_t smem) {
-  return h16 ? batch_occupancy<true>(smem) : batch_occupancy<false>(smem);
+int batch_blocks_per_sm(bool h16, size_t smem, int variant) {
+  if (variant)
+    return h16 ? batch_occupancy<true, 1>(smem)
+               : batch_occupancy<false, 1>(smem);
+  return h16 ? batch_occupancy<true, 0>(smem) : batch_occupancy<false, 0>(smem);
 }
 
 cudaError_t launch_batch(const BatchParams &B, bool h16, int grid,
-                         size_t smem, cudaStream_t st) {
+                         size_t smem, cudaStream_t st, int variant) {
   const int threads = kSearchWarps * 32;
-  if (h16)
-    k_batch<true><<<grid, threads, smem, st>>>(B);
-  else
-    k_batch<false><<<grid, threads, smem, st>>>(B);
+  if (variant) {
+    if (h16)
+      k_batch<true, 1><<<grid, threads, smem, st>>>(B);
+    else
+      k_batch<false, 1><<<grid, threads, smem, st>>>(B);
+  } else if (h16) {
+    k_batch<true, 0><<<grid, threads, smem, st>>>(B);
+  } else {
+    k_batch<false, 0><<<grid, threads, smem, st>>>(B);
+  }
   return cudaGetLastError();
 }
 

@@ -963,6 +963,8 @@ struct BatchHost {
   std::vector<double> tables;  // u0 | cos | sin | 1/(tE D) | t0 | tE | t0rel
   long long pilot_count = 0, pilot_stride = 0;
   int ep_cap = 0;
+  int main_global = 0;  // the main pass's units of unstaged light curves,
+                        // first in `main` (a launch of their own)
 };
 
 // Units of one pass over `pairs` pairs: groups [0, groups(p)) of each pair
@@ -1027,9 +1029,8 @@ struct BatchLayout {
 };
 
 struct BatchHdr {
-  unsigned counter[2];
+  unsigned counter[3];  // pilot, main (unstaged units), main (staged)
   unsigned err;
-  unsigned pad;
   unsigned long long stat_exact;
 };
 
@@ -1148,6 +1149,18 @@ morse_status batch_prepare(morse_ctx *ctx, const morse_event *const *evs,
   batch_units(order, shape_pair, gm, pairs, H.main, H.main_list0);
   if ((long long)H.main_list0.back() >= 0x7fffffffLL / std::max(K, 1))
     return fail(ctx, MORSE_EINVAL, "batch needs too many partial lists");
+  // units of light curves that are not staged run first, in a launch with
+  // no staging space (the shared memory it leaves serves as L1 for their
+  // epochs); each part keeps the map-major order
+  std::stable_partition(H.main.begin(), H.main.end(),
+                        [&](const morse::BatchUnit &u) {
+                          return !(u.stage && H.ev[(size_t)(u.pair / n_maps)]
+                                                      .n_ep <= H.ep_cap);
+                        });
+  H.main_global = 0;
+  for (const morse::BatchUnit &u : H.main)
+    if (!(u.stage && H.ev[(size_t)(u.pair / n_maps)].n_ep <= H.ep_cap))
+      ++H.main_global;
   return MORSE_OK;
 }
 
@@ -1250,7 +1263,8 @@ morse_status batch_enqueue(morse_ctx *ctx, const BatchLayout &L, char *base,
                            const morse::BatchParams &Bp,
                            const morse::BatchParams &Bm, bool h16, int pairs,
                            const double *t0abs, const double *tEv,
-                           int grid, size_t smem) {
+                           int grid, size_t smem, int main_global,
+                           int grid_g, size_t smem_g) {
   const int K = Bm.S.top_k;
   MORSE_CUDA(ctx, cudaMemsetAsync(base + L.off_gthr, 0xFF,
                                   sizeof(unsigned long long) * pairs,
@@ -1277,9 +1291,25 @@ morse_status batch_enqueue(morse_ctx *ctx, const BatchLayout &L, char *base,
     t_end(ctx, r);
     ctx->launches += 2;
   }
+  // main pass: the unstaged light curves' units in a launch without
+  // staging space, then the staged ones
+  morse::BatchParams Bg = Bm, Bs = Bm;
+  Bg.n_units = main_global;
+  Bg.ep_cap = 0;
+  Bs.units = Bm.units + main_global;
+  Bs.n_units = Bm.n_units - main_global;
+  Bs.counter = &((BatchHdr *)(base + L.off_hdr))->counter[2];
   r = t_begin(ctx, KT_SEARCH);
-  MORSE_CUDA(ctx, morse::launch_batch(Bm, h16, std::min(grid, Bm.n_units),
-                                      smem, ctx->stream));
+  if (Bg.n_units > 0) {
+    MORSE_CUDA(ctx, morse::launch_batch(Bg, h16, std::min(grid_g, Bg.n_units),
+                                        smem_g, ctx->stream, 1));
+    ctx->launches += 1;
+  }
+  if (Bs.n_units > 0) {
+    MORSE_CUDA(ctx, morse::launch_batch(Bs, h16, std::min(grid, Bs.n_units),
+                                        smem, ctx->stream));
+    ctx->launches += 1;
+  }
   t_end(ctx, r);
   r = t_begin(ctx, KT_MERGE);
   MORSE_CUDA(ctx, morse::launch_batch_merge(pa, pb,
@@ -1287,7 +1317,7 @@ morse_status batch_enqueue(morse_ctx *ctx, const BatchLayout &L, char *base,
                                             pairs, K, res, nullptr,
                                             ctx->stream));
   t_end(ctx, r);
-  ctx->launches += 2;
+  ctx->launches += 1;
   r = t_begin(ctx, KT_FILL);
   MORSE_CUDA(ctx, morse::launch_batch_fill(Bm, h16, res, pairs, t0abs, tEv,
                                            (morse_fit *)(base + L.off_fit),
@@ -2487,7 +2517,9 @@ morse_status morse_grid_chi2_batch(morse_ctx *ctx,
                          &t0abs, &tEv));
   const size_t smem = morse::batch_smem_bytes(H.ep_cap, K);
   const int bps = morse::batch_blocks_per_sm(h16, smem);
-  if (bps < 1)
+  const size_t smem_g = morse::batch_smem_bytes(0, K);
+  const int bps_g = morse::batch_blocks_per_sm(h16, smem_g, 1);
+  if (bps < 1 || bps_g < 1)
     return fail(ctx, MORSE_EUNSUPPORTED,
                 "batched search kernel does not fit (%d staged epochs, "
                 "top_k %d)", H.ep_cap, K);
@@ -2499,7 +2531,8 @@ morse_status morse_grid_chi2_batch(morse_ctx *ctx,
   MORSE_CUDA(ctx, cudaStreamBeginCapture(ctx->stream,
                                          cudaStreamCaptureModeThreadLocal));
   morse_status st = batch_enqueue(ctx, L, base, Bp, Bm, h16, pairs, t0abs,
-                                  tEv, bps * ctx->sm_count, smem);
+                                  tEv, bps * ctx->sm_count, smem, H.main_global,
+                                  bps_g * ctx->sm_count, smem_g);
   cudaGraph_t graph = nullptr;
   cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
   if (st != MORSE_OK || ce != cudaSuccess) {

@@ -468,9 +468,11 @@ struct BatchParams {
 };
 
 size_t batch_smem_bytes(int ep_cap, int top_k);
-int batch_blocks_per_sm(bool h16, size_t smem);
+// variant 1: the copy of the kernel for the launch of unstaged light
+// curves (its own shared-memory carveout)
+int batch_blocks_per_sm(bool h16, size_t smem, int variant = 0);
 cudaError_t launch_batch(const BatchParams &B, bool h16, int grid,
-                         size_t smem, cudaStream_t st);
+                         size_t smem, cudaStream_t st, int variant = 0);
 // per pair: merge lists [list0[p], list0[p+1]) of a and b (ping-pong) into
 // result[p]; with gthr set, also lower gthr[p] to the merged K-th chi^2
 cudaError_t launch_batch_merge(Entry *a, Entry *b, const int *list0,
