@@ -476,6 +476,30 @@ def test_sweep_equals_per_map_searches(ctx, m):
     assert ctx.kernel_ms(2) > 0.0
 
 
+def test_sweep_buffers_across_map_sizes(ctx, m):
+    """A sweep builds map i + 1 (second buffer, second stream) while map i
+    is searched.  Sweeps of one, two and five maps, at two map sizes in
+    turn on the same context (both buffers reallocated), each equal to one
+    build and search per map."""
+    c = synth.CFG0
+    t, F, sig = _event(c, n=250, seed=9)
+    ev = ctx.event(t, F, sig)
+    g = m.Grid.make(3, 8, 3, 3, 0.01, 0.4, -1.0, 1.0, 8.0, 40.0, True, True,
+                    5)
+    S = np.array([0.7, 1.0, 1.4, 0.9, 1.2])
+    Q = np.array([1e-3, 1e-2, 3e-4, 3e-3, 1e-4])
+    for npix, n in ((64, 5), (96, 2), (64, 1), (96, 5)):
+        fits = ctx.sweep(ev, S[:n], Q[:n], 2.0, npix, 500, g,
+                         image_halfwidth=3.0, deflect="fp32")
+        for i in range(n):
+            mp = ctx.build_map(S[i], Q[i], 2.0, npix, 500,
+                               image_halfwidth=3.0, deflect="fp32")
+            ref = ctx.grid_chi2(ev, mp, g)
+            mp.free()
+            assert np.array_equal(fits[i]["idx"], ref["idx"]), (npix, n, i)
+            assert np.array_equal(fits[i]["chi2"], ref["chi2"]), (npix, n, i)
+
+
 def test_epoch_order_does_not_matter(ctx, m, cfg0_maps):
     """Events are stored time-sorted; a shuffled copy searches the same."""
     mp, A_o, *_ = cfg0_maps
