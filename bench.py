@@ -258,7 +258,7 @@ def peak_library(ctx, m, cfg, delta=0.1, max_peaks=8):
     mp = ctx.build_map(cfg["s"], cfg["q"], cfg["L"], cfg["npix"], cfg["nray"],
                        image_halfwidth=cfg["X"], deflect="fp32")
     lines = grid_lines(cfg)
-    times = []
+    times, kt = [], []
     for _ in range(3):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -266,6 +266,7 @@ def peak_library(ctx, m, cfg, delta=0.1, max_peaks=8):
                                      delta=delta)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
+        kt.append(ctx.kernel_ms(7))  # the launch alone (CUDA events)
     mp.free()
     h = 2.0 * cfg["L"] / cfg["npix"] / 2
     n = inside_samples(lines, cfg["L"], h)
@@ -276,25 +277,33 @@ def peak_library(ctx, m, cfg, delta=0.1, max_peaks=8):
     maps = [ctx.build_map(S[j], Q[j], cfg["L"], cfg["npix"], cfg["nray"],
                           image_halfwidth=cfg["X"], deflect="fp32")
             for j in pick]
-    tb = []
+    tb, ktb = [], []
     for _ in range(3):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.line_peaks_batch(maps, lines, sub=2, max_peaks=max_peaks,
-                             delta=delta)
+        cb, _, _ = ctx.line_peaks_batch(maps, lines, sub=2,
+                                        max_peaks=max_peaks, delta=delta)
         torch.cuda.synchronize()
         tb.append(time.perf_counter() - t0)
+        ktb.append(ctx.kernel_ms(7))
     for mp in maps:
         mp.free()
     return {"lines": len(lines), "ms": 1e3 * t, "samples": n,
             "samples_per_s": n / t, "delta": delta,
+            "kernel_ms": min(kt), "kernel_samples_per_s": n / min(kt) * 1e3,
             "median_peaks_per_line": float(np.median(count)),
+            "mean_peaks_per_line": float(np.mean(count)),
             "max_peaks_per_line": int(count.max()),
+            "batch_mean_peaks_per_line": float(np.mean(cb)),
             "batch_64_maps_ms": 1e3 * min(tb),
             "batch_samples_per_s": 64 * n / min(tb),
+            "batch_kernel_ms": min(ktb),
+            "batch_kernel_samples_per_s": 64 * n / min(ktb) * 1e3,
             "note": "samples of the lines inside the map, every half "
-                    "texel; the batch is one launch over 64 maps' lines "
-                    "(C-ABI call, device synchronised)"}
+                    "texel; the batch is one launch over 64 maps' lines; "
+                    "ms: the C-ABI call, device synchronised (host copies "
+                    "of the results included); kernel_ms: the launch "
+                    "alone, CUDA events"}
 
 
 def adjoint_section(ctx, m, cfg, ev, n_ep, stream, probes, peak_instr_s,

@@ -604,7 +604,7 @@ morse_status morse_measure_peaks(morse_ctx *ctx, morse_peaks *out);
  * milliseconds (CUDA events on the context stream), summed over every
  * launch of that kind in the call: which = 0 ray shooting, 1 counts-to-map,
  * 2 grid search, 3 top-K merge, 4 fit fill, 5 adjoint evaluations, 6
- * refine steps; 7 reserved (0). */
+ * refine steps, 7 peak-library lines (morse_line_peaks and its batch). */
 morse_status morse_last_kernel_ms(const morse_ctx *ctx, int which,
                                   double *ms);
 

@@ -16,17 +16,20 @@
 // the count, with every operation rounded explicitly (no contraction), so
 // the result is the same bit for bit wherever it is computed.
 //
-// GB300 design: one warp per line.  The lanes evaluate 32 consecutive
-// samples at once (the line's texels stream through L1/L2, the map having
-// just been built); the sequential peak detector then steps through them
-// with every lane holding the same state: a chunk whose extremes show
-// that it cannot change the state (most chunks: a line has a few peaks)
-// only moves the running extreme; otherwise a warp scan of the running
-// maximum (or minimum) finds the first sample of the 32 that changes the
-// state, everything before it moves only the running extreme, and the
-// scan resumes after it -- no shared memory, no divergence.  The highest peaks are kept one per lane, the
-// list shifted by a warp shuffle on the rare insertion.  The expansion into trajectory
-// entries is one thread per (line, slot).
+// GB300 design: one warp per line.  The line's FP64 set-up (its texel
+// coordinates and sample run) is spread over lanes, the FP64 pipe being
+// narrow on this part.
+// The lanes evaluate 32 consecutive samples at once (the line's texels
+// stream through L1/L2, the map having just been built); the sequential
+// peak detector then steps through them with every lane holding the same
+// state: a chunk whose extremes show that it cannot change the state
+// (most chunks: a line has a few peaks) only moves the running extreme;
+// otherwise a warp scan of the running maximum (or minimum) finds the
+// first sample of the 32 that changes the state, everything before it
+// moves only the running extreme, and the scan resumes after it -- no
+// shared memory, no divergence.  The highest peaks are kept one per lane,
+// the list shifted by a warp shuffle on the rare insertion.  The expansion
+// into trajectory entries is one thread per (line, slot).
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
@@ -39,58 +42,22 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPkWarps = 4;
+#ifdef MORSE_PK_MINB
+#define MORSE_PK_BOUNDS __launch_bounds__(kPkWarps * 32, MORSE_PK_MINB)
+#else
+#define MORSE_PK_BOUNDS __launch_bounds__(kPkWarps * 32)
+#endif
 
-// Warp w takes line w % n_lines of map w / n_lines: the map A0, or As[m]
-// of a batch of maps of one geometry (more warps per SM than one map's
-// lines give).  Outputs of map m, line j at index m n_lines + j.
-__global__ void __launch_bounds__(kPkWarps * 32)
-    k_line_peaks(const float *__restrict__ A0,
-                 const float *const *__restrict__ As, int n_maps, int npix,
-                 double L, const double *__restrict__ lu,
-                 const double *__restrict__ lc,
-                 const double *__restrict__ ls, const double *__restrict__ lsh,
-                 int n_lines, int sub, float r, int max_peaks,
-                 int *__restrict__ count, double *__restrict__ pos,
-                 double *__restrict__ height, unsigned *__restrict__ err) {
-  const int lane = threadIdx.x & 31;
-  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= (long long)n_lines * n_maps) return;  // warp-uniform, no barrier
-  const int mi = (int)(w / n_lines);
-  const int line = (int)(w - (long long)mi * n_lines);
-  const float *__restrict__ A = As ? As[mi] : A0;
-  const long long out = w;  // mi n_lines + line
-  const double u = lu[line], c = lc[line], s = ls[line], sh = lsh[line];
-  // the line in texel coordinates, p = a tau + b, in FP64 then FP32
-  const double dlt = __ddiv_rn(__dmul_rn(2.0, L), (double)npix);
-  const double h = __ddiv_rn(dlt, (double)sub);
-  const double ax = __ddiv_rn(c, dlt), ay = __ddiv_rn(s, dlt);
-  const double bx =
-      __dsub_rn(__ddiv_rn(__dsub_rn(L, __dmul_rn(u, s)), dlt), 0.5);
-  const double by =
-      __dsub_rn(__ddiv_rn(__dadd_rn(L, __dmul_rn(u, c)), dlt), 0.5);
-  const float axf = __double2float_rn(ax), ayf = __double2float_rn(ay);
-  const float bxf = __double2float_rn(bx), byf = __double2float_rn(by);
-  const float hf = __double2float_rn(h);
+// The sequential peak detector on one line of one map, with the line's
+// set-up (FP32 line p = a tau + b, the sample run [k0, k1]) done by the
+// caller; writes count[out], pos and height[out * max_peaks + q].
+__device__ __forceinline__ void detect_line(
+    const float *__restrict__ A, int npix, int lane, int K, int k0, int k1,
+    float axf, float ayf, float bxf, float byf, float hf, double h,
+    double sh, float r, int max_peaks, long long out, int *__restrict__ count,
+    double *__restrict__ pos, double *__restrict__ height,
+    unsigned *__restrict__ err) {
   const float lo = -0.5f, hi = (float)npix - 0.5f, pmax = (float)(npix - 1);
-  const int K = sub * npix;
-  // Samples inside the map form one run of k (p is monotone in k); a
-  // superset of it from the FP64 line, two samples wider on each side.
-  int k0 = -K, k1 = K;
-  auto clip = [&](double a, double b, float bf) {
-    const double ah = a * h;
-    if (ah != 0.0) {
-      const double ka = (-0.5 - b) / ah, kb = ((double)npix - 0.5 - b) / ah;
-      double f0 = floor(fmin(ka, kb)) - 2.0, f1 = ceil(fmax(ka, kb)) + 2.0;
-      f0 = fmin(fmax(f0, (double)-K), (double)K + 1.0);
-      f1 = fmin(fmax(f1, (double)-K - 1.0), (double)K);
-      k0 = max(k0, (int)f0);
-      k1 = min(k1, (int)f1);
-    } else if (!(bf > lo && bf < hi)) {  // a = 0: p = b for every sample
-      k1 = k0 - 1;
-    }
-  };
-  clip(ax, bx, bxf);
-  clip(ay, by, byf);
   // The detector's state is the same in every lane (each step reads one
   // broadcast sample), so its branches are warp-uniform.  Kept peak q
   // (highest first) lives in lane q.
@@ -99,41 +66,44 @@ __global__ void __launch_bounds__(kPkWarps * 32)
   float mn = CUDART_INF_F, mx = -CUDART_INF_F;
   float kh = -CUDART_INF_F;
   int kk = 0;
+  // The superset must start and end outside the map (unless it reaches
+  // the ends of the sampled range): otherwise samples were missed.  The
+  // first sample and the last are tested once, as the chunk loop below
+  // decides inside.
+  if (k0 <= k1) {
+    const int ke = lane == 0 ? k0 : k1;
+    const float te = __fmul_rn((float)ke, hf);
+    const float ex = __fadd_rn(__fmul_rn(axf, te), bxf);
+    const float ey = __fadd_rn(__fmul_rn(ayf, te), byf);
+    const bool ein = ex > lo && ex < hi && ey > lo && ey < hi;
+    if ((lane == 0 && ein && k0 > -K) || (lane == 1 && ein && k1 < K))
+      atomicOr(err, 1u);
+  }
   for (int kb = k0; kb <= k1; kb += 32) {
+    // Every lane evaluates its sample, branch-free: the clamps keep the
+    // texel reads inside the map, and only the samples of the run inside
+    // the map (in) count.
     const int k = kb + lane;
-    float v = 0.f;
-    bool in = false;
-    if (k <= k1) {
-      const float tk = __fmul_rn((float)k, hf);
-      const float px = __fadd_rn(__fmul_rn(axf, tk), bxf);
-      const float py = __fadd_rn(__fmul_rn(ayf, tk), byf);
-      in = px > lo && px < hi && py > lo && py < hi;
-      if (in) {
-        float qx = px < 0.f ? 0.f : px, qy = py < 0.f ? 0.f : py;
-        if (qx > pmax) qx = pmax;
-        if (qy > pmax) qy = pmax;
-        int i0 = (int)floorf(qx), j0 = (int)floorf(qy);
-        if (i0 > npix - 2) i0 = npix - 2;
-        if (j0 > npix - 2) j0 = npix - 2;
-        const float fx = __fsub_rn(qx, (float)i0);
-        const float fy = __fsub_rn(qy, (float)j0);
-        const float *row = A + (size_t)j0 * npix + i0;
-        const float a00 = __ldg(row), a10 = __ldg(row + 1);
-        const float a01 = __ldg(row + npix), a11 = __ldg(row + npix + 1);
-        const float gx = __fsub_rn(1.f, fx), gy = __fsub_rn(1.f, fy);
-        const float r0 = __fadd_rn(__fmul_rn(gx, a00), __fmul_rn(fx, a10));
-        const float r1 = __fadd_rn(__fmul_rn(gx, a01), __fmul_rn(fx, a11));
-        v = __fadd_rn(__fmul_rn(gy, r0), __fmul_rn(fy, r1));
-      }
-    }
+    const float tk = __fmul_rn((float)k, hf);
+    const float px = __fadd_rn(__fmul_rn(axf, tk), bxf);
+    const float py = __fadd_rn(__fmul_rn(ayf, tk), byf);
+    const bool in = k <= k1 && px > lo && px < hi && py > lo && py < hi;
+    float qx = px < 0.f ? 0.f : px, qy = py < 0.f ? 0.f : py;
+    if (qx > pmax) qx = pmax;
+    if (qy > pmax) qy = pmax;
+    int i0 = (int)floorf(qx), j0 = (int)floorf(qy);
+    if (i0 > npix - 2) i0 = npix - 2;
+    if (j0 > npix - 2) j0 = npix - 2;
+    const float fx = __fsub_rn(qx, (float)i0);
+    const float fy = __fsub_rn(qy, (float)j0);
+    const float *row = A + (size_t)j0 * npix + i0;
+    const float a00 = __ldg(row), a10 = __ldg(row + 1);
+    const float a01 = __ldg(row + npix), a11 = __ldg(row + npix + 1);
+    const float gx = __fsub_rn(1.f, fx), gy = __fsub_rn(1.f, fy);
+    const float r0 = __fadd_rn(__fmul_rn(gx, a00), __fmul_rn(fx, a10));
+    const float r1 = __fadd_rn(__fmul_rn(gx, a01), __fmul_rn(fx, a11));
+    const float v = __fadd_rn(__fmul_rn(gy, r0), __fmul_rn(fy, r1));
     const unsigned m = __ballot_sync(kFull, in);
-    // the superset must start and end outside the map (unless it reaches
-    // the ends of the sampled range): otherwise samples were missed
-    if (lane == 0) {
-      if (kb == k0 && (m & 1u) && k0 > -K) atomicOr(err, 1u);
-      if (k1 - kb < 32 && ((m >> (k1 - kb)) & 1u) && k1 < K)
-        atomicOr(err, 1u);
-    }
     if (m == 0u) continue;
     // Most chunks cannot change the detector's state, which the chunk's
     // extremes show (one integer reduction each: the samples are
@@ -181,7 +151,7 @@ __global__ void __launch_bounds__(kPkWarps * 32)
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const float y = __shfl_up_sync(kFull, pm, o);
-          if (lane >= o) pm = fmaxf(pm, y);
+          pm = fmaxf(pm, y);  // lanes below o get their own value
         }
         pm = fmaxf(pm, mx);
         const unsigned f = __ballot_sync(kFull, a && pm > __fmul_rn(r, v));
@@ -220,7 +190,7 @@ __global__ void __launch_bounds__(kPkWarps * 32)
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const float y = __shfl_up_sync(kFull, pn, o);
-          if (lane >= o) pn = fminf(pn, y);
+          pn = fminf(pn, y);
         }
         pn = fminf(pn, mn);
         const unsigned f = __ballot_sync(kFull, a && v > __fmul_rn(r, pn));
@@ -254,6 +224,81 @@ __global__ void __launch_bounds__(kPkWarps * 32)
       height[o] = CUDART_NAN;
     }
   }
+}
+
+// Warp w takes line w % n_lines of map w / n_lines: the map A0, or As[m]
+// of a batch of maps of one geometry (more warps per SM than one map's
+// lines give).  Outputs of map m, line j at index m n_lines + j.  Slower
+// on 64 maps, and not kept: a warp running one line on several maps (its
+// set-up shared; fewer warps), reading a chunk's texels while the chunk
+// before it is scanned, and steps of 2 or 4 chunks under one test.
+__global__ void MORSE_PK_BOUNDS
+    k_line_peaks(const float *__restrict__ A0,
+                 const float *const *__restrict__ As, int n_maps, int npix,
+                 double L, double dlt, double h,
+                 const double *__restrict__ lu,
+                 const double *__restrict__ lc,
+                 const double *__restrict__ ls, const double *__restrict__ lsh,
+                 int n_lines, int sub, float r, int max_peaks,
+                 int *__restrict__ count, double *__restrict__ pos,
+                 double *__restrict__ height, unsigned *__restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= (long long)n_lines * n_maps) return;  // warp-uniform, no barrier
+  const int mi = (int)(w / n_lines);
+  const int line = (int)(w - (long long)mi * n_lines);
+  const double u = lu[line], c = lc[line], s = ls[line], sh = lsh[line];
+  // The line in texel coordinates, p = a tau + b, in FP64 then FP32, with
+  // the texel size dlt = 2 L / npix and the step h = dlt / sub (both
+  // rounded once, by the caller).  The set-up's divisions are spread over
+  // lanes 0-3, one quotient each (the FP64 pipe is narrow): ax, ay, bx, by.
+  const int l4 = lane & 3;
+  const double num = l4 == 0   ? c
+                     : l4 == 1 ? s
+                     : l4 == 2 ? __dsub_rn(L, __dmul_rn(u, s))
+                               : __dadd_rn(L, __dmul_rn(u, c));
+  double q = __ddiv_rn(num, dlt);
+  if (l4 >= 2) q = __dsub_rn(q, 0.5);
+  const float qf = __double2float_rn(q);
+  const double ax = __shfl_sync(kFull, q, 0), ay = __shfl_sync(kFull, q, 1);
+  const double bx = __shfl_sync(kFull, q, 2), by = __shfl_sync(kFull, q, 3);
+  const float axf = __shfl_sync(kFull, qf, 0), ayf = __shfl_sync(kFull, qf, 1);
+  const float bxf = __shfl_sync(kFull, qf, 2), byf = __shfl_sync(kFull, qf, 3);
+  const float hf = __double2float_rn(h);
+  const float lo = -0.5f, hi = (float)npix - 0.5f;
+  const int K = sub * npix;
+  // Samples inside the map form one run of k (p is monotone in k); a
+  // superset of it from the FP64 line, two samples wider on each side:
+  // per axis the k where p crosses -0.5 and npix - 0.5 (lanes 0-3 again:
+  // x low, x high, y low, y high), then lanes 0 (x) and 1 (y) round and
+  // clamp their axis's interval, [-K, -K - 1] (empty) for an axis along
+  // which the line is constant outside the map.
+  const double ahx = ax * h, ahy = ay * h;
+  const double bb = l4 < 2 ? bx : by;
+  const double kq =
+      ((l4 & 1) ? ((double)npix - 0.5 - bb) : (-0.5 - bb)) /
+      (l4 < 2 ? ahx : ahy);  // unused where the divisor is 0
+  int c0 = -K, c1 = K;
+  {
+    const int ax_i = lane & 1;
+    const double ka = __shfl_sync(kFull, kq, 2 * ax_i);
+    const double kb = __shfl_sync(kFull, kq, 2 * ax_i + 1);
+    const double ah = ax_i ? ahy : ahx;
+    const float bf = ax_i ? byf : bxf;
+    if (ah != 0.0) {
+      double f0 = floor(fmin(ka, kb)) - 2.0, f1 = ceil(fmax(ka, kb)) + 2.0;
+      f0 = fmin(fmax(f0, (double)-K), (double)K + 1.0);
+      f1 = fmin(fmax(f1, (double)-K - 1.0), (double)K);
+      c0 = (int)f0;
+      c1 = (int)f1;
+    } else if (!(bf > lo && bf < hi)) {  // a = 0: p = b for every sample
+      c1 = -K - 1;
+    }
+  }
+  const int k0 = max(__shfl_sync(kFull, c0, 0), __shfl_sync(kFull, c0, 1));
+  const int k1 = min(__shfl_sync(kFull, c1, 0), __shfl_sync(kFull, c1, 1));
+  detect_line(As ? As[mi] : A0, npix, lane, K, k0, k1, axf, ayf, bxf, byf, hf,
+              h, sh, r, max_peaks, w, count, pos, height, err);
 }
 
 // Entry (line j, slot) of the peak-aligned line grid, one thread each.
@@ -323,9 +368,12 @@ cudaError_t launch_line_peaks(const float *A, const float *const *As,
   const long long warps = (long long)n_lines * n_maps;
   if (warps <= 0) return cudaSuccess;
   const long long blocks = (warps + kPkWarps - 1) / kPkWarps;
+  // texel size and step, each one correctly rounded FP64 operation
+  const double dlt = (2.0 * L) / (double)npix;
+  const double h = dlt / (double)sub;
   k_line_peaks<<<(unsigned)blocks, kPkWarps * 32, 0, st>>>(
-      A, As, n_maps, npix, L, lu, lc, ls, lsh, n_lines, sub, r, max_peaks,
-      count, pos, height, err);
+      A, As, n_maps, npix, L, dlt, h, lu, lc, ls, lsh, n_lines, sub, r,
+      max_peaks, count, pos, height, err);
   return cudaGetLastError();
 }
 

@@ -2955,11 +2955,13 @@ morse_status enqueue_peak_lib(morse_ctx *ctx, const morse_map *map,
                               const morse_peak_opts *o) {
   MORSE_CUDA(ctx, cudaMemsetAsync(L.err, 0, sizeof(unsigned), ctx->stream));
   const float r = (float)(1.0 + o->delta);
+  const int tr = t_begin(ctx, KT_PEAKS);
   MORSE_CUDA(ctx, morse::launch_line_peaks(
                       map->A, nullptr, 1, map->npix, map->L, L.lines,
                       L.lines + n, L.lines + 2 * (size_t)n,
                       L.lines + 3 * (size_t)n, n, o->sub, r, o->max_peaks,
                       L.count, L.pos, L.height, L.err, ctx->stream));
+  t_end(ctx, tr);
   ctx->launches += 1;
   return MORSE_OK;
 }
@@ -3039,11 +3041,13 @@ morse_status morse_line_peaks_batch(morse_ctx *ctx,
   MORSE_CUDA(ctx, cudaMemsetAsync(L.err, 0, sizeof(unsigned), ctx->stream));
   const float r = (float)(1.0 + opts->delta);
   const int n = n_lines;
+  const int tr = t_begin(ctx, KT_PEAKS);
   MORSE_CUDA(ctx, morse::launch_line_peaks(
                       nullptr, L.maps, n_maps, maps[0]->npix, maps[0]->L,
                       L.lines, L.lines + n, L.lines + 2 * (size_t)n,
                       L.lines + 3 * (size_t)n, n, opts->sub, r, P, L.count,
                       L.pos, L.height, L.err, ctx->stream));
+  t_end(ctx, tr);
   ctx->launches += 1;
   unsigned err = 0;
   MORSE_CUDA(ctx, cudaMemcpyAsync(count, L.count, sizeof(int) * nm,

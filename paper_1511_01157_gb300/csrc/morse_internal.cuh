@@ -13,7 +13,7 @@
 
 // kernel kinds timed per call (morse_last_kernel_ms)
 enum { KT_RAY = 0, KT_MAP = 1, KT_SEARCH = 2, KT_MERGE = 3, KT_FILL = 4,
-       KT_ADJ = 5, KT_LM = 6, KT_COUNT = 8 };
+       KT_ADJ = 5, KT_LM = 6, KT_PEAKS = 7, KT_COUNT = 8 };
 
 struct morse_ctx {
   int device;
