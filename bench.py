@@ -288,6 +288,14 @@ def peak_library(ctx, m, cfg, delta=0.1, max_peaks=8):
         ktb.append(ctx.kernel_ms(7))
     for mp in maps:
         mp.free()
+    # ALU roofline of a sample: about 20 FP32 instructions (its position,
+    # the clamps, the bilinear lookup and the comparisons) on every lane
+    # of every SM at the maximum clock
+    pk, pk_kind = measured_peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = float(pk.get("sm_max_mhz", 2070.0))
+    roof = sms * 128 * mhz * 1e6 / 20.0
+    bk = 64 * n / min(ktb) * 1e3
     return {"lines": len(lines), "ms": 1e3 * t, "samples": n,
             "samples_per_s": n / t, "delta": delta,
             "kernel_ms": min(kt), "kernel_samples_per_s": n / min(kt) * 1e3,
@@ -298,7 +306,13 @@ def peak_library(ctx, m, cfg, delta=0.1, max_peaks=8):
             "batch_64_maps_ms": 1e3 * min(tb),
             "batch_samples_per_s": 64 * n / min(tb),
             "batch_kernel_ms": min(ktb),
-            "batch_kernel_samples_per_s": 64 * n / min(ktb) * 1e3,
+            "batch_kernel_samples_per_s": bk,
+            "roofline": {"bound": "alu", "achieved": bk, "peak": roof,
+                         "unit": "samples/s", "frac": bk / roof,
+                         "peak_source": f"{sms} SMs x 128 FP32 lanes x "
+                                        f"{mhz} MHz ({pk_kind} sm_max_mhz)"
+                                        " / 20 instructions per sample",
+                         "kernel": "k_line_peaks, the 64-map launch"},
             "note": "samples of the lines inside the map, every half "
                     "texel; the batch is one launch over 64 maps' lines; "
                     "ms: the C-ABI call, device synchronised (host copies "
