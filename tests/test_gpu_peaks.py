@@ -75,7 +75,11 @@ def _all_lines(m, ctx):
 def _compare_library(ctx, mp, A, lines, sub, max_peaks, delta):
     c, p, h = ctx.line_peaks(mp, lines, sub=sub, max_peaks=max_peaks,
                              delta=delta)
-    co, po, ho, eo, unsure = orc.line_peaks(A, L_, lines, sub=sub,
+    return _check_library(c, p, h, A, L_, lines, sub, max_peaks, delta)
+
+
+def _check_library(c, p, h, A, L, lines, sub, max_peaks, delta):
+    co, po, ho, eo, unsure = orc.line_peaks(A, L, lines, sub=sub,
                                             delta=delta,
                                             max_peaks=max_peaks,
                                             bounds=True)
@@ -221,6 +225,35 @@ def test_peak_search_all_cut_and_errors(ctx, m, amap):
     with pytest.raises(m.MorseError) as e:  # two peak times fix tE
         ctx.peak_search(ev, mp, g, lines, tp=tps)
     assert e.value.status == m.EINVAL
+
+
+def test_library_config1_full_size(ctx, m):
+    # The timed workload at full size, in its launch form: the 2880 (u0,
+    # alpha) lines of the config-1 grid on 1024^2 maps of 10^8 FP32 rays
+    # (the truth lens and a resonant one), both maps in one
+    # morse_line_peaks_batch launch, two samples per texel, the 8 highest
+    # peaks kept, delta 0.1; a seeded sample of 160 lines of each map
+    # against the oracle on that map's values.
+    cfg = synth.CFG1
+    g = cfg["grid"]
+    u0 = np.exp(np.linspace(np.log(g["u0_lo"]), np.log(g["u0_hi"]),
+                            g["n_u0"]))
+    lines = np.array([(u, 2 * math.pi * k / g["n_alpha"], 0.0) for u in u0
+                      for k in range(g["n_alpha"])])
+    maps = [ctx.build_map(s, q, cfg["L"], cfg["npix"], cfg["nray"],
+                          image_halfwidth=cfg["X"], deflect="fp32")
+            for s, q in ((cfg["s"], cfg["q"]), (1.0, 1e-2))]
+    cb, pb, hb = ctx.line_peaks_batch(maps, lines, sub=2, max_peaks=8,
+                                      delta=0.1)
+    rng = np.random.default_rng(11)
+    for k, mp in enumerate(maps):
+        pick = np.sort(rng.choice(len(lines), 160, replace=False))
+        c, co, unsure = _check_library(cb[k][pick], pb[k][pick],
+                                       hb[k][pick], mp.values(), cfg["L"],
+                                       lines[pick], 2, 8, 0.1)
+        assert unsure.mean() <= 0.5
+        assert co[~unsure].max() >= 2
+        mp.free()
 
 
 def test_library_batch_over_maps_equals_per_map(ctx, m):
