@@ -42,11 +42,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPkWarps = 4;
-#ifdef MORSE_PK_MINB
-#define MORSE_PK_BOUNDS __launch_bounds__(kPkWarps * 32, MORSE_PK_MINB)
-#else
-#define MORSE_PK_BOUNDS __launch_bounds__(kPkWarps * 32)
-#endif
 
 // The sequential peak detector on one line of one map, with the line's
 // set-up (FP32 line p = a tau + b, the sample run [k0, k1]) done by the
@@ -232,7 +227,7 @@ __device__ __forceinline__ void detect_line(
 // on 64 maps, and not kept: a warp running one line on several maps (its
 // set-up shared; fewer warps), reading a chunk's texels while the chunk
 // before it is scanned, and steps of 2 or 4 chunks under one test.
-__global__ void MORSE_PK_BOUNDS
+__global__ void __launch_bounds__(kPkWarps * 32)
     k_line_peaks(const float *__restrict__ A0,
                  const float *const *__restrict__ As, int n_maps, int npix,
                  double L, double dlt, double h,
